@@ -1,0 +1,326 @@
+"""Python side of the FP64 CPU oracle for the frozen Gaussian approximation (FGA).
+
+THIS MODULE IS TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.  It shares no code
+with the CUDA library (``paper_1810_06760_gb300``) and never imports it.
+
+It compiles ``fga_oracle.c`` with gcc on first use (into ``oracle/_build/``) and drives it
+through ctypes.  Everything is FP64.  The three steps follow the paper's algorithm
+(Fig. ``fig:FGA_alg``): decompose the initial data into Gaussian packets (Eqs. psi, alpha^k),
+propagate every packet with RK4 (Eqs. char_plus, char_minus, amp_P, amp_SV, amp_SH, DzDt),
+and sum the packets (Eq. FGA).
+
+Parity status: every routine here is pinned by ``tests/test_oracle_*.py`` against closed forms,
+invariants, brute force or an independent formulation; see the test docstrings.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fga_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libfga_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CLS_PP, CLS_PM, CLS_SP, CLS_SM = 0, 1, 2, 3
+META_REF_E1 = 4
+META_VECTOR = 8
+STATE_DOUBLES = 48
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, FP64, OpenMP over independent beams)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-std=gnu11", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads the oracle uses (beams and points are independent)."""
+    lib()
+    gomp = C.CDLL("libgomp.so.1")
+    gomp.omp_set_num_threads(int(n))
+
+
+def get_threads() -> int:
+    lib()
+    gomp = C.CDLL("libgomp.so.1")
+    gomp.omp_get_max_threads.restype = C.c_int
+    return int(gomp.omp_get_max_threads())
+
+
+class _Model(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int),
+        ("cp0", C.c_double), ("cs0", C.c_double),
+        ("amp", C.c_double), ("cs_ratio", C.c_double),
+        ("n", C.c_int * 3), ("o", C.c_double * 3), ("h", C.c_double * 3),
+        ("gp", C.c_void_p), ("gs", C.c_void_p),
+        ("nlay", C.c_int),
+        ("zif", C.c_void_p), ("lcp", C.c_void_p), ("lcs", C.c_void_p), ("lrho", C.c_void_p),
+    ]
+
+
+_P = C.c_void_p
+
+
+def _declare(L):
+    L.orc_model_eval_many.argtypes = [_P, C.c_int, C.c_int, _P, _P]
+    L.orc_fbi_direct.argtypes = [_P, _P, _P, _P, C.c_double, C.c_int, _P, _P, C.c_int, _P, _P, _P]
+    L.orc_fbi_separable.argtypes = L.orc_fbi_direct.argtypes
+    L.orc_beam_init.argtypes = [_P, C.c_double, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P,
+                                C.c_int, C.c_int, _P, _P]
+    L.orc_rhs_many.argtypes = [_P, C.c_int, _P, _P, _P]
+    L.orc_propagate.argtypes = [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int, _P, _P,
+                                C.c_double, _P]
+    L.orc_records.argtypes = [C.c_int, _P, _P, C.c_double, _P]
+    L.orc_gauss_sum.argtypes = [C.c_int, _P, C.c_double, C.c_double, C.c_int, _P, _P]
+    L.orc_bin_keys_f32.argtypes = [C.c_int, _P, _P, C.c_float, _P, _P]
+    L.orc_bin_sort.argtypes = [C.c_int, _P, C.c_int, _P, _P]
+    L.orc_s_ref_e1.argtypes = [_P]
+    L.orc_s_ref_e1.restype = C.c_int
+    if hasattr(L, "orc_interface_event"):
+        L.orc_interface_event.argtypes = [_P, C.c_int, _P, C.c_int, C.c_int, _P, _P, _P]
+        L.orc_interface_event.restype = C.c_int
+    if hasattr(L, "orc_zoeppritz_p"):
+        L.orc_zoeppritz_p.argtypes = [C.c_double] * 7 + [_P, _P]
+        L.orc_zoeppritz_p.restype = C.c_int
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _d3(v):
+    return np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(3))
+
+
+class Model:
+    """Velocity model for the oracle.  kinds: 'const', 'sine', 'grid', 'layered'."""
+
+    def __init__(self, kind: str, *, cp0=2.0, cs0=1.0, amp=0.0, cs_ratio=1.0 / math.sqrt(3.0),
+                 grid_p=None, grid_s=None, origin=(0, 0, 0), spacing=(1, 1, 1),
+                 z_interfaces=(), layer_cp=(), layer_cs=(), layer_rho=()):
+        s = _Model()
+        self._keep = []
+        s.kind = {"const": 0, "sine": 1, "grid": 2, "layered": 3}[kind]
+        s.cp0, s.cs0, s.amp, s.cs_ratio = cp0, cs0, amp, cs_ratio
+        if kind == "grid":
+            gp = np.ascontiguousarray(grid_p, dtype=np.float32)
+            gs = np.ascontiguousarray(grid_s, dtype=np.float32)
+            assert gp.ndim == 4 and gp.shape[3] == 10 and gs.shape == gp.shape
+            self._keep += [gp, gs]
+            s.n[:] = gp.shape[:3]
+            s.o[:] = [float(v) for v in origin]
+            s.h[:] = [float(v) for v in spacing]
+            s.gp, s.gs = gp.ctypes.data, gs.ctypes.data
+        if kind == "layered":
+            zi = np.ascontiguousarray(z_interfaces, dtype=np.float64)
+            lc = np.ascontiguousarray(layer_cp, dtype=np.float64)
+            ls = np.ascontiguousarray(layer_cs, dtype=np.float64)
+            lr = np.ascontiguousarray(layer_rho, dtype=np.float64)
+            assert lc.size == zi.size + 1 == ls.size == lr.size
+            self._keep += [zi, lc, ls, lr]
+            s.nlay = lc.size
+            s.zif, s.lcp, s.lcs, s.lrho = zi.ctypes.data, lc.ctypes.data, ls.ctypes.data, lr.ctypes.data
+        self.s = s
+        self.kind = kind
+
+    @property
+    def ptr(self):
+        return C.cast(C.pointer(self.s), C.c_void_p)
+
+    def eval(self, wave: int, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+        out = np.zeros((x.shape[0], 10))
+        lib().orc_model_eval_many(self.ptr, int(wave), x.shape[0], _ptr(x), _ptr(out))
+        return out
+
+
+class Mesh:
+    """Tensor (q, p) mesh: q_{d,i} = q0[d] + i dq[d] (nq per axis), p_{d,j} = p0[d] + j dp[d]."""
+
+    def __init__(self, nq, q0, dq, np_, p0, dp):
+        self.nq, self.np = int(nq), int(np_)
+        self.q0, self.dq, self.p0, self.dp = _d3(q0), _d3(dq), _d3(p0), _d3(dp)
+
+    @property
+    def M(self):
+        return self.nq ** 3 * self.np ** 3
+
+    def weight(self, k: float) -> float:
+        """delta q delta p / (2 pi / k)^{9/2}, the quadrature weight of Eq. FGA."""
+        return float(np.prod(self.dq) * np.prod(self.dp) / (2.0 * math.pi / k) ** 4.5)
+
+    def points(self):
+        """(q, p) of every mesh point, mesh order (q-major, p-minor)."""
+        iq = np.arange(self.nq)
+        ip = np.arange(self.np)
+        Q = np.stack(np.meshgrid(iq, iq, iq, indexing="ij"), -1).reshape(-1, 3) * self.dq + self.q0
+        P = np.stack(np.meshgrid(ip, ip, ip, indexing="ij"), -1).reshape(-1, 3) * self.dp + self.p0
+        q = np.repeat(Q, P.shape[0], axis=0)
+        p = np.tile(P, (Q.shape[0], 1))
+        return q, p
+
+
+def fbi(f: np.ndarray, y0, dy, k: float, mesh: Mesh, method: str = "separable") -> np.ndarray:
+    """Wave-packet transform F(q,p) = sum_y f(y) exp(-ik p.(y-q) - k|y-q|^2/2) dy^3 (Eq. psi).
+
+    f: complex [ny0, ny1, ny2, 3] sampled at y0 + i*dy.  Returns complex [M, 3] in mesh order."""
+    f = np.ascontiguousarray(f, dtype=np.complex128)
+    ny = np.ascontiguousarray(f.shape[:3], dtype=np.int32)
+    F = np.zeros((mesh.M, 3), dtype=np.complex128)
+    fn = lib().orc_fbi_separable if method == "separable" else lib().orc_fbi_direct
+    fn(_ptr(ny), _ptr(_d3(y0)), _ptr(_d3(dy)), _ptr(f), float(k), mesh.nq, _ptr(mesh.q0), _ptr(mesh.dq),
+       mesh.np, _ptr(mesh.p0), _ptr(mesh.dp), _ptr(F))
+    return F
+
+
+def beam_init(model: Model, k: float, mesh: Mesh, F: np.ndarray, G, cls: int, vector_form: bool = False):
+    """Beams of one class (0 P+, 1 P-, 2 S+, 3 S-) at t = 0.  Returns (state [M,48], meta [M])."""
+    F = np.ascontiguousarray(F, dtype=np.complex128)
+    Gp = None
+    if G is not None:
+        G = np.ascontiguousarray(G, dtype=np.complex128)
+        Gp = _ptr(G)
+    st = np.zeros((mesh.M, STATE_DOUBLES))
+    meta = np.zeros(mesh.M, dtype=np.int32)
+    lib().orc_beam_init(model.ptr, float(k), mesh.nq, _ptr(mesh.q0), _ptr(mesh.dq), mesh.np, _ptr(mesh.p0),
+                        _ptr(mesh.dp), _ptr(F), Gp, int(cls), int(bool(vector_form)), _ptr(st), _ptr(meta))
+    return st, meta
+
+
+def rhs(model: Model, st: np.ndarray, meta: np.ndarray) -> np.ndarray:
+    st = np.ascontiguousarray(st, dtype=np.float64)
+    meta = np.ascontiguousarray(meta, dtype=np.int32)
+    out = np.zeros_like(st)
+    lib().orc_rhs_many(model.ptr, st.shape[0], _ptr(st), _ptr(meta), _ptr(out))
+    return out
+
+
+def sample_schedule(times, dt: float, nsteps: int, t0: float = 0.0):
+    """Step index and fraction of each sample time: n = min(floor((t - t0)/dt), nsteps - 1),
+    theta = (t - t0)/dt - n."""
+    times = np.asarray(times, dtype=np.float64)
+    u = (times - t0) / dt
+    n = np.minimum(np.floor(u), nsteps - 1).astype(np.int32)
+    th = u - n
+    return n, th
+
+
+def propagate(model: Model, st: np.ndarray, meta: np.ndarray, dt: float, nsteps: int,
+              s_step=None, s_theta=None, w: float = 1.0):
+    """RK4 (in place on st) with reconstruction records at the scheduled samples: [ns, nb, 12]."""
+    assert st.flags.c_contiguous and st.dtype == np.float64
+    meta = np.ascontiguousarray(meta, dtype=np.int32)
+    if s_step is None:
+        s_step = np.zeros(0, dtype=np.int32)
+        s_theta = np.zeros(0)
+    s_step = np.ascontiguousarray(s_step, dtype=np.int32)
+    s_theta = np.ascontiguousarray(s_theta, dtype=np.float64)
+    assert np.all(np.diff(s_step) >= 0)
+    nb = st.shape[0]
+    rec = np.zeros((s_step.size, nb, 12))
+    lib().orc_propagate(model.ptr, nb, _ptr(st), _ptr(meta), float(dt), int(nsteps), s_step.size,
+                        _ptr(s_step), _ptr(s_theta), float(w), _ptr(rec))
+    return rec
+
+
+def records(st: np.ndarray, meta: np.ndarray, w: float) -> np.ndarray:
+    st = np.ascontiguousarray(st, dtype=np.float64)
+    meta = np.ascontiguousarray(meta, dtype=np.int32)
+    rec = np.zeros((st.shape[0], 12))
+    lib().orc_records(st.shape[0], _ptr(st), _ptr(meta), float(w), _ptr(rec))
+    return rec
+
+
+def gauss_sum(rec: np.ndarray, k: float, rw: float, x: np.ndarray) -> np.ndarray:
+    """u(x) = sum_b A_b exp(ik P_b.(x-Q_b) - k|x-Q_b|^2/2) (Eq. FGA); rw <= 0: every beam."""
+    rec = np.ascontiguousarray(rec, dtype=np.float64).reshape(-1, 12)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    u = np.zeros((x.shape[0], 3), dtype=np.complex128)
+    lib().orc_gauss_sum(rec.shape[0], _ptr(rec), float(k), float(rw), x.shape[0], _ptr(x), _ptr(u))
+    return u
+
+
+def bin_keys_f32(Q: np.ndarray, origin, inv_h: float, nc) -> np.ndarray:
+    Q = np.ascontiguousarray(Q, dtype=np.float32).reshape(-1, 3)
+    o = np.ascontiguousarray(origin, dtype=np.float32).reshape(3)
+    nc = np.ascontiguousarray(nc, dtype=np.int32).reshape(3)
+    key = np.zeros(Q.shape[0], dtype=np.int32)
+    lib().orc_bin_keys_f32(Q.shape[0], _ptr(Q), _ptr(o), C.c_float(np.float32(inv_h)), _ptr(nc), _ptr(key))
+    return key
+
+
+def bin_sort(key: np.ndarray, ncells: int):
+    key = np.ascontiguousarray(key, dtype=np.int32)
+    perm = np.zeros(key.size, dtype=np.int32)
+    start = np.zeros(ncells + 1, dtype=np.int32)
+    lib().orc_bin_sort(key.size, _ptr(key), int(ncells), _ptr(perm), _ptr(start))
+    return perm, start
+
+
+# --------------------------------------------------------------------------------------------
+# views of the 48-double state
+# --------------------------------------------------------------------------------------------
+
+def state_Q(st):
+    return st[:, 0:3]
+
+
+def state_P(st):
+    return st[:, 3:6]
+
+
+def state_DQ(st):
+    """dz Q as complex [nb, 3, 3], row m = d/dz_m."""
+    return st[:, 6:24].view(np.complex128).reshape(-1, 3, 3)
+
+
+def state_DP(st):
+    return st[:, 24:42].view(np.complex128).reshape(-1, 3, 3)
+
+
+def state_a(st):
+    return st[:, 42:48].view(np.complex128).reshape(-1, 3)
+
+
+# --------------------------------------------------------------------------------------------
+# the whole forward solve, step by step (Fig. fig:FGA_alg)
+# --------------------------------------------------------------------------------------------
+
+def solve(model: Model, k: float, mesh: Mesh, F: np.ndarray, G, classes, dt: float, nsteps: int,
+          times, x: np.ndarray, rw: float, vector_form: bool = False):
+    """Decomposed data (F, G) -> beams of the given classes -> RK4 -> Gaussian sums at points x
+    and sample times.  Returns complex [ns, nx, 3]."""
+    s_step, s_theta = sample_schedule(times, dt, nsteps)
+    w = mesh.weight(k)
+    out = np.zeros((len(times), x.shape[0], 3), dtype=np.complex128)
+    for cls in classes:
+        st, meta = beam_init(model, k, mesh, F, G, cls, vector_form)
+        rec = propagate(model, st, meta, dt, nsteps, s_step, s_theta, w)
+        for j in range(len(times)):
+            out[j] += gauss_sum(rec[j], k, rw, x)
+    return out

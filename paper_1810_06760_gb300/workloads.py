@@ -1,0 +1,196 @@
+"""Seeded synthetic inputs for the FGA solves (shared by the tests, the oracle and the benchmark).
+
+This module only builds inputs: media, initial data sampled on the decomposition grid, (q,p)
+meshes, receivers, sample times.  It holds none of the method's arithmetic (no transform,
+no ray or amplitude equations, no summation) and imports neither the GPU library nor the oracle.
+
+The workloads are shaped like the paper's experiments:
+  * ``homogeneous``: constant c_p = 2, c_s = 1; a rightward P packet
+    u0 = e1 exp(-k|x-x0|^2/2) exp(i k x1), v0 = -i k c_p u0 (P+ beams only); k = 32,
+    q 12^3 x p 6^3 (373,248 beams) over x0 +- 4.8/sqrt(k) and (1,0,0) +- 4.8/sqrt(k), RK4 dt = 0.005 to T = 0.5, 1,000 seeded-uniform receivers.
+  * ``smooth``: c_p = 2 + 0.2 sin(2 pi x1) sin(2 pi x2) sin(2 pi x3), c_s = c_p/sqrt(3), rho = 1,
+    sampled with its analytic derivatives on a 128^3 FP32 node grid over [0,1]^3; a packet
+    polarised neither along nor across its direction, so P, SV and SH are all excited; k = 64,
+    q 24^3 over x0 +- 6/sqrt(k) x p 8^3 over d +- 4.8/sqrt(k) (7,077,888 mesh points, x4 classes), dt = 0.0025 to T = 1, a 64^3 snapshot and
+    400 surface receivers x 1,000 samples.
+Reduced sizes of the same recipes serve as parity cases.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional, Sequence
+
+import numpy as np
+
+SQRT3 = math.sqrt(3.0)
+
+
+def mesh_radius(k: float, rho: float = 4.8) -> float:
+    """Half-width R = rho/sqrt(k) of a q or p mesh.  The wave-packet weights of a packet decay like
+    exp(-k(|q-x0|^2 + |p-p0|^2)/4), i.e. exp(-rho^2/4) at the mesh edge (rho = 4.8: 3e-3 of the peak;
+    rho = 7.43: 1e-6).  A wider mesh with the same point count aliases the phase of the
+    reconstruction integrand, so rho is chosen together with the point count."""
+    return rho / math.sqrt(k)
+
+
+def window_radius(k: float) -> float:
+    """Truncation radius 6/sqrt(k) of the Gaussian sum (exp(-k r^2/2) = e^-18 at the edge)."""
+    return 6.0 / math.sqrt(k)
+
+
+@dataclasses.dataclass
+class MeshSpec:
+    nq: int
+    q0: np.ndarray   # first q node, per axis
+    dq: np.ndarray   # q spacing, per axis
+    np_: int
+    p0: np.ndarray
+    dp: np.ndarray
+
+    @property
+    def M(self) -> int:
+        return self.nq ** 3 * self.np_ ** 3
+
+
+def centred_mesh(nq: int, qc, np_: int, pc, R: float, Rp: Optional[float] = None) -> MeshSpec:
+    """Cell-centred tensor meshes over qc +- R (nq per axis) and pc +- Rp (np per axis; Rp = R if
+    not given)."""
+    Rp = R if Rp is None else Rp
+    qc = np.asarray(qc, dtype=np.float64)
+    pc = np.asarray(pc, dtype=np.float64)
+    dq = np.full(3, 2.0 * R / nq)
+    dp = np.full(3, 2.0 * Rp / np_)
+    return MeshSpec(nq, qc - R + 0.5 * dq, dq, np_, pc - Rp + 0.5 * dp, dp)
+
+
+@dataclasses.dataclass
+class Medium:
+    kind: str                       # 'const' | 'sine' | 'grid'
+    cp0: float = 2.0
+    cs0: float = 1.0
+    amp: float = 0.0
+    cs_ratio: float = 1.0 / SQRT3
+    grid_p: Optional[np.ndarray] = None   # float32 [n0, n1, n2, 10]
+    grid_s: Optional[np.ndarray] = None
+    origin: Sequence[float] = (0.0, 0.0, 0.0)
+    spacing: Sequence[float] = (1.0, 1.0, 1.0)
+
+
+def sine_fields_on_nodes(n: int, c0: float, amp: float, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """c = c0 + amp sin(2 pi x1) sin(2 pi x2) sin(2 pi x3) with its exact gradient and Hessian,
+    sampled on an n^3 node grid over [lo, hi]^3.  Field order: c, c_1, c_2, c_3, c_11, c_12, c_13,
+    c_22, c_23, c_33.  Returns float32 [n, n, n, 10]."""
+    x = np.linspace(lo, hi, n)
+    w = 2.0 * math.pi
+    s, co = np.sin(w * x), np.cos(w * x)
+    S1, S2, S3 = np.meshgrid(s, s, s, indexing="ij")
+    C1, C2, C3 = np.meshgrid(co, co, co, indexing="ij")
+    out = np.empty((n, n, n, 10))
+    out[..., 0] = c0 + amp * S1 * S2 * S3
+    out[..., 1] = amp * w * C1 * S2 * S3
+    out[..., 2] = amp * w * S1 * C2 * S3
+    out[..., 3] = amp * w * S1 * S2 * C3
+    out[..., 4] = -amp * w * w * S1 * S2 * S3
+    out[..., 5] = amp * w * w * C1 * C2 * S3
+    out[..., 6] = amp * w * w * C1 * S2 * C3
+    out[..., 7] = -amp * w * w * S1 * S2 * S3
+    out[..., 8] = amp * w * w * S1 * C2 * C3
+    out[..., 9] = -amp * w * w * S1 * S2 * S3
+    return out.astype(np.float32)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    k: float
+    medium: Medium
+    ny: int
+    y0: np.ndarray            # first y node per axis
+    dy: np.ndarray            # y spacing per axis
+    f: np.ndarray             # complex128 [ny, ny, ny, 3] initial displacement on the y grid
+    g: Optional[np.ndarray]   # complex128 [ny, ny, ny, 3] initial velocity, or None (zero)
+    mesh: MeshSpec
+    classes: tuple            # subset of (0 P+, 1 P-, 2 S+, 3 S-)
+    dt: float
+    nsteps: int
+    times: np.ndarray         # sample times, increasing, in (0, nsteps*dt]
+    receivers: np.ndarray     # float64 [nr, 3]
+    rw: float                 # Gaussian-sum truncation radius
+    snapshot: Optional[np.ndarray] = None   # float64 [ns, 3] grid points sampled at T
+
+    @property
+    def T(self) -> float:
+        return self.dt * self.nsteps
+
+    @property
+    def n_beams(self) -> int:
+        return self.mesh.M * len(self.classes)
+
+
+def _ygrid(x0, half: float, ny: int):
+    dy = np.full(3, 2.0 * half / ny)
+    y0 = np.asarray(x0, dtype=np.float64) - half + 0.5 * dy
+    return y0, dy
+
+
+def _packet(y0, dy, ny: int, k: float, x0, pol, d) -> np.ndarray:
+    """pol * exp(-k|y-x0|^2/2) * exp(i k d.y) on the y grid (a complex [ny,ny,ny,3] array)."""
+    ax = [y0[a] + dy[a] * np.arange(ny) for a in range(3)]
+    Y = np.stack(np.meshgrid(*ax, indexing="ij"), -1)
+    r2 = np.sum((Y - np.asarray(x0)) ** 2, axis=-1)
+    ph = k * (Y @ np.asarray(d, dtype=np.float64))
+    env = np.exp(-0.5 * k * r2 + 1j * ph)
+    return env[..., None] * np.asarray(pol, dtype=np.float64)
+
+
+def homogeneous(nq: int = 12, np_: int = 6, ny: int = 96, nsteps: int = 100, dt: float = 0.005,
+                n_receivers: int = 1000, k: float = 32.0, seed: int = 0, n_times: int = 1) -> Workload:
+    x0 = np.array([0.5, 0.5, 0.5])
+    y0, dy = _ygrid(x0, window_radius(k), ny)
+    f = _packet(y0, dy, ny, k, x0, [1.0, 0.0, 0.0], [1.0, 0.0, 0.0])
+    cp = 2.0
+    g = -1j * k * cp * f
+    mesh = centred_mesh(nq, x0, np_, [1.0, 0.0, 0.0], mesh_radius(k, 4.8))
+    rng = np.random.default_rng(seed)
+    rx = rng.uniform(0.0, 1.0, size=(n_receivers, 3))
+    T = dt * nsteps
+    times = T * np.arange(1, n_times + 1) / n_times
+    return Workload("homogeneous", k, Medium("const", cp0=cp, cs0=1.0), ny, y0, dy, f, g, mesh, (0,),
+                    dt, nsteps, times, rx, window_radius(k))
+
+
+def smooth(nq: int = 24, np_: int = 8, ny: int = 128, nsteps: int = 400, dt: float = 0.0025,
+           n_samples: int = 1000, rx_side: int = 20, snap_side: int = 64, grid_n: int = 128,
+           k: float = 64.0, grid: bool = True, classes=(0, 1, 2, 3)) -> Workload:
+    x0 = np.array([0.35, 0.45, 0.55])
+    dhat = np.array([3.0, 2.0, 1.0]) / math.sqrt(14.0)
+    b = np.array([0.2, -0.5, 1.0])
+    b = b / np.linalg.norm(b)
+    y0, dy = _ygrid(x0, window_radius(k), ny)
+    f = _packet(y0, dy, ny, k, x0, b, dhat)
+    mesh = centred_mesh(nq, x0, np_, dhat, mesh_radius(k, 6.0), mesh_radius(k, 4.8))
+    if grid:
+        gp = sine_fields_on_nodes(grid_n, 2.0, 0.2)
+        gs = (gp.astype(np.float64) / SQRT3).astype(np.float32)
+        h = 1.0 / (grid_n - 1)
+        med = Medium("grid", grid_p=gp, grid_s=gs, origin=(0.0, 0.0, 0.0), spacing=(h, h, h))
+    else:
+        med = Medium("sine", cp0=2.0, amp=0.2, cs_ratio=1.0 / SQRT3)
+    T = dt * nsteps
+    times = T * np.arange(1, n_samples + 1) / n_samples
+    r = (np.arange(rx_side) + 0.5) / rx_side
+    R1, R2 = np.meshgrid(r, r, indexing="ij")
+    rx = np.stack([R1.ravel(), R2.ravel(), np.zeros(R1.size)], -1)
+    snap = None
+    if snap_side:
+        s = (np.arange(snap_side) + 0.5) / snap_side
+        S1, S2, S3 = np.meshgrid(s, s, s, indexing="ij")
+        snap = np.stack([S1.ravel(), S2.ravel(), S3.ravel()], -1)
+    return Workload("smooth", k, med, ny, y0, dy, f, None, mesh, tuple(classes), dt, nsteps, times, rx,
+                    window_radius(k), snap)
+
+
+def random_points(n: int, lo, hi, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(n, 3))

@@ -1,0 +1,493 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it pins.  None of them re-types the oracle's formula: they use
+closed forms, invariants, an independent formulation, finite differences, brute force or a
+library routine (numpy FFT) for a special case.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1810_06760_gb300 import workloads as W
+
+
+def _mesh(O, nq, qc, np_, pc, R):
+    m = W.centred_mesh(nq, qc, np_, pc, R)
+    return O.Mesh(m.nq, m.q0, m.dq, m.np_, m.p0, m.dp)
+
+
+def _model(O, med):
+    return O.Model(med.kind, cp0=med.cp0, cs0=med.cs0, amp=med.amp, cs_ratio=med.cs_ratio,
+                   grid_p=med.grid_p, grid_s=med.grid_s, origin=med.origin, spacing=med.spacing)
+
+
+def _run(O, model, st, meta, dt, nsteps):
+    """RK4 states after each step (list of copies, including t = 0)."""
+    out = [st.copy()]
+    for _ in range(nsteps):
+        O.propagate(model, st, meta, dt, 1)
+        out.append(st.copy())
+    return out
+
+
+def _generic_beams(O, model, k=32.0, cls=0, n=2):
+    mesh = _mesh(O, n, [0.45, 0.5, 0.55], n, [0.7, -0.4, 0.5], 0.3)
+    F = np.zeros((mesh.M, 3), complex)
+    F[:, 0] = 1.0
+    F[:, 1] = 0.5j
+    F[:, 2] = -0.25
+    return O.beam_init(model, k, mesh, F, None, cls)
+
+
+# ---------------------------------------------------------------------------------------------
+# closed forms in a homogeneous medium (Eqs. char_plus/char_minus, DzDt, amp_P..amp_SH)
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("cls", [0, 1, 2, 3])
+def test_homogeneous_closed_form(oracle, cls):
+    """grad c = 0: Q = q + sigma c t p/|p|, P = p, dzQ = I - i sigma c t (I - p p^T/|p|^2)/|p|,
+    dzP = -iI, and the amplitude ODE integrates to a(t) = a(0)(1 - i sigma c t/(2|p|))."""
+    O = oracle
+    c = 2.0 if cls < 2 else 1.0
+    model = O.Model("const", cp0=2.0, cs0=1.0)
+    mesh = _mesh(O, 2, [0.5] * 3, 3, [0.6, 0.3, -0.9], 0.5)
+    F = (np.arange(mesh.M * 3).reshape(-1, 3) % 7 + 1j * (np.arange(mesh.M * 3).reshape(-1, 3) % 5)).astype(complex)
+    st, meta = O.beam_init(model, 16.0, mesh, F, None, cls)
+    a0 = O.state_a(st).copy()
+    dt, n = 0.004, 50
+    O.propagate(model, st, meta, dt, n)
+    t = dt * n
+    sg = -1.0 if cls & 1 else 1.0
+    q, p = mesh.points()
+    pn = np.linalg.norm(p, axis=1)
+    ph = p / pn[:, None]
+    np.testing.assert_allclose(O.state_Q(st), q + sg * c * t * ph, atol=1e-13)
+    np.testing.assert_allclose(O.state_P(st), p, atol=1e-13)
+    proj = np.eye(3)[None] - ph[:, :, None] * ph[:, None, :]
+    DQ = np.eye(3)[None] - 1j * sg * c * t * proj / pn[:, None, None]
+    np.testing.assert_allclose(O.state_DQ(st), DQ, atol=1e-12)
+    np.testing.assert_allclose(O.state_DP(st), np.broadcast_to(-1j * np.eye(3), DQ.shape), atol=1e-13)
+    fac = (1.0 - 1j * sg * c * t / (2.0 * pn))[:, None]
+    np.testing.assert_allclose(O.state_a(st), a0 * fac, rtol=1e-9, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------------
+# smooth medium: closed-form amplitude, H conservation, RK4 order, Jacobian, symplecticity
+# ---------------------------------------------------------------------------------------------
+
+def _sine(O):
+    return O.Model("sine", cp0=2.0, amp=0.2, cs_ratio=1.0 / math.sqrt(3.0))
+
+
+def _continuous_sqrt(z):
+    """sqrt along a sequence, choosing the branch closest to the previous value."""
+    out = np.empty_like(z)
+    out[0] = np.sqrt(z[0])
+    for i in range(1, len(z)):
+        r = np.sqrt(z[i])
+        out[i] = np.where(np.abs(r - out[i - 1]) <= np.abs(-r - out[i - 1]), r, -r)
+    return out
+
+
+@pytest.mark.parametrize("cls", [0, 1])
+def test_amplitude_closed_form_smooth_medium_P(oracle, cls):
+    """Along a ray of H = +-c|P|, sigma grad c . P/|P| = d/dt ln c(Q) and tr(Z^-1 Z') = d/dt ln det Z,
+    so Eq. amp_P integrates to a(t) = a(0) c(Q_t)/c(q) sqrt(det Z(t)/det Z(0)) (continuous branch)."""
+    O = oracle
+    model = _sine(O)
+    st, meta = _generic_beams(O, model, cls=cls, n=3)
+    a0 = O.state_a(st)[:, 0].copy()
+    c0 = model.eval(0, O.state_Q(st))[:, 0]
+    traj = _run(O, model, st, meta, 0.005, 120)
+    detz = np.array([np.linalg.det(O.state_DQ(s) + 1j * O.state_DP(s)) for s in traj])
+    sq = _continuous_sqrt(detz / detz[0])
+    cT = model.eval(0, O.state_Q(traj[-1]))[:, 0]
+    pred = a0 * cT / c0 * sq[-1]
+    np.testing.assert_allclose(O.state_a(traj[-1])[:, 0], pred, rtol=2e-8)
+
+
+@pytest.mark.parametrize("cls", [2, 3])
+def test_amplitude_norm_smooth_medium_S(oracle, cls):
+    """The SV/SH coupling of Eqs. amp_SV/amp_SH is a real rotation, so |a_sv|^2 + |a_sh|^2 obeys the
+    scalar law: |A(t)| = |A(0)| c_s(Q_t)/c_s(q) |sqrt(det Z(t)/det Z(0))|."""
+    O = oracle
+    model = _sine(O)
+    st, meta = _generic_beams(O, model, cls=cls, n=3)
+    a = O.state_a(st)
+    n0 = np.sqrt(np.abs(a[:, 0]) ** 2 + np.abs(a[:, 1]) ** 2)
+    c0 = model.eval(1, O.state_Q(st))[:, 0]
+    traj = _run(O, model, st, meta, 0.005, 120)
+    detz = np.array([np.linalg.det(O.state_DQ(s) + 1j * O.state_DP(s)) for s in traj])
+    cT = model.eval(1, O.state_Q(traj[-1]))[:, 0]
+    aT = O.state_a(traj[-1])
+    nT = np.sqrt(np.abs(aT[:, 0]) ** 2 + np.abs(aT[:, 1]) ** 2)
+    np.testing.assert_allclose(nT, n0 * cT / c0 * np.sqrt(np.abs(detz[-1] / detz[0])), rtol=2e-8)
+
+
+def _hamiltonian(O, model, st, wave):
+    return model.eval(wave, O.state_Q(st))[:, 0] * np.linalg.norm(O.state_P(st), axis=1)
+
+
+@pytest.mark.parametrize("cls", [0, 3])
+def test_hamiltonian_conserved_and_rk4_order(oracle, cls):
+    """H = c(Q)|P| is constant along Eqs. char_plus/char_minus; classical RK4 conserves it up to a
+    global O(dt^4) error, so halving dt divides the drift by about 16."""
+    O = oracle
+    model = _sine(O)
+    wave = cls >= 2
+    drifts = []
+    for dt, n in [(0.02, 25), (0.01, 50)]:
+        st, meta = _generic_beams(O, model, cls=cls, n=2)
+        H0 = _hamiltonian(O, model, st, wave)
+        O.propagate(model, st, meta, dt, n)
+        drifts.append(np.max(np.abs(_hamiltonian(O, model, st, wave) / H0 - 1.0)))
+    assert drifts[1] < 1e-7
+    ratio = drifts[0] / drifts[1]
+    assert 10.0 < ratio < 25.0, ratio
+
+
+@pytest.mark.parametrize("cls", [0, 2])
+def test_jacobian_matches_finite_differences(oracle, cls):
+    """dzQ, dzP integrated by Eq. DzDt equal the Jacobian of the ray flow:
+    d Q_j/d q_m = Re (dzQ)_mj and d Q_j/d p_m = -Im (dzQ)_mj (dz = dq - i dp), checked by central
+    differences of the flow itself (no Jacobian equation involved)."""
+    O = oracle
+    model = _sine(O)
+    mesh = _mesh(O, 1, [0.3, 0.6, 0.45], 1, [0.5, 0.8, -0.3], 0.0)
+    F = np.ones((1, 3), complex)
+    st, meta = O.beam_init(model, 32.0, mesh, F, None, cls)
+    base = st.copy()
+    dt, n = 0.01, 40
+    O.propagate(model, st, meta, dt, n)
+    DQ, DP = O.state_DQ(st)[0], O.state_DP(st)[0]
+    h = 1e-5
+    for m in range(3):
+        for which in ("q", "p"):
+            col = m if which == "q" else 3 + m
+            sp, sm = base.copy(), base.copy()
+            sp[0, col] += h
+            sm[0, col] -= h
+            O.propagate(model, sp, meta, dt, n)
+            O.propagate(model, sm, meta, dt, n)
+            dQ = (sp[0, 0:3] - sm[0, 0:3]) / (2 * h)
+            dP = (sp[0, 3:6] - sm[0, 3:6]) / (2 * h)
+            if which == "q":
+                np.testing.assert_allclose(dQ, DQ[m].real, atol=1e-7)
+                np.testing.assert_allclose(dP, DP[m].real, atol=1e-7)
+            else:
+                np.testing.assert_allclose(dQ, -DQ[m].imag, atol=1e-7)
+                np.testing.assert_allclose(dP, -DP[m].imag, atol=1e-7)
+
+
+@pytest.mark.parametrize("cls", [1, 2])
+def test_symplectic_symmetric_and_invertible(oracle, cls):
+    """App. A: J^T Omega J = Omega (Eq. symplectic); Z^{-1} dzQ is symmetric (Eqs. p1-p6);
+    Z Z^* = (Jv)^*(Jv) + 2I so every singular value of Z is >= sqrt(2)."""
+    O = oracle
+    model = _sine(O)
+    st, meta = _generic_beams(O, model, cls=cls, n=2)
+    O.propagate(model, st, meta, 0.0025, 240)   # RK4 is not symplectic: the defect is O(dt^4)
+    DQ, DP = O.state_DQ(st), O.state_DP(st)
+    Om = np.block([[np.zeros((3, 3)), np.eye(3)], [-np.eye(3), np.zeros((3, 3))]])
+    for b in range(st.shape[0]):
+        J = np.block([[DQ[b].real.T, -DQ[b].imag.T], [DP[b].real.T, -DP[b].imag.T]])
+        np.testing.assert_allclose(J.T @ Om @ J, Om, atol=1e-9)
+        Z = DQ[b] + 1j * DP[b]
+        S = np.linalg.solve(Z, DQ[b])
+        np.testing.assert_allclose(S, S.T, atol=1e-8)
+        assert np.linalg.svd(Z, compute_uv=False).min() >= math.sqrt(2.0) * (1 - 1e-8)
+
+
+def test_phase_is_stationary(oracle):
+    """No phase S appears in Eq. FGA: for H = +-c|P| (homogeneous of degree 1 in P),
+    dS/dt = P.dQ/dt - H = 0 on both branches and both wave types."""
+    O = oracle
+    model = _sine(O)
+    for cls in range(4):
+        st, meta = _generic_beams(O, model, cls=cls, n=2)
+        O.propagate(model, st, meta, 0.01, 10)
+        f = O.rhs(model, st, meta)
+        sg = -1.0 if cls & 1 else 1.0
+        H = sg * _hamiltonian(O, model, st, cls >= 2)
+        np.testing.assert_allclose(np.sum(O.state_P(st) * f[:, 0:3], axis=1), H, rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------------------------
+# S polarisation: the paper's frame form against a frame-free form; planar rays decouple
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("cls", [2, 3])
+def test_sv_sh_coupling_equals_parallel_transport(oracle, cls):
+    """Eqs. amp_SV/amp_SH with the coupling term (dN_sh/dt . N_sv) are equivalent to moving the
+    vector A = a_sv N_sv + a_sh N_sh by A' = gamma A - (A . dP^/dt) P^ (no frame at all).
+    The two forms share only the ray and Z equations."""
+    O = oracle
+    model = _sine(O)
+    mesh = _mesh(O, 2, [0.4, 0.5, 0.6], 2, [0.6, 0.5, 0.4], 0.4)
+    F = np.zeros((mesh.M, 3), complex)
+    F[:, 0], F[:, 1], F[:, 2] = 1.0, -0.3j, 0.7
+    st_f, meta_f = O.beam_init(model, 32.0, mesh, F, None, cls, vector_form=False)
+    st_v, meta_v = O.beam_init(model, 32.0, mesh, F, None, cls, vector_form=True)
+    times = np.array([0.2, 0.5])
+    s_step, s_th = O.sample_schedule(times, 0.01, 50)
+    rf = O.propagate(model, st_f, meta_f, 0.01, 50, s_step, s_th, 1.0)
+    rv = O.propagate(model, st_v, meta_v, 0.01, 50, s_step, s_th, 1.0)
+    np.testing.assert_allclose(rf, rv, atol=1e-9)
+    # the coupling is really active on this path: the frame form's a_sh differs from an uncoupled run
+    assert np.max(np.abs(rf[..., 6:] - rf[..., 6:].mean())) > 0
+
+
+def test_sv_sh_decouple_for_planar_rays(oracle):
+    """For c = c(x3) the ray stays in the vertical plane of P, N_sh = e3 x P/|e3 x P| is constant,
+    the coupling term vanishes, and a beam started as pure SV (a_sh = 0) stays pure SV."""
+    O = oracle
+    n = 33
+    z = np.linspace(0.0, 1.0, n)
+    c = 2.0 + 0.3 * np.sin(2 * np.pi * z)
+    dc = 0.3 * 2 * np.pi * np.cos(2 * np.pi * z)
+    d2c = -0.3 * (2 * np.pi) ** 2 * np.sin(2 * np.pi * z)
+    g = np.zeros((n, n, n, 10), np.float32)
+    g[..., 0] = c[None, None, :]
+    g[..., 3] = dc[None, None, :]
+    g[..., 9] = d2c[None, None, :]
+    model = O.Model("grid", grid_p=g, grid_s=g, origin=(0, 0, 0), spacing=(1 / (n - 1),) * 3)
+    mesh = O.Mesh(1, [0.5, 0.5, 0.3], [0.1] * 3, 1, [0.8, 0.0, 0.6], [0.1] * 3)
+    st, meta = O.beam_init(model, 32.0, mesh, np.array([[0.6, 0.0, -0.8]], complex), None, 2)
+    a = O.state_a(st)
+    assert abs(a[0, 1]) < 1e-15 and abs(a[0, 0]) > 0.1
+    O.propagate(model, st, meta, 0.01, 40)
+    assert abs(O.state_P(st)[0, 2] - 0.6) > 1e-3      # the ray really bends
+    assert abs(O.state_a(st)[0, 1]) < 1e-14
+
+
+# ---------------------------------------------------------------------------------------------
+# decomposition (Eqs. psi, alpha^k): closed form, direct vs separable
+# ---------------------------------------------------------------------------------------------
+
+def test_fbi_direct_equals_separable(oracle):
+    """The kernel of Eq. psi factors over the three axes, so the separable contraction equals the
+    direct triple sum (brute force on a tiny mesh)."""
+    O = oracle
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((16, 14, 12, 3)) + 1j * rng.standard_normal((16, 14, 12, 3))
+    mesh = O.Mesh(3, [0.1, 0.2, 0.3], [0.2, 0.25, 0.3], 2, [0.9, -0.1, 0.2], [0.3, 0.2, 0.4])
+    y0, dy = [-0.1, 0.0, 0.05], [0.07, 0.08, 0.09]
+    Fd = O.fbi(f, y0, dy, 12.0, mesh, "direct")
+    Fs = O.fbi(f, y0, dy, 12.0, mesh, "separable")
+    np.testing.assert_allclose(Fs, Fd, rtol=0, atol=1e-12 * np.abs(Fd).max())
+
+
+def test_fbi_gaussian_closed_form(oracle):
+    """For f = b exp(i k p0.y - k|y-x0|^2/2) the integral of Eq. psi is Gaussian:
+    F(q,p) = b (pi/k)^{3/2} exp(k m.m - k(|x0|^2+|q|^2)/2 + i k p.q), m = (x0+q + i(p0-p))/2."""
+    O = oracle
+    k = 24.0
+    x0 = np.array([0.5, 0.45, 0.55])
+    p0 = np.array([0.6, 0.7, -0.4])
+    b = np.array([1.0, -0.5j, 0.25])
+    half = 7.0 / math.sqrt(k)
+    ny = 72
+    dy = np.full(3, 2 * half / ny)
+    y0 = x0 - half + 0.5 * dy
+    ax = [y0[a] + dy[a] * np.arange(ny) for a in range(3)]
+    Y = np.stack(np.meshgrid(*ax, indexing="ij"), -1)
+    f = np.exp(1j * k * (Y @ p0) - 0.5 * k * np.sum((Y - x0) ** 2, -1))[..., None] * b
+    mesh = _mesh(O, 3, x0, 3, p0, 0.4)
+    F = O.fbi(f, y0, dy, k, mesh)
+    q, p = mesh.points()
+    m = 0.5 * (x0 + q + 1j * (p0 - p))
+    ex = (math.pi / k) ** 1.5 * np.exp(k * np.sum(m * m, 1) - 0.5 * k * (x0 @ x0 + np.sum(q * q, 1))
+                                       + 1j * k * np.sum(p * q, 1))
+    np.testing.assert_allclose(F, ex[:, None] * b[None, :], rtol=0, atol=1e-9 * np.abs(ex).max())
+
+
+# ---------------------------------------------------------------------------------------------
+# t = 0 reproduction: Eqs. FGA + psi + alpha^k with a = 2^{3/2} reproduce the initial data
+# ---------------------------------------------------------------------------------------------
+
+def _packet_data(k, x0, p0, pol, half_mult=6.5, ny=64):
+    half = half_mult / math.sqrt(k)
+    dy = np.full(3, 2 * half / ny)
+    y0 = np.asarray(x0) - half + 0.5 * dy
+    ax = [y0[a] + dy[a] * np.arange(ny) for a in range(3)]
+    Y = np.stack(np.meshgrid(*ax, indexing="ij"), -1)
+    f = np.exp(1j * k * (Y @ np.asarray(p0)) - 0.5 * k * np.sum((Y - x0) ** 2, -1))[..., None] * np.asarray(pol)
+    return f, y0, dy
+
+
+def _packet_at(x, k, x0, p0, pol):
+    return (np.exp(1j * k * (x @ np.asarray(p0)) - 0.5 * k * np.sum((x - x0) ** 2, -1))[:, None]
+            * np.asarray(pol)[None, :])
+
+
+def test_initial_data_reproduced(oracle):
+    """At t = 0 the four classes together return f: sum over P+- gives (F.p^) p^, over S+- gives
+    (F.N_sv) N_sv + (F.N_sh) N_sh, and with a = 2^{3/2} the weight 2^{3/2}/(2pi/k)^{9/2} inverts the
+    wave-packet transform exactly (int int e^{ikp(x-q)-k|x-q|^2/2} e^{-ikp(y-q)-k|y-q|^2/2} dq dp =
+    (2pi/k)^{9/2} 2^{-3/2} delta(x-y)).  The error is quadrature error and falls as the mesh refines."""
+    O = oracle
+    k = 16.0
+    x0 = np.array([0.5, 0.5, 0.5])
+    p0 = np.array([3.0, 2.0, 1.0]) / math.sqrt(14.0)
+    pol = np.array([0.2, -0.5, 1.0])
+    f, y0, dy = _packet_data(k, x0, p0, pol)
+    model = O.Model("const", cp0=2.0, cs0=1.0)
+    x = x0 + W.random_points(24, -0.35, 0.35, 7)
+    exact = _packet_at(x, k, x0, p0, pol)
+    errs = []
+    for n in (8, 10):
+        mesh = _mesh(O, n, x0, n, p0, W.mesh_radius(k, 4.8))
+        F = O.fbi(f, y0, dy, k, mesh)
+        u = np.zeros_like(exact)
+        for cls in range(4):
+            st, meta = O.beam_init(model, k, mesh, F, None, cls)
+            u += O.gauss_sum(O.records(st, meta, mesh.weight(k)), k, 0.0, x)
+        errs.append(np.linalg.norm(u - exact) / np.linalg.norm(exact))
+    assert errs[1] < 3e-4, errs
+    assert errs[1] < 0.1 * errs[0], errs
+
+
+def test_initial_velocity_reproduced_with_p_not_unit(oracle):
+    """Eq. alpha^k read with |p| (not |p|^3): the + and - packets oscillate as exp(-+ i k c|p| t), so
+    d/dt of the sum at t = 0 returns g up to O(1/k).  With |p0| = 2 the |p|^3 reading would return
+    g/4 instead.  The time derivative is a central difference of two RK4 steps of +-1e-4."""
+    O = oracle
+    k = 32.0
+    x0 = np.array([0.5, 0.5, 0.5])
+    p0 = np.array([2.0, 0.0, 0.0])
+    polf = np.array([1.0, 0.3, 0.0])
+    polg = np.array([0.4, -0.8j, 0.5])
+    f, y0, dy = _packet_data(k, x0, p0, polf)
+    g = k * _packet_data(k, x0, p0, polg)[0]
+    model = O.Model("const", cp0=2.0, cs0=1.0)
+    mesh = _mesh(O, 10, x0, 10, p0, W.mesh_radius(k, 4.8))
+    F = O.fbi(f, y0, dy, k, mesh)
+    G = O.fbi(g, y0, dy, k, mesh)
+    x = x0 + W.random_points(16, -0.2, 0.2, 8)
+    h = 1e-4
+    ut = np.zeros((x.shape[0], 3), complex)
+    for cls in range(4):
+        st, meta = O.beam_init(model, k, mesh, F, G, cls)
+        sp, sm = st.copy(), st.copy()
+        O.propagate(model, sp, meta, h, 1)
+        O.propagate(model, sm, meta, -h, 1)
+        w = mesh.weight(k)
+        ut += (O.gauss_sum(O.records(sp, meta, w), k, 0.0, x) - O.gauss_sum(O.records(sm, meta, w), k, 0.0, x)) / (2 * h)
+    exact = k * _packet_at(x, k, x0, p0, polg)
+    err = np.linalg.norm(ut - exact) / np.linalg.norm(exact)
+    assert err < 0.08, err
+
+
+# ---------------------------------------------------------------------------------------------
+# O(1/k) convergence to the exact elastic solution (spectral, periodic box, homogeneous medium)
+# ---------------------------------------------------------------------------------------------
+
+def _spectral_exact(k, x0, p0, pol, cp, cs, t, pts_idx_fn):
+    """Exact solution of rho u_tt = (lambda+mu) grad div u + mu Lap u (Eq. ewe, constant medium,
+    g = 0) by the Helmholtz split in Fourier space: u^ = P_L cos(cp|xi|t) f^ + P_T cos(cs|xi|t) f^."""
+    L = 2.0 * (cp * t + 7.5 / math.sqrt(k))
+    kmax = k * np.linalg.norm(p0) + 7.0 * math.sqrt(k)
+    N = int(2 ** math.ceil(math.log2(max(32, 1.15 * kmax * L / math.pi))))
+    xs = x0[0] - L / 2 + L * np.arange(N) / N
+    ax = [x0[a] - L / 2 + L * np.arange(N) / N for a in range(3)]
+    X = np.stack(np.meshgrid(*ax, indexing="ij"), -1)
+    f = np.exp(1j * k * (X @ p0) - 0.5 * k * np.sum((X - x0) ** 2, -1))[..., None] * pol
+    fh = np.fft.fftn(f, axes=(0, 1, 2))
+    xi1 = 2 * np.pi * np.fft.fftfreq(N, d=L / N)
+    XI = np.stack(np.meshgrid(xi1, xi1, xi1, indexing="ij"), -1)
+    n = np.linalg.norm(XI, axis=-1)
+    nz = np.where(n == 0, 1.0, n)
+    xh = XI / nz[..., None]
+    lon = np.sum(xh * fh, -1)[..., None] * xh
+    tra = fh - lon
+    uh = lon * np.cos(cp * n * t)[..., None] + tra * np.cos(cs * n * t)[..., None]
+    u = np.fft.ifftn(uh, axes=(0, 1, 2))
+    idx = pts_idx_fn(u, N)
+    pts = np.stack([ax[a][idx[:, a]] for a in range(3)], -1)
+    return pts, u[idx[:, 0], idx[:, 1], idx[:, 2]]
+
+
+@pytest.mark.slow
+def test_first_order_convergence_in_k(oracle):
+    """FGA is an O(1/k) asymptotic method (Sec. 1, Sec. 5): against the exact solution the relative
+    error roughly halves each time k doubles."""
+    O = oracle
+    x0 = np.array([0.5, 0.5, 0.5])
+    p0 = np.array([3.0, 2.0, 1.0]) / math.sqrt(14.0)
+    pol = np.array([0.2, -0.5, 1.0]) / math.sqrt(1.29)
+    cp, cs, t = 2.0, 1.0, 0.12
+    model = O.Model("const", cp0=cp, cs0=cs)
+    errs = []
+    for k in (16.0, 32.0, 64.0):
+        rng = np.random.default_rng(int(k))
+
+        def pick(u, N):
+            mag = np.linalg.norm(u, axis=-1)
+            cand = np.argwhere(mag > 0.2 * mag.max())
+            return cand[rng.choice(len(cand), size=min(120, len(cand)), replace=False)]
+
+        pts, ex = _spectral_exact(k, x0, p0, pol, cp, cs, t, pick)
+        f, y0, dy = _packet_data(k, x0, p0, pol, ny=72)
+        mesh = _mesh(O, 10, x0, 10, p0, W.mesh_radius(k, 4.8))
+        F = O.fbi(f, y0, dy, k, mesh)
+        u = np.zeros_like(ex)
+        for cls in range(4):
+            st, meta = O.beam_init(model, k, mesh, F, None, cls)
+            O.propagate(model, st, meta, t / 6, 6)
+            u += O.gauss_sum(O.records(st, meta, mesh.weight(k)), k, 0.0, pts)
+        errs.append(np.linalg.norm(u - ex) / np.linalg.norm(ex))
+    assert errs[0] < 0.25, errs
+    assert 1.5 < errs[0] / errs[1] < 3.0, errs
+    assert 1.5 < errs[1] / errs[2] < 3.0, errs
+
+
+# ---------------------------------------------------------------------------------------------
+# Gaussian sum: truncation bound; binning
+# ---------------------------------------------------------------------------------------------
+
+def test_truncated_sum_within_window_bound(oracle):
+    """Dropping beams with |x-Q| > rw = 6/sqrt(k) changes the sum by at most e^{-18} sum |A_b|
+    (each dropped term has |exp(...)| = exp(-k|x-Q|^2/2) < e^{-18}); the kept terms are identical."""
+    O = oracle
+    k = 64.0
+    rng = np.random.default_rng(11)
+    nb = 4000
+    rec = np.zeros((nb, 12))
+    rec[:, 0:3] = rng.uniform(-0.5, 1.5, (nb, 3))
+    rec[:, 3:6] = rng.normal(size=(nb, 3))
+    rec[:, 6:] = rng.normal(size=(nb, 6))
+    x = rng.uniform(0, 1, (30, 3))
+    rw = W.window_radius(k)
+    ut = O.gauss_sum(rec, k, rw, x)
+    uf = O.gauss_sum(rec, k, 0.0, x)
+    amp = np.sum(np.abs(rec[:, 6::2] + 1j * rec[:, 7::2]), axis=0)
+    assert np.all(np.abs(ut - uf) <= math.exp(-18.0) * amp[None, :] + 1e-15)
+    # brute force of the truncated sum for one point
+    d = x[0] - rec[:, 0:3]
+    r2 = np.sum(d * d, 1)
+    keep = r2 <= rw * rw
+    e = np.exp(1j * k * np.sum(rec[:, 3:6] * d, 1) - 0.5 * k * r2)
+    A = rec[:, 6::2] + 1j * rec[:, 7::2]
+    np.testing.assert_allclose(ut[0], np.sum((A * e[:, None])[keep], 0), rtol=1e-12)
+
+
+def test_binning_keys_and_stable_sort(oracle):
+    """Cell keys are floor((Q - o) * inv_h) in FP32 (one rounding per operation), clamped; the sort
+    is stable.  Checked against numpy's float32 arithmetic and a stable argsort."""
+    O = oracle
+    rng = np.random.default_rng(5)
+    Q = rng.uniform(-0.6, 1.7, (20000, 3)).astype(np.float32)
+    Q[:50] = np.float32(0.25) * rng.integers(-2, 8, (50, 3))     # points on cell faces
+    o = np.array([-0.5, -0.5, -0.5], np.float32)
+    inv_h = np.float32(1.0 / 0.375)
+    nc = np.array([6, 5, 7], np.int32)
+    key = O.bin_keys_f32(Q, o, inv_h, nc)
+    t = np.floor((Q - o) * inv_h)
+    cell = np.clip(t, 0, nc - 1).astype(np.int64)
+    ref = (cell[:, 0] * nc[1] + cell[:, 1]) * nc[2] + cell[:, 2]
+    np.testing.assert_array_equal(key, ref)
+    ncell = int(np.prod(nc))
+    perm, start = O.bin_sort(key, ncell)
+    np.testing.assert_array_equal(perm, np.argsort(key, kind="stable"))
+    np.testing.assert_array_equal(start, np.searchsorted(np.sort(key), np.arange(ncell + 1)))
