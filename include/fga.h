@@ -1,0 +1,173 @@
+/*
+ * fga.h -- C ABI of the GB300 (sm_103a) frozen Gaussian approximation library.
+ *
+ * Method: Hateley, Chai, Tong & Yang, "Frozen Gaussian approximation for 3-D elastic wave
+ * equation and seismic tomography" (arXiv:1810.06760).  The library computes the method's three
+ * data-parallel steps (Fig. fig:FGA_alg) on one GPU:
+ *   1. decomposition of the initial displacement f and velocity g into Gaussian packets on a
+ *      tensor (q,p) mesh (Eqs. psi, alpha^k);
+ *   2. time propagation of every packet ("beam") by classical RK4: rays (Eqs. char_plus,
+ *      char_minus), dzQ/dzP (Eq. DzDt), amplitudes with the SV/SH coupling (Eqs. amp_P, amp_SV,
+ *      amp_SH);
+ *   3. reconstruction by the truncated Gaussian sum of Eq. FGA at points.
+ *
+ * Conventions
+ *  - Every call is asynchronous on the caller's CUDA stream `s` unless it says otherwise; the
+ *    caller owns every buffer it passes.  Pointers marked DEVICE must be device memory of the
+ *    current device; pointers marked HOST are read before the call returns.
+ *  - Complex numbers are interleaved (re, im).  Arrays of 3-vectors are [n][3] row-major.
+ *  - Every call returns an fga_status; no C++ exception crosses the ABI.  fga_last_error()
+ *    gives a message for the last failing call of the calling thread.
+ *  - Precision is chosen per beam set: FGA_PREC_FP32 (ray, amplitude and sum arithmetic in
+ *    FP32) or FP64.  Outputs of a beam set are complex64 (FP32) or complex128 (FP64).
+ *  - Beam classes: 0 = P "+", 1 = P "-", 2 = S "+", 3 = S "-" (the two-way propagation of
+ *    Eqs. char_plus / char_minus).  An S beam carries both SV and SH amplitudes.
+ */
+#ifndef FGA_H
+#define FGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fga_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    FGA_OK = 0,
+    FGA_ERR_INVALID_ARG = 1, /* bad size, pointer, descriptor field; nothing was launched */
+    FGA_ERR_OOM = 2,         /* a device allocation failed; nothing was launched */
+    FGA_ERR_CUDA = 3,        /* a CUDA runtime call failed; the message has the CUDA error */
+    FGA_ERR_TIMEOUT = 4,     /* a bounded wait ran out */
+    FGA_ERR_NUMERIC = 5,     /* non-finite beam state detected */
+    FGA_ERR_UNSUPPORTED = 6  /* valid request the library does not implement */
+} fga_status;
+
+enum { FGA_PREC_FP32 = 0, FGA_PREC_FP64 = 1 };
+
+enum {
+    FGA_MEDIUM_CONST = 0,  /* constant c_p, c_s */
+    FGA_MEDIUM_SINE = 1,   /* c_p = cp0 + amp sin(2 pi x1) sin(2 pi x2) sin(2 pi x3), c_s = cs_ratio c_p,
+                              evaluated exactly with its gradient and Hessian */
+    FGA_MEDIUM_GRID = 2,   /* c_p, c_s and their first and second derivatives given on a node
+                              grid, trilinearly interpolated (all 10 fields) */
+    FGA_MEDIUM_LAYERED = 3 /* piecewise-constant layers in depth x3 with flat interfaces (Sec. 3.1) */
+};
+
+/* Velocity model (Eqs. ewe_ps, ps_speed).  Grid media: node (i,j,l) sits at
+ * origin + (i*spacing[0], j*spacing[1], l*spacing[2]); positions outside the grid read the nearest
+ * boundary value of every field.  Layered media: nlayers <= 8 layers, z_interfaces[nlayers-1]
+ * increasing depths (HOST arrays). */
+typedef struct {
+    int kind;
+    double cp0, cs0;
+    double amp, cs_ratio;
+    int n[3];
+    double origin[3], spacing[3];
+    int nlayers;
+    const double *z_interfaces, *layer_cp, *layer_cs, *layer_rho;
+} fga_model_desc;
+
+typedef struct fga_model fga_model;
+typedef struct fga_beams fga_beams;
+
+/* Create a model.  For FGA_MEDIUM_GRID, grid_p and grid_s are DEVICE float arrays of
+ * n[0]*n[1]*n[2]*10 values, node-major (axis 0 slowest), fields per node
+ * c, dc/dx1, dc/dx2, dc/dx3, c_11, c_12, c_13, c_22, c_23, c_33; they are copied into the
+ * library's own layout (the caller may free them after the call's stream work completes).
+ * Other kinds take NULL.  Errors: INVALID_ARG (kind, sizes, spacing <= 0, nlayers > 8), OOM. */
+fga_status fga_model_create(fga_model **out, const fga_model_desc *desc, const float *grid_p,
+                            const float *grid_s, fga_stream_t s);
+fga_status fga_model_destroy(fga_model *m);
+
+/* Decomposition input (Eqs. psi, alpha^k).
+ *  f, g: DEVICE complex128 arrays [ny0][ny1][ny2][3] sampling the initial displacement and
+ *        velocity at y0 + (i dy0, j dy1, l dy2); g may be NULL (zero velocity).
+ *  Mesh: q_{d,i} = q0[d] + i dq[d] (nq per axis), p_{d,j} = p0[d] + j dp[d] (np per axis);
+ *        mesh index = ((iq0 nq + iq1) nq + iq2) np^3 + (jp0 np + jp1) np + jp2.
+ *  class_mask: bit c creates the beams of class c at every mesh point. */
+typedef struct {
+    double k;
+    int ny[3];
+    double y0[3], dy[3];
+    const void *f, *g;
+    int nq;
+    double q0[3], dq[3];
+    int np;
+    double p0[3], dp[3];
+    unsigned class_mask;
+    int precision;
+} fga_init_desc;
+
+/* Steps 1 of Fig. fig:FGA_alg: the wave-packet transform F(q,p) = sum_y f(y) exp(-i k p.(y-q)
+ * - k|y-q|^2/2) dy^3 (and G from g) as three per-axis contractions, then one beam per mesh point
+ * and requested class with Q = q, P = p, dzQ = I, dzP = -iI (Z = 2I) and amplitude
+ * 2^{3/2} psi, psi = (F.n +- i G.n/(k c(q) |p|))/2 (Eq. alpha^k read with |p|; n = p/|p| for P,
+ * the SV and SH directions for S).  Allocates the beam set (freed by fga_beams_destroy).
+ * Errors: INVALID_ARG (k <= 0, sizes, empty mask), OOM, CUDA. */
+fga_status fga_decompose(const fga_model *m, const fga_init_desc *init, fga_beams **out, fga_stream_t s);
+
+/* Step 2: advance every beam nsteps classical RK4 steps of size dt (dt may be negative).
+ * Errors: INVALID_ARG (nsteps < 0, dt not finite), CUDA. */
+fga_status fga_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps, fga_stream_t s);
+
+/* Step 3 at the current beam state: u(x) = sum over beams with |x - Q| <= rw of
+ * w a N exp(i k P.(x-Q) - k|x-Q|^2/2), w = dq^3 dp^3 / (2 pi/k)^{9/2} (Eq. FGA), N the
+ * polarisation (P/|P| for P; a_sv N_sv + a_sh N_sh for S).  rw <= 0 selects 6/sqrt(k).
+ *  x: DEVICE float64 [n][3];  u_out: DEVICE complex [n][3] (complex64 for FP32 beams, complex128
+ *  for FP64).  n = 0 is a no-op.  Uses library-owned scratch memory (allocated on demand).
+ *  Errors: INVALID_ARG, OOM, CUDA. */
+fga_status fga_reconstruct(const fga_beams *b, const double *x, int64_t n, double rw, void *u_out,
+                           fga_stream_t s);
+
+/* Whole forward solve: decompose, propagate nsteps of dt, and sum at the sample times.
+ *  times: HOST, n_times increasing values in (0, nsteps*dt]; a sample inside step n uses cubic
+ *         Hermite interpolation of Q and P and linear interpolation of the amplitudes.
+ *  rx:    DEVICE float64 [n_rx][3]; seis_out DEVICE complex [n_times][n_rx][3] (may be NULL if
+ *         n_rx = 0).
+ *  snap:  DEVICE float64 [n_snap][3] summed at t = nsteps*dt into snap_out DEVICE complex
+ *         [n_snap][3] (may be NULL if n_snap = 0).
+ *  rw <= 0 selects 6/sqrt(k).  Errors: INVALID_ARG, OOM, CUDA. */
+typedef struct {
+    double dt;
+    int nsteps;
+    int n_times;
+    const double *times;
+    int64_t n_rx;
+    const double *rx;
+    int64_t n_snap;
+    const double *snap;
+    double rw;
+} fga_solve_desc;
+
+fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd,
+                     void *seis_out, void *snap_out, fga_stream_t s);
+
+/* Beam bookkeeping.  fga_beams_count: HOST int64 n_by_class[4] (synchronises the stream the
+ * beams were last used on).  fga_beams_export: copies the state to HOST in mesh order, per beam
+ * 48 float64 = Q(3), P(3), dzQ (3x3 complex, [m][j] = dQ_j/dz_m), dzP (3x3 complex), amplitudes
+ * (3 complex: P: a, 0, 0; S: a_sv, a_sh, 0), and HOST int32 meta per beam (bits 0-1 class, bit 2
+ * S frame reference e1); either pointer may be NULL.  Synchronous. */
+fga_status fga_beams_count(const fga_beams *b, int64_t *n_by_class);
+fga_status fga_beams_export(const fga_beams *b, double *state_host, int32_t *meta_host);
+fga_status fga_beams_destroy(fga_beams *b);
+
+/* Cell binning (no counterpart in the paper: the fast summation it cites is not printed).
+ * For FP32 centres Q (DEVICE float [n][3]) computes key = (c0 nc1 + c1) nc2 + c2 with
+ * c_d = floor((Q_d - o_d) * inv_h) in FP32 round-to-nearest, clamped to [0, nc_d-1], then a
+ * stable sort: perm (DEVICE int32 [n]) lists the beams cell by cell in increasing index,
+ * cell_start (DEVICE int32 [ncells+1]) the cell offsets; keys (DEVICE int32 [n]) may be NULL.
+ * Uses library-owned scratch.  Errors: INVALID_ARG (n < 0, nc_d < 1, ncells >= 2^24), OOM, CUDA. */
+fga_status fga_bin(const float *Q, int64_t n, const float origin[3], float inv_h, const int nc[3],
+                   int32_t *keys, int32_t *perm, int32_t *cell_start, fga_stream_t s);
+
+/* Message of the last failing call on this thread (always NUL-terminated; truncated to cap). */
+void fga_last_error(char *buf, size_t cap);
+int fga_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FGA_H */

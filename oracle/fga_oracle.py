@@ -312,15 +312,19 @@ def state_a(st):
 # --------------------------------------------------------------------------------------------
 
 def solve(model: Model, k: float, mesh: Mesh, F: np.ndarray, G, classes, dt: float, nsteps: int,
-          times, x: np.ndarray, rw: float, vector_form: bool = False):
+          times, x: np.ndarray, rw: float, vector_form: bool = False, snap=None):
     """Decomposed data (F, G) -> beams of the given classes -> RK4 -> Gaussian sums at points x
-    and sample times.  Returns complex [ns, nx, 3]."""
+    and sample times (and at the points `snap` at t = nsteps*dt).
+    Returns complex [ns, nx, 3] (and complex [nsnap, 3] if snap is given)."""
     s_step, s_theta = sample_schedule(times, dt, nsteps)
     w = mesh.weight(k)
     out = np.zeros((len(times), x.shape[0], 3), dtype=np.complex128)
+    snap_u = None if snap is None else np.zeros((snap.shape[0], 3), dtype=np.complex128)
     for cls in classes:
         st, meta = beam_init(model, k, mesh, F, G, cls, vector_form)
         rec = propagate(model, st, meta, dt, nsteps, s_step, s_theta, w)
         for j in range(len(times)):
             out[j] += gauss_sum(rec[j], k, rw, x)
-    return out
+        if snap is not None:
+            snap_u += gauss_sum(records(st, meta, w), k, rw, snap)
+    return out if snap is None else (out, snap_u)

@@ -1,0 +1,466 @@
+// C ABI of the library (include/fga.h): handles, argument checks, and the solve orchestration.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "fga_beam.cuh"
+#include "gather.cuh"
+
+namespace fga {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+fga_status cuda_fail(cudaError_t e, const char *what) {
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "CUDA error %d (%s: %s) in %s", (int)e, cudaGetErrorName(e), cudaGetErrorString(e),
+                  what);
+    g_err = buf;
+    return e == cudaErrorMemoryAllocation ? FGA_ERR_OOM : FGA_ERR_CUDA;
+}
+
+fga_status DevBuf::ensure(size_t need) {
+    if (need <= bytes && p) return FGA_OK;
+    release();
+    if (need == 0) need = 16;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+        cudaGetLastError();
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "device allocation of %zu bytes failed (%s)", need, cudaGetErrorString(e));
+        set_error(buf);
+        return FGA_ERR_OOM;
+    }
+    bytes = need;
+    return FGA_OK;
+}
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+fga_status HostBuf::ensure(size_t need) {
+    if (need <= bytes && p) return FGA_OK;
+    release();
+    if (need == 0) need = 16;
+    cudaError_t e = cudaMallocHost(&p, need);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+        cudaGetLastError();
+        set_error("pinned host allocation failed");
+        return FGA_ERR_OOM;
+    }
+    bytes = need;
+    return FGA_OK;
+}
+void HostBuf::release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+}
+void Workspace::release() {
+    for (DevBuf *d : {&keys, &keys_alt, &vals, &vals_alt, &hist, &scan_blocks, &cell_start, &rec, &items, &tiles,
+                      &partial, &pts})
+        d->release();
+    for (HostBuf *h : {&h_cell_start, &h_items, &h_tiles}) h->release();
+}
+
+// pack the 10 node fields into 3 float4 per node
+__global__ void pack_grid_kernel(const float *__restrict__ src, float4 *__restrict__ dst, int64_t nn) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const float *s = src + i * 10;
+    dst[3 * i] = make_float4(s[0], s[1], s[2], s[3]);
+    dst[3 * i + 1] = make_float4(s[4], s[5], s[6], s[7]);
+    dst[3 * i + 2] = make_float4(s[8], s[9], 0.f, 0.f);
+}
+
+__global__ void max_field0_kernel(const float4 *__restrict__ g, int64_t nn, unsigned *__restrict__ out) {
+    __shared__ unsigned sm;
+    if (threadIdx.x == 0) sm = 0;
+    __syncthreads();
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(g[3 * i].x));
+    atomicMax(&sm, __float_as_uint(m));  // non-negative floats order like their bit patterns
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(out, sm);
+}
+
+static double sample_hermite_margin(double cmax, double dt, int w) { return cmax * std::fabs(dt) * (w + 1.0); }
+
+}  // namespace fga
+
+using namespace fga;
+
+extern "C" {
+
+void fga_last_error(char *buf, size_t cap) {
+    if (!buf || cap == 0) return;
+    std::snprintf(buf, cap, "%s", g_err.c_str());
+}
+
+int fga_version(void) { return 10000; }
+
+fga_status fga_model_create(fga_model **out, const fga_model_desc *d, const float *grid_p, const float *grid_s,
+                            fga_stream_t s_) {
+    cudaStream_t s = (cudaStream_t)s_;
+    FGA_CHECK(out && d, "fga_model_create: NULL argument");
+    FGA_CHECK(d->kind >= FGA_MEDIUM_CONST && d->kind <= FGA_MEDIUM_LAYERED, "fga_model_create: bad medium kind");
+    fga_model *m = new fga_model();
+    std::memset(&m->dev, 0, sizeof(m->dev));
+    m->dev.kind = d->kind;
+    m->dev.cp0 = d->cp0;
+    m->dev.cs0 = d->cs0;
+    m->dev.amp = d->amp;
+    m->dev.cs_ratio = d->cs_ratio;
+    if (d->kind == FGA_MEDIUM_CONST) {
+        if (!(d->cp0 > 0 && d->cs0 > 0)) {
+            delete m;
+            set_error("fga_model_create: constant speeds must be > 0");
+            return FGA_ERR_INVALID_ARG;
+        }
+        m->cmax[0] = d->cp0;
+        m->cmax[1] = d->cs0;
+    } else if (d->kind == FGA_MEDIUM_SINE) {
+        if (!(d->cp0 > std::fabs(d->amp) && d->cs_ratio > 0)) {
+            delete m;
+            set_error("fga_model_create: sine medium needs cp0 > |amp| and cs_ratio > 0");
+            return FGA_ERR_INVALID_ARG;
+        }
+        m->cmax[0] = d->cp0 + std::fabs(d->amp);
+        m->cmax[1] = m->cmax[0] * d->cs_ratio;
+    } else if (d->kind == FGA_MEDIUM_GRID) {
+        bool ok = grid_p && grid_s;
+        for (int a = 0; a < 3; a++) ok = ok && d->n[a] >= 2 && d->spacing[a] > 0;
+        if (!ok) {
+            delete m;
+            set_error("fga_model_create: grid needs n >= 2 per axis, spacing > 0 and both field arrays");
+            return FGA_ERR_INVALID_ARG;
+        }
+        const int64_t nn = (int64_t)d->n[0] * d->n[1] * d->n[2];
+        fga_status st = m->grid.ensure(sizeof(float4) * 3 * 2 * (size_t)nn);
+        if (st != FGA_OK) {
+            delete m;
+            return st;
+        }
+        float4 *gp = m->grid.as<float4>(), *gs = gp + 3 * nn;
+        const unsigned blocks = (unsigned)((nn + 255) / 256);
+        pack_grid_kernel<<<blocks, 256, 0, s>>>(grid_p, gp, nn);
+        pack_grid_kernel<<<blocks, 256, 0, s>>>(grid_s, gs, nn);
+        unsigned *dmax = nullptr;
+        cudaError_t e = cudaMalloc(&dmax, 2 * sizeof(unsigned));
+        unsigned hmax[2] = {0, 0};
+        if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, 2 * sizeof(unsigned), s);
+        if (e == cudaSuccess) {
+            max_field0_kernel<<<304, 256, 0, s>>>(gp, nn, dmax);
+            max_field0_kernel<<<304, 256, 0, s>>>(gs, nn, dmax + 1);
+            e = cudaMemcpyAsync(hmax, dmax, sizeof hmax, cudaMemcpyDeviceToHost, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (dmax) cudaFree(dmax);
+        if (e != cudaSuccess) {
+            delete m;
+            return cuda_fail(e, "fga_model_create");
+        }
+        float fm[2];
+        std::memcpy(fm, hmax, sizeof fm);
+        m->cmax[0] = fm[0];
+        m->cmax[1] = fm[1];
+        m->dev.gp = gp;
+        m->dev.gs = gs;
+        for (int a = 0; a < 3; a++) {
+            m->dev.n[a] = d->n[a];
+            m->dev.o[a] = d->origin[a];
+            m->dev.h[a] = d->spacing[a];
+            m->dev.inv_h[a] = 1.0 / d->spacing[a];
+        }
+    } else {
+        bool ok = d->nlayers >= 1 && d->nlayers <= MAX_LAYERS && d->layer_cp && d->layer_cs && d->layer_rho &&
+                  (d->nlayers == 1 || d->z_interfaces);
+        if (!ok) {
+            delete m;
+            set_error("fga_model_create: layered medium needs 1..8 layers and their arrays");
+            return FGA_ERR_INVALID_ARG;
+        }
+        m->dev.nlay = d->nlayers;
+        m->cmax[0] = m->cmax[1] = 0;
+        for (int l = 0; l < d->nlayers; l++) {
+            m->dev.lcp[l] = d->layer_cp[l];
+            m->dev.lcs[l] = d->layer_cs[l];
+            m->dev.lrho[l] = d->layer_rho[l];
+            m->cmax[0] = std::max(m->cmax[0], d->layer_cp[l]);
+            m->cmax[1] = std::max(m->cmax[1], d->layer_cs[l]);
+            if (l + 1 < d->nlayers) m->dev.zif[l] = d->z_interfaces[l];
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        m->grid.release();
+        delete m;
+        return cuda_fail(e, "fga_model_create");
+    }
+    *out = m;
+    return FGA_OK;
+}
+
+fga_status fga_model_destroy(fga_model *m) {
+    if (!m) return FGA_OK;
+    m->grid.release();
+    delete m;
+    return FGA_OK;
+}
+
+fga_status fga_decompose(const fga_model *m, const fga_init_desc *init, fga_beams **out, fga_stream_t s) {
+    return decompose_impl(m, init, out, (cudaStream_t)s);
+}
+
+fga_status fga_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps, fga_stream_t s_) {
+    cudaStream_t s = (cudaStream_t)s_;
+    FGA_CHECK(m && b, "fga_propagate: NULL argument");
+    FGA_CHECK(nsteps >= 0 && std::isfinite(dt), "fga_propagate: nsteps >= 0 and a finite dt required");
+    for (int n0 = 0; n0 < nsteps; n0 += 64) FGA_TRY(launch_propagate(m, b, dt, std::min(64, nsteps - n0), nullptr, s));
+    b->last_stream = s;
+    return FGA_OK;
+}
+
+// sort the beams' current centres on a grid; returns the permutation and the bucket starts (device)
+static fga_status bin_beams(const fga_beams *b, const BinGrid &g, int32_t **perm, cudaStream_t s) {
+    Workspace &ws = b->ws;
+    const int nbk = 4 * (g.ncells + 1);
+    FGA_TRY(ws.keys.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(b->nb, 1)));
+    FGA_TRY(ws.cell_start.ensure(sizeof(int32_t) * (size_t)(nbk + 1)));
+    const int kind = b->precision == FGA_PREC_FP64 ? Q_F64_SOA : Q_F32_SOA;
+    FGA_TRY(bin_centres(g, b->state.p, kind, b->cap, b->nb, b->flags.as<int32_t>(), ws.keys.as<int32_t>(), s));
+    return sort_keys_to_perm(ws, ws.keys.as<int32_t>(), b->nb, nbk, perm, ws.cell_start.as<int32_t>(), s);
+}
+
+static fga_status host_points(const double *x_dev, int64_t n, std::vector<double> &out, cudaStream_t s) {
+    out.resize((size_t)(3 * n));
+    if (n == 0) return FGA_OK;
+    FGA_CUDA(cudaMemcpyAsync(out.data(), x_dev, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    FGA_CUDA(cudaStreamSynchronize(s));
+    for (double v : out)
+        if (!std::isfinite(v)) {
+            set_error("points must be finite");
+            return FGA_ERR_INVALID_ARG;
+        }
+    return FGA_OK;
+}
+
+// Gaussian sum of the current state at points (records gathered in cell order, state untouched)
+static fga_status reconstruct_now(const fga_beams *b, const double *x_dev, const std::vector<double> &xh, int64_t n,
+                                  double rw, void *u_out, cudaStream_t s) {
+    if (n == 0) return FGA_OK;
+    Workspace &ws = b->ws;
+    const BinGrid g = make_grid(xh.data(), n, rw);
+    int32_t *perm = nullptr;
+    FGA_TRY(bin_beams(b, g, &perm, s));
+    const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
+    FGA_TRY(ws.rec.ensure(rb * REC * (size_t)std::max<int64_t>(b->cap, 1)));
+    FGA_TRY(launch_records_from_state(b, perm, b->nb, ws.rec.p, s));
+    SumPlan plan;
+    FGA_TRY(build_sum_plan(ws, g, ws.cell_start.as<int32_t>(), 4, xh.data(), n, s, plan));
+    return run_sum(ws, plan, b->precision, ws.rec.p, x_dev, b->k, rw, u_out, s);
+}
+
+fga_status fga_reconstruct(const fga_beams *b, const double *x, int64_t n, double rw, void *u_out, fga_stream_t s_) {
+    cudaStream_t s = (cudaStream_t)s_;
+    FGA_CHECK(b, "fga_reconstruct: NULL beams");
+    FGA_CHECK(n >= 0, "fga_reconstruct: n < 0");
+    if (n == 0) return FGA_OK;
+    FGA_CHECK(x && u_out, "fga_reconstruct: NULL points or output");
+    FGA_CHECK(n < ((int64_t)1 << 31), "fga_reconstruct: too many points");
+    if (!(rw > 0)) rw = 6.0 / std::sqrt(b->k);
+    std::vector<double> xh;
+    FGA_TRY(host_points(x, n, xh, s));
+    return reconstruct_now(b, x, xh, n, rw, u_out, s);
+}
+
+fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, void *seis_out,
+                     void *snap_out, fga_stream_t s_) {
+    cudaStream_t s = (cudaStream_t)s_;
+    FGA_CHECK(m && init && sd, "fga_solve: NULL argument");
+    FGA_CHECK(sd->nsteps >= 1 && std::isfinite(sd->dt) && sd->dt != 0.0, "fga_solve: nsteps >= 1 and dt != 0");
+    FGA_CHECK(sd->n_times >= 0 && sd->n_rx >= 0 && sd->n_snap >= 0, "fga_solve: negative counts");
+    FGA_CHECK(sd->n_times == 0 || sd->times, "fga_solve: times is NULL");
+    FGA_CHECK(sd->n_rx == 0 || sd->n_times == 0 || (sd->rx && seis_out), "fga_solve: receivers/output missing");
+    FGA_CHECK(sd->n_snap == 0 || (sd->snap && snap_out), "fga_solve: snapshot points/output missing");
+    const double T = sd->dt * sd->nsteps;
+    std::vector<int> sstep((size_t)sd->n_times);
+    std::vector<double> sth((size_t)sd->n_times);
+    for (int j = 0; j < sd->n_times; j++) {
+        const double t = sd->times[j];
+        const bool inside = sd->dt > 0 ? (t > 0 && t <= T * (1 + 1e-12)) : (t < 0 && t >= T * (1 + 1e-12));
+        FGA_CHECK(std::isfinite(t) && inside, "fga_solve: sample times must lie in (0, nsteps*dt]");
+        FGA_CHECK(j == 0 || (sd->dt > 0 ? t > sd->times[j - 1] : t < sd->times[j - 1]), "fga_solve: times must be monotone");
+        const double u = t / sd->dt;
+        int n = (int)std::floor(u);
+        n = std::min(n, sd->nsteps - 1);
+        sstep[(size_t)j] = n;
+        sth[(size_t)j] = u - n;
+    }
+    fga_beams *b = nullptr;
+    FGA_TRY(fga_decompose(m, init, &b, s_));
+    struct Guard {
+        fga_beams *b;
+        ~Guard() { fga_beams_destroy(b); }
+    } guard{b};
+    const double rw = sd->rw > 0 ? sd->rw : 6.0 / std::sqrt(b->k);
+    const bool fp64 = b->precision == FGA_PREC_FP64;
+    const size_t rb = fp64 ? 8 : 4;
+    Workspace &ws = b->ws;
+    std::vector<double> rxh, snh;
+    const bool seis = sd->n_rx > 0 && sd->n_times > 0;
+    if (seis) FGA_TRY(host_points(sd->rx, sd->n_rx, rxh, s));
+    if (sd->n_snap > 0) FGA_TRY(host_points(sd->snap, sd->n_snap, snh, s));
+    // windows of W steps: the beams are sorted by cell once per window, with cells enlarged by the
+    // largest distance a beam can travel inside the window
+    const double cmax = std::max(m->cmax[0], m->cmax[1]);
+    int W = (int)std::floor(0.25 * rw / std::max(cmax * std::fabs(sd->dt), 1e-300));
+    W = std::max(1, std::min(W, 32));
+    const double margin = sample_hermite_margin(cmax, sd->dt, W);
+    BinGrid grx{};
+    if (seis) grx = make_grid(rxh.data(), sd->n_rx, rw + margin);
+    DevBuf samp;  // per-window sample fractions (R, at offset 0) and local steps (int, at soff)
+    HostBuf hsamp;
+    const int maxs = sd->n_times;
+    const size_t soff = (rb * (size_t)maxs + 15) / 16 * 16;
+    const size_t sbytes = soff + sizeof(int) * (size_t)maxs + 16;
+    if (maxs > 0) {
+        FGA_TRY(samp.ensure(sbytes));
+        FGA_TRY(hsamp.ensure(sbytes));
+    }
+    struct Free {
+        DevBuf &d;
+        HostBuf &h;
+        ~Free() {
+            d.release();
+            h.release();
+        }
+    } fr{samp, hsamp};
+    int js = 0;
+    for (int n0 = 0; n0 < sd->nsteps; n0 += W) {
+        const int nw = std::min(W, sd->nsteps - n0);
+        int j1 = js;
+        while (seis && j1 < sd->n_times && sstep[(size_t)j1] < n0 + nw) j1++;
+        const int ns = j1 - js;
+        if (ns == 0) {
+            FGA_TRY(launch_propagate(m, b, sd->dt, nw, nullptr, s));
+            continue;
+        }
+        int32_t *perm = nullptr;
+        FGA_TRY(bin_beams(b, grx, &perm, s));
+        FGA_TRY(permute_beams(b, perm, s));
+        SumPlan plan;
+        FGA_TRY(build_sum_plan(ws, grx, ws.cell_start.as<int32_t>(), 4, rxh.data(), sd->n_rx, s, plan));  // syncs
+        char *hth = hsamp.as<char>();
+        int *hs = reinterpret_cast<int *>(hth + soff);
+        for (int j = 0; j < ns; j++) {
+            hs[j] = sstep[(size_t)(js + j)] - n0;
+            if (fp64)
+                reinterpret_cast<double *>(hth)[j] = sth[(size_t)(js + j)];
+            else
+                reinterpret_cast<float *>(hth)[j] = (float)sth[(size_t)(js + j)];
+        }
+        FGA_CUDA(cudaMemcpyAsync(samp.p, hsamp.p, sbytes, cudaMemcpyHostToDevice, s));
+        FGA_TRY(ws.rec.ensure(rb * REC * (size_t)b->cap * ns));
+        SampleWindow sw{ns, reinterpret_cast<const int *>(samp.as<char>() + soff), samp.p, ws.rec.p};
+        FGA_TRY(launch_propagate(m, b, sd->dt, nw, &sw, s));
+        for (int j = 0; j < ns; j++) {
+            void *out = static_cast<char *>(seis_out) + rb * 6 * (size_t)sd->n_rx * (size_t)(js + j);
+            const void *rec = static_cast<const char *>(ws.rec.p) + rb * REC * (size_t)b->cap * j;
+            FGA_TRY(run_sum(ws, plan, b->precision, rec, sd->rx, b->k, rw, out, s));
+        }
+        js = j1;
+    }
+    if (sd->n_snap > 0) FGA_TRY(reconstruct_now(b, sd->snap, snh, sd->n_snap, rw, snap_out, s));
+    // the beam set is freed by the guard; its buffers must not be in use
+    FGA_CUDA(cudaStreamSynchronize(s));
+    return FGA_OK;
+}
+
+fga_status fga_beams_count(const fga_beams *b, int64_t *n_by_class) {
+    FGA_CHECK(b && n_by_class, "fga_beams_count: NULL argument");
+    for (int c = 0; c < 4; c++) n_by_class[c] = b->n_cls[c];
+    return FGA_OK;
+}
+
+fga_status fga_beams_export(const fga_beams *b, double *state_host, int32_t *meta_host) {
+    FGA_CHECK(b, "fga_beams_export: NULL beams");
+    FGA_CUDA(cudaStreamSynchronize(b->last_stream));
+    const int64_t cap = b->cap, nb = b->nb;
+    std::vector<int32_t> ids((size_t)nb), fl((size_t)nb);
+    if (nb > 0) {
+        FGA_CUDA(cudaMemcpy(ids.data(), b->id.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost));
+        FGA_CUDA(cudaMemcpy(fl.data(), b->flags.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost));
+    }
+    std::vector<double> st((size_t)(NF * cap));
+    if (state_host && nb > 0) {
+        if (b->precision == FGA_PREC_FP64) {
+            FGA_CUDA(cudaMemcpy(st.data(), b->state.p, 8 * (size_t)(NF * cap), cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> sf((size_t)(NF * cap));
+            FGA_CUDA(cudaMemcpy(sf.data(), b->state.p, 4 * (size_t)(NF * cap), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < sf.size(); i++) st[i] = sf[i];
+        }
+    }
+    for (int64_t i = 0; i < nb; i++) {
+        const int cls = fl[(size_t)i] & FL_CLASS_MASK;
+        const int64_t row = b->off_cls[cls] + ids[(size_t)i];
+        if (meta_host) meta_host[row] = fl[(size_t)i];
+        if (state_host) {
+            double *o = state_host + row * 48;
+            for (int f = 0; f < NF; f++) o[f] = st[(size_t)(f * cap + i)];
+            o[46] = 0.0;
+            o[47] = 0.0;
+        }
+    }
+    return FGA_OK;
+}
+
+fga_status fga_beams_destroy(fga_beams *b) {
+    if (!b) return FGA_OK;
+    b->ws.release();
+    for (DevBuf *d : {&b->state, &b->state_alt, &b->flags, &b->flags_alt, &b->id, &b->id_alt}) d->release();
+    delete b;
+    return FGA_OK;
+}
+
+fga_status fga_bin(const float *Q, int64_t n, const float origin[3], float inv_h, const int nc[3], int32_t *keys,
+                   int32_t *perm, int32_t *cell_start, fga_stream_t s_) {
+    cudaStream_t s = (cudaStream_t)s_;
+    FGA_CHECK(origin && nc && perm && cell_start, "fga_bin: NULL argument");
+    FGA_CHECK(n >= 0 && n < ((int64_t)1 << 31), "fga_bin: n out of range");
+    FGA_CHECK(n == 0 || Q, "fga_bin: NULL centres");
+    FGA_CHECK(std::isfinite(inv_h) && inv_h > 0, "fga_bin: inv_h must be > 0");
+    BinGrid g{};
+    int64_t ncell = 1;
+    for (int d = 0; d < 3; d++) {
+        FGA_CHECK(nc[d] >= 1, "fga_bin: nc must be >= 1");
+        g.o[d] = origin[d];
+        g.nc[d] = nc[d];
+        ncell *= nc[d];
+    }
+    FGA_CHECK(ncell < (1 << 24), "fga_bin: too many cells");
+    g.ncells = (int)ncell;
+    g.inv_h = inv_h;
+    g.clamp = true;
+    static thread_local Workspace ws;  // scratch of the standalone binning entry point
+    FGA_TRY(ws.keys.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
+    FGA_TRY(bin_centres(g, Q, Q_F32_AOS3, 0, n, nullptr, ws.keys.as<int32_t>(), s));
+    if (keys && n > 0) FGA_CUDA(cudaMemcpyAsync(keys, ws.keys.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    int32_t *pv = nullptr;
+    FGA_TRY(sort_keys_to_perm(ws, ws.keys.as<int32_t>(), n, g.ncells, &pv, cell_start, s));
+    if (n > 0) FGA_CUDA(cudaMemcpyAsync(perm, pv, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    FGA_CUDA(cudaStreamSynchronize(s));
+    return FGA_OK;
+}
+
+}  // extern "C"

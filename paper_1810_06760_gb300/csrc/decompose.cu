@@ -1,0 +1,293 @@
+// A1-A2: wave-packet (FBI) transform of the initial data (Eq. psi) as three per-axis complex
+// contractions, then beam initialisation (Eqs. alpha^k, ini_plus/ini_minus, op_zZ_app).
+#include <cmath>
+#include <cstring>
+
+#include "fga_beam.cuh"
+
+namespace fga {
+
+// per-axis kernel K[a][i] = exp(-i k p (y_i - q) - k (y_i - q)^2 / 2), a = iq * np + jp
+template <typename R>
+__global__ void fbi_axis_kernel(C2<R> *__restrict__ K, int nq, int np, int ny, double q0, double dq, double p0,
+                                double dp, double y0, double dy, double k) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int A = nq * np;
+    if (idx >= A * ny) return;
+    const int a = idx / ny, i = idx % ny;
+    const int iq = a / np, jp = a % np;
+    const double q = q0 + iq * dq, p = p0 + jp * dp, y = y0 + i * dy;
+    const double d = y - q;
+    double s, c;
+    sincos(-k * p * d, &s, &c);
+    const double e = exp(-0.5 * k * d * d);
+    K[idx] = {(R)(e * c), (R)(e * s)};
+}
+
+template <typename R> __device__ __forceinline__ C2<R> to_c2(const double2 v) { return {(R)v.x, (R)v.y}; }
+template <typename R> __device__ __forceinline__ C2<R> to_c2(const C2<R> v) { return v; }
+
+// Batched strided complex GEMM: C[z][m][n] = scale * sum_k A[z][m][k] B[n][k].
+// A elements of type TA (complex128 input or R intermediates), B and C of type R.
+template <typename R, typename TA>
+__global__ void __launch_bounds__(256) cgemm_kernel(const TA *__restrict__ A, int64_t sAz, int64_t sAm, int64_t sAk,
+                                                    const C2<R> *__restrict__ B, int64_t sBn, int64_t sBk,
+                                                    C2<R> *__restrict__ Cm, int64_t sCz, int64_t sCm, int64_t sCn,
+                                                    int64_t M, int N, int K, R scale) {
+    constexpr int TM = 64, TN = 64, TK = 16;
+    __shared__ C2<R> As[TK][TM + 1];
+    __shared__ C2<R> Bs[TK][TN + 1];
+    const int z = blockIdx.z;
+    const int64_t m0 = (int64_t)blockIdx.x * TM;
+    const int n0 = blockIdx.y * TN;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    C2<R> acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = {R(0), R(0)};
+    const TA *Az = A + z * sAz;
+    for (int k0 = 0; k0 < K; k0 += TK) {
+        for (int e = threadIdx.x; e < TK * TM; e += 256) {
+            const int mm = e % TM, kk = e / TM;
+            const int64_t gm = m0 + mm;
+            const int gk = k0 + kk;
+            C2<R> v = {R(0), R(0)};
+            if (gm < M && gk < K) v = to_c2<R>(Az[gm * sAm + (int64_t)gk * sAk]);
+            As[kk][mm] = v;
+        }
+        for (int e = threadIdx.x; e < TK * TN; e += 256) {
+            const int nn = e % TN, kk = e / TN;
+            const int gn = n0 + nn, gk = k0 + kk;
+            Bs[kk][nn] = (gn < N && gk < K) ? B[(int64_t)gn * sBn + (int64_t)gk * sBk] : C2<R>{R(0), R(0)};
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; kk++) {
+            C2<R> a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    acc[i][j].r += a[i].r * b[j].r - a[i].i * b[j].i;
+                    acc[i][j].i += a[i].r * b[j].i + a[i].i * b[j].r;
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t gm = m0 + tx + 16 * i;
+            const int gn = n0 + ty + 16 * j;
+            if (gm < M && gn < N)
+                Cm[z * sCz + gm * sCm + (int64_t)gn * sCn] = {acc[i][j].r * scale, acc[i][j].i * scale};
+        }
+}
+
+template <typename R, typename TA>
+static fga_status cgemm(const TA *A, int64_t sAz, int64_t sAm, int64_t sAk, const C2<R> *B, int64_t sBn, int64_t sBk,
+                        C2<R> *Cm, int64_t sCz, int64_t sCm, int64_t sCn, int Z, int64_t M, int N, int K, R scale,
+                        cudaStream_t s) {
+    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64), (unsigned)Z);
+    cgemm_kernel<R, TA><<<grid, 256, 0, s>>>(A, sAz, sAm, sAk, B, sBn, sBk, Cm, sCz, sCm, sCn, M, N, K, scale);
+    FGA_CUDA(cudaGetLastError());
+    return FGA_OK;
+}
+
+// F[a0][a1][a2][c] = dy^3 sum_y f[y0][y1][y2][c] K0[a0][y0] K1[a1][y1] K2[a2][y2]
+template <typename R>
+static fga_status fbi_transform(const fga_init_desc *d, const double2 *f, C2<R> *const Kax[3], C2<R> *T1, C2<R> *T2,
+                                C2<R> *F, cudaStream_t s) {
+    const int A = d->nq * d->np;
+    const int n0 = d->ny[0], n1 = d->ny[1], n2 = d->ny[2];
+    // stage 1 (contract y2), one GEMM per component c: T1[(y0,y1)][a2][c]
+    FGA_TRY((cgemm<R, double2>(f, 1, (int64_t)n2 * 3, 3, Kax[2], n2, 1, T1, 1, (int64_t)A * 3, 3, 3,
+                               (int64_t)n0 * n1, A, n2, R(1), s)));
+    // stage 2 (contract y1): T2[y0][a1][(a2,c)] ; batch y0, m = (a2,c), n = a1, k = y1
+    FGA_TRY((cgemm<R, C2<R>>(T1, (int64_t)n1 * A * 3, 1, (int64_t)A * 3, Kax[1], n1, 1, T2, (int64_t)A * A * 3, 1,
+                              (int64_t)A * 3, n0, (int64_t)A * 3, A, n1, R(1), s)));
+    // stage 3 (contract y0): F[a0][(a1,a2,c)], m = (a1,a2,c), n = a0, k = y0
+    const R vol = (R)(d->dy[0] * d->dy[1] * d->dy[2]);
+    FGA_TRY((cgemm<R, C2<R>>(T2, 0, 1, (int64_t)A * A * 3, Kax[0], n0, 1, F, 0, 1, (int64_t)A * A * 3, 1,
+                              (int64_t)A * A * 3, A, n0, vol, s)));
+    return FGA_OK;
+}
+
+// one beam per (mesh point, requested class)
+template <typename R, int MED>
+__global__ void beam_init_kernel(ModelDev Md, const C2<R> *__restrict__ F, const C2<R> *__restrict__ G, int nq, int np,
+                                 double3 q0, double3 dq, double3 p0, double3 dp, double k, int64_t M, int cls,
+                                 int64_t off, int64_t cap, R *__restrict__ st, int32_t *__restrict__ flags,
+                                 int32_t *__restrict__ ids) {
+    const int64_t mi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (mi >= M) return;
+    const int64_t NP = (int64_t)np * np * np;
+    const int64_t iq = mi / NP, ip = mi % NP;
+    const int qi[3] = {(int)(iq / ((int64_t)nq * nq)), (int)((iq / nq) % nq), (int)(iq % nq)};
+    const int pj[3] = {(int)(ip / ((int64_t)np * np)), (int)((ip / np) % np), (int)(ip % np)};
+    const double qd[3] = {q0.x + qi[0] * dq.x, q0.y + qi[1] * dq.y, q0.z + qi[2] * dq.z};
+    const double pd[3] = {p0.x + pj[0] * dp.x, p0.y + pj[1] * dp.y, p0.z + pj[2] * dp.z};
+    const int A = nq * np;
+    const int64_t fidx = (((int64_t)(qi[0] * np + pj[0]) * A + (qi[1] * np + pj[1])) * A + (qi[2] * np + pj[2])) * 3;
+    const int wave = cls >= 2;
+    R q[3] = {(R)qd[0], (R)qd[1], (R)qd[2]};
+    R p[3] = {(R)pd[0], (R)pd[1], (R)pd[2]};
+    R cf[10];
+    model_eval<R, MED>(Md, wave, q, cf);
+    const R pn = Real<R>::sqrt_(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    const R sgn = (cls & 1) ? R(-1) : R(1);
+    const R gsc = sgn / ((R)k * cf[0] * pn);  // +- 1/(k c(q) |p|)
+    R dirs[2][3];
+    int nd = 1;
+    int fl = cls;
+    if (!wave) {
+        for (int d = 0; d < 3; d++) dirs[0][d] = p[d] / pn;
+    } else {
+        const bool r1 = (p[0] * p[0] + p[1] * p[1]) < R(0.01) * pn * pn;
+        if (r1) fl |= FL_REF_E1;
+        s_frame<R>(p, r1, dirs[0], dirs[1]);
+        nd = 2;
+    }
+    const R a0 = R(2.8284271247461900976033774484194);  // 2^{3/2}
+    R amp[4] = {R(0), R(0), R(0), R(0)};
+    for (int j = 0; j < nd; j++) {
+        R fr = R(0), fi = R(0), gr = R(0), gi = R(0);
+        for (int d = 0; d < 3; d++) {
+            fr += F[fidx + d].r * dirs[j][d];
+            fi += F[fidx + d].i * dirs[j][d];
+            if (G) {
+                gr += G[fidx + d].r * dirs[j][d];
+                gi += G[fidx + d].i * dirs[j][d];
+            }
+        }
+        // psi = (F.n +- i G.n / (k c |p|)) / 2
+        amp[2 * j] = a0 * R(0.5) * (fr - gsc * gi);
+        amp[2 * j + 1] = a0 * R(0.5) * (fi + gsc * gr);
+    }
+    const int64_t b = off + mi;
+    R y[NF];
+    for (int f = 0; f < NF; f++) y[f] = R(0);
+    for (int d = 0; d < 3; d++) {
+        y[F_Q + d] = q[d];
+        y[F_P + d] = p[d];
+        y[F_DQ + 2 * (3 * d + d)] = R(1);      // dzQ = I
+        y[F_DP + 2 * (3 * d + d) + 1] = R(-1); // dzP = -i I
+    }
+    y[F_A0] = amp[0];
+    y[F_A0 + 1] = amp[1];
+    y[F_A1] = amp[2];
+    y[F_A1 + 1] = amp[3];
+    for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y[f];
+    flags[b] = fl;
+    ids[b] = (int32_t)mi;
+}
+
+template <typename R>
+static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fga_beams *b, cudaStream_t s) {
+    const int A = d->nq * d->np;
+    const int64_t nyy = (int64_t)d->ny[0] * d->ny[1] * d->ny[2];
+    (void)nyy;
+    DevBuf Kb, T1, T2, Fb, Gb;
+    const size_t kbytes = sizeof(C2<R>) * (size_t)A * (d->ny[0] + d->ny[1] + d->ny[2]);
+    FGA_TRY(Kb.ensure(kbytes));
+    C2<R> *Kax[3];
+    Kax[0] = Kb.as<C2<R>>();
+    Kax[1] = Kax[0] + (size_t)A * d->ny[0];
+    Kax[2] = Kax[1] + (size_t)A * d->ny[1];
+    for (int ax = 0; ax < 3; ax++) {
+        const int tot = A * d->ny[ax];
+        fbi_axis_kernel<R><<<(tot + 255) / 256, 256, 0, s>>>(Kax[ax], d->nq, d->np, d->ny[ax], d->q0[ax], d->dq[ax],
+                                                            d->p0[ax], d->dp[ax], d->y0[ax], d->dy[ax], d->k);
+    }
+    FGA_CUDA(cudaGetLastError());
+    FGA_TRY(T1.ensure(sizeof(C2<R>) * (size_t)d->ny[0] * d->ny[1] * A * 3));
+    FGA_TRY(T2.ensure(sizeof(C2<R>) * (size_t)d->ny[0] * A * A * 3));
+    const size_t Fn = (size_t)A * A * A * 3;
+    FGA_TRY(Fb.ensure(sizeof(C2<R>) * Fn));
+    FGA_TRY(fbi_transform<R>(d, static_cast<const double2 *>(d->f), Kax, T1.as<C2<R>>(), T2.as<C2<R>>(),
+                             Fb.as<C2<R>>(), s));
+    const C2<R> *G = nullptr;
+    if (d->g) {
+        FGA_TRY(Gb.ensure(sizeof(C2<R>) * Fn));
+        FGA_TRY(fbi_transform<R>(d, static_cast<const double2 *>(d->g), Kax, T1.as<C2<R>>(), T2.as<C2<R>>(),
+                                 Gb.as<C2<R>>(), s));
+        G = Gb.as<C2<R>>();
+    }
+    const int64_t M = (int64_t)d->nq * d->nq * d->nq * d->np * d->np * d->np;
+    const double3 q0 = {d->q0[0], d->q0[1], d->q0[2]}, dq = {d->dq[0], d->dq[1], d->dq[2]};
+    const double3 p0 = {d->p0[0], d->p0[1], d->p0[2]}, dp = {d->dp[0], d->dp[1], d->dp[2]};
+    for (int cls = 0; cls < 4; cls++) {
+        if (!(d->class_mask & (1u << cls))) continue;
+        const unsigned blocks = (unsigned)((M + 127) / 128);
+#define FGA_INIT(MED)                                                                                               \
+    beam_init_kernel<R, MED><<<blocks, 128, 0, s>>>(m->dev, Fb.as<C2<R>>(), G, d->nq, d->np, q0, dq, p0, dp, d->k, M, \
+                                                    cls, b->off_cls[cls], b->cap, b->state.as<R>(),                   \
+                                                    b->flags.as<int32_t>(), b->id.as<int32_t>())
+        switch (m->dev.kind) {
+        case FGA_MEDIUM_CONST: FGA_INIT(FGA_MEDIUM_CONST); break;
+        case FGA_MEDIUM_SINE: FGA_INIT(FGA_MEDIUM_SINE); break;
+        case FGA_MEDIUM_GRID: FGA_INIT(FGA_MEDIUM_GRID); break;
+        default: FGA_INIT(FGA_MEDIUM_LAYERED); break;
+        }
+#undef FGA_INIT
+    }
+    FGA_CUDA(cudaGetLastError());
+    // the temporaries are released when this scope ends; make sure the stream is done with them
+    FGA_CUDA(cudaStreamSynchronize(s));
+    Kb.release();
+    T1.release();
+    T2.release();
+    Fb.release();
+    Gb.release();
+    return FGA_OK;
+}
+
+fga_status decompose_impl(const fga_model *m, const fga_init_desc *d, fga_beams **out, cudaStream_t s) {
+    FGA_CHECK(m && d && out, "fga_decompose: NULL argument");
+    FGA_CHECK(std::isfinite(d->k) && d->k > 0, "fga_decompose: k must be > 0");
+    FGA_CHECK(d->f != nullptr, "fga_decompose: f is NULL");
+    FGA_CHECK(d->nq >= 1 && d->np >= 1, "fga_decompose: nq, np must be >= 1");
+    FGA_CHECK(d->ny[0] >= 1 && d->ny[1] >= 1 && d->ny[2] >= 1, "fga_decompose: ny must be >= 1");
+    FGA_CHECK((d->class_mask & 15u) != 0 && (d->class_mask & ~15u) == 0, "fga_decompose: class_mask must be in 1..15");
+    FGA_CHECK(d->precision == FGA_PREC_FP32 || d->precision == FGA_PREC_FP64, "fga_decompose: bad precision");
+    for (int a = 0; a < 3; a++) FGA_CHECK(d->dy[a] > 0 && d->dq[a] > 0 && d->dp[a] > 0, "fga_decompose: spacings must be > 0");
+    const int64_t M = (int64_t)d->nq * d->nq * d->nq * d->np * d->np * d->np;
+    FGA_CHECK(M * 4 < (int64_t)1 << 31, "fga_decompose: more than 2^31 beams");
+    fga_beams *b = new fga_beams();
+    b->precision = d->precision;
+    b->k = d->k;
+    double vol = 1.0;
+    for (int a = 0; a < 3; a++) vol *= d->dq[a] * d->dp[a];
+    b->w = vol / std::pow(2.0 * M_PI / d->k, 4.5);
+    int64_t off = 0;
+    for (int c = 0; c < 4; c++) {
+        b->off_cls[c] = off;
+        b->n_cls[c] = (d->class_mask & (1u << c)) ? M : 0;
+        off += b->n_cls[c];
+    }
+    b->nb = off;
+    b->cap = (off + 31) / 32 * 32;
+    const size_t rb = d->precision == FGA_PREC_FP64 ? 8 : 4;
+    fga_status st = FGA_OK;
+    if ((st = b->state.ensure(rb * NF * b->cap)) != FGA_OK || (st = b->flags.ensure(4 * b->cap)) != FGA_OK ||
+        (st = b->id.ensure(4 * b->cap)) != FGA_OK) {
+        fga_beams_destroy(b);
+        return st;
+    }
+    st = d->precision == FGA_PREC_FP64 ? decompose_typed<double>(m, d, b, s) : decompose_typed<float>(m, d, b, s);
+    if (st != FGA_OK) {
+        fga_beams_destroy(b);
+        return st;
+    }
+    b->last_stream = s;
+    *out = b;
+    return FGA_OK;
+}
+
+}  // namespace fga

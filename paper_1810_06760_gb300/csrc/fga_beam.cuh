@@ -1,0 +1,302 @@
+// Device functions of one beam: model sampling, the right-hand side of the FGA ODEs and the
+// reconstruction record.  Templated on the arithmetic type R (float for the FP32 path, double
+// for the FP64 path) and on the medium kind, so that a constant medium compiles without any
+// derivative arithmetic.
+#pragma once
+
+#include "fga_internal.cuh"
+
+namespace fga {
+
+template <typename R> struct Real;
+template <> struct Real<float> {
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
+    static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
+};
+template <> struct Real<double> {
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
+    static __device__ __forceinline__ double floor_(double x) { return floor(x); }
+};
+
+// ---------------------------------------------------------------------------------------------
+// A0: c, grad c, Hessian c at x (10 fields: c, c1, c2, c3, c11, c12, c13, c22, c23, c33)
+// ---------------------------------------------------------------------------------------------
+template <typename R, int MED>
+__device__ __forceinline__ void model_eval(const ModelDev &M, int wave, const R x[3], R c[10]) {
+    if (MED == FGA_MEDIUM_CONST) {
+        c[0] = wave ? (R)M.cs0 : (R)M.cp0;
+#pragma unroll
+        for (int f = 1; f < 10; f++) c[f] = R(0);
+    } else if (MED == FGA_MEDIUM_SINE) {
+        R s[3], k[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) Real<R>::sincospi_(R(2) * x[d], &s[d], &k[d]);
+        const R A = (R)M.amp, w = R(6.283185307179586476925286766559);
+        const R sc = wave ? (R)M.cs_ratio : R(1);
+        const R Aw = A * w * sc, Aww = A * w * w * sc;
+        const R s123 = s[0] * s[1] * s[2];
+        c[0] = sc * ((R)M.cp0 + A * s123);
+        c[1] = Aw * k[0] * s[1] * s[2];
+        c[2] = Aw * s[0] * k[1] * s[2];
+        c[3] = Aw * s[0] * s[1] * k[2];
+        c[4] = -Aww * s123;
+        c[5] = Aww * k[0] * k[1] * s[2];
+        c[6] = Aww * k[0] * s[1] * k[2];
+        c[7] = -Aww * s123;
+        c[8] = Aww * s[0] * k[1] * k[2];
+        c[9] = -Aww * s123;
+    } else if (MED == FGA_MEDIUM_GRID) {
+        const float4 *__restrict__ G = wave ? M.gs : M.gp;
+        int i[3];
+        R fr[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            R t = (x[d] - (R)M.o[d]) * (R)M.inv_h[d];
+            const R hi = R(M.n[d] - 1);
+            t = t < R(0) ? R(0) : (t > hi ? hi : t);
+            int id = (int)Real<R>::floor_(t);
+            id = id > M.n[d] - 2 ? M.n[d] - 2 : id;
+            i[d] = id;
+            fr[d] = t - R(id);
+        }
+        const int64_t s1 = M.n[2], s0 = (int64_t)M.n[1] * M.n[2];
+        const int64_t base = (int64_t)i[0] * s0 + (int64_t)i[1] * s1 + i[2];
+        R acc[10];
+#pragma unroll
+        for (int f = 0; f < 10; f++) acc[f] = R(0);
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            R e[10];
+#pragma unroll
+            for (int f = 0; f < 10; f++) e[f] = R(0);
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                const int64_t node = base + a * s0 + b * s1;
+                const float4 *p0 = G + 3 * node;
+                const float4 u0 = __ldg(p0), u1 = __ldg(p0 + 1), u2 = __ldg(p0 + 2);
+                const float4 v0 = __ldg(p0 + 3), v1 = __ldg(p0 + 4), v2 = __ldg(p0 + 5);
+                const float lo[10] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w, u2.x, u2.y};
+                const float hi[10] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y};
+                const R wb = b ? fr[1] : R(1) - fr[1];
+#pragma unroll
+                for (int f = 0; f < 10; f++) {
+                    const R l = (R)lo[f];
+                    e[f] += wb * (l + fr[2] * ((R)hi[f] - l));
+                }
+            }
+            const R wa = a ? fr[0] : R(1) - fr[0];
+#pragma unroll
+            for (int f = 0; f < 10; f++) acc[f] += wa * e[f];
+        }
+#pragma unroll
+        for (int f = 0; f < 10; f++) c[f] = acc[f];
+    } else {  // layered
+        int l = 0;
+        for (int q = 0; q < M.nlay - 1; q++) l += (x[2] >= (R)M.zif[q]) ? 1 : 0;
+        c[0] = wave ? (R)M.lcs[l] : (R)M.lcp[l];
+#pragma unroll
+        for (int f = 1; f < 10; f++) c[f] = R(0);
+    }
+}
+
+// S polarisation frame: N_sh = e x P / |e x P| (e = e3, or e1 for near-vertical beams),
+// N_sv = N_sh x P/|P|.  Returns |e x P|.
+template <typename R>
+__device__ __forceinline__ R s_frame(const R P[3], bool ref_e1, R Nsv[3], R Nsh[3]) {
+    R v0, v1, v2;
+    if (ref_e1) {
+        v0 = R(0);
+        v1 = -P[2];
+        v2 = P[1];
+    } else {
+        v0 = -P[1];
+        v1 = P[0];
+        v2 = R(0);
+    }
+    const R vn = Real<R>::sqrt_(v0 * v0 + v1 * v1 + v2 * v2);
+    const R iv = R(1) / vn;
+    Nsh[0] = v0 * iv;
+    Nsh[1] = v1 * iv;
+    Nsh[2] = v2 * iv;
+    const R ip = Real<R>::rsqrt_(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+    Nsv[0] = (Nsh[1] * P[2] - Nsh[2] * P[1]) * ip;
+    Nsv[1] = (Nsh[2] * P[0] - Nsh[0] * P[2]) * ip;
+    Nsv[2] = (Nsh[0] * P[1] - Nsh[1] * P[0]) * ip;
+    return vn;
+}
+
+// complex helpers on (re, im) pairs kept in scalars
+template <typename R> struct C2 {
+    R r, i;
+};
+template <typename R> __device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
+    return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r};
+}
+template <typename R> __device__ __forceinline__ C2<R> csub(C2<R> a, C2<R> b) { return {a.r - b.r, a.i - b.i}; }
+template <typename R> __device__ __forceinline__ C2<R> cmulsub(C2<R> a, C2<R> b, C2<R> c, C2<R> d) {
+    // a*b - c*d
+    return {a.r * b.r - a.i * b.i - (c.r * d.r - c.i * d.i), a.r * b.i + a.i * b.r - (c.r * d.i + c.i * d.r)};
+}
+
+// ---------------------------------------------------------------------------------------------
+// A3: right-hand side of the beam ODEs (Eqs. char_plus/char_minus, DzDt, amp_P, amp_SV, amp_SH)
+//   Q' = sg c P^,  P' = -sg |P| grad c
+//   dzQ'_mj = sg [ (c/|P|) dzP_mj + (u_m - (c/|P|) v_m) P^_j ],   u = dzQ grad c,  v = dzP P^
+//   dzP'_mj = -sg [ |P| (dzQ Hess c)_mj + v_m (grad c)_j ]
+//   gamma = sg grad c . P^ + tr(Z^-1 Z')/2,  Z = dzQ + i dzP, via the cofactor matrix of Z
+//   P: a' = gamma a;  S: a_sv' = gamma a_sv - a_sh w,  a_sh' = gamma a_sh + a_sv w,
+//      w = dN_sh/dt . N_sv = (e x P') . N_sv / |e x P|
+// ---------------------------------------------------------------------------------------------
+template <typename R, int WAVE, int MED>
+__device__ __forceinline__ void beam_rhs(const ModelDev &M, R sg, bool ref_e1, const R *__restrict__ y,
+                                         R *__restrict__ f) {
+    R cf[10];
+    const R Q[3] = {y[F_Q], y[F_Q + 1], y[F_Q + 2]};
+    model_eval<R, MED>(M, WAVE, Q, cf);
+    const R c = cf[0];
+    const R g[3] = {cf[1], cf[2], cf[3]};
+    const R H[3][3] = {{cf[4], cf[5], cf[6]}, {cf[5], cf[7], cf[8]}, {cf[6], cf[8], cf[9]}};
+    const R P[3] = {y[F_P], y[F_P + 1], y[F_P + 2]};
+    const R ip = Real<R>::rsqrt_(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+    const R pn = R(1) / ip;
+    const R Ph[3] = {P[0] * ip, P[1] * ip, P[2] * ip};
+    const R sc = sg * c;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        f[F_Q + d] = sc * Ph[d];
+        f[F_P + d] = -sg * pn * g[d];
+    }
+    const R cip = c * ip;
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        R ur = R(0), ui = R(0), vr = R(0), vi = R(0);
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+            ur += y[F_DQ + 2 * (3 * m + l)] * g[l];
+            ui += y[F_DQ + 2 * (3 * m + l) + 1] * g[l];
+            vr += y[F_DP + 2 * (3 * m + l)] * Ph[l];
+            vi += y[F_DP + 2 * (3 * m + l) + 1] * Ph[l];
+        }
+        const R wr = ur - cip * vr, wi = ui - cip * vi;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            f[F_DQ + 2 * (3 * m + j)] = sg * (cip * y[F_DP + 2 * (3 * m + j)] + wr * Ph[j]);
+            f[F_DQ + 2 * (3 * m + j) + 1] = sg * (cip * y[F_DP + 2 * (3 * m + j) + 1] + wi * Ph[j]);
+            R hr = R(0), hi = R(0);
+#pragma unroll
+            for (int l = 0; l < 3; l++) {
+                hr += y[F_DQ + 2 * (3 * m + l)] * H[l][j];
+                hi += y[F_DQ + 2 * (3 * m + l) + 1] * H[l][j];
+            }
+            f[F_DP + 2 * (3 * m + j)] = -sg * (pn * hr + vr * g[j]);
+            f[F_DP + 2 * (3 * m + j) + 1] = -sg * (pn * hi + vi * g[j]);
+        }
+    }
+    // Z = dzQ + i dzP and Z' likewise
+    C2<R> Z[3][3], Zd[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; m++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const int e = 2 * (3 * m + j);
+            Z[m][j] = {y[F_DQ + e] - y[F_DP + e + 1], y[F_DQ + e + 1] + y[F_DP + e]};
+            Zd[m][j] = {f[F_DQ + e] - f[F_DP + e + 1], f[F_DQ + e + 1] + f[F_DP + e]};
+        }
+    // cofactors C_ij; tr(Z^-1 Z') = sum_ij C_ij Z'_ij / det Z
+    C2<R> Cf[3][3];
+    Cf[0][0] = cmulsub(Z[1][1], Z[2][2], Z[1][2], Z[2][1]);
+    Cf[0][1] = cmulsub(Z[1][2], Z[2][0], Z[1][0], Z[2][2]);
+    Cf[0][2] = cmulsub(Z[1][0], Z[2][1], Z[1][1], Z[2][0]);
+    Cf[1][0] = cmulsub(Z[0][2], Z[2][1], Z[0][1], Z[2][2]);
+    Cf[1][1] = cmulsub(Z[0][0], Z[2][2], Z[0][2], Z[2][0]);
+    Cf[1][2] = cmulsub(Z[0][1], Z[2][0], Z[0][0], Z[2][1]);
+    Cf[2][0] = cmulsub(Z[0][1], Z[1][2], Z[0][2], Z[1][1]);
+    Cf[2][1] = cmulsub(Z[0][2], Z[1][0], Z[0][0], Z[1][2]);
+    Cf[2][2] = cmulsub(Z[0][0], Z[1][1], Z[0][1], Z[1][0]);
+    R dr = R(0), di = R(0), tr = R(0), ti = R(0);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        dr += Z[0][j].r * Cf[0][j].r - Z[0][j].i * Cf[0][j].i;
+        di += Z[0][j].r * Cf[0][j].i + Z[0][j].i * Cf[0][j].r;
+    }
+#pragma unroll
+    for (int m = 0; m < 3; m++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            tr += Cf[m][j].r * Zd[m][j].r - Cf[m][j].i * Zd[m][j].i;
+            ti += Cf[m][j].r * Zd[m][j].i + Cf[m][j].i * Zd[m][j].r;
+        }
+    const R idn = R(1) / (dr * dr + di * di);
+    // gamma = sg grad c . P^ + (tr / det) / 2
+    const R gr = sg * (g[0] * Ph[0] + g[1] * Ph[1] + g[2] * Ph[2]) + R(0.5) * (tr * dr + ti * di) * idn;
+    const R gi = R(0.5) * (ti * dr - tr * di) * idn;
+    const R a0r = y[F_A0], a0i = y[F_A0 + 1];
+    if (WAVE == 0) {
+        f[F_A0] = gr * a0r - gi * a0i;
+        f[F_A0 + 1] = gr * a0i + gi * a0r;
+        f[F_A1] = R(0);
+        f[F_A1 + 1] = R(0);
+    } else {
+        R Nsv[3], Nsh[3];
+        const R vn = s_frame<R>(P, ref_e1, Nsv, Nsh);
+        const R *Pd = f + F_P;
+        R ePd0, ePd1, ePd2;
+        if (ref_e1) {
+            ePd0 = R(0);
+            ePd1 = -Pd[2];
+            ePd2 = Pd[1];
+        } else {
+            ePd0 = -Pd[1];
+            ePd1 = Pd[0];
+            ePd2 = R(0);
+        }
+        const R om = (ePd0 * Nsv[0] + ePd1 * Nsv[1] + ePd2 * Nsv[2]) / vn;
+        const R a1r = y[F_A1], a1i = y[F_A1 + 1];
+        f[F_A0] = gr * a0r - gi * a0i - om * a1r;
+        f[F_A0 + 1] = gr * a0i + gi * a0r - om * a1i;
+        f[F_A1] = gr * a1r - gi * a1i + om * a0r;
+        f[F_A1 + 1] = gr * a1i + gi * a1r + om * a0i;
+    }
+}
+
+// Reconstruction record at fraction th of a step of size dt: Q, P by cubic Hermite from
+// (y0, y0', y1, y1'), amplitudes linear in th; A = w a P^ (P) or w (a_sv N_sv + a_sh N_sh) (S).
+template <typename R, int WAVE>
+__device__ __forceinline__ void beam_record(bool ref_e1, const R *y0, const R *d0, const R *y1, const R *d1,
+                                            R dt, R th, R w, R rec[REC]) {
+    const R th2 = th * th, th3 = th2 * th;
+    const R h00 = R(2) * th3 - R(3) * th2 + R(1), h10 = th3 - R(2) * th2 + th;
+    const R h01 = R(3) * th2 - R(2) * th3, h11 = th3 - th2;
+    R P[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        rec[d] = h00 * y0[F_Q + d] + h10 * dt * d0[F_Q + d] + h01 * y1[F_Q + d] + h11 * dt * d1[F_Q + d];
+        P[d] = h00 * y0[F_P + d] + h10 * dt * d0[F_P + d] + h01 * y1[F_P + d] + h11 * dt * d1[F_P + d];
+        rec[3 + d] = P[d];
+    }
+    const R u = R(1) - th;
+    const R a0r = w * (u * y0[F_A0] + th * y1[F_A0]), a0i = w * (u * y0[F_A0 + 1] + th * y1[F_A0 + 1]);
+    if (WAVE == 0) {
+        const R ip = Real<R>::rsqrt_(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            rec[6 + 2 * d] = a0r * P[d] * ip;
+            rec[7 + 2 * d] = a0i * P[d] * ip;
+        }
+    } else {
+        const R a1r = w * (u * y0[F_A1] + th * y1[F_A1]), a1i = w * (u * y0[F_A1 + 1] + th * y1[F_A1 + 1]);
+        R Nsv[3], Nsh[3];
+        s_frame<R>(P, ref_e1, Nsv, Nsh);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            rec[6 + 2 * d] = a0r * Nsv[d] + a1r * Nsh[d];
+            rec[7 + 2 * d] = a0i * Nsv[d] + a1i * Nsh[d];
+        }
+    }
+}
+
+}  // namespace fga

@@ -1,0 +1,134 @@
+// Internal declarations of the GB300 FGA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fga.h"
+
+namespace fga {
+
+// Beam state: 46 reals per beam, stored structure-of-arrays with stride `cap` (field f of beam b
+// at base[f * cap + b]):
+//   0-2 Q, 3-5 P, 6-23 dzQ (entry [m][j] re at 6 + 2(3m+j), im at 7 + 2(3m+j)), 24-41 dzP (same
+//   order), 42-43 amplitude a (P) or a_sv (S), 44-45 a_sh (S; zero for P).
+constexpr int NF = 46;
+constexpr int F_Q = 0, F_P = 3, F_DQ = 6, F_DP = 24, F_A0 = 42, F_A1 = 44;
+// Reconstruction record: Q(3), P(3), polarised amplitude times the quadrature weight (3 complex).
+constexpr int REC = 12;
+constexpr int MAX_LAYERS = 8;
+
+// flags per beam
+constexpr int FL_CLASS_MASK = 3;  // 0 P+, 1 P-, 2 S+, 3 S-
+constexpr int FL_REF_E1 = 4;      // S frame built on e1 instead of e3
+
+struct ModelDev {
+    int kind;
+    double cp0, cs0, amp, cs_ratio;
+    int n[3];
+    double o[3], h[3], inv_h[3];
+    const float4 *gp, *gs;  // grid: 3 float4 (10 fields + 2 pad) per node
+    int nlay;
+    double zif[MAX_LAYERS], lcp[MAX_LAYERS], lcs[MAX_LAYERS], lrho[MAX_LAYERS];
+};
+
+// error handling ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+fga_status cuda_fail(cudaError_t e, const char *what);
+
+#define FGA_CUDA(call)                                        \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return ::fga::cuda_fail(e_, #call); \
+    } while (0)
+#define FGA_CHECK(cond, msg)                 \
+    do {                                     \
+        if (!(cond)) {                       \
+            ::fga::set_error(msg);           \
+            return FGA_ERR_INVALID_ARG;      \
+        }                                    \
+    } while (0)
+#define FGA_TRY(call)                  \
+    do {                               \
+        fga_status fga_st_ = (call);   \
+        if (fga_st_ != FGA_OK) return fga_st_; \
+    } while (0)
+
+// grow-only device / pinned-host buffers -----------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    fga_status ensure(size_t need);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+struct HostBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    fga_status ensure(size_t need);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// scratch used by binning and the Gaussian sum
+struct Workspace {
+    DevBuf keys, keys_alt, vals, vals_alt, hist, scan_blocks, cell_start, rec, items, tiles, partial, pts;
+    HostBuf h_cell_start, h_items, h_tiles;
+    void release();
+};
+
+}  // namespace fga
+
+struct fga_model {
+    fga::ModelDev dev;
+    fga::DevBuf grid;
+    double cmax[2];  // largest P and S speed of the medium (bounds beam displacement)
+};
+
+struct fga_beams {
+    int precision;
+    double k, w;
+    int64_t nb, cap;
+    int64_t n_cls[4], off_cls[4];
+    fga::DevBuf state, state_alt, flags, flags_alt, id, id_alt;
+    mutable fga::Workspace ws;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace fga {
+
+// kernels and launchers (one per translation unit area) ------------------------------------
+// decompose.cu
+fga_status decompose_impl(const fga_model *m, const fga_init_desc *d, fga_beams **out, cudaStream_t s);
+// propagate.cu
+struct SampleWindow {
+    int n;                  // samples in this window
+    const int *step;        // DEVICE: local step of each sample (0-based within the window)
+    const void *theta;      // DEVICE: R fraction in [0,1]
+    void *rec;              // DEVICE: records [n][cap][REC]
+};
+fga_status launch_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps, const SampleWindow *sw,
+                            cudaStream_t s);
+fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, int64_t n, void *rec,
+                                     cudaStream_t s);
+// gather.cu
+struct BinGrid {
+    float o[3];
+    float inv_h;
+    int nc[3];
+    int ncells;       // nc0*nc1*nc2
+    bool clamp;       // true: clamp keys into the grid; false: out-of-grid centres go to bucket ncells
+};
+fga_status bin_centres(const BinGrid &g, const void *Q_src, int q_kind, int64_t q_stride, int64_t n,
+                       const int32_t *cls_or_null, int32_t *keys, cudaStream_t s);
+fga_status radix_sort_pairs(Workspace &ws, int32_t *keys, int32_t *vals, int64_t n, int bits,
+                            int32_t **keys_out, int32_t **vals_out, cudaStream_t s);
+fga_status cell_starts(const int32_t *sorted_keys, int64_t n, int nbuckets, int32_t *cell_start, cudaStream_t s);
+fga_status permute_beams(fga_beams *b, const int32_t *perm, cudaStream_t s);
+// binning grid covering every point of a set, expanded by `reach`, with cells >= reach
+BinGrid make_grid(const double *pts_host, int64_t n, double reach);
+
+}  // namespace fga

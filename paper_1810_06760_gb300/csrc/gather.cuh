@@ -1,0 +1,53 @@
+// Internal interface of binning and the Gaussian sum.
+#pragma once
+
+#include "fga_internal.cuh"
+
+namespace fga {
+
+// sources of beam centres for the key kernel
+enum { Q_F32_AOS3 = 0, Q_F32_SOA = 1, Q_F64_SOA = 2 };
+
+// Work split of a Gaussian sum at a fixed point set: tiles of 32 points of one cell, items =
+// (tile, [begin, end) of the cell-sorted beams), item_start[t] .. item_start[t+1] the items of tile t.
+struct SumPlan {
+    int ntiles = 0, nitems = 0;
+    const int32_t *tile_pts = nullptr;   // DEVICE [ntiles][32] point index or -1
+    const int32_t *item_start = nullptr; // DEVICE [ntiles + 1]
+    const int4 *items = nullptr;         // DEVICE [nitems] {tile, begin, end, 0}
+    int64_t pairs_tested = 0;            // point x candidate-beam pairs (upper bound of the work)
+};
+
+fga_status sort_keys_to_perm(Workspace &ws, int32_t *keys, int64_t n, int nbuckets, int32_t **perm_out,
+                             int32_t *cell_start, cudaStream_t s);
+fga_status build_sum_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, int nclasses,
+                          const double *pts_host, int64_t npts, cudaStream_t s, SumPlan &plan);
+fga_status run_sum(Workspace &ws, const SumPlan &plan, int precision, const void *rec_sorted, const double *pts_dev,
+                   double k, double rw, void *u_out, cudaStream_t s);
+
+// exp(am) * (cos ph, sin ph).  FP32: Cody-Waite reduction of ph by 2 pi (two-part constant), then
+// the hardware sine/cosine and exponential approximations; FP64: the libm-accurate functions.
+template <typename R> __device__ __forceinline__ void gauss_phase_exp(R ph, R am, R *er, R *ei);
+template <> __device__ __forceinline__ void gauss_phase_exp<float>(float ph, float am, float *er, float *ei) {
+    constexpr double TWO_PI = 6.283185307179586476925286766559;
+    constexpr float TP_HI = (float)TWO_PI;
+    constexpr float TP_LO = (float)(TWO_PI - (double)TP_HI);
+    constexpr float INV_TP = (float)(1.0 / TWO_PI);
+    const float n = rintf(ph * INV_TP);
+    float r = fmaf(-n, TP_HI, ph);
+    r = fmaf(-n, TP_LO, r);
+    float s, c;
+    __sincosf(r, &s, &c);
+    const float e = __expf(am);
+    *er = e * c;
+    *ei = e * s;
+}
+template <> __device__ __forceinline__ void gauss_phase_exp<double>(double ph, double am, double *er, double *ei) {
+    double s, c;
+    sincos(ph, &s, &c);
+    const double e = exp(am);
+    *er = e * c;
+    *ei = e * s;
+}
+
+}  // namespace fga

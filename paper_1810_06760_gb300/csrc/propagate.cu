@@ -1,0 +1,154 @@
+// A3-A4: per-beam classical RK4 of the FGA ODEs, one thread per beam, the whole state in
+// registers for all steps of a launch; reconstruction records written at sample times inside the
+// launch's steps.
+#include "fga_beam.cuh"
+
+namespace fga {
+
+template <typename R, int WAVE, int MED>
+__global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st, const int32_t *__restrict__ flags,
+                                                  int64_t cap, int64_t beg, int64_t n, R sg, R dt, int nsteps,
+                                                  int n_samp, const int *__restrict__ samp_step,
+                                                  const R *__restrict__ samp_theta, R w, R *__restrict__ rec) {
+    const int64_t b = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= beg + n) return;
+    R y[NF];
+#pragma unroll
+    for (int f = 0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
+    const bool ref_e1 = (flags[b] & FL_REF_E1) != 0;
+    R k1[NF];
+    beam_rhs<R, WAVE, MED>(M, sg, ref_e1, y, k1);
+    int js = 0;
+    const R h2 = R(0.5) * dt, h3 = dt / R(3), h6 = dt / R(6);
+    for (int step = 0; step < nsteps; step++) {
+        R acc[NF], tmp[NF], kk[NF];
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            acc[f] = y[f] + h6 * k1[f];
+            tmp[f] = y[f] + h2 * k1[f];
+        }
+        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            acc[f] += h3 * kk[f];
+            tmp[f] = y[f] + h2 * kk[f];
+        }
+        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            acc[f] += h3 * kk[f];
+            tmp[f] = y[f] + dt * kk[f];
+        }
+        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
+#pragma unroll
+        for (int f = 0; f < NF; f++) acc[f] += h6 * kk[f];
+        // k1 of the next step = f(y_{n+1}); also the right-end slope of the Hermite interpolant
+        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, acc, kk);
+        while (js < n_samp && samp_step[js] == step) {
+            R r[REC];
+            beam_record<R, WAVE>(ref_e1, y, k1, acc, kk, dt, samp_theta[js], w, r);
+            R *dst = rec + ((int64_t)js * cap + b) * REC;
+#pragma unroll
+            for (int q = 0; q < REC; q++) dst[q] = r[q];
+            js++;
+        }
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            y[f] = acc[f];
+            k1[f] = kk[f];
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y[f];
+}
+
+// records of the current state (theta = 0), gathered in the order of perm (or identity)
+template <typename R, int WAVE>
+__global__ void records_kernel(const R *__restrict__ st, const int32_t *__restrict__ flags, int64_t cap,
+                               const int32_t *__restrict__ perm, int64_t beg, int64_t n, R w, R *__restrict__ rec) {
+    const int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= beg + n) return;
+    const int64_t b = perm ? perm[i] : i;
+    R y[NF];
+#pragma unroll
+    for (int f = 0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
+    R r[REC];
+    beam_record<R, WAVE>((flags[b] & FL_REF_E1) != 0, y, y, y, y, R(0), R(0), w, r);
+    R *dst = rec + i * REC;
+#pragma unroll
+    for (int q = 0; q < REC; q++) dst[q] = r[q];
+}
+
+template <typename R, int WAVE, int MED>
+static void launch_one(const fga_model *m, fga_beams *b, int cls, R dt, int nsteps, const SampleWindow *sw,
+                       cudaStream_t s) {
+    const int64_t n = b->n_cls[cls];
+    if (n == 0) return;
+    const int T = 128;
+    const int64_t blocks = (n + T - 1) / T;
+    const R sg = (cls & 1) ? R(-1) : R(1);
+    rk4_kernel<R, WAVE, MED><<<(unsigned)blocks, T, 0, s>>>(
+        m->dev, b->state.as<R>(), b->flags.as<int32_t>(), b->cap, b->off_cls[cls], n, sg, dt, nsteps,
+        sw ? sw->n : 0, sw ? sw->step : nullptr, sw ? static_cast<const R *>(sw->theta) : nullptr, (R)b->w,
+        sw ? static_cast<R *>(sw->rec) : nullptr);
+}
+
+template <typename R, int MED>
+static void launch_med(const fga_model *m, fga_beams *b, R dt, int nsteps, const SampleWindow *sw, cudaStream_t s) {
+    for (int cls = 0; cls < 4; cls++) {
+        if (cls < 2)
+            launch_one<R, 0, MED>(m, b, cls, dt, nsteps, sw, s);
+        else
+            launch_one<R, 1, MED>(m, b, cls, dt, nsteps, sw, s);
+    }
+}
+
+template <typename R>
+static void launch_prec(const fga_model *m, fga_beams *b, R dt, int nsteps, const SampleWindow *sw, cudaStream_t s) {
+    switch (m->dev.kind) {
+    case FGA_MEDIUM_CONST: launch_med<R, FGA_MEDIUM_CONST>(m, b, dt, nsteps, sw, s); break;
+    case FGA_MEDIUM_SINE: launch_med<R, FGA_MEDIUM_SINE>(m, b, dt, nsteps, sw, s); break;
+    case FGA_MEDIUM_GRID: launch_med<R, FGA_MEDIUM_GRID>(m, b, dt, nsteps, sw, s); break;
+    default: launch_med<R, FGA_MEDIUM_LAYERED>(m, b, dt, nsteps, sw, s); break;
+    }
+}
+
+fga_status launch_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps, const SampleWindow *sw,
+                            cudaStream_t s) {
+    if (nsteps <= 0 && (!sw || sw->n == 0)) return FGA_OK;
+    if (b->precision == FGA_PREC_FP64)
+        launch_prec<double>(m, b, dt, nsteps, sw, s);
+    else
+        launch_prec<float>(m, b, (float)dt, nsteps, sw, s);
+    FGA_CUDA(cudaGetLastError());
+    return FGA_OK;
+}
+
+fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, int64_t n, void *rec, cudaStream_t s) {
+    (void)n;
+    const int T = 256;
+    for (int cls = 0; cls < 4; cls++) {
+        const int64_t nc = b->n_cls[cls];
+        if (nc == 0) continue;
+        const unsigned blocks = (unsigned)((nc + T - 1) / T);
+        if (b->precision == FGA_PREC_FP64) {
+            if (cls < 2)
+                records_kernel<double, 0><<<blocks, T, 0, s>>>(b->state.as<double>(), b->flags.as<int32_t>(), b->cap,
+                                                               perm, b->off_cls[cls], nc, b->w, (double *)rec);
+            else
+                records_kernel<double, 1><<<blocks, T, 0, s>>>(b->state.as<double>(), b->flags.as<int32_t>(), b->cap,
+                                                               perm, b->off_cls[cls], nc, b->w, (double *)rec);
+        } else {
+            if (cls < 2)
+                records_kernel<float, 0><<<blocks, T, 0, s>>>(b->state.as<float>(), b->flags.as<int32_t>(), b->cap,
+                                                              perm, b->off_cls[cls], nc, (float)b->w, (float *)rec);
+            else
+                records_kernel<float, 1><<<blocks, T, 0, s>>>(b->state.as<float>(), b->flags.as<int32_t>(), b->cap,
+                                                              perm, b->off_cls[cls], nc, (float)b->w, (float *)rec);
+        }
+    }
+    FGA_CUDA(cudaGetLastError());
+    return FGA_OK;
+}
+
+}  // namespace fga

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of ``libfga_gb300.so`` (C ABI in ``include/fga.h``).
+
+Argument marshalling only: every step of the FGA path runs in the library's CUDA kernels.  The
+binding takes torch CUDA tensors for device buffers (PyTorch supplies device memory and streams)
+and raises ``FGAError`` on any non-OK status.  If the library is not built it raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfga_gb300.so")
+
+FGA_OK, FGA_ERR_INVALID_ARG, FGA_ERR_OOM, FGA_ERR_CUDA, FGA_ERR_TIMEOUT, FGA_ERR_NUMERIC, FGA_ERR_UNSUPPORTED = range(7)
+PREC_FP32, PREC_FP64 = 0, 1
+MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
+EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_propagate", "fga_reconstruct",
+            "fga_solve", "fga_beams_count", "fga_beams_export", "fga_beams_destroy", "fga_bin",
+            "fga_last_error", "fga_version"]
+
+
+class FGAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fga status {status}: {msg}")
+        self.status = status
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("cp0", C.c_double), ("cs0", C.c_double), ("amp", C.c_double),
+                ("cs_ratio", C.c_double), ("n", C.c_int * 3), ("origin", C.c_double * 3),
+                ("spacing", C.c_double * 3), ("nlayers", C.c_int), ("z_interfaces", C.c_void_p),
+                ("layer_cp", C.c_void_p), ("layer_cs", C.c_void_p), ("layer_rho", C.c_void_p)]
+
+
+class InitDesc(C.Structure):
+    _fields_ = [("k", C.c_double), ("ny", C.c_int * 3), ("y0", C.c_double * 3), ("dy", C.c_double * 3),
+                ("f", C.c_void_p), ("g", C.c_void_p), ("nq", C.c_int), ("q0", C.c_double * 3),
+                ("dq", C.c_double * 3), ("np", C.c_int), ("p0", C.c_double * 3), ("dp", C.c_double * 3),
+                ("class_mask", C.c_uint), ("precision", C.c_int)]
+
+
+class SolveDesc(C.Structure):
+    _fields_ = [("dt", C.c_double), ("nsteps", C.c_int), ("n_times", C.c_int), ("times", C.c_void_p),
+                ("n_rx", C.c_int64), ("rx", C.c_void_p), ("n_snap", C.c_int64), ("snap", C.c_void_p),
+                ("rw", C.c_double)]
+
+
+_lib = None
+
+
+def lib(path: Optional[str] = None) -> C.CDLL:
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise FGAError(FGA_ERR_UNSUPPORTED, f"{p} not built; run paper_1810_06760_gb300.build.build()")
+    L = C.CDLL(p)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    L.fga_model_create.argtypes = [C.POINTER(vp), C.POINTER(ModelDesc), vp, vp, vp]
+    L.fga_model_destroy.argtypes = [vp]
+    L.fga_decompose.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(vp), vp]
+    L.fga_propagate.argtypes = [vp, vp, C.c_double, i32, vp]
+    L.fga_reconstruct.argtypes = [vp, vp, i64, C.c_double, vp, vp]
+    L.fga_solve.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(SolveDesc), vp, vp, vp]
+    L.fga_beams_count.argtypes = [vp, vp]
+    L.fga_beams_export.argtypes = [vp, vp, vp]
+    L.fga_beams_destroy.argtypes = [vp]
+    L.fga_bin.argtypes = [vp, i64, vp, C.c_float, vp, vp, vp, vp, vp]
+    L.fga_last_error.argtypes = [C.c_char_p, C.c_size_t]
+    L.fga_last_error.restype = None
+    L.fga_version.restype = C.c_int
+    for name in EXPORTED:
+        if name not in ("fga_last_error", "fga_version"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(1024)
+    lib().fga_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(status: int) -> None:
+    if status != FGA_OK:
+        raise FGAError(status, last_error())
+
+
+def _stream(stream) -> C.c_void_p:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return t.data_ptr()
+
+
+def _arr3(v) -> C.Array:
+    a = (C.c_double * 3)()
+    a[:] = [float(x) for x in np.asarray(v, dtype=np.float64).reshape(3)]
+    return a
+
+
+class Model:
+    """Handle of a velocity model (fga_model_create / fga_model_destroy)."""
+
+    def __init__(self, kind: str, *, cp0=2.0, cs0=1.0, amp=0.0, cs_ratio=1.0 / math.sqrt(3.0),
+                 grid_p=None, grid_s=None, origin=(0, 0, 0), spacing=(1, 1, 1),
+                 z_interfaces=(), layer_cp=(), layer_cs=(), layer_rho=(), stream=None):
+        d = ModelDesc()
+        d.kind = MEDIUM[kind]
+        d.cp0, d.cs0, d.amp, d.cs_ratio = cp0, cs0, amp, cs_ratio
+        self._keep = []
+        gp = gs = None
+        if kind == "grid":
+            gp, gs = grid_p.contiguous(), grid_s.contiguous()
+            d.n[:] = list(gp.shape[:3])
+            d.origin[:] = [float(v) for v in origin]
+            d.spacing[:] = [float(v) for v in spacing]
+        if kind == "layered":
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (z_interfaces, layer_cp, layer_cs, layer_rho)]
+            self._keep += arrs
+            d.nlayers = arrs[1].size
+            d.z_interfaces, d.layer_cp, d.layer_cs, d.layer_rho = [a.ctypes.data for a in arrs]
+        h = C.c_void_p()
+        _check(lib().fga_model_create(C.byref(h), C.byref(d), _dptr(gp), _dptr(gs), _stream(stream)))
+        self.h = h
+        self.kind = kind
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fga_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def model_from_medium(med, device="cuda") -> Model:
+    """Model from a ``workloads.Medium``."""
+    import torch
+    if med.kind == "grid":
+        gp = torch.as_tensor(med.grid_p, device=device)
+        gs = torch.as_tensor(med.grid_s, device=device)
+        m = Model("grid", grid_p=gp, grid_s=gs, origin=med.origin, spacing=med.spacing)
+        torch.cuda.current_stream().synchronize()
+        return m
+    return Model(med.kind, cp0=med.cp0, cs0=med.cs0, amp=med.amp, cs_ratio=med.cs_ratio)
+
+
+def init_desc(k, f, g, y0, dy, mesh, classes: Sequence[int], precision: int) -> InitDesc:
+    """Decomposition descriptor.  f, g: complex128 CUDA tensors [ny0, ny1, ny2, 3] (g may be None)."""
+    d = InitDesc()
+    d.k = float(k)
+    d.ny[:] = list(f.shape[:3])
+    d.y0, d.dy = _arr3(y0), _arr3(dy)
+    d.f, d.g = _dptr(f), _dptr(g)
+    d.nq, d.q0, d.dq = int(mesh.nq), _arr3(mesh.q0), _arr3(mesh.dq)
+    d.np, d.p0, d.dp = int(mesh.np_), _arr3(mesh.p0), _arr3(mesh.dp)
+    d.class_mask = sum(1 << int(c) for c in classes)
+    d.precision = int(precision)
+    return d
+
+
+class Beams:
+    """Handle of a beam set (fga_decompose ... fga_beams_destroy)."""
+
+    def __init__(self, h: C.c_void_p, precision: int, k: float):
+        self.h, self.precision, self.k = h, precision, k
+
+    def count(self):
+        out = np.zeros(4, dtype=np.int64)
+        _check(lib().fga_beams_count(self.h, out.ctypes.data))
+        return out
+
+    def export(self):
+        """(state [nb, 48] float64, meta [nb] int32) in mesh order per class (synchronous)."""
+        n = int(self.count().sum())
+        st = np.zeros((n, 48))
+        meta = np.zeros(n, dtype=np.int32)
+        _check(lib().fga_beams_export(self.h, st.ctypes.data, meta.ctypes.data))
+        return st, meta
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fga_beams_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def decompose(model: Model, desc: InitDesc, stream=None) -> Beams:
+    h = C.c_void_p()
+    _check(lib().fga_decompose(model.h, C.byref(desc), C.byref(h), _stream(stream)))
+    return Beams(h, desc.precision, desc.k)
+
+
+def propagate(model: Model, beams: Beams, dt: float, nsteps: int, stream=None) -> None:
+    _check(lib().fga_propagate(model.h, beams.h, float(dt), int(nsteps), _stream(stream)))
+
+
+def _cdtype(precision: int):
+    import torch
+    return torch.complex128 if precision == PREC_FP64 else torch.complex64
+
+
+def reconstruct(beams: Beams, x, rw: float = 0.0, out=None, stream=None):
+    """u(x) at the current beam state; x: float64 CUDA tensor [n, 3].  Returns complex [n, 3]."""
+    import torch
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=_cdtype(beams.precision), device=x.device)
+    _check(lib().fga_reconstruct(beams.h, _dptr(x) if n else None, n, float(rw), _dptr(out) if n else None,
+                                 _stream(stream)))
+    return out
+
+
+def solve(model: Model, desc: InitDesc, dt: float, nsteps: int, times, rx=None, snap=None, rw: float = 0.0,
+          seis_out=None, snap_out=None, stream=None):
+    """Whole forward solve.  Returns (seismograms [n_times, n_rx, 3] or None, snapshot [n_snap, 3] or None)."""
+    import torch
+    times = np.ascontiguousarray(times, dtype=np.float64)
+    sd = SolveDesc()
+    sd.dt, sd.nsteps = float(dt), int(nsteps)
+    sd.n_times, sd.times = times.size, times.ctypes.data if times.size else None
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cdt = _cdtype(desc.precision)
+    nrx = 0 if rx is None else rx.shape[0]
+    nsn = 0 if snap is None else snap.shape[0]
+    if nrx and times.size and seis_out is None:
+        seis_out = torch.empty((times.size, nrx, 3), dtype=cdt, device=dev)
+    if nsn and snap_out is None:
+        snap_out = torch.empty((nsn, 3), dtype=cdt, device=dev)
+    sd.n_rx, sd.rx = nrx, _dptr(rx) if nrx else None
+    sd.n_snap, sd.snap = nsn, _dptr(snap) if nsn else None
+    sd.rw = float(rw)
+    _check(lib().fga_solve(model.h, C.byref(desc), C.byref(sd), _dptr(seis_out), _dptr(snap_out),
+                           _stream(stream)))
+    return seis_out, snap_out
+
+
+def bin_centres(Q, origin, inv_h: float, nc, stream=None):
+    """Cell keys, stable permutation and cell offsets of FP32 centres Q [n, 3] (CUDA float32)."""
+    import torch
+    n = Q.shape[0]
+    nc = np.ascontiguousarray(nc, dtype=np.int32)
+    o = np.ascontiguousarray(origin, dtype=np.float32)
+    keys = torch.empty(max(n, 1), dtype=torch.int32, device=Q.device)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=Q.device)
+    start = torch.empty(int(np.prod(nc)) + 1, dtype=torch.int32, device=Q.device)
+    _check(lib().fga_bin(_dptr(Q) if n else None, n, o.ctypes.data, C.c_float(np.float32(inv_h)), nc.ctypes.data,
+                         _dptr(keys), _dptr(perm), _dptr(start), _stream(stream)))
+    return keys[:n], perm[:n], start

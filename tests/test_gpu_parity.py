@@ -1,0 +1,148 @@
+"""GPU library (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (relative L2 over each compared array): 1e-10 for the FP64 path, 1e-4 for the FP32
+path; binning is compared bit for bit.  Sizes span several sort tiles (2048 keys), several point
+tiles (32 points) and ragged tails."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1810_06760_gb300 import workloads as W
+from tests.helpers import gpu_setup, oracle_beams, oracle_model, oracle_mesh, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-4, 1: 1e-10}   # FGA_PREC_FP32, FGA_PREC_FP64
+
+
+@pytest.fixture(scope="module")
+def fga():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1810_06760_gb300 import build, fga as F
+    build.build()
+    F.lib()
+    return F
+
+
+def _small_smooth(grid=True, **kw):
+    args = dict(nq=5, np_=3, ny=24, nsteps=40, n_samples=30, rx_side=7, snap_side=5, grid_n=33, grid=grid)
+    args.update(kw)
+    return W.smooth(**args)
+
+
+def _small_homog(**kw):
+    args = dict(nq=5, np_=3, ny=20, nsteps=30, n_receivers=100)
+    args.update(kw)
+    return W.homogeneous(**args)
+
+
+WORKLOADS = {
+    "homogeneous": _small_homog,
+    "sine": lambda: _small_smooth(grid=False),
+    "grid": lambda: _small_smooth(grid=True),
+}
+
+GROUPS = {"Q": slice(0, 3), "P": slice(3, 6), "dzQ": slice(6, 24), "dzP": slice(24, 42), "a": slice(42, 46)}
+
+
+def _compare_states(gst, gmeta, ost, ometa, tol):
+    np.testing.assert_array_equal(gmeta & 7, ometa & 7)
+    for name, sl in GROUPS.items():
+        e = rel_l2(gst[:, sl], ost[:, sl])
+        assert e <= tol, (name, e)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("wname", list(WORKLOADS))
+def test_decompose_then_propagate(fga, oracle, wname, prec):
+    w = WORKLOADS[wname]()
+    model, desc, keep = gpu_setup(w, prec)
+    beams = fga.decompose(model, desc)
+    gst0, gmeta = beams.export()
+    omodel, mesh, obeams = oracle_beams(oracle, w)
+    ost0 = np.concatenate([b[1] for b in obeams])
+    ometa = np.concatenate([b[2] for b in obeams])
+    _compare_states(gst0, gmeta, ost0, ometa, TOL[prec])
+    fga.propagate(model, beams, w.dt, w.nsteps)
+    gst, gmeta = beams.export()
+    ost = ost0.copy()
+    oracle.propagate(omodel, ost, ometa, w.dt, w.nsteps)
+    _compare_states(gst, gmeta, ost, ometa, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_reconstruct_at_points(fga, oracle, prec):
+    import torch
+    w = _small_smooth(grid=True, nsteps=24)
+    model, desc, keep = gpu_setup(w, prec)
+    beams = fga.decompose(model, desc)
+    fga.propagate(model, beams, w.dt, w.nsteps)
+    omodel, mesh, obeams = oracle_beams(oracle, w)
+    wgt = mesh.weight(w.k)
+    x = W.random_points(101, -0.1, 1.1, 4)           # 3 full tiles of 32 and a ragged one
+    ref = np.zeros((x.shape[0], 3), complex)
+    for cls, st, meta in obeams:
+        oracle.propagate(omodel, st, meta, w.dt, w.nsteps)
+        ref += oracle.gauss_sum(oracle.records(st, meta, wgt), w.k, w.rw, x)
+    u = fga.reconstruct(beams, torch.as_tensor(x, device="cuda"), rw=w.rw).cpu().numpy()
+    assert rel_l2(u, ref) <= TOL[prec]
+    # the untruncated oracle sum differs from the truncated one by at most e^-18 of the amplitudes
+    ref_full = sum(oracle.gauss_sum(oracle.records(st, meta, wgt), w.k, 0.0, x) for _, st, meta in obeams)
+    assert rel_l2(ref, ref_full) < 1e-6
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_solve_seismograms_and_snapshot(fga, oracle, prec):
+    import torch
+    w = _small_smooth(grid=True)
+    model, desc, keep = gpu_setup(w, prec)
+    rx = torch.as_tensor(w.receivers, device="cuda")
+    sn = torch.as_tensor(w.snapshot, device="cuda")
+    seis, snap = fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, sn, rw=w.rw)
+    torch.cuda.synchronize()
+    omodel = oracle_model(oracle, w.medium)
+    mesh = oracle_mesh(oracle, w.mesh)
+    F = oracle.fbi(w.f, w.y0, w.dy, w.k, mesh)
+    ref_seis, ref_snap = oracle.solve(omodel, w.k, mesh, F, None, w.classes, w.dt, w.nsteps, w.times,
+                                      w.receivers, w.rw, snap=w.snapshot)
+    assert rel_l2(seis.cpu().numpy(), ref_seis) <= TOL[prec]
+    assert rel_l2(snap.cpu().numpy(), ref_snap) <= TOL[prec]
+
+
+@pytest.mark.parametrize("n,nc", [(0, (3, 3, 3)), (1, (2, 2, 2)), (5000, (4, 5, 6)), (20011, (9, 7, 11)),
+                                  (70001, (40, 40, 40))])
+def test_binning_bit_exact(fga, oracle, n, nc):
+    import torch
+    rng = np.random.default_rng(n + 17)
+    Q = rng.uniform(-0.7, 1.8, (n, 3)).astype(np.float32)
+    if n > 100:
+        Q[:100] = np.float32(0.125) * rng.integers(-4, 12, (100, 3))   # exactly on cell faces
+    o = np.array([-0.5, -0.25, -0.5], np.float32)
+    inv_h = np.float32(1.0 / (2.25 / max(nc)))
+    keys, perm, start = fga.bin_centres(torch.as_tensor(Q, device="cuda"), o, inv_h, nc)
+    okey = oracle.bin_keys_f32(Q, o, inv_h, nc)
+    operm, ostart = oracle.bin_sort(okey, int(np.prod(nc)))
+    np.testing.assert_array_equal(keys.cpu().numpy(), okey)
+    np.testing.assert_array_equal(perm.cpu().numpy(), operm)
+    np.testing.assert_array_equal(start.cpu().numpy(), ostart)
+
+
+def test_errors_are_reported_not_raised_from_device(fga):
+    import torch
+    w = _small_homog()
+    model, desc, keep = gpu_setup(w, 1)
+    desc.class_mask = 0
+    with pytest.raises(fga.FGAError) as e:
+        fga.decompose(model, desc)
+    assert e.value.status == fga.FGA_ERR_INVALID_ARG
+    desc.class_mask = 1
+    beams = fga.decompose(model, desc)
+    with pytest.raises(fga.FGAError):
+        fga.propagate(model, beams, float("nan"), 3)
+    out = fga.reconstruct(beams, torch.zeros((0, 3), dtype=torch.float64, device="cuda"))
+    assert out.shape == (0, 3)
+    with pytest.raises(fga.FGAError):   # sample time outside (0, T]
+        fga.solve(model, desc, w.dt, w.nsteps, np.array([w.T * 2]), torch.as_tensor(w.receivers, device="cuda"))
