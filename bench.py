@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""FGA forward-solve benchmark on GB300.
+
+One step = one whole forward solve of the smooth heterogeneous workload through the C ABI
+(fga_solve): wave-packet decomposition of the initial data, RK4 propagation of every P+, P-, S+
+and S- beam (24^3 q x 8^3 p mesh points, 28.3 M beams, 400 steps of dt = 0.0025), seismograms at
+400 surface receivers x 1,000 samples and a 64^3 snapshot at T = 1.  The medium is
+c_p = 2 + 0.2 sin(2 pi x1) sin(2 pi x2) sin(2 pi x3), c_s = c_p/sqrt(3), on a 128^3 FP32 grid.
+
+value = beam-steps/s (whole job, all ranks), with inputs resident in HBM; e2e = the same metric with
+host buffers copied in and results copied out inside the timed region.  The reference arm
+(--impl reference) times the FP64 CPU oracle on a strided sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP32 operations per beam-step and per Gaussian-sum pair, counted from the kernels' source (FMA = 2)
+FLOP_PER_BEAM_STEP = {"P": 4180.0, "S": 4400.0}
+FLOP_PER_PAIR_IN = 43.0       # dx, r^2, phase, exponent, e*(cos, sin), 3 complex multiply-adds
+FLOP_PER_PAIR_OUT = 9.0       # dx, r^2, compare
+MUFU_PER_PAIR_IN = 3.0        # exp2, sin, cos
+SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--small", action="store_true", help="reduced sizes (debugging only; not a bench line)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(small: bool):
+    from paper_1810_06760_gb300 import workloads as W
+    if small:
+        return W.smooth(nq=8, np_=4, ny=48, nsteps=40, n_samples=100, rx_side=10, snap_side=16, grid_n=65)
+    return W.smooth()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                smax.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v: float, device=None) -> float:
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle on a strided sample of the workload
+# ------------------------------------------------------------------------------------------------
+
+def oracle_sample(w, q_stride: int, p_stride: int, n_samples_cap=None):
+    """Oracle propagation + seismogram sums of the beams of every q_stride-th q node and p_stride-th
+    p node per axis (all four classes).  Returns (beam_steps, seconds, threads, description)."""
+    from oracle import fga_oracle as O
+    O.build()
+    med = w.medium
+    om = O.Model(med.kind, cp0=med.cp0, cs0=med.cs0, amp=med.amp, cs_ratio=med.cs_ratio, grid_p=med.grid_p,
+                 grid_s=med.grid_s, origin=med.origin, spacing=med.spacing)
+    m = w.mesh
+    full = O.Mesh(m.nq, m.q0, m.dq, m.np_, m.p0, m.dp)
+    sub = O.Mesh(len(range(0, m.nq, q_stride)), m.q0, m.dq * q_stride, len(range(0, m.np_, p_stride)), m.p0,
+                 m.dp * p_stride)
+    F = O.fbi(w.f, w.y0, w.dy, w.k, sub)           # untimed: the sample's wave-packet weights
+    times = w.times if n_samples_cap is None else w.times[:n_samples_cap]
+    s_step, s_th = O.sample_schedule(times, w.dt, w.nsteps)
+    wgt = full.weight(w.k)
+    beams = [O.beam_init(om, w.k, sub, F, None, c) for c in w.classes]
+    t0 = time.perf_counter()
+    for st, meta in beams:
+        rec = O.propagate(om, st, meta, w.dt, w.nsteps, s_step, s_th, wgt)
+        for j in range(len(times)):
+            O.gauss_sum(rec[j], w.k, w.rw, w.receivers)
+    dt = time.perf_counter() - t0
+    nb = sub.M * len(w.classes)
+    desc = (f"{nb} beams (q stride {q_stride}, p stride {p_stride} per axis, 4 classes) x {w.nsteps} RK4 steps "
+            f"+ {len(w.receivers)} receivers x {len(times)} samples; decomposition untimed")
+    return nb * w.nsteps, dt, O.get_threads(), desc
+
+
+# ------------------------------------------------------------------------------------------------
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return 0
+    w = workload(args.small)
+    for _ in range(args.warmup):
+        oracle_sample(w, 12, 8, n_samples_cap=50)
+    vals = []
+    for _ in range(args.steps):
+        bs, secs, thr, desc = oracle_sample(w, 6, 2)
+        vals.append((bs, secs))
+    tot_bs = sum(v[0] for v in vals)
+    tot_s = sum(v[1] for v in vals)
+    value = tot_bs / tot_s
+    line = {"impl": "reference", "metric": "FGA beam-steps/s (smooth heterogeneous medium, 128^3 grid, k=64)",
+            "value": value, "unit": "beam-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "smooth-heterogeneous 128^3, 24^3 q x 8^3 p x 4 classes, 400 steps, "
+                                   "400 rx x 1000 samples", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "beam-steps/s", "cores": thr, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "beam-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1810_06760_gb300 import fga
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = fga.PREC_FP32 if args.precision == "fp32" else fga.PREC_FP64
+    w = workload(args.small)
+    nb = w.n_beams
+    beam_steps = nb * w.nsteps
+    model = fga.model_from_medium(w.medium, dev)
+    f = torch.as_tensor(w.f, device=dev)
+    rx = torch.as_tensor(w.receivers, device=dev)
+    sn = torch.as_tensor(w.snapshot, device=dev)
+    desc = fga.init_desc(w.k, f, None, w.y0, w.dy, w.mesh, w.classes, prec)
+    cdt = torch.complex64 if prec == fga.PREC_FP32 else torch.complex128
+    seis = torch.empty((len(w.times), rx.shape[0], 3), dtype=cdt, device=dev)
+    snap = torch.empty((sn.shape[0], 3), dtype=cdt, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, sn, rw=w.rw, seis_out=seis, snap_out=snap)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # timed region: device time with CUDA events on the launching stream, per-kernel event times live
+    fga.profile_enable(2)
+    fga.profile_read(reset=True)
+    clk = Clocks(local)
+    clk.start()
+    barrier(pg)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
+        step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = clk.stop()
+    prof = fga.profile_read(reset=True)
+    fga.profile_enable(0)
+    per_step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    total_ms = max_over_ranks(pg, total_ms, dev)
+    value = world * args.steps * beam_steps / (total_ms / 1e3)
+    assert torch.isfinite(torch.view_as_real(seis)).all() and torch.isfinite(torch.view_as_real(snap)).all()
+
+    # dominant kernel and its roofline (FP32 ALU-bound: FP32 pipe peak from SM count x lanes x clock)
+    pk, pk_kind = peaks()
+    ms = prof["ms"]
+    top = max(ms, key=lambda c: ms[c])
+    sm_clock = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    fp32_peak = SMS * 128 * 2 * sm_clock
+    if prec == fga.PREC_FP32 and top == "propagate":
+        nP = sum(1 for c in w.classes if c < 2) * w.mesh.M
+        nS = sum(1 for c in w.classes if c >= 2) * w.mesh.M
+        flops = (nP * FLOP_PER_BEAM_STEP["P"] + nS * FLOP_PER_BEAM_STEP["S"]) * w.nsteps * args.steps
+    elif prec == fga.PREC_FP32 and top == "gauss_sum":
+        pin, pt = prof["pairs_in_window"], prof["pairs_tested"]
+        flops = pin * FLOP_PER_PAIR_IN + (pt - pin) * FLOP_PER_PAIR_OUT
+    else:
+        flops = None
+    launches = max(prof["count"][top], 1)
+    per_launch_ms = ms[top] / launches
+    roof = None
+    if flops is not None:
+        achieved = flops / (ms[top] / 1e3) / 1e12
+        peak = fp32_peak / 1e12
+        roof = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_basis": f"FP32 pipe: {SMS} SMs x 128 lanes x 2 x {sm_clock / 1e6:.0f} MHz "
+                              f"(max SM clock of {pk_kind} peaks file)",
+                "per_launch_ms": per_launch_ms, "launches": launches}
+    gauss_s = ms["gauss_sum"] / 1e3
+    line = {
+        "metric": "FGA beam-steps/s (smooth heterogeneous medium, 128^3 grid, k=64)",
+        "value": value, "unit": "beam-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
+        "config": {"workload": "smooth-heterogeneous: 128^3 grid medium, k=64, 24^3 q x 8^3 p mesh x 4 classes "
+                               f"({nb} beams), 400 RK4 steps, 400 rx x 1000 samples + 64^3 snapshot",
+                   "l2": "inputs larger than L2 (beam state 5.2 GB)", "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": statistics.median(per_step_ms),
+                       "p99": sorted(per_step_ms)[min(len(per_step_ms) - 1, math.ceil(0.99 * len(per_step_ms)) - 1)]},
+        "gauss_sum_pairs_per_s": prof["pairs_in_window"] / gauss_s if gauss_s > 0 else None,
+        "receiver_samples_per_s": world * args.steps * (len(w.times) * rx.shape[0] + sn.shape[0]) / (total_ms / 1e3),
+        "kernel_ms": {k: v / args.steps for k, v in ms.items() if v > 0},
+        "roofline": roof,
+        "clocks": clocks,
+        "gpu_launches": prof["launches"],
+    }
+
+    if not args.no_e2e:
+        # end to end through the public API from pinned host buffers: inputs in, solve, results out
+        hf = torch.as_tensor(w.f).pin_memory()
+        hrx = torch.as_tensor(w.receivers).pin_memory()
+        hsn = torch.as_tensor(w.snapshot).pin_memory()
+        hgp = torch.as_tensor(w.medium.grid_p).pin_memory()
+        hgs = torch.as_tensor(w.medium.grid_s).pin_memory()
+        oseis = torch.empty(seis.shape, dtype=cdt).pin_memory()
+        osnap = torch.empty(snap.shape, dtype=cdt).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in (hf, hrx, hsn, hgp, hgs))
+        d2h = oseis.numel() * oseis.element_size() + osnap.numel() * osnap.element_size()
+
+        def e2e_step():
+            df = hf.to(dev, non_blocking=True)
+            drx = hrx.to(dev, non_blocking=True)
+            dsn = hsn.to(dev, non_blocking=True)
+            gp = hgp.to(dev, non_blocking=True)
+            gs = hgs.to(dev, non_blocking=True)
+            m2 = fga.Model("grid", grid_p=gp, grid_s=gs, origin=w.medium.origin, spacing=w.medium.spacing)
+            d2 = fga.init_desc(w.k, df, None, w.y0, w.dy, w.mesh, w.classes, prec)
+            s_, n_ = fga.solve(m2, d2, w.dt, w.nsteps, w.times, drx, dsn, rw=w.rw)
+            oseis.copy_(s_, non_blocking=True)
+            osnap.copy_(n_, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            m2.close()
+
+        e2e_step()
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier(pg)
+        e2e_s = max_over_ranks(pg, time.perf_counter() - t0, dev)
+        line["e2e"] = {"value": world * args.steps * beam_steps / e2e_s, "unit": "beam-steps/s",
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        bs, secs, thr, desc_s = oracle_sample(w, 6, 2) if not args.small else oracle_sample(w, 4, 2)
+        line["cpu_baseline"] = {"value": bs / secs, "unit": "beam-steps/s", "cores": thr, "kind": "oracle",
+                                "sample": desc_s}
+    if rank == 0:
+        print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -163,6 +163,26 @@ fga_status fga_beams_destroy(fga_beams *b);
 fga_status fga_bin(const float *Q, int64_t n, const float origin[3], float inv_h, const int nc[3],
                    int32_t *keys, int32_t *perm, int32_t *cell_start, fga_stream_t s);
 
+/* Profiling of the library's own kernels (no counterpart in the paper; used to measure it).
+ * mode 0: off (default); 1: launch and work counters; 2: counters plus device time of every kernel
+ * launch, taken with CUDA events recorded on the launching stream around it.  Categories of
+ * count[] / ms[]: 0 decomposition, 1 RK4 propagation, 2 binning (keys, sort, permutation),
+ * 3 records, 4 Gaussian sum, 5 Gaussian-sum reduction, 6 other.  pairs_in_window counts the
+ * (beam, point) pairs inside the truncation window that the Gaussian sum evaluated; pairs_tested the
+ * pairs it examined; beam_steps the beam RK4 steps advanced.  fga_profile_read waits for the timed
+ * launches to finish; reset != 0 zeroes the counters afterwards.  Process-wide state, meant to be
+ * driven from one host thread. */
+typedef struct {
+    int64_t launches;
+    int64_t count[8];
+    double ms[8];
+    int64_t beam_steps;
+    int64_t pairs_in_window;
+    int64_t pairs_tested;
+} fga_profile_t;
+fga_status fga_profile_enable(int mode);
+fga_status fga_profile_read(fga_profile_t *out, int reset);
+
 /* Message of the last failing call on this thread (always NUL-terminated; truncated to cap). */
 void fga_last_error(char *buf, size_t cap);
 int fga_version(void);

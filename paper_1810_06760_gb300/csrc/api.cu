@@ -95,6 +95,59 @@ __global__ void max_field0_kernel(const float4 *__restrict__ g, int64_t nn, unsi
 
 static double sample_hermite_margin(double cmax, double dt, int w) { return cmax * std::fabs(dt) * (w + 1.0); }
 
+// profiling state (process-wide; the profiling calls are meant for one host thread)
+struct ProfState {
+    int mode = 0;  // 0 off, 1 counters, 2 counters + event times
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_cat;
+    size_t used = 0;
+    int64_t launches = 0, count[P_NCAT] = {};
+    double ms[P_NCAT] = {};
+    int64_t beam_steps = 0, pairs_tested = 0;
+    void fold() {  // accumulate the recorded event pairs
+        for (size_t i = 0; i + 1 < used; i += 2) {
+            float t = 0.f;
+            if (cudaEventSynchronize(ev[i + 1]) == cudaSuccess && cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess)
+                ms[ev_cat[i]] += t;
+            else
+                cudaGetLastError();
+        }
+        used = 0;
+    }
+};
+static ProfState g_prof;
+
+ProfScope::ProfScope(int cat, cudaStream_t st) : idx(-1), s(st) {
+    if (g_prof.mode == 0) return;
+    g_prof.launches++;
+    g_prof.count[cat]++;
+    if (g_prof.mode < 2) return;
+    if (g_prof.used + 2 > 8192) g_prof.fold();
+    while (g_prof.ev.size() < g_prof.used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        g_prof.ev.push_back(e);
+        g_prof.ev_cat.push_back(0);
+    }
+    idx = (int)g_prof.used;
+    g_prof.used += 2;
+    g_prof.ev_cat[idx] = cat;
+    cudaEventRecord(g_prof.ev[idx], s);
+}
+ProfScope::~ProfScope() {
+    if (idx >= 0) cudaEventRecord(g_prof.ev[idx + 1], s);
+}
+bool prof_counting() { return g_prof.mode > 0; }
+void prof_add_beam_steps(int64_t n) {
+    if (g_prof.mode) g_prof.beam_steps += n;
+}
+void prof_add_pairs_tested(int64_t n) {
+    if (g_prof.mode) g_prof.pairs_tested += n;
+}
+
 }  // namespace fga
 
 using namespace fga;
@@ -262,11 +315,11 @@ static fga_status reconstruct_now(const fga_beams *b, const double *x_dev, const
     const BinGrid g = make_grid(xh.data(), n, rw);
     int32_t *perm = nullptr;
     FGA_TRY(bin_beams(b, g, &perm, s));
-    const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
-    FGA_TRY(ws.rec.ensure(rb * REC * (size_t)std::max<int64_t>(b->cap, 1)));
-    FGA_TRY(launch_records_from_state(b, perm, b->nb, ws.rec.p, s));
     SumPlan plan;
-    FGA_TRY(build_sum_plan(ws, g, ws.cell_start.as<int32_t>(), 4, xh.data(), n, s, plan));
+    FGA_TRY(build_sum_plan(ws, g, ws.cell_start.as<int32_t>(), 4, xh.data(), n, s, plan));  // syncs
+    const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
+    FGA_TRY(ws.rec.ensure(rb * REC * (size_t)std::max<int64_t>(plan.n_rec, 1)));
+    FGA_TRY(launch_records_from_state(b, perm, plan.n_in, plan.rec_off, ws.rec.p, s));
     return run_sum(ws, plan, b->precision, ws.rec.p, x_dev, b->k, rw, u_out, s);
 }
 
@@ -345,14 +398,18 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
             h.release();
         }
     } fr{samp, hsamp};
+    // records of one window live in one buffer; cap its size
+    size_t free_b = 0, total_b = 0;
+    FGA_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const double rec_budget = std::min(12.0e9, 0.4 * (double)free_b);
     int js = 0;
-    for (int n0 = 0; n0 < sd->nsteps; n0 += W) {
-        const int nw = std::min(W, sd->nsteps - n0);
+    for (int n0 = 0; n0 < sd->nsteps;) {
+        int nw = std::min(W, sd->nsteps - n0);
         int j1 = js;
         while (seis && j1 < sd->n_times && sstep[(size_t)j1] < n0 + nw) j1++;
-        const int ns = j1 - js;
-        if (ns == 0) {
+        if (j1 == js) {
             FGA_TRY(launch_propagate(m, b, sd->dt, nw, nullptr, s));
+            n0 += nw;
             continue;
         }
         int32_t *perm = nullptr;
@@ -360,6 +417,16 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
         FGA_TRY(permute_beams(b, perm, s));
         SumPlan plan;
         FGA_TRY(build_sum_plan(ws, grx, ws.cell_start.as<int32_t>(), 4, rxh.data(), sd->n_rx, s, plan));  // syncs
+        // shorten the window so that its samples' records fit the budget (a shorter window keeps the
+        // cell margin valid)
+        const int64_t per_sample = (int64_t)rb * REC * std::max<int64_t>(plan.n_rec, 1);
+        const int smax = (int)std::max<double>(1.0, std::floor(rec_budget / (double)per_sample));
+        if (j1 - js > smax) {
+            j1 = js + smax;
+            nw = sstep[(size_t)(j1 - 1)] - n0 + 1;  // end the window with the step of its last sample
+            while (j1 < sd->n_times && sstep[(size_t)j1] < n0 + nw) j1++;
+        }
+        const int ns = j1 - js;
         char *hth = hsamp.as<char>();
         int *hs = reinterpret_cast<int *>(hth + soff);
         for (int j = 0; j < ns; j++) {
@@ -370,15 +437,20 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
                 reinterpret_cast<float *>(hth)[j] = (float)sth[(size_t)(js + j)];
         }
         FGA_CUDA(cudaMemcpyAsync(samp.p, hsamp.p, sbytes, cudaMemcpyHostToDevice, s));
-        FGA_TRY(ws.rec.ensure(rb * REC * (size_t)b->cap * ns));
-        SampleWindow sw{ns, reinterpret_cast<const int *>(samp.as<char>() + soff), samp.p, ws.rec.p};
+        FGA_TRY(ws.rec.ensure((size_t)per_sample * ns));
+        SampleWindow sw{ns, reinterpret_cast<const int *>(samp.as<char>() + soff), samp.p, ws.rec.p, {}, {}, plan.n_rec};
+        for (int c = 0; c < 4; c++) {
+            sw.n_in[c] = plan.n_in[c];
+            sw.rec_off[c] = plan.rec_off[c];
+        }
         FGA_TRY(launch_propagate(m, b, sd->dt, nw, &sw, s));
         for (int j = 0; j < ns; j++) {
             void *out = static_cast<char *>(seis_out) + rb * 6 * (size_t)sd->n_rx * (size_t)(js + j);
-            const void *rec = static_cast<const char *>(ws.rec.p) + rb * REC * (size_t)b->cap * j;
+            const void *rec = static_cast<const char *>(ws.rec.p) + (size_t)per_sample * j;
             FGA_TRY(run_sum(ws, plan, b->precision, rec, sd->rx, b->k, rw, out, s));
         }
         js = j1;
+        n0 += nw;
     }
     if (sd->n_snap > 0) FGA_TRY(reconstruct_now(b, sd->snap, snh, sd->n_snap, rw, snap_out, s));
     // the beam set is freed by the guard; its buffers must not be in use
@@ -430,6 +502,34 @@ fga_status fga_beams_destroy(fga_beams *b) {
     b->ws.release();
     for (DevBuf *d : {&b->state, &b->state_alt, &b->flags, &b->flags_alt, &b->id, &b->id_alt}) d->release();
     delete b;
+    return FGA_OK;
+}
+
+fga_status fga_profile_enable(int mode) {
+    FGA_CHECK(mode >= 0 && mode <= 2, "fga_profile_enable: mode must be 0, 1 or 2");
+    g_prof.mode = mode;
+    return FGA_OK;
+}
+
+fga_status fga_profile_read(fga_profile_t *out, int reset) {
+    FGA_CHECK(out, "fga_profile_read: NULL argument");
+    g_prof.fold();
+    std::memset(out, 0, sizeof *out);
+    out->launches = g_prof.launches;
+    for (int c = 0; c < 8; c++) {
+        out->count[c] = g_prof.count[c];
+        out->ms[c] = g_prof.ms[c];
+    }
+    out->beam_steps = g_prof.beam_steps;
+    out->pairs_tested = g_prof.pairs_tested;
+    out->pairs_in_window = read_pair_counter(reset != 0);
+    if (reset) {
+        g_prof.launches = g_prof.beam_steps = g_prof.pairs_tested = 0;
+        for (int c = 0; c < P_NCAT; c++) {
+            g_prof.count[c] = 0;
+            g_prof.ms[c] = 0.0;
+        }
+    }
     return FGA_OK;
 }
 

@@ -95,6 +95,7 @@ static fga_status cgemm(const TA *A, int64_t sAz, int64_t sAm, int64_t sAk, cons
                         C2<R> *Cm, int64_t sCz, int64_t sCm, int64_t sCn, int Z, int64_t M, int N, int K, R scale,
                         cudaStream_t s) {
     dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64), (unsigned)Z);
+    ProfScope ps(P_DECOMP, s);
     cgemm_kernel<R, TA><<<grid, 256, 0, s>>>(A, sAz, sAm, sAk, B, sBn, sBk, Cm, sCz, sCm, sCn, M, N, K, scale);
     FGA_CUDA(cudaGetLastError());
     return FGA_OK;
@@ -202,6 +203,7 @@ static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fg
     Kax[2] = Kax[1] + (size_t)A * d->ny[1];
     for (int ax = 0; ax < 3; ax++) {
         const int tot = A * d->ny[ax];
+        ProfScope ps(P_DECOMP, s);
         fbi_axis_kernel<R><<<(tot + 255) / 256, 256, 0, s>>>(Kax[ax], d->nq, d->np, d->ny[ax], d->q0[ax], d->dq[ax],
                                                             d->p0[ax], d->dp[ax], d->y0[ax], d->dy[ax], d->k);
     }
@@ -225,6 +227,7 @@ static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fg
     for (int cls = 0; cls < 4; cls++) {
         if (!(d->class_mask & (1u << cls))) continue;
         const unsigned blocks = (unsigned)((M + 127) / 128);
+        ProfScope ps(P_DECOMP, s);
 #define FGA_INIT(MED)                                                                                               \
     beam_init_kernel<R, MED><<<blocks, 128, 0, s>>>(m->dev, Fb.as<C2<R>>(), G, d->nq, d->np, q0, dq, p0, dp, d->k, M, \
                                                     cls, b->off_cls[cls], b->cap, b->state.as<R>(),                   \

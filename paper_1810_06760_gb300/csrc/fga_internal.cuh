@@ -57,6 +57,19 @@ fga_status cuda_fail(cudaError_t e, const char *what);
         if (fga_st_ != FGA_OK) return fga_st_; \
     } while (0)
 
+// profiling: launch counters and CUDA-event device times per kernel category -------------------
+enum ProfCat { P_DECOMP = 0, P_PROP = 1, P_BIN = 2, P_REC = 3, P_GATHER = 4, P_REDUCE = 5, P_OTHER = 6, P_NCAT = 8 };
+struct ProfScope {  // wraps one kernel launch on stream s
+    ProfScope(int cat, cudaStream_t s);
+    ~ProfScope();
+    int idx;
+    cudaStream_t s;
+};
+bool prof_counting();
+void prof_add_beam_steps(int64_t n);
+void prof_add_pairs_tested(int64_t n);
+int64_t read_pair_counter(bool reset);  // gather.cu
+
 // grow-only device / pinned-host buffers -----------------------------------------------------
 struct DevBuf {
     void *p = nullptr;
@@ -108,12 +121,17 @@ struct SampleWindow {
     int n;                  // samples in this window
     const int *step;        // DEVICE: local step of each sample (0-based within the window)
     const void *theta;      // DEVICE: R fraction in [0,1]
-    void *rec;              // DEVICE: records [n][cap][REC]
+    void *rec;              // DEVICE: records [n][n_rec][REC]
+    int64_t n_in[4];        // class c: the first n_in[c] beams of its block get records ...
+    int64_t rec_off[4];     // ... at record index rec_off[c] + (position - off_cls[c])
+    int64_t n_rec;          // records per sample
 };
 fga_status launch_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps, const SampleWindow *sw,
                             cudaStream_t s);
-fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, int64_t n, void *rec,
-                                     cudaStream_t s);
+// records of the current state for the first n_in[c] sorted beams of each class (perm: sorted
+// position -> beam), written at rec_off[c] + (position - off_cls[c])
+fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, const int64_t n_in[4],
+                                     const int64_t rec_off[4], void *rec, cudaStream_t s);
 // gather.cu
 struct BinGrid {
     float o[3];

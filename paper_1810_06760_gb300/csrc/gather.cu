@@ -49,6 +49,7 @@ fga_status bin_centres(const BinGrid &g, const void *Q_src, int q_kind, int64_t 
                        const int32_t *cls_or_null, int32_t *keys, cudaStream_t s) {
     if (n == 0) return FGA_OK;
     const unsigned blocks = (unsigned)((n + 255) / 256);
+    ProfScope ps(P_BIN, s);
     switch (q_kind) {
     case Q_F32_AOS3: keys_kernel<float><<<blocks, 256, 0, s>>>(g, (const float *)Q_src, 3, 1, n, cls_or_null, keys); break;
     case Q_F32_SOA: keys_kernel<float><<<blocks, 256, 0, s>>>(g, (const float *)Q_src, 1, q_stride, n, cls_or_null, keys); break;
@@ -189,9 +190,18 @@ static fga_status exclusive_scan(Workspace &ws, uint32_t *a, int64_t n, cudaStre
     }
     FGA_TRY(ws.scan_blocks.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(nb, 1)));
     uint32_t *bs = ws.scan_blocks.as<uint32_t>();
-    scan_block_kernel<<<(unsigned)nb, SC_T, 0, s>>>(a, n, bs);
-    scan_sums_kernel<<<1, 1024, 0, s>>>(bs, (int)nb);
-    scan_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n, bs);
+    {
+        ProfScope ps(P_BIN, s);
+        scan_block_kernel<<<(unsigned)nb, SC_T, 0, s>>>(a, n, bs);
+    }
+    {
+        ProfScope ps(P_BIN, s);
+        scan_sums_kernel<<<1, 1024, 0, s>>>(bs, (int)nb);
+    }
+    {
+        ProfScope ps(P_BIN, s);
+        scan_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n, bs);
+    }
     FGA_CUDA(cudaGetLastError());
     return FGA_OK;
 }
@@ -213,8 +223,12 @@ fga_status radix_sort_pairs(Workspace &ws, int32_t *keys, int32_t *vals, int64_t
     int32_t *ka = keys, *va = vals, *kb = ws.keys_alt.as<int32_t>(), *vb = ws.vals_alt.as<int32_t>();
     uint32_t *hist = ws.hist.as<uint32_t>();
     for (int shift = 0; shift < bits; shift += 8) {
-        rs_hist_kernel<<<ntiles, RS_T, 0, s>>>(ka, n, shift, ntiles, hist);
+        {
+            ProfScope ps(P_BIN, s);
+            rs_hist_kernel<<<ntiles, RS_T, 0, s>>>(ka, n, shift, ntiles, hist);
+        }
         FGA_TRY(exclusive_scan(ws, hist, (int64_t)256 * ntiles, s));
+        ProfScope ps(P_BIN, s);
         rs_scatter_kernel<<<ntiles, RS_T, 0, s>>>(ka, va, n, shift, ntiles, hist, kb, vb);
         FGA_CUDA(cudaGetLastError());
         std::swap(ka, kb);
@@ -234,6 +248,7 @@ __global__ void cell_start_kernel(const int32_t *__restrict__ keys, int64_t n, i
 }
 
 fga_status cell_starts(const int32_t *sorted_keys, int64_t n, int nbuckets, int32_t *cell_start, cudaStream_t s) {
+    ProfScope ps(P_BIN, s);
     cell_start_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(sorted_keys, n, nbuckets, cell_start);
     FGA_CUDA(cudaGetLastError());
     return FGA_OK;
@@ -243,6 +258,7 @@ fga_status sort_keys_to_perm(Workspace &ws, int32_t *keys, int64_t n, int nbucke
                              int32_t *cell_start, cudaStream_t s) {
     FGA_TRY(ws.vals.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
     int32_t *vals = ws.vals.as<int32_t>();
+    ProfScope ps(P_BIN, s);
     if (n > 0) iota_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(vals, n);
     int bits = 0;
     while ((1ll << bits) < (long long)nbuckets) bits++;
@@ -277,6 +293,7 @@ fga_status permute_beams(fga_beams *b, const int32_t *perm, cudaStream_t s) {
     FGA_TRY(b->id_alt.ensure(4 * b->cap));
     const unsigned blocks = (unsigned)((b->nb + 255) / 256);
     if (b->nb > 0) {
+        ProfScope ps(P_BIN, s);
         if (rb == 8)
             permute_kernel<double><<<blocks, 256, 0, s>>>(b->state.as<double>(), b->state_alt.as<double>(),
                                                           b->flags.as<int32_t>(), b->flags_alt.as<int32_t>(),
@@ -319,11 +336,30 @@ BinGrid make_grid(const double *pts, int64_t n, double reach) {
     return g;
 }
 
+// (beam, point) pairs that fell inside the window, counted when profiling is on
+static __device__ unsigned long long g_pairs_in_window;
+
+int64_t read_pair_counter(bool reset) {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_pairs_in_window, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (reset) {
+        const unsigned long long z = 0;
+        cudaMemcpyToSymbol(g_pairs_in_window, &z, sizeof z);
+    }
+    return (int64_t)v;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(128) gather_kernel(const R *__restrict__ rec, const double *__restrict__ pts,
                                                     const int32_t *__restrict__ tile_pts, const int4 *__restrict__ items,
-                                                    R k, R rw2, R *__restrict__ partial) {
+                                                    R k, R rw2, R *__restrict__ partial, int count_pairs) {
     __shared__ R red[4][32][6];
+    __shared__ unsigned npairs;
+    if (threadIdx.x == 0) npairs = 0;
+    unsigned mine = 0;
     const int4 it = items[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pi = tile_pts[it.x * 32 + lane];
@@ -360,6 +396,7 @@ __global__ void __launch_bounds__(128) gather_kernel(const R *__restrict__ rec, 
         const R d0 = x0 - q[0], d1 = x1 - q[1], d2 = x2 - q[2];
         const R r2 = d0 * d0 + d1 * d1 + d2 * d2;
         if (r2 <= rw2) {
+            mine++;
             const R ph = k * (q[3] * d0 + q[4] * d1 + q[5] * d2);
             R er, ei;
             gauss_phase_exp<R>(ph, hk * r2, &er, &ei);
@@ -373,7 +410,9 @@ __global__ void __launch_bounds__(128) gather_kernel(const R *__restrict__ rec, 
     }
 #pragma unroll
     for (int j = 0; j < 6; j++) red[warp][lane][j] = acc[j];
+    if (count_pairs) atomicAdd(&npairs, mine);
     __syncthreads();
+    if (count_pairs && threadIdx.x == 0) atomicAdd(&g_pairs_in_window, (unsigned long long)npairs);
     if (warp == 0) {
 #pragma unroll
         for (int j = 0; j < 6; j++) {
@@ -437,6 +476,16 @@ fga_status build_sum_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_s
     }
     const int ntiles = (int)tile_cell.size();
     FGA_CUDA(cudaStreamSynchronize(s));  // cell_start on the host
+    plan.n_rec = 0;
+    for (int cl = 0; cl < 4; cl++) {
+        plan.n_in[cl] = 0;
+        plan.rec_off[cl] = plan.n_rec;
+        if (cl < nclasses) {
+            const int cb = cl * (g.ncells + 1);
+            plan.n_in[cl] = cs[cb + g.ncells] - cs[cb];
+        }
+        plan.n_rec += plan.n_in[cl];
+    }
     // candidate ranges per tile: (c0 +- 1, c1 +- 1) x contiguous c2 - 1 .. c2 + 1, per class
     struct Rg {
         int tile, b, e;
@@ -452,7 +501,9 @@ fga_status build_sum_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_s
             for (int a0 = std::max(c0 - 1, 0); a0 <= std::min(c0 + 1, g.nc[0] - 1); a0++)
                 for (int a1 = std::max(c1 - 1, 0); a1 <= std::min(c1 + 1, g.nc[1] - 1); a1++) {
                     const int id0 = (a0 * g.nc[1] + a1) * g.nc[2];
-                    const int bb = cs[cb + id0 + lo2], ee = cs[cb + id0 + hi2 + 1];
+                    // sorted positions -> compact record indices of class cl
+                    const int64_t shift = plan.rec_off[cl] - cs[cb];
+                    const int bb = (int)(cs[cb + id0 + lo2] + shift), ee = (int)(cs[cb + id0 + hi2 + 1] + shift);
                     if (ee > bb) {
                         ranges.push_back({t, bb, ee});
                         total += ee - bb;
@@ -495,22 +546,29 @@ fga_status build_sum_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_s
     return FGA_OK;
 }
 
+const int32_t *plan_host_cell_start(const Workspace &ws) { return ws.h_cell_start.as<int32_t>(); }
+
 fga_status run_sum(Workspace &ws, const SumPlan &plan, int precision, const void *rec_sorted, const double *pts_dev,
                    double k, double rw, void *u_out, cudaStream_t s) {
     if (plan.ntiles == 0) return FGA_OK;
     const size_t rb = precision == FGA_PREC_FP64 ? 8 : 4;
     FGA_TRY(ws.partial.ensure(rb * 32 * 6 * (size_t)std::max(plan.nitems, 1)));
+    const int cnt = prof_counting() ? 1 : 0;
+    prof_add_pairs_tested(plan.pairs_tested);
     if (plan.nitems > 0) {
+        ProfScope ps(P_GATHER, s);
         if (rb == 8)
             gather_kernel<double><<<plan.nitems, 128, 0, s>>>((const double *)rec_sorted, pts_dev, plan.tile_pts,
-                                                              plan.items, k, rw * rw, ws.partial.as<double>());
+                                                              plan.items, k, rw * rw, ws.partial.as<double>(), cnt);
         else
             gather_kernel<float><<<plan.nitems, 128, 0, s>>>((const float *)rec_sorted, pts_dev, plan.tile_pts,
-                                                             plan.items, (float)k, (float)(rw * rw), ws.partial.as<float>());
+                                                             plan.items, (float)k, (float)(rw * rw), ws.partial.as<float>(),
+                                                             cnt);
         FGA_CUDA(cudaGetLastError());
     }
     const int tpb = 4;  // tiles per 128-thread block
     const unsigned blocks = (unsigned)((plan.ntiles + tpb - 1) / tpb);
+    ProfScope ps(P_REDUCE, s);
     if (rb == 8)
         reduce_kernel<double><<<blocks, 32 * tpb, 0, s>>>(ws.partial.as<double>(), plan.tile_pts, plan.item_start,
                                                           plan.ntiles, (double *)u_out);

@@ -14,8 +14,11 @@ struct SumPlan {
     int ntiles = 0, nitems = 0;
     const int32_t *tile_pts = nullptr;   // DEVICE [ntiles][32] point index or -1
     const int32_t *item_start = nullptr; // DEVICE [ntiles + 1]
-    const int4 *items = nullptr;         // DEVICE [nitems] {tile, begin, end, 0}
+    const int4 *items = nullptr;         // DEVICE [nitems] {tile, begin, end, 0}: record indices
     int64_t pairs_tested = 0;            // point x candidate-beam pairs (upper bound of the work)
+    // Records are kept only for beams inside the grid: class c's in-grid beams sit at sorted
+    // positions off_cls[c] .. off_cls[c] + n_in[c] and get record indices rec_off[c] + (pos - off_cls[c]).
+    int64_t n_in[4] = {0, 0, 0, 0}, rec_off[4] = {0, 0, 0, 0}, n_rec = 0;
 };
 
 fga_status sort_keys_to_perm(Workspace &ws, int32_t *keys, int64_t n, int nbuckets, int32_t **perm_out,
@@ -24,6 +27,8 @@ fga_status build_sum_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_s
                           const double *pts_host, int64_t npts, cudaStream_t s, SumPlan &plan);
 fga_status run_sum(Workspace &ws, const SumPlan &plan, int precision, const void *rec_sorted, const double *pts_dev,
                    double k, double rw, void *u_out, cudaStream_t s);
+// bucket starts copied to the host by build_sum_plan (valid after it returns)
+const int32_t *plan_host_cell_start(const Workspace &ws);
 
 // exp(am) * (cos ph, sin ph).  FP32: Cody-Waite reduction of ph by 2 pi (two-part constant), then
 // the hardware sine/cosine and exponential approximations; FP64: the libm-accurate functions.

@@ -9,7 +9,8 @@ template <typename R, int WAVE, int MED>
 __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st, const int32_t *__restrict__ flags,
                                                   int64_t cap, int64_t beg, int64_t n, R sg, R dt, int nsteps,
                                                   int n_samp, const int *__restrict__ samp_step,
-                                                  const R *__restrict__ samp_theta, R w, R *__restrict__ rec) {
+                                                  const R *__restrict__ samp_theta, R w, R *__restrict__ rec,
+                                                  int64_t rec_lim, int64_t rec_stride) {
     const int64_t b = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= beg + n) return;
     R y[NF];
@@ -45,11 +46,13 @@ __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st
         // k1 of the next step = f(y_{n+1}); also the right-end slope of the Hermite interpolant
         beam_rhs<R, WAVE, MED>(M, sg, ref_e1, acc, kk);
         while (js < n_samp && samp_step[js] == step) {
-            R r[REC];
-            beam_record<R, WAVE>(ref_e1, y, k1, acc, kk, dt, samp_theta[js], w, r);
-            R *dst = rec + ((int64_t)js * cap + b) * REC;
+            if (b - beg < rec_lim) {
+                R r[REC];
+                beam_record<R, WAVE>(ref_e1, y, k1, acc, kk, dt, samp_theta[js], w, r);
+                R *dst = rec + ((int64_t)js * rec_stride + (b - beg)) * REC;
 #pragma unroll
-            for (int q = 0; q < REC; q++) dst[q] = r[q];
+                for (int q = 0; q < REC; q++) dst[q] = r[q];
+            }
             js++;
         }
 #pragma unroll
@@ -66,9 +69,9 @@ __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st
 template <typename R, int WAVE>
 __global__ void records_kernel(const R *__restrict__ st, const int32_t *__restrict__ flags, int64_t cap,
                                const int32_t *__restrict__ perm, int64_t beg, int64_t n, R w, R *__restrict__ rec) {
-    const int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= beg + n) return;
-    const int64_t b = perm ? perm[i] : i;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t b = perm ? perm[beg + i] : beg + i;
     R y[NF];
 #pragma unroll
     for (int f = 0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
@@ -87,10 +90,13 @@ static void launch_one(const fga_model *m, fga_beams *b, int cls, R dt, int nste
     const int T = 128;
     const int64_t blocks = (n + T - 1) / T;
     const R sg = (cls & 1) ? R(-1) : R(1);
+    R *rec = sw ? static_cast<R *>(sw->rec) + sw->rec_off[cls] * REC : nullptr;
+    prof_add_beam_steps(n * (int64_t)nsteps);
+    ProfScope ps(P_PROP, s);
     rk4_kernel<R, WAVE, MED><<<(unsigned)blocks, T, 0, s>>>(
         m->dev, b->state.as<R>(), b->flags.as<int32_t>(), b->cap, b->off_cls[cls], n, sg, dt, nsteps,
-        sw ? sw->n : 0, sw ? sw->step : nullptr, sw ? static_cast<const R *>(sw->theta) : nullptr, (R)b->w,
-        sw ? static_cast<R *>(sw->rec) : nullptr);
+        sw ? sw->n : 0, sw ? sw->step : nullptr, sw ? static_cast<const R *>(sw->theta) : nullptr, (R)b->w, rec,
+        sw ? sw->n_in[cls] : 0, sw ? sw->n_rec : 0);
 }
 
 template <typename R, int MED>
@@ -124,27 +130,30 @@ fga_status launch_propagate(const fga_model *m, fga_beams *b, double dt, int nst
     return FGA_OK;
 }
 
-fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, int64_t n, void *rec, cudaStream_t s) {
-    (void)n;
+fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, const int64_t n_in[4],
+                                     const int64_t rec_off[4], void *rec, cudaStream_t s) {
     const int T = 256;
     for (int cls = 0; cls < 4; cls++) {
-        const int64_t nc = b->n_cls[cls];
+        const int64_t nc = n_in[cls];
         if (nc == 0) continue;
         const unsigned blocks = (unsigned)((nc + T - 1) / T);
+        ProfScope ps(P_REC, s);
         if (b->precision == FGA_PREC_FP64) {
+            double *dst = (double *)rec + rec_off[cls] * REC;
             if (cls < 2)
                 records_kernel<double, 0><<<blocks, T, 0, s>>>(b->state.as<double>(), b->flags.as<int32_t>(), b->cap,
-                                                               perm, b->off_cls[cls], nc, b->w, (double *)rec);
+                                                               perm, b->off_cls[cls], nc, b->w, dst);
             else
                 records_kernel<double, 1><<<blocks, T, 0, s>>>(b->state.as<double>(), b->flags.as<int32_t>(), b->cap,
-                                                               perm, b->off_cls[cls], nc, b->w, (double *)rec);
+                                                               perm, b->off_cls[cls], nc, b->w, dst);
         } else {
+            float *dst = (float *)rec + rec_off[cls] * REC;
             if (cls < 2)
                 records_kernel<float, 0><<<blocks, T, 0, s>>>(b->state.as<float>(), b->flags.as<int32_t>(), b->cap,
-                                                              perm, b->off_cls[cls], nc, (float)b->w, (float *)rec);
+                                                              perm, b->off_cls[cls], nc, (float)b->w, dst);
             else
                 records_kernel<float, 1><<<blocks, T, 0, s>>>(b->state.as<float>(), b->flags.as<int32_t>(), b->cap,
-                                                              perm, b->off_cls[cls], nc, (float)b->w, (float *)rec);
+                                                              perm, b->off_cls[cls], nc, (float)b->w, dst);
         }
     }
     FGA_CUDA(cudaGetLastError());

@@ -22,7 +22,8 @@ PREC_FP32, PREC_FP64 = 0, 1
 MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
 EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_propagate", "fga_reconstruct",
             "fga_solve", "fga_beams_count", "fga_beams_export", "fga_beams_destroy", "fga_bin",
-            "fga_last_error", "fga_version"]
+            "fga_profile_enable", "fga_profile_read", "fga_last_error", "fga_version"]
+PROFILE_CATEGORIES = ["decompose", "propagate", "binning", "records", "gauss_sum", "gauss_reduce", "other", "unused"]
 
 
 class FGAError(RuntimeError):
@@ -43,6 +44,11 @@ class InitDesc(C.Structure):
                 ("f", C.c_void_p), ("g", C.c_void_p), ("nq", C.c_int), ("q0", C.c_double * 3),
                 ("dq", C.c_double * 3), ("np", C.c_int), ("p0", C.c_double * 3), ("dp", C.c_double * 3),
                 ("class_mask", C.c_uint), ("precision", C.c_int)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("count", C.c_int64 * 8), ("ms", C.c_double * 8),
+                ("beam_steps", C.c_int64), ("pairs_in_window", C.c_int64), ("pairs_tested", C.c_int64)]
 
 
 class SolveDesc(C.Structure):
@@ -74,6 +80,8 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_beams_export.argtypes = [vp, vp, vp]
     L.fga_beams_destroy.argtypes = [vp]
     L.fga_bin.argtypes = [vp, i64, vp, C.c_float, vp, vp, vp, vp, vp]
+    L.fga_profile_enable.argtypes = [i32]
+    L.fga_profile_read.argtypes = [C.POINTER(Profile), i32]
     L.fga_last_error.argtypes = [C.c_char_p, C.c_size_t]
     L.fga_last_error.restype = None
     L.fga_version.restype = C.c_int
@@ -258,6 +266,20 @@ def solve(model: Model, desc: InitDesc, dt: float, nsteps: int, times, rx=None, 
     _check(lib().fga_solve(model.h, C.byref(desc), C.byref(sd), _dptr(seis_out), _dptr(snap_out),
                            _stream(stream)))
     return seis_out, snap_out
+
+
+def profile_enable(mode: int) -> None:
+    """0 off, 1 counters, 2 counters + per-kernel CUDA-event device times."""
+    _check(lib().fga_profile_enable(int(mode)))
+
+
+def profile_read(reset: bool = True) -> dict:
+    p = Profile()
+    _check(lib().fga_profile_read(C.byref(p), int(bool(reset))))
+    return {"launches": p.launches,
+            "count": {n: p.count[i] for i, n in enumerate(PROFILE_CATEGORIES[:7])},
+            "ms": {n: p.ms[i] for i, n in enumerate(PROFILE_CATEGORIES[:7])},
+            "beam_steps": p.beam_steps, "pairs_in_window": p.pairs_in_window, "pairs_tested": p.pairs_tested}
 
 
 def bin_centres(Q, origin, inv_h: float, nc, stream=None):
