@@ -122,6 +122,21 @@ fga_status fga_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps
 fga_status fga_reconstruct(const fga_beams *b, const double *x, int64_t n, double rw, void *u_out,
                            fga_stream_t s);
 
+/* The same sum as fga_reconstruct, for callers that may not allocate device memory: code running
+ * where cudaMalloc/cudaFree are unavailable or unsafe (a host callback, a real-time loop that must
+ * not stall on the allocator's implicit synchronisation, a plug-in handed buffers by an outside
+ * memory pool).  The paper has no counterpart; this is a service of the library.
+ * It allocates nothing: its only scratch is a fixed 12 MiB device array inside the library (held by
+ * every GPU that loads the library until the process exits).  It tests every beam against every
+ * point (no binning), so it suits modest beam counts; n must be <= 4096 (larger n is rejected with
+ * FGA_ERR_INVALID_ARG and a message).  The first call on each device looks up the scratch array's
+ * address, so make that first call before any stream capture.  All calls share the scratch array:
+ * calls that overlap on the GPU (e.g. on two streams) race; calls ordered on one stream do not.
+ * Nothing in the scratch has to start at zero (each call overwrites what it reads).
+ *  x: DEVICE float64 [n][3]; u_out: DEVICE complex [n][3] in the beams' precision. */
+fga_status fga_reconstruct_noalloc(const fga_beams *b, const double *x, int64_t n, double rw, void *u_out,
+                                   fga_stream_t s);
+
 /* Whole forward solve: decompose, propagate nsteps of dt, and sum at the sample times.
  *  times: HOST, n_times increasing values in (0, nsteps*dt]; a sample inside step n uses cubic
  *         Hermite interpolation of Q and P and linear interpolation of the amplitudes.

@@ -21,7 +21,7 @@ FGA_OK, FGA_ERR_INVALID_ARG, FGA_ERR_OOM, FGA_ERR_CUDA, FGA_ERR_TIMEOUT, FGA_ERR
 PREC_FP32, PREC_FP64 = 0, 1
 MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
 EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_propagate", "fga_reconstruct",
-            "fga_solve", "fga_beams_count", "fga_beams_export", "fga_beams_destroy", "fga_bin",
+            "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export", "fga_beams_destroy", "fga_bin",
             "fga_profile_enable", "fga_profile_read", "fga_last_error", "fga_version"]
 PROFILE_CATEGORIES = ["decompose", "propagate", "binning", "records", "gauss_sum", "gauss_reduce", "other", "unused"]
 
@@ -75,6 +75,7 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_decompose.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(vp), vp]
     L.fga_propagate.argtypes = [vp, vp, C.c_double, i32, vp]
     L.fga_reconstruct.argtypes = [vp, vp, i64, C.c_double, vp, vp]
+    L.fga_reconstruct_noalloc.argtypes = [vp, vp, i64, C.c_double, vp, vp]
     L.fga_solve.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(SolveDesc), vp, vp, vp]
     L.fga_beams_count.argtypes = [vp, vp]
     L.fga_beams_export.argtypes = [vp, vp, vp]
@@ -241,6 +242,16 @@ def reconstruct(beams: Beams, x, rw: float = 0.0, out=None, stream=None):
         out = torch.empty((n, 3), dtype=_cdtype(beams.precision), device=x.device)
     _check(lib().fga_reconstruct(beams.h, _dptr(x) if n else None, n, float(rw), _dptr(out) if n else None,
                                  _stream(stream)))
+    return out
+
+
+def reconstruct_noalloc(beams: Beams, x, out, rw: float = 0.0, stream=None):
+    """fga_reconstruct_noalloc: the same sum as ``reconstruct`` without any device allocation inside
+    the library (fixed internal scratch; at most 4096 points per call).  The caller supplies ``out``
+    (complex [n, 3] in the beams' precision) as well as ``x``."""
+    n = x.shape[0]
+    _check(lib().fga_reconstruct_noalloc(beams.h, _dptr(x) if n else None, n, float(rw), _dptr(out) if n else None,
+                                         _stream(stream)))
     return out
 
 
