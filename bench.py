@@ -31,6 +31,8 @@ FLOP_PER_BEAM_STEP = {"P": 4180.0, "S": 4400.0}
 FLOP_PER_PAIR_IN = 43.0       # dx, r^2, phase, exponent, e*(cos, sin), 3 complex multiply-adds
 FLOP_PER_PAIR_OUT = 9.0       # dx, r^2, compare
 MUFU_PER_PAIR_IN = 3.0        # exp2, sin, cos
+FLOP_PER_LATTICE_PAIR_IN = 26.0   # window test (add, compare) + 3 complex multiply-adds
+FLOP_PER_LATTICE_PAIR_OUT = 2.0   # window test
 SMS = 152
 
 
@@ -214,16 +216,15 @@ def run_ours(args):
     beam_steps = nb * w.nsteps
     model = fga.model_from_medium(w.medium, dev)
     f = torch.as_tensor(w.f, device=dev)
-    rx = torch.as_tensor(w.receivers, device=dev)
-    sn = torch.as_tensor(w.snapshot, device=dev)
     desc = fga.init_desc(w.k, f, None, w.y0, w.dy, w.mesh, w.classes, prec)
     cdt = torch.complex64 if prec == fga.PREC_FP32 else torch.complex128
-    seis = torch.empty((len(w.times), rx.shape[0], 3), dtype=cdt, device=dev)
-    snap = torch.empty((sn.shape[0], 3), dtype=cdt, device=dev)
+    seis = torch.empty((len(w.times),) + tuple(len(a) for a in w.rx_axes) + (3,), dtype=cdt, device=dev)
+    snap = torch.empty(tuple(len(a) for a in w.snap_axes) + (3,), dtype=cdt, device=dev)
     stream = torch.cuda.current_stream()
 
     def step():
-        fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, sn, rw=w.rw, seis_out=seis, snap_out=snap)
+        fga.solve(model, desc, w.dt, w.nsteps, w.times, rw=w.rw, seis_out=seis, snap_out=snap, rx_axes=w.rx_axes,
+                  snap_axes=w.snap_axes)
 
     for _ in range(args.warmup):
         step()
@@ -262,8 +263,9 @@ def run_ours(args):
         nS = sum(1 for c in w.classes if c >= 2) * w.mesh.M
         flops = (nP * FLOP_PER_BEAM_STEP["P"] + nS * FLOP_PER_BEAM_STEP["S"]) * w.nsteps * args.steps
     elif prec == fga.PREC_FP32 and top == "gauss_sum":
+        # lattice sum: one complex product per component and point (24 FLOP) + the window test (2)
         pin, pt = prof["pairs_in_window"], prof["pairs_tested"]
-        flops = pin * FLOP_PER_PAIR_IN + (pt - pin) * FLOP_PER_PAIR_OUT
+        flops = pin * FLOP_PER_LATTICE_PAIR_IN + (pt - pin) * FLOP_PER_LATTICE_PAIR_OUT
     else:
         flops = None
     launches = max(prof["count"][top], 1)
@@ -289,7 +291,8 @@ def run_ours(args):
         "latency_ms": {"p50": statistics.median(per_step_ms),
                        "p99": sorted(per_step_ms)[min(len(per_step_ms) - 1, math.ceil(0.99 * len(per_step_ms)) - 1)]},
         "gauss_sum_pairs_per_s": prof["pairs_in_window"] / gauss_s if gauss_s > 0 else None,
-        "receiver_samples_per_s": world * args.steps * (len(w.times) * rx.shape[0] + sn.shape[0]) / (total_ms / 1e3),
+        "receiver_samples_per_s": world * args.steps * (len(w.times) * len(w.receivers) + len(w.snapshot))
+        / (total_ms / 1e3),
         "kernel_ms": {k: v / args.steps for k, v in ms.items() if v > 0},
         "roofline": roof,
         "clocks": clocks,
@@ -299,24 +302,21 @@ def run_ours(args):
     if not args.no_e2e:
         # end to end through the public API from pinned host buffers: inputs in, solve, results out
         hf = torch.as_tensor(w.f).pin_memory()
-        hrx = torch.as_tensor(w.receivers).pin_memory()
-        hsn = torch.as_tensor(w.snapshot).pin_memory()
         hgp = torch.as_tensor(w.medium.grid_p).pin_memory()
         hgs = torch.as_tensor(w.medium.grid_s).pin_memory()
         oseis = torch.empty(seis.shape, dtype=cdt).pin_memory()
         osnap = torch.empty(snap.shape, dtype=cdt).pin_memory()
-        h2d = sum(t.numel() * t.element_size() for t in (hf, hrx, hsn, hgp, hgs))
+        h2d = sum(t.numel() * t.element_size() for t in (hf, hgp, hgs))
+        h2d += 8 * sum(len(a) for a in w.rx_axes + w.snap_axes)   # lattice axes, copied by the library
         d2h = oseis.numel() * oseis.element_size() + osnap.numel() * osnap.element_size()
 
         def e2e_step():
             df = hf.to(dev, non_blocking=True)
-            drx = hrx.to(dev, non_blocking=True)
-            dsn = hsn.to(dev, non_blocking=True)
             gp = hgp.to(dev, non_blocking=True)
             gs = hgs.to(dev, non_blocking=True)
             m2 = fga.Model("grid", grid_p=gp, grid_s=gs, origin=w.medium.origin, spacing=w.medium.spacing)
             d2 = fga.init_desc(w.k, df, None, w.y0, w.dy, w.mesh, w.classes, prec)
-            s_, n_ = fga.solve(m2, d2, w.dt, w.nsteps, w.times, drx, dsn, rw=w.rw)
+            s_, n_ = fga.solve(m2, d2, w.dt, w.nsteps, w.times, rw=w.rw, rx_axes=w.rx_axes, snap_axes=w.snap_axes)
             oseis.copy_(s_, non_blocking=True)
             osnap.copy_(n_, non_blocking=True)
             torch.cuda.current_stream().synchronize()

@@ -122,6 +122,20 @@ fga_status fga_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps
 fga_status fga_reconstruct(const fga_beams *b, const double *x, int64_t n, double rw, void *u_out,
                            fga_stream_t s);
 
+/* A tensor lattice of points x_{ijl} = (axis[0][i], axis[1][j], axis[2][l]) (HOST arrays of n[d]
+ * increasing coordinates).  Results on a lattice are stored [i][j][l][3] (l fastest). */
+typedef struct {
+    int n[3];
+    const double *axis[3];
+} fga_lattice;
+
+/* Step 3 on a lattice (snapshot grids, receiver arrays): the same sum as fga_reconstruct at the
+ * lattice points, evaluated with the per-axis factorisation exp(i k P.(x-Q) - k|x-Q|^2/2) =
+ * prod_d exp(i k P_d (x_d-Q_d) - k (x_d-Q_d)^2/2) of Eq. FGA's Gaussian.  u_out: DEVICE complex
+ * [n0][n1][n2][3].  Errors: INVALID_ARG (empty axis, non-increasing axis), OOM, CUDA. */
+fga_status fga_reconstruct_lattice(const fga_beams *b, const fga_lattice *lat, double rw, void *u_out,
+                                   fga_stream_t s);
+
 /* The same sum as fga_reconstruct, for callers that may not allocate device memory: code running
  * where cudaMalloc/cudaFree are unavailable or unsafe (a host callback, a real-time loop that must
  * not stall on the allocator's implicit synchronisation, a plug-in handed buffers by an outside
@@ -141,9 +155,11 @@ fga_status fga_reconstruct_noalloc(const fga_beams *b, const double *x, int64_t 
  *  times: HOST, n_times increasing values in (0, nsteps*dt]; a sample inside step n uses cubic
  *         Hermite interpolation of Q and P and linear interpolation of the amplitudes.
  *  rx:    DEVICE float64 [n_rx][3]; seis_out DEVICE complex [n_times][n_rx][3] (may be NULL if
- *         n_rx = 0).
+ *         n_rx = 0).  Or rx_lattice (non-NULL): receivers on a lattice, n_rx and rx ignored,
+ *         seis_out [n_times][n0][n1][n2][3].
  *  snap:  DEVICE float64 [n_snap][3] summed at t = nsteps*dt into snap_out DEVICE complex
- *         [n_snap][3] (may be NULL if n_snap = 0).
+ *         [n_snap][3] (may be NULL if n_snap = 0).  Or snap_lattice (non-NULL): n_snap and snap
+ *         ignored, snap_out [n0][n1][n2][3].
  *  rw <= 0 selects 6/sqrt(k).  Errors: INVALID_ARG, OOM, CUDA. */
 typedef struct {
     double dt;
@@ -155,6 +171,8 @@ typedef struct {
     int64_t n_snap;
     const double *snap;
     double rw;
+    const fga_lattice *rx_lattice;
+    const fga_lattice *snap_lattice;
 } fga_solve_desc;
 
 fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd,

@@ -253,6 +253,7 @@ fga_status fga_model_create(fga_model **out, const fga_model_desc *d, const floa
             if (l + 1 < d->nlayers) m->dev.zif[l] = d->z_interfaces[l];
         }
     }
+    m->dev.fill_f32();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         m->grid.release();
@@ -323,6 +324,62 @@ static fga_status reconstruct_now(const fga_beams *b, const double *x_dev, const
     return run_sum(ws, plan, b->precision, ws.rec.p, x_dev, b->k, rw, u_out, s);
 }
 
+static fga_status check_lattice(const fga_lattice *L, const char *who) {
+    for (int d = 0; d < 3; d++) {
+        if (L->n[d] < 1 || !L->axis[d]) {
+            set_error(std::string(who) + ": lattice axes need n >= 1 and a coordinate array");
+            return FGA_ERR_INVALID_ARG;
+        }
+        for (int i = 0; i < L->n[d]; i++)
+            if (!std::isfinite(L->axis[d][i]) || (i > 0 && !(L->axis[d][i] > L->axis[d][i - 1]))) {
+                set_error(std::string(who) + ": lattice coordinates must be finite and increasing");
+                return FGA_ERR_INVALID_ARG;
+            }
+    }
+    if ((int64_t)L->n[0] * L->n[1] * L->n[2] >= ((int64_t)1 << 31)) {
+        set_error(std::string(who) + ": lattice too large");
+        return FGA_ERR_INVALID_ARG;
+    }
+    return FGA_OK;
+}
+
+static std::vector<double> lattice_corners(const fga_lattice *L) {
+    std::vector<double> c;
+    for (int a = 0; a < 2; a++)
+        for (int b2 = 0; b2 < 2; b2++)
+            for (int e = 0; e < 2; e++) {
+                c.push_back(L->axis[0][a ? L->n[0] - 1 : 0]);
+                c.push_back(L->axis[1][b2 ? L->n[1] - 1 : 0]);
+                c.push_back(L->axis[2][e ? L->n[2] - 1 : 0]);
+            }
+    return c;
+}
+
+// lattice sum of the current state (records gathered in cell order, state untouched)
+static fga_status reconstruct_lattice_now(const fga_beams *b, const fga_lattice *L, double rw, void *u_out,
+                                          cudaStream_t s) {
+    Workspace &ws = b->ws;
+    const std::vector<double> corners = lattice_corners(L);
+    const BinGrid g = make_grid(corners.data(), 8, rw);
+    int32_t *perm = nullptr;
+    FGA_TRY(bin_beams(b, g, &perm, s));
+    LatticePlan plan;
+    FGA_TRY(build_lattice_plan(ws, g, ws.cell_start.as<int32_t>(), *L, s, plan));  // syncs
+    const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
+    FGA_TRY(ws.rec.ensure(rb * REC * (size_t)std::max<int64_t>(plan.n_rec, 1)));
+    FGA_TRY(launch_records_from_state(b, perm, plan.n_in, plan.rec_off, ws.rec.p, s));
+    return run_lattice(ws, plan, b->precision, ws.rec.p, b->k, rw, u_out, s);
+}
+
+fga_status fga_reconstruct_lattice(const fga_beams *b, const fga_lattice *lat, double rw, void *u_out,
+                                   fga_stream_t s_) {
+    cudaStream_t s = (cudaStream_t)s_;
+    FGA_CHECK(b && lat && u_out, "fga_reconstruct_lattice: NULL argument");
+    FGA_TRY(check_lattice(lat, "fga_reconstruct_lattice"));
+    if (!(rw > 0)) rw = 6.0 / std::sqrt(b->k);
+    return reconstruct_lattice_now(b, lat, rw, u_out, s);
+}
+
 fga_status fga_reconstruct(const fga_beams *b, const double *x, int64_t n, double rw, void *u_out, fga_stream_t s_) {
     cudaStream_t s = (cudaStream_t)s_;
     FGA_CHECK(b, "fga_reconstruct: NULL beams");
@@ -343,8 +400,13 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
     FGA_CHECK(sd->nsteps >= 1 && std::isfinite(sd->dt) && sd->dt != 0.0, "fga_solve: nsteps >= 1 and dt != 0");
     FGA_CHECK(sd->n_times >= 0 && sd->n_rx >= 0 && sd->n_snap >= 0, "fga_solve: negative counts");
     FGA_CHECK(sd->n_times == 0 || sd->times, "fga_solve: times is NULL");
-    FGA_CHECK(sd->n_rx == 0 || sd->n_times == 0 || (sd->rx && seis_out), "fga_solve: receivers/output missing");
-    FGA_CHECK(sd->n_snap == 0 || (sd->snap && snap_out), "fga_solve: snapshot points/output missing");
+    const fga_lattice *rxL = sd->rx_lattice, *snL = sd->snap_lattice;
+    if (rxL) FGA_TRY(check_lattice(rxL, "fga_solve (receivers)"));
+    if (snL) FGA_TRY(check_lattice(snL, "fga_solve (snapshot)"));
+    FGA_CHECK(rxL || sd->n_rx == 0 || sd->n_times == 0 || (sd->rx && seis_out), "fga_solve: receivers/output missing");
+    FGA_CHECK(!rxL || sd->n_times == 0 || seis_out, "fga_solve: seismogram output missing");
+    FGA_CHECK(snL || sd->n_snap == 0 || (sd->snap && snap_out), "fga_solve: snapshot points/output missing");
+    FGA_CHECK(!snL || snap_out, "fga_solve: snapshot output missing");
     const double T = sd->dt * sd->nsteps;
     std::vector<int> sstep((size_t)sd->n_times);
     std::vector<double> sth((size_t)sd->n_times);
@@ -370,9 +432,15 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
     const size_t rb = fp64 ? 8 : 4;
     Workspace &ws = b->ws;
     std::vector<double> rxh, snh;
-    const bool seis = sd->n_rx > 0 && sd->n_times > 0;
-    if (seis) FGA_TRY(host_points(sd->rx, sd->n_rx, rxh, s));
-    if (sd->n_snap > 0) FGA_TRY(host_points(sd->snap, sd->n_snap, snh, s));
+    const bool seis = (rxL || sd->n_rx > 0) && sd->n_times > 0;
+    const int64_t nrx = rxL ? (int64_t)rxL->n[0] * rxL->n[1] * rxL->n[2] : sd->n_rx;
+    if (seis) {
+        if (rxL)
+            rxh = lattice_corners(rxL);
+        else
+            FGA_TRY(host_points(sd->rx, sd->n_rx, rxh, s));
+    }
+    if (!snL && sd->n_snap > 0) FGA_TRY(host_points(sd->snap, sd->n_snap, snh, s));
     // windows of W steps: the beams are sorted by cell once per window, with cells enlarged by the
     // largest distance a beam can travel inside the window
     const double cmax = std::max(m->cmax[0], m->cmax[1]);
@@ -380,7 +448,7 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
     W = std::max(1, std::min(W, 32));
     const double margin = sample_hermite_margin(cmax, sd->dt, W);
     BinGrid grx{};
-    if (seis) grx = make_grid(rxh.data(), sd->n_rx, rw + margin);
+    if (seis) grx = make_grid(rxh.data(), (int64_t)rxh.size() / 3, rw + margin);
     DevBuf samp;  // per-window sample fractions (R, at offset 0) and local steps (int, at soff)
     HostBuf hsamp;
     const int maxs = sd->n_times;
@@ -416,7 +484,17 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
         FGA_TRY(bin_beams(b, grx, &perm, s));
         FGA_TRY(permute_beams(b, perm, s));
         SumPlan plan;
-        FGA_TRY(build_sum_plan(ws, grx, ws.cell_start.as<int32_t>(), 4, rxh.data(), sd->n_rx, s, plan));  // syncs
+        LatticePlan lplan;
+        if (rxL) {
+            FGA_TRY(build_lattice_plan(ws, grx, ws.cell_start.as<int32_t>(), *rxL, s, lplan));  // syncs
+            for (int c = 0; c < 4; c++) {
+                plan.n_in[c] = lplan.n_in[c];
+                plan.rec_off[c] = lplan.rec_off[c];
+            }
+            plan.n_rec = lplan.n_rec;
+        } else {
+            FGA_TRY(build_sum_plan(ws, grx, ws.cell_start.as<int32_t>(), 4, rxh.data(), sd->n_rx, s, plan));  // syncs
+        }
         // shorten the window so that its samples' records fit the budget (a shorter window keeps the
         // cell margin valid)
         const int64_t per_sample = (int64_t)rb * REC * std::max<int64_t>(plan.n_rec, 1);
@@ -445,14 +523,20 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
         }
         FGA_TRY(launch_propagate(m, b, sd->dt, nw, &sw, s));
         for (int j = 0; j < ns; j++) {
-            void *out = static_cast<char *>(seis_out) + rb * 6 * (size_t)sd->n_rx * (size_t)(js + j);
+            void *out = static_cast<char *>(seis_out) + rb * 6 * (size_t)nrx * (size_t)(js + j);
             const void *rec = static_cast<const char *>(ws.rec.p) + (size_t)per_sample * j;
-            FGA_TRY(run_sum(ws, plan, b->precision, rec, sd->rx, b->k, rw, out, s));
+            if (rxL)
+                FGA_TRY(run_lattice(ws, lplan, b->precision, rec, b->k, rw, out, s));
+            else
+                FGA_TRY(run_sum(ws, plan, b->precision, rec, sd->rx, b->k, rw, out, s));
         }
         js = j1;
         n0 += nw;
     }
-    if (sd->n_snap > 0) FGA_TRY(reconstruct_now(b, sd->snap, snh, sd->n_snap, rw, snap_out, s));
+    if (snL)
+        FGA_TRY(reconstruct_lattice_now(b, snL, rw, snap_out, s));
+    else if (sd->n_snap > 0)
+        FGA_TRY(reconstruct_now(b, sd->snap, snh, sd->n_snap, rw, snap_out, s));
     // the beam set is freed by the guard; its buffers must not be in use
     FGA_CUDA(cudaStreamSynchronize(s));
     return FGA_OK;
@@ -522,7 +606,7 @@ fga_status fga_profile_read(fga_profile_t *out, int reset) {
     }
     out->beam_steps = g_prof.beam_steps;
     out->pairs_tested = g_prof.pairs_tested;
-    out->pairs_in_window = read_pair_counter(reset != 0);
+    out->pairs_in_window = read_pair_counter(reset != 0) + read_lattice_pair_counter(reset != 0);
     if (reset) {
         g_prof.launches = g_prof.beam_steps = g_prof.pairs_tested = 0;
         for (int c = 0; c < P_NCAT; c++) {

@@ -22,24 +22,29 @@ template <> struct Real<double> {
     static __device__ __forceinline__ double floor_(double x) { return floor(x); }
 };
 
+// model parameter in the kernel's precision (double field for FP64, its FP32 copy for FP32)
+template <typename R> __device__ __forceinline__ R mp(double d, float f);
+template <> __device__ __forceinline__ float mp<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double mp<double>(double d, float) { return d; }
+
 // ---------------------------------------------------------------------------------------------
 // A0: c, grad c, Hessian c at x (10 fields: c, c1, c2, c3, c11, c12, c13, c22, c23, c33)
 // ---------------------------------------------------------------------------------------------
 template <typename R, int MED>
 __device__ __forceinline__ void model_eval(const ModelDev &M, int wave, const R x[3], R c[10]) {
     if (MED == FGA_MEDIUM_CONST) {
-        c[0] = wave ? (R)M.cs0 : (R)M.cp0;
+        c[0] = wave ? mp<R>(M.cs0, M.fcs0) : mp<R>(M.cp0, M.fcp0);
 #pragma unroll
         for (int f = 1; f < 10; f++) c[f] = R(0);
     } else if (MED == FGA_MEDIUM_SINE) {
         R s[3], k[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) Real<R>::sincospi_(R(2) * x[d], &s[d], &k[d]);
-        const R A = (R)M.amp, w = R(6.283185307179586476925286766559);
-        const R sc = wave ? (R)M.cs_ratio : R(1);
+        const R A = mp<R>(M.amp, M.famp), w = R(6.283185307179586476925286766559);
+        const R sc = wave ? mp<R>(M.cs_ratio, M.fcs_ratio) : R(1);
         const R Aw = A * w * sc, Aww = A * w * w * sc;
         const R s123 = s[0] * s[1] * s[2];
-        c[0] = sc * ((R)M.cp0 + A * s123);
+        c[0] = sc * (mp<R>(M.cp0, M.fcp0) + A * s123);
         c[1] = Aw * k[0] * s[1] * s[2];
         c[2] = Aw * s[0] * k[1] * s[2];
         c[3] = Aw * s[0] * s[1] * k[2];
@@ -55,7 +60,7 @@ __device__ __forceinline__ void model_eval(const ModelDev &M, int wave, const R 
         R fr[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            R t = (x[d] - (R)M.o[d]) * (R)M.inv_h[d];
+            R t = (x[d] - mp<R>(M.o[d], M.fo[d])) * mp<R>(M.inv_h[d], M.finv_h[d]);
             const R hi = R(M.n[d] - 1);
             t = t < R(0) ? R(0) : (t > hi ? hi : t);
             int id = (int)Real<R>::floor_(t);
@@ -96,8 +101,8 @@ __device__ __forceinline__ void model_eval(const ModelDev &M, int wave, const R 
         for (int f = 0; f < 10; f++) c[f] = acc[f];
     } else {  // layered
         int l = 0;
-        for (int q = 0; q < M.nlay - 1; q++) l += (x[2] >= (R)M.zif[q]) ? 1 : 0;
-        c[0] = wave ? (R)M.lcs[l] : (R)M.lcp[l];
+        for (int q = 0; q < M.nlay - 1; q++) l += (x[2] >= mp<R>(M.zif[q], M.fzif[q])) ? 1 : 0;
+        c[0] = wave ? mp<R>(M.lcs[l], M.flcs[l]) : mp<R>(M.lcp[l], M.flcp[l]);
 #pragma unroll
         for (int f = 1; f < 10; f++) c[f] = R(0);
     }

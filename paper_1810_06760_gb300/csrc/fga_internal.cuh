@@ -33,6 +33,24 @@ struct ModelDev {
     const float4 *gp, *gs;  // grid: 3 float4 (10 fields + 2 pad) per node
     int nlay;
     double zif[MAX_LAYERS], lcp[MAX_LAYERS], lcs[MAX_LAYERS], lrho[MAX_LAYERS];
+    // FP32 copies of the scalar parameters: the FP32 kernels read these and never convert from
+    // double (FP64 instructions are very slow on this GPU)
+    float fcp0, fcs0, famp, fcs_ratio, fo[3], finv_h[3], fzif[MAX_LAYERS], flcp[MAX_LAYERS], flcs[MAX_LAYERS];
+    void fill_f32() {
+        fcp0 = (float)cp0;
+        fcs0 = (float)cs0;
+        famp = (float)amp;
+        fcs_ratio = (float)cs_ratio;
+        for (int d = 0; d < 3; d++) {
+            fo[d] = (float)o[d];
+            finv_h[d] = (float)inv_h[d];
+        }
+        for (int l = 0; l < MAX_LAYERS; l++) {
+            fzif[l] = (float)zif[l];
+            flcp[l] = (float)lcp[l];
+            flcs[l] = (float)lcs[l];
+        }
+    }
 };
 
 // error handling ---------------------------------------------------------------------------

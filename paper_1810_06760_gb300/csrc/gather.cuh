@@ -21,6 +21,22 @@ struct SumPlan {
     int64_t n_in[4] = {0, 0, 0, 0}, rec_off[4] = {0, 0, 0, 0}, n_rec = 0;
 };
 
+// Work split of a Gaussian sum on a tensor lattice: tiles are T0 x T1 x T2 boxes of the lattice.
+struct LatticePlan {
+    int T[3] = {1, 1, 1}, n[3] = {0, 0, 0}, nt[3] = {0, 0, 0};
+    int ntiles = 0, nitems = 0;
+    const double *ax[3] = {nullptr, nullptr, nullptr};  // DEVICE axis coordinates
+    const int32_t *item_start = nullptr;
+    const int4 *items = nullptr;
+    int64_t pairs_tested = 0;
+    int64_t n_in[4] = {0, 0, 0, 0}, rec_off[4] = {0, 0, 0, 0}, n_rec = 0;
+};
+fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, const fga_lattice &L,
+                              cudaStream_t s, LatticePlan &plan);
+fga_status run_lattice(Workspace &ws, const LatticePlan &plan, int precision, const void *rec, double k, double rw,
+                       void *u, cudaStream_t s);
+int64_t read_lattice_pair_counter(bool reset);
+
 fga_status sort_keys_to_perm(Workspace &ws, int32_t *keys, int64_t n, int nbuckets, int32_t **perm_out,
                              int32_t *cell_start, cudaStream_t s);
 fga_status build_sum_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, int nclasses,

@@ -21,7 +21,7 @@ FGA_OK, FGA_ERR_INVALID_ARG, FGA_ERR_OOM, FGA_ERR_CUDA, FGA_ERR_TIMEOUT, FGA_ERR
 PREC_FP32, PREC_FP64 = 0, 1
 MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
 EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_propagate", "fga_reconstruct",
-            "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export", "fga_beams_destroy", "fga_bin",
+            "fga_reconstruct_lattice", "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export", "fga_beams_destroy", "fga_bin",
             "fga_profile_enable", "fga_profile_read", "fga_last_error", "fga_version"]
 PROFILE_CATEGORIES = ["decompose", "propagate", "binning", "records", "gauss_sum", "gauss_reduce", "other", "unused"]
 
@@ -51,10 +51,24 @@ class Profile(C.Structure):
                 ("beam_steps", C.c_int64), ("pairs_in_window", C.c_int64), ("pairs_tested", C.c_int64)]
 
 
+class Lattice(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("axis", C.c_void_p * 3)]
+
+
 class SolveDesc(C.Structure):
     _fields_ = [("dt", C.c_double), ("nsteps", C.c_int), ("n_times", C.c_int), ("times", C.c_void_p),
                 ("n_rx", C.c_int64), ("rx", C.c_void_p), ("n_snap", C.c_int64), ("snap", C.c_void_p),
-                ("rw", C.c_double)]
+                ("rw", C.c_double), ("rx_lattice", C.c_void_p), ("snap_lattice", C.c_void_p)]
+
+
+def make_lattice(axes):
+    """(ctypes Lattice, kept arrays) from three 1-D coordinate arrays."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in axes]
+    L = Lattice()
+    L.n[:] = [a.size for a in arrs]
+    for d in range(3):
+        L.axis[d] = arrs[d].ctypes.data
+    return L, arrs
 
 
 _lib = None
@@ -76,6 +90,7 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_propagate.argtypes = [vp, vp, C.c_double, i32, vp]
     L.fga_reconstruct.argtypes = [vp, vp, i64, C.c_double, vp, vp]
     L.fga_reconstruct_noalloc.argtypes = [vp, vp, i64, C.c_double, vp, vp]
+    L.fga_reconstruct_lattice.argtypes = [vp, C.POINTER(Lattice), C.c_double, vp, vp]
     L.fga_solve.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(SolveDesc), vp, vp, vp]
     L.fga_beams_count.argtypes = [vp, vp]
     L.fga_beams_export.argtypes = [vp, vp, vp]
@@ -245,6 +260,17 @@ def reconstruct(beams: Beams, x, rw: float = 0.0, out=None, stream=None):
     return out
 
 
+def reconstruct_lattice(beams: Beams, axes, rw: float = 0.0, out=None, stream=None):
+    """u at the lattice points (axes[0][i], axes[1][j], axes[2][l]); returns complex [n0, n1, n2, 3]."""
+    import torch
+    L, keep = make_lattice(axes)
+    shape = tuple(int(a.size) for a in keep)
+    if out is None:
+        out = torch.empty(shape + (3,), dtype=_cdtype(beams.precision), device=torch.device("cuda", torch.cuda.current_device()))
+    _check(lib().fga_reconstruct_lattice(beams.h, C.byref(L), float(rw), _dptr(out), _stream(stream)))
+    return out
+
+
 def reconstruct_noalloc(beams: Beams, x, out, rw: float = 0.0, stream=None):
     """fga_reconstruct_noalloc: the same sum as ``reconstruct`` without any device allocation inside
     the library (fixed internal scratch; at most 4096 points per call).  The caller supplies ``out``
@@ -256,8 +282,10 @@ def reconstruct_noalloc(beams: Beams, x, out, rw: float = 0.0, stream=None):
 
 
 def solve(model: Model, desc: InitDesc, dt: float, nsteps: int, times, rx=None, snap=None, rw: float = 0.0,
-          seis_out=None, snap_out=None, stream=None):
-    """Whole forward solve.  Returns (seismograms [n_times, n_rx, 3] or None, snapshot [n_snap, 3] or None)."""
+          seis_out=None, snap_out=None, stream=None, rx_axes=None, snap_axes=None):
+    """Whole forward solve.  Receivers: points rx [n_rx, 3] (CUDA float64) or a lattice rx_axes (three
+    1-D arrays); snapshot likewise (snap or snap_axes).  Returns (seismograms [n_times, n_rx, 3] or
+    [n_times, n0, n1, n2, 3], snapshot [n_snap, 3] or [n0, n1, n2, 3]); None where not requested."""
     import torch
     times = np.ascontiguousarray(times, dtype=np.float64)
     sd = SolveDesc()
@@ -265,12 +293,30 @@ def solve(model: Model, desc: InitDesc, dt: float, nsteps: int, times, rx=None, 
     sd.n_times, sd.times = times.size, times.ctypes.data if times.size else None
     dev = torch.device("cuda", torch.cuda.current_device())
     cdt = _cdtype(desc.precision)
-    nrx = 0 if rx is None else rx.shape[0]
-    nsn = 0 if snap is None else snap.shape[0]
-    if nrx and times.size and seis_out is None:
-        seis_out = torch.empty((times.size, nrx, 3), dtype=cdt, device=dev)
-    if nsn and snap_out is None:
-        snap_out = torch.empty((nsn, 3), dtype=cdt, device=dev)
+    keep = []
+    if rx_axes is not None:
+        Lr, ka = make_lattice(rx_axes)
+        keep += [Lr, ka]
+        sd.rx_lattice = C.cast(C.pointer(Lr), C.c_void_p)
+        rshape = tuple(a.size for a in ka)
+        if times.size and seis_out is None:
+            seis_out = torch.empty((times.size,) + rshape + (3,), dtype=cdt, device=dev)
+        nrx = 0
+    else:
+        nrx = 0 if rx is None else rx.shape[0]
+        if nrx and times.size and seis_out is None:
+            seis_out = torch.empty((times.size, nrx, 3), dtype=cdt, device=dev)
+    if snap_axes is not None:
+        Ls, ks = make_lattice(snap_axes)
+        keep += [Ls, ks]
+        sd.snap_lattice = C.cast(C.pointer(Ls), C.c_void_p)
+        if snap_out is None:
+            snap_out = torch.empty(tuple(a.size for a in ks) + (3,), dtype=cdt, device=dev)
+        nsn = 0
+    else:
+        nsn = 0 if snap is None else snap.shape[0]
+        if nsn and snap_out is None:
+            snap_out = torch.empty((nsn, 3), dtype=cdt, device=dev)
     sd.n_rx, sd.rx = nrx, _dptr(rx) if nrx else None
     sd.n_snap, sd.snap = nsn, _dptr(snap) if nsn else None
     sd.rw = float(rw)

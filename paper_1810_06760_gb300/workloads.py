@@ -118,6 +118,8 @@ class Workload:
     receivers: np.ndarray     # float64 [nr, 3]
     rw: float                 # Gaussian-sum truncation radius
     snapshot: Optional[np.ndarray] = None   # float64 [ns, 3] grid points sampled at T
+    rx_axes: Optional[tuple] = None         # receivers as a lattice (three 1-D arrays), same order
+    snap_axes: Optional[tuple] = None       # snapshot as a lattice, same order as `snapshot`
 
     @property
     def T(self) -> float:
@@ -182,13 +184,15 @@ def smooth(nq: int = 24, np_: int = 8, ny: int = 128, nsteps: int = 400, dt: flo
     r = (np.arange(rx_side) + 0.5) / rx_side
     R1, R2 = np.meshgrid(r, r, indexing="ij")
     rx = np.stack([R1.ravel(), R2.ravel(), np.zeros(R1.size)], -1)
-    snap = None
+    rx_axes = (r, r, np.zeros(1))
+    snap = snap_axes = None
     if snap_side:
         s = (np.arange(snap_side) + 0.5) / snap_side
         S1, S2, S3 = np.meshgrid(s, s, s, indexing="ij")
         snap = np.stack([S1.ravel(), S2.ravel(), S3.ravel()], -1)
+        snap_axes = (s, s, s)
     return Workload("smooth", k, med, ny, y0, dy, f, None, mesh, tuple(classes), dt, nsteps, times, rx,
-                    window_radius(k), snap)
+                    window_radius(k), snap, rx_axes, snap_axes)
 
 
 def random_points(n: int, lo, hi, seed: int) -> np.ndarray:

@@ -112,6 +112,46 @@ def test_solve_seismograms_and_snapshot(fga, oracle, prec):
     assert rel_l2(snap.cpu().numpy(), ref_snap) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("shape", [(19, 21, 1), (9, 17, 10)])
+def test_reconstruct_on_lattice(fga, oracle, prec, shape):
+    """Lattice sum (per-axis factorised Gaussians) equals the oracle's brute-force sum at the same
+    points; shapes give ragged tiles in every axis for both tile shapes (16x16x1 and 8x8x8)."""
+    import torch
+    w = _small_smooth(grid=True, nsteps=16)
+    model, desc, keep = gpu_setup(w, prec)
+    beams = fga.decompose(model, desc)
+    fga.propagate(model, beams, w.dt, w.nsteps)
+    axes = tuple(np.sort(W.random_points(1, 0, 1, 30 + a)[0, :1].tolist() + list(np.linspace(-0.05, 1.05, n)[1:]))
+                 if n > 1 else np.array([0.02]) for a, n in enumerate(shape))
+    axes = tuple(np.asarray(a, dtype=np.float64) for a in axes)
+    u = fga.reconstruct_lattice(beams, axes, rw=w.rw).cpu().numpy()
+    assert u.shape == tuple(len(a) for a in axes) + (3,)
+    X = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    omodel, mesh, obeams = oracle_beams(oracle, w)
+    ref = np.zeros((X.shape[0], 3), complex)
+    for cls, st, meta in obeams:
+        oracle.propagate(omodel, st, meta, w.dt, w.nsteps)
+        ref += oracle.gauss_sum(oracle.records(st, meta, mesh.weight(w.k)), w.k, w.rw, X)
+    assert rel_l2(u.reshape(-1, 3), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_solve_on_lattices_equals_solve_on_points(fga, prec):
+    """Receivers and snapshot given as lattices give the same seismograms and snapshot as the same
+    points given one by one."""
+    import torch
+    w = _small_smooth(grid=True)
+    model, desc, keep = gpu_setup(w, prec)
+    rx = torch.as_tensor(w.receivers, device="cuda")
+    sn = torch.as_tensor(w.snapshot, device="cuda")
+    s1, n1 = fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, sn, rw=w.rw)
+    s2, n2 = fga.solve(model, desc, w.dt, w.nsteps, w.times, rw=w.rw, rx_axes=w.rx_axes, snap_axes=w.snap_axes)
+    torch.cuda.synchronize()
+    assert rel_l2(s2.reshape(s1.shape).cpu().numpy(), s1.cpu().numpy()) <= TOL[prec]
+    assert rel_l2(n2.reshape(n1.shape).cpu().numpy(), n1.cpu().numpy()) <= TOL[prec]
+
+
 @pytest.mark.parametrize("n,nc", [(0, (3, 3, 3)), (1, (2, 2, 2)), (5000, (4, 5, 6)), (20011, (9, 7, 11)),
                                   (70001, (40, 40, 40))])
 def test_binning_bit_exact(fga, oracle, n, nc):
