@@ -197,10 +197,13 @@ fga_status fga_bin(const float *Q, int64_t n, const float origin[3], float inv_h
                    int32_t *keys, int32_t *perm, int32_t *cell_start, fga_stream_t s);
 
 /* Profiling of the library's own kernels (no counterpart in the paper; used to measure it).
- * mode 0: off (default); 1: launch and work counters; 2: counters plus device time of every kernel
- * launch, taken with CUDA events recorded on the launching stream around it.  Categories of
+ * mode 0: off (default); 1: launch and work counters, including the in-window pair count (which
+ * adds a few instructions to the Gaussian-sum kernels); 2: launch counters plus the device time of
+ * every kernel launch, taken with CUDA events recorded on the launching stream around it (no pair
+ * count); 3: both.  Categories of
  * count[] / ms[]: 0 decomposition, 1 RK4 propagation, 2 binning (keys, sort, permutation),
- * 3 records, 4 Gaussian sum, 5 Gaussian-sum reduction, 6 other.  pairs_in_window counts the
+ * 3 records, 4 Gaussian sums at sample times inside fga_solve, 5 Gaussian-sum reductions,
+ * 6 Gaussian sums at the current beam state (snapshots, fga_reconstruct, fga_reconstruct_lattice).  pairs_in_window counts the
  * (beam, point) pairs inside the truncation window that the Gaussian sum evaluated; pairs_tested the
  * pairs it examined; beam_steps the beam RK4 steps advanced.  fga_profile_read waits for the timed
  * launches to finish; reset != 0 zeroes the counters afterwards.  Process-wide state, meant to be

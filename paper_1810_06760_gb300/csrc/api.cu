@@ -140,7 +140,7 @@ ProfScope::ProfScope(int cat, cudaStream_t st) : idx(-1), s(st) {
 ProfScope::~ProfScope() {
     if (idx >= 0) cudaEventRecord(g_prof.ev[idx + 1], s);
 }
-bool prof_counting() { return g_prof.mode > 0; }
+bool prof_counting() { return g_prof.mode == 1 || g_prof.mode == 3; }
 void prof_add_beam_steps(int64_t n) {
     if (g_prof.mode) g_prof.beam_steps += n;
 }
@@ -321,7 +321,7 @@ static fga_status reconstruct_now(const fga_beams *b, const double *x_dev, const
     const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
     FGA_TRY(ws.rec.ensure(rb * REC * (size_t)std::max<int64_t>(plan.n_rec, 1)));
     FGA_TRY(launch_records_from_state(b, perm, plan.n_in, plan.rec_off, ws.rec.p, s));
-    return run_sum(ws, plan, b->precision, ws.rec.p, x_dev, b->k, rw, u_out, s);
+    return run_sum(ws, plan, b->precision, ws.rec.p, x_dev, b->k, rw, u_out, s, P_GATHER_STATE);
 }
 
 static fga_status check_lattice(const fga_lattice *L, const char *who) {
@@ -368,7 +368,7 @@ static fga_status reconstruct_lattice_now(const fga_beams *b, const fga_lattice 
     const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
     FGA_TRY(ws.rec.ensure(rb * REC * (size_t)std::max<int64_t>(plan.n_rec, 1)));
     FGA_TRY(launch_records_from_state(b, perm, plan.n_in, plan.rec_off, ws.rec.p, s));
-    return run_lattice(ws, plan, b->precision, ws.rec.p, b->k, rw, u_out, s);
+    return run_lattice(ws, plan, b->precision, ws.rec.p, b->k, rw, u_out, s, P_GATHER_STATE);
 }
 
 fga_status fga_reconstruct_lattice(const fga_beams *b, const fga_lattice *lat, double rw, void *u_out,
@@ -590,7 +590,7 @@ fga_status fga_beams_destroy(fga_beams *b) {
 }
 
 fga_status fga_profile_enable(int mode) {
-    FGA_CHECK(mode >= 0 && mode <= 2, "fga_profile_enable: mode must be 0, 1 or 2");
+    FGA_CHECK(mode >= 0 && mode <= 3, "fga_profile_enable: mode must be 0, 1, 2 or 3");
     g_prof.mode = mode;
     return FGA_OK;
 }

@@ -76,7 +76,9 @@ fga_status cuda_fail(cudaError_t e, const char *what);
     } while (0)
 
 // profiling: launch counters and CUDA-event device times per kernel category -------------------
-enum ProfCat { P_DECOMP = 0, P_PROP = 1, P_BIN = 2, P_REC = 3, P_GATHER = 4, P_REDUCE = 5, P_OTHER = 6, P_NCAT = 8 };
+// P_GATHER: Gaussian sums at sample times inside a solve; P_GATHER_STATE: sums at the current state
+// (snapshots, fga_reconstruct*)
+enum ProfCat { P_DECOMP = 0, P_PROP = 1, P_BIN = 2, P_REC = 3, P_GATHER = 4, P_REDUCE = 5, P_GATHER_STATE = 6, P_NCAT = 8 };
 struct ProfScope {  // wraps one kernel launch on stream s
     ProfScope(int cat, cudaStream_t s);
     ~ProfScope();

@@ -549,14 +549,14 @@ fga_status build_sum_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_s
 const int32_t *plan_host_cell_start(const Workspace &ws) { return ws.h_cell_start.as<int32_t>(); }
 
 fga_status run_sum(Workspace &ws, const SumPlan &plan, int precision, const void *rec_sorted, const double *pts_dev,
-                   double k, double rw, void *u_out, cudaStream_t s) {
+                   double k, double rw, void *u_out, cudaStream_t s, int cat) {
     if (plan.ntiles == 0) return FGA_OK;
     const size_t rb = precision == FGA_PREC_FP64 ? 8 : 4;
     FGA_TRY(ws.partial.ensure(rb * 32 * 6 * (size_t)std::max(plan.nitems, 1)));
     const int cnt = prof_counting() ? 1 : 0;
     prof_add_pairs_tested(plan.pairs_tested);
     if (plan.nitems > 0) {
-        ProfScope ps(P_GATHER, s);
+        ProfScope ps(cat, s);
         if (rb == 8)
             gather_kernel<double><<<plan.nitems, 128, 0, s>>>((const double *)rec_sorted, pts_dev, plan.tile_pts,
                                                               plan.items, k, rw * rw, ws.partial.as<double>(), cnt);

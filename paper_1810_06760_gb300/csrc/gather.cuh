@@ -34,7 +34,7 @@ struct LatticePlan {
 fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, const fga_lattice &L,
                               cudaStream_t s, LatticePlan &plan);
 fga_status run_lattice(Workspace &ws, const LatticePlan &plan, int precision, const void *rec, double k, double rw,
-                       void *u, cudaStream_t s);
+                       void *u, cudaStream_t s, int cat = P_GATHER);
 int64_t read_lattice_pair_counter(bool reset);
 
 fga_status sort_keys_to_perm(Workspace &ws, int32_t *keys, int64_t n, int nbuckets, int32_t **perm_out,
@@ -42,7 +42,7 @@ fga_status sort_keys_to_perm(Workspace &ws, int32_t *keys, int64_t n, int nbucke
 fga_status build_sum_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, int nclasses,
                           const double *pts_host, int64_t npts, cudaStream_t s, SumPlan &plan);
 fga_status run_sum(Workspace &ws, const SumPlan &plan, int precision, const void *rec_sorted, const double *pts_dev,
-                   double k, double rw, void *u_out, cudaStream_t s);
+                   double k, double rw, void *u_out, cudaStream_t s, int cat = P_GATHER);
 // bucket starts copied to the host by build_sum_plan (valid after it returns)
 const int32_t *plan_host_cell_start(const Workspace &ws);
 

@@ -31,38 +31,130 @@ int64_t read_lattice_pair_counter(bool reset) {
     return (int64_t)v;
 }
 
-template <typename R, int T0, int T1, int T2, int NBB>
+// Shared-memory layout of one batch of at most NB kept beams (runtime tile T0 x T1 x T2):
+//   ae0[b][i]  = (A_c E0(x_i) for c = 0..2 as re/im, (x_i - Q_0)^2, 0)              8 reals
+//   ed12[b][jl] = (E1(x_j) E2(x_l) re/im, (x_j - Q_1)^2 + (x_l - Q_2)^2, 0)         4 reals
+// so that a point reads its beam terms with three 16-byte (FP32) loads.
+struct LatSmem {
+    int NB, T0, T1, T2, T12, TP, B0, B1, B2, nblk0, nblk1, nblk2;
+    size_t rec, mask, ae0, ed12, e1, e2, x, bytes;
+    template <typename R> __host__ __device__ void init(int nb, int t0, int t1, int t2) {
+        NB = nb;
+        T0 = t0;
+        T1 = t1;
+        T2 = t2;
+        T12 = t1 * t2;
+        TP = t0 * T12;
+        // warp blocks of 32 points, compact in the lattice: 4 x 8 x 1 on planes, 2 x 4 x 4 in volumes
+        if (T2 == 1) {
+            B0 = 4;
+            B1 = 8;
+            B2 = 1;
+        } else {
+            B0 = 2;
+            B1 = 4;
+            B2 = 4;
+        }
+        nblk0 = (T0 + B0 - 1) / B0;
+        nblk1 = (T1 + B1 - 1) / B1;
+        nblk2 = (T2 + B2 - 1) / B2;
+        size_t o = 0;
+        auto take = [&](size_t n) {
+            const size_t r = o;
+            o += (n * sizeof(R) + 15) / 16 * 16;
+            return r;
+        };
+        rec = take((size_t)NB * REC);
+        mask = take((size_t)NB * (sizeof(unsigned) + sizeof(R) - 1) / sizeof(R));
+        ae0 = take((size_t)NB * T0 * 8);
+        ed12 = take((size_t)NB * T12 * 4);
+        e1 = take((size_t)NB * T1 * 4);
+        e2 = take((size_t)NB * T2 * 4);
+        x = take((size_t)(T0 + T1 + T2));
+        bytes = o;
+    }
+    __host__ __device__ int nblocks() const { return nblk0 * nblk1 * nblk2; }
+};
+
+template <typename R> struct V4;
+template <> struct V4<float> {
+    using T = float4;
+};
+template <> struct V4<double> {
+    using T = double4;
+};
+
+// One CTA = one (tile, chunk of candidate beams).  Per batch: the first NB threads hold candidate
+// records (loaded one batch ahead) and keep those within rw of the tile's box; warps form the kept
+// beams' 1-D factors and which warp blocks each beam reaches; then every warp adds the batch to its
+// blocks of 32 points, skipping (warp-uniformly) blocks the beam cannot reach.
+template <typename R, int PTS, bool COUNT>
 __global__ void __launch_bounds__(256) lattice_gather_kernel(const R *__restrict__ rec, const double *__restrict__ ax0,
                                                             const double *__restrict__ ax1, const double *__restrict__ ax2,
-                                                            int n0, int n1, int n2, int nt1, int nt2,
+                                                            int n0, int n1, int n2, LatSmem L, int nt1, int nt2,
                                                             const int4 *__restrict__ items, R k, R rw2,
-                                                            R *__restrict__ partial, int count_pairs) {
-    constexpr int T12 = T1 * T2, TP = T0 * T12, PTS = (TP + 255) / 256;
-    __shared__ R s_ae0[NBB][T0][6];  // A_c * E0(x_i)
-    __shared__ R s_d0[NBB][T0];      // (x_i - Q_0)^2
-    __shared__ R s_e12[NBB][T12][2]; // E1(x_j) E2(x_l)
-    __shared__ R s_d12[NBB][T12];    // (x_j - Q_1)^2 + (x_l - Q_2)^2
-    __shared__ R s_e1[NBB][T1][2], s_e2[NBB][T2][2], s_d1[NBB][T1], s_d2[NBB][T2];
-    __shared__ R s_rec[NBB][REC];
-    __shared__ R s_x[T0 + T1 + T2];
-    __shared__ int s_nb;
+                                                            R *__restrict__ partial) {
+    using R4 = typename V4<R>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    R *s_rec = reinterpret_cast<R *>(smem + L.rec);
+    R4 *s_ae0 = reinterpret_cast<R4 *>(smem + L.ae0);    // [NB][T0][2]
+    R4 *s_ed12 = reinterpret_cast<R4 *>(smem + L.ed12);  // [NB][T12]
+    R4 *s_e1 = reinterpret_cast<R4 *>(smem + L.e1);       // [NB][T1]: re, im, d^2, -
+    R4 *s_e2 = reinterpret_cast<R4 *>(smem + L.e2);       // [NB][T2]
+    R *s_x = reinterpret_cast<R *>(smem + L.x);
+    unsigned *s_mask = reinterpret_cast<unsigned *>(smem + L.mask);  // [NB]: warp blocks within rw
+    __shared__ int s_wcnt[2];
     __shared__ unsigned s_pairs;
+    const int T0 = L.T0, T1 = L.T1, T2 = L.T2, T12 = L.T12, NB = L.NB, TA = T0 + T1 + T2;
 
     const int4 it = items[blockIdx.x];
     const int t = it.x;
     const int tt0 = t / (nt1 * nt2), tt1 = (t / nt2) % nt1, tt2 = t % nt2;
     const int i0 = tt0 * T0, j0 = tt1 * T1, l0 = tt2 * T2;
     const int e0 = min(T0, n0 - i0), e1 = min(T1, n1 - j0), e2 = min(T2, n2 - l0);
-    const int tid = threadIdx.x;
-    // tile coordinates (ragged tiles repeat their last coordinate; those points are not written)
-    if (tid < T0) s_x[tid] = (R)ax0[i0 + min(tid, e0 - 1)];
-    else if (tid < T0 + T1) s_x[tid] = (R)ax1[j0 + min(tid - T0, e1 - 1)];
-    else if (tid < T0 + T1 + T2) s_x[tid] = (R)ax2[l0 + min(tid - T0 - T1, e2 - 1)];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int a = tid; a < TA; a += 256) {
+        R v;
+        if (a < T0) v = (R)ax0[i0 + min(a, e0 - 1)];
+        else if (a < T0 + T1) v = (R)ax1[j0 + min(a - T0, e1 - 1)];
+        else v = (R)ax2[l0 + min(a - T0 - T1, e2 - 1)];
+        s_x[a] = v;
+    }
     if (tid == 0) s_pairs = 0;
     __syncthreads();
     const R lo0 = s_x[0], hi0 = s_x[T0 - 1], lo1 = s_x[T0], hi1 = s_x[T0 + T1 - 1];
-    const R lo2 = s_x[T0 + T1], hi2 = s_x[T0 + T1 + T2 - 1];
+    const R lo2 = s_x[T0 + T1], hi2 = s_x[TA - 1];
 
+    // this thread's points: lane (di, dj, dl) of warp blocks warp + 8 q; offsets into the factors
+    int o12[PTS], o0[PTS];
+    bool pin[PTS];
+    unsigned pval[PTS];
+    {
+        const int dl = lane % L.B2, dj = (lane / L.B2) % L.B1, di = lane / (L.B2 * L.B1);
+#pragma unroll
+        for (int q = 0; q < PTS; q++) {
+            const int blk = warp + 8 * q;
+            const int b2 = blk % L.nblk2, b1 = (blk / L.nblk2) % L.nblk1, b0 = blk / (L.nblk2 * L.nblk1);
+            const int i = b0 * L.B0 + di, j = b1 * L.B1 + dj, l = b2 * L.B2 + dl;
+            pin[q] = blk < L.nblocks() && i < T0 && j < T1 && l < T2;
+            o12[q] = pin[q] ? j * T2 + l : 0;
+            o0[q] = pin[q] ? 2 * i : 0;
+            pval[q] = (pin[q] && i < e0 && j < e1 && l < e2) ? 1u : 0u;
+        }
+    }
+    // warp-block boxes of this lane's block (for the reach masks)
+    const int nblk = L.nblocks();
+    R blo[3] = {R(0), R(0), R(0)}, bhi[3] = {R(0), R(0), R(0)};
+    if (lane < nblk) {
+        const int b2 = lane % L.nblk2, b1 = (lane / L.nblk2) % L.nblk1, b0 = lane / (L.nblk2 * L.nblk1);
+        const int ia = b0 * L.B0, ja = b1 * L.B1, la = b2 * L.B2;
+        blo[0] = s_x[ia];
+        bhi[0] = s_x[min(ia + L.B0, T0) - 1];
+        blo[1] = s_x[T0 + ja];
+        bhi[1] = s_x[T0 + min(ja + L.B1, T1) - 1];
+        blo[2] = s_x[T0 + T1 + la];
+        bhi[2] = s_x[T0 + T1 + min(la + L.B2, T2) - 1];
+    }
     R acc[PTS][6];
 #pragma unroll
     for (int q = 0; q < PTS; q++)
@@ -71,86 +163,106 @@ __global__ void __launch_bounds__(256) lattice_gather_kernel(const R *__restrict
     unsigned mine = 0;
     const R hk = R(-0.5) * k;
 
-    for (int64_t base = it.y; base < it.z; base += NBB) {
-        // 1. load up to NBB candidate records; keep those within rw of the tile's box
-        if (tid < 32) {
-            const int64_t b = base + tid;
-            bool keep = false;
-            R r[REC];
-            if (tid < NBB && b < it.z) {
+    R r[REC];
+    auto load = [&](int64_t bbase) {
+        const int64_t b = bbase + tid;
+        if (tid < NB && b < it.z) {
 #pragma unroll
-                for (int q = 0; q < REC; q++) r[q] = rec[b * REC + q];
-                const R g0 = fmax(fmax(lo0 - r[0], r[0] - hi0), R(0));
-                const R g1 = fmax(fmax(lo1 - r[1], r[1] - hi1), R(0));
-                const R g2 = fmax(fmax(lo2 - r[2], r[2] - hi2), R(0));
-                keep = g0 * g0 + g1 * g1 + g2 * g2 <= rw2;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int slot = __popc(m & ((1u << tid) - 1u));
-#pragma unroll
-                for (int q = 0; q < REC; q++) s_rec[slot][q] = r[q];
-            }
-            if (tid == 0) s_nb = __popc(m);
+            for (int q = 0; q < REC; q++) r[q] = rec[b * REC + q];
+        }
+    };
+    load(it.y);
+    for (int64_t base = it.y; base < it.z; base += NB) {
+        // 1. candidates -> kept beams (order preserved)
+        bool keep = false;
+        if (tid < NB && base + tid < it.z) {
+            const R g0 = fmax(fmax(lo0 - r[0], r[0] - hi0), R(0));
+            const R g1 = fmax(fmax(lo1 - r[1], r[1] - hi1), R(0));
+            const R g2 = fmax(fmax(lo2 - r[2], r[2] - hi2), R(0));
+            keep = g0 * g0 + g1 * g1 + g2 * g2 <= rw2;
+        }
+        unsigned m = 0;
+        if (warp < 2) {
+            m = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) s_wcnt[warp] = __popc(m);
         }
         __syncthreads();
-        const int nb = s_nb;
-        if (nb == 0) {
-            __syncthreads();
-            continue;
-        }
-        // 2. per-axis factors of the kept beams
-        for (int e = tid; e < nb * (T0 + T1 + T2); e += 256) {
-            const int b = e / (T0 + T1 + T2), a = e % (T0 + T1 + T2);
-            const int d = a < T0 ? 0 : (a < T0 + T1 ? 1 : 2);
-            const R dx = s_x[a] - s_rec[b][d];
-            R er, ei;
-            gauss_phase_exp<R>(k * s_rec[b][3 + d] * dx, hk * dx * dx, &er, &ei);
-            if (d == 0) {
-                s_d0[b][a] = dx * dx;
+        const int nb = s_wcnt[0] + (NB > 32 ? s_wcnt[1] : 0);
+        if (keep) {
+            const int slot = (warp ? s_wcnt[0] : 0) + __popc(m & ((1u << lane) - 1u));
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    const R ar = s_rec[b][6 + 2 * c], ai = s_rec[b][7 + 2 * c];
-                    s_ae0[b][a][2 * c] = ar * er - ai * ei;
-                    s_ae0[b][a][2 * c + 1] = ar * ei + ai * er;
+            for (int q = 0; q < REC; q++) s_rec[slot * REC + q] = r[q];
+        }
+        __syncthreads();
+        load(base + NB);  // next batch, in flight during the work below
+        if (nb == 0) continue;
+        // 2a. reach masks (a warp per kept beam, lane = warp block)
+        for (int b = warp; b < nb; b += 8) {
+            const R *rb = s_rec + b * REC;
+            const R g0 = fmax(fmax(blo[0] - rb[0], rb[0] - bhi[0]), R(0));
+            const R g1 = fmax(fmax(blo[1] - rb[1], rb[1] - bhi[1]), R(0));
+            const R g2 = fmax(fmax(blo[2] - rb[2], rb[2] - bhi[2]), R(0));
+            const unsigned bm = __ballot_sync(0xffffffffu, lane < nblk && g0 * g0 + g1 * g1 + g2 * g2 <= rw2);
+            if (lane == 0) s_mask[b] = bm;
+        }
+        // 2b. 1-D factors: every (beam, tile coordinate) pair is one task, spread over all threads
+        // (b = floor((e + 1/2) / TA) is exact in FP32 for these small integers)
+        {
+            const float inv_ta = 1.0f / (float)TA;
+            for (int e = tid; e < nb * TA; e += 256) {
+                const int b = (int)(((float)e + 0.5f) * inv_ta), a = e - b * TA;
+                const R *rb = s_rec + b * REC;
+                const int d = a < T0 ? 0 : (a < T0 + T1 ? 1 : 2);
+                const R dx = s_x[a] - rb[d];
+                R er, ei;
+                gauss_phase_exp<R>(k * rb[3 + d] * dx, hk * dx * dx, &er, &ei);
+                if (d == 0) {
+                    R o[6];
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const R ar = rb[6 + 2 * c], ai = rb[7 + 2 * c];
+                        o[2 * c] = ar * er - ai * ei;
+                        o[2 * c + 1] = ar * ei + ai * er;
+                    }
+                    R4 *dst = s_ae0 + (b * T0 + a) * 2;
+                    dst[0] = R4{o[0], o[1], o[2], o[3]};
+                    dst[1] = R4{o[4], o[5], dx * dx, R(0)};
+                } else if (d == 1) {
+                    s_e1[b * T1 + (a - T0)] = R4{er, ei, dx * dx, R(0)};
+                } else {
+                    s_e2[b * T2 + (a - T0 - T1)] = R4{er, ei, dx * dx, R(0)};
                 }
-            } else if (d == 1) {
-                s_d1[b][a - T0] = dx * dx;
-                s_e1[b][a - T0][0] = er;
-                s_e1[b][a - T0][1] = ei;
-            } else {
-                s_d2[b][a - T0 - T1] = dx * dx;
-                s_e2[b][a - T0 - T1][0] = er;
-                s_e2[b][a - T0 - T1][1] = ei;
             }
         }
         __syncthreads();
-        for (int e = tid; e < nb * T12; e += 256) {
-            const int b = e / T12, jl = e % T12, j = jl / T2, l = jl % T2;
-            const R ar = s_e1[b][j][0], ai = s_e1[b][j][1], br = s_e2[b][l][0], bi = s_e2[b][l][1];
-            s_e12[b][jl][0] = ar * br - ai * bi;
-            s_e12[b][jl][1] = ar * bi + ai * br;
-            s_d12[b][jl] = s_d1[b][j] + s_d2[b][l];
+        {
+            const float inv_t12 = 1.0f / (float)T12, inv_t2 = 1.0f / (float)T2;
+            for (int e = tid; e < nb * T12; e += 256) {
+                const int b = (int)(((float)e + 0.5f) * inv_t12), jl = e - b * T12;
+                const int j = (int)(((float)jl + 0.5f) * inv_t2), l = jl - j * T2;
+                const R4 u = s_e1[b * T1 + j], v = s_e2[b * T2 + l];
+                s_ed12[e] = R4{u.x * v.x - u.y * v.y, u.x * v.y + u.y * v.x, u.z + v.z, R(0)};
+            }
         }
         __syncthreads();
-        // 3. every thread adds the kept beams to its points
+        // 3. the batch's contribution to this thread's points
+        for (int b = 0; b < nb; b++) {
+            const unsigned bm = s_mask[b];
+            const R4 *ed = s_ed12 + b * T12;
+            const R4 *ae = s_ae0 + b * 2 * T0;
 #pragma unroll
-        for (int q = 0; q < PTS; q++) {
-            const int p = tid + 256 * q;
-            if (p < TP) {
-                const int i = p / T12, jl = p % T12;
-                const unsigned valid = (i < e0 && jl / T2 < e1 && jl % T2 < e2) ? 1u : 0u;
-                for (int b = 0; b < nb; b++) {
-                    const R d2 = s_d0[b][i] + s_d12[b][jl];
-                    if (d2 <= rw2) {
-                        mine += valid;
-                        const R er = s_e12[b][jl][0], ei = s_e12[b][jl][1];
-#pragma unroll
-                        for (int c = 0; c < 3; c++) {
-                            const R ar = s_ae0[b][i][2 * c], ai = s_ae0[b][i][2 * c + 1];
-                            acc[q][2 * c] += ar * er - ai * ei;
-                            acc[q][2 * c + 1] += ar * ei + ai * er;
-                        }
+            for (int q = 0; q < PTS; q++) {
+                if ((bm >> (warp + 8 * q)) & 1u) {
+                    const R4 e = ed[o12[q]];
+                    const R4 a0 = ae[o0[q]], a1 = ae[o0[q] + 1];
+                    if (pin[q] && a1.z + e.z <= rw2) {
+                        if (COUNT) mine += pval[q];
+                        acc[q][0] += a0.x * e.x - a0.y * e.y;
+                        acc[q][1] += a0.x * e.y + a0.y * e.x;
+                        acc[q][2] += a0.z * e.x - a0.w * e.y;
+                        acc[q][3] += a0.z * e.y + a0.w * e.x;
+                        acc[q][4] += a1.x * e.x - a1.y * e.y;
+                        acc[q][5] += a1.x * e.y + a1.y * e.x;
                     }
                 }
             }
@@ -159,46 +271,61 @@ __global__ void __launch_bounds__(256) lattice_gather_kernel(const R *__restrict
     }
 #pragma unroll
     for (int q = 0; q < PTS; q++) {
-        const int p = tid + 256 * q;
-        if (p < TP) {
-            R *dst = partial + ((int64_t)blockIdx.x * TP + p) * 6;
+        if (pin[q]) {
+            R *dst = partial + ((int64_t)blockIdx.x * L.TP + (o0[q] / 2) * T12 + o12[q]) * 6;
 #pragma unroll
             for (int c = 0; c < 6; c++) dst[c] = acc[q][c];
         }
     }
-    if (count_pairs) {
+    if (COUNT) {
         atomicAdd(&s_pairs, mine);
         __syncthreads();
         if (tid == 0) atomicAdd(&g_lattice_pairs, (unsigned long long)s_pairs);
     }
 }
 
-template <typename R, int T0, int T1, int T2>
+// u at every lattice point: a warp per point, lanes striding over the tile's items, then a fixed
+// shuffle tree (deterministic for a given work split)
+template <typename R>
 __global__ void lattice_reduce_kernel(const R *__restrict__ partial, const int32_t *__restrict__ item_start, int n0,
-                                      int n1, int n2, int nt1, int nt2, R *__restrict__ u) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                      int n1, int n2, int T0, int T1, int T2, int nt1, int nt2, R *__restrict__ u) {
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)n0 * n1 * n2;
     if (g >= total) return;
     const int l = (int)(g % n2), j = (int)((g / n2) % n1), i = (int)(g / ((int64_t)n1 * n2));
     const int t = ((i / T0) * nt1 + j / T1) * nt2 + l / T2;
     const int p = ((i % T0) * T1 + j % T1) * T2 + l % T2;
-    constexpr int TP = T0 * T1 * T2;
+    const int TP = T0 * T1 * T2;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int it = item_start[t]; it < item_start[t + 1]; it++)
+    for (int it = item_start[t] + lane; it < item_start[t + 1]; it += 32)
 #pragma unroll
         for (int c = 0; c < 6; c++) acc[c] += (double)partial[((int64_t)it * TP + p) * 6 + c];
 #pragma unroll
-    for (int c = 0; c < 6; c++) u[g * 6 + c] = (R)acc[c];
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 6; c++) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane < 6) {
+        double v = acc[0];
+#pragma unroll
+        for (int c = 1; c < 6; c++)
+            if (lane == c) v = acc[c];
+        u[g * 6 + lane] = (R)v;
+    }
 }
 
-// tile shapes: planes (one point along axis 2) use 16 x 16 x 1, volumes 8 x 8 x 8
+// tile shape: at most 1024 points and 64 per axis; axis 2 first (up to 16), then 1, then 0
 static void tile_shape(const fga_lattice &L, int T[3]) {
-    if (L.n[2] == 1) {
-        T[0] = 16;
-        T[1] = 16;
-        T[2] = 1;
-    } else {
-        T[0] = T[1] = T[2] = 8;
+    T[2] = std::min(L.n[2], 16);
+    T[1] = std::min(L.n[1], std::max(1, std::min(64, 1024 / (T[2] * std::min(L.n[0], 8)))));
+    T[0] = std::min(L.n[0], std::max(1, std::min(64, 1024 / (T[1] * T[2]))));
+    // at most 32 warp blocks (4 per warp of a 256-thread CTA)
+    const int B0 = T[2] == 1 ? 4 : 2, B1 = T[2] == 1 ? 8 : 4, B2 = T[2] == 1 ? 1 : 4;
+    auto nblk = [&]() { return ((T[0] + B0 - 1) / B0) * ((T[1] + B1 - 1) / B1) * ((T[2] + B2 - 1) / B2); };
+    while (nblk() > 32) {
+        if (T[0] > B0) T[0] -= B0;
+        else if (T[1] > B1) T[1] -= B1;
+        else T[2] -= B2;
     }
 }
 
@@ -257,8 +384,8 @@ fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *ce
                 }
         }
     }
-    int64_t B = std::max<int64_t>(256, (total + 4095) / 4096);
-    B = (B + 31) / 32 * 32;
+    int64_t B = std::max<int64_t>(256, (total + 2047) / 2048);
+    B = (B + 63) / 64 * 64;
     std::vector<int32_t> item_start((size_t)ntiles + 1, 0);
     std::vector<int4> items;
     size_t ri = 0;
@@ -300,37 +427,64 @@ fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *ce
     return FGA_OK;
 }
 
-template <typename R, int T0, int T1, int T2>
+template <typename R>
 static fga_status run_lattice_t(Workspace &ws, const LatticePlan &plan, const void *rec, double k, double rw, void *u,
-                                cudaStream_t s) {
-    constexpr int TP = T0 * T1 * T2;
-    constexpr int NBB = sizeof(R) == 4 ? 32 : 16;
+                                cudaStream_t s, int cat) {
+    const int TP = plan.T[0] * plan.T[1] * plan.T[2];
+    // batch capacity: up to 64 beams, within ~72 KB of shared memory
+    LatSmem L;
+    int nb = 64;
+    for (; nb > 8; nb -= 8) {
+        L.init<R>(nb, plan.T[0], plan.T[1], plan.T[2]);
+        if (L.bytes <= 72 * 1024) break;
+    }
+    L.init<R>(nb, plan.T[0], plan.T[1], plan.T[2]);
     FGA_TRY(ws.partial.ensure(sizeof(R) * 6 * (size_t)TP * (size_t)std::max(plan.nitems, 1)));
     const int cnt = prof_counting() ? 1 : 0;
     prof_add_pairs_tested(plan.pairs_tested);
     if (plan.nitems > 0) {
-        ProfScope ps(P_GATHER, s);
-        lattice_gather_kernel<R, T0, T1, T2, NBB><<<plan.nitems, 256, 0, s>>>(
-            (const R *)rec, plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2], plan.nt[1], plan.nt[2],
-            plan.items, (R)k, (R)(rw * rw), ws.partial.as<R>(), cnt);
+        const int pts = (L.nblocks() + 7) / 8;  // warp blocks per warp
+        if (pts > 4) {
+            set_error("lattice tile has more than 32 warp blocks");
+            return FGA_ERR_UNSUPPORTED;
+        }
+        ProfScope ps(cat, s);
+#define FGA_LAT2(PTS, CNT)                                                                                          \
+    do {                                                                                                            \
+        FGA_CUDA(cudaFuncSetAttribute(lattice_gather_kernel<R, PTS, CNT>,                                           \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes));                 \
+        lattice_gather_kernel<R, PTS, CNT><<<plan.nitems, 256, L.bytes, s>>>(                                      \
+            (const R *)rec, plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2], L, plan.nt[1],    \
+            plan.nt[2], plan.items, (R)k, (R)(rw * rw), ws.partial.as<R>());                                        \
+    } while (0)
+#define FGA_LAT(PTS)            \
+    do {                        \
+        if (cnt)                \
+            FGA_LAT2(PTS, true);  \
+        else                    \
+            FGA_LAT2(PTS, false); \
+    } while (0)
+        if (pts == 1) FGA_LAT(1);
+        else if (pts == 2) FGA_LAT(2);
+        else if (pts == 3) FGA_LAT(3);
+        else FGA_LAT(4);
+#undef FGA_LAT
+#undef FGA_LAT2
         FGA_CUDA(cudaGetLastError());
     }
     const int64_t total = (int64_t)plan.n[0] * plan.n[1] * plan.n[2];
     ProfScope ps(P_REDUCE, s);
-    lattice_reduce_kernel<R, T0, T1, T2><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        ws.partial.as<R>(), plan.item_start, plan.n[0], plan.n[1], plan.n[2], plan.nt[1], plan.nt[2], (R *)u);
+    lattice_reduce_kernel<R><<<(unsigned)((total * 32 + 255) / 256), 256, 0, s>>>(
+        ws.partial.as<R>(), plan.item_start, plan.n[0], plan.n[1], plan.n[2], plan.T[0], plan.T[1], plan.T[2],
+        plan.nt[1], plan.nt[2], (R *)u);
     FGA_CUDA(cudaGetLastError());
     return FGA_OK;
 }
 
 fga_status run_lattice(Workspace &ws, const LatticePlan &plan, int precision, const void *rec, double k, double rw,
-                       void *u, cudaStream_t s) {
-    const bool plane = plan.T[2] == 1;
-    if (precision == FGA_PREC_FP64)
-        return plane ? run_lattice_t<double, 16, 16, 1>(ws, plan, rec, k, rw, u, s)
-                     : run_lattice_t<double, 8, 8, 8>(ws, plan, rec, k, rw, u, s);
-    return plane ? run_lattice_t<float, 16, 16, 1>(ws, plan, rec, k, rw, u, s)
-                 : run_lattice_t<float, 8, 8, 8>(ws, plan, rec, k, rw, u, s);
+                       void *u, cudaStream_t s, int cat) {
+    if (precision == FGA_PREC_FP64) return run_lattice_t<double>(ws, plan, rec, k, rw, u, s, cat);
+    return run_lattice_t<float>(ws, plan, rec, k, rw, u, s, cat);
 }
 
 }  // namespace fga

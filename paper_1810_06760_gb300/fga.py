@@ -23,7 +23,8 @@ MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
 EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_propagate", "fga_reconstruct",
             "fga_reconstruct_lattice", "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export", "fga_beams_destroy", "fga_bin",
             "fga_profile_enable", "fga_profile_read", "fga_last_error", "fga_version"]
-PROFILE_CATEGORIES = ["decompose", "propagate", "binning", "records", "gauss_sum", "gauss_reduce", "other", "unused"]
+PROFILE_CATEGORIES = ["decompose", "propagate", "binning", "records", "gauss_sum", "gauss_reduce", "gauss_sum_state",
+                      "unused"]
 
 
 class FGAError(RuntimeError):
@@ -326,7 +327,7 @@ def solve(model: Model, desc: InitDesc, dt: float, nsteps: int, times, rx=None, 
 
 
 def profile_enable(mode: int) -> None:
-    """0 off, 1 counters, 2 counters + per-kernel CUDA-event device times."""
+    """0 off, 1 counters incl. in-window pairs, 2 counters + per-kernel CUDA-event device times, 3 both."""
     _check(lib().fga_profile_enable(int(mode)))
 
 

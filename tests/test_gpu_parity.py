@@ -113,7 +113,7 @@ def test_solve_seismograms_and_snapshot(fga, oracle, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 0])
-@pytest.mark.parametrize("shape", [(19, 21, 1), (9, 17, 10)])
+@pytest.mark.parametrize("shape", [(19, 21, 1), (70, 9, 1), (9, 17, 10)])
 def test_reconstruct_on_lattice(fga, oracle, prec, shape):
     """Lattice sum (per-axis factorised Gaussians) equals the oracle's brute-force sum at the same
     points; shapes give ragged tiles in every axis for both tile shapes (16x16x1 and 8x8x8)."""
