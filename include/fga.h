@@ -99,6 +99,13 @@ typedef struct {
     double p0[3], dp[3];
     unsigned class_mask;
     int precision;
+    /* layered media only (0 selects the default): a beam is dropped at its (max_interfaces+1)-th
+     * interface (default 4); children whose amplitude is below child_rel_min of the incident one
+     * are not created (default 1e-6); room is reserved for growth x the initial beam count
+     * (default 4; children beyond it are dropped and counted). */
+    int max_interfaces;
+    double child_rel_min;
+    double growth;
 } fga_init_desc;
 
 /* Steps 1 of Fig. fig:FGA_alg: the wave-packet transform F(q,p) = sum_y f(y) exp(-i k p.(y-q)
@@ -187,6 +194,36 @@ fga_status fga_beams_count(const fga_beams *b, int64_t *n_by_class);
 fga_status fga_beams_export(const fga_beams *b, double *state_host, int32_t *meta_host);
 fga_status fga_beams_destroy(fga_beams *b);
 
+/* All live beams in storage order (the form for layered media, where beams split at interfaces).
+ * Writes up to cap beams: HOST state [n][48] (as fga_beams_export), meta int32 [n] (bits 0-1 class,
+ * 2 S frame e1, 4-7 layer, 8-11 interfaces crossed, 13-14 class of the initial beam of the lineage),
+ * mesh_id int64 [n] (the mesh point the beam descends from; with bits 13-14 of meta it names the
+ * initial beam), path int64 [n] (lineage: 0 for an initial beam, parent*4 + child + 1 for a child,
+ * child 0 reflected P, 1 reflected S, 2 transmitted P, 3 transmitted S); *n_out = live beams (may
+ * exceed cap; nothing beyond cap is written); *dropped = children lost to the reserved capacity.
+ * Synchronous. */
+fga_status fga_beams_export_all(const fga_beams *b, int64_t cap, int64_t *n_out, int64_t *dropped, double *state,
+                                int32_t *meta, int64_t *mesh_id, int64_t *path);
+
+/* Reverse mode of fga_solve's seismograms (no counterpart in the paper, which uses the method as the
+ * forward model of tomography and waveform inversion and leaves the adjoint to that literature).
+ * For a cotangent ubar of the seismograms, DEVICE complex [n_times][n_rx][3] in the init
+ * precision (dL/dRe u + i dL/dIm u; ubar = u - d for L = 1/2 sum |u - d|^2), ADDS dL/d(node field)
+ * to grad_p and grad_s, DEVICE float64 arrays shaped like the model grids, [n0][n1][n2][10] in the
+ * field order of fga_model_create (the caller zeroes them first; several sources may accumulate).
+ * L is the discrete forward map fga_solve computes: initialisation (its c(q) term), classical RK4,
+ * Hermite-interpolated records and the windowed Gaussian sums (the window's edge is not
+ * differentiated).  The forward pass stores the beam state every checkpoint_every steps (<= 0: 20);
+ * each segment is recomputed in reverse, so device memory holds (ceil(nsteps/C) + C + 2) beam states
+ * (46 values per beam).  Grid and constant media (constant media have no node fields: grad_p and
+ * grad_s may be NULL); receivers as points (sd->rx, sd->n_rx >= 1); snapshots are ignored; at most
+ * 4 sample times inside one step and n_rx * (3 + 6 * samples in a step) values of the init
+ * precision within 200 KiB.  Node cotangents are accumulated with FP64 atomics, so the last bits
+ * depend on the order of the updates.  Synchronous on s.  Errors: INVALID_ARG, UNSUPPORTED
+ * (other media), OOM, CUDA. */
+fga_status fga_solve_vjp(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, const void *ubar,
+                         double *grad_p, double *grad_s, int checkpoint_every, fga_stream_t s);
+
 /* Cell binning (no counterpart in the paper: the fast summation it cites is not printed).
  * For FP32 centres Q (DEVICE float [n][3]) computes key = (c0 nc1 + c1) nc2 + c2 with
  * c_d = floor((Q_d - o_d) * inv_h) in FP32 round-to-nearest, clamped to [0, nc_d-1], then a
@@ -203,15 +240,17 @@ fga_status fga_bin(const float *Q, int64_t n, const float origin[3], float inv_h
  * count); 3: both.  Categories of
  * count[] / ms[]: 0 decomposition, 1 RK4 propagation, 2 binning (keys, sort, permutation),
  * 3 records, 4 Gaussian sums at sample times inside fga_solve, 5 Gaussian-sum reductions,
- * 6 Gaussian sums at the current beam state (snapshots, fga_reconstruct, fga_reconstruct_lattice).  pairs_in_window counts the
+ * 6 Gaussian sums at the current beam state (snapshots, fga_reconstruct, fga_reconstruct_lattice),
+ * 7 layered-medium steps with interface events, 8 adjoint forward recomputation (checkpoints and
+ * segments), 9 adjoint reverse steps, 10 adjoint initial-amplitude term, 11 unused.  pairs_in_window counts the
  * (beam, point) pairs inside the truncation window that the Gaussian sum evaluated; pairs_tested the
  * pairs it examined; beam_steps the beam RK4 steps advanced.  fga_profile_read waits for the timed
  * launches to finish; reset != 0 zeroes the counters afterwards.  Process-wide state, meant to be
  * driven from one host thread. */
 typedef struct {
     int64_t launches;
-    int64_t count[8];
-    double ms[8];
+    int64_t count[12];
+    double ms[12];
     int64_t beam_steps;
     int64_t pairs_in_window;
     int64_t pairs_tested;

@@ -263,10 +263,14 @@ typedef struct {
 } orc_state;            /* 48 doubles */
 
 /* meta bits: 0-1 class (0 P+, 1 P-, 2 S+, 3 S-), bit 2: S frame reference e1 (else e3),
- * bit 3: S amplitude carried as a complex 3-vector (parallel-transport form) */
+ * bit 3: S amplitude carried as a complex 3-vector (parallel-transport form),
+ * bits 4-7: layer of the beam (layered media), bits 8-11: interfaces crossed so far */
 #define META_CLS(mt) ((mt) & 3)
 #define META_REF_E1 4
 #define META_VECTOR 8
+#define META_LAYER(mt) (((mt) >> 4) & 15)
+#define META_GEN(mt) (((mt) >> 8) & 15)
+#define META_ROOT(mt) (((mt) >> 13) & 3)
 
 static void cross3(const double a[3], const double b[3], double c[3])
 {
@@ -332,6 +336,8 @@ void orc_beam_init(const orc_model *m, double k, int nq, const double q0[3], con
         orc_model_eval(m, wave, y->Q, cf);
         double pn = norm3(y->P);
         const cplx *Fm = F + mi * 3;
+        /* layered media: layer (bits 4-7) and the class of the root beam of the lineage (bits 13-14) */
+        int lay_bits = m->kind == ORC_LAYERED ? ((layer_of(m, y->Q[2]) << 4) | (cls << 13)) : 0;
         const cplx *Gm = G ? G + mi * 3 : NULL;
         double dirs[2][3];
         int ndir;
@@ -364,7 +370,7 @@ void orc_beam_init(const orc_model *m, double k, int nq, const double q0[3], con
             mt |= META_VECTOR;
             for (int d = 0; d < 3; d++) y->a[d] = a0 * (psi[0] * dirs[0][d] + psi[1] * dirs[1][d]);
         }
-        meta[mi] = mt;
+        meta[mi] = mt | lay_bits;
     }
 }
 
@@ -417,7 +423,13 @@ void orc_rhs(const orc_model *m, int mt, const orc_state *y, orc_state *f)
     const int cls = META_CLS(mt), wave = cls >= 2;
     const double sgm = (cls & 1) ? -1.0 : 1.0;
     double cf[10];
-    orc_model_eval(m, wave, y->Q, cf);
+    if (m->kind == ORC_LAYERED) {
+        /* the beam's own layer (a beam sitting on an interface belongs to the side it travels in) */
+        for (int f = 0; f < 10; f++) cf[f] = 0.0;
+        cf[0] = wave ? m->lcs[META_LAYER(mt)] : m->lcp[META_LAYER(mt)];
+    } else {
+        orc_model_eval(m, wave, y->Q, cf);
+    }
     const double c = cf[0];
     const double g[3] = {cf[1], cf[2], cf[3]};
     const double Hs[3][3] = {{cf[4], cf[5], cf[6]}, {cf[5], cf[7], cf[8]}, {cf[6], cf[8], cf[9]}};
@@ -633,4 +645,811 @@ void orc_bin_sort(int nb, const int32_t *key, int ncells, int32_t *perm, int32_t
     memcpy(cell_start, cnt, sizeof(int32_t) * ((size_t)ncells + 1));
     for (int b = 0; b < nb; b++) perm[cnt[key[b]]++] = b;
     free(cnt);
+}
+
+/* ------------------------------------------------------------------------- */
+/* flat interfaces (Sec. 3.1)                                                 */
+/* ------------------------------------------------------------------------- */
+/* A beam crossing the plane x3 = zif between layer A (incident side) and layer B scatters into up to
+ * four beams: reflected P and S (back into A), transmitted P and S (into B).  All share the
+ * horizontal part of P (tangential continuity); each has c_w |P_w| = c_in |P_in| (the frequency is
+ * conserved, so H = c|P| is continuous); reflected beams flip the sign of P_3, transmitted ones keep
+ * it (Eq. p:int).  The amplitudes solve the plane-wave continuity conditions of a welded interface:
+ * displacement u = a N and traction sigma.e3 continuous, with sigma_i3 = lambda delta_i3 (P.N)
+ * + mu (P_i N_3 + P_3 N_i) per unit (i k a) -- the system Eq. Yilmaz writes in angles for a P
+ * incidence, here for any incidence and both S polarisations at once (6 x 6, complex so that a
+ * post-critical wave keeps its decaying P_3 and the others stay correct).  dzQ, dzP jump by
+ * Eq. Inter_DzQDzP: dzQ' = dzQ F, dzP' = dzP W, W = F^{-T} (grad c = 0 on both sides of a flat
+ * interface between homogeneous layers). */
+
+/* 6x6 complex solve by Gaussian elimination with partial pivoting; returns 0 if singular */
+static int csolve6(cplx A[6][6], cplx b[6], cplx x[6])
+{
+    for (int c = 0; c < 6; c++) {
+        int piv = c;
+        for (int r = c + 1; r < 6; r++)
+            if (cabs(A[r][c]) > cabs(A[piv][c])) piv = r;
+        if (cabs(A[piv][c]) < 1e-300) return 0;
+        if (piv != c) {
+            for (int j = 0; j < 6; j++) {
+                cplx t = A[c][j];
+                A[c][j] = A[piv][j];
+                A[piv][j] = t;
+            }
+            cplx t = b[c];
+            b[c] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = c + 1; r < 6; r++) {
+            cplx f = A[r][c] / A[c][c];
+            for (int j = c; j < 6; j++) A[r][j] -= f * A[c][j];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = 5; r >= 0; r--) {
+        cplx s = b[r];
+        for (int j = r + 1; j < 6; j++) s -= A[r][j] * x[j];
+        x[r] = s / A[r][r];
+    }
+    return 1;
+}
+
+/* Polarisation vectors of a wave with (possibly complex) propagation vector P of real length pn:
+ * P: P/pn;  SH: nsh (shared by every wave of the event);  SV: nsh x P/pn. */
+static void wave_pol(const cplx P[3], double pn, const double nsh[3], int which, cplx N[3])
+{
+    if (which == 0) {
+        for (int d = 0; d < 3; d++) N[d] = P[d] / pn;
+    } else if (which == 2) {
+        for (int d = 0; d < 3; d++) N[d] = nsh[d];
+    } else {
+        N[0] = (nsh[1] * P[2] - nsh[2] * P[1]) / pn;
+        N[1] = (nsh[2] * P[0] - nsh[0] * P[2]) / pn;
+        N[2] = (nsh[0] * P[1] - nsh[1] * P[0]) / pn;
+    }
+}
+
+/* traction sigma . e3 of a plane wave a N exp(i k P.x), per unit i k a */
+static void traction(double lam, double mu, const cplx P[3], const cplx N[3], cplx T[3])
+{
+    cplx pn = P[0] * N[0] + P[1] * N[1] + P[2] * N[2];
+    for (int i = 0; i < 3; i++) T[i] = mu * (P[i] * N[2] + P[2] * N[i]);
+    T[2] += lam * pn;
+}
+
+/* Children of beam y (meta mt, in layer la) that reached the interface to layer lb; at most 4,
+ * written in the order reflected P, reflected S, transmitted P, transmitted S (propagating ones
+ * whose amplitude is at least rel_min of the incident one).  Returns the count. */
+int orc_interface_event(const orc_model *m, int mt, const double *y_, int lb, double rel_min, double *out_, int *meta_out)
+{
+    const orc_state *y = (const orc_state *)y_;
+    orc_state *out = (orc_state *)out_;
+    const int la = META_LAYER(mt), cls = META_CLS(mt), wave = cls >= 2;
+    const double sgn = (cls & 1) ? -1.0 : 1.0;
+    const double cin = wave ? m->lcs[la] : m->lcp[la];
+    const double pin = norm3(y->P), om = cin * pin; /* c |P| is conserved */
+    const double ph2 = y->P[0] * y->P[0] + y->P[1] * y->P[1];
+    double nsh[3];
+    if (ph2 > 0.0) {
+        double phn = sqrt(ph2);
+        nsh[0] = -y->P[1] / phn;
+        nsh[1] = y->P[0] / phn;
+        nsh[2] = 0.0;
+    } else {
+        nsh[0] = 0.0;
+        nsh[1] = 1.0;
+        nsh[2] = 0.0;
+    }
+    /* incident displacement vector */
+    cplx Uin[3];
+    {
+        double Ph[3] = {y->P[0] / pin, y->P[1] / pin, y->P[2] / pin};
+        if (!wave) {
+            for (int d = 0; d < 3; d++) Uin[d] = y->a[0] * Ph[d];
+        } else if (mt & META_VECTOR) {
+            for (int d = 0; d < 3; d++) Uin[d] = y->a[d];
+        } else {
+            double Nsv[3], Nsh[3];
+            s_frame(y->P, (mt & META_REF_E1) != 0, Nsv, Nsh, NULL);
+            for (int d = 0; d < 3; d++) Uin[d] = y->a[0] * Nsv[d] + y->a[1] * Nsh[d];
+        }
+    }
+    const double lamA = m->lrho[la] * (m->lcp[la] * m->lcp[la] - 2.0 * m->lcs[la] * m->lcs[la]);
+    const double muA = m->lrho[la] * m->lcs[la] * m->lcs[la];
+    const double lamB = m->lrho[lb] * (m->lcp[lb] * m->lcp[lb] - 2.0 * m->lcs[lb] * m->lcs[lb]);
+    const double muB = m->lrho[lb] * m->lcs[lb] * m->lcs[lb];
+    cplx Tin[3];
+    {
+        cplx Pc[3] = {y->P[0], y->P[1], y->P[2]};
+        traction(wave ? lamA : lamA, muA, Pc, Uin, Tin);
+    }
+    /* the four outgoing waves: 0 rP, 1 rS, 2 tP, 3 tS */
+    const double sz = y->P[2] >= 0.0 ? 1.0 : -1.0;
+    cplx Pw[4][3];
+    double pnw[4], cw[4];
+    int prop[4];
+    for (int w = 0; w < 4; w++) {
+        int trans = w >= 2, s_wave = w & 1;
+        int L = trans ? lb : la;
+        cw[w] = s_wave ? m->lcs[L] : m->lcp[L];
+        pnw[w] = om / cw[w];
+        double pz2 = pnw[w] * pnw[w] - ph2;
+        double side = trans ? sz : -sz;
+        Pw[w][0] = y->P[0];
+        Pw[w][1] = y->P[1];
+        if (pz2 >= 0.0) {
+            Pw[w][2] = side * sqrt(pz2);
+            prop[w] = 1;
+        } else {
+            Pw[w][2] = I * sgn * side * sqrt(-pz2); /* decays away from the interface */
+            prop[w] = 0;
+        }
+    }
+    /* unknowns: a_rP, a_rSV, a_rSH, a_tP, a_tSV, a_tSH */
+    cplx A[6][6], b[6], x[6];
+    const int wv[6] = {0, 1, 1, 2, 3, 3}, pol[6] = {0, 1, 2, 0, 1, 2};
+    for (int u = 0; u < 6; u++) {
+        const int w = wv[u], trans = w >= 2;
+        cplx N[3], T[3];
+        wave_pol(Pw[w], pnw[w], nsh, pol[u], N);
+        traction(trans ? lamB : lamA, trans ? muB : muA, Pw[w], N, T);
+        double sg = trans ? -1.0 : 1.0;
+        for (int d = 0; d < 3; d++) {
+            A[d][u] = sg * N[d];
+            A[3 + d][u] = sg * T[d];
+        }
+    }
+    for (int d = 0; d < 3; d++) {
+        b[d] = -Uin[d];
+        b[3 + d] = -Tin[d];
+    }
+    if (!csolve6(A, b, x)) return 0;
+    double ain = sqrt(creal(Uin[0] * conj(Uin[0]) + Uin[1] * conj(Uin[1]) + Uin[2] * conj(Uin[2])));
+    int nout = 0;
+    for (int w = 0; w < 4; w++) {
+        if (!prop[w]) continue;
+        int s_wave = w & 1, trans = w >= 2;
+        cplx a0 = s_wave ? x[w == 1 ? 1 : 4] : x[w == 0 ? 0 : 3];
+        cplx a1 = s_wave ? x[w == 1 ? 2 : 5] : 0.0;
+        double amag = sqrt(creal(a0 * conj(a0) + a1 * conj(a1)));
+        if (!(amag >= rel_min * ain) || amag == 0.0) continue;
+        orc_state *c = out + nout;
+        *c = *y;
+        double Pr[3] = {creal(Pw[w][0]), creal(Pw[w][1]), creal(Pw[w][2])};
+        for (int d = 0; d < 3; d++) c->P[d] = Pr[d];
+        /* dzQ' = dzQ F, dzP' = dzP F^{-T}; F = I except its last row
+         * ((kappa-1) p_x/p_z, (kappa-1) p_y/p_z, kappa p_z'/p_z), kappa = (c_out/c_in)^2 */
+        double kap = (cw[w] / cin) * (cw[w] / cin);
+        double Fm[3][3] = {{1, 0, 0}, {0, 1, 0},
+                           {(kap - 1.0) * y->P[0] / y->P[2], (kap - 1.0) * y->P[1] / y->P[2], kap * Pr[2] / y->P[2]}};
+        /* F^{-T}: inverse of the transpose of a matrix that differs from I in its last row */
+        double Wm[3][3];
+        {
+            double f20 = Fm[2][0], f21 = Fm[2][1], f22 = Fm[2][2];
+            /* F^{-1} = [[1,0,0],[0,1,0],[-f20/f22, -f21/f22, 1/f22]]; W = (F^{-1})^T */
+            double Fi[3][3] = {{1, 0, 0}, {0, 1, 0}, {-f20 / f22, -f21 / f22, 1.0 / f22}};
+            for (int r = 0; r < 3; r++)
+                for (int q = 0; q < 3; q++) Wm[r][q] = Fi[q][r];
+        }
+        for (int mm = 0; mm < 3; mm++)
+            for (int j = 0; j < 3; j++) {
+                cplx sq = 0, sp = 0;
+                for (int l = 0; l < 3; l++) {
+                    sq += y->DQ[3 * mm + l] * Fm[l][j];
+                    sp += y->DP[3 * mm + l] * Wm[l][j];
+                }
+                c->DQ[3 * mm + j] = sq;
+                c->DP[3 * mm + j] = sp;
+            }
+        int cc = (s_wave ? 2 : 0) | (cls & 1);
+        int mt_c = cc | ((trans ? lb : la) << 4) | ((META_GEN(mt) + 1) << 8) | (mt & (3 << 13));
+        c->a[0] = c->a[1] = c->a[2] = 0;
+        if (!s_wave) {
+            c->a[0] = a0;
+        } else {
+            /* SV along nsh x P/|P|, SH along nsh (the e3 frame); re-expressed in the child's own frame */
+            cplx Nsv[3], Ag[3];
+            cplx Pc[3] = {Pr[0], Pr[1], Pr[2]};
+            wave_pol(Pc, pnw[w], nsh, 1, Nsv);
+            for (int d = 0; d < 3; d++) Ag[d] = a0 * Nsv[d] + a1 * nsh[d];
+            if (mt & META_VECTOR) {
+                mt_c |= META_VECTOR;
+                for (int d = 0; d < 3; d++) c->a[d] = Ag[d];
+            } else {
+                int r = orc_s_ref_e1(Pr);
+                if (r) mt_c |= META_REF_E1;
+                double fsv[3], fsh[3];
+                s_frame(Pr, r, fsv, fsh, NULL);
+                c->a[0] = Ag[0] * fsv[0] + Ag[1] * fsv[1] + Ag[2] * fsv[2];
+                c->a[1] = Ag[0] * fsh[0] + Ag[1] * fsh[1] + Ag[2] * fsh[2];
+            }
+        }
+        meta_out[nout] = mt_c;
+        nout++;
+    }
+    return nout;
+}
+
+/* One RK4 step of size dt for every beam of a layered medium, with interface events (Sec. 3.1):
+ * a beam whose step crosses an interface is advanced to the crossing (its motion is straight in a
+ * homogeneous layer), replaced by its children, and every child is advanced through the rest of the
+ * step.  Beams that have crossed gmax interfaces are dropped at their next one.  The new population
+ * (parents without events in input order, children in place of their parent) goes to out/meta_out,
+ * with path[] recording the lineage (parent path * 4 + child slot + 1).  Returns the new count or
+ * -1 if cap is too small. */
+int orc_layered_step(const orc_model *m, int nb, const double *st_, const int *meta, const long long *path,
+                     double dt, int gmax, double rel_min, int cap, double *out_, int *meta_out, long long *path_out,
+                     int *parent_out)
+{
+    const orc_state *st = (const orc_state *)st_;
+    orc_state *out = (orc_state *)out_;
+    int n = 0;
+    for (int b = 0; b < nb; b++) {
+        const int mt = meta[b], L = META_LAYER(mt);
+        orc_state y = st[b], f0, y1;
+        orc_rhs(m, mt, &y, &f0);
+        rk4_step(m, mt, &y, &f0, dt, &y1);
+        double ztop = L > 0 ? m->zif[L - 1] : -INFINITY, zbot = L < m->nlay - 1 ? m->zif[L] : INFINITY;
+        if (y1.Q[2] >= ztop && y1.Q[2] < zbot) {
+            if (n >= cap) return -1;
+            out[n] = y1;
+            meta_out[n] = mt;
+            path_out[n] = path[b];
+            if (parent_out) parent_out[n] = b;
+            n++;
+            continue;
+        }
+        int down = y1.Q[2] >= zbot;
+        double zc = down ? zbot : ztop;
+        int lb = down ? L + 1 : L - 1;
+        double th = (zc - y.Q[2]) / (y1.Q[2] - y.Q[2]);
+        if (META_GEN(mt) >= gmax) continue;
+        orc_state yc;
+        rk4_step(m, mt, &y, &f0, th * dt, &yc);
+        yc.Q[2] = zc;
+        orc_state ch[4];
+        int cm[4];
+        int nc = orc_interface_event(m, mt, (const double *)&yc, lb, rel_min, (double *)ch, cm);
+        for (int c = 0; c < nc; c++) {
+            orc_state fc, ye;
+            orc_rhs(m, cm[c], &ch[c], &fc);
+            rk4_step(m, cm[c], &ch[c], &fc, (1.0 - th) * dt, &ye);
+            if (n >= cap) return -1;
+            out[n] = ye;
+            meta_out[n] = cm[c];
+            /* child slot: 0 rP, 1 rS, 2 tP, 3 tS */
+            int slot = ((cm[c] >> 4) & 15) == L ? ((cm[c] & 2) ? 1 : 0) : ((cm[c] & 2) ? 3 : 2);
+            path_out[n] = path[b] * 4 + slot + 1;
+            if (parent_out) parent_out[n] = b;
+            n++;
+        }
+    }
+    return n;
+}
+
+/* ------------------------------------------------------------------------- */
+/* discrete adjoint (no counterpart in the paper, which defers its kernels to other works)  */
+/* ------------------------------------------------------------------------- */
+/* Reverse mode of the forward solve above for grid media, for the waveform misfit
+ * L = 1/2 sum |u - d|^2 over receivers and samples, with respect to the 10 node fields of the P and
+ * S grids.  Complex adjoints follow z_bar = dL/dRe z + i dL/dIm z: for w = f(z) holomorphic
+ * z_bar += conj(f'(z)) w_bar, and a real r feeding w gets r_bar += Re(conj(dw/dr) w_bar). */
+
+/* trilinear weights of a grid point and their derivatives along each axis (zero where clamped) */
+static void grid_weights(const orc_model *m, const double x[3], size_t node[8], double wgt[8], double dw[8][3])
+{
+    int i[3];
+    double fr[3], dfr[3];
+    for (int d = 0; d < 3; d++) {
+        double t = (x[d] - m->o[d]) / m->h[d];
+        dfr[d] = 1.0 / m->h[d];
+        if (t < 0.0) {
+            t = 0.0;
+            dfr[d] = 0.0;
+        }
+        if (t > (double)(m->n[d] - 1)) {
+            t = (double)(m->n[d] - 1);
+            dfr[d] = 0.0;
+        }
+        int id = (int)floor(t);
+        if (id > m->n[d] - 2) id = m->n[d] - 2;
+        i[d] = id;
+        fr[d] = t - (double)id;
+    }
+    int c = 0;
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            for (int e = 0; e < 2; e++, c++) {
+                double w0 = a ? fr[0] : 1.0 - fr[0], w1 = b ? fr[1] : 1.0 - fr[1], w2 = e ? fr[2] : 1.0 - fr[2];
+                double s0 = a ? 1.0 : -1.0, s1 = b ? 1.0 : -1.0, s2 = e ? 1.0 : -1.0;
+                node[c] = ((size_t)(i[0] + a) * m->n[1] + (size_t)(i[1] + b)) * m->n[2] + (size_t)(i[2] + e);
+                wgt[c] = w0 * w1 * w2;
+                dw[c][0] = s0 * dfr[0] * w1 * w2;
+                dw[c][1] = w0 * s1 * dfr[1] * w2;
+                dw[c][2] = w0 * w1 * s2 * dfr[2];
+            }
+}
+
+/* adjoint of the model fields at Q: Q_bar += sum_f cbar[f] d field_f/dQ; node grads += weights cbar */
+static void model_vjp(const orc_model *m, int wave, const double Q[3], const double cbar[10], double Qbar[3],
+                      double *gp, double *gs)
+{
+    if (m->kind != ORC_GRID) return; /* constant media: the fields do not depend on Q or on nodes */
+    size_t node[8];
+    double wgt[8], dw[8][3];
+    grid_weights(m, Q, node, wgt, dw);
+    const float *g = wave ? m->gs : m->gp;
+    double *G = wave ? gs : gp;
+    for (int c = 0; c < 8; c++)
+        for (int f = 0; f < 10; f++) {
+            const double v = (double)g[node[c] * 10 + f];
+            for (int d = 0; d < 3; d++) Qbar[d] += cbar[f] * v * dw[c][d];
+            if (G) {
+                const double add = cbar[f] * wgt[c];
+#pragma omp atomic
+                G[node[c] * 10 + f] += add;
+            }
+        }
+}
+
+/* ybar += (d rhs/dy)^T fbar; model adjoints scattered onto the node grids gp/gs (may be NULL) */
+void orc_rhs_vjp(const orc_model *m, int mt, const orc_state *y, const orc_state *fb, orc_state *yb, double *gp,
+                 double *gs)
+{
+    const int cls = META_CLS(mt), wave = cls >= 2;
+    const double sg = (cls & 1) ? -1.0 : 1.0;
+    double cf[10];
+    orc_model_eval(m, wave, y->Q, cf);
+    const double c = cf[0];
+    const double g[3] = {cf[1], cf[2], cf[3]};
+    const double H[3][3] = {{cf[4], cf[5], cf[6]}, {cf[5], cf[7], cf[8]}, {cf[6], cf[8], cf[9]}};
+    const double pn = norm3(y->P), ip = 1.0 / pn;
+    double Ph[3];
+    for (int d = 0; d < 3; d++) Ph[d] = y->P[d] * ip;
+    const double cip = c * ip;
+    /* forward intermediates */
+    cplx u[3], v[3], t3[3][3], fDQ[3][3], fDP[3][3];
+    for (int mm = 0; mm < 3; mm++) {
+        u[mm] = 0;
+        v[mm] = 0;
+        for (int l = 0; l < 3; l++) {
+            u[mm] += y->DQ[3 * mm + l] * g[l];
+            v[mm] += y->DP[3 * mm + l] * Ph[l];
+        }
+        for (int j = 0; j < 3; j++) {
+            t3[mm][j] = 0;
+            for (int l = 0; l < 3; l++) t3[mm][j] += y->DQ[3 * mm + l] * H[l][j];
+            fDQ[mm][j] = sg * (u[mm] * Ph[j] + cip * y->DP[3 * mm + j] - cip * v[mm] * Ph[j]);
+            fDP[mm][j] = -sg * (pn * t3[mm][j] + v[mm] * g[j]);
+        }
+    }
+    double fP[3];
+    for (int d = 0; d < 3; d++) fP[d] = -sg * pn * g[d];
+    cplx Z[9], Zd[9], Zi[9];
+    for (int mm = 0; mm < 3; mm++)
+        for (int j = 0; j < 3; j++) {
+            Z[3 * mm + j] = y->DQ[3 * mm + j] + I * y->DP[3 * mm + j];
+            Zd[3 * mm + j] = fDQ[mm][j] + I * fDP[mm][j];
+        }
+    /* Z^{-1} by Gauss-Jordan on [Z | I] */
+    {
+        cplx a[3][6];
+        for (int r = 0; r < 3; r++)
+            for (int q = 0; q < 3; q++) {
+                a[r][q] = Z[3 * r + q];
+                a[r][3 + q] = (r == q) ? 1.0 : 0.0;
+            }
+        for (int col = 0; col < 3; col++) {
+            int piv = col;
+            for (int r = col + 1; r < 3; r++)
+                if (cabs(a[r][col]) > cabs(a[piv][col])) piv = r;
+            for (int q = 0; q < 6; q++) {
+                cplx t = a[col][q];
+                a[col][q] = a[piv][q];
+                a[piv][q] = t;
+            }
+            cplx inv = 1.0 / a[col][col];
+            for (int q = 0; q < 6; q++) a[col][q] *= inv;
+            for (int r = 0; r < 3; r++) {
+                if (r == col) continue;
+                cplx fct = a[r][col];
+                for (int q = 0; q < 6; q++) a[r][q] -= fct * a[col][q];
+            }
+        }
+        for (int r = 0; r < 3; r++)
+            for (int q = 0; q < 3; q++) Zi[3 * r + q] = a[r][3 + q];
+    }
+    cplx tr = 0;
+    for (int mm = 0; mm < 3; mm++)
+        for (int j = 0; j < 3; j++) tr += Zi[3 * j + mm] * Zd[3 * mm + j];
+    const cplx gam = sg * (g[0] * Ph[0] + g[1] * Ph[1] + g[2] * Ph[2]) + 0.5 * tr;
+
+    /* adjoint accumulators */
+    double cb[10] = {0}, Phb[3] = {0}, pnb = 0, cipb = 0, fPb[3];
+    cplx fDQb[3][3], fDPb[3][3], ub[3] = {0}, vb[3] = {0}, t3b[3][3];
+    for (int d = 0; d < 3; d++) fPb[d] = fb->P[d];
+    for (int mm = 0; mm < 3; mm++)
+        for (int j = 0; j < 3; j++) {
+            fDQb[mm][j] = fb->DQ[3 * mm + j];
+            fDPb[mm][j] = fb->DP[3 * mm + j];
+        }
+    /* amplitudes */
+    cplx gamb = 0;
+    if (!wave) {
+        yb->a[0] += conj(gam) * fb->a[0];
+        gamb = conj(y->a[0]) * fb->a[0];
+    } else {
+        /* omega = -s1 s2 / D, s1 = fP.(e x P), s2 = e.P, D = |P|^3 - s2^2 |P| */
+        const int r1 = (mt & META_REF_E1) != 0;
+        const double e[3] = {r1 ? 1.0 : 0.0, 0.0, r1 ? 0.0 : 1.0};
+        double exP[3], fPxe[3];
+        cross3(e, y->P, exP);
+        cross3(fP, e, fPxe);
+        const double s1 = fP[0] * exP[0] + fP[1] * exP[1] + fP[2] * exP[2];
+        const double s2 = e[0] * y->P[0] + e[1] * y->P[1] + e[2] * y->P[2];
+        const double D = pn * pn * pn - s2 * s2 * pn;
+        const double om = -s1 * s2 / D;
+        yb->a[0] += conj(gam) * fb->a[0] + om * fb->a[1];
+        yb->a[1] += conj(gam) * fb->a[1] - om * fb->a[0];
+        gamb = conj(y->a[0]) * fb->a[0] + conj(y->a[1]) * fb->a[1];
+        const double omb = creal(-conj(y->a[1]) * fb->a[0] + conj(y->a[0]) * fb->a[1]);
+        /* d omega / d fP = -(s2/D) e x P;  d omega / dP = -(s2/D) fP x e - (s1/D) e + (s1 s2/D^2) dD/dP */
+        for (int d = 0; d < 3; d++) {
+            fPb[d] += omb * (-(s2 / D) * exP[d]);
+            const double dD = 3.0 * pn * y->P[d] - 2.0 * s2 * pn * e[d] - s2 * s2 * y->P[d] / pn;
+            yb->P[d] += omb * (-(s2 / D) * fPxe[d] - (s1 / D) * e[d] + (s1 * s2 / (D * D)) * dD);
+        }
+    }
+    /* gamma = sg g.Ph + tr/2 */
+    for (int d = 0; d < 3; d++) {
+        cb[1 + d] += sg * Ph[d] * creal(gamb);
+        Phb[d] += sg * g[d] * creal(gamb);
+    }
+    const cplx trb = 0.5 * gamb;
+    /* tr = sum_mj Zi_jm Zd_mj: Zd_bar = conj(Zi^T) trb, Z_bar = -conj((Zi Zd Zi)^T) trb */
+    cplx ZiZdZi[9];
+    for (int r = 0; r < 3; r++)
+        for (int q = 0; q < 3; q++) {
+            cplx s = 0;
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) s += Zi[3 * r + a] * Zd[3 * a + b] * Zi[3 * b + q];
+            ZiZdZi[3 * r + q] = s;
+        }
+    for (int mm = 0; mm < 3; mm++)
+        for (int j = 0; j < 3; j++) {
+            const cplx zdb = conj(Zi[3 * j + mm]) * trb;
+            const cplx zb = -conj(ZiZdZi[3 * j + mm]) * trb;
+            fDQb[mm][j] += zdb;
+            fDPb[mm][j] += -I * zdb;
+            yb->DQ[3 * mm + j] += zb;
+            yb->DP[3 * mm + j] += -I * zb;
+        }
+    /* fDP = -sg (pn t3 + v g) */
+    for (int mm = 0; mm < 3; mm++)
+        for (int j = 0; j < 3; j++) {
+            pnb += creal(conj(-sg * t3[mm][j]) * fDPb[mm][j]);
+            t3b[mm][j] = -sg * pn * fDPb[mm][j];
+            vb[mm] += -sg * g[j] * fDPb[mm][j];
+            cb[1 + j] += creal(conj(-sg * v[mm]) * fDPb[mm][j]);
+        }
+    /* t3 = DQ H */
+    for (int mm = 0; mm < 3; mm++)
+        for (int l = 0; l < 3; l++)
+            for (int j = 0; j < 3; j++) {
+                yb->DQ[3 * mm + l] += H[l][j] * t3b[mm][j];
+                const double hb = creal(conj(y->DQ[3 * mm + l]) * t3b[mm][j]);
+                /* H_lj is field 4.. (symmetric storage) */
+                static const int hidx[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};
+                cb[hidx[l][j]] += hb;
+            }
+    /* fDQ = sg (u Ph + cip DP - cip v Ph) */
+    for (int mm = 0; mm < 3; mm++)
+        for (int j = 0; j < 3; j++) {
+            const cplx b = fDQb[mm][j];
+            ub[mm] += sg * Ph[j] * b;
+            yb->DP[3 * mm + j] += sg * cip * b;
+            vb[mm] += -sg * cip * Ph[j] * b;
+            cipb += creal(conj(sg * (y->DP[3 * mm + j] - v[mm] * Ph[j])) * b);
+            Phb[j] += creal(conj(sg * (u[mm] - cip * v[mm])) * b);
+        }
+    /* u = DQ g, v = DP Ph */
+    for (int mm = 0; mm < 3; mm++)
+        for (int l = 0; l < 3; l++) {
+            yb->DQ[3 * mm + l] += g[l] * ub[mm];
+            cb[1 + l] += creal(conj(y->DQ[3 * mm + l]) * ub[mm]);
+            yb->DP[3 * mm + l] += Ph[l] * vb[mm];
+            Phb[l] += creal(conj(y->DP[3 * mm + l]) * vb[mm]);
+        }
+    /* fP = -sg pn g, fQ = sg c Ph */
+    for (int d = 0; d < 3; d++) {
+        pnb += -sg * g[d] * fPb[d];
+        cb[1 + d] += -sg * pn * fPb[d];
+        cb[0] += sg * Ph[d] * fb->Q[d];
+        Phb[d] += sg * c * fb->Q[d];
+    }
+    /* cip = c / pn */
+    cb[0] += ip * cipb;
+    pnb += -c * ip * ip * cipb;
+    /* Ph = P / pn, pn = |P| */
+    double phd = Phb[0] * Ph[0] + Phb[1] * Ph[1] + Phb[2] * Ph[2];
+    for (int d = 0; d < 3; d++) yb->P[d] += (Phb[d] - Ph[d] * phd) * ip + pnb * Ph[d];
+    model_vjp(m, wave, y->Q, cb, yb->Q, gp, gs);
+}
+
+/* adjoint of the S frame: given Nsv_bar, Nsh_bar, add the cotangent of P (Nsh = e x P/|e x P|, Nsv = Nsh x P^) */
+static void s_frame_vjp(const double P[3], int ref_e1, const double Nsvb[3], const double Nshb[3], double Pb[3])
+{
+    const double e[3] = {ref_e1 ? 1.0 : 0.0, 0.0, ref_e1 ? 0.0 : 1.0};
+    double v[3], Nsh[3], Ph[3], Nshb2[3], Phb[3], vb[3], tmp[3];
+    cross3(e, P, v);
+    const double nv = norm3(v), nP = norm3(P);
+    for (int d = 0; d < 3; d++) {
+        Nsh[d] = v[d] / nv;
+        Ph[d] = P[d] / nP;
+    }
+    /* Nsv = Nsh x Ph: Nsh_bar += Ph x Nsv_bar, Ph_bar = Nsv_bar x Nsh */
+    cross3(Ph, Nsvb, tmp);
+    for (int d = 0; d < 3; d++) Nshb2[d] = Nshb[d] + tmp[d];
+    cross3(Nsvb, Nsh, Phb);
+    const double s1 = Nsh[0] * Nshb2[0] + Nsh[1] * Nshb2[1] + Nsh[2] * Nshb2[2];
+    for (int d = 0; d < 3; d++) vb[d] = (Nshb2[d] - Nsh[d] * s1) / nv;
+    /* v = e x P: P_bar += v_bar x e */
+    cross3(vb, e, tmp);
+    const double s2 = Ph[0] * Phb[0] + Ph[1] * Phb[1] + Ph[2] * Phb[2];
+    for (int d = 0; d < 3; d++) Pb[d] += tmp[d] + (Phb[d] - Ph[d] * s2) / nP;
+}
+
+/* cotangent of one record from the receiver cotangents ub [nx][3] (complex) of its sample:
+ * u(x) = sum A exp(phi), phi = i k P.(x-Q) - k|x-Q|^2/2 inside the window |x-Q| <= rw (rw <= 0: no window). */
+static void gauss_vjp_record(const double r[12], double k, double rw, int nx, const double *x, const cplx *ub,
+                             double rb[12])
+{
+    cplx Ab[3] = {0, 0, 0};
+    double Qb[3] = {0, 0, 0}, Pb[3] = {0, 0, 0};
+    const cplx A[3] = {r[6] + I * r[7], r[8] + I * r[9], r[10] + I * r[11]};
+    for (int i = 0; i < nx; i++) {
+        const double *xi = x + 3 * i;
+        const double dx[3] = {xi[0] - r[0], xi[1] - r[1], xi[2] - r[2]};
+        const double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+        if (rw > 0.0 && r2 > rw * rw) continue;
+        const double ph = r[3] * dx[0] + r[4] * dx[1] + r[5] * dx[2];
+        const cplx E = cexp(I * k * ph - 0.5 * k * r2);
+        const cplx *u = ub + (size_t)i * 3;
+        cplx Eb = 0;
+        for (int d = 0; d < 3; d++) {
+            Ab[d] += conj(E) * u[d];
+            Eb += conj(A[d]) * u[d];
+        }
+        const cplx phb = conj(E) * Eb; /* d phi/d P = i k dx, d phi/d Q = -i k P + k dx */
+        for (int d = 0; d < 3; d++) {
+            Pb[d] += creal(conj(I * k * dx[d]) * phb);
+            Qb[d] += creal(conj(-I * k * r[3 + d] + k * dx[d]) * phb);
+        }
+    }
+    for (int d = 0; d < 3; d++) {
+        rb[d] += Qb[d];
+        rb[3 + d] += Pb[d];
+        rb[6 + 2 * d] += creal(Ab[d]);
+        rb[7 + 2 * d] += cimag(Ab[d]);
+    }
+}
+
+/* adjoint of make_record (frame or scalar form): record cotangent rb -> cotangents of y0, f0, y1, f1 */
+static void make_record_vjp(int mt, const orc_state *y0, const orc_state *f0, const orc_state *y1,
+                            const orc_state *f1, double dt, double th, double w, const double rb[12], orc_state *y0b,
+                            orc_state *f0b, orc_state *y1b, orc_state *f1b)
+{
+    const double h00 = 2 * th * th * th - 3 * th * th + 1, h10 = th * th * th - 2 * th * th + th;
+    const double h01 = -2 * th * th * th + 3 * th * th, h11 = th * th * th - th * th;
+    double P[3], Pb[3];
+    for (int d = 0; d < 3; d++) {
+        P[d] = h00 * y0->P[d] + h10 * dt * f0->P[d] + h01 * y1->P[d] + h11 * dt * f1->P[d];
+        Pb[d] = rb[3 + d];
+    }
+    cplx a[3], ab[3] = {0, 0, 0};
+    for (int j = 0; j < 3; j++) a[j] = (1.0 - th) * y0->a[j] + th * y1->a[j];
+    const cplx Ab[3] = {rb[6] + I * rb[7], rb[8] + I * rb[9], rb[10] + I * rb[11]};
+    const int cls = META_CLS(mt);
+    if (cls < 2) {
+        const double pn = norm3(P);
+        double Ph[3], Phb[3];
+        for (int d = 0; d < 3; d++) Ph[d] = P[d] / pn;
+        for (int d = 0; d < 3; d++) {
+            ab[0] += w * Ph[d] * Ab[d];
+            Phb[d] = creal(conj(w * a[0]) * Ab[d]);
+        }
+        const double s = Ph[0] * Phb[0] + Ph[1] * Phb[1] + Ph[2] * Phb[2];
+        for (int d = 0; d < 3; d++) Pb[d] += (Phb[d] - Ph[d] * s) / pn;
+    } else if (!(mt & META_VECTOR)) {
+        double Nsv[3], Nsh[3], Nsvb[3], Nshb[3];
+        s_frame(P, (mt & META_REF_E1) != 0, Nsv, Nsh, NULL);
+        for (int d = 0; d < 3; d++) {
+            ab[0] += w * Nsv[d] * Ab[d];
+            ab[1] += w * Nsh[d] * Ab[d];
+            Nsvb[d] = creal(conj(w * a[0]) * Ab[d]);
+            Nshb[d] = creal(conj(w * a[1]) * Ab[d]);
+        }
+        s_frame_vjp(P, (mt & META_REF_E1) != 0, Nsvb, Nshb, Pb);
+    } else {
+        for (int d = 0; d < 3; d++) ab[d] = w * Ab[d];
+    }
+    for (int j = 0; j < 3; j++) {
+        y0b->a[j] += (1.0 - th) * ab[j];
+        y1b->a[j] += th * ab[j];
+    }
+    for (int d = 0; d < 3; d++) {
+        y0b->Q[d] += h00 * rb[d];
+        f0b->Q[d] += h10 * dt * rb[d];
+        y1b->Q[d] += h01 * rb[d];
+        f1b->Q[d] += h11 * dt * rb[d];
+        y0b->P[d] += h00 * Pb[d];
+        f0b->P[d] += h10 * dt * Pb[d];
+        y1b->P[d] += h01 * Pb[d];
+        f1b->P[d] += h11 * dt * Pb[d];
+    }
+}
+
+static void state_axpy_inplace(orc_state *o, double h, const orc_state *d)
+{
+    double *oo = (double *)o;
+    const double *dd = (const double *)d;
+    for (int i = 0; i < 48; i++) oo[i] += h * dd[i];
+}
+
+static int state_is_zero(const orc_state *s)
+{
+    const double *v = (const double *)s;
+    for (int i = 0; i < 48; i++)
+        if (v[i] != 0.0) return 0;
+    return 1;
+}
+
+/* adjoint of rk4_step: given yb1 (cotangent of y_{n+1}) and an extra cotangent on k1 = f(y_n),
+ * add the cotangent of y_n to yb0 and the model cotangents to gp/gs */
+static void rk4_step_vjp(const orc_model *m, int mt, const orc_state *y, double dt, const orc_state *yb1,
+                         const orc_state *k1b_extra, orc_state *yb0, double *gp, double *gs)
+{
+    orc_state k1, k2, k3, y2, y3, y4;
+    orc_rhs(m, mt, y, &k1);
+    axpy_state(&y2, y, 0.5 * dt, &k1);
+    orc_rhs(m, mt, &y2, &k2);
+    axpy_state(&y3, y, 0.5 * dt, &k2);
+    orc_rhs(m, mt, &y3, &k3);
+    axpy_state(&y4, y, dt, &k3);
+    orc_state k1b, k2b, k3b, k4b, sb;
+    memset(&k1b, 0, sizeof k1b);
+    memset(&k2b, 0, sizeof k2b);
+    memset(&k3b, 0, sizeof k3b);
+    memset(&k4b, 0, sizeof k4b);
+    state_axpy_inplace(yb0, 1.0, yb1);
+    state_axpy_inplace(&k1b, dt / 6.0, yb1);
+    state_axpy_inplace(&k2b, dt / 3.0, yb1);
+    state_axpy_inplace(&k3b, dt / 3.0, yb1);
+    state_axpy_inplace(&k4b, dt / 6.0, yb1);
+    if (k1b_extra) state_axpy_inplace(&k1b, 1.0, k1b_extra);
+    /* k4 = f(y + dt k3) */
+    memset(&sb, 0, sizeof sb);
+    orc_rhs_vjp(m, mt, &y4, &k4b, &sb, gp, gs);
+    state_axpy_inplace(yb0, 1.0, &sb);
+    state_axpy_inplace(&k3b, dt, &sb);
+    /* k3 = f(y + dt/2 k2) */
+    memset(&sb, 0, sizeof sb);
+    orc_rhs_vjp(m, mt, &y3, &k3b, &sb, gp, gs);
+    state_axpy_inplace(yb0, 1.0, &sb);
+    state_axpy_inplace(&k2b, 0.5 * dt, &sb);
+    /* k2 = f(y + dt/2 k1) */
+    memset(&sb, 0, sizeof sb);
+    orc_rhs_vjp(m, mt, &y2, &k2b, &sb, gp, gs);
+    state_axpy_inplace(yb0, 1.0, &sb);
+    state_axpy_inplace(&k1b, 0.5 * dt, &sb);
+    /* k1 = f(y) */
+    orc_rhs_vjp(m, mt, y, &k1b, yb0, gp, gs);
+}
+
+/* Reverse mode of orc_propagate + records + Gaussian sums at the nx points x for every sample:
+ * u_j(x) = sum_b rec_jb(x).  Given the cotangents ub [ns][nx][3] (complex; dL/dRe u + i dL/dIm u)
+ * writes the cotangent of each beam's initial state to stb [nb][48] and adds the model cotangents
+ * (node fields of the P and S grids) to gp/gs (may be NULL).  Every trajectory is stored in full. */
+int orc_solve_vjp(const orc_model *m, int nb, const double *st_, const int *meta, double dt, int nsteps, int ns,
+                  const int *s_step, const double *s_theta, double w, double k, double rw, int nx, const double *x,
+                  const double *ub_, double *stb_, double *gp, double *gs)
+{
+    const orc_state *st = (const orc_state *)st_;
+    const cplx *ub = (const cplx *)ub_;
+    orc_state *stb = (orc_state *)stb_;
+    for (int b = 0; b < nb; b++)
+        if ((meta[b] & META_VECTOR) || m->kind == ORC_LAYERED) return -1;
+    int bad = 0;
+#pragma omp parallel
+    {
+        orc_state *Y = (orc_state *)malloc(sizeof(orc_state) * (size_t)(nsteps + 1));
+        orc_state *Fv = (orc_state *)malloc(sizeof(orc_state) * (size_t)(nsteps + 1));
+        if (!Y || !Fv) {
+#pragma omp atomic write
+            bad = 1;
+        }
+#pragma omp for schedule(dynamic, 4)
+        for (int b = 0; b < nb; b++) {
+            if (!Y || !Fv) continue;
+            const int mt = meta[b];
+            Y[0] = st[b];
+            orc_rhs(m, mt, &Y[0], &Fv[0]);
+            for (int n = 0; n < nsteps; n++) {
+                rk4_step(m, mt, &Y[n], &Fv[n], dt, &Y[n + 1]);
+                orc_rhs(m, mt, &Y[n + 1], &Fv[n + 1]);
+            }
+            orc_state yb1;
+            memset(&yb1, 0, sizeof yb1);
+            int j = ns - 1;
+            for (int n = nsteps - 1; n >= 0; n--) {
+                orc_state y0b, f0b, f1b;
+                memset(&y0b, 0, sizeof y0b);
+                memset(&f0b, 0, sizeof f0b);
+                memset(&f1b, 0, sizeof f1b);
+                for (; j >= 0 && s_step[j] == n; j--) {
+                    double rec[12], rb[12] = {0};
+                    make_record(mt, &Y[n], &Fv[n], &Y[n + 1], &Fv[n + 1], dt, s_theta[j], w, rec);
+                    gauss_vjp_record(rec, k, rw, nx, x, ub + (size_t)j * nx * 3, rb);
+                    make_record_vjp(mt, &Y[n], &Fv[n], &Y[n + 1], &Fv[n + 1], dt, s_theta[j], w, rb, &y0b, &f0b,
+                                    &yb1, &f1b);
+                }
+                if (!state_is_zero(&f1b)) orc_rhs_vjp(m, mt, &Y[n + 1], &f1b, &yb1, gp, gs);
+                rk4_step_vjp(m, mt, &Y[n], dt, &yb1, &f0b, &y0b, gp, gs);
+                yb1 = y0b;
+            }
+            stb[b] = yb1;
+        }
+        free(Y);
+        free(Fv);
+    }
+    return bad ? -2 : 0;
+}
+
+/* Reverse mode of orc_beam_init with respect to the model: a = 2^{3/2} (F.n +- i G.n/(k c(q) |p|))/2
+ * depends on the model only through c(q) in the G term.  Given the initial-state cotangents stb
+ * (mesh order, one class) adds dL/dc(q) to the node fields through the interpolation weights. */
+void orc_beam_init_vjp(const orc_model *m, double k, int nq, const double q0[3], const double dq[3], int np,
+                       const double p0[3], const double dp[3], const double *F_, const double *G_, int cls,
+                       const double *stb_, double *gp, double *gs)
+{
+    (void)F_;
+    if (!G_) return;
+    const cplx *G = (const cplx *)G_;
+    const orc_state *stb = (const orc_state *)stb_;
+    const long NP = (long)np * np * np;
+    const long M = (long)nq * nq * nq * NP;
+    const int wave = cls >= 2;
+    const double sgn = (cls & 1) ? -1.0 : 1.0;
+    for (long mi = 0; mi < M; mi++) {
+        long iq = mi / NP, ip = mi % NP;
+        int qi[3] = {(int)(iq / ((long)nq * nq)), (int)((iq / nq) % nq), (int)(iq % nq)};
+        int pj[3] = {(int)(ip / ((long)np * np)), (int)((ip / np) % np), (int)(ip % np)};
+        double q[3], p[3];
+        for (int d = 0; d < 3; d++) {
+            q[d] = q0[d] + qi[d] * dq[d];
+            p[d] = p0[d] + pj[d] * dp[d];
+        }
+        const double pn = norm3(p);
+        double cf[10];
+        orc_model_eval(m, wave, q, cf);
+        double dirs[2][3];
+        int ndir;
+        if (!wave) {
+            for (int d = 0; d < 3; d++) dirs[0][d] = p[d] / pn;
+            ndir = 1;
+        } else {
+            s_frame(p, orc_s_ref_e1(p), dirs[0], dirs[1], NULL);
+            ndir = 2;
+        }
+        double cb = 0.0;
+        for (int j = 0; j < ndir; j++) {
+            cplx gn = 0;
+            for (int d = 0; d < 3; d++) gn += G[mi * 3 + d] * dirs[j][d];
+            /* d a_j / d c = -2^{3/2} (1/2) sgn i G.n / (k c^2 |p|) */
+            const cplx da = -pow(2.0, 1.5) * 0.5 * sgn * I * gn / (k * cf[0] * cf[0] * pn);
+            cb += creal(conj(da) * stb[mi].a[j]);
+        }
+        double cbar[10] = {cb, 0, 0, 0, 0, 0, 0, 0, 0, 0}, qb[3] = {0, 0, 0};
+        model_vjp(m, wave, q, cbar, qb, gp, gs);
+    }
 }

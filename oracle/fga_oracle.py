@@ -33,6 +33,20 @@ _lib = None
 CLS_PP, CLS_PM, CLS_SP, CLS_SM = 0, 1, 2, 3
 META_REF_E1 = 4
 META_VECTOR = 8
+
+
+def meta_layer(mt):
+    return (np.asarray(mt) >> 4) & 15
+
+
+def meta_gen(mt):
+    return (np.asarray(mt) >> 8) & 15
+
+
+def meta_root(mt):
+    """Class of the initial beam a layered-medium beam descends from."""
+    return (np.asarray(mt) >> 13) & 3
+
 STATE_DOUBLES = 48
 
 
@@ -101,12 +115,15 @@ def _declare(L):
     L.orc_bin_sort.argtypes = [C.c_int, _P, C.c_int, _P, _P]
     L.orc_s_ref_e1.argtypes = [_P]
     L.orc_s_ref_e1.restype = C.c_int
-    if hasattr(L, "orc_interface_event"):
-        L.orc_interface_event.argtypes = [_P, C.c_int, _P, C.c_int, C.c_int, _P, _P, _P]
-        L.orc_interface_event.restype = C.c_int
-    if hasattr(L, "orc_zoeppritz_p"):
-        L.orc_zoeppritz_p.argtypes = [C.c_double] * 7 + [_P, _P]
-        L.orc_zoeppritz_p.restype = C.c_int
+    L.orc_interface_event.argtypes = [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]
+    L.orc_interface_event.restype = C.c_int
+    L.orc_layered_step.argtypes = [_P, C.c_int, _P, _P, _P, C.c_double, C.c_int, C.c_double, C.c_int, _P, _P, _P, _P]
+    L.orc_layered_step.restype = C.c_int
+    L.orc_rhs_vjp.argtypes = [_P, C.c_int, _P, _P, _P, _P, _P]
+    L.orc_solve_vjp.argtypes = [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int, _P, _P, C.c_double,
+                                C.c_double, C.c_double, C.c_int, _P, _P, _P, _P, _P]
+    L.orc_solve_vjp.restype = C.c_int
+    L.orc_beam_init_vjp.argtypes = [_P, C.c_double, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P, C.c_int, _P, _P, _P]
 
 
 def _ptr(a: np.ndarray):
@@ -265,6 +282,35 @@ def gauss_sum(rec: np.ndarray, k: float, rw: float, x: np.ndarray) -> np.ndarray
     return u
 
 
+def interface_event(model: Model, mt: int, state: np.ndarray, lb: int, rel_min: float = 1e-6):
+    """Children (states [n,48], metas [n]) of one beam at the interface to layer lb (Sec. 3.1)."""
+    st = np.ascontiguousarray(state, dtype=np.float64).reshape(STATE_DOUBLES)
+    out = np.zeros((4, STATE_DOUBLES))
+    mo = np.zeros(4, dtype=np.int32)
+    n = lib().orc_interface_event(model.ptr, int(mt), _ptr(st), int(lb), float(rel_min), _ptr(out), _ptr(mo))
+    return out[:n].copy(), mo[:n].copy()
+
+
+def layered_step(model: Model, st: np.ndarray, meta: np.ndarray, path: np.ndarray, dt: float, gmax: int = 4,
+                 rel_min: float = 1e-6, return_parent: bool = False):
+    """One RK4 step of a layered medium with interface events; returns the new (st, meta, path)
+    (and the index of each output beam's input beam if return_parent)."""
+    st = np.ascontiguousarray(st, dtype=np.float64)
+    meta = np.ascontiguousarray(meta, dtype=np.int32)
+    path = np.ascontiguousarray(path, dtype=np.int64)
+    cap = 4 * st.shape[0] + 4
+    out = np.zeros((cap, STATE_DOUBLES))
+    mo = np.zeros(cap, dtype=np.int32)
+    po = np.zeros(cap, dtype=np.int64)
+    par = np.zeros(cap, dtype=np.int32)
+    n = lib().orc_layered_step(model.ptr, st.shape[0], _ptr(st), _ptr(meta), _ptr(path), float(dt), int(gmax),
+                               float(rel_min), cap, _ptr(out), _ptr(mo), _ptr(po), _ptr(par))
+    assert n >= 0
+    if return_parent:
+        return out[:n].copy(), mo[:n].copy(), po[:n].copy(), par[:n].copy()
+    return out[:n].copy(), mo[:n].copy(), po[:n].copy()
+
+
 def bin_keys_f32(Q: np.ndarray, origin, inv_h: float, nc) -> np.ndarray:
     Q = np.ascontiguousarray(Q, dtype=np.float32).reshape(-1, 3)
     o = np.ascontiguousarray(origin, dtype=np.float32).reshape(3)
@@ -328,3 +374,46 @@ def solve(model: Model, k: float, mesh: Mesh, F: np.ndarray, G, classes, dt: flo
         if snap is not None:
             snap_u += gauss_sum(records(st, meta, w), k, rw, snap)
     return out if snap is None else (out, snap_u)
+
+
+def rhs_vjp(model: Model, state: np.ndarray, mt: int, fbar: np.ndarray, grads: bool = True):
+    """Reverse mode of rhs at one state: returns (ybar [48], gp_bar, gs_bar) for the cotangent fbar
+    of dy/dt (the node-field cotangents are None unless the model is a grid and grads is set)."""
+    y = np.ascontiguousarray(state, dtype=np.float64).reshape(STATE_DOUBLES)
+    fb = np.ascontiguousarray(fbar, dtype=np.float64).reshape(STATE_DOUBLES)
+    yb = np.zeros(STATE_DOUBLES)
+    gp = gs = None
+    if grads and model.kind == "grid":
+        shp = tuple(model.s.n) + (10,)
+        gp, gs = np.zeros(shp), np.zeros(shp)
+    lib().orc_rhs_vjp(model.ptr, int(mt), _ptr(y), _ptr(fb), _ptr(yb), None if gp is None else _ptr(gp),
+                      None if gs is None else _ptr(gs))
+    return yb, gp, gs
+
+
+def solve_vjp(model: Model, k: float, mesh: Mesh, F: np.ndarray, G, classes, dt: float, nsteps: int, times,
+              x: np.ndarray, rw: float, ubar: np.ndarray):
+    """Reverse mode of `solve` (seismograms only) with respect to the node fields of a grid model.
+    ubar: complex [ns, nx, 3] cotangent of the seismograms (dL/dRe u + i dL/dIm u).  Returns
+    (gp_bar, gs_bar), float64 arrays shaped like the model's grids."""
+    assert model.kind == "grid"
+    s_step, s_theta = sample_schedule(times, dt, nsteps)
+    w = mesh.weight(k)
+    shp = tuple(model.s.n) + (10,)
+    gp, gs = np.zeros(shp), np.zeros(shp)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    ub = np.ascontiguousarray(ubar, dtype=np.complex128)
+    assert ub.shape == (len(times), x.shape[0], 3)
+    Fc = np.ascontiguousarray(F, dtype=np.complex128)
+    Gc = None if G is None else np.ascontiguousarray(G, dtype=np.complex128)
+    for cls in classes:
+        st, meta = beam_init(model, k, mesh, F, G, cls, False)
+        stb = np.zeros_like(st)
+        rc = lib().orc_solve_vjp(model.ptr, st.shape[0], _ptr(st), _ptr(meta), float(dt), int(nsteps), len(times),
+                                 _ptr(s_step), _ptr(s_theta), w, float(k), float(rw), x.shape[0], _ptr(x), _ptr(ub),
+                                 _ptr(stb), _ptr(gp), _ptr(gs))
+        assert rc == 0, rc
+        lib().orc_beam_init_vjp(model.ptr, float(k), mesh.nq, _ptr(mesh.q0), _ptr(mesh.dq), mesh.np, _ptr(mesh.p0),
+                                _ptr(mesh.dp), _ptr(Fc), None if Gc is None else _ptr(Gc), int(cls), _ptr(stb),
+                                _ptr(gp), _ptr(gs))
+    return gp, gs

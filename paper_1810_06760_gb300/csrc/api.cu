@@ -150,6 +150,17 @@ void prof_add_pairs_tested(int64_t n) {
 
 }  // namespace fga
 
+namespace fga {
+fga_status sync_layered_count(fga_beams *b, cudaStream_t s) {
+    if (!b->layered) return FGA_OK;
+    unsigned long long c[2] = {0, 0};
+    FGA_CUDA(cudaMemcpyAsync(c, b->counts.p, sizeof c, cudaMemcpyDeviceToHost, s));
+    FGA_CUDA(cudaStreamSynchronize(s));
+    b->nb = (int64_t)std::min<unsigned long long>(c[0], (unsigned long long)b->cap);
+    return FGA_OK;
+}
+}  // namespace fga
+
 using namespace fga;
 
 extern "C" {
@@ -279,7 +290,14 @@ fga_status fga_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps
     cudaStream_t s = (cudaStream_t)s_;
     FGA_CHECK(m && b, "fga_propagate: NULL argument");
     FGA_CHECK(nsteps >= 0 && std::isfinite(dt), "fga_propagate: nsteps >= 0 and a finite dt required");
-    for (int n0 = 0; n0 < nsteps; n0 += 64) FGA_TRY(launch_propagate(m, b, dt, std::min(64, nsteps - n0), nullptr, s));
+    FGA_CHECK(b->layered == (m->dev.kind == FGA_MEDIUM_LAYERED), "fga_propagate: beams made for another kind of medium");
+    if (b->layered) {
+        FGA_TRY(launch_layered_steps(m, b, dt, nsteps, s));
+        FGA_TRY(sync_layered_count(b, s));
+    } else {
+        for (int n0 = 0; n0 < nsteps; n0 += 64)
+            FGA_TRY(launch_propagate(m, b, dt, std::min(64, nsteps - n0), nullptr, s));
+    }
     b->last_stream = s;
     return FGA_OK;
 }
@@ -320,7 +338,7 @@ static fga_status reconstruct_now(const fga_beams *b, const double *x_dev, const
     FGA_TRY(build_sum_plan(ws, g, ws.cell_start.as<int32_t>(), 4, xh.data(), n, s, plan));  // syncs
     const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
     FGA_TRY(ws.rec.ensure(rb * REC * (size_t)std::max<int64_t>(plan.n_rec, 1)));
-    FGA_TRY(launch_records_from_state(b, perm, plan.n_in, plan.rec_off, ws.rec.p, s));
+    FGA_TRY(launch_records_from_state(b, perm, plan.beg, plan.n_in, plan.rec_off, ws.rec.p, s));
     return run_sum(ws, plan, b->precision, ws.rec.p, x_dev, b->k, rw, u_out, s, P_GATHER_STATE);
 }
 
@@ -367,7 +385,7 @@ static fga_status reconstruct_lattice_now(const fga_beams *b, const fga_lattice 
     FGA_TRY(build_lattice_plan(ws, g, ws.cell_start.as<int32_t>(), *L, s, plan));  // syncs
     const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
     FGA_TRY(ws.rec.ensure(rb * REC * (size_t)std::max<int64_t>(plan.n_rec, 1)));
-    FGA_TRY(launch_records_from_state(b, perm, plan.n_in, plan.rec_off, ws.rec.p, s));
+    FGA_TRY(launch_records_from_state(b, perm, plan.beg, plan.n_in, plan.rec_off, ws.rec.p, s));
     return run_lattice(ws, plan, b->precision, ws.rec.p, b->k, rw, u_out, s, P_GATHER_STATE);
 }
 
@@ -377,6 +395,7 @@ fga_status fga_reconstruct_lattice(const fga_beams *b, const fga_lattice *lat, d
     FGA_CHECK(b && lat && u_out, "fga_reconstruct_lattice: NULL argument");
     FGA_TRY(check_lattice(lat, "fga_reconstruct_lattice"));
     if (!(rw > 0)) rw = 6.0 / std::sqrt(b->k);
+    FGA_TRY(sync_layered_count(const_cast<fga_beams *>(b), s));
     return reconstruct_lattice_now(b, lat, rw, u_out, s);
 }
 
@@ -390,6 +409,7 @@ fga_status fga_reconstruct(const fga_beams *b, const double *x, int64_t n, doubl
     if (!(rw > 0)) rw = 6.0 / std::sqrt(b->k);
     std::vector<double> xh;
     FGA_TRY(host_points(x, n, xh, s));
+    FGA_TRY(sync_layered_count(const_cast<fga_beams *>(b), s));
     return reconstruct_now(b, x, xh, n, rw, u_out, s);
 }
 
@@ -466,6 +486,39 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
             h.release();
         }
     } fr{samp, hsamp};
+    if (b->layered) {
+        // layered media: samples sit on step ends (every step may split beams at interfaces), and the
+        // sums at a sample are taken from the state after that step
+        std::vector<int> at((size_t)sd->n_times);
+        for (int j = 0; j < sd->n_times; j++) {
+            const double u = sd->times[j] / sd->dt;
+            const int n = (int)std::lround(u);
+            FGA_CHECK(std::fabs(u - n) <= 1e-9 * std::max(1.0, std::fabs(u)) && n >= 1,
+                      "fga_solve: in a layered medium the sample times must be whole steps");
+            at[(size_t)j] = n;
+        }
+        int js = 0;
+        for (int n = 1; n <= sd->nsteps; n++) {
+            FGA_TRY(launch_layered_steps(m, b, sd->dt, 1, s));
+            if (!seis || js >= sd->n_times || at[(size_t)js] != n) continue;
+            FGA_TRY(sync_layered_count(b, s));
+            while (js < sd->n_times && at[(size_t)js] == n) {
+                void *out = static_cast<char *>(seis_out) + rb * 6 * (size_t)nrx * (size_t)js;
+                if (rxL)
+                    FGA_TRY(reconstruct_lattice_now(b, rxL, rw, out, s));
+                else
+                    FGA_TRY(reconstruct_now(b, sd->rx, rxh, sd->n_rx, rw, out, s));
+                js++;
+            }
+        }
+        FGA_TRY(sync_layered_count(b, s));
+        if (snL)
+            FGA_TRY(reconstruct_lattice_now(b, snL, rw, snap_out, s));
+        else if (sd->n_snap > 0)
+            FGA_TRY(reconstruct_now(b, sd->snap, snh, sd->n_snap, rw, snap_out, s));
+        FGA_CUDA(cudaStreamSynchronize(s));
+        return FGA_OK;
+    }
     // records of one window live in one buffer; cap its size
     size_t free_b = 0, total_b = 0;
     FGA_CUDA(cudaMemGetInfo(&free_b, &total_b));
@@ -544,12 +597,74 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
 
 fga_status fga_beams_count(const fga_beams *b, int64_t *n_by_class) {
     FGA_CHECK(b && n_by_class, "fga_beams_count: NULL argument");
-    for (int c = 0; c < 4; c++) n_by_class[c] = b->n_cls[c];
+    if (!b->layered) {
+        for (int c = 0; c < 4; c++) n_by_class[c] = b->n_cls[c];
+        return FGA_OK;
+    }
+    FGA_TRY(sync_layered_count(const_cast<fga_beams *>(b), b->last_stream));
+    std::vector<int32_t> fl((size_t)b->nb);
+    if (b->nb > 0) FGA_CUDA(cudaMemcpy(fl.data(), b->flags.p, 4 * (size_t)b->nb, cudaMemcpyDeviceToHost));
+    for (int c = 0; c < 4; c++) n_by_class[c] = 0;
+    for (int32_t f : fl)
+        if (!(f & FL_DEAD)) n_by_class[f & FL_CLASS_MASK]++;
+    return FGA_OK;
+}
+
+fga_status fga_beams_export_all(const fga_beams *b, int64_t cap, int64_t *n_out, int64_t *dropped, double *state,
+                                int32_t *meta, int64_t *mesh_id, int64_t *path) {
+    FGA_CHECK(b && n_out && cap >= 0, "fga_beams_export_all: NULL argument or negative cap");
+    FGA_CUDA(cudaStreamSynchronize(b->last_stream));
+    FGA_TRY(sync_layered_count(const_cast<fga_beams *>(b), b->last_stream));
+    const int64_t nb = b->nb, scap = b->cap;
+    std::vector<int32_t> ids((size_t)nb), fl((size_t)nb);
+    std::vector<long long> pa((size_t)nb, 0);
+    if (nb > 0) {
+        FGA_CUDA(cudaMemcpy(ids.data(), b->id.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost));
+        FGA_CUDA(cudaMemcpy(fl.data(), b->flags.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost));
+        if (b->layered) FGA_CUDA(cudaMemcpy(pa.data(), b->path.p, 8 * (size_t)nb, cudaMemcpyDeviceToHost));
+    }
+    std::vector<double> st;
+    if (state && nb > 0) {
+        st.resize((size_t)(NF * scap));
+        if (b->precision == FGA_PREC_FP64) {
+            FGA_CUDA(cudaMemcpy(st.data(), b->state.p, 8 * (size_t)(NF * scap), cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> sf((size_t)(NF * scap));
+            FGA_CUDA(cudaMemcpy(sf.data(), b->state.p, 4 * (size_t)(NF * scap), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < sf.size(); i++) st[i] = sf[i];
+        }
+    }
+    int64_t k = 0;
+    for (int64_t i = 0; i < nb; i++) {
+        if (fl[(size_t)i] & FL_DEAD) continue;
+        if (k < cap) {
+            if (meta) meta[k] = fl[(size_t)i];
+            if (mesh_id) mesh_id[k] = ids[(size_t)i];
+            if (path) path[k] = pa[(size_t)i];
+            if (state) {
+                double *o = state + k * 48;
+                for (int f = 0; f < NF; f++) o[f] = st[(size_t)(f * scap + i)];
+                o[46] = 0.0;
+                o[47] = 0.0;
+            }
+        }
+        k++;
+    }
+    *n_out = k;
+    if (dropped) {
+        unsigned long long c[2] = {0, 0};
+        if (b->layered) FGA_CUDA(cudaMemcpy(c, b->counts.p, sizeof c, cudaMemcpyDeviceToHost));
+        *dropped = (int64_t)c[1];
+    }
     return FGA_OK;
 }
 
 fga_status fga_beams_export(const fga_beams *b, double *state_host, int32_t *meta_host) {
     FGA_CHECK(b, "fga_beams_export: NULL beams");
+    if (b->layered) {
+        set_error("fga_beams_export: beams of a layered medium split at interfaces; use fga_beams_export_all");
+        return FGA_ERR_UNSUPPORTED;
+    }
     FGA_CUDA(cudaStreamSynchronize(b->last_stream));
     const int64_t cap = b->cap, nb = b->nb;
     std::vector<int32_t> ids((size_t)nb), fl((size_t)nb);
@@ -584,7 +699,9 @@ fga_status fga_beams_export(const fga_beams *b, double *state_host, int32_t *met
 fga_status fga_beams_destroy(fga_beams *b) {
     if (!b) return FGA_OK;
     b->ws.release();
-    for (DevBuf *d : {&b->state, &b->state_alt, &b->flags, &b->flags_alt, &b->id, &b->id_alt}) d->release();
+    for (DevBuf *d : {&b->state, &b->state_alt, &b->flags, &b->flags_alt, &b->id, &b->id_alt, &b->path, &b->counts,
+                      &b->n_begin})
+        d->release();
     delete b;
     return FGA_OK;
 }
@@ -600,7 +717,7 @@ fga_status fga_profile_read(fga_profile_t *out, int reset) {
     g_prof.fold();
     std::memset(out, 0, sizeof *out);
     out->launches = g_prof.launches;
-    for (int c = 0; c < 8; c++) {
+    for (int c = 0; c < P_NCAT; c++) {
         out->count[c] = g_prof.count[c];
         out->ms[c] = g_prof.ms[c];
     }

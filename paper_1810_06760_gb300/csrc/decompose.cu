@@ -1,5 +1,6 @@
 // A1-A2: wave-packet (FBI) transform of the initial data (Eq. psi) as three per-axis complex
 // contractions, then beam initialisation (Eqs. alpha^k, ini_plus/ini_minus, op_zZ_app).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -171,6 +172,11 @@ __global__ void beam_init_kernel(ModelDev Md, const C2<R> *__restrict__ F, const
         amp[2 * j] = a0 * R(0.5) * (fr - gsc * gi);
         amp[2 * j + 1] = a0 * R(0.5) * (fi + gsc * gr);
     }
+    if (MED == FGA_MEDIUM_LAYERED) {
+        int l = 0;
+        for (int q = 0; q < Md.nlay - 1; q++) l += (qd[2] >= Md.zif[q]) ? 1 : 0;
+        fl |= (l << 4) | (cls << FL_ROOT_SHIFT);
+    }
     const int64_t b = off + mi;
     R y[NF];
     for (int f = 0; f < NF; f++) y[f] = R(0);
@@ -275,13 +281,36 @@ fga_status decompose_impl(const fga_model *m, const fga_init_desc *d, fga_beams 
         off += b->n_cls[c];
     }
     b->nb = off;
-    b->cap = (off + 31) / 32 * 32;
+    b->layered = m->dev.kind == FGA_MEDIUM_LAYERED;
+    if (b->layered) {
+        b->gmax = d->max_interfaces > 0 ? d->max_interfaces : 4;
+        b->rel_min = d->child_rel_min > 0 ? d->child_rel_min : 1e-6;
+        const double growth = d->growth > 0 ? std::max(1.0, d->growth) : 4.0;
+        b->cap = ((int64_t)std::ceil(growth * (double)off) + 31) / 32 * 32;
+    } else {
+        b->cap = (off + 31) / 32 * 32;
+    }
     const size_t rb = d->precision == FGA_PREC_FP64 ? 8 : 4;
     fga_status st = FGA_OK;
     if ((st = b->state.ensure(rb * NF * b->cap)) != FGA_OK || (st = b->flags.ensure(4 * b->cap)) != FGA_OK ||
         (st = b->id.ensure(4 * b->cap)) != FGA_OK) {
         fga_beams_destroy(b);
         return st;
+    }
+    if (b->layered) {
+        if ((st = b->path.ensure(8 * b->cap)) != FGA_OK || (st = b->counts.ensure(16)) != FGA_OK ||
+            (st = b->n_begin.ensure(8)) != FGA_OK) {
+            fga_beams_destroy(b);
+            return st;
+        }
+        const unsigned long long c0[2] = {(unsigned long long)off, 0ull};
+        cudaError_t e = cudaMemsetAsync(b->path.p, 0, 8 * b->cap, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->counts.p, c0, sizeof c0, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            fga_beams_destroy(b);
+            return cuda_fail(e, "fga_decompose");
+        }
     }
     st = d->precision == FGA_PREC_FP64 ? decompose_typed<double>(m, d, b, s) : decompose_typed<float>(m, d, b, s);
     if (st != FGA_OK) {

@@ -24,6 +24,9 @@ constexpr int MAX_LAYERS = 8;
 // flags per beam
 constexpr int FL_CLASS_MASK = 3;  // 0 P+, 1 P-, 2 S+, 3 S-
 constexpr int FL_REF_E1 = 4;      // S frame built on e1 instead of e3
+// bits 4-7: layer of the beam (layered media); bits 8-11: interfaces crossed so far
+constexpr int FL_DEAD = 1 << 12;  // dropped at an interface (layered media)
+constexpr int FL_ROOT_SHIFT = 13; // bits 13-14: class of the initial beam of the lineage (layered media)
 
 struct ModelDev {
     int kind;
@@ -78,7 +81,20 @@ fga_status cuda_fail(cudaError_t e, const char *what);
 // profiling: launch counters and CUDA-event device times per kernel category -------------------
 // P_GATHER: Gaussian sums at sample times inside a solve; P_GATHER_STATE: sums at the current state
 // (snapshots, fga_reconstruct*)
-enum ProfCat { P_DECOMP = 0, P_PROP = 1, P_BIN = 2, P_REC = 3, P_GATHER = 4, P_REDUCE = 5, P_GATHER_STATE = 6, P_NCAT = 8 };
+enum ProfCat {
+    P_DECOMP = 0,
+    P_PROP = 1,
+    P_BIN = 2,
+    P_REC = 3,
+    P_GATHER = 4,
+    P_REDUCE = 5,
+    P_GATHER_STATE = 6,
+    P_OTHER_LAYER = 7,
+    P_ADJ_FWD = 8,   // adjoint: forward recomputation (checkpoints, segments)
+    P_ADJ_REV = 9,   // adjoint: reverse steps
+    P_ADJ_INIT = 10, // adjoint: initial-amplitude term
+    P_NCAT = 12
+};
 struct ProfScope {  // wraps one kernel launch on stream s
     ProfScope(int cat, cudaStream_t s);
     ~ProfScope();
@@ -129,6 +145,11 @@ struct fga_beams {
     fga::DevBuf state, state_alt, flags, flags_alt, id, id_alt;
     mutable fga::Workspace ws;
     cudaStream_t last_stream = nullptr;
+    // layered media: the population grows at interfaces (slots [0, counts[0]) used, capacity cap)
+    bool layered = false;
+    int gmax = 4;            // a beam is dropped at its (gmax+1)-th interface
+    double rel_min = 1e-6;   // children below rel_min of the incident amplitude are not created
+    fga::DevBuf path, counts, n_begin;  // lineage (parent*4 + child slot + 1); [slots used, overflow]
 };
 
 namespace fga {
@@ -148,10 +169,14 @@ struct SampleWindow {
 };
 fga_status launch_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps, const SampleWindow *sw,
                             cudaStream_t s);
-// records of the current state for the first n_in[c] sorted beams of each class (perm: sorted
-// position -> beam), written at rec_off[c] + (position - off_cls[c])
-fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, const int64_t n_in[4],
-                                     const int64_t rec_off[4], void *rec, cudaStream_t s);
+// records of the current state for the first n_in[c] sorted beams of class c, which start at sorted
+// position beg[c] (perm: sorted position -> beam), written at rec_off[c] + (position - beg[c])
+fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, const int64_t beg[4],
+                                     const int64_t n_in[4], const int64_t rec_off[4], void *rec, cudaStream_t s);
+// layered.cu
+fga_status launch_layered_steps(const fga_model *m, fga_beams *b, double dt, int nsteps, cudaStream_t s);
+// layered media: refresh b->nb from the device slot counter (synchronises s)
+fga_status sync_layered_count(fga_beams *b, cudaStream_t s);
 // gather.cu
 struct BinGrid {
     float o[3];

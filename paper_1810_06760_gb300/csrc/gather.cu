@@ -40,7 +40,7 @@ __global__ void keys_kernel(BinGrid g, const TQ *__restrict__ Q, int64_t sb, int
         cell[d] = cd;
     }
     int key = (cell[0] * g.nc[1] + cell[1]) * g.nc[2] + cell[2];
-    if (!g.clamp && !inside) key = g.ncells;
+    if (!g.clamp && (!inside || (cls && (cls[b] & FL_DEAD)))) key = g.ncells;
     if (cls) key += (cls[b] & FL_CLASS_MASK) * (g.ncells + 1);
     keys[b] = key;
 }
@@ -401,11 +401,7 @@ __global__ void __launch_bounds__(128) gather_kernel(const R *__restrict__ rec, 
             R er, ei;
             gauss_phase_exp<R>(ph, hk * r2, &er, &ei);
 #pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const R ar = q[6 + 2 * d], ai = q[7 + 2 * d];
-                acc[2 * d] += ar * er - ai * ei;
-                acc[2 * d + 1] += ar * ei + ai * er;
-            }
+            for (int d = 0; d < 3; d++) cmac<R>(acc[2 * d], acc[2 * d + 1], q[6 + 2 * d], q[7 + 2 * d], er, ei);
         }
     }
 #pragma unroll
@@ -483,6 +479,7 @@ fga_status build_sum_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_s
         if (cl < nclasses) {
             const int cb = cl * (g.ncells + 1);
             plan.n_in[cl] = cs[cb + g.ncells] - cs[cb];
+            plan.beg[cl] = cs[cb];
         }
         plan.n_rec += plan.n_in[cl];
     }

@@ -18,7 +18,7 @@ struct SumPlan {
     int64_t pairs_tested = 0;            // point x candidate-beam pairs (upper bound of the work)
     // Records are kept only for beams inside the grid: class c's in-grid beams sit at sorted
     // positions off_cls[c] .. off_cls[c] + n_in[c] and get record indices rec_off[c] + (pos - off_cls[c]).
-    int64_t n_in[4] = {0, 0, 0, 0}, rec_off[4] = {0, 0, 0, 0}, n_rec = 0;
+    int64_t n_in[4] = {0, 0, 0, 0}, rec_off[4] = {0, 0, 0, 0}, n_rec = 0, beg[4] = {0, 0, 0, 0};
 };
 
 // Work split of a Gaussian sum on a tensor lattice: tiles are T0 x T1 x T2 boxes of the lattice.
@@ -29,7 +29,7 @@ struct LatticePlan {
     const int32_t *item_start = nullptr;
     const int4 *items = nullptr;
     int64_t pairs_tested = 0;
-    int64_t n_in[4] = {0, 0, 0, 0}, rec_off[4] = {0, 0, 0, 0}, n_rec = 0;
+    int64_t n_in[4] = {0, 0, 0, 0}, rec_off[4] = {0, 0, 0, 0}, n_rec = 0, beg[4] = {0, 0, 0, 0};
 };
 fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, const fga_lattice &L,
                               cudaStream_t s, LatticePlan &plan);
@@ -45,6 +45,15 @@ fga_status run_sum(Workspace &ws, const SumPlan &plan, int precision, const void
                    double k, double rw, void *u_out, cudaStream_t s, int cat = P_GATHER);
 // bucket starts copied to the host by build_sum_plan (valid after it returns)
 const int32_t *plan_host_cell_start(const Workspace &ws);
+
+// acc += a * b for complex a, b as two fused multiply-add chains (the compiler may not reassociate
+// acc + (ar br - ai bi) into FMAs itself)
+template <typename R> __device__ __forceinline__ void cmac(R &accr, R &acci, R ar, R ai, R br, R bi) {
+    accr = fma(ar, br, accr);
+    accr = fma(-ai, bi, accr);
+    acci = fma(ar, bi, acci);
+    acci = fma(ai, br, acci);
+}
 
 // exp(am) * (cos ph, sin ph).  FP32: Cody-Waite reduction of ph by 2 pi (two-part constant), then
 // the hardware sine/cosine and exponential approximations; FP64: the libm-accurate functions.

@@ -257,12 +257,9 @@ __global__ void __launch_bounds__(256) lattice_gather_kernel(const R *__restrict
                     const R4 a0 = ae[o0[q]], a1 = ae[o0[q] + 1];
                     if (pin[q] && a1.z + e.z <= rw2) {
                         if (COUNT) mine += pval[q];
-                        acc[q][0] += a0.x * e.x - a0.y * e.y;
-                        acc[q][1] += a0.x * e.y + a0.y * e.x;
-                        acc[q][2] += a0.z * e.x - a0.w * e.y;
-                        acc[q][3] += a0.z * e.y + a0.w * e.x;
-                        acc[q][4] += a1.x * e.x - a1.y * e.y;
-                        acc[q][5] += a1.x * e.y + a1.y * e.x;
+                        cmac<R>(acc[q][0], acc[q][1], a0.x, a0.y, e.x, e.y);
+                        cmac<R>(acc[q][2], acc[q][3], a0.z, a0.w, e.x, e.y);
+                        cmac<R>(acc[q][4], acc[q][5], a1.x, a1.y, e.x, e.y);
                     }
                 }
             }
@@ -350,6 +347,7 @@ fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *ce
     for (int cl = 0; cl < 4; cl++) {
         const int cb = cl * (g.ncells + 1);
         plan.n_in[cl] = cs[cb + g.ncells] - cs[cb];
+        plan.beg[cl] = cs[cb];
         plan.rec_off[cl] = plan.n_rec;
         plan.n_rec += plan.n_in[cl];
     }

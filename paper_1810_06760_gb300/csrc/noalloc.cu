@@ -162,6 +162,10 @@ extern "C" fga_status fga_reconstruct_noalloc(const fga_beams *b, const double *
                                               fga_stream_t s_) {
     cudaStream_t s = (cudaStream_t)s_;
     FGA_CHECK(b, "fga_reconstruct_noalloc: NULL beams");
+    if (b->layered) {
+        set_error("fga_reconstruct_noalloc: beams of a layered medium are not supported");
+        return FGA_ERR_UNSUPPORTED;
+    }
     FGA_CHECK(n >= 0, "fga_reconstruct_noalloc: n < 0");
     if (n == 0) return FGA_OK;
     FGA_CHECK(n <= NA_MAX_POINTS,

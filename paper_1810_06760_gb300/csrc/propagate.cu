@@ -130,8 +130,8 @@ fga_status launch_propagate(const fga_model *m, fga_beams *b, double dt, int nst
     return FGA_OK;
 }
 
-fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, const int64_t n_in[4],
-                                     const int64_t rec_off[4], void *rec, cudaStream_t s) {
+fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, const int64_t beg[4],
+                                     const int64_t n_in[4], const int64_t rec_off[4], void *rec, cudaStream_t s) {
     const int T = 256;
     for (int cls = 0; cls < 4; cls++) {
         const int64_t nc = n_in[cls];
@@ -142,18 +142,18 @@ fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, co
             double *dst = (double *)rec + rec_off[cls] * REC;
             if (cls < 2)
                 records_kernel<double, 0><<<blocks, T, 0, s>>>(b->state.as<double>(), b->flags.as<int32_t>(), b->cap,
-                                                               perm, b->off_cls[cls], nc, b->w, dst);
+                                                               perm, beg[cls], nc, b->w, dst);
             else
                 records_kernel<double, 1><<<blocks, T, 0, s>>>(b->state.as<double>(), b->flags.as<int32_t>(), b->cap,
-                                                               perm, b->off_cls[cls], nc, b->w, dst);
+                                                               perm, beg[cls], nc, b->w, dst);
         } else {
             float *dst = (float *)rec + rec_off[cls] * REC;
             if (cls < 2)
                 records_kernel<float, 0><<<blocks, T, 0, s>>>(b->state.as<float>(), b->flags.as<int32_t>(), b->cap,
-                                                              perm, b->off_cls[cls], nc, (float)b->w, dst);
+                                                              perm, beg[cls], nc, (float)b->w, dst);
             else
                 records_kernel<float, 1><<<blocks, T, 0, s>>>(b->state.as<float>(), b->flags.as<int32_t>(), b->cap,
-                                                              perm, b->off_cls[cls], nc, (float)b->w, dst);
+                                                              perm, beg[cls], nc, (float)b->w, dst);
         }
     }
     FGA_CUDA(cudaGetLastError());

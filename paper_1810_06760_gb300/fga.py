@@ -21,10 +21,11 @@ FGA_OK, FGA_ERR_INVALID_ARG, FGA_ERR_OOM, FGA_ERR_CUDA, FGA_ERR_TIMEOUT, FGA_ERR
 PREC_FP32, PREC_FP64 = 0, 1
 MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
 EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_propagate", "fga_reconstruct",
-            "fga_reconstruct_lattice", "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export", "fga_beams_destroy", "fga_bin",
-            "fga_profile_enable", "fga_profile_read", "fga_last_error", "fga_version"]
+            "fga_reconstruct_lattice", "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export",
+            "fga_beams_export_all", "fga_beams_destroy", "fga_bin", "fga_profile_enable", "fga_profile_read",
+            "fga_solve_vjp", "fga_last_error", "fga_version"]
 PROFILE_CATEGORIES = ["decompose", "propagate", "binning", "records", "gauss_sum", "gauss_reduce", "gauss_sum_state",
-                      "unused"]
+                      "interfaces", "adjoint_forward", "adjoint_reverse", "adjoint_init", "unused"]
 
 
 class FGAError(RuntimeError):
@@ -44,11 +45,12 @@ class InitDesc(C.Structure):
     _fields_ = [("k", C.c_double), ("ny", C.c_int * 3), ("y0", C.c_double * 3), ("dy", C.c_double * 3),
                 ("f", C.c_void_p), ("g", C.c_void_p), ("nq", C.c_int), ("q0", C.c_double * 3),
                 ("dq", C.c_double * 3), ("np", C.c_int), ("p0", C.c_double * 3), ("dp", C.c_double * 3),
-                ("class_mask", C.c_uint), ("precision", C.c_int)]
+                ("class_mask", C.c_uint), ("precision", C.c_int), ("max_interfaces", C.c_int),
+                ("child_rel_min", C.c_double), ("growth", C.c_double)]
 
 
 class Profile(C.Structure):
-    _fields_ = [("launches", C.c_int64), ("count", C.c_int64 * 8), ("ms", C.c_double * 8),
+    _fields_ = [("launches", C.c_int64), ("count", C.c_int64 * 12), ("ms", C.c_double * 12),
                 ("beam_steps", C.c_int64), ("pairs_in_window", C.c_int64), ("pairs_tested", C.c_int64)]
 
 
@@ -93,8 +95,10 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_reconstruct_noalloc.argtypes = [vp, vp, i64, C.c_double, vp, vp]
     L.fga_reconstruct_lattice.argtypes = [vp, C.POINTER(Lattice), C.c_double, vp, vp]
     L.fga_solve.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(SolveDesc), vp, vp, vp]
+    L.fga_solve_vjp.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(SolveDesc), vp, vp, vp, i32, vp]
     L.fga_beams_count.argtypes = [vp, vp]
     L.fga_beams_export.argtypes = [vp, vp, vp]
+    L.fga_beams_export_all.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
     L.fga_beams_destroy.argtypes = [vp]
     L.fga_bin.argtypes = [vp, i64, vp, C.c_float, vp, vp, vp, vp, vp]
     L.fga_profile_enable.argtypes = [i32]
@@ -163,6 +167,7 @@ class Model:
             d.z_interfaces, d.layer_cp, d.layer_cs, d.layer_rho = [a.ctypes.data for a in arrs]
         h = C.c_void_p()
         _check(lib().fga_model_create(C.byref(h), C.byref(d), _dptr(gp), _dptr(gs), _stream(stream)))
+        self.grid_shape = tuple(gp.shape[:3]) if gp is not None else None
         self.h = h
         self.kind = kind
 
@@ -181,6 +186,9 @@ class Model:
 def model_from_medium(med, device="cuda") -> Model:
     """Model from a ``workloads.Medium``."""
     import torch
+    if med.kind == "layered":
+        return Model("layered", z_interfaces=med.z_interfaces, layer_cp=med.layer_cp, layer_cs=med.layer_cs,
+                     layer_rho=med.layer_rho)
     if med.kind == "grid":
         gp = torch.as_tensor(med.grid_p, device=device)
         gs = torch.as_tensor(med.grid_s, device=device)
@@ -204,6 +212,11 @@ def init_desc(k, f, g, y0, dy, mesh, classes: Sequence[int], precision: int) -> 
     return d
 
 
+def set_layered_options(desc: InitDesc, max_interfaces: int = 0, child_rel_min: float = 0.0, growth: float = 0.0):
+    desc.max_interfaces, desc.child_rel_min, desc.growth = int(max_interfaces), float(child_rel_min), float(growth)
+    return desc
+
+
 class Beams:
     """Handle of a beam set (fga_decompose ... fga_beams_destroy)."""
 
@@ -222,6 +235,20 @@ class Beams:
         meta = np.zeros(n, dtype=np.int32)
         _check(lib().fga_beams_export(self.h, st.ctypes.data, meta.ctypes.data))
         return st, meta
+
+    def export_all(self):
+        """Live beams in storage order: (state [n,48], meta [n], mesh_id [n], path [n], dropped)."""
+        n = C.c_int64()
+        dropped = C.c_int64()
+        _check(lib().fga_beams_export_all(self.h, 0, C.byref(n), C.byref(dropped), None, None, None, None))
+        cnt = n.value
+        st = np.zeros((cnt, 48))
+        meta = np.zeros(cnt, dtype=np.int32)
+        mid = np.zeros(cnt, dtype=np.int64)
+        path = np.zeros(cnt, dtype=np.int64)
+        _check(lib().fga_beams_export_all(self.h, cnt, C.byref(n), C.byref(dropped), st.ctypes.data, meta.ctypes.data,
+                                          mid.ctypes.data, path.ctypes.data))
+        return st, meta, mid, path, dropped.value
 
     def close(self):
         if getattr(self, "h", None):
@@ -326,6 +353,35 @@ def solve(model: Model, desc: InitDesc, dt: float, nsteps: int, times, rx=None, 
     return seis_out, snap_out
 
 
+def solve_vjp(model: Model, desc: InitDesc, dt: float, nsteps: int, times, rx, ubar, grad_p=None, grad_s=None,
+              rw: float = 0.0, checkpoint_every: int = 20, stream=None):
+    """Reverse mode of the seismograms of `solve` (receivers as points rx [n_rx, 3], CUDA float64) with
+    respect to the model's node fields.  ubar: CUDA complex [n_times, n_rx, 3] in the init precision
+    (dL/dRe u + i dL/dIm u).  Adds into grad_p / grad_s (CUDA float64 [n0, n1, n2, 10], created zeroed
+    when None; None is returned for both with a constant medium) and returns them."""
+    import torch
+    times = np.ascontiguousarray(times, dtype=np.float64)
+    sd = SolveDesc()
+    sd.dt, sd.nsteps = float(dt), int(nsteps)
+    sd.n_times, sd.times = times.size, times.ctypes.data
+    sd.n_rx, sd.rx = rx.shape[0], _dptr(rx)
+    sd.rw = float(rw)
+    ub = ubar.contiguous()
+    assert ub.dtype == _cdtype(desc.precision) and tuple(ub.shape) == (times.size, rx.shape[0], 3)
+    if model.kind == "grid":
+        shape = tuple(model.grid_shape) + (10,)
+        dev = ub.device
+        if grad_p is None:
+            grad_p = torch.zeros(shape, dtype=torch.float64, device=dev)
+        if grad_s is None:
+            grad_s = torch.zeros(shape, dtype=torch.float64, device=dev)
+        assert grad_p.dtype == torch.float64 and grad_p.is_contiguous() and tuple(grad_p.shape) == shape
+        assert grad_s.dtype == torch.float64 and grad_s.is_contiguous() and tuple(grad_s.shape) == shape
+    _check(lib().fga_solve_vjp(model.h, C.byref(desc), C.byref(sd), _dptr(ub), _dptr(grad_p), _dptr(grad_s),
+                               int(checkpoint_every), _stream(stream)))
+    return grad_p, grad_s
+
+
 def profile_enable(mode: int) -> None:
     """0 off, 1 counters incl. in-window pairs, 2 counters + per-kernel CUDA-event device times, 3 both."""
     _check(lib().fga_profile_enable(int(mode)))
@@ -335,8 +391,8 @@ def profile_read(reset: bool = True) -> dict:
     p = Profile()
     _check(lib().fga_profile_read(C.byref(p), int(bool(reset))))
     return {"launches": p.launches,
-            "count": {n: p.count[i] for i, n in enumerate(PROFILE_CATEGORIES[:7])},
-            "ms": {n: p.ms[i] for i, n in enumerate(PROFILE_CATEGORIES[:7])},
+            "count": {n: p.count[i] for i, n in enumerate(PROFILE_CATEGORIES[:11])},
+            "ms": {n: p.ms[i] for i, n in enumerate(PROFILE_CATEGORIES[:11])},
             "beam_steps": p.beam_steps, "pairs_in_window": p.pairs_in_window, "pairs_tested": p.pairs_tested}
 
 

@@ -75,6 +75,10 @@ class Medium:
     grid_s: Optional[np.ndarray] = None
     origin: Sequence[float] = (0.0, 0.0, 0.0)
     spacing: Sequence[float] = (1.0, 1.0, 1.0)
+    z_interfaces: Sequence[float] = ()
+    layer_cp: Sequence[float] = ()
+    layer_cs: Sequence[float] = ()
+    layer_rho: Sequence[float] = ()
 
 
 def sine_fields_on_nodes(n: int, c0: float, amp: float, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
@@ -198,3 +202,111 @@ def smooth(nq: int = 24, np_: int = 8, ny: int = 128, nsteps: int = 400, dt: flo
 def random_points(n: int, lo, hi, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=(n, 3))
+
+
+def explosive_source(y0, dy, ny: int, x0, ell: float, sigma: float) -> np.ndarray:
+    """u0 = grad[exp(-r^2/(2 sigma^2)) cos(2 pi r/ell)], r = |y - x0| (the radially symmetric source form
+    of the paper's layered-Earth example), on the y grid: complex [ny, ny, ny, 3]."""
+    ax = [y0[a] + dy[a] * np.arange(ny) for a in range(3)]
+    Y = np.stack(np.meshgrid(*ax, indexing="ij"), -1) - np.asarray(x0)
+    r = np.sqrt(np.sum(Y * Y, -1))
+    rs = np.where(r == 0, 1.0, r)
+    dphi = np.exp(-r * r / (2 * sigma * sigma)) * (-r / sigma ** 2 * np.cos(2 * np.pi * r / ell)
+                                                   - 2 * np.pi / ell * np.sin(2 * np.pi * r / ell))
+    return (dphi / rs)[..., None] * Y + 0j
+
+
+def layered(nq: int = 4, np_: int = 6, ny: int = 32, nsteps: int = 60, dt: float = 0.05, n_times: int = 12,
+            rx_side: int = 8, extent: float = 40.0, classes=(0, 1, 2, 3)) -> Workload:
+    """Flat 3-layer crust in km and s: 0-15 km (c_p 5.8, c_s 3.46, rho 2.72), 15-35 km (6.5, 3.85, 2.92),
+    half-space (8.04, 4.47, 3.32); depth is x3.  Explosive source at 10 km depth with dominant
+    frequency 2 Hz: ell = c_p/2 Hz = 2.9 km, sigma = 0.45 ell, k = 2 pi/ell; v0 = 0.  The wavefront is
+    spherical, so the p-mesh is the cube [-1.5, 1.5]^3 and the q-mesh spans the source.  Receivers on
+    an rx_side^2 lattice at the surface spanning +-extent/2 km; samples on step ends."""
+    ell = 5.8 / 2.0
+    sigma = 0.45 * ell
+    k = 2 * math.pi / ell
+    x0 = np.array([0.0, 0.0, 10.0])
+    half = 3.2 * sigma
+    y0, dy = _ygrid(x0, half, ny)
+    f = explosive_source(y0, dy, ny, x0, ell, sigma)
+    mesh = centred_mesh(nq, x0, np_, [0.0, 0.0, 0.0], 2.2 * sigma, 1.5)
+    med = Medium("layered", z_interfaces=(15.0, 35.0), layer_cp=(5.8, 6.5, 8.04), layer_cs=(3.46, 3.85, 4.47),
+                 layer_rho=(2.72, 2.92, 3.32))
+    T = dt * nsteps
+    every = max(1, nsteps // n_times)
+    times = dt * np.arange(every, nsteps + 1, every)
+    r = np.linspace(-extent / 2, extent / 2, rx_side)
+    R1, R2 = np.meshgrid(r, r, indexing="ij")
+    rx = np.stack([R1.ravel(), R2.ravel(), np.zeros(R1.size)], -1)
+    return Workload("layered", k, med, ny, y0, dy, f, None, mesh, tuple(classes), dt, nsteps, times, rx,
+                    window_radius(k), None, (r, r, np.zeros(1)), None)
+
+
+def _bump_fields(fields: np.ndarray, n: int, centre, sigma: float, eps: float, lo: float = 0.0,
+                 hi: float = 1.0) -> np.ndarray:
+    """Fields (c, grad c, Hess c) of c * (1 + eps exp(-|x - centre|^2 / (2 sigma^2))) by the product rule,
+    from the fields of c on the same n^3 node grid over [lo, hi]^3."""
+    x = np.linspace(lo, hi, n)
+    X = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1) - np.asarray(centre, dtype=np.float64)
+    e = np.exp(-np.sum(X * X, -1) / (2.0 * sigma * sigma))
+    s = 1.0 + eps * e
+    gs = (eps * e / sigma ** 2)[..., None] * -X                        # grad s
+    Hs = (eps * e)[..., None, None] * (X[..., :, None] * X[..., None, :] / sigma ** 4 - np.eye(3) / sigma ** 2)
+    F = fields.astype(np.float64)
+    c = F[..., 0]
+    gc = F[..., 1:4]
+    iu = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    Hc = np.zeros(c.shape + (3, 3))
+    for f, (a, b) in enumerate(iu):
+        Hc[..., a, b] = Hc[..., b, a] = F[..., 4 + f]
+    out = np.empty_like(F)
+    out[..., 0] = c * s
+    out[..., 1:4] = s[..., None] * gc + c[..., None] * gs
+    Ht = (s[..., None, None] * Hc + gc[..., :, None] * gs[..., None, :] + gs[..., :, None] * gc[..., None, :]
+          + c[..., None, None] * Hs)
+    for f, (a, b) in enumerate(iu):
+        out[..., 4 + f] = Ht[..., a, b]
+    return out.astype(np.float32)
+
+
+def crosswell(n_src_side: int = 4, nq: int = 12, np_: int = 8, ny: int = 128, nsteps: int = 200,
+              dt: float = 0.0025, k: float = 64.0, grid_n: int = 64, rx_side: int = 16, n_times: int = 100,
+              classes=(0, 1, 2, 3), src_x1: float = 0.1, rx_x1: float = 0.9, times=None, v0=None,
+              src_offset=(0.0, 0.0)):
+    """Crosswell geometry for the adjoint: the smooth medium (c_p = 2 + 0.2 sin sin sin, c_s = c_p/sqrt 3)
+    on a grid_n^3 node grid is the background; the true medium multiplies c_p and c_s by
+    1 + 0.05 exp(-|x - (.5,.5,.5)|^2 / (2 0.1^2)).  Sources on an n_src_side^2 lattice in the plane
+    x1 = src_x1 (shifted by src_offset in x2, x3), each a packet travelling along e1 with the polarisation
+    of the smooth workload (P and S excited); v0 = None gives zero initial velocity, else g = v0 * f.
+    Receivers on an rx_side^2 lattice in the plane x1 = rx_x1; samples t_j = (j+1) T / n_times unless
+    `times` is given.  Returns (list of per-source Workloads on the background, true Medium)."""
+    gp = sine_fields_on_nodes(grid_n, 2.0, 0.2)
+    gs = (gp.astype(np.float64) / SQRT3).astype(np.float32)
+    h = 1.0 / (grid_n - 1)
+    back = Medium("grid", grid_p=gp, grid_s=gs, origin=(0.0, 0.0, 0.0), spacing=(h, h, h))
+    tp = _bump_fields(gp, grid_n, (0.5, 0.5, 0.5), 0.1, 0.05)
+    ts = (tp.astype(np.float64) / SQRT3).astype(np.float32)
+    true = Medium("grid", grid_p=tp, grid_s=ts, origin=(0.0, 0.0, 0.0), spacing=(h, h, h))
+    dhat = np.array([1.0, 0.0, 0.0])
+    b = np.array([0.2, -0.5, 1.0])
+    b = b / np.linalg.norm(b)
+    T = dt * nsteps
+    if times is None:
+        times = T * np.arange(1, n_times + 1) / n_times
+    times = np.asarray(times, dtype=np.float64)
+    r = (np.arange(rx_side) + 0.5) / rx_side
+    R1, R2 = np.meshgrid(r, r, indexing="ij")
+    rx = np.stack([np.full(R1.size, rx_x1), R1.ravel(), R2.ravel()], -1)
+    out = []
+    sp = (np.arange(n_src_side) + 0.5) / n_src_side
+    for a in sp:
+        for c in sp:
+            x0 = np.array([src_x1, a + src_offset[0], c + src_offset[1]])
+            y0, dy = _ygrid(x0, window_radius(k), ny)
+            f = _packet(y0, dy, ny, k, x0, b, dhat)
+            g = None if v0 is None else v0 * f
+            mesh = centred_mesh(nq, x0, np_, dhat, mesh_radius(k, 6.0), mesh_radius(k, 4.8))
+            out.append(Workload("crosswell", k, back, ny, y0, dy, f, g, mesh, tuple(classes), dt, nsteps, times,
+                                rx, window_radius(k)))
+    return out, true
