@@ -801,6 +801,7 @@ extern "C" fga_status fga_solve_vjp(const fga_model *m, const fga_init_desc *ini
         fga_init_desc d2 = *init;
         d2.f = guard.zero.p;
         FGA_TRY(decompose_impl(m, &d2, &bg, s));
+        FGA_CHECK(bg->cap == b->cap && bg->nb == b->nb, "fga_solve_vjp: internal beam layout mismatch");
     }
     if (b->precision == FGA_PREC_FP64) {
         if (kind == FGA_MEDIUM_GRID)
