@@ -205,6 +205,54 @@ fga_status fga_beams_destroy(fga_beams *b);
 fga_status fga_beams_export_all(const fga_beams *b, int64_t cap, int64_t *n_out, int64_t *dropped, double *state,
                                 int32_t *meta, int64_t *mesh_id, int64_t *path);
 
+/* Serving loop for forward solves (no counterpart in the paper; the paper runs one solve at a time).
+ * Requests (a decomposition descriptor plus a solve descriptor, as for fga_solve, each with its own
+ * source data, k, mesh, sample times and receivers) share one resident model.  A request's peak
+ * device memory is estimated from its sizes; requests start in submission order while the running
+ * ones fit hbm_budget_bytes (<= 0: 85% of the free device memory at creation); one that exceeds the
+ * budget on its own runs when nothing else runs.  n_workers threads each own a non-blocking stream
+ * and run one request at a time, so up to n_workers solves share the GPU; record_cap_bytes (<= 0:
+ * 2e9) caps each solve's per-window record buffer.  The caller keeps every buffer a request names
+ * (f, g, receivers, snapshot points, outputs; all DEVICE as for fga_solve) alive and untouched until
+ * fga_server_wait returns for it; the times array is copied at submission.  Layered media are not
+ * served.  Kernel profiling (fga_profile_enable) must be off while a server runs.
+ *  fga_server_wait blocks until the request is done (timeout_s <= 0: no limit; else FGA_ERR_TIMEOUT),
+ *  returns the request's own status and fills info (may be NULL); a request id can be waited once.
+ *  fga_server_destroy finishes the queued requests, then stops the workers. */
+typedef struct {
+    int n_workers;
+    double hbm_budget_bytes;
+    double record_cap_bytes;
+} fga_server_desc;
+
+typedef struct {
+    int status;       /* the request's fga_status */
+    int worker;       /* worker that ran it */
+    double t_submit;  /* seconds since the server was created (host steady clock) */
+    double t_start;
+    double t_end;     /* after the request's stream drained */
+    double bytes;     /* estimated peak device memory */
+    int64_t beams;
+} fga_request_info;
+
+typedef struct {
+    int64_t queued;
+    int64_t running;
+    int64_t completed;
+    int64_t peak_running;
+    double inflight_bytes;
+    double peak_bytes;
+    double budget_bytes;
+} fga_server_stats_t;
+
+typedef struct fga_server fga_server;
+fga_status fga_server_create(fga_server **out, const fga_model *m, const fga_server_desc *d);
+fga_status fga_server_submit(fga_server *sv, const fga_init_desc *init, const fga_solve_desc *sd, void *seis_out,
+                             void *snap_out, int64_t *id);
+fga_status fga_server_wait(fga_server *sv, int64_t id, double timeout_s, fga_request_info *info);
+fga_status fga_server_stats(fga_server *sv, fga_server_stats_t *out);
+fga_status fga_server_destroy(fga_server *sv);
+
 /* Reverse mode of fga_solve's seismograms (no counterpart in the paper, which uses the method as the
  * forward model of tomography and waveform inversion and leaves the adjoint to that literature).
  * For a cotangent ubar of the seismograms, DEVICE complex [n_times][n_rx][3] in the init

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "fga_beam.cuh"
@@ -22,11 +23,73 @@ fga_status cuda_fail(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? FGA_ERR_OOM : FGA_ERR_CUDA;
 }
 
+// Per-thread block cache.  Off by default: every DevBuf/HostBuf then maps to cudaMalloc/cudaFree
+// (whose implicit device synchronisation also orders reuse).  A thread that issues all its work on
+// one stream (a server worker) turns it on: released blocks go to the thread's cache and are handed
+// back to later allocations of the same thread, whose work is ordered after every earlier use on
+// that stream, so no allocation or free stalls the other streams.  Pinned host blocks are cached only
+// after the stream has drained (the host writes into them).
+namespace {
+struct BlockCache {
+    bool on = false;
+    cudaStream_t stream = nullptr;
+    std::multimap<size_t, void *> dev, host;
+    size_t dev_bytes = 0, host_bytes = 0;
+};
+thread_local BlockCache tl_cache;
+// a cached block of at least need bytes and not much larger; its size goes to *size
+void *cache_take(std::multimap<size_t, void *> &c, size_t &total, size_t need, size_t *size) {
+    auto it = c.lower_bound(need);
+    if (it == c.end() || it->first > 2 * need + ((size_t)1 << 20)) return nullptr;
+    void *p = it->second;
+    *size = it->first;
+    total -= it->first;
+    c.erase(it);
+    return p;
+}
+}  // namespace
+
+void block_cache_enable(cudaStream_t s) {
+    tl_cache.on = true;
+    tl_cache.stream = s;
+}
+size_t block_cache_bytes() { return tl_cache.dev_bytes; }
+void block_cache_trim(size_t keep) {
+    // largest blocks first
+    while (tl_cache.dev_bytes > keep && !tl_cache.dev.empty()) {
+        auto it = std::prev(tl_cache.dev.end());
+        cudaFree(it->second);
+        tl_cache.dev_bytes -= it->first;
+        tl_cache.dev.erase(it);
+    }
+}
+void block_cache_disable() {
+    block_cache_trim(0);
+    for (auto &kv : tl_cache.host) cudaFreeHost(kv.second);
+    tl_cache.host.clear();
+    tl_cache.host_bytes = 0;
+    tl_cache.on = false;
+    tl_cache.stream = nullptr;
+}
+
 fga_status DevBuf::ensure(size_t need) {
     if (need <= bytes && p) return FGA_OK;
     release();
     if (need == 0) need = 16;
+    if (tl_cache.on) {
+        size_t got = 0;
+        if (void *q = cache_take(tl_cache.dev, tl_cache.dev_bytes, need, &got)) {
+            p = q;
+            bytes = got;
+            return FGA_OK;
+        }
+    }
     cudaError_t e = cudaMalloc(&p, need);
+    if (e == cudaErrorMemoryAllocation && tl_cache.on && tl_cache.dev_bytes > 0) {
+        cudaGetLastError();
+        block_cache_trim(0);
+        e = cudaMalloc(&p, need);
+    }
     if (e != cudaSuccess) {
         p = nullptr;
         bytes = 0;
@@ -40,7 +103,14 @@ fga_status DevBuf::ensure(size_t need) {
     return FGA_OK;
 }
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        if (tl_cache.on) {
+            tl_cache.dev.emplace(bytes, p);
+            tl_cache.dev_bytes += bytes;
+        } else {
+            cudaFree(p);
+        }
+    }
     p = nullptr;
     bytes = 0;
 }
@@ -48,6 +118,14 @@ fga_status HostBuf::ensure(size_t need) {
     if (need <= bytes && p) return FGA_OK;
     release();
     if (need == 0) need = 16;
+    if (tl_cache.on) {
+        size_t got = 0;
+        if (void *q = cache_take(tl_cache.host, tl_cache.host_bytes, need, &got)) {
+            p = q;
+            bytes = got;
+            return FGA_OK;
+        }
+    }
     cudaError_t e = cudaMallocHost(&p, need);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -60,7 +138,15 @@ fga_status HostBuf::ensure(size_t need) {
     return FGA_OK;
 }
 void HostBuf::release() {
-    if (p) cudaFreeHost(p);
+    if (p) {
+        if (tl_cache.on) {
+            cudaStreamSynchronize(tl_cache.stream);
+            tl_cache.host.emplace(bytes, p);
+            tl_cache.host_bytes += bytes;
+        } else {
+            cudaFreeHost(p);
+        }
+    }
     p = nullptr;
     bytes = 0;
 }
@@ -415,7 +501,15 @@ fga_status fga_reconstruct(const fga_beams *b, const double *x, int64_t n, doubl
 
 fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, void *seis_out,
                      void *snap_out, fga_stream_t s_) {
-    cudaStream_t s = (cudaStream_t)s_;
+    return solve_impl(m, init, sd, seis_out, snap_out, (cudaStream_t)s_, 12.0e9);
+}
+
+}  // extern "C"
+
+namespace fga {
+fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, void *seis_out,
+                      void *snap_out, cudaStream_t s, double rec_cap) {
+    fga_stream_t s_ = (fga_stream_t)s;
     FGA_CHECK(m && init && sd, "fga_solve: NULL argument");
     FGA_CHECK(sd->nsteps >= 1 && std::isfinite(sd->dt) && sd->dt != 0.0, "fga_solve: nsteps >= 1 and dt != 0");
     FGA_CHECK(sd->n_times >= 0 && sd->n_rx >= 0 && sd->n_snap >= 0, "fga_solve: negative counts");
@@ -522,7 +616,7 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
     // records of one window live in one buffer; cap its size
     size_t free_b = 0, total_b = 0;
     FGA_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const double rec_budget = std::min(12.0e9, 0.4 * (double)free_b);
+    const double rec_budget = std::min(rec_cap, 0.4 * (double)free_b);
     int js = 0;
     for (int n0 = 0; n0 < sd->nsteps;) {
         int nw = std::min(W, sd->nsteps - n0);
@@ -594,6 +688,9 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
     FGA_CUDA(cudaStreamSynchronize(s));
     return FGA_OK;
 }
+}  // namespace fga
+
+extern "C" {
 
 fga_status fga_beams_count(const fga_beams *b, int64_t *n_by_class) {
     FGA_CHECK(b && n_by_class, "fga_beams_count: NULL argument");

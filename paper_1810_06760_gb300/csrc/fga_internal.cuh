@@ -122,6 +122,12 @@ struct HostBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+// per-thread block cache for DevBuf/HostBuf (see api.cu); s: the one stream the thread uses
+void block_cache_enable(cudaStream_t s);
+void block_cache_disable();
+void block_cache_trim(size_t keep_bytes);
+size_t block_cache_bytes();
+
 // scratch used by binning and the Gaussian sum
 struct Workspace {
     DevBuf keys, keys_alt, vals, vals_alt, hist, scan_blocks, cell_start, rec, items, tiles, partial, pts;
@@ -173,6 +179,9 @@ fga_status launch_propagate(const fga_model *m, fga_beams *b, double dt, int nst
 // position beg[c] (perm: sorted position -> beam), written at rec_off[c] + (position - beg[c])
 fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, const int64_t beg[4],
                                      const int64_t n_in[4], const int64_t rec_off[4], void *rec, cudaStream_t s);
+// api.cu: the whole forward solve (fga_solve) with a cap on the record buffer of one window
+fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, void *seis_out,
+                      void *snap_out, cudaStream_t s, double rec_cap);
 // layered.cu
 fga_status launch_layered_steps(const fga_model *m, fga_beams *b, double dt, int nsteps, cudaStream_t s);
 // layered media: refresh b->nb from the device slot counter (synchronises s)

@@ -23,7 +23,8 @@ MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
 EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_propagate", "fga_reconstruct",
             "fga_reconstruct_lattice", "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export",
             "fga_beams_export_all", "fga_beams_destroy", "fga_bin", "fga_profile_enable", "fga_profile_read",
-            "fga_solve_vjp", "fga_last_error", "fga_version"]
+            "fga_solve_vjp", "fga_server_create", "fga_server_submit", "fga_server_wait", "fga_server_stats",
+            "fga_server_destroy", "fga_last_error", "fga_version"]
 PROFILE_CATEGORIES = ["decompose", "propagate", "binning", "records", "gauss_sum", "gauss_reduce", "gauss_sum_state",
                       "interfaces", "adjoint_forward", "adjoint_reverse", "adjoint_init", "unused"]
 
@@ -52,6 +53,20 @@ class InitDesc(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("count", C.c_int64 * 12), ("ms", C.c_double * 12),
                 ("beam_steps", C.c_int64), ("pairs_in_window", C.c_int64), ("pairs_tested", C.c_int64)]
+
+
+class ServerDesc(C.Structure):
+    _fields_ = [("n_workers", C.c_int), ("hbm_budget_bytes", C.c_double), ("record_cap_bytes", C.c_double)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("worker", C.c_int), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_end", C.c_double), ("bytes", C.c_double), ("beams", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("running", C.c_int64), ("completed", C.c_int64), ("peak_running", C.c_int64),
+                ("inflight_bytes", C.c_double), ("peak_bytes", C.c_double), ("budget_bytes", C.c_double)]
 
 
 class Lattice(C.Structure):
@@ -96,6 +111,11 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_reconstruct_lattice.argtypes = [vp, C.POINTER(Lattice), C.c_double, vp, vp]
     L.fga_solve.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(SolveDesc), vp, vp, vp]
     L.fga_solve_vjp.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(SolveDesc), vp, vp, vp, i32, vp]
+    L.fga_server_create.argtypes = [C.POINTER(vp), vp, C.POINTER(ServerDesc)]
+    L.fga_server_submit.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(SolveDesc), vp, vp, C.POINTER(i64)]
+    L.fga_server_wait.argtypes = [vp, i64, C.c_double, C.POINTER(RequestInfo)]
+    L.fga_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    L.fga_server_destroy.argtypes = [vp]
     L.fga_beams_count.argtypes = [vp, vp]
     L.fga_beams_export.argtypes = [vp, vp, vp]
     L.fga_beams_export_all.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
@@ -380,6 +400,61 @@ def solve_vjp(model: Model, desc: InitDesc, dt: float, nsteps: int, times, rx, u
     _check(lib().fga_solve_vjp(model.h, C.byref(desc), C.byref(sd), _dptr(ub), _dptr(grad_p), _dptr(grad_s),
                                int(checkpoint_every), _stream(stream)))
     return grad_p, grad_s
+
+
+class Server:
+    """Serving loop (fga_server_*): forward solves of independent requests on one resident model.
+    submit() returns a request id; wait(id) blocks until it is done and returns its timing record
+    (seconds since the server started).  Tensors a request uses are kept alive until it is waited."""
+
+    def __init__(self, model: Model, n_workers: int = 4, hbm_budget_bytes: float = 0.0,
+                 record_cap_bytes: float = 0.0):
+        d = ServerDesc(int(n_workers), float(hbm_budget_bytes), float(record_cap_bytes))
+        h = C.c_void_p()
+        _check(lib().fga_server_create(C.byref(h), model.h, C.byref(d)))
+        self.h, self.model, self._keep = h, model, {}
+
+    def submit(self, desc: InitDesc, dt: float, nsteps: int, times, rx, rw: float = 0.0, keep=()):
+        import torch
+        times = np.ascontiguousarray(times, dtype=np.float64)
+        sd = SolveDesc()
+        sd.dt, sd.nsteps = float(dt), int(nsteps)
+        sd.n_times, sd.times = times.size, times.ctypes.data if times.size else None
+        sd.n_rx, sd.rx = rx.shape[0], _dptr(rx)
+        sd.rw = float(rw)
+        out = torch.empty((times.size, rx.shape[0], 3), dtype=_cdtype(desc.precision), device=rx.device)
+        rid = C.c_int64()
+        _check(lib().fga_server_submit(self.h, C.byref(desc), C.byref(sd), _dptr(out), None, C.byref(rid)))
+        self._keep[rid.value] = (desc, times, rx, out, keep)
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = 0.0):
+        """(seismograms, info dict); raises FGAError with the request's own status on failure."""
+        info = RequestInfo()
+        st = lib().fga_server_wait(self.h, int(rid), float(timeout), C.byref(info))
+        if st == FGA_ERR_TIMEOUT:       # still queued or running: its buffers stay referenced
+            raise FGAError(st, last_error())
+        kept = self._keep.pop(rid, None)
+        if st != 0:
+            raise FGAError(st, last_error())
+        return kept[3], {"worker": info.worker, "t_submit": info.t_submit, "t_start": info.t_start,
+                         "t_end": info.t_end, "bytes": info.bytes, "beams": info.beams}
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().fga_server_stats(self.h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fga_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def profile_enable(mode: int) -> None:

@@ -310,3 +310,52 @@ def crosswell(n_src_side: int = 4, nq: int = 12, np_: int = 8, ny: int = 128, ns
             out.append(Workload("crosswell", k, back, ny, y0, dy, f, g, mesh, tuple(classes), dt, nsteps, times,
                                 rx, window_radius(k)))
     return out, true
+
+
+@dataclasses.dataclass
+class ServingRequest:
+    arrival: float            # seconds after the first arrival (rate 1; scale by 1/rate)
+    workload: Workload
+    n_target: int             # the drawn mesh size N (the realised count is workload.mesh.M)
+
+
+def serving_requests(n: int = 64, seed: int = 1, n_range=(1e5, 2e7), ks=(32.0, 64.0, 128.0), np_: int = 8,
+                     nsteps: int = 200, dt: float = 0.0025, rx_side: int = 16, n_times: int = 200,
+                     grid_n: int = 128, classes=(0, 1, 2, 3)):
+    """Request mix for the serving loop, on the smooth medium (resident, shared): arrivals of a Poisson
+    process of rate 1 (exponential gaps, seed `seed`); per request a source centre x0 uniform in
+    [0.2, 0.8]^3, k drawn from ks, N log-uniform in n_range mapped to p 8^3 and q n_q^3 with
+    n_q = round((N/512)^(1/3)), a random unit direction d and a random unit polarisation b; zero initial
+    velocity; the y grid spans x0 +- 6/sqrt(k) with ny = 8 ceil(sqrt(k)) points per axis (at least ~4
+    points per wavelength).  Receivers rx_side^2 at x3 = 0, samples t_j = (j+1) T / n_times."""
+    rng = np.random.default_rng(seed)
+    gp = sine_fields_on_nodes(grid_n, 2.0, 0.2)
+    gs = (gp.astype(np.float64) / SQRT3).astype(np.float32)
+    h = 1.0 / (grid_n - 1)
+    med = Medium("grid", grid_p=gp, grid_s=gs, origin=(0.0, 0.0, 0.0), spacing=(h, h, h))
+    r = (np.arange(rx_side) + 0.5) / rx_side
+    R1, R2 = np.meshgrid(r, r, indexing="ij")
+    rx = np.stack([R1.ravel(), R2.ravel(), np.zeros(R1.size)], -1)
+    T = dt * nsteps
+    times = T * np.arange(1, n_times + 1) / n_times
+    t = 0.0
+    out = []
+    for i in range(n):
+        if i > 0:
+            t += rng.exponential(1.0)
+        x0 = rng.uniform(0.2, 0.8, 3)
+        k = float(ks[rng.integers(len(ks))])
+        N = math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))
+        nq = max(1, int(round((N / np_ ** 3) ** (1.0 / 3.0))))
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        b = rng.normal(size=3)
+        b /= np.linalg.norm(b)
+        ny = 8 * int(math.ceil(math.sqrt(k)))
+        y0, dy = _ygrid(x0, window_radius(k), ny)
+        f = _packet(y0, dy, ny, k, x0, b, d)
+        mesh = centred_mesh(nq, x0, np_, d, mesh_radius(k, 6.0), mesh_radius(k, 4.8))
+        w = Workload("serving", k, med, ny, y0, dy, f, None, mesh, tuple(classes), dt, nsteps, times, rx,
+                     window_radius(k))
+        out.append(ServingRequest(t, w, int(round(N))))
+    return out

@@ -15,11 +15,10 @@ from tests.helpers import gpu_setup, oracle_beams, oracle_model, oracle_mesh, re
 
 pytestmark = pytest.mark.gpu
 
-# FP64: the GPU and the oracle evaluate the same discrete map in the same precision; the gradient sums
-# ~1e6 products per node in a different order (FP64 atomics), so agreement is near 1e-12.
-# FP32: the adjoint of a phase k P.(x - Q) with |k x| ~ 10 carries the FP32 rounding of the forward
-# state (~1e-6 relative in Q, P) times k |x| into every record cotangent; measured agreement ~1e-4.
-TOL = {1: 1e-10, 0: 2e-3}
+# The FP64 and FP32 bars of the forward path (relative L2 1e-10 and 1e-4 against the FP64 oracle).
+# Measured on GB300: FP64 2e-15 (same discrete map, different summation order), FP32 2e-5 (the FP32
+# rounding of the trajectory, amplified by k |x - Q| in the phase derivatives).
+TOL = {1: 1e-10, 0: 1e-4}
 
 
 @pytest.fixture(scope="module")
