@@ -43,16 +43,20 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--small", action="store_true", help="reduced sizes (debugging only; not a bench line)")
+    ap.add_argument("--size", default="full", choices=["full", "medium", "small"],
+                    help="workload size: full = the benchmark; medium (16^3 q, 8.4 M beams, 1.5 GB of state) is "
+                         "the profiler capture case; small is for debugging (neither is a bench line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def workload(small: bool):
+def workload(size: str):
     from paper_1810_06760_gb300 import workloads as W
-    if small:
+    if size == "small":
         return W.smooth(nq=8, np_=4, ny=48, nsteps=40, n_samples=100, rx_side=10, snap_side=16, grid_n=65)
+    if size == "medium":
+        return W.smooth(nq=16, nsteps=100, n_samples=250)
     return W.smooth()
 
 
@@ -179,7 +183,7 @@ def run_reference(args):
     # the oracle runs on rank 0's host cores only; other ranks exit at once (no process group needed)
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
-    w = workload(args.small)
+    w = workload(args.size)
     for _ in range(args.warmup):
         oracle_sample(w, 12, 8, n_samples_cap=50)
     vals = []
@@ -211,7 +215,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = fga.PREC_FP32 if args.precision == "fp32" else fga.PREC_FP64
-    w = workload(args.small)
+    w = workload(args.size)
     nb = w.n_beams
     beam_steps = nb * w.nsteps
     model = fga.model_from_medium(w.medium, dev)
@@ -296,7 +300,7 @@ def run_ours(args):
                 "per_launch_ms": per_launch_ms, "launches": launches}
     gauss_s = gauss_ms_total / 1e3
     line = {
-        "metric": "FGA beam-steps/s (smooth heterogeneous medium, 128^3 grid, k=64)",
+        "metric": "FGA beam-steps/s and Gaussian-sum pts/s at fixed error; p50/p99 solve latency",
         "value": value, "unit": "beam-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
@@ -348,7 +352,7 @@ def run_ours(args):
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        bs, secs, thr, desc_s = oracle_sample(w, 6, 2) if not args.small else oracle_sample(w, 4, 2)
+        bs, secs, thr, desc_s = oracle_sample(w, 6, 2) if args.size != "small" else oracle_sample(w, 4, 2)
         line["cpu_baseline"] = {"value": bs / secs, "unit": "beam-steps/s", "cores": thr, "kind": "oracle",
                                 "sample": desc_s}
     if rank == 0:

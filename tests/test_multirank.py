@@ -51,7 +51,7 @@ def _ref_worker(rank, world, q):
     import json
     import sys
     import bench
-    sys.argv = ["bench.py", "--impl", "reference", "--gpus", str(world), "--steps", "1", "--warmup", "0", "--small"]
+    sys.argv = ["bench.py", "--impl", "reference", "--gpus", str(world), "--steps", "1", "--warmup", "0", "--size", "small"]
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
         rc = bench.main()
