@@ -468,7 +468,7 @@ static fga_status reconstruct_lattice_now(const fga_beams *b, const fga_lattice 
     int32_t *perm = nullptr;
     FGA_TRY(bin_beams(b, g, &perm, s));
     LatticePlan plan;
-    FGA_TRY(build_lattice_plan(ws, g, ws.cell_start.as<int32_t>(), *L, s, plan));  // syncs
+    FGA_TRY(build_lattice_plan(ws, g, ws.cell_start.as<int32_t>(), *L, s, plan, b->precision == FGA_PREC_FP32));  // syncs
     const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
     FGA_TRY(ws.rec.ensure(rb * REC * (size_t)std::max<int64_t>(plan.n_rec, 1)));
     FGA_TRY(launch_records_from_state(b, perm, plan.beg, plan.n_in, plan.rec_off, ws.rec.p, s));
@@ -633,7 +633,7 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
         SumPlan plan;
         LatticePlan lplan;
         if (rxL) {
-            FGA_TRY(build_lattice_plan(ws, grx, ws.cell_start.as<int32_t>(), *rxL, s, lplan));  // syncs
+            FGA_TRY(build_lattice_plan(ws, grx, ws.cell_start.as<int32_t>(), *rxL, s, lplan, !fp64));  // syncs
             for (int c = 0; c < 4; c++) {
                 plan.n_in[c] = lplan.n_in[c];
                 plan.rec_off[c] = lplan.rec_off[c];
@@ -686,6 +686,10 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
         FGA_TRY(reconstruct_now(b, sd->snap, snh, sd->n_snap, rw, snap_out, s));
     // the beam set is freed by the guard; its buffers must not be in use
     FGA_CUDA(cudaStreamSynchronize(s));
+    if (read_tc_lattice_error(true)) {
+        set_error("fga_solve: a tensor-core wait of the Gaussian sum ran out");
+        return FGA_ERR_TIMEOUT;
+    }
     return FGA_OK;
 }
 }  // namespace fga
@@ -820,7 +824,8 @@ fga_status fga_profile_read(fga_profile_t *out, int reset) {
     }
     out->beam_steps = g_prof.beam_steps;
     out->pairs_tested = g_prof.pairs_tested;
-    out->pairs_in_window = read_pair_counter(reset != 0) + read_lattice_pair_counter(reset != 0);
+    out->pairs_in_window =
+        read_pair_counter(reset != 0) + read_lattice_pair_counter(reset != 0) + read_tc_pair_counter(reset != 0);
     if (reset) {
         g_prof.launches = g_prof.beam_steps = g_prof.pairs_tested = 0;
         for (int c = 0; c < P_NCAT; c++) {

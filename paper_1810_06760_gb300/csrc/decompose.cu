@@ -103,22 +103,87 @@ static fga_status cgemm(const TA *A, int64_t sAz, int64_t sAm, int64_t sAk, cons
 }
 
 // F[a0][a1][a2][c] = dy^3 sum_y f[y0][y1][y2][c] K0[a0][y0] K1[a1][y1] K2[a2][y2]
+// The three stages (contract y2, then y1, then y0) are batched strided complex GEMMs: on the tensor
+// cores (FP16 split, FP32 accumulation) for the FP32 path, on the FP64 pipe for the FP64 path.
+struct TransformScratch {
+    float *amax = nullptr;   // DEVICE: max |Re|, |Im| of the input
+    int *err = nullptr;      // DEVICE: set by a tensor-core wait that ran out
+    double S[3] = {1, 1, 1}; // max over kernel rows of sum_i |K_d[a][i]| per axis (bounds of the stages)
+};
+
+template <typename R>
+static fga_status stage_gemm(const double2 *A, int64_t sAz, int64_t sAm, int64_t sAk, const C2<R> *B, int64_t sBn,
+                             int64_t sBk, C2<R> *Cm, int64_t sCz, int64_t sCm, int64_t sCn, int Z, int64_t M, int N,
+                             int K, R scale, const TransformScratch &ts, double factor, cudaStream_t s);
+template <typename R>
+static fga_status stage_gemm(const C2<R> *A, int64_t sAz, int64_t sAm, int64_t sAk, const C2<R> *B, int64_t sBn,
+                             int64_t sBk, C2<R> *Cm, int64_t sCz, int64_t sCm, int64_t sCn, int Z, int64_t M, int N,
+                             int K, R scale, const TransformScratch &ts, double factor, cudaStream_t s);
+
+template <>
+fga_status stage_gemm<double>(const double2 *A, int64_t sAz, int64_t sAm, int64_t sAk, const C2<double> *B,
+                              int64_t sBn, int64_t sBk, C2<double> *Cm, int64_t sCz, int64_t sCm, int64_t sCn, int Z,
+                              int64_t M, int N, int K, double scale, const TransformScratch &, double, cudaStream_t s) {
+    return cgemm<double, double2>(A, sAz, sAm, sAk, B, sBn, sBk, Cm, sCz, sCm, sCn, Z, M, N, K, scale, s);
+}
+template <>
+fga_status stage_gemm<double>(const C2<double> *A, int64_t sAz, int64_t sAm, int64_t sAk, const C2<double> *B,
+                              int64_t sBn, int64_t sBk, C2<double> *Cm, int64_t sCz, int64_t sCm, int64_t sCn, int Z,
+                              int64_t M, int N, int K, double scale, const TransformScratch &, double, cudaStream_t s) {
+    return cgemm<double, C2<double>>(A, sAz, sAm, sAk, B, sBn, sBk, Cm, sCz, sCm, sCn, Z, M, N, K, scale, s);
+}
+template <>
+fga_status stage_gemm<float>(const double2 *A, int64_t sAz, int64_t sAm, int64_t sAk, const C2<float> *B, int64_t sBn,
+                             int64_t sBk, C2<float> *Cm, int64_t sCz, int64_t sCm, int64_t sCn, int Z, int64_t M, int N,
+                             int K, float scale, const TransformScratch &ts, double factor, cudaStream_t s) {
+    return tc_cgemm<double2>(A, sAz, sAm, sAk, reinterpret_cast<const float2 *>(B), sBn, sBk,
+                             reinterpret_cast<float2 *>(Cm), sCz, sCm, sCn, Z, M, N, K, scale, ts.amax, (float)factor,
+                             ts.err, s);
+}
+template <>
+fga_status stage_gemm<float>(const C2<float> *A, int64_t sAz, int64_t sAm, int64_t sAk, const C2<float> *B,
+                             int64_t sBn, int64_t sBk, C2<float> *Cm, int64_t sCz, int64_t sCm, int64_t sCn, int Z,
+                             int64_t M, int N, int K, float scale, const TransformScratch &ts, double factor,
+                             cudaStream_t s) {
+    return tc_cgemm<float2>(reinterpret_cast<const float2 *>(A), sAz, sAm, sAk, reinterpret_cast<const float2 *>(B),
+                            sBn, sBk, reinterpret_cast<float2 *>(Cm), sCz, sCm, sCn, Z, M, N, K, scale, ts.amax,
+                            (float)factor, ts.err, s);
+}
+
 template <typename R>
 static fga_status fbi_transform(const fga_init_desc *d, const double2 *f, C2<R> *const Kax[3], C2<R> *T1, C2<R> *T2,
-                                C2<R> *F, cudaStream_t s) {
+                                C2<R> *F, const TransformScratch &ts, cudaStream_t s) {
     const int A = d->nq * d->np;
     const int n0 = d->ny[0], n1 = d->ny[1], n2 = d->ny[2];
+    if (sizeof(R) == 4) FGA_TRY(tc_absmax(f, (int64_t)n0 * n1 * n2 * 3, ts.amax, s));
+    // |Re|, |Im| of a stage's output <= sqrt(2) max(|Re|, |Im|) of its input x sum_i |K[a][i]|
+    const double g1 = std::sqrt(2.0) * ts.S[2], g2 = g1 * std::sqrt(2.0) * ts.S[1];
     // stage 1 (contract y2), one GEMM per component c: T1[(y0,y1)][a2][c]
-    FGA_TRY((cgemm<R, double2>(f, 1, (int64_t)n2 * 3, 3, Kax[2], n2, 1, T1, 1, (int64_t)A * 3, 3, 3,
-                               (int64_t)n0 * n1, A, n2, R(1), s)));
+    FGA_TRY((stage_gemm<R>(f, 1, (int64_t)n2 * 3, 3, Kax[2], n2, 1, T1, 1, (int64_t)A * 3, 3, 3, (int64_t)n0 * n1, A,
+                           n2, R(1), ts, 1.0, s)));
     // stage 2 (contract y1): T2[y0][a1][(a2,c)] ; batch y0, m = (a2,c), n = a1, k = y1
-    FGA_TRY((cgemm<R, C2<R>>(T1, (int64_t)n1 * A * 3, 1, (int64_t)A * 3, Kax[1], n1, 1, T2, (int64_t)A * A * 3, 1,
-                              (int64_t)A * 3, n0, (int64_t)A * 3, A, n1, R(1), s)));
+    FGA_TRY((stage_gemm<R>((const C2<R> *)T1, (int64_t)n1 * A * 3, 1, (int64_t)A * 3, Kax[1], n1, 1, T2,
+                           (int64_t)A * A * 3, 1, (int64_t)A * 3, n0, (int64_t)A * 3, A, n1, R(1), ts, g1, s)));
     // stage 3 (contract y0): F[a0][(a1,a2,c)], m = (a1,a2,c), n = a0, k = y0
     const R vol = (R)(d->dy[0] * d->dy[1] * d->dy[2]);
-    FGA_TRY((cgemm<R, C2<R>>(T2, 0, 1, (int64_t)A * A * 3, Kax[0], n0, 1, F, 0, 1, (int64_t)A * A * 3, 1,
-                              (int64_t)A * A * 3, A, n0, vol, s)));
+    FGA_TRY((stage_gemm<R>((const C2<R> *)T2, 0, 1, (int64_t)A * A * 3, Kax[0], n0, 1, F, 0, 1, (int64_t)A * A * 3, 1,
+                           (int64_t)A * A * 3, A, n0, vol, ts, g2, s)));
     return FGA_OK;
+}
+
+// max over the q nodes of sum_i exp(-k (y_i - q)^2 / 2): the largest row sum of |K| on one axis
+static double kernel_row_sum_max(int nq, double q0, double dq, int ny, double y0, double dy, double k) {
+    double best = 0.0;
+    for (int iq = 0; iq < nq; iq++) {
+        const double q = q0 + iq * dq;
+        double sum = 0.0;
+        for (int i = 0; i < ny; i++) {
+            const double t = y0 + i * dy - q;
+            sum += std::exp(-0.5 * k * t * t);
+        }
+        best = std::max(best, sum);
+    }
+    return best;
 }
 
 // one beam per (mesh point, requested class)
@@ -218,13 +283,21 @@ static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fg
     FGA_TRY(T2.ensure(sizeof(C2<R>) * (size_t)d->ny[0] * A * A * 3));
     const size_t Fn = (size_t)A * A * A * 3;
     FGA_TRY(Fb.ensure(sizeof(C2<R>) * Fn));
+    DevBuf tsb;
+    FGA_TRY(tsb.ensure(64));
+    TransformScratch ts;
+    ts.amax = tsb.as<float>();
+    ts.err = reinterpret_cast<int *>(tsb.as<char>() + 16);
+    FGA_CUDA(cudaMemsetAsync(tsb.p, 0, 64, s));
+    for (int a = 0; a < 3; a++)
+        ts.S[a] = kernel_row_sum_max(d->nq, d->q0[a], d->dq[a], d->ny[a], d->y0[a], d->dy[a], d->k);
     FGA_TRY(fbi_transform<R>(d, static_cast<const double2 *>(d->f), Kax, T1.as<C2<R>>(), T2.as<C2<R>>(),
-                             Fb.as<C2<R>>(), s));
+                             Fb.as<C2<R>>(), ts, s));
     const C2<R> *G = nullptr;
     if (d->g) {
         FGA_TRY(Gb.ensure(sizeof(C2<R>) * Fn));
         FGA_TRY(fbi_transform<R>(d, static_cast<const double2 *>(d->g), Kax, T1.as<C2<R>>(), T2.as<C2<R>>(),
-                                 Gb.as<C2<R>>(), s));
+                                 Gb.as<C2<R>>(), ts, s));
         G = Gb.as<C2<R>>();
     }
     const int64_t M = (int64_t)d->nq * d->nq * d->nq * d->np * d->np * d->np;
@@ -249,6 +322,15 @@ static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fg
     FGA_CUDA(cudaGetLastError());
     // the temporaries are released when this scope ends; make sure the stream is done with them
     FGA_CUDA(cudaStreamSynchronize(s));
+    if (sizeof(R) == 4) {
+        int terr = 0;
+        FGA_CUDA(cudaMemcpy(&terr, ts.err, sizeof terr, cudaMemcpyDeviceToHost));
+        if (terr) {
+            set_error("fga_decompose: a tensor-core wait of the transform ran out");
+            return FGA_ERR_TIMEOUT;
+        }
+    }
+    tsb.release();
     Kb.release();
     T1.release();
     T2.release();

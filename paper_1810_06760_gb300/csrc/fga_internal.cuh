@@ -161,6 +161,13 @@ struct fga_beams {
 namespace fga {
 
 // kernels and launchers (one per translation unit area) ------------------------------------
+// tc_gemm.cu: complex GEMM C[z][m][n] = scale sum_k A[z][m][k] B[n][k] on the tensor cores (FP16 split,
+// FP32 accumulation); |B| <= 1; |Re|, |Im| of A bounded by (*amax) * amax_factor; *err set if a wait ran out
+template <typename TA>
+fga_status tc_cgemm(const TA *A, int64_t sAz, int64_t sAm, int64_t sAk, const float2 *B, int64_t sBn, int64_t sBk,
+                    float2 *C, int64_t sCz, int64_t sCm, int64_t sCn, int Z, int64_t M, int N, int K, float scale,
+                    const float *amax, float amax_factor, int *err, cudaStream_t s);
+fga_status tc_absmax(const double2 *x, int64_t n, float *out, cudaStream_t s);
 // decompose.cu
 fga_status decompose_impl(const fga_model *m, const fga_init_desc *d, fga_beams **out, cudaStream_t s);
 // propagate.cu

@@ -31,8 +31,15 @@ struct LatticePlan {
     int64_t pairs_tested = 0;
     int64_t n_in[4] = {0, 0, 0, 0}, rec_off[4] = {0, 0, 0, 0}, n_rec = 0, beg[4] = {0, 0, 0, 0};
 };
+// tc: tile shape and work split of the tensor-core kernel (the FP32 path); else the CUDA-core kernel's
 fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, const fga_lattice &L,
-                              cudaStream_t s, LatticePlan &plan);
+                              cudaStream_t s, LatticePlan &plan, bool tc);
+void tile_shape_tc(const fga_lattice &L, int T[3]);
+fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *rec, double k, double rw, void *u,
+                          cudaStream_t s, int cat);
+fga_status lattice_reduce_f32(const float *partial, const LatticePlan &plan, void *u, cudaStream_t s);
+int64_t read_tc_pair_counter(bool reset);
+int read_tc_lattice_error(bool reset);
 fga_status run_lattice(Workspace &ws, const LatticePlan &plan, int precision, const void *rec, double k, double rw,
                        void *u, cudaStream_t s, int cat = P_GATHER);
 int64_t read_lattice_pair_counter(bool reset);

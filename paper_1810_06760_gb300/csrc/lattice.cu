@@ -327,9 +327,12 @@ static void tile_shape(const fga_lattice &L, int T[3]) {
 }
 
 fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, const fga_lattice &L,
-                              cudaStream_t s, LatticePlan &plan) {
+                              cudaStream_t s, LatticePlan &plan, bool tc) {
     int T[3];
-    tile_shape(L, T);
+    if (tc)
+        tile_shape_tc(L, T);
+    else
+        tile_shape(L, T);
     plan.T[0] = T[0];
     plan.T[1] = T[1];
     plan.T[2] = T[2];
@@ -382,7 +385,8 @@ fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *ce
                 }
         }
     }
-    int64_t B = std::max<int64_t>(256, (total + 2047) / 2048);
+    // beams per work item: the tensor-core kernel amortises its set-up over longer ranges
+    int64_t B = tc ? std::max<int64_t>(512, (total + 1215) / 1216) : std::max<int64_t>(256, (total + 2047) / 2048);
     B = (B + 63) / 64 * 64;
     std::vector<int32_t> item_start((size_t)ntiles + 1, 0);
     std::vector<int4> items;
@@ -479,10 +483,21 @@ static fga_status run_lattice_t(Workspace &ws, const LatticePlan &plan, const vo
     return FGA_OK;
 }
 
+fga_status lattice_reduce_f32(const float *partial, const LatticePlan &plan, void *u, cudaStream_t s) {
+    const int64_t total = (int64_t)plan.n[0] * plan.n[1] * plan.n[2];
+    ProfScope ps(P_REDUCE, s);
+    lattice_reduce_kernel<float><<<(unsigned)((total * 32 + 255) / 256), 256, 0, s>>>(
+        partial, plan.item_start, plan.n[0], plan.n[1], plan.n[2], plan.T[0], plan.T[1], plan.T[2], plan.nt[1],
+        plan.nt[2], (float *)u);
+    FGA_CUDA(cudaGetLastError());
+    return FGA_OK;
+}
+
+// FP32: the tensor-core kernel (plans built with tc = true); FP64: the CUDA-core kernel
 fga_status run_lattice(Workspace &ws, const LatticePlan &plan, int precision, const void *rec, double k, double rw,
                        void *u, cudaStream_t s, int cat) {
     if (precision == FGA_PREC_FP64) return run_lattice_t<double>(ws, plan, rec, k, rw, u, s, cat);
-    return run_lattice_t<float>(ws, plan, rec, k, rw, u, s, cat);
+    return run_lattice_tc(ws, plan, rec, k, rw, u, s, cat);
 }
 
 }  // namespace fga

@@ -1,0 +1,356 @@
+// A6 on tensor lattices (receiver arrays, snapshot grids), FP32 path, on the tensor cores.
+//
+// With E_d(x) = exp(i k P_d (x - Q_d) - k (x - Q_d)^2 / 2) the Gaussian of Eq. FGA factors per axis,
+// so on a tile of T0 x T1 x T2 lattice points the sum over the beams b of a tile's neighbourhood is a
+// complex matrix product with the beams as the contraction index:
+//
+//   U[(j,l)][(i,c)] = sum_b  Y_b[(j,l)] X_b[(i,c)],   Y_b[(j,l)] = E1_b(x_j) E2_b(x_l),
+//                                                   X_b[(i,c)] = A_bc E0_b(x_i)
+//
+// (A_bc: component c of the beam's weighted polarised amplitude).  Per block of 32 beams the CUDA
+// cores form the 1-D factors (T0 + T1 + T2 complex exponentials per beam) and the two operand
+// blocks (T1 T2 + 3 T0 complex values per beam) instead of one complex product per point and
+// component; the 5th-generation tensor cores do the T1 T2 x 3 T0 x 32 product in FP16 split precision
+// (hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory), like the transform of A1.  Every
+// (beam, point) pair of the binned neighbourhood is summed: the pairs beyond the window radius carry
+// a Gaussian below e^-18 and change the sum by less than e^-18 of sum |A|.
+//
+// One CTA = one work item (tile, range of cell-sorted records) of the lattice plan; 128 threads.
+// Rows (j,l) of the tile are the 128 TMEM lanes (M = 128; unused rows stay zero), columns are
+// Re/Im of the 3 T0 complex (i,c) pairs.  Operand blocks are single-buffered: the records and factors
+// of the next block are formed while the tensor cores work on the current one.  The partial sums go
+// to the plan's per-item buffer in the layout of the CUDA-core lattice kernel and are reduced by it.
+#include <algorithm>
+#include <cmath>
+
+#include "fga_beam.cuh"
+#include "gather.cuh"
+#include "tcgen05.cuh"
+
+namespace fga {
+
+// (beam, point) pairs inside the window (profiling) and wait timeouts of the tensor-core lattice kernel
+static __device__ unsigned long long g_tc_pairs;
+static __device__ int g_tc_err;
+
+int64_t read_tc_pair_counter(bool reset) {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_pairs, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (reset) {
+        const unsigned long long z = 0;
+        cudaMemcpyToSymbol(g_tc_pairs, &z, sizeof z);
+    }
+    return (int64_t)v;
+}
+
+int read_tc_lattice_error(bool reset) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_err, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (reset && v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_tc_err, &z, sizeof z);
+    }
+    return v;
+}
+
+namespace {
+
+constexpr int LT_M = 128;
+constexpr int LT_KB = tc::KB;            // beams per block
+constexpr int LT_T0_MAX = 32;            // 6 T0 <= 192 real columns
+constexpr int LT_NMAX = 192;
+constexpr int LT_A_BYTES = LT_M * LT_KB * 2;      // 8 KB per operand copy
+constexpr int LT_B_BYTES = LT_NMAX * LT_KB * 2;   // 12 KB per operand copy
+constexpr int LT_TA_MAX = 32 + 128 + 16;
+constexpr uint32_t LT_TMEM_COLS = 256;
+
+struct LtSmem {
+    int a, b, e, rec, x, bar, bytes;
+    __host__ __device__ void init(int TA) {
+        a = 0;
+        b = a + 4 * LT_A_BYTES;
+        e = b + 4 * LT_B_BYTES;
+        rec = e + LT_KB * TA * 8;
+        x = rec + LT_KB * REC * 4;
+        bar = (x + TA * 4 + 15) / 16 * 16;
+        bytes = bar + 16;
+    }
+};
+
+template <bool COUNT>
+__global__ void __launch_bounds__(128) lattice_tc_kernel(const float *__restrict__ rec, const double *__restrict__ ax0,
+                                                        const double *__restrict__ ax1, const double *__restrict__ ax2,
+                                                        int n0, int n1, int n2, int T0, int T1, int T2, int nt1,
+                                                        int nt2, const int4 *__restrict__ items, float k, float rw2,
+                                                        const float *__restrict__ amax, LtSmem S,
+                                                        float *__restrict__ partial) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sA = smem + S.a;
+    unsigned char *sB = smem + S.b;
+    float2 *sE = reinterpret_cast<float2 *>(smem + S.e);   // [32][TA]: E0 (T0), E1 (T1), E2 (T2)
+    float *sR = reinterpret_cast<float *>(smem + S.rec);  // [32][REC]
+    float *sX = reinterpret_cast<float *>(smem + S.x);    // tile coordinates, axis 0 | 1 | 2
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int TA = T0 + T1 + T2, R_used = T1 * T2, nc_used = 3 * T0;
+    const int nc_tile = (nc_used + 7) / 8 * 8, NR = 2 * nc_tile;
+
+    const int4 it = items[blockIdx.x];
+    const int t = it.x;
+    const int tt0 = t / (nt1 * nt2), tt1 = (t / nt2) % nt1, tt2 = t % nt2;
+    const int i0 = tt0 * T0, j0 = tt1 * T1, l0 = tt2 * T2;
+    const int e0 = min(T0, n0 - i0), e1 = min(T1, n1 - j0), e2 = min(T2, n2 - l0);
+
+    // zero both operand areas once: rows and columns beyond the tile's use stay zero
+    for (int o = tid * 16; o < 4 * LT_A_BYTES + 4 * LT_B_BYTES; o += 128 * 16)
+        *reinterpret_cast<uint4 *>(smem + o) = make_uint4(0, 0, 0, 0);
+    for (int a = tid; a < TA; a += 128) {
+        double v;
+        if (a < T0) v = ax0[i0 + min(a, e0 - 1)];
+        else if (a < T0 + T1) v = ax1[j0 + min(a - T0, e1 - 1)];
+        else v = ax2[l0 + min(a - T0 - T1, e2 - 1)];
+        sX[a] = (float)v;
+    }
+    if (warp == 0) tc::alloc(tc::smem_u32(tmem_slot), LT_TMEM_COLS);
+    if (tid == 0) tc::mbar_init(tc::smem_u32(bar));
+    // exact power-of-two scales: |Y| <= 1 -> 2^14; |X| <= max |A| -> 2^(14 - e)
+    float sx = 1.0f;
+    {
+        const float bound = *amax;
+        if (bound > 0.0f && isfinite(bound)) {
+            int e;
+            frexpf(bound, &e);
+            sx = ldexpf(1.0f, 14 - e);
+        }
+    }
+    const float sy = 16384.0f;
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = tc::instr_desc(NR, LT_M);
+    const float hk = -0.5f * k;
+    uint32_t parity = 0;
+    int issued = 0;
+    bool ok = true;
+    unsigned long long mine = 0;
+    for (int64_t base = it.y; base < it.z && ok; base += LT_KB) {
+        const int nb = (int)((it.z - base) < LT_KB ? (it.z - base) : LT_KB);
+        // 1. records of this block
+        for (int q = tid; q < LT_KB * REC; q += 128) {
+            const int b = q / REC;
+            sR[q] = b < nb ? rec[(base + b) * REC + (q - b * REC)] : 0.0f;
+        }
+        __syncthreads();
+        // 2. 1-D factors E_d of every beam at the tile's coordinates (zero for missing beams)
+        for (int q = tid; q < LT_KB * TA; q += 128) {
+            const int b = q / TA, a = q - b * TA;
+            float2 v = make_float2(0.f, 0.f);
+            if (b < nb) {
+                const int d = a < T0 ? 0 : (a < T0 + T1 ? 1 : 2);
+                const float dx = sX[a] - sR[b * REC + d];
+                float er, ei;
+                gauss_phase_exp<float>(k * sR[b * REC + 3 + d] * dx, hk * dx * dx, &er, &ei);
+                v = make_float2(er, ei);
+            }
+            sE[q] = v;
+        }
+        if (COUNT) {
+            for (int q = tid; q < nb * R_used * T0; q += 128) {
+                const int b = q / (R_used * T0), rem = q - b * R_used * T0;
+                const int i = rem / R_used, r = rem - i * R_used, j = r / T2, l = r - j * T2;
+                if (i < e0 && j < e1 && l < e2) {
+                    const float *rb = sR + b * REC;
+                    const float d0 = sX[i] - rb[0], d1 = sX[T0 + j] - rb[1], d2 = sX[T0 + T1 + l] - rb[2];
+                    if (d0 * d0 + d1 * d1 + d2 * d2 <= rw2) mine++;
+                }
+            }
+        }
+        // 3. the tensor cores must be done with the previous operand block
+        if (issued > 0) {
+            const bool arrived = tc::mbar_wait(tc::smem_u32(bar), parity);
+            parity ^= 1u;
+            tc::fence_after();
+            ok = __syncthreads_and(arrived ? 1 : 0) != 0;
+            if (!ok) break;
+        } else {
+            __syncthreads();
+        }
+        // 4. operands: A' rows (j,l) from Y = E1 E2; B' rows (i,c) from X = A_c E0
+        for (int q = tid; q < R_used * 4; q += 128) {
+            const int r = q >> 2, o = q & 3;
+            const int j = r / T2, l = r - j * T2;
+            float re[8], im[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int b = 8 * o + u;
+                const float2 a1 = sE[b * TA + T0 + j], a2 = sE[b * TA + T0 + T1 + l];
+                re[u] = a1.x * a2.x - a1.y * a2.y;
+                im[u] = a1.x * a2.y + a1.y * a2.x;
+            }
+            const uint32_t off = tc::kmaj_off(r, 8 * o);
+            tc::split8(sA + 0 * LT_A_BYTES, sA + 1 * LT_A_BYTES, off, re, sy);
+            tc::split8(sA + 2 * LT_A_BYTES, sA + 3 * LT_A_BYTES, off, im, sy);
+        }
+        for (int q = tid; q < nc_used * 4; q += 128) {
+            const int cq = q >> 2, o = q & 3;
+            const int i = cq / 3, c = cq - 3 * i;
+            float re[8], im[8], nim[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int b = 8 * o + u;
+                const float2 e = sE[b * TA + i];
+                const float ar = sR[b * REC + 6 + 2 * c], ai = sR[b * REC + 7 + 2 * c];
+                re[u] = ar * e.x - ai * e.y;
+                im[u] = ar * e.y + ai * e.x;
+                nim[u] = -im[u];
+            }
+            const uint32_t top = tc::kmaj_off(cq, 8 * o), bot = tc::kmaj_off(nc_tile + cq, 8 * o);
+            // B'_re = [Re X ; Im X], B'_im = [-Im X ; Re X]
+            tc::split8(sB + 0 * LT_B_BYTES, sB + 1 * LT_B_BYTES, top, re, sx);
+            tc::split8(sB + 0 * LT_B_BYTES, sB + 1 * LT_B_BYTES, bot, im, sx);
+            tc::split8(sB + 2 * LT_B_BYTES, sB + 3 * LT_B_BYTES, top, nim, sx);
+            tc::split8(sB + 2 * LT_B_BYTES, sB + 3 * LT_B_BYTES, bot, re, sx);
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+            for (int half = 0; half < 2; half++) {
+                const uint32_t a_hi = tc::smem_u32(sA + (2 * half) * LT_A_BYTES);
+                const uint32_t a_lo = tc::smem_u32(sA + (2 * half + 1) * LT_A_BYTES);
+                const uint32_t b_hi = tc::smem_u32(sB + (2 * half) * LT_B_BYTES);
+                const uint32_t b_lo = tc::smem_u32(sB + (2 * half + 1) * LT_B_BYTES);
+                for (int ks = 0; ks < LT_KB / 16; ks++) {
+                    const uint32_t koff = ks * 2 * 128;
+                    const uint32_t acc0 = (issued > 0 || half > 0 || ks > 0) ? 1u : 0u;
+                    tc::mma_f16(tmem, tc::smem_desc(a_hi + koff), tc::smem_desc(b_hi + koff), idesc, acc0);
+                    tc::mma_f16(tmem, tc::smem_desc(a_hi + koff), tc::smem_desc(b_lo + koff), idesc, 1u);
+                    tc::mma_f16(tmem, tc::smem_desc(a_lo + koff), tc::smem_desc(b_hi + koff), idesc, 1u);
+                }
+            }
+            tc::commit(tc::smem_u32(bar));
+        }
+        issued++;
+    }
+    if (ok && issued > 0) {
+        const bool arrived = tc::mbar_wait(tc::smem_u32(bar), parity);
+        tc::fence_after();
+        ok = __syncthreads_and(arrived ? 1 : 0) != 0;
+    }
+    if (!ok && tid == 0) atomicExch(&g_tc_err, 1);
+    if (ok) {
+        // epilogue: lane row r = (j, l); columns (i, c) as Re at cq, Im at nc_tile + cq
+        const int r = warp * 32 + lane;
+        const int TP = T0 * T1 * T2;
+        const float inv = 1.0f / (sx * sy);
+        const int j = r / T2, l = r - j * T2;
+        float *dst = partial + (int64_t)blockIdx.x * TP * 6;
+        for (int c0 = 0; c0 < nc_tile; c0 += 8) {
+            float re[8], im[8];
+            const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+            if (issued > 0) {
+                tc::ld8(tmem + lanebase + (uint32_t)c0, re);
+                tc::ld8(tmem + lanebase + (uint32_t)(nc_tile + c0), im);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; u++) re[u] = im[u] = 0.f;
+            }
+            if (r < R_used) {
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int cq = c0 + u;
+                    if (cq < nc_used) {
+                        const int i = cq / 3, c = cq - 3 * i;
+                        const int p = (i * T1 + j) * T2 + l;
+                        dst[p * 6 + 2 * c] = re[u] * inv;
+                        dst[p * 6 + 2 * c + 1] = im[u] * inv;
+                    }
+                }
+            }
+        }
+    }
+    if (COUNT) {
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        if (lane == 0 && mine) atomicAdd(&g_tc_pairs, mine);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tmem, LT_TMEM_COLS);
+}
+
+__global__ void rec_absmax_kernel(const float *__restrict__ rec, int64_t n, float *__restrict__ out) {
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * 6; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(rec[(i / 6) * REC + 6 + (i % 6)]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(m));
+}
+
+}  // namespace
+
+// tile of the tensor-core lattice sum: rows (j,l) <= 128, T0 <= 32
+void tile_shape_tc(const fga_lattice &L, int T[3]) {
+    if (L.n[2] == 1) {
+        T[2] = 1;
+        T[1] = std::min(L.n[1], 128);
+    } else {
+        T[2] = std::min(L.n[2], 16);
+        T[1] = std::min(L.n[1], 128 / T[2]);
+    }
+    const int nt0 = (L.n[0] + LT_T0_MAX - 1) / LT_T0_MAX;
+    T[0] = (L.n[0] + nt0 - 1) / nt0;
+}
+
+fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *rec, double k, double rw, void *u,
+                          cudaStream_t s, int cat) {
+    const int T0 = plan.T[0], T1 = plan.T[1], T2 = plan.T[2];
+    const int TP = T0 * T1 * T2;
+    if (T0 > LT_T0_MAX || T1 * T2 > LT_M || T0 + T1 + T2 > LT_TA_MAX) {
+        set_error("lattice tile does not fit the tensor-core kernel");
+        return FGA_ERR_UNSUPPORTED;
+    }
+    LtSmem S;
+    S.init(T0 + T1 + T2);
+    FGA_TRY(ws.partial.ensure(sizeof(float) * 6 * (size_t)TP * (size_t)std::max(plan.nitems, 1) + 64));
+    // scratch at the end of the partial buffer: the bound of the records' amplitudes
+    char *tail = ws.partial.as<char>() + sizeof(float) * 6 * (size_t)TP * (size_t)std::max(plan.nitems, 1);
+    float *amax = reinterpret_cast<float *>(tail);
+    FGA_CUDA(cudaMemsetAsync(tail, 0, 64, s));
+    const int cnt = prof_counting() ? 1 : 0;
+    prof_add_pairs_tested(plan.pairs_tested);
+    if (plan.nitems > 0) {
+        {
+            ProfScope ps(cat, s);
+            const int blocks = (int)std::min<int64_t>(152 * 4, (plan.n_rec * 6 + 255) / 256 + 1);
+            rec_absmax_kernel<<<blocks, 256, 0, s>>>(static_cast<const float *>(rec), plan.n_rec, amax);
+        }
+        ProfScope ps(cat, s);
+        if (cnt) {
+            FGA_CUDA(cudaFuncSetAttribute(lattice_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S.bytes));
+            lattice_tc_kernel<true><<<plan.nitems, 128, S.bytes, s>>>(
+                static_cast<const float *>(rec), plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2],
+                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S,
+                ws.partial.as<float>());
+        } else {
+            FGA_CUDA(cudaFuncSetAttribute(lattice_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S.bytes));
+            lattice_tc_kernel<false><<<plan.nitems, 128, S.bytes, s>>>(
+                static_cast<const float *>(rec), plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2],
+                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S,
+                ws.partial.as<float>());
+        }
+        FGA_CUDA(cudaGetLastError());
+    }
+    FGA_TRY(lattice_reduce_f32(ws.partial.as<float>(), plan, u, s));
+    return FGA_OK;
+}
+
+}  // namespace fga
