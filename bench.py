@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--size", default="full", choices=["full", "medium", "small"],
                     help="workload size: full = the benchmark; medium (16^3 q, 8.4 M beams, 1.5 GB of state) is "
                          "the profiler capture case; small is for debugging (neither is a bench line)")
+    ap.add_argument("--serving", action="store_true",
+                    help="the serving stream instead: 64 Poisson-arriving requests of mixed k and size on the resident "
+                         "smooth model at 0.7 of the measured solo capacity; p50/p99 latency and beam-steps/s")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -362,10 +365,93 @@ def run_ours(args):
     return 0
 
 
+def run_serving(args):
+    """Serving stream (the paper runs one solve at a time; this is the library's request loop)."""
+    import numpy as np
+    import torch
+
+    from paper_1810_06760_gb300 import fga
+    from paper_1810_06760_gb300 import workloads as W
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = fga.PREC_FP32 if args.precision == "fp32" else fga.PREC_FP64
+    reqs = W.serving_requests(n=64, seed=1)
+    model = fga.model_from_medium(reqs[0].workload.medium, dev)
+    # inputs resident before the timed region: per request its initial data, receivers, descriptor
+    staged = []
+    for r in reqs:
+        w = r.workload
+        f = torch.as_tensor(w.f, device=dev)
+        rx = torch.as_tensor(w.receivers, device=dev)
+        staged.append((w, fga.init_desc(w.k, f, None, w.y0, w.dy, w.mesh, w.classes, prec), f, rx))
+    torch.cuda.synchronize()
+    n_workers = 4
+
+    def run(arrivals, workers):
+        server = fga.Server(model, n_workers=workers)
+        t0 = time.perf_counter()
+        ids = []
+        for (w, desc, f, rx), ta in zip(staged, arrivals):
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(server.submit(desc, w.dt, w.nsteps, w.times, rx, rw=w.rw, keep=(f,)))
+        infos = [server.wait(i)[1] for i in ids]
+        wall = time.perf_counter() - t0
+        st = server.stats()
+        server.close()
+        return infos, wall, st
+
+    # warm-up (compilation of nothing, allocator and caches): the four smallest requests
+    order = np.argsort([w.n_beams for w, *_ in staged])
+    small = [staged[i] for i in order[:4]]
+    sv = fga.Server(model, n_workers=1)
+    for w, desc, f, rx in small:
+        sv.wait(sv.submit(desc, w.dt, w.nsteps, w.times, rx, rw=w.rw, keep=(f,)))
+    sv.close()
+    # solo capacity: every request alone, back to back on one worker
+    solo, solo_wall, _ = run([0.0] * len(staged), 1)
+    service = [i["t_end"] - i["t_start"] for i in solo]
+    capacity = 1.0 / float(np.mean(service))        # requests per second, one at a time
+    rate = 0.7 * capacity
+    arrivals = [r.arrival / rate for r in reqs]
+    clk = Clocks(local)
+    clk.start()
+    infos, wall, st = run(arrivals, n_workers)
+    clocks = clk.stop()
+    lat = sorted(i["t_end"] - i["t_submit"] for i in infos)
+    q = lambda p: float(np.percentile(lat, p))
+    beam_steps = sum(w.n_beams * w.nsteps for w, *_ in staged)
+    line = {
+        "metric": "FGA beam-steps/s and Gaussian-sum pts/s at fixed error; p50/p99 solve latency",
+        "value": beam_steps / wall, "unit": "beam-steps/s", "n_gpus": world, "steps": len(reqs), "warmup": 4,
+        "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
+        "config": {"workload": "serving stream: 64 requests, Poisson arrivals (seed 1) at 0.7 x solo capacity, "
+                               "k in {32,64,128}, N log-uniform 1e5..2e7 -> q n_q^3 x p 8^3 x 4 classes, "
+                               "smooth 128^3 model resident, T=0.5 (200 steps), 256 rx x 200 samples",
+                   "workers": n_workers, "parallelism": f"replicas x{world}"},
+        "latency_s": {"p50": q(50), "p99": q(99), "max": lat[-1], "mean": float(np.mean(lat))},
+        "solo": {"capacity_req_per_s": capacity, "service_s_p50": float(np.median(service)),
+                 "beam_steps_per_s": beam_steps / solo_wall},
+        "offered_rate_req_per_s": rate,
+        "server": {"peak_running": st["peak_running"], "peak_bytes": st["peak_bytes"],
+                   "budget_bytes": st["budget_bytes"]},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -30,6 +30,10 @@ struct LatticePlan {
     const int4 *items = nullptr;
     int64_t pairs_tested = 0;
     int64_t n_in[4] = {0, 0, 0, 0}, rec_off[4] = {0, 0, 0, 0}, n_rec = 0, beg[4] = {0, 0, 0, 0};
+    // axes with uniform spacing (coordinate i = x0 + i * dx to 1e-12 relative): the tensor-core kernel forms
+    // their 1-D factors by recurrence
+    bool uniform[3] = {false, false, false};
+    double dx[3] = {0, 0, 0};
 };
 // tc: tile shape and work split of the tensor-core kernel (the FP32 path); else the CUDA-core kernel's
 fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, const fga_lattice &L,

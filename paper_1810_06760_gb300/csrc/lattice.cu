@@ -402,6 +402,16 @@ fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *ce
     item_start[(size_t)ntiles] = (int32_t)items.size();
     plan.ntiles = ntiles;
     plan.nitems = (int)items.size();
+    for (int d = 0; d < 3; d++) {
+        const double *a = L.axis[d];
+        const int n = L.n[d];
+        bool uni = n >= 2;
+        const double step = n >= 2 ? (a[n - 1] - a[0]) / (n - 1) : 0.0;
+        const double scale = std::max(std::fabs(a[0]), std::fabs(a[n - 1])) + std::fabs(step) * n;
+        for (int i = 0; uni && i < n; i++) uni = std::fabs(a[i] - (a[0] + i * step)) <= 1e-12 * scale;
+        plan.uniform[d] = uni && step != 0.0;
+        plan.dx[d] = step;
+    }
     plan.pairs_tested = total * (int64_t)T[0] * T[1] * T[2];
     // device copies: axes, item starts, items
     const size_t axb = sizeof(double) * (size_t)(L.n[0] + L.n[1] + L.n[2]);

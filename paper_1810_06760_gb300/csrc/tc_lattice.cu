@@ -8,14 +8,16 @@
 //                                                   X_b[(i,c)] = A_bc E0_b(x_i)
 //
 // (A_bc: component c of the beam's weighted polarised amplitude).  Per block of 32 beams the CUDA
-// cores form the 1-D factors (T0 + T1 + T2 complex exponentials per beam) and the two operand
-// blocks (T1 T2 + 3 T0 complex values per beam) instead of one complex product per point and
-// component; the 5th-generation tensor cores do the T1 T2 x 3 T0 x 32 product in FP16 split precision
+// cores form the 1-D factors (on an axis with uniform spacing h by the recurrence E(x + h) = E(x) R(x),
+// R(x + h) = R(x) exp(-k h^2), restarted with two exponentials every 8 points; else one exponential
+// per point) and the two operand blocks (T1 T2 + 3 T0 complex values per beam) instead of one complex
+// product per point and component; the 5th-generation tensor cores do the T1 T2 x 3 T0 x 32 product in FP16 split precision
 // (hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory), like the transform of A1.  Every
 // (beam, point) pair of the binned neighbourhood is summed: the pairs beyond the window radius carry
 // a Gaussian below e^-18 and change the sum by less than e^-18 of sum |A|.
 //
-// One CTA = one work item (tile, range of cell-sorted records) of the lattice plan; 128 threads.
+// One CTA = one work item (tile, range of cell-sorted records) of the lattice plan; 256 threads, two
+// CTAs per SM (the tensor cores of one overlap the operand formation of the other).
 // Rows (j,l) of the tile are the 128 TMEM lanes (M = 128; unused rows stay zero), columns are
 // Re/Im of the 3 T0 complex (i,c) pairs.  Operand blocks are single-buffered: the records and factors
 // of the next block are formed while the tensor cores work on the current one.  The partial sums go
@@ -62,6 +64,8 @@ int read_tc_lattice_error(bool reset) {
 namespace {
 
 constexpr int LT_M = 128;
+constexpr int LT_THREADS = 256;
+constexpr int LT_CHUNK = 8;              // points per factor recurrence on a uniform axis
 constexpr int LT_KB = tc::KB;            // beams per block
 constexpr int LT_T0_MAX = 32;            // 6 T0 <= 192 real columns
 constexpr int LT_NMAX = 192;
@@ -83,12 +87,20 @@ struct LtSmem {
     }
 };
 
+// per-axis factor chunks: uniform axes in runs of LT_CHUNK points (one exponential for the first point
+// and one for the ratio, then E <- E R, R <- R G with G = exp(-k dx^2)), other axes point by point
+struct LtAxes {
+    int len[3];    // points per chunk
+    int nch[3];    // chunks per axis
+    float dx[3];   // spacing of uniform axes
+};
+
 template <bool COUNT>
-__global__ void __launch_bounds__(128) lattice_tc_kernel(const float *__restrict__ rec, const double *__restrict__ ax0,
+__global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *__restrict__ rec, const double *__restrict__ ax0,
                                                         const double *__restrict__ ax1, const double *__restrict__ ax2,
                                                         int n0, int n1, int n2, int T0, int T1, int T2, int nt1,
                                                         int nt2, const int4 *__restrict__ items, float k, float rw2,
-                                                        const float *__restrict__ amax, LtSmem S,
+                                                        const float *__restrict__ amax, LtSmem S, LtAxes X,
                                                         float *__restrict__ partial) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem + S.a;
@@ -109,9 +121,9 @@ __global__ void __launch_bounds__(128) lattice_tc_kernel(const float *__restrict
     const int e0 = min(T0, n0 - i0), e1 = min(T1, n1 - j0), e2 = min(T2, n2 - l0);
 
     // zero both operand areas once: rows and columns beyond the tile's use stay zero
-    for (int o = tid * 16; o < 4 * LT_A_BYTES + 4 * LT_B_BYTES; o += 128 * 16)
+    for (int o = tid * 16; o < 4 * LT_A_BYTES + 4 * LT_B_BYTES; o += LT_THREADS * 16)
         *reinterpret_cast<uint4 *>(smem + o) = make_uint4(0, 0, 0, 0);
-    for (int a = tid; a < TA; a += 128) {
+    for (int a = tid; a < TA; a += LT_THREADS) {
         double v;
         if (a < T0) v = ax0[i0 + min(a, e0 - 1)];
         else if (a < T0 + T1) v = ax1[j0 + min(a - T0, e1 - 1)];
@@ -144,26 +156,48 @@ __global__ void __launch_bounds__(128) lattice_tc_kernel(const float *__restrict
     for (int64_t base = it.y; base < it.z && ok; base += LT_KB) {
         const int nb = (int)((it.z - base) < LT_KB ? (it.z - base) : LT_KB);
         // 1. records of this block
-        for (int q = tid; q < LT_KB * REC; q += 128) {
+        for (int q = tid; q < LT_KB * REC; q += LT_THREADS) {
             const int b = q / REC;
             sR[q] = b < nb ? rec[(base + b) * REC + (q - b * REC)] : 0.0f;
         }
         __syncthreads();
         // 2. 1-D factors E_d of every beam at the tile's coordinates (zero for missing beams)
-        for (int q = tid; q < LT_KB * TA; q += 128) {
-            const int b = q / TA, a = q - b * TA;
-            float2 v = make_float2(0.f, 0.f);
-            if (b < nb) {
-                const int d = a < T0 ? 0 : (a < T0 + T1 ? 1 : 2);
-                const float dx = sX[a] - sR[b * REC + d];
+        {
+            const int nch = X.nch[0] + X.nch[1] + X.nch[2];
+            for (int q = tid; q < LT_KB * nch; q += LT_THREADS) {
+                const int b = q / nch, c = q - b * nch;
+                const int d = c < X.nch[0] ? 0 : (c < X.nch[0] + X.nch[1] ? 1 : 2);
+                const int cc = c - (d == 0 ? 0 : (d == 1 ? X.nch[0] : X.nch[0] + X.nch[1]));
+                const int off = d == 0 ? 0 : (d == 1 ? T0 : T0 + T1), Td = d == 0 ? T0 : (d == 1 ? T1 : T2);
+                const int a0 = cc * X.len[d], a1 = min(a0 + X.len[d], Td);
+                float2 *dst = sE + b * TA + off;
+                if (b >= nb) {
+                    for (int a = a0; a < a1; a++) dst[a] = make_float2(0.f, 0.f);
+                    continue;
+                }
+                const float Qd = sR[b * REC + d], Pd = sR[b * REC + 3 + d];
+                const float x = sX[off + a0] - Qd;
                 float er, ei;
-                gauss_phase_exp<float>(k * sR[b * REC + 3 + d] * dx, hk * dx * dx, &er, &ei);
-                v = make_float2(er, ei);
+                gauss_phase_exp<float>(k * Pd * x, hk * x * x, &er, &ei);
+                dst[a0] = make_float2(er, ei);
+                if (a1 - a0 > 1) {
+                    const float h = X.dx[d];
+                    float rr, ri;
+                    gauss_phase_exp<float>(k * Pd * h, -k * h * (x + 0.5f * h), &rr, &ri);
+                    const float g = __expf(-k * h * h);
+                    for (int a = a0 + 1; a < a1; a++) {
+                        const float nr = er * rr - ei * ri, ni = er * ri + ei * rr;
+                        er = nr;
+                        ei = ni;
+                        dst[a] = make_float2(er, ei);
+                        rr *= g;
+                        ri *= g;
+                    }
+                }
             }
-            sE[q] = v;
         }
         if (COUNT) {
-            for (int q = tid; q < nb * R_used * T0; q += 128) {
+            for (int q = tid; q < nb * R_used * T0; q += LT_THREADS) {
                 const int b = q / (R_used * T0), rem = q - b * R_used * T0;
                 const int i = rem / R_used, r = rem - i * R_used, j = r / T2, l = r - j * T2;
                 if (i < e0 && j < e1 && l < e2) {
@@ -184,7 +218,7 @@ __global__ void __launch_bounds__(128) lattice_tc_kernel(const float *__restrict
             __syncthreads();
         }
         // 4. operands: A' rows (j,l) from Y = E1 E2; B' rows (i,c) from X = A_c E0
-        for (int q = tid; q < R_used * 4; q += 128) {
+        for (int q = tid; q < R_used * 4; q += LT_THREADS) {
             const int r = q >> 2, o = q & 3;
             const int j = r / T2, l = r - j * T2;
             float re[8], im[8];
@@ -199,7 +233,7 @@ __global__ void __launch_bounds__(128) lattice_tc_kernel(const float *__restrict
             tc::split8(sA + 0 * LT_A_BYTES, sA + 1 * LT_A_BYTES, off, re, sy);
             tc::split8(sA + 2 * LT_A_BYTES, sA + 3 * LT_A_BYTES, off, im, sy);
         }
-        for (int q = tid; q < nc_used * 4; q += 128) {
+        for (int q = tid; q < nc_used * 4; q += LT_THREADS) {
             const int cq = q >> 2, o = q & 3;
             const int i = cq / 3, c = cq - 3 * i;
             float re[8], im[8], nim[8];
@@ -248,15 +282,16 @@ __global__ void __launch_bounds__(128) lattice_tc_kernel(const float *__restrict
     }
     if (!ok && tid == 0) atomicExch(&g_tc_err, 1);
     if (ok) {
-        // epilogue: lane row r = (j, l); columns (i, c) as Re at cq, Im at nc_tile + cq
-        const int r = warp * 32 + lane;
+        // epilogue: warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31 (rows (j, l)) and split the
+        // 8-column chunks of (i, c) (Re at cq, Im at nc_tile + cq) between them
+        const int quarter = warp & 3, r = quarter * 32 + lane;
         const int TP = T0 * T1 * T2;
         const float inv = 1.0f / (sx * sy);
         const int j = r / T2, l = r - j * T2;
         float *dst = partial + (int64_t)blockIdx.x * TP * 6;
-        for (int c0 = 0; c0 < nc_tile; c0 += 8) {
+        const uint32_t lanebase = (uint32_t)(quarter * 32) << 16;
+        for (int c0 = (warp >> 2) * 8; c0 < nc_tile; c0 += 16) {
             float re[8], im[8];
-            const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
             if (issued > 0) {
                 tc::ld8(tmem + lanebase + (uint32_t)c0, re);
                 tc::ld8(tmem + lanebase + (uint32_t)(nc_tile + c0), im);
@@ -320,6 +355,13 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
     }
     LtSmem S;
     S.init(T0 + T1 + T2);
+    LtAxes X;
+    for (int d = 0; d < 3; d++) {
+        const int Td = plan.T[d];
+        X.len[d] = plan.uniform[d] ? LT_CHUNK : 1;
+        X.nch[d] = (Td + X.len[d] - 1) / X.len[d];
+        X.dx[d] = (float)plan.dx[d];
+    }
     FGA_TRY(ws.partial.ensure(sizeof(float) * 6 * (size_t)TP * (size_t)std::max(plan.nitems, 1) + 64));
     // scratch at the end of the partial buffer: the bound of the records' amplitudes
     char *tail = ws.partial.as<char>() + sizeof(float) * 6 * (size_t)TP * (size_t)std::max(plan.nitems, 1);
@@ -336,15 +378,15 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
         ProfScope ps(cat, s);
         if (cnt) {
             FGA_CUDA(cudaFuncSetAttribute(lattice_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S.bytes));
-            lattice_tc_kernel<true><<<plan.nitems, 128, S.bytes, s>>>(
+            lattice_tc_kernel<true><<<plan.nitems, LT_THREADS, S.bytes, s>>>(
                 static_cast<const float *>(rec), plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2],
-                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S,
+                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S, X,
                 ws.partial.as<float>());
         } else {
             FGA_CUDA(cudaFuncSetAttribute(lattice_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S.bytes));
-            lattice_tc_kernel<false><<<plan.nitems, 128, S.bytes, s>>>(
+            lattice_tc_kernel<false><<<plan.nitems, LT_THREADS, S.bytes, s>>>(
                 static_cast<const float *>(rec), plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2],
-                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S,
+                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S, X,
                 ws.partial.as<float>());
         }
         FGA_CUDA(cudaGetLastError());
