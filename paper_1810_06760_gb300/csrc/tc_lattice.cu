@@ -74,15 +74,20 @@ constexpr int LT_B_BYTES = LT_NMAX * LT_KB * 2;   // 12 KB per operand copy
 constexpr int LT_TA_MAX = 32 + 128 + 16;
 constexpr uint32_t LT_TMEM_COLS = 256;
 
+constexpr int LT_CAND = 4 * LT_THREADS;   // candidates tested per filter round
+
 struct LtSmem {
-    int a, b, e, rec, x, bar, bytes;
+    int a, b, e, rec, x, keep, cnt, bar, bytes;
     __host__ __device__ void init(int TA) {
         a = 0;
         b = a + 4 * LT_A_BYTES;
         e = b + 4 * LT_B_BYTES;
         rec = e + LT_KB * TA * 8;
         x = rec + LT_KB * REC * 4;
-        bar = (x + TA * 4 + 15) / 16 * 16;
+        keep = (x + TA * 4 + 15) / 16 * 16;
+        cnt = keep + LT_CAND * 4;
+        bar = cnt + (4 * (LT_THREADS / 32) + 1) * 4;
+        bar = (bar + 15) / 16 * 16;
         bytes = bar + 16;
     }
 };
@@ -108,6 +113,8 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
     float2 *sE = reinterpret_cast<float2 *>(smem + S.e);   // [32][TA]: E0 (T0), E1 (T1), E2 (T2)
     float *sR = reinterpret_cast<float *>(smem + S.rec);  // [32][REC]
     float *sX = reinterpret_cast<float *>(smem + S.x);    // tile coordinates, axis 0 | 1 | 2
+    int *sK = reinterpret_cast<int *>(smem + S.keep);     // kept candidates (offsets from the item start)
+    int *sCnt = reinterpret_cast<int *>(smem + S.cnt);    // [4 rounds x warps] counts, then offsets; [last]: total
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -153,12 +160,59 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
     int issued = 0;
     bool ok = true;
     unsigned long long mine = 0;
-    for (int64_t base = it.y; base < it.z && ok; base += LT_KB) {
-        const int nb = (int)((it.z - base) < LT_KB ? (it.z - base) : LT_KB);
+    // the tile's box, for the reach test of the candidates
+    float blo[3], bhi[3];
+    blo[0] = sX[0];
+    bhi[0] = sX[e0 - 1];
+    blo[1] = sX[T0];
+    bhi[1] = sX[T0 + e1 - 1];
+    blo[2] = sX[T0 + T1];
+    bhi[2] = sX[T0 + T1 + e2 - 1];
+    constexpr int NW = LT_THREADS / 32;
+    for (int64_t cbase = it.y; cbase < it.z && ok; cbase += LT_CAND) {
+        // 0. keep the candidates within rw of the tile's box, in order
+        bool kp[4];
+        unsigned bal[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int64_t c = cbase + r * LT_THREADS + tid;
+            kp[r] = false;
+            if (c < it.z) {
+                const float *q = rec + c * REC;
+                const float g0 = fmaxf(fmaxf(blo[0] - q[0], q[0] - bhi[0]), 0.f);
+                const float g1 = fmaxf(fmaxf(blo[1] - q[1], q[1] - bhi[1]), 0.f);
+                const float g2 = fmaxf(fmaxf(blo[2] - q[2], q[2] - bhi[2]), 0.f);
+                kp[r] = g0 * g0 + g1 * g1 + g2 * g2 <= rw2;
+            }
+            bal[r] = __ballot_sync(0xffffffffu, kp[r]);
+            if (lane == 0) sCnt[r * NW + warp] = __popc(bal[r]);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int v = lane < 4 * NW ? sCnt[lane] : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (lane < 4 * NW) sCnt[lane] = incl - v;
+            if (lane == 31) sCnt[4 * NW] = incl;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+            if (kp[r])
+                sK[sCnt[r * NW + warp] + __popc(bal[r] & ((1u << lane) - 1u))] =
+                    (int)(cbase - it.y) + r * LT_THREADS + tid;
+        const int nk = sCnt[4 * NW];
+        __syncthreads();
+    for (int kb0 = 0; kb0 < nk && ok; kb0 += LT_KB) {
+        const int nb = min(LT_KB, nk - kb0);
         // 1. records of this block
         for (int q = tid; q < LT_KB * REC; q += LT_THREADS) {
             const int b = q / REC;
-            sR[q] = b < nb ? rec[(base + b) * REC + (q - b * REC)] : 0.0f;
+            sR[q] = b < nb ? rec[(it.y + sK[kb0 + b]) * REC + (q - b * REC)] : 0.0f;
         }
         __syncthreads();
         // 2. 1-D factors E_d of every beam at the tile's coordinates (zero for missing beams)
@@ -274,6 +328,7 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
             tc::commit(tc::smem_u32(bar));
         }
         issued++;
+    }
     }
     if (ok && issued > 0) {
         const bool arrived = tc::mbar_wait(tc::smem_u32(bar), parity);
