@@ -32,7 +32,6 @@ FLOP_PER_PAIR_IN = 43.0       # dx, r^2, phase, exponent, e*(cos, sin), 3 comple
 FLOP_PER_PAIR_OUT = 9.0       # dx, r^2, compare
 MUFU_PER_PAIR_IN = 3.0        # exp2, sin, cos
 FLOP_PER_LATTICE_PAIR_IN = 26.0   # window test (add, compare) + 3 complex multiply-adds
-FLOP_PER_LATTICE_PAIR_OUT = 2.0   # window test
 SMS = 152
 
 
@@ -285,9 +284,10 @@ def run_ours(args):
         nS = sum(1 for c in w.classes if c >= 2) * w.mesh.M
         flops = (nP * FLOP_PER_BEAM_STEP["P"] + nS * FLOP_PER_BEAM_STEP["S"]) * w.nsteps * args.steps
     elif prec == fga.PREC_FP32 and top == "gauss_sum_all":
-        # lattice sum: one complex product per component and point (24 FLOP) + the window test (2)
-        pin, pt = prof["pairs_in_window"], prof["pairs_tested"]
-        flops = pin * FLOP_PER_LATTICE_PAIR_IN + (pt - pin) * FLOP_PER_LATTICE_PAIR_OUT
+        # lattice sum: algorithmic work of the in-window pairs, one complex product per component and point
+        # plus the window test (26 FLOP); the tensor-core kernel's extra (out-of-window, split) products are
+        # not counted
+        flops = prof["pairs_in_window"] * FLOP_PER_LATTICE_PAIR_IN
     else:
         flops = None
     launches = max(cnts[top], 1)

@@ -65,88 +65,6 @@ __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st
     for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y[f];
 }
 
-// The same RK4 with the step's start state y and the RK4 accumulator in shared memory
-// ([field][thread], conflict-free) instead of registers: only the stage input and the stage slope stay
-// in registers, so three CTAs of 128 threads fit per SM (12 warps) instead of two, to hide the model
-// loads.  For the records the start state's Q, P, amplitudes and the start slope's Q, P are kept.
-template <typename R, int WAVE, int MED>
-__global__ void __launch_bounds__(128, 3) rk4_smem_kernel(ModelDev M, R *__restrict__ st,
-                                                          const int32_t *__restrict__ flags, int64_t cap, int64_t beg,
-                                                          int64_t n, R sg, R dt, int nsteps, int n_samp,
-                                                          const int *__restrict__ samp_step,
-                                                          const R *__restrict__ samp_theta, R w, R *__restrict__ rec,
-                                                          int64_t rec_lim, int64_t rec_stride) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *sy = reinterpret_cast<R *>(smem_raw);   // [NF][128]
-    R *sa = sy + NF * 128;                      // [NF][128]
-    const int t = threadIdx.x;
-    const int64_t b = beg + (int64_t)blockIdx.x * blockDim.x + t;
-    if (b >= beg + n) return;
-    R tmp[NF], kk[NF];
-#pragma unroll
-    for (int f = 0; f < NF; f++) {
-        tmp[f] = st[(int64_t)f * cap + b];
-        sy[f * 128 + t] = tmp[f];
-    }
-    const bool ref_e1 = (flags[b] & FL_REF_E1) != 0;
-    beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-    int js = 0;
-    const R h2 = R(0.5) * dt, h3 = dt / R(3), h6 = dt / R(6);
-    for (int step = 0; step < nsteps; step++) {
-        const bool sample = js < n_samp && samp_step[js] == step;
-        R y0[NF], d0[NF];  // only Q, P, amplitudes (y0) and Q, P (d0) are read, at sample steps
-        if (sample) {
-#pragma unroll
-            for (int f = 0; f < 6; f++) {
-                y0[f] = sy[f * 128 + t];
-                d0[f] = kk[f];
-            }
-#pragma unroll
-            for (int f = F_A0; f < NF; f++) y0[f] = sy[f * 128 + t];
-        }
-#pragma unroll
-        for (int f = 0; f < NF; f++) {
-            const R yf = sy[f * 128 + t];
-            sa[f * 128 + t] = yf + h6 * kk[f];
-            tmp[f] = yf + h2 * kk[f];
-        }
-        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-#pragma unroll
-        for (int f = 0; f < NF; f++) {
-            const R yf = sy[f * 128 + t];
-            sa[f * 128 + t] += h3 * kk[f];
-            tmp[f] = yf + h2 * kk[f];
-        }
-        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-#pragma unroll
-        for (int f = 0; f < NF; f++) {
-            const R yf = sy[f * 128 + t];
-            sa[f * 128 + t] += h3 * kk[f];
-            tmp[f] = yf + dt * kk[f];
-        }
-        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-#pragma unroll
-        for (int f = 0; f < NF; f++) {
-            tmp[f] = sa[f * 128 + t] + h6 * kk[f];
-            sy[f * 128 + t] = tmp[f];
-        }
-        // slope at y_{n+1}: k1 of the next step and the right-end slope of the Hermite interpolant
-        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-        while (js < n_samp && samp_step[js] == step) {
-            if (b - beg < rec_lim) {
-                R r[REC];
-                beam_record<R, WAVE>(ref_e1, y0, d0, tmp, kk, dt, samp_theta[js], w, r);
-                R *dst = rec + ((int64_t)js * rec_stride + (b - beg)) * REC;
-#pragma unroll
-                for (int q = 0; q < REC; q++) dst[q] = r[q];
-            }
-            js++;
-        }
-    }
-#pragma unroll
-    for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = sy[f * 128 + t];
-}
-
 // records of the current state (theta = 0), gathered in the order of perm (or identity)
 template <typename R, int WAVE>
 __global__ void records_kernel(const R *__restrict__ st, const int32_t *__restrict__ flags, int64_t cap,
@@ -175,15 +93,6 @@ static void launch_one(const fga_model *m, fga_beams *b, int cls, R dt, int nste
     R *rec = sw ? static_cast<R *>(sw->rec) + sw->rec_off[cls] * REC : nullptr;
     prof_add_beam_steps(n * (int64_t)nsteps);
     ProfScope ps(P_PROP, s);
-    if (sizeof(R) == 4 && MED == FGA_MEDIUM_GRID) {
-        const int smem = 2 * NF * T * (int)sizeof(R);
-        cudaFuncSetAttribute(rk4_smem_kernel<R, WAVE, MED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        rk4_smem_kernel<R, WAVE, MED><<<(unsigned)blocks, T, smem, s>>>(
-            m->dev, b->state.as<R>(), b->flags.as<int32_t>(), b->cap, b->off_cls[cls], n, sg, dt, nsteps,
-            sw ? sw->n : 0, sw ? sw->step : nullptr, sw ? static_cast<const R *>(sw->theta) : nullptr, (R)b->w, rec,
-            sw ? sw->n_in[cls] : 0, sw ? sw->n_rec : 0);
-        return;
-    }
     rk4_kernel<R, WAVE, MED><<<(unsigned)blocks, T, 0, s>>>(
         m->dev, b->state.as<R>(), b->flags.as<int32_t>(), b->cap, b->off_cls[cls], n, sg, dt, nsteps,
         sw ? sw->n : 0, sw ? sw->step : nullptr, sw ? static_cast<const R *>(sw->theta) : nullptr, (R)b->w, rec,
