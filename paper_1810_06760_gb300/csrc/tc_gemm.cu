@@ -154,10 +154,11 @@ __global__ void __launch_bounds__(128, 1) tc_cgemm_kernel(const TA *__restrict__
                          : "memory");
         }
         // the MMAs read shared memory until the commit arrives: wait before restaging
-        const bool arrived = tc::mbar_wait(tc::smem_u32(bar), parity);
+        bool arrived = true;
+        if (tid == 0) arrived = tc::mbar_wait(tc::smem_u32(bar), parity);   // one poller
         parity ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         ok = __syncthreads_and(arrived ? 1 : 0) != 0;   // uniform across the CTA
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok && tid == 0) atomicExch(err, 1);
     }
     if (ok) {

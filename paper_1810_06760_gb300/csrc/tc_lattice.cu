@@ -72,21 +72,19 @@ constexpr int LT_NMAX = 192;
 constexpr int LT_A_BYTES = LT_M * LT_KB * 2;      // 8 KB per operand copy
 constexpr int LT_B_BYTES = LT_NMAX * LT_KB * 2;   // 12 KB per operand copy
 constexpr int LT_TA_MAX = 32 + 128 + 16;
+constexpr int LT_CAND = 4096;           // candidates filtered per round (per-CTA kept-list scratch)
 constexpr uint32_t LT_TMEM_COLS = 256;
 
-constexpr int LT_CAND = 4 * LT_THREADS;   // candidates tested per filter round
-
 struct LtSmem {
-    int a, b, e, rec, x, keep, cnt, bar, bytes;
+    int a, b, e, rec, x, cnt, bar, bytes;
     __host__ __device__ void init(int TA) {
         a = 0;
         b = a + 4 * LT_A_BYTES;
-        e = b + 4 * LT_B_BYTES;
-        rec = e + LT_KB * TA * 8;
-        x = rec + LT_KB * REC * 4;
-        keep = (x + TA * 4 + 15) / 16 * 16;
-        cnt = keep + LT_CAND * 4;
-        bar = cnt + (4 * (LT_THREADS / 32) + 1) * 4;
+        e = b + 4 * LT_B_BYTES;                 // 2 x [32][TA] float2
+        rec = e + 2 * LT_KB * TA * 8;           // 2 x [32][REC] float
+        x = rec + 2 * LT_KB * REC * 4;
+        cnt = (x + TA * 4 + 15) / 16 * 16;
+        bar = cnt + (LT_THREADS / 32 + 1) * 4;
         bar = (bar + 15) / 16 * 16;
         bytes = bar + 16;
     }
@@ -100,25 +98,28 @@ struct LtAxes {
     float dx[3];   // spacing of uniform axes
 };
 
+// Operand mapping.  crow = 0: rows (j, l), columns (i, c): Y = E1 E2, X = A_c E0.
+//                  crow = 1 (small T1 T2): rows (j, l, c), columns i: Y = A_c E1 E2, X = E0.
 template <bool COUNT>
 __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *__restrict__ rec, const double *__restrict__ ax0,
                                                         const double *__restrict__ ax1, const double *__restrict__ ax2,
                                                         int n0, int n1, int n2, int T0, int T1, int T2, int nt1,
                                                         int nt2, const int4 *__restrict__ items, float k, float rw2,
-                                                        const float *__restrict__ amax, LtSmem S, LtAxes X,
-                                                        float *__restrict__ partial) {
+                                                        const float *__restrict__ amax, LtSmem S, LtAxes X, int crow,
+                                                        int *__restrict__ kept, float *__restrict__ partial) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem + S.a;
     unsigned char *sB = smem + S.b;
-    float2 *sE = reinterpret_cast<float2 *>(smem + S.e);   // [32][TA]: E0 (T0), E1 (T1), E2 (T2)
-    float *sR = reinterpret_cast<float *>(smem + S.rec);  // [32][REC]
-    float *sX = reinterpret_cast<float *>(smem + S.x);    // tile coordinates, axis 0 | 1 | 2
-    int *sK = reinterpret_cast<int *>(smem + S.keep);     // kept candidates (offsets from the item start)
-    int *sCnt = reinterpret_cast<int *>(smem + S.cnt);    // [4 rounds x warps] counts, then offsets; [last]: total
+    float2 *sE0 = reinterpret_cast<float2 *>(smem + S.e);   // 2 x [32][TA]: E0 (T0), E1 (T1), E2 (T2)
+    float *sR0 = reinterpret_cast<float *>(smem + S.rec);   // 2 x [32][REC]
+    float *sX = reinterpret_cast<float *>(smem + S.x);      // tile coordinates, axis 0 | 1 | 2
+    int *sCnt = reinterpret_cast<int *>(smem + S.cnt);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    constexpr int NW = LT_THREADS / 32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int TA = T0 + T1 + T2, R_used = T1 * T2, nc_used = 3 * T0;
+    const int TA = T0 + T1 + T2;
+    const int R_used = crow ? 3 * T1 * T2 : T1 * T2, nc_used = crow ? T0 : 3 * T0;
     const int nc_tile = (nc_used + 7) / 8 * 8, NR = 2 * nc_tile;
 
     const int4 it = items[blockIdx.x];
@@ -127,7 +128,6 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
     const int i0 = tt0 * T0, j0 = tt1 * T1, l0 = tt2 * T2;
     const int e0 = min(T0, n0 - i0), e1 = min(T1, n1 - j0), e2 = min(T2, n2 - l0);
 
-    // zero both operand areas once: rows and columns beyond the tile's use stay zero
     for (int o = tid * 16; o < 4 * LT_A_BYTES + 4 * LT_B_BYTES; o += LT_THREADS * 16)
         *reinterpret_cast<uint4 *>(smem + o) = make_uint4(0, 0, 0, 0);
     for (int a = tid; a < TA; a += LT_THREADS) {
@@ -139,7 +139,6 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
     }
     if (warp == 0) tc::alloc(tc::smem_u32(tmem_slot), LT_TMEM_COLS);
     if (tid == 0) tc::mbar_init(tc::smem_u32(bar));
-    // exact power-of-two scales: |Y| <= 1 -> 2^14; |X| <= max |A| -> 2^(14 - e)
     float sx = 1.0f;
     {
         const float bound = *amax;
@@ -150,73 +149,60 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
         }
     }
     const float sy = 16384.0f;
+    // the A_c factor carries the amplitude scale on whichever side it sits
+    const float sA_scale = crow ? sx : sy, sB_scale = crow ? sy : sx;
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = tc::instr_desc(NR, LT_M);
     const float hk = -0.5f * k;
+
+    const float blo0 = sX[0], bhi0 = sX[e0 - 1], blo1 = sX[T0], bhi1 = sX[T0 + e1 - 1];
+    const float blo2 = sX[T0 + T1], bhi2 = sX[T0 + T1 + e2 - 1];
+    int *keptc = kept + (int64_t)blockIdx.x * LT_CAND;   // this CTA's kept list of one candidate round
+    bool ok = true;
     uint32_t parity = 0;
     int issued = 0;
-    bool ok = true;
-    unsigned long long mine = 0;
-    // the tile's box, for the reach test of the candidates
-    float blo[3], bhi[3];
-    blo[0] = sX[0];
-    bhi[0] = sX[e0 - 1];
-    blo[1] = sX[T0];
-    bhi[1] = sX[T0 + e1 - 1];
-    blo[2] = sX[T0 + T1];
-    bhi[2] = sX[T0 + T1 + e2 - 1];
-    constexpr int NW = LT_THREADS / 32;
-    for (int64_t cbase = it.y; cbase < it.z && ok; cbase += LT_CAND) {
-        // 0. keep the candidates within rw of the tile's box, in order
-        bool kp[4];
-        unsigned bal[4];
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            const int64_t c = cbase + r * LT_THREADS + tid;
-            kp[r] = false;
-            if (c < it.z) {
+    for (int64_t cand0 = it.y; cand0 < it.z && ok; cand0 += LT_CAND) {
+        // ---- 0. keep the round's candidates within rw of the tile's box, in order ----
+        const int64_t cend = (it.z < cand0 + LT_CAND) ? (int64_t)it.z : cand0 + LT_CAND;
+        int nk = 0;
+        for (int64_t c0 = cand0; c0 < cend; c0 += LT_THREADS) {
+            const int64_t c = c0 + tid;
+            bool kp = false;
+            if (c < cend) {
                 const float *q = rec + c * REC;
-                const float g0 = fmaxf(fmaxf(blo[0] - q[0], q[0] - bhi[0]), 0.f);
-                const float g1 = fmaxf(fmaxf(blo[1] - q[1], q[1] - bhi[1]), 0.f);
-                const float g2 = fmaxf(fmaxf(blo[2] - q[2], q[2] - bhi[2]), 0.f);
-                kp[r] = g0 * g0 + g1 * g1 + g2 * g2 <= rw2;
+                const float g0 = fmaxf(fmaxf(blo0 - q[0], q[0] - bhi0), 0.f);
+                const float g1 = fmaxf(fmaxf(blo1 - q[1], q[1] - bhi1), 0.f);
+                const float g2 = fmaxf(fmaxf(blo2 - q[2], q[2] - bhi2), 0.f);
+                kp = g0 * g0 + g1 * g1 + g2 * g2 <= rw2;
             }
-            bal[r] = __ballot_sync(0xffffffffu, kp[r]);
-            if (lane == 0) sCnt[r * NW + warp] = __popc(bal[r]);
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const int v = lane < 4 * NW ? sCnt[lane] : 0;
-            int incl = v;
+            const unsigned bl = __ballot_sync(0xffffffffu, kp);
+            if (lane == 0) sCnt[warp] = __popc(bl);
+            __syncthreads();
+            int before = 0, total = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
+            for (int w = 0; w < NW; w++) {
+                const int v = sCnt[w];
+                before += w < warp ? v : 0;
+                total += v;
             }
-            if (lane < 4 * NW) sCnt[lane] = incl - v;
-            if (lane == 31) sCnt[4 * NW] = incl;
+            if (kp) keptc[nk + before + __popc(bl & ((1u << lane) - 1u))] = (int)(c - it.y);
+            nk += total;
+            __syncthreads();
         }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < 4; r++)
-            if (kp[r])
-                sK[sCnt[r * NW + warp] + __popc(bal[r] & ((1u << lane) - 1u))] =
-                    (int)(cbase - it.y) + r * LT_THREADS + tid;
-        const int nk = sCnt[4 * NW];
-        __syncthreads();
-    for (int kb0 = 0; kb0 < nk && ok; kb0 += LT_KB) {
-        const int nb = min(LT_KB, nk - kb0);
-        // 1. records of this block
-        for (int q = tid; q < LT_KB * REC; q += LT_THREADS) {
-            const int b = q / REC;
-            sR[q] = b < nb ? rec[(it.y + sK[kb0 + b]) * REC + (q - b * REC)] : 0.0f;
-        }
-        __syncthreads();
-        // 2. 1-D factors E_d of every beam at the tile's coordinates (zero for missing beams)
-        {
+        const int nblk = (nk + LT_KB - 1) / LT_KB;
+
+        auto load_records = [&](int blk, float *dst) {
+            const int kb0 = blk * LT_KB, nb = min(LT_KB, nk - kb0);
+            for (int q = tid; q < LT_KB * REC; q += LT_THREADS) {
+                const int b = q / REC;
+                dst[q] = b < nb ? rec[(it.y + keptc[kb0 + b]) * REC + (q - b * REC)] : 0.0f;
+            }
+        };
+        auto factors = [&](int blk, const float *sR, float2 *sE) {
+            const int nb = min(LT_KB, nk - blk * LT_KB);
             const int nch = X.nch[0] + X.nch[1] + X.nch[2];
             for (int q = tid; q < LT_KB * nch; q += LT_THREADS) {
                 const int b = q / nch, c = q - b * nch;
@@ -249,63 +235,97 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
                     }
                 }
             }
-        }
-        if (COUNT) {
-            for (int q = tid; q < nb * R_used * T0; q += LT_THREADS) {
-                const int b = q / (R_used * T0), rem = q - b * R_used * T0;
-                const int i = rem / R_used, r = rem - i * R_used, j = r / T2, l = r - j * T2;
-                if (i < e0 && j < e1 && l < e2) {
-                    const float *rb = sR + b * REC;
-                    const float d0 = sX[i] - rb[0], d1 = sX[T0 + j] - rb[1], d2 = sX[T0 + T1 + l] - rb[2];
-                    if (d0 * d0 + d1 * d1 + d2 * d2 <= rw2) mine++;
+            if (COUNT) {
+                unsigned long long mine = 0;
+                const int np = T0 * T1 * T2;
+                for (int q = tid; q < nb * np; q += LT_THREADS) {
+                    const int b = q / np, rem = q - b * np;
+                    const int i = rem / (T1 * T2), r = rem - i * (T1 * T2), j = r / T2, l = r - j * T2;
+                    if (i < e0 && j < e1 && l < e2) {
+                        const float *rb = sR + b * REC;
+                        const float d0 = sX[i] - rb[0], d1 = sX[T0 + j] - rb[1], d2 = sX[T0 + T1 + l] - rb[2];
+                        if (d0 * d0 + d1 * d1 + d2 * d2 <= rw2) mine++;
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+                if (lane == 0 && mine) atomicAdd(&g_tc_pairs, mine);
+            }
+        };
+
+        // ---- software pipeline over the round's blocks of 32 kept beams ----
+        // block n: operands from (sR, sE)[n % 2]; while the tensor cores run block n, the factors of
+        // n+1 are formed and the records of n+2 loaded
+        if (nblk > 0) load_records(0, sR0);
+        __syncthreads();
+        if (nblk > 0) factors(0, sR0, sE0);
+        if (nblk > 1) load_records(1, sR0 + LT_KB * REC);
+        for (int n = 0; n < nblk; n++) {
+            const float *sR = sR0 + (n & 1) * LT_KB * REC;
+            const float2 *sE = sE0 + (n & 1) * LT_KB * TA;
+            bool arrived = true;
+            if (issued > 0 && tid == 0) arrived = tc::mbar_wait(tc::smem_u32(bar), parity);
+            if (issued > 0) parity ^= 1u;
+            ok = __syncthreads_and(arrived ? 1 : 0) != 0;   // factors(n) visible; the previous MMAs done
+            tc::fence_after();
+            if (!ok) break;
+        // operands: consecutive threads take consecutive rows (conflict-free 16-byte stores)
+        for (int q = tid; q < R_used * 4; q += LT_THREADS) {
+            const int r = q % R_used, o = q / R_used;
+            float re[8], im[8];
+            if (!crow) {
+                const int j = r / T2, l = r - j * T2;
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int b = 8 * o + u;
+                    const float2 a1 = sE[b * TA + T0 + j], a2 = sE[b * TA + T0 + T1 + l];
+                    re[u] = a1.x * a2.x - a1.y * a2.y;
+                    im[u] = a1.x * a2.y + a1.y * a2.x;
+                }
+            } else {
+                const int c = r % 3, jl = r / 3, j = jl / T2, l = jl - j * T2;
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int b = 8 * o + u;
+                    const float2 a1 = sE[b * TA + T0 + j], a2 = sE[b * TA + T0 + T1 + l];
+                    const float er = a1.x * a2.x - a1.y * a2.y, ei = a1.x * a2.y + a1.y * a2.x;
+                    const float ar = sR[b * REC + 6 + 2 * c], ai = sR[b * REC + 7 + 2 * c];
+                    re[u] = ar * er - ai * ei;
+                    im[u] = ar * ei + ai * er;
                 }
             }
-        }
-        // 3. the tensor cores must be done with the previous operand block
-        if (issued > 0) {
-            const bool arrived = tc::mbar_wait(tc::smem_u32(bar), parity);
-            parity ^= 1u;
-            tc::fence_after();
-            ok = __syncthreads_and(arrived ? 1 : 0) != 0;
-            if (!ok) break;
-        } else {
-            __syncthreads();
-        }
-        // 4. operands: A' rows (j,l) from Y = E1 E2; B' rows (i,c) from X = A_c E0
-        for (int q = tid; q < R_used * 4; q += LT_THREADS) {
-            const int r = q >> 2, o = q & 3;
-            const int j = r / T2, l = r - j * T2;
-            float re[8], im[8];
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int b = 8 * o + u;
-                const float2 a1 = sE[b * TA + T0 + j], a2 = sE[b * TA + T0 + T1 + l];
-                re[u] = a1.x * a2.x - a1.y * a2.y;
-                im[u] = a1.x * a2.y + a1.y * a2.x;
-            }
             const uint32_t off = tc::kmaj_off(r, 8 * o);
-            tc::split8(sA + 0 * LT_A_BYTES, sA + 1 * LT_A_BYTES, off, re, sy);
-            tc::split8(sA + 2 * LT_A_BYTES, sA + 3 * LT_A_BYTES, off, im, sy);
+            tc::split8(sA + 0 * LT_A_BYTES, sA + 1 * LT_A_BYTES, off, re, sA_scale);
+            tc::split8(sA + 2 * LT_A_BYTES, sA + 3 * LT_A_BYTES, off, im, sA_scale);
         }
         for (int q = tid; q < nc_used * 4; q += LT_THREADS) {
-            const int cq = q >> 2, o = q & 3;
-            const int i = cq / 3, c = cq - 3 * i;
+            const int cq = q % nc_used, o = q / nc_used;
             float re[8], im[8], nim[8];
+            if (!crow) {
+                const int i = cq / 3, c = cq - 3 * i;
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int b = 8 * o + u;
-                const float2 e = sE[b * TA + i];
-                const float ar = sR[b * REC + 6 + 2 * c], ai = sR[b * REC + 7 + 2 * c];
-                re[u] = ar * e.x - ai * e.y;
-                im[u] = ar * e.y + ai * e.x;
-                nim[u] = -im[u];
+                for (int u = 0; u < 8; u++) {
+                    const int b = 8 * o + u;
+                    const float2 e = sE[b * TA + i];
+                    const float ar = sR[b * REC + 6 + 2 * c], ai = sR[b * REC + 7 + 2 * c];
+                    re[u] = ar * e.x - ai * e.y;
+                    im[u] = ar * e.y + ai * e.x;
+                    nim[u] = -im[u];
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const float2 e = sE[(8 * o + u) * TA + cq];
+                    re[u] = e.x;
+                    im[u] = e.y;
+                    nim[u] = -e.y;
+                }
             }
             const uint32_t top = tc::kmaj_off(cq, 8 * o), bot = tc::kmaj_off(nc_tile + cq, 8 * o);
             // B'_re = [Re X ; Im X], B'_im = [-Im X ; Re X]
-            tc::split8(sB + 0 * LT_B_BYTES, sB + 1 * LT_B_BYTES, top, re, sx);
-            tc::split8(sB + 0 * LT_B_BYTES, sB + 1 * LT_B_BYTES, bot, im, sx);
-            tc::split8(sB + 2 * LT_B_BYTES, sB + 3 * LT_B_BYTES, top, nim, sx);
-            tc::split8(sB + 2 * LT_B_BYTES, sB + 3 * LT_B_BYTES, bot, re, sx);
+            tc::split8(sB + 0 * LT_B_BYTES, sB + 1 * LT_B_BYTES, top, re, sB_scale);
+            tc::split8(sB + 0 * LT_B_BYTES, sB + 1 * LT_B_BYTES, bot, im, sB_scale);
+            tc::split8(sB + 2 * LT_B_BYTES, sB + 3 * LT_B_BYTES, top, nim, sB_scale);
+            tc::split8(sB + 2 * LT_B_BYTES, sB + 3 * LT_B_BYTES, bot, re, sB_scale);
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -328,21 +348,25 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
             tc::commit(tc::smem_u32(bar));
         }
         issued++;
-    }
+        // while the tensor cores work: factors of block n+1, records of block n+2
+        if (n + 1 < nblk)
+            factors(n + 1, sR0 + ((n + 1) & 1) * LT_KB * REC, sE0 + ((n + 1) & 1) * LT_KB * TA);
+        if (n + 2 < nblk) load_records(n + 2, sR0 + (n & 1) * LT_KB * REC);
+        }
+        __syncthreads();   // the round's kept list and staging buffers are reused by the next round
     }
     if (ok && issued > 0) {
-        const bool arrived = tc::mbar_wait(tc::smem_u32(bar), parity);
-        tc::fence_after();
+        bool arrived = true;
+        if (tid == 0) arrived = tc::mbar_wait(tc::smem_u32(bar), parity);
         ok = __syncthreads_and(arrived ? 1 : 0) != 0;
+        tc::fence_after();
     }
     if (!ok && tid == 0) atomicExch(&g_tc_err, 1);
     if (ok) {
-        // epilogue: warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31 (rows (j, l)) and split the
-        // 8-column chunks of (i, c) (Re at cq, Im at nc_tile + cq) between them
+        // epilogue: warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31 and split the 8-column chunks
         const int quarter = warp & 3, r = quarter * 32 + lane;
         const int TP = T0 * T1 * T2;
         const float inv = 1.0f / (sx * sy);
-        const int j = r / T2, l = r - j * T2;
         float *dst = partial + (int64_t)blockIdx.x * TP * 6;
         const uint32_t lanebase = (uint32_t)(quarter * 32) << 16;
         for (int c0 = (warp >> 2) * 8; c0 < nc_tile; c0 += 16) {
@@ -359,7 +383,19 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
                 for (int u = 0; u < 8; u++) {
                     const int cq = c0 + u;
                     if (cq < nc_used) {
-                        const int i = cq / 3, c = cq - 3 * i;
+                        int i, c, j, l;
+                        if (!crow) {
+                            i = cq / 3;
+                            c = cq - 3 * i;
+                            j = r / T2;
+                            l = r - j * T2;
+                        } else {
+                            i = cq;
+                            c = r % 3;
+                            const int jl = r / 3;
+                            j = jl / T2;
+                            l = jl - j * T2;
+                        }
                         const int p = (i * T1 + j) * T2 + l;
                         dst[p * 6 + 2 * c] = re[u] * inv;
                         dst[p * 6 + 2 * c + 1] = im[u] * inv;
@@ -367,10 +403,6 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
                 }
             }
         }
-    }
-    if (COUNT) {
-        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-        if (lane == 0 && mine) atomicAdd(&g_tc_pairs, mine);
     }
     tc::fence_before();
     __syncthreads();
@@ -417,10 +449,13 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
         X.nch[d] = (Td + X.len[d] - 1) / X.len[d];
         X.dx[d] = (float)plan.dx[d];
     }
-    FGA_TRY(ws.partial.ensure(sizeof(float) * 6 * (size_t)TP * (size_t)std::max(plan.nitems, 1) + 64));
-    // scratch at the end of the partial buffer: the bound of the records' amplitudes
+    FGA_TRY(ws.partial.ensure(sizeof(float) * 6 * (size_t)TP * (size_t)std::max(plan.nitems, 1) + 64 +
+                              sizeof(int) * (size_t)LT_CAND * (size_t)std::max(plan.nitems, 1)));
+    const int crow = 3 * T1 * T2 <= LT_M ? 1 : 0;
+    // scratch after the partial sums: the bound of the records' amplitudes, the kept-beam lists
     char *tail = ws.partial.as<char>() + sizeof(float) * 6 * (size_t)TP * (size_t)std::max(plan.nitems, 1);
     float *amax = reinterpret_cast<float *>(tail);
+    int *kept = reinterpret_cast<int *>(tail + 64);
     FGA_CUDA(cudaMemsetAsync(tail, 0, 64, s));
     const int cnt = prof_counting() ? 1 : 0;
     prof_add_pairs_tested(plan.pairs_tested);
@@ -435,14 +470,14 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
             FGA_CUDA(cudaFuncSetAttribute(lattice_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S.bytes));
             lattice_tc_kernel<true><<<plan.nitems, LT_THREADS, S.bytes, s>>>(
                 static_cast<const float *>(rec), plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2],
-                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S, X,
-                ws.partial.as<float>());
+                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S, X, crow,
+                kept, ws.partial.as<float>());
         } else {
             FGA_CUDA(cudaFuncSetAttribute(lattice_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S.bytes));
             lattice_tc_kernel<false><<<plan.nitems, LT_THREADS, S.bytes, s>>>(
                 static_cast<const float *>(rec), plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2],
-                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S, X,
-                ws.partial.as<float>());
+                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S, X, crow,
+                kept, ws.partial.as<float>());
         }
         FGA_CUDA(cudaGetLastError());
     }
