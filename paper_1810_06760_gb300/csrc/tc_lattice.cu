@@ -76,13 +76,14 @@ constexpr int LT_CAND = 4096;           // candidates filtered per round (per-CT
 constexpr uint32_t LT_TMEM_COLS = 256;
 
 struct LtSmem {
-    int a, b, e, rec, x, cnt, bar, bytes;
-    __host__ __device__ void init(int TA) {
+    int a, b, e, rec, w, x, cnt, bar, bytes;
+    __host__ __device__ void init(int TA, bool with_w) {
         a = 0;
         b = a + 4 * LT_A_BYTES;
         e = b + 4 * LT_B_BYTES;                 // 2 x [32][TA] float2
         rec = e + 2 * LT_KB * TA * 8;           // 2 x [32][REC] float
-        x = rec + 2 * LT_KB * REC * 4;
+        w = rec + 2 * LT_KB * REC * 4;          // 2 x [32][3] float2: A_c E2 of single-plane tiles
+        x = w + (with_w ? 2 * LT_KB * 3 * 8 : 0);
         cnt = (x + TA * 4 + 15) / 16 * 16;
         bar = cnt + (LT_THREADS / 32 + 1) * 4;
         bar = (bar + 15) / 16 * 16;
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
     unsigned char *sB = smem + S.b;
     float2 *sE0 = reinterpret_cast<float2 *>(smem + S.e);   // 2 x [32][TA]: E0 (T0), E1 (T1), E2 (T2)
     float *sR0 = reinterpret_cast<float *>(smem + S.rec);   // 2 x [32][REC]
+    float2 *sW0 = reinterpret_cast<float2 *>(smem + S.w);   // 2 x [32][3]
     float *sX = reinterpret_cast<float *>(smem + S.x);      // tile coordinates, axis 0 | 1 | 2
     int *sCnt = reinterpret_cast<int *>(smem + S.cnt);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);
@@ -157,6 +159,10 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = tc::instr_desc(NR, LT_M);
     const float hk = -0.5f * k;
+    // exact small-integer division by float reciprocals (quotients below 2^12, divisors below 2^8)
+    const int nch = X.nch[0] + X.nch[1] + X.nch[2];
+    const float inv_nch = 1.0f / (float)nch, inv_R = 1.0f / (float)R_used, inv_nc = 1.0f / (float)nc_used;
+    const float inv_T2 = 1.0f / (float)T2, inv_3 = 1.0f / 3.0f;
 
     const float blo0 = sX[0], bhi0 = sX[e0 - 1], blo1 = sX[T0], bhi1 = sX[T0 + e1 - 1];
     const float blo2 = sX[T0 + T1], bhi2 = sX[T0 + T1 + e2 - 1];
@@ -201,18 +207,20 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
                 dst[q] = b < nb ? rec[(it.y + keptc[kb0 + b]) * REC + (q - b * REC)] : 0.0f;
             }
         };
-        auto factors = [&](int blk, const float *sR, float2 *sE) {
+        auto factors = [&](int blk, const float *sR, float2 *sE, float2 *sW) {
             const int nb = min(LT_KB, nk - blk * LT_KB);
-            const int nch = X.nch[0] + X.nch[1] + X.nch[2];
             for (int q = tid; q < LT_KB * nch; q += LT_THREADS) {
-                const int b = q / nch, c = q - b * nch;
+                const int b = (int)(((float)q + 0.5f) * inv_nch), c = q - b * nch;
                 const int d = c < X.nch[0] ? 0 : (c < X.nch[0] + X.nch[1] ? 1 : 2);
                 const int cc = c - (d == 0 ? 0 : (d == 1 ? X.nch[0] : X.nch[0] + X.nch[1]));
                 const int off = d == 0 ? 0 : (d == 1 ? T0 : T0 + T1), Td = d == 0 ? T0 : (d == 1 ? T1 : T2);
                 const int a0 = cc * X.len[d], a1 = min(a0 + X.len[d], Td);
                 float2 *dst = sE + b * TA + off;
+                const bool wfold = crow && d == 2 && T2 == 1;   // also A_c E2 for the component rows
                 if (b >= nb) {
                     for (int a = a0; a < a1; a++) dst[a] = make_float2(0.f, 0.f);
+                    if (wfold)
+                        for (int c = 0; c < 3; c++) sW[b * 3 + c] = make_float2(0.f, 0.f);
                     continue;
                 }
                 const float Qd = sR[b * REC + d], Pd = sR[b * REC + 3 + d];
@@ -220,6 +228,11 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
                 float er, ei;
                 gauss_phase_exp<float>(k * Pd * x, hk * x * x, &er, &ei);
                 dst[a0] = make_float2(er, ei);
+                if (wfold)
+                    for (int c = 0; c < 3; c++) {
+                        const float ar = sR[b * REC + 6 + 2 * c], ai = sR[b * REC + 7 + 2 * c];
+                        sW[b * 3 + c] = make_float2(ar * er - ai * ei, ar * ei + ai * er);
+                    }
                 if (a1 - a0 > 1) {
                     const float h = X.dx[d];
                     float rr, ri;
@@ -257,7 +270,7 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
         // n+1 are formed and the records of n+2 loaded
         if (nblk > 0) load_records(0, sR0);
         __syncthreads();
-        if (nblk > 0) factors(0, sR0, sE0);
+        if (nblk > 0) factors(0, sR0, sE0, sW0);
         if (nblk > 1) load_records(1, sR0 + LT_KB * REC);
         for (int n = 0; n < nblk; n++) {
             const float *sR = sR0 + (n & 1) * LT_KB * REC;
@@ -269,11 +282,12 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
             tc::fence_after();
             if (!ok) break;
         // operands: consecutive threads take consecutive rows (conflict-free 16-byte stores)
+        const float2 *sW = sW0 + (n & 1) * LT_KB * 3;
         for (int q = tid; q < R_used * 4; q += LT_THREADS) {
-            const int r = q % R_used, o = q / R_used;
+            const int o = (int)(((float)q + 0.5f) * inv_R), r = q - o * R_used;
             float re[8], im[8];
             if (!crow) {
-                const int j = r / T2, l = r - j * T2;
+                const int j = (int)(((float)r + 0.5f) * inv_T2), l = r - j * T2;
 #pragma unroll
                 for (int u = 0; u < 8; u++) {
                     const int b = 8 * o + u;
@@ -282,15 +296,26 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
                     im[u] = a1.x * a2.y + a1.y * a2.x;
                 }
             } else {
-                const int c = r % 3, jl = r / 3, j = jl / T2, l = jl - j * T2;
+                const int jl = (int)(((float)r + 0.5f) * inv_3), c = r - 3 * jl;
+                if (T2 == 1) {
 #pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const int b = 8 * o + u;
-                    const float2 a1 = sE[b * TA + T0 + j], a2 = sE[b * TA + T0 + T1 + l];
-                    const float er = a1.x * a2.x - a1.y * a2.y, ei = a1.x * a2.y + a1.y * a2.x;
-                    const float ar = sR[b * REC + 6 + 2 * c], ai = sR[b * REC + 7 + 2 * c];
-                    re[u] = ar * er - ai * ei;
-                    im[u] = ar * ei + ai * er;
+                    for (int u = 0; u < 8; u++) {
+                        const int b = 8 * o + u;
+                        const float2 e = sE[b * TA + T0 + jl], wv = sW[b * 3 + c];
+                        re[u] = wv.x * e.x - wv.y * e.y;
+                        im[u] = wv.x * e.y + wv.y * e.x;
+                    }
+                } else {
+                    const int j = (int)(((float)jl + 0.5f) * inv_T2), l = jl - j * T2;
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        const int b = 8 * o + u;
+                        const float2 a1 = sE[b * TA + T0 + j], a2 = sE[b * TA + T0 + T1 + l];
+                        const float er = a1.x * a2.x - a1.y * a2.y, ei = a1.x * a2.y + a1.y * a2.x;
+                        const float ar = sR[b * REC + 6 + 2 * c], ai = sR[b * REC + 7 + 2 * c];
+                        re[u] = ar * er - ai * ei;
+                        im[u] = ar * ei + ai * er;
+                    }
                 }
             }
             const uint32_t off = tc::kmaj_off(r, 8 * o);
@@ -298,10 +323,10 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
             tc::split8(sA + 2 * LT_A_BYTES, sA + 3 * LT_A_BYTES, off, im, sA_scale);
         }
         for (int q = tid; q < nc_used * 4; q += LT_THREADS) {
-            const int cq = q % nc_used, o = q / nc_used;
+            const int o = (int)(((float)q + 0.5f) * inv_nc), cq = q - o * nc_used;
             float re[8], im[8], nim[8];
             if (!crow) {
-                const int i = cq / 3, c = cq - 3 * i;
+                const int i = (int)(((float)cq + 0.5f) * inv_3), c = cq - 3 * i;
 #pragma unroll
                 for (int u = 0; u < 8; u++) {
                     const int b = 8 * o + u;
@@ -350,7 +375,8 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
         issued++;
         // while the tensor cores work: factors of block n+1, records of block n+2
         if (n + 1 < nblk)
-            factors(n + 1, sR0 + ((n + 1) & 1) * LT_KB * REC, sE0 + ((n + 1) & 1) * LT_KB * TA);
+            factors(n + 1, sR0 + ((n + 1) & 1) * LT_KB * REC, sE0 + ((n + 1) & 1) * LT_KB * TA,
+                    sW0 + ((n + 1) & 1) * LT_KB * 3);
         if (n + 2 < nblk) load_records(n + 2, sR0 + (n & 1) * LT_KB * REC);
         }
         __syncthreads();   // the round's kept list and staging buffers are reused by the next round
@@ -440,8 +466,9 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
         set_error("lattice tile does not fit the tensor-core kernel");
         return FGA_ERR_UNSUPPORTED;
     }
+    const int crow = 3 * T1 * T2 <= LT_M ? 1 : 0;
     LtSmem S;
-    S.init(T0 + T1 + T2);
+    S.init(T0 + T1 + T2, crow && T2 == 1);
     LtAxes X;
     for (int d = 0; d < 3; d++) {
         const int Td = plan.T[d];
@@ -451,7 +478,6 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
     }
     FGA_TRY(ws.partial.ensure(sizeof(float) * 6 * (size_t)TP * (size_t)std::max(plan.nitems, 1) + 64 +
                               sizeof(int) * (size_t)LT_CAND * (size_t)std::max(plan.nitems, 1)));
-    const int crow = 3 * T1 * T2 <= LT_M ? 1 : 0;
     // scratch after the partial sums: the bound of the records' amplitudes, the kept-beam lists
     char *tail = ws.partial.as<char>() + sizeof(float) * 6 * (size_t)TP * (size_t)std::max(plan.nitems, 1);
     float *amax = reinterpret_cast<float *>(tail);

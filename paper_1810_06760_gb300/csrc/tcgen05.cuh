@@ -82,17 +82,21 @@ __device__ __forceinline__ void store8(unsigned char *base, uint32_t off, const 
     v.w = (uint32_t)__half_as_ushort(h[6]) | ((uint32_t)__half_as_ushort(h[7]) << 16);
     *reinterpret_cast<uint4 *>(base + off) = v;
 }
-// hi/lo split of 8 values scaled by s, stored as two 16-byte rows (hi and lo operand copies)
+// hi/lo split of 8 values scaled by s, stored as two 16-byte rows (hi and lo operand copies); pairs of
+// values are rounded to FP16 together (one f16x2 conversion per pair)
 __device__ __forceinline__ void split8(unsigned char *hi, unsigned char *lo, uint32_t off, const float x[8], float s) {
-    __half h[8], l[8];
+    uint32_t h[4], l[4];
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-        const float v = x[q] * s;
-        h[q] = __float2half_rn(v);
-        l[q] = __float2half_rn(v - __half2float(h[q]));
+    for (int q = 0; q < 4; q++) {
+        const float a = x[2 * q] * s, b = x[2 * q + 1] * s;
+        const __half2 hh = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(hh);
+        const __half2 ll = __floats2half2_rn(a - hf.x, b - hf.y);
+        h[q] = *reinterpret_cast<const uint32_t *>(&hh);
+        l[q] = *reinterpret_cast<const uint32_t *>(&ll);
     }
-    store8(hi, off, h);
-    store8(lo, off, l);
+    *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
