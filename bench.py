@@ -397,7 +397,7 @@ def run_serving(args):
             delay = t0 + ta - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            ids.append(server.submit(desc, w.dt, w.nsteps, w.times, rx, rw=w.rw, keep=(f,)))
+            ids.append(server.submit(desc, w.dt, w.nsteps, w.times, rw=w.rw, keep=(f,), rx_axes=w.rx_axes))
         infos = [server.wait(i)[1] for i in ids]
         wall = time.perf_counter() - t0
         st = server.stats()
@@ -409,7 +409,7 @@ def run_serving(args):
     small = [staged[i] for i in order[:4]]
     sv = fga.Server(model, n_workers=1)
     for w, desc, f, rx in small:
-        sv.wait(sv.submit(desc, w.dt, w.nsteps, w.times, rx, rw=w.rw, keep=(f,)))
+        sv.wait(sv.submit(desc, w.dt, w.nsteps, w.times, rw=w.rw, keep=(f,), rx_axes=w.rx_axes))
     sv.close()
     # solo capacity: every request alone, back to back on one worker
     solo, solo_wall, _ = run([0.0] * len(staged), 1)
@@ -431,7 +431,7 @@ def run_serving(args):
         "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
         "config": {"workload": "serving stream: 64 requests, Poisson arrivals (seed 1) at 0.7 x solo capacity, "
                                "k in {32,64,128}, N log-uniform 1e5..2e7 -> q n_q^3 x p 8^3 x 4 classes, "
-                               "smooth 128^3 model resident, T=0.5 (200 steps), 256 rx x 200 samples",
+                               "smooth 128^3 model resident, T=0.5 (200 steps), 256 rx (16x16 lattice) x 200 samples",
                    "workers": n_workers, "parallelism": f"replicas x{world}"},
         "latency_s": {"p50": q(50), "p99": q(99), "max": lat[-1], "mean": float(np.mean(lat))},
         "solo": {"capacity_req_per_s": capacity, "service_s_p50": float(np.median(service)),

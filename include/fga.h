@@ -214,7 +214,8 @@ fga_status fga_beams_export_all(const fga_beams *b, int64_t cap, int64_t *n_out,
  * and run one request at a time, so up to n_workers solves share the GPU; record_cap_bytes (<= 0:
  * 2e9) caps each solve's per-window record buffer.  The caller keeps every buffer a request names
  * (f, g, receivers, snapshot points, outputs; all DEVICE as for fga_solve) alive and untouched until
- * fga_server_wait returns for it; the times array is copied at submission.  Layered media are not
+ * fga_server_wait returns for it; the times array and lattice descriptors (with their host axes) are copied
+ * at submission.  Layered media are not
  * served.  Kernel profiling (fga_profile_enable) must be off while a server runs.
  *  fga_server_wait blocks until the request is done (timeout_s <= 0: no limit; else FGA_ERR_TIMEOUT),
  *  returns the request's own status and fills info (may be NULL); a request id can be waited once.

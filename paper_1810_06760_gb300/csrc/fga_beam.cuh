@@ -70,6 +70,47 @@ __device__ __forceinline__ void model_eval(const ModelDev &M, int wave, const R 
         }
         const int64_t s1 = M.n[2], s0 = (int64_t)M.n[1] * M.n[2];
         const int64_t base = (int64_t)i[0] * s0 + (int64_t)i[1] * s1 + i[2];
+        if constexpr (sizeof(R) == 4) {
+            // FP32: the 10 fields as 5 pairs, each lerp step one packed FP32x2 FMA
+            float2 acc2[5];
+#pragma unroll
+            for (int f = 0; f < 5; f++) acc2[f] = make_float2(0.f, 0.f);
+            const float2 f2 = make_float2(fr[2], fr[2]), m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+                float2 e2[5];
+#pragma unroll
+                for (int f = 0; f < 5; f++) e2[f] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < 2; b++) {
+                    const int64_t node = base + a * s0 + b * s1;
+                    const float4 *p0 = G + 3 * node;
+                    const float4 u0 = __ldg(p0), u1 = __ldg(p0 + 1), u2 = __ldg(p0 + 2);
+                    const float4 v0 = __ldg(p0 + 3), v1 = __ldg(p0 + 4), v2 = __ldg(p0 + 5);
+                    const float2 lo[5] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
+                                          make_float2(u1.z, u1.w), make_float2(u2.x, u2.y)};
+                    const float2 hi[5] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                                          make_float2(v1.z, v1.w), make_float2(v2.x, v2.y)};
+                    const float wb = b ? fr[1] : 1.0f - fr[1];
+                    const float2 wb2 = make_float2(wb, wb);
+#pragma unroll
+                    for (int f = 0; f < 5; f++) {
+                        const float2 d = __ffma2_rn(lo[f], m1, hi[f]);   // hi - lo
+                        const float2 t = __ffma2_rn(f2, d, lo[f]);       // lo + fr2 (hi - lo)
+                        e2[f] = __ffma2_rn(wb2, t, e2[f]);
+                    }
+                }
+                const float wa = a ? fr[0] : 1.0f - fr[0];
+                const float2 wa2 = make_float2(wa, wa);
+#pragma unroll
+                for (int f = 0; f < 5; f++) acc2[f] = __ffma2_rn(wa2, e2[f], acc2[f]);
+            }
+#pragma unroll
+            for (int f = 0; f < 5; f++) {
+                c[2 * f] = acc2[f].x;
+                c[2 * f + 1] = acc2[f].y;
+            }
+        } else {
         R acc[10];
 #pragma unroll
         for (int f = 0; f < 10; f++) acc[f] = R(0);
@@ -99,6 +140,7 @@ __device__ __forceinline__ void model_eval(const ModelDev &M, int wave, const R 
         }
 #pragma unroll
         for (int f = 0; f < 10; f++) c[f] = acc[f];
+        }
     } else {  // layered
         int l = 0;
         for (int q = 0; q < M.nlay - 1; q++) l += (x[2] >= mp<R>(M.zif[q], M.fzif[q])) ? 1 : 0;

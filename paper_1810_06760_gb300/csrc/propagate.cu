@@ -5,6 +5,22 @@
 
 namespace fga {
 
+// out = x + h k over the NF state reals (FP32: pairs as packed FP32x2 FMAs)
+template <typename R> __device__ __forceinline__ void axpy_state(R *out, const R *x, R h, const R *kv) {
+    if constexpr (sizeof(R) == 4) {
+        const float2 h2 = make_float2(h, h);
+#pragma unroll
+        for (int f = 0; f < NF; f += 2) {
+            const float2 r = __ffma2_rn(h2, make_float2(kv[f], kv[f + 1]), make_float2(x[f], x[f + 1]));
+            out[f] = r.x;
+            out[f + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < NF; f++) out[f] = x[f] + h * kv[f];
+    }
+}
+
 template <typename R, int WAVE, int MED>
 __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st, const int32_t *__restrict__ flags,
                                                   int64_t cap, int64_t beg, int64_t n, R sg, R dt, int nsteps,
@@ -23,26 +39,16 @@ __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st
     const R h2 = R(0.5) * dt, h3 = dt / R(3), h6 = dt / R(6);
     for (int step = 0; step < nsteps; step++) {
         R acc[NF], tmp[NF], kk[NF];
-#pragma unroll
-        for (int f = 0; f < NF; f++) {
-            acc[f] = y[f] + h6 * k1[f];
-            tmp[f] = y[f] + h2 * k1[f];
-        }
+        axpy_state<R>(acc, y, h6, k1);
+        axpy_state<R>(tmp, y, h2, k1);
         beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-#pragma unroll
-        for (int f = 0; f < NF; f++) {
-            acc[f] += h3 * kk[f];
-            tmp[f] = y[f] + h2 * kk[f];
-        }
+        axpy_state<R>(acc, acc, h3, kk);
+        axpy_state<R>(tmp, y, h2, kk);
         beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-#pragma unroll
-        for (int f = 0; f < NF; f++) {
-            acc[f] += h3 * kk[f];
-            tmp[f] = y[f] + dt * kk[f];
-        }
+        axpy_state<R>(acc, acc, h3, kk);
+        axpy_state<R>(tmp, y, dt, kk);
         beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-#pragma unroll
-        for (int f = 0; f < NF; f++) acc[f] += h6 * kk[f];
+        axpy_state<R>(acc, acc, h6, kk);
         // k1 of the next step = f(y_{n+1}); also the right-end slope of the Hermite interpolant
         beam_rhs<R, WAVE, MED>(M, sg, ref_e1, acc, kk);
         while (js < n_samp && samp_step[js] == step) {

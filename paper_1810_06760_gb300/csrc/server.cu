@@ -34,6 +34,8 @@ struct Request {
     fga_init_desc init{};
     fga_solve_desc sd{};
     std::vector<double> times;
+    fga_lattice rxL{}, snL{};                  // copies of lattice descriptors (axes below)
+    std::vector<double> rx_axes[3], sn_axes[3];
     void *seis_out = nullptr, *snap_out = nullptr;
     double bytes = 0.0;
     int64_t beams = 0;
@@ -178,6 +180,26 @@ fga_status fga_server_submit(fga_server *sv, const fga_init_desc *init, const fg
     r->sd = *sd;
     r->times.assign(sd->times, sd->times + sd->n_times);
     r->sd.times = r->times.data();
+    // lattice descriptors are host data: keep copies with the request
+    auto copy_lattice = [](const fga_lattice *src, fga_lattice &dst, std::vector<double> ax[3]) {
+        dst = *src;
+        for (int d = 0; d < 3; d++) {
+            ax[d].assign(src->axis[d], src->axis[d] + std::max(src->n[d], 0));
+            dst.axis[d] = ax[d].data();
+        }
+    };
+    if (sd->rx_lattice) {
+        FGA_CHECK(sd->rx_lattice->n[0] >= 1 && sd->rx_lattice->n[1] >= 1 && sd->rx_lattice->n[2] >= 1,
+                  "fga_server_submit: bad receiver lattice");
+        copy_lattice(sd->rx_lattice, r->rxL, r->rx_axes);
+        r->sd.rx_lattice = &r->rxL;
+    }
+    if (sd->snap_lattice) {
+        FGA_CHECK(sd->snap_lattice->n[0] >= 1 && sd->snap_lattice->n[1] >= 1 && sd->snap_lattice->n[2] >= 1,
+                  "fga_server_submit: bad snapshot lattice");
+        copy_lattice(sd->snap_lattice, r->snL, r->sn_axes);
+        r->sd.snap_lattice = &r->snL;
+    }
     r->seis_out = seis_out;
     r->snap_out = snap_out;
     r->bytes = estimate_solve_bytes(init, sv->rec_cap);

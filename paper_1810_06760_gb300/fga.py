@@ -414,18 +414,31 @@ class Server:
         _check(lib().fga_server_create(C.byref(h), model.h, C.byref(d)))
         self.h, self.model, self._keep = h, model, {}
 
-    def submit(self, desc: InitDesc, dt: float, nsteps: int, times, rx, rw: float = 0.0, keep=()):
+    def submit(self, desc: InitDesc, dt: float, nsteps: int, times, rx=None, rw: float = 0.0, keep=(),
+               rx_axes=None):
+        """Queue a forward solve; receivers as points rx [n_rx, 3] (CUDA float64) or a lattice rx_axes
+        (three 1-D arrays).  Returns the request id."""
         import torch
         times = np.ascontiguousarray(times, dtype=np.float64)
         sd = SolveDesc()
         sd.dt, sd.nsteps = float(dt), int(nsteps)
         sd.n_times, sd.times = times.size, times.ctypes.data if times.size else None
-        sd.n_rx, sd.rx = rx.shape[0], _dptr(rx)
         sd.rw = float(rw)
-        out = torch.empty((times.size, rx.shape[0], 3), dtype=_cdtype(desc.precision), device=rx.device)
+        extra = ()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if rx_axes is not None:
+            Lr, ka = make_lattice(rx_axes)
+            sd.rx_lattice = C.cast(C.pointer(Lr), C.c_void_p)
+            shape = (times.size,) + tuple(a.size for a in ka) + (3,)
+            extra = (Lr, ka)
+        else:
+            sd.n_rx, sd.rx = rx.shape[0], _dptr(rx)
+            shape = (times.size, rx.shape[0], 3)
+            dev = rx.device
+        out = torch.empty(shape, dtype=_cdtype(desc.precision), device=dev)
         rid = C.c_int64()
         _check(lib().fga_server_submit(self.h, C.byref(desc), C.byref(sd), _dptr(out), None, C.byref(rid)))
-        self._keep[rid.value] = (desc, times, rx, out, keep)
+        self._keep[rid.value] = (desc, times, rx, out, keep, extra)
         return rid.value
 
     def wait(self, rid: int, timeout: float = 0.0):

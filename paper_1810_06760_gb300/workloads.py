@@ -356,6 +356,6 @@ def serving_requests(n: int = 64, seed: int = 1, n_range=(1e5, 2e7), ks=(32.0, 6
         f = _packet(y0, dy, ny, k, x0, b, d)
         mesh = centred_mesh(nq, x0, np_, d, mesh_radius(k, 6.0), mesh_radius(k, 4.8))
         w = Workload("serving", k, med, ny, y0, dy, f, None, mesh, tuple(classes), dt, nsteps, times, rx,
-                     window_radius(k))
+                     window_radius(k), rx_axes=(r, r, np.zeros(1)))
         out.append(ServingRequest(t, w, int(round(N))))
     return out

@@ -27,18 +27,6 @@ def _requests():
                               rx_side=4, n_times=6, grid_n=32)
 
 
-def _submit_all(fga, server, reqs, prec=0):
-    import torch
-    ids, keep = [], []
-    for r in reqs:
-        w = r.workload
-        model, desc, k = gpu_setup(w, prec)
-        rx = torch.as_tensor(w.receivers, device="cuda")
-        ids.append(server.submit(desc, w.dt, w.nsteps, w.times, rx, rw=w.rw, keep=(k, model)))
-        keep.append((model, desc, k, rx))
-    return ids, keep
-
-
 @pytest.mark.parametrize("prec", [0, 1])
 def test_results_identical_alone_and_in_mix(fga, prec):
     import torch
@@ -46,11 +34,15 @@ def test_results_identical_alone_and_in_mix(fga, prec):
     w0 = reqs[0].workload
     model = fga.model_from_medium(w0.medium)
     alone = []
+    lattice = prec == 0   # FP32 requests take their receivers as a lattice, FP64 ones as points
     for r in reqs:
         w = r.workload
         _, desc, k = gpu_setup(w, prec)
         rx = torch.as_tensor(w.receivers, device="cuda")
-        u, _ = fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, rw=w.rw)
+        if lattice:
+            u, _ = fga.solve(model, desc, w.dt, w.nsteps, w.times, rw=w.rw, rx_axes=w.rx_axes)
+        else:
+            u, _ = fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, rw=w.rw)
         torch.cuda.synchronize()
         alone.append(u.cpu())
     server = fga.Server(model, n_workers=3)
@@ -60,7 +52,10 @@ def test_results_identical_alone_and_in_mix(fga, prec):
         w = r.workload
         _, desc, k = gpu_setup(w, prec)
         rx = torch.as_tensor(w.receivers, device="cuda")
-        ids.append(server.submit(desc, w.dt, w.nsteps, w.times, rx, rw=w.rw, keep=k))
+        if lattice:
+            ids.append(server.submit(desc, w.dt, w.nsteps, w.times, rw=w.rw, keep=k, rx_axes=w.rx_axes))
+        else:
+            ids.append(server.submit(desc, w.dt, w.nsteps, w.times, rx, rw=w.rw, keep=k))
     infos = []
     for i, rid in enumerate(ids):
         u, info = server.wait(rid)
