@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="the serving stream instead: 64 Poisson-arriving requests of mixed k and size on the resident "
                          "smooth model at 0.7 of the measured solo capacity; p50/p99 latency and beam-steps/s")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="the crosswell gradient instead: 16 sources x 3.5 M beams, 200 steps, 256 receivers, L2 "
+                         "misfit against data of the bumped model; time per gradient (forward + adjoint)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -446,12 +449,83 @@ def run_serving(args):
     return 0
 
 
+def run_adjoint(args):
+    """Gradient of the L2 waveform misfit over 16 crosswell sources with respect to the 64^3 model grids."""
+    import numpy as np
+    import torch
+
+    from paper_1810_06760_gb300 import fga
+    from paper_1810_06760_gb300 import workloads as W
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = fga.PREC_FP32 if args.precision == "fp32" else fga.PREC_FP64
+    ws, true = W.crosswell()
+    model = fga.model_from_medium(ws[0].medium, dev)
+    tmodel = fga.model_from_medium(true, dev)
+    staged = []
+    for w in ws:
+        f = torch.as_tensor(w.f, device=dev)
+        rx = torch.as_tensor(w.receivers, device=dev)
+        desc = fga.init_desc(w.k, f, None, w.y0, w.dy, w.mesh, w.classes, prec)
+        d, _ = fga.solve(tmodel, desc, w.dt, w.nsteps, w.times, rx, rw=w.rw)   # observed data (input)
+        staged.append((w, desc, f, rx, d))
+    torch.cuda.synchronize()
+    shape = tuple(ws[0].medium.grid_p.shape[:3]) + (10,)
+    gp = torch.zeros(shape, dtype=torch.float64, device=dev)
+    gs = torch.zeros(shape, dtype=torch.float64, device=dev)
+
+    def gradient():
+        gp.zero_()
+        gs.zero_()
+        misfit = 0.0
+        for w, desc, f, rx, d in staged:
+            u, _ = fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, rw=w.rw)
+            r = u - d
+            misfit += 0.5 * float(r.abs().pow(2).sum())
+            fga.solve_vjp(model, desc, w.dt, w.nsteps, w.times, rx, r, grad_p=gp, grad_s=gs, rw=w.rw,
+                          checkpoint_every=20)
+        return misfit
+
+    for _ in range(max(1, args.warmup)):
+        gradient()
+    fga.profile_enable(2)
+    fga.profile_read(reset=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        misfit = gradient()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    prof = fga.profile_read(reset=True)
+    fga.profile_enable(0)
+    beam_steps = sum(w.n_beams * w.nsteps for w in ws)
+    line = {
+        "metric": "crosswell L2-misfit gradient (forward + discrete adjoint), 16 sources",
+        "value": wall / args.steps, "unit": "s/gradient", "higher_is_better": False, "n_gpus": world,
+        "steps": args.steps, "warmup": max(1, args.warmup), "dtype": "f32" if prec == fga.PREC_FP32 else "f64",
+        "data": "synthetic", "config": {"workload": "crosswell: 64^3 smooth model, 16 sources x 12^3 q x 8^3 p x 4 "
+                                                     "classes, k=64, T=0.5 (200 steps), 256 rx x 100 samples, "
+                                                     "checkpoints every 20 steps"},
+        "per_source_s": wall / args.steps / len(ws),
+        "beam_steps_per_s": 2 * beam_steps * args.steps / wall,
+        "kernel_ms_per_gradient": {k: v / args.steps for k, v in prof["ms"].items() if v > 0},
+        "misfit": misfit, "grad_norm": [float(gp.norm()), float(gs.norm())],
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.serving:
         return run_serving(args)
+    if args.adjoint:
+        return run_adjoint(args)
     return run_ours(args)
 
 
