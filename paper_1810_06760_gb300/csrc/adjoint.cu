@@ -633,7 +633,7 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
     const int nseg = (N + C - 1) / C;
     const int64_t nrx = sd->n_rx;
     const double rw = sd->rw > 0 ? sd->rw : 6.0 / std::sqrt(b->k);
-    DevBuf ck, seg, yb, rxd;
+    ScopedDevBuf ck, seg, yb, rxd;
     FGA_TRY(ck.ensure(sizeof(R) * (size_t)slot * (size_t)(nseg + 1)));
     FGA_TRY(seg.ensure(sizeof(R) * (size_t)slot * (size_t)(C + 1)));
     FGA_TRY(yb.ensure(sizeof(R) * (size_t)slot));

@@ -265,7 +265,7 @@ static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fg
     const int A = d->nq * d->np;
     const int64_t nyy = (int64_t)d->ny[0] * d->ny[1] * d->ny[2];
     (void)nyy;
-    DevBuf Kb, T1, T2, Fb, Gb;
+    ScopedDevBuf Kb, T1, T2, Fb, Gb;
     const size_t kbytes = sizeof(C2<R>) * (size_t)A * (d->ny[0] + d->ny[1] + d->ny[2]);
     FGA_TRY(Kb.ensure(kbytes));
     C2<R> *Kax[3];
@@ -283,7 +283,7 @@ static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fg
     FGA_TRY(T2.ensure(sizeof(C2<R>) * (size_t)d->ny[0] * A * A * 3));
     const size_t Fn = (size_t)A * A * A * 3;
     FGA_TRY(Fb.ensure(sizeof(C2<R>) * Fn));
-    DevBuf tsb;
+    ScopedDevBuf tsb;
     FGA_TRY(tsb.ensure(64));
     TransformScratch ts;
     ts.amax = tsb.as<float>();

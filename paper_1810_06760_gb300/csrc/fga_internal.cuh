@@ -114,6 +114,13 @@ struct DevBuf {
     void release();
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
+// a DevBuf owned by one scope (function-local scratch): released when the scope ends, also on early returns
+struct ScopedDevBuf : DevBuf {
+    ScopedDevBuf() = default;
+    ScopedDevBuf(const ScopedDevBuf &) = delete;
+    ScopedDevBuf &operator=(const ScopedDevBuf &) = delete;
+    ~ScopedDevBuf() { release(); }
+};
 struct HostBuf {
     void *p = nullptr;
     size_t bytes = 0;

@@ -217,3 +217,23 @@ def test_vjp_32_seeded_cells(fga, oracle_case):
             fd = (L(grids[0], A) - L(grids[0], B)) / (2 * step)
         errs.append(abs(fd - grads[wave][nd]) / abs(grads[wave][nd]))
     assert len(errs) == 32 and max(errs) <= 1e-5, max(errs)
+
+
+def test_vjp_releases_device_memory(fga):
+    """Repeated adjoint calls return their checkpoint and segment storage."""
+    import torch
+    ws, true = W.crosswell(n_src_side=1, nq=6, np_=6, ny=32, nsteps=40, dt=0.005, k=32.0, grid_n=17, rx_side=4,
+                           n_times=10)
+    w = ws[0]
+    model, desc, keep = gpu_setup(w, 0)
+    rx = torch.as_tensor(w.receivers, device="cuda")
+    u, _ = fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, rw=w.rw)
+    gp, gs = fga.solve_vjp(model, desc, w.dt, w.nsteps, w.times, rx, u)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        fga.solve_vjp(model, desc, w.dt, w.nsteps, w.times, rx, u, grad_p=gp, grad_s=gs)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    # one call holds (ceil(40/20) + 20 + 2) x 46 x 4 B per beam ~ 160 MB; five leaked calls would lose 800 MB
+    assert free0 - free1 < 64 * 2 ** 20, (free0 - free1) / 2 ** 20
