@@ -35,12 +35,33 @@ template <typename R> __device__ __forceinline__ void add2(R *p, C2<R> v) {
     p[1] += v.i;
 }
 
+// Node-field cotangent accumulators.  FP64: atomics straight into the caller's [node][10] doubles.
+// FP32: 16-byte vector atomics into a scratch grid of 3 float4 per node (fields 0-9, 2 pad), added
+// to the caller's doubles at the end (3 reductions per node instead of 10 FP64 atomics).
+template <typename R> struct GradAcc;
+template <> struct GradAcc<double> {
+    double *p;
+    __device__ __forceinline__ void add(int64_t node, const double cb[10], double w) const {
+#pragma unroll
+        for (int f = 0; f < 10; f++) atomicAdd(p + node * 10 + f, cb[f] * w);
+    }
+};
+template <> struct GradAcc<float> {
+    float4 *p;
+    __device__ __forceinline__ void add(int64_t node, const float cb[10], float w) const {
+        float4 *q = p + 3 * node;
+        atomicAdd(q, make_float4(cb[0] * w, cb[1] * w, cb[2] * w, cb[3] * w));
+        atomicAdd(q + 1, make_float4(cb[4] * w, cb[5] * w, cb[6] * w, cb[7] * w));
+        atomicAdd(q + 2, make_float4(cb[8] * w, cb[9] * w, 0.f, 0.f));
+    }
+};
+
 // ---------------------------------------------------------------------------------------------
 // adjoint of the trilinear model sampling: Qb += sum_f cb_f d field_f / dQ; grad[node][f] += w cb_f
 // ---------------------------------------------------------------------------------------------
 template <typename R, int MED>
 __device__ __forceinline__ void model_vjp(const ModelDev &M, int wave, const R x[3], const R cb[10], R Qb[3],
-                                          double *__restrict__ grad) {
+                                          GradAcc<R> grad) {
     if (MED != FGA_MEDIUM_GRID) return;  // constant media: no position or node dependence
     const float4 *__restrict__ G = wave ? M.gs : M.gp;
     int i[3];
@@ -84,12 +105,7 @@ __device__ __forceinline__ void model_vjp(const ModelDev &M, int wave, const R x
                 Qb[0] += dot * g0 * w1 * w2;
                 Qb[1] += dot * w0 * g1 * w2;
                 Qb[2] += dot * w0 * w1 * g2;
-                if (grad) {
-                    const R wgt = w0 * w1 * w2;
-                    double *gn = grad + node * 10;
-#pragma unroll
-                    for (int f = 0; f < 10; f++) atomicAdd(gn + f, (double)(cb[f] * wgt));
-                }
+                if (grad.p) grad.add(node, cb, w0 * w1 * w2);
             }
 }
 
@@ -99,7 +115,7 @@ __device__ __forceinline__ void model_vjp(const ModelDev &M, int wave, const R x
 // ---------------------------------------------------------------------------------------------
 template <typename R, int WAVE, int MED>
 __device__ __noinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, const R *__restrict__ y,
-                                     const R *__restrict__ fb, R *__restrict__ yb, double *__restrict__ grad) {
+                                     const R *__restrict__ fb, R *__restrict__ yb, GradAcc<R> grad) {
     R cf[10];
     const R Q[3] = {y[F_Q], y[F_Q + 1], y[F_Q + 2]};
     model_eval<R, MED>(M, WAVE, Q, cf);
@@ -508,7 +524,7 @@ __global__ void __launch_bounds__(128) adj_step_kernel(ModelDev M, const R *__re
                                                       R *__restrict__ YB, int64_t cap, const int32_t *__restrict__ flags,
                                                       int64_t off, int64_t n, R sg, R dt, R w, R k, R rw2, int nrx,
                                                       const R *__restrict__ rx, const R *__restrict__ ub,
-                                                      StepSamples ss, double *__restrict__ grad) {
+                                                      StepSamples ss, GradAcc<R> grad) {
     extern __shared__ unsigned char smem_raw[];
     R *xs = reinterpret_cast<R *>(smem_raw);
     R *us = xs + 3 * nrx;
@@ -604,7 +620,7 @@ __global__ void __launch_bounds__(128) adj_step_kernel(ModelDev M, const R *__re
 template <typename R, int WAVE, int MED>
 __global__ void __launch_bounds__(128) adj_init_kernel(ModelDev M, const R *__restrict__ S0, const R *__restrict__ SG,
                                                       const R *__restrict__ YB, int64_t cap, int64_t off, int64_t n,
-                                                      double *__restrict__ grad) {
+                                                      GradAcc<R> grad) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t b = off + i;
@@ -623,6 +639,49 @@ __global__ void __launch_bounds__(128) adj_init_kernel(ModelDev M, const R *__re
     R qb[3] = {R(0), R(0), R(0)};
     model_vjp<R, MED>(M, WAVE, q, cb, qb, grad);
 }
+
+// FP32 scratch grid (3 float4 per node) -> caller's FP64 [node][10]
+__global__ void add_scratch_kernel(const float4 *__restrict__ src, double *__restrict__ dst, int64_t nn) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const float4 a = src[3 * i], b = src[3 * i + 1], c = src[3 * i + 2];
+    double *d = dst + i * 10;
+    d[0] += a.x;
+    d[1] += a.y;
+    d[2] += a.z;
+    d[3] += a.w;
+    d[4] += b.x;
+    d[5] += b.y;
+    d[6] += b.z;
+    d[7] += b.w;
+    d[8] += c.x;
+    d[9] += c.y;
+}
+
+template <typename R> struct AccSetup;
+template <> struct AccSetup<double> {
+    static fga_status make(double *g, int64_t, ScopedDevBuf &, cudaStream_t, GradAcc<double> &a) {
+        a.p = g;
+        return FGA_OK;
+    }
+    static fga_status finish(const ScopedDevBuf &, double *, int64_t, cudaStream_t) { return FGA_OK; }
+};
+template <> struct AccSetup<float> {
+    static fga_status make(double *g, int64_t nn, ScopedDevBuf &buf, cudaStream_t s, GradAcc<float> &a) {
+        a.p = nullptr;
+        if (!g || nn == 0) return FGA_OK;
+        FGA_TRY(buf.ensure(sizeof(float4) * 3 * (size_t)nn));
+        FGA_CUDA(cudaMemsetAsync(buf.p, 0, sizeof(float4) * 3 * (size_t)nn, s));
+        a.p = buf.as<float4>();
+        return FGA_OK;
+    }
+    static fga_status finish(const ScopedDevBuf &buf, double *g, int64_t nn, cudaStream_t s) {
+        if (!g || nn == 0 || !buf.p) return FGA_OK;
+        add_scratch_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(buf.as<float4>(), g, nn);
+        FGA_CUDA(cudaGetLastError());
+        return FGA_OK;
+    }
+};
 
 template <typename R, int MED>
 fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, fga_beams *b,
@@ -647,6 +706,11 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
         FGA_CUDA(cudaStreamSynchronize(s));
     }
     R *CK = ck.as<R>(), *SEG = seg.as<R>(), *YB = yb.as<R>();
+    const int64_t nn = MED == FGA_MEDIUM_GRID ? (int64_t)m->dev.n[0] * m->dev.n[1] * m->dev.n[2] : 0;
+    ScopedDevBuf sgp, sgs;
+    GradAcc<R> accp, accs;
+    FGA_TRY(AccSetup<R>::make(grad_p, nn, sgp, s, accp));
+    FGA_TRY(AccSetup<R>::make(grad_s, nn, sgs, s, accs));
     const R *ub = static_cast<const R *>(ubar);
     FGA_CUDA(cudaMemsetAsync(YB, 0, sizeof(R) * (size_t)slot, s));
     FGA_CUDA(cudaMemcpyAsync(CK, b->state.p, sizeof(R) * (size_t)slot, cudaMemcpyDeviceToDevice, s));
@@ -711,7 +775,7 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
                 if (!nc) continue;
                 const R sg = (cls & 1) ? R(-1) : R(1);
                 const unsigned blocks = (unsigned)((nc + 127) / 128);
-                double *gr = cls < 2 ? grad_p : grad_s;
+                const GradAcc<R> gr = cls < 2 ? accp : accs;
                 ProfScope ps(P_ADJ_REV, s);
                 if (cls < 2) {
                     auto kern = adj_step_kernel<R, 0, MED>;
@@ -737,13 +801,15 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
             ProfScope ps(P_ADJ_INIT, s);
             if (cls < 2)
                 adj_init_kernel<R, 0, MED><<<blocks, 128, 0, s>>>(m->dev, CK, bg->state.as<R>(), YB, cap,
-                                                                 b->off_cls[cls], nc, grad_p);
+                                                                 b->off_cls[cls], nc, accp);
             else
                 adj_init_kernel<R, 1, MED><<<blocks, 128, 0, s>>>(m->dev, CK, bg->state.as<R>(), YB, cap,
-                                                                 b->off_cls[cls], nc, grad_s);
+                                                                 b->off_cls[cls], nc, accs);
         }
         FGA_CUDA(cudaGetLastError());
     }
+    FGA_TRY(AccSetup<R>::finish(sgp, grad_p, nn, s));
+    FGA_TRY(AccSetup<R>::finish(sgs, grad_s, nn, s));
     if (prof_counting()) prof_add_beam_steps(b->nb * (int64_t)N);
     FGA_CUDA(cudaStreamSynchronize(s));
     return FGA_OK;
