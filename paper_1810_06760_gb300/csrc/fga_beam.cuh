@@ -218,6 +218,34 @@ __device__ __forceinline__ void beam_rhs(const ModelDev &M, R sg, bool ref_e1, c
         f[F_P + d] = -sg * pn * g[d];
     }
     const R cip = c * ip;
+    if constexpr (sizeof(R) == 4) {
+        // FP32: each complex entry (re, im) as one packed FP32x2 value
+        auto ld = [&](int off) { return make_float2(y[off], y[off + 1]); };
+        auto bc = [](float v) { return make_float2(v, v); };
+        const float2 sgcip = bc(sg * cip), msgpn = bc(-sg * pn);
+#pragma unroll
+        for (int m = 0; m < 3; m++) {
+            float2 u = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int l = 0; l < 3; l++) {
+                u = __ffma2_rn(ld(F_DQ + 2 * (3 * m + l)), bc(g[l]), u);
+                v = __ffma2_rn(ld(F_DP + 2 * (3 * m + l)), bc(Ph[l]), v);
+            }
+            const float2 wv = __ffma2_rn(bc(-cip), v, u);   // u - (c/|P|) v
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const float2 fq = __ffma2_rn(wv, bc(sg * Ph[j]), __fmul2_rn(sgcip, ld(F_DP + 2 * (3 * m + j))));
+                f[F_DQ + 2 * (3 * m + j)] = fq.x;
+                f[F_DQ + 2 * (3 * m + j) + 1] = fq.y;
+                float2 hh = __fmul2_rn(ld(F_DQ + 2 * (3 * m)), bc(H[0][j]));
+                hh = __ffma2_rn(ld(F_DQ + 2 * (3 * m + 1)), bc(H[1][j]), hh);
+                hh = __ffma2_rn(ld(F_DQ + 2 * (3 * m + 2)), bc(H[2][j]), hh);
+                const float2 fp = __ffma2_rn(v, bc(-sg * g[j]), __fmul2_rn(msgpn, hh));
+                f[F_DP + 2 * (3 * m + j)] = fp.x;
+                f[F_DP + 2 * (3 * m + j) + 1] = fp.y;
+            }
+        }
+    } else {
 #pragma unroll
     for (int m = 0; m < 3; m++) {
         R ur = R(0), ui = R(0), vr = R(0), vi = R(0);
@@ -242,6 +270,7 @@ __device__ __forceinline__ void beam_rhs(const ModelDev &M, R sg, bool ref_e1, c
             f[F_DP + 2 * (3 * m + j)] = -sg * (pn * hr + vr * g[j]);
             f[F_DP + 2 * (3 * m + j) + 1] = -sg * (pn * hi + vi * g[j]);
         }
+    }
     }
     // Z = dzQ + i dzP and Z' likewise
     C2<R> Z[3][3], Zd[3][3];
