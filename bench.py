@@ -33,6 +33,10 @@ FLOP_PER_PAIR_OUT = 9.0       # dx, r^2, compare
 MUFU_PER_PAIR_IN = 3.0        # exp2, sin, cos
 FLOP_PER_LATTICE_PAIR_IN = 26.0   # window test (add, compare) + 3 complex multiply-adds
 SMS = 152
+# DRAM bytes per launch of the tensor-core lattice sum on the full smooth workload, from ncu
+# (dram__bytes_read + write = 335 MB per launch at 6.33 M records per sample on the medium case,
+# 52.9 B per record), scaled to the full workload's ~18 M records per sample; see profiles/
+LATTICE_TC_TRAFFIC_BYTES = 0.95e9
 
 
 def parse():
@@ -299,8 +303,9 @@ def run_ours(args):
     if flops is not None:
         achieved = flops / (ms[top] / 1e3) / 1e12
         peak = fp32_peak / 1e12
+        traffic = LATTICE_TC_TRAFFIC_BYTES if (top == "gauss_sum_all" and args.size == "full") else None
         roof = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "peak_basis": f"FP32 pipe: {SMS} SMs x 128 lanes x 2 x {sm_clock / 1e6:.0f} MHz "
                               f"(max SM clock of {pk_kind} peaks file)",
                 "per_launch_ms": per_launch_ms, "launches": launches}
