@@ -70,17 +70,20 @@ constexpr int LT_KB = tc::KB;            // beams per block
 constexpr int LT_T0_MAX = 32;            // 6 T0 <= 192 real columns
 constexpr int LT_NMAX = 192;
 constexpr int LT_A_BYTES = LT_M * LT_KB * 2;      // 8 KB per operand copy
-constexpr int LT_B_BYTES = LT_NMAX * LT_KB * 2;   // 12 KB per operand copy
 constexpr int LT_TA_MAX = 32 + 128 + 16;
 constexpr int LT_CAND = 4096;           // candidates filtered per round (per-CTA kept-list scratch)
-constexpr uint32_t LT_TMEM_COLS = 256;
 
+// shared-memory layout; the B operand copies and the tensor-memory columns are sized to the tile's
+// real width NR, so narrow tiles (single receiver planes) fit three CTAs per SM
 struct LtSmem {
-    int a, b, e, rec, w, x, cnt, bar, bytes;
-    __host__ __device__ void init(int TA, bool with_w) {
+    int a, b, e, rec, w, x, cnt, bar, bytes, bbytes;
+    uint32_t tcols;
+    __host__ __device__ void init(int TA, bool with_w, int NR) {
+        bbytes = NR * LT_KB * 2;
+        tcols = NR <= 32 ? 32u : (NR <= 64 ? 64u : (NR <= 128 ? 128u : 256u));
         a = 0;
         b = a + 4 * LT_A_BYTES;
-        e = b + 4 * LT_B_BYTES;                 // 2 x [32][TA] float2
+        e = b + 4 * bbytes;                     // 2 x [32][TA] float2
         rec = e + 2 * LT_KB * TA * 8;           // 2 x [32][REC] float
         w = rec + 2 * LT_KB * REC * 4;          // 2 x [32][3] float2: A_c E2 of single-plane tiles
         x = w + (with_w ? 2 * LT_KB * 3 * 8 : 0);
@@ -101,8 +104,8 @@ struct LtAxes {
 
 // Operand mapping.  crow = 0: rows (j, l), columns (i, c): Y = E1 E2, X = A_c E0.
 //                  crow = 1 (small T1 T2): rows (j, l, c), columns i: Y = A_c E1 E2, X = E0.
-template <bool COUNT>
-__global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *__restrict__ rec, const double *__restrict__ ax0,
+template <bool COUNT, int MINB>
+__global__ void __launch_bounds__(LT_THREADS, MINB) lattice_tc_kernel(const float *__restrict__ rec, const double *__restrict__ ax0,
                                                         const double *__restrict__ ax1, const double *__restrict__ ax2,
                                                         int n0, int n1, int n2, int T0, int T1, int T2, int nt1,
                                                         int nt2, const int4 *__restrict__ items, float k, float rw2,
@@ -130,6 +133,7 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
     const int i0 = tt0 * T0, j0 = tt1 * T1, l0 = tt2 * T2;
     const int e0 = min(T0, n0 - i0), e1 = min(T1, n1 - j0), e2 = min(T2, n2 - l0);
 
+    const int LT_B_BYTES = S.bbytes;
     for (int o = tid * 16; o < 4 * LT_A_BYTES + 4 * LT_B_BYTES; o += LT_THREADS * 16)
         *reinterpret_cast<uint4 *>(smem + o) = make_uint4(0, 0, 0, 0);
     for (int a = tid; a < TA; a += LT_THREADS) {
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
         else v = ax2[l0 + min(a - T0 - T1, e2 - 1)];
         sX[a] = (float)v;
     }
-    if (warp == 0) tc::alloc(tc::smem_u32(tmem_slot), LT_TMEM_COLS);
+    if (warp == 0) tc::alloc(tc::smem_u32(tmem_slot), S.tcols);
     if (tid == 0) tc::mbar_init(tc::smem_u32(bar));
     float sx = 1.0f;
     {
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(LT_THREADS, 2) lattice_tc_kernel(const float *
     }
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::dealloc(tmem, LT_TMEM_COLS);
+    if (warp == 0) tc::dealloc(tmem, S.tcols);
 }
 
 __global__ void rec_absmax_kernel(const float *__restrict__ rec, int64_t n, float *__restrict__ out) {
@@ -467,8 +471,15 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
         return FGA_ERR_UNSUPPORTED;
     }
     const int crow = 3 * T1 * T2 <= LT_M ? 1 : 0;
+    const int nc_used = crow ? T0 : 3 * T0, NR = 2 * ((nc_used + 7) / 8 * 8);
+    if (NR > LT_NMAX) {
+        set_error("lattice tile too wide for the tensor-core kernel");
+        return FGA_ERR_UNSUPPORTED;
+    }
     LtSmem S;
-    S.init(T0 + T1 + T2, crow && T2 == 1);
+    S.init(T0 + T1 + T2, crow && T2 == 1, NR);
+    // three CTAs per SM when their tensor memory (3 x tcols <= 512) and shared memory fit
+    const bool three = S.tcols <= 128 && S.bytes <= 74 * 1024;
     LtAxes X;
     for (int d = 0; d < 3; d++) {
         const int Td = plan.T[d];
@@ -492,19 +503,23 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
             rec_absmax_kernel<<<blocks, 256, 0, s>>>(static_cast<const float *>(rec), plan.n_rec, amax);
         }
         ProfScope ps(cat, s);
+#define FGA_LTC(CNT, MB)                                                                                          \
+    do {                                                                                                          \
+        FGA_CUDA(cudaFuncSetAttribute(lattice_tc_kernel<CNT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                      S.bytes));                                                                  \
+        lattice_tc_kernel<CNT, MB><<<plan.nitems, LT_THREADS, S.bytes, s>>>(                                      \
+            static_cast<const float *>(rec), plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2], \
+            T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S, X, crow, kept,   \
+            ws.partial.as<float>());                                                                              \
+    } while (0)
         if (cnt) {
-            FGA_CUDA(cudaFuncSetAttribute(lattice_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S.bytes));
-            lattice_tc_kernel<true><<<plan.nitems, LT_THREADS, S.bytes, s>>>(
-                static_cast<const float *>(rec), plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2],
-                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S, X, crow,
-                kept, ws.partial.as<float>());
+            if (three) FGA_LTC(true, 3);
+            else FGA_LTC(true, 2);
         } else {
-            FGA_CUDA(cudaFuncSetAttribute(lattice_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S.bytes));
-            lattice_tc_kernel<false><<<plan.nitems, LT_THREADS, S.bytes, s>>>(
-                static_cast<const float *>(rec), plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2],
-                T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S, X, crow,
-                kept, ws.partial.as<float>());
+            if (three) FGA_LTC(false, 3);
+            else FGA_LTC(false, 2);
         }
+#undef FGA_LTC
         FGA_CUDA(cudaGetLastError());
     }
     FGA_TRY(lattice_reduce_f32(ws.partial.as<float>(), plan, u, s));
