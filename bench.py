@@ -466,7 +466,12 @@ def run_adjoint(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = fga.PREC_FP32 if args.precision == "fp32" else fga.PREC_FP64
-    ws, true = W.crosswell()
+    if args.size == "full":
+        ws, true = W.crosswell()
+    elif args.size == "medium":   # one source, 8^3 q: the profiler capture case
+        ws, true = W.crosswell(n_src_side=1, nq=8)
+    else:
+        ws, true = W.crosswell(n_src_side=1, nq=4, np_=4, ny=32, nsteps=40, grid_n=17, rx_side=4, n_times=20)
     model = fga.model_from_medium(ws[0].medium, dev)
     tmodel = fga.model_from_medium(true, dev)
     staged = []
@@ -507,11 +512,13 @@ def run_adjoint(args):
     fga.profile_enable(0)
     beam_steps = sum(w.n_beams * w.nsteps for w in ws)
     line = {
-        "metric": "crosswell L2-misfit gradient (forward + discrete adjoint), 16 sources",
+        "metric": "crosswell L2-misfit gradient (forward + discrete adjoint)",
         "value": wall / args.steps, "unit": "s/gradient", "higher_is_better": False, "n_gpus": world,
         "steps": args.steps, "warmup": max(1, args.warmup), "dtype": "f32" if prec == fga.PREC_FP32 else "f64",
-        "data": "synthetic", "config": {"workload": "crosswell: 64^3 smooth model, 16 sources x 12^3 q x 8^3 p x 4 "
-                                                     "classes, k=64, T=0.5 (200 steps), 256 rx x 100 samples, "
+        "data": "synthetic", "config": {"workload": f"crosswell ({args.size}): 64^3 smooth model, {len(ws)} sources x "
+                                                     f"{ws[0].mesh.nq}^3 q x {ws[0].mesh.np_}^3 p x 4 classes, "
+                                                     f"k={ws[0].k:g}, {ws[0].nsteps} steps, "
+                                                     f"{len(ws[0].receivers)} rx x {len(ws[0].times)} samples, "
                                                      "checkpoints every 20 steps"},
         "per_source_s": wall / args.steps / len(ws),
         "beam_steps_per_s": 2 * beam_steps * args.steps / wall,
