@@ -34,9 +34,9 @@ MUFU_PER_PAIR_IN = 3.0        # exp2, sin, cos
 FLOP_PER_LATTICE_PAIR_IN = 26.0   # window test (add, compare) + 3 complex multiply-adds
 SMS = 152
 # DRAM bytes per launch of the tensor-core lattice sum on the full smooth workload, from ncu
-# (dram__bytes_read + write = 335 MB per launch at 6.33 M records per sample on the medium case,
-# 52.9 B per record), scaled to the full workload's ~18 M records per sample; see profiles/
-LATTICE_TC_TRAFFIC_BYTES = 0.95e9
+# (dram__bytes_read + write = 384 MB per launch at 6.33 M records per sample on the medium case,
+# 60.6 B per record), scaled to the full workload's ~18 M records per sample; see profiles/
+LATTICE_TC_TRAFFIC_BYTES = 1.09e9
 
 
 def parse():
