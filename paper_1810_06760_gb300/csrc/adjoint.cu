@@ -7,13 +7,14 @@
 //
 // Schedule (one thread per beam throughout):
 //   1. forward pass storing the state every C steps (checkpoints);
-//   2. for each segment, last to first: recompute its C states from the checkpoint, then one
-//      reverse-step launch per step, last to first.  A reverse step reads y_n, y_{n+1} and the
-//      running cotangent ybar_{n+1}; adds the record cotangents of the step's samples (receivers and
-//      the step's seismogram cotangents staged in shared memory), then runs RK4 backwards through
-//      its four stages with the hand-written adjoint of dy/dt; writes ybar_n.
+//   2. for each segment, last to first: recompute its C states from the checkpoint, then the reverse
+//      steps, last to first.  A reverse step reads y_n, y_{n+1} and the running cotangent
+//      ybar_{n+1}; adds the record cotangents of the step's samples (receivers and the step's
+//      seismogram cotangents staged in shared memory), then runs RK4 backwards through its four
+//      stages with the hand-written adjoint of dy/dt (one kernel per part, see reverse_step); writes
+//      ybar_n.
 //   3. the cotangent of the initial amplitudes gives dL/dc(q) through the initial-velocity term.
-// Node-field cotangents are scattered with FP64 atomics through the interpolation weights.
+// Node-field cotangents are scattered with atomics through the interpolation weights (GradAcc).
 #include <cmath>
 #include <vector>
 
@@ -113,9 +114,9 @@ __device__ __forceinline__ void model_vjp(const ModelDev &M, int wave, const R x
 // adjoint of dy/dt (the right-hand side of beam_rhs): yb += (d rhs / dy)^T fb, node-field
 // cotangents to grad.  Complex cotangents follow zb = dL/dRe z + i dL/dIm z.
 // ---------------------------------------------------------------------------------------------
-template <typename R, int WAVE, int MED>
-__device__ __noinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, const R *__restrict__ y,
-                                     const R *__restrict__ fb, R *__restrict__ yb, GradAcc<R> grad) {
+template <typename R, int WAVE, int MED, class FB>
+__device__ __forceinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, const R *__restrict__ y, FB fb,
+                                        R *__restrict__ yb, GradAcc<R> grad) {
     R cf[10];
     const R Q[3] = {y[F_Q], y[F_Q + 1], y[F_Q + 2]};
     model_eval<R, MED>(M, WAVE, Q, cf);
@@ -187,15 +188,15 @@ __device__ __noinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, const
 #pragma unroll
     for (int f = 0; f < 10; f++) cb[f] = R(0);
     R Phb[3] = {R(0), R(0), R(0)}, Pb[3] = {R(0), R(0), R(0)}, pnb = R(0), cipb = R(0);
-    R fPb[3] = {fb[F_P], fb[F_P + 1], fb[F_P + 2]};
-    const C2<R> a0 = ld2(y + F_A0), fa0 = ld2(fb + F_A0);
+    R fPb[3] = {fb(F_P), fb(F_P + 1), fb(F_P + 2)};
+    const C2<R> a0 = ld2(y + F_A0), fa0 = {fb(F_A0), fb(F_A0 + 1)};
     C2<R> gamb;
     if (WAVE == 0) {
         add2(yb + F_A0, cconj_mul(gam, fa0));
         gamb = cconj_mul(a0, fa0);
     } else {
         // omega = -s1 s2 / D, s1 = P'.(e x P), s2 = e.P, D = |P|^3 - s2^2 |P|,  P' = -sg |P| g
-        const C2<R> a1 = ld2(y + F_A1), fa1 = ld2(fb + F_A1);
+        const C2<R> a1 = ld2(y + F_A1), fa1 = {fb(F_A1), fb(F_A1 + 1)};
         R exP[3], e[3];
         if (ref_e1) {
             e[0] = R(1); e[1] = R(0); e[2] = R(0);
@@ -261,8 +262,8 @@ __device__ __noinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, const
                 const C2<R> zb = cscale(R(-1), cconj_mul(M3, trb));
                 const int e = 2 * (3 * m + j);
                 // Z = dzQ + i dzP: dzQ_b += zb, dzP_b += -i zb; likewise for Z'
-                fDQb[m][j] = cadd(ld2(fb + F_DQ + e), zdb);
-                fDPb[m][j] = cadd(ld2(fb + F_DP + e), {zdb.i, -zdb.r});
+                fDQb[m][j] = cadd(C2<R>{fb(F_DQ + e), fb(F_DQ + e + 1)}, zdb);
+                fDPb[m][j] = cadd(C2<R>{fb(F_DP + e), fb(F_DP + e + 1)}, C2<R>{zdb.i, -zdb.r});
                 add2(yb + F_DQ + e, zb);
                 add2(yb + F_DP + e, {zb.i, -zb.r});
             }
@@ -318,8 +319,9 @@ __device__ __noinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, const
     for (int d = 0; d < 3; d++) {
         pnb += -sg * g[d] * fPb[d];
         cb[1 + d] += -sg * pn * fPb[d];
-        cb[0] += sg * Ph[d] * fb[F_Q + d];
-        Phb[d] += sg * c * fb[F_Q + d];
+        const R fq = fb(F_Q + d);
+        cb[0] += sg * Ph[d] * fq;
+        Phb[d] += sg * c * fq;
     }
     cb[0] += ip * cipb;
     pnb += -c * ip * ip * cipb;
@@ -464,13 +466,15 @@ __device__ __forceinline__ void record_vjp(bool ref_e1, const R *y0, const R *d0
     }
 }
 
+// Beam states, slopes and cotangents stream through once per launch (hundreds of MB): evict-first
+// loads and stores keep the model grids and the node-cotangent scratch resident in L2.
 template <typename R> __device__ __forceinline__ void load_state(const R *__restrict__ S, int64_t cap, int64_t b, R *y) {
 #pragma unroll
-    for (int f = 0; f < NF; f++) y[f] = S[(int64_t)f * cap + b];
+    for (int f = 0; f < NF; f++) y[f] = __ldcs(S + (int64_t)f * cap + b);
 }
 template <typename R> __device__ __forceinline__ void store_state(R *__restrict__ S, int64_t cap, int64_t b, const R *y) {
 #pragma unroll
-    for (int f = 0; f < NF; f++) S[(int64_t)f * cap + b] = y[f];
+    for (int f = 0; f < NF; f++) __stcs(S + (int64_t)f * cap + b, y[f]);
 }
 
 // Forward RK4 from src (SoA, stride cap) for nsteps; the state after step s (1-based) is stored in
@@ -512,107 +516,203 @@ __global__ void __launch_bounds__(128) adj_forward_kernel(ModelDev M, const R *_
     }
 }
 
-// One reverse step n: YB holds ybar_{n+1} on entry and ybar_n on exit.  Samples of the step:
-// nsj (<= 4) fractions th[], cotangents ub [nsj][nrx][3] complex; need_d1: some fraction is inside (0,1).
+// Reverse step n, split into one kernel per part so that each keeps about three 46-real arrays
+// live (a single kernel holding the step's state, slopes and cotangents spilled to local memory):
+//   adj_records_kernel  (steps with samples) record cotangents: ybar_{n+1} += those of y_{n+1} (with
+//                       the adjoint of its slope when a sample lies inside the step); the cotangents of
+//                       y_n and of k1 (Q, P) go to RB;
+//   adj_stage4_kernel   recomputes the stage inputs t2 = y + h k1 and t3 = y + h k2 (stored) and
+//                       t4 = y + dt k3; sb4 = (df/dy(t4))^T (dt/6 ybar_{n+1});
+//   adj_stage_kernel    sb3 at t3 from dt/3 ybar_{n+1} + dt sb4, then sb2 at t2 from dt/3 ybar_{n+1} + h sb3;
+//   adj_stage1_kernel   ybar_n = ybar_{n+1} + sb4 + sb3 + sb2 + RB + (df/dy(y))^T (dt/6 ybar_{n+1} + h sb2
+//                       + RB's k1 part).
+// All buffers are SoA with stride cap, indexed by the beam's slot.
 struct StepSamples {
     int nsj, need_d1;
     float th[4];
     double thd[4];
+    double lo[3], hi[3];  // bounding box of the receivers
 };
+constexpr int ADJ_THREADS = 128;
+
+// RB layout: fields 0-5 = cotangent of y_n's Q, P; 6-9 = of its amplitudes; 10-15 = of k1's Q, P
+constexpr int RB_FIELDS = 16;
+
+// Cotangent of a stage slope, a ybar_{n+1} + c sb (+ the records' k1 cotangent on Q, P), formed once
+// at kernel start into the thread's own column of shared memory (column stride ADJ_THREADS): all of
+// its global loads go out together instead of one round trip per use inside the adjoint.
+template <typename R> struct StagedBar {
+    const R *p;  // &column[threadIdx.x]
+    __device__ __forceinline__ R operator()(int f) const { return p[f * ADJ_THREADS]; }
+};
+template <typename R>
+__device__ __forceinline__ StagedBar<R> stage_slope_bar(R *col, const R *yb, const R *sb, const R *rb, int64_t cap,
+                                                        int64_t b, R a, R c) {
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        const int64_t o = (int64_t)f * cap + b;
+        R v = a * __ldcs(yb + o);
+        if (sb) v += c * __ldcs(sb + o);
+        if (f < 6 && rb) v += __ldcs(rb + (int64_t)(10 + f) * cap + b);
+        col[f * ADJ_THREADS] = v;
+    }
+    return StagedBar<R>{col};
+}
+// cotangent held in registers on Q, P only (the records' slope term at y_{n+1})
+template <typename R> struct QPBar {
+    const R *v;
+    __device__ __forceinline__ R operator()(int f) const { return f < 6 ? v[f] : R(0); }
+};
+
 template <typename R, int WAVE, int MED>
-__global__ void __launch_bounds__(128) adj_step_kernel(ModelDev M, const R *__restrict__ Sn, const R *__restrict__ Sn1,
-                                                      R *__restrict__ YB, int64_t cap, const int32_t *__restrict__ flags,
-                                                      int64_t off, int64_t n, R sg, R dt, R w, R k, R rw2, int nrx,
-                                                      const R *__restrict__ rx, const R *__restrict__ ub,
-                                                      StepSamples ss, GradAcc<R> grad) {
+__global__ void __launch_bounds__(ADJ_THREADS) adj_records_kernel(ModelDev M, const R *__restrict__ Sn,
+                                                         const R *__restrict__ Sn1, R *__restrict__ YB,
+                                                         R *__restrict__ RB, int64_t cap,
+                                                         const int32_t *__restrict__ flags, int64_t off, int64_t n,
+                                                         R sg, R dt, R w, R k, R rw2, int nrx,
+                                                         const R *__restrict__ rx, const R *__restrict__ ub,
+                                                         StepSamples ss, GradAcc<R> grad) {
     extern __shared__ unsigned char smem_raw[];
     R *xs = reinterpret_cast<R *>(smem_raw);
     R *us = xs + 3 * nrx;
-    if (ss.nsj > 0) {
-        for (int i = threadIdx.x; i < 3 * nrx; i += blockDim.x) xs[i] = rx[i];
-        for (int i = threadIdx.x; i < 6 * nrx * ss.nsj; i += blockDim.x) us[i] = ub[i];
-        __syncthreads();
-    }
+    for (int i = threadIdx.x; i < 3 * nrx; i += blockDim.x) xs[i] = rx[i];
+    for (int i = threadIdx.x; i < 6 * nrx * ss.nsj; i += blockDim.x) us[i] = ub[i];
+    __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t b = off + i;
     const bool e1 = (flags[b] & FL_REF_E1) != 0;
-    R y[NF], y1[NF], yb1[NF], yb0[NF], k1[NF];
+    R y[NF], k1[NF], y1[NF], d1[NF], y0b[NF], y1b[NF];
     load_state(Sn, cap, b, y);
-    load_state(YB, cap, b, yb1);
     beam_rhs<R, WAVE, MED>(M, sg, e1, y, k1);
-    R f0b[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    load_state(Sn1, cap, b, y1);
+    if (ss.need_d1)
+        beam_rhs<R, WAVE, MED>(M, sg, e1, y1, d1);
+    else
 #pragma unroll
-    for (int f = 0; f < NF; f++) yb0[f] = R(0);
-    if (ss.nsj > 0) {
-        load_state(Sn1, cap, b, y1);
-        R d1[NF];
-        if (ss.need_d1)
-            beam_rhs<R, WAVE, MED>(M, sg, e1, y1, d1);
-        else
+        for (int f = 0; f < NF; f++) d1[f] = R(0);
 #pragma unroll
-            for (int f = 0; f < NF; f++) d1[f] = R(0);
-        R f1b[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-        for (int s = 0; s < ss.nsj; s++) {
-            const R th = sizeof(R) == 8 ? (R)ss.thd[s] : (R)ss.th[s];
-            R rec[REC], rb[REC];
-            beam_record<R, WAVE>(e1, y, k1, y1, d1, dt, th, w, rec);
-            gauss_vjp<R>(rec, xs, us + (size_t)6 * nrx * s, nrx, k, rw2, rb);
-            record_vjp<R, WAVE>(e1, y, k1, y1, d1, dt, th, w, rb, yb0, f0b, yb1, f1b);
-        }
-        if (ss.need_d1) {
-            R fb[NF];
-#pragma unroll
-            for (int f = 0; f < NF; f++) fb[f] = R(0);
-#pragma unroll
-            for (int d = 0; d < 6; d++) fb[F_Q + d] = f1b[d];
-            rhs_vjp<R, WAVE, MED>(M, sg, e1, y1, fb, yb1, grad);
-        }
+    for (int f = 0; f < NF; f++) {
+        y0b[f] = R(0);
+        y1b[f] = R(0);
     }
-    // RK4 backwards: y1 = y + dt/6 (k1 + 2 k2 + 2 k3 + k4), k2 = f(y + dt/2 k1), k3 = f(y + dt/2 k2),
-    // k4 = f(y + dt k3)
-    R k2[NF], k3[NF], t[NF], kb[NF], sb[NF];
+    R f0b[6] = {R(0), R(0), R(0), R(0), R(0), R(0)}, f1b[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    for (int s = 0; s < ss.nsj; s++) {
+        const R th = sizeof(R) == 8 ? (R)ss.thd[s] : (R)ss.th[s];
+        R rec[REC], rb[REC];
+        beam_record<R, WAVE>(e1, y, k1, y1, d1, dt, th, w, rec);
+        // no receiver within the window (with a margin over rounding): the record's cotangent is zero
+        R bd2 = R(0);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const R lo = (R)ss.lo[d] - rec[d], hi = rec[d] - (R)ss.hi[d];
+            const R o = lo > hi ? lo : hi;
+            if (o > R(0)) bd2 += o * o;
+        }
+        if (bd2 > rw2 * R(1.001)) continue;
+        gauss_vjp<R>(rec, xs, us + (size_t)6 * nrx * s, nrx, k, rw2, rb);
+        record_vjp<R, WAVE>(e1, y, k1, y1, d1, dt, th, w, rb, y0b, f0b, y1b, f1b);
+    }
+    if (ss.need_d1) {
+        rhs_vjp<R, WAVE, MED>(M, sg, e1, y1, QPBar<R>{f1b}, y1b, grad);
+#pragma unroll
+        for (int f = 0; f < NF; f++) YB[(int64_t)f * cap + b] += y1b[f];
+    } else {
+#pragma unroll
+        for (int f = 0; f < 6; f++) YB[(int64_t)f * cap + b] += y1b[f];
+#pragma unroll
+        for (int f = 0; f < 4; f++) YB[(int64_t)(F_A0 + f) * cap + b] += y1b[F_A0 + f];
+    }
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+        RB[(int64_t)f * cap + b] = y0b[f];
+        RB[(int64_t)(10 + f) * cap + b] = f0b[f];
+    }
+#pragma unroll
+    for (int f = 0; f < 4; f++) RB[(int64_t)(6 + f) * cap + b] = y0b[F_A0 + f];
+}
+
+template <typename R, int WAVE, int MED>
+__global__ void __launch_bounds__(ADJ_THREADS) adj_stage4_kernel(ModelDev M, const R *__restrict__ Sn,
+                                                        const R *__restrict__ YB, R *__restrict__ T2,
+                                                        R *__restrict__ T3, R *__restrict__ SB4, int64_t cap,
+                                                        const int32_t *__restrict__ flags, int64_t off, int64_t n,
+                                                        R sg, R dt, GradAcc<R> grad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t b = off + i;
+    const bool e1 = (flags[b] & FL_REF_E1) != 0;
+    __shared__ R col[NF * ADJ_THREADS];
+    const StagedBar<R> fb = stage_slope_bar<R>(col + threadIdx.x, YB, nullptr, nullptr, cap, b, dt / R(6), R(0));
+    R y[NF], kk[NF], t[NF];
+    load_state(Sn, cap, b, y);
     const R h = R(0.5) * dt;
+    beam_rhs<R, WAVE, MED>(M, sg, e1, y, kk);
 #pragma unroll
-    for (int f = 0; f < NF; f++) t[f] = y[f] + h * k1[f];
-    beam_rhs<R, WAVE, MED>(M, sg, e1, t, k2);
+    for (int f = 0; f < NF; f++) t[f] = y[f] + h * kk[f];
+    store_state(T2, cap, b, t);
+    beam_rhs<R, WAVE, MED>(M, sg, e1, t, kk);
 #pragma unroll
-    for (int f = 0; f < NF; f++) t[f] = y[f] + h * k2[f];
-    beam_rhs<R, WAVE, MED>(M, sg, e1, t, k3);
-    const R s6 = dt / R(6), s3 = dt / R(3);
+    for (int f = 0; f < NF; f++) t[f] = y[f] + h * kk[f];
+    store_state(T3, cap, b, t);
+    beam_rhs<R, WAVE, MED>(M, sg, e1, t, kk);
+#pragma unroll
+    for (int f = 0; f < NF; f++) t[f] = y[f] + dt * kk[f];
+    R sb[NF];
+#pragma unroll
+    for (int f = 0; f < NF; f++) sb[f] = R(0);
+    rhs_vjp<R, WAVE, MED>(M, sg, e1, t, fb, sb, grad);
+    store_state(SB4, cap, b, sb);
+}
+
+// sb_out = (df/dy(t))^T (a ybar_{n+1} + c sb_in)
+template <typename R, int WAVE, int MED>
+__global__ void __launch_bounds__(ADJ_THREADS) adj_stage_kernel(ModelDev M, const R *__restrict__ T, const R *__restrict__ YB,
+                                                       const R *__restrict__ SBin, R *__restrict__ SBout, int64_t cap,
+                                                       const int32_t *__restrict__ flags, int64_t off, int64_t n,
+                                                       R sg, R a, R c, GradAcc<R> grad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t b = off + i;
+    const bool e1 = (flags[b] & FL_REF_E1) != 0;
+    __shared__ R col[NF * ADJ_THREADS];
+    const StagedBar<R> fb = stage_slope_bar<R>(col + threadIdx.x, YB, SBin, nullptr, cap, b, a, c);
+    R t[NF], sb[NF];
+    load_state(T, cap, b, t);
+#pragma unroll
+    for (int f = 0; f < NF; f++) sb[f] = R(0);
+    rhs_vjp<R, WAVE, MED>(M, sg, e1, t, fb, sb, grad);
+    store_state(SBout, cap, b, sb);
+}
+
+// YB: ybar_{n+1} on entry, ybar_n on exit (read and written by the same thread only)
+template <typename R, int WAVE, int MED>
+__global__ void __launch_bounds__(ADJ_THREADS) adj_stage1_kernel(ModelDev M, const R *__restrict__ Sn, R *YB,
+                                                        const R *__restrict__ SB4, const R *__restrict__ SB3,
+                                                        const R *__restrict__ SB2, const R *__restrict__ RB,
+                                                        int64_t cap, const int32_t *__restrict__ flags, int64_t off,
+                                                        int64_t n, R sg, R dt, GradAcc<R> grad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t b = off + i;
+    const bool e1 = (flags[b] & FL_REF_E1) != 0;
+    __shared__ R col[NF * ADJ_THREADS];
+    const StagedBar<R> fb = stage_slope_bar<R>(col + threadIdx.x, YB, SB2, RB, cap, b, dt / R(6), R(0.5) * dt);
+    R y[NF], yb[NF];
+    load_state(Sn, cap, b, y);
 #pragma unroll
     for (int f = 0; f < NF; f++) {
-        yb0[f] += yb1[f];
-        kb[f] = s6 * yb1[f];
-        t[f] = y[f] + dt * k3[f];
-        sb[f] = R(0);
+        const int64_t o = (int64_t)f * cap + b;
+        yb[f] = __ldcs(YB + o) + __ldcs(SB4 + o) + __ldcs(SB3 + o) + __ldcs(SB2 + o);
     }
-    rhs_vjp<R, WAVE, MED>(M, sg, e1, t, kb, sb, grad);  // k4 stage
+    if (RB) {
 #pragma unroll
-    for (int f = 0; f < NF; f++) {
-        yb0[f] += sb[f];
-        kb[f] = s3 * yb1[f] + dt * sb[f];
-        t[f] = y[f] + h * k2[f];
-        sb[f] = R(0);
+        for (int f = 0; f < 6; f++) yb[f] += RB[(int64_t)f * cap + b];
+#pragma unroll
+        for (int f = 0; f < 4; f++) yb[F_A0 + f] += RB[(int64_t)(6 + f) * cap + b];
     }
-    rhs_vjp<R, WAVE, MED>(M, sg, e1, t, kb, sb, grad);  // k3 stage
-#pragma unroll
-    for (int f = 0; f < NF; f++) {
-        yb0[f] += sb[f];
-        kb[f] = s3 * yb1[f] + h * sb[f];
-        t[f] = y[f] + h * k1[f];
-        sb[f] = R(0);
-    }
-    rhs_vjp<R, WAVE, MED>(M, sg, e1, t, kb, sb, grad);  // k2 stage
-#pragma unroll
-    for (int f = 0; f < NF; f++) {
-        yb0[f] += sb[f];
-        kb[f] = s6 * yb1[f] + h * sb[f];
-    }
-#pragma unroll
-    for (int d = 0; d < 6; d++) kb[F_Q + d] += f0b[d];
-    rhs_vjp<R, WAVE, MED>(M, sg, e1, y, kb, yb0, grad);  // k1 stage
-    store_state(YB, cap, b, yb0);
+    rhs_vjp<R, WAVE, MED>(M, sg, e1, y, fb, yb, grad);
+    store_state(YB, cap, b, yb);
 }
 
 // dL/dc(q) of the initial amplitudes: a = 2^{3/2}(F.n +- i G.n/(k c(q) |p|))/2, so da/dc = -a_G/c with
@@ -683,6 +783,33 @@ template <> struct AccSetup<float> {
     }
 };
 
+// One reverse step of one class (beams off .. off+n-1).  RS: 4 state slots + RB_FIELDS fields.
+template <typename R, int WAVE, int MED>
+fga_status reverse_step(const ModelDev &dev, const R *Sn, const R *Sn1, R *YB, R *RS, int64_t cap, int64_t slot,
+                        const int32_t *fl, int64_t off, int64_t nc, R sg, R dt, R w, R k, R rw2, int nrx,
+                        const R *rx, const R *ubs, const StepSamples &ss, size_t smem, GradAcc<R> gr,
+                        cudaStream_t s) {
+    R *T2 = RS, *T3 = RS + slot, *SB4 = RS + 2 * slot, *SB3 = RS + 3 * slot, *RB = RS + 4 * slot;
+    R *SB2 = T3;  // t3 is dead once sb3 is formed
+    const unsigned blocks = (unsigned)((nc + ADJ_THREADS - 1) / ADJ_THREADS);
+    ProfScope ps(P_ADJ_REV, s);
+    if (ss.nsj > 0) {
+        auto kern = adj_records_kernel<R, WAVE, MED>;
+        if (smem > 48 * 1024)
+            FGA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<blocks, ADJ_THREADS, smem, s>>>(dev, Sn, Sn1, YB, RB, cap, fl, off, nc, sg, dt, w, k, rw2, nrx, rx, ubs, ss, gr);
+    }
+    adj_stage4_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, Sn, YB, T2, T3, SB4, cap, fl, off, nc, sg, dt, gr);
+    adj_stage_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, T3, YB, SB4, SB3, cap, fl, off, nc, sg, dt / R(3), dt,
+                                                         gr);
+    adj_stage_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, T2, YB, SB3, SB2, cap, fl, off, nc, sg, dt / R(3),
+                                                         R(0.5) * dt, gr);
+    adj_stage1_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, Sn, YB, SB4, SB3, SB2, ss.nsj > 0 ? RB : nullptr,
+                                                          cap, fl, off, nc, sg, dt, gr);
+    FGA_CUDA(cudaGetLastError());
+    return FGA_OK;
+}
+
 template <typename R, int MED>
 fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, fga_beams *b,
                    fga_beams *bg, const std::vector<int> &sstep, const std::vector<double> &sth, const void *ubar,
@@ -697,15 +824,24 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
     FGA_TRY(seg.ensure(sizeof(R) * (size_t)slot * (size_t)(C + 1)));
     FGA_TRY(yb.ensure(sizeof(R) * (size_t)slot));
     FGA_TRY(rxd.ensure(sizeof(R) * 3 * (size_t)std::max<int64_t>(nrx, 1)));
+    double box_lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, box_hi[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
     {
         std::vector<double> rh((size_t)(3 * nrx));
         if (nrx > 0) FGA_CUDA(cudaMemcpyAsync(rh.data(), sd->rx, 8 * rh.size(), cudaMemcpyDeviceToHost, s));
         FGA_CUDA(cudaStreamSynchronize(s));
         std::vector<R> rr(rh.begin(), rh.end());
+        for (int64_t r = 0; r < nrx; r++)
+            for (int d = 0; d < 3; d++) {
+                box_lo[d] = std::min(box_lo[d], (double)rr[(size_t)(3 * r + d)]);
+                box_hi[d] = std::max(box_hi[d], (double)rr[(size_t)(3 * r + d)]);
+            }
         if (nrx > 0) FGA_CUDA(cudaMemcpyAsync(rxd.p, rr.data(), sizeof(R) * rr.size(), cudaMemcpyHostToDevice, s));
         FGA_CUDA(cudaStreamSynchronize(s));
     }
-    R *CK = ck.as<R>(), *SEG = seg.as<R>(), *YB = yb.as<R>();
+    // reverse-step scratch: t2, t3 (t3's slot then holds sb2), sb4, sb3, and RB_FIELDS record fields
+    ScopedDevBuf rs;
+    FGA_TRY(rs.ensure(sizeof(R) * ((size_t)slot * 4 + (size_t)RB_FIELDS * (size_t)cap)));
+    R *CK = ck.as<R>(), *SEG = seg.as<R>(), *YB = yb.as<R>(), *RS = rs.as<R>();
     const int64_t nn = MED == FGA_MEDIUM_GRID ? (int64_t)m->dev.n[0] * m->dev.n[1] * m->dev.n[2] : 0;
     ScopedDevBuf sgp, sgs;
     GradAcc<R> accp, accs;
@@ -754,6 +890,10 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
         // 2b. reverse steps
         for (int n = n0 + len - 1; n >= n0; n--) {
             StepSamples ss{};
+            for (int d = 0; d < 3; d++) {
+                ss.lo[d] = box_lo[d];
+                ss.hi[d] = box_hi[d];
+            }
             int jl = j;
             while (jl >= 0 && sstep[(size_t)jl] == n) jl--;
             ss.nsj = j - jl;
@@ -773,21 +913,14 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
             for (int cls = 0; cls < 4; cls++) {
                 const int64_t nc = b->n_cls[cls];
                 if (!nc) continue;
-                const R sg = (cls & 1) ? R(-1) : R(1);
-                const unsigned blocks = (unsigned)((nc + 127) / 128);
-                const GradAcc<R> gr = cls < 2 ? accp : accs;
-                ProfScope ps(P_ADJ_REV, s);
-                if (cls < 2) {
-                    auto kern = adj_step_kernel<R, 0, MED>;
-                    if (smem > 48 * 1024) FGA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                    kern<<<blocks, 128, smem, s>>>(m->dev, Sn, Sn1, YB, cap, fl, b->off_cls[cls], nc, sg, dt, (R)b->w,
-                                                   (R)b->k, (R)(rw * rw), (int)nrx, rxd.as<R>(), ubs, ss, gr);
-                } else {
-                    auto kern = adj_step_kernel<R, 1, MED>;
-                    if (smem > 48 * 1024) FGA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                    kern<<<blocks, 128, smem, s>>>(m->dev, Sn, Sn1, YB, cap, fl, b->off_cls[cls], nc, sg, dt, (R)b->w,
-                                                   (R)b->k, (R)(rw * rw), (int)nrx, rxd.as<R>(), ubs, ss, gr);
-                }
+                if (cls < 2)
+                    FGA_TRY((reverse_step<R, 0, MED>(m->dev, Sn, Sn1, YB, RS, cap, slot, fl, b->off_cls[cls], nc,
+                                                     (cls & 1) ? R(-1) : R(1), dt, (R)b->w, (R)b->k, (R)(rw * rw),
+                                                     (int)nrx, rxd.as<R>(), ubs, ss, smem, accp, s)));
+                else
+                    FGA_TRY((reverse_step<R, 1, MED>(m->dev, Sn, Sn1, YB, RS, cap, slot, fl, b->off_cls[cls], nc,
+                                                     (cls & 1) ? R(-1) : R(1), dt, (R)b->w, (R)b->k, (R)(rw * rw),
+                                                     (int)nrx, rxd.as<R>(), ubs, ss, smem, accs, s)));
             }
             FGA_CUDA(cudaGetLastError());
         }
