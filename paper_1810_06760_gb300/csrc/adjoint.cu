@@ -57,16 +57,26 @@ template <> struct GradAcc<float> {
     }
 };
 
-// ---------------------------------------------------------------------------------------------
-// adjoint of the trilinear model sampling: Qb += sum_f cb_f d field_f / dQ; grad[node][f] += w cb_f
-// ---------------------------------------------------------------------------------------------
-template <typename R, int MED>
-__device__ __forceinline__ void model_vjp(const ModelDev &M, int wave, const R x[3], const R cb[10], R Qb[3],
-                                          GradAcc<R> grad) {
-    if (MED != FGA_MEDIUM_GRID) return;  // constant media: no position or node dependence
-    const float4 *__restrict__ G = wave ? M.gs : M.gp;
-    int i[3];
-    R fr[3], dfr[3];
+// Deferred node cotangents: a stage adjoint records its sampling point and field cotangents (13
+// reals per beam, SoA with stride cap) instead of scattering; adj_scatter_kernel later adds the
+// records of one step that share a trilinear cell together and scatters each distinct cell once.
+template <typename R> struct DeferAcc {
+    R *p;
+    int64_t cap, b;
+    __device__ __forceinline__ void put(const R x[3], const R cb[10]) const {
+#pragma unroll
+        for (int d = 0; d < 3; d++) __stcs(p + (int64_t)d * cap + b, x[d]);
+#pragma unroll
+        for (int f = 0; f < 10; f++) __stcs(p + (int64_t)(3 + f) * cap + b, cb[f]);
+    }
+};
+constexpr int DEFER_FIELDS = 13;
+template <typename G> struct is_deferred { static constexpr bool value = false; };
+template <typename R> struct is_deferred<DeferAcc<R>> { static constexpr bool value = true; };
+
+// the trilinear cell of x: lower corner i[], fractions fr[], d fr/dx (zero where x is clamped)
+template <typename R>
+__device__ __forceinline__ void trilinear_cell(const ModelDev &M, const R x[3], int i[3], R fr[3], R dfr[3]) {
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const R ih = mp<R>(M.inv_h[d], M.finv_h[d]);
@@ -86,6 +96,21 @@ __device__ __forceinline__ void model_vjp(const ModelDev &M, int wave, const R x
         i[d] = id;
         fr[d] = t - R(id);
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// adjoint of the trilinear model sampling: Qb += sum_f cb_f d field_f / dQ; grad[node][f] += w cb_f
+// (G = GradAcc: scattered here; G = DeferAcc: recorded for adj_scatter_kernel)
+// ---------------------------------------------------------------------------------------------
+template <typename R, int MED, class G>
+__device__ __forceinline__ void model_vjp(const ModelDev &M, int wave, const R x[3], const R cb[10], R Qb[3],
+                                          G grad) {
+    if (MED != FGA_MEDIUM_GRID) return;  // constant media: no position or node dependence
+    const float4 *__restrict__ Gm = wave ? M.gs : M.gp;
+    int i[3];
+    R fr[3], dfr[3];
+    trilinear_cell<R>(M, x, i, fr, dfr);
+    if constexpr (is_deferred<G>::value) grad.put(x, cb);
     const int64_t s1 = M.n[2], s0 = (int64_t)M.n[1] * M.n[2];
     const int64_t base = (int64_t)i[0] * s0 + (int64_t)i[1] * s1 + i[2];
 #pragma unroll
@@ -97,7 +122,7 @@ __device__ __forceinline__ void model_vjp(const ModelDev &M, int wave, const R x
                 const int64_t node = base + a * s0 + b * s1 + c;
                 const R w0 = a ? fr[0] : R(1) - fr[0], w1 = b ? fr[1] : R(1) - fr[1], w2 = c ? fr[2] : R(1) - fr[2];
                 const R g0 = a ? dfr[0] : -dfr[0], g1 = b ? dfr[1] : -dfr[1], g2 = c ? dfr[2] : -dfr[2];
-                const float4 *p = G + 3 * node;
+                const float4 *p = Gm + 3 * node;
                 const float4 u0 = __ldg(p), u1 = __ldg(p + 1), u2 = __ldg(p + 2);
                 const float v[10] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w, u2.x, u2.y};
                 R dot = R(0);
@@ -106,7 +131,8 @@ __device__ __forceinline__ void model_vjp(const ModelDev &M, int wave, const R x
                 Qb[0] += dot * g0 * w1 * w2;
                 Qb[1] += dot * w0 * g1 * w2;
                 Qb[2] += dot * w0 * w1 * g2;
-                if (grad.p) grad.add(node, cb, w0 * w1 * w2);
+                if constexpr (!is_deferred<G>::value)
+                    if (grad.p) grad.add(node, cb, w0 * w1 * w2);
             }
 }
 
@@ -114,9 +140,9 @@ __device__ __forceinline__ void model_vjp(const ModelDev &M, int wave, const R x
 // adjoint of dy/dt (the right-hand side of beam_rhs): yb += (d rhs / dy)^T fb, node-field
 // cotangents to grad.  Complex cotangents follow zb = dL/dRe z + i dL/dIm z.
 // ---------------------------------------------------------------------------------------------
-template <typename R, int WAVE, int MED, class FB>
+template <typename R, int WAVE, int MED, class FB, class G>
 __device__ __forceinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, const R *__restrict__ y, FB fb,
-                                        R *__restrict__ yb, GradAcc<R> grad) {
+                                        R *__restrict__ yb, G grad) {
     R cf[10];
     const R Q[3] = {y[F_Q], y[F_Q + 1], y[F_Q + 2]};
     model_eval<R, MED>(M, WAVE, Q, cf);
@@ -637,11 +663,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_stage4_kernel(ModelDev M, con
                                                         const R *__restrict__ YB, R *__restrict__ T2,
                                                         R *__restrict__ T3, R *__restrict__ SB4, int64_t cap,
                                                         const int32_t *__restrict__ flags, int64_t off, int64_t n,
-                                                        R sg, R dt, GradAcc<R> grad) {
+                                                        R sg, R dt, R *__restrict__ CBr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t b = off + i;
     const bool e1 = (flags[b] & FL_REF_E1) != 0;
+    const DeferAcc<R> grad{CBr, cap, b};
     __shared__ R col[NF * ADJ_THREADS];
     const StagedBar<R> fb = stage_slope_bar<R>(col + threadIdx.x, YB, nullptr, nullptr, cap, b, dt / R(6), R(0));
     R y[NF], kk[NF], t[NF];
@@ -670,11 +697,12 @@ template <typename R, int WAVE, int MED>
 __global__ void __launch_bounds__(ADJ_THREADS) adj_stage_kernel(ModelDev M, const R *__restrict__ T, const R *__restrict__ YB,
                                                        const R *__restrict__ SBin, R *__restrict__ SBout, int64_t cap,
                                                        const int32_t *__restrict__ flags, int64_t off, int64_t n,
-                                                       R sg, R a, R c, GradAcc<R> grad) {
+                                                       R sg, R a, R c, R *__restrict__ CBr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t b = off + i;
     const bool e1 = (flags[b] & FL_REF_E1) != 0;
+    const DeferAcc<R> grad{CBr, cap, b};
     __shared__ R col[NF * ADJ_THREADS];
     const StagedBar<R> fb = stage_slope_bar<R>(col + threadIdx.x, YB, SBin, nullptr, cap, b, a, c);
     R t[NF], sb[NF];
@@ -691,11 +719,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_stage1_kernel(ModelDev M, con
                                                         const R *__restrict__ SB4, const R *__restrict__ SB3,
                                                         const R *__restrict__ SB2, const R *__restrict__ RB,
                                                         int64_t cap, const int32_t *__restrict__ flags, int64_t off,
-                                                        int64_t n, R sg, R dt, GradAcc<R> grad) {
+                                                        int64_t n, R sg, R dt, R *__restrict__ CBr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t b = off + i;
     const bool e1 = (flags[b] & FL_REF_E1) != 0;
+    const DeferAcc<R> grad{CBr, cap, b};
     __shared__ R col[NF * ADJ_THREADS];
     const StagedBar<R> fb = stage_slope_bar<R>(col + threadIdx.x, YB, SB2, RB, cap, b, dt / R(6), R(0.5) * dt);
     R y[NF], yb[NF];
@@ -713,6 +742,62 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_stage1_kernel(ModelDev M, con
     }
     rhs_vjp<R, WAVE, MED>(M, sg, e1, y, fb, yb, grad);
     store_state(YB, cap, b, yb);
+}
+
+// Node cotangents of one reverse step: the four stage records (DEFER_FIELDS reals each, record r at
+// CB + r * DEFER_FIELDS * cap) are grouped by trilinear cell; each distinct cell is scattered once with
+// the weighted sum of its records (stage inputs lie within dt c of each other, a fraction of a cell,
+// so most steps of a beam touch one or two cells instead of four).
+template <typename R, int WAVE>
+__global__ void __launch_bounds__(ADJ_THREADS) adj_scatter_kernel(ModelDev M, const R *__restrict__ CB, int64_t cap,
+                                                                  int64_t off, int64_t n, GradAcc<R> grad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !grad.p) return;
+    const int64_t b = off + i;
+    constexpr int NR = 4;
+    const int64_t s1 = M.n[2], s0 = (int64_t)M.n[1] * M.n[2];
+    int64_t base[NR];
+    R fr[NR][3], cb[NR][10];
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        const R *rp = CB + (int64_t)r * DEFER_FIELDS * cap + b;
+        const R x[3] = {__ldcs(rp), __ldcs(rp + cap), __ldcs(rp + 2 * cap)};
+#pragma unroll
+        for (int f = 0; f < 10; f++) cb[r][f] = __ldcs(rp + (int64_t)(3 + f) * cap);
+        int id[3];
+        R dfr[3];
+        trilinear_cell<R>(M, x, id, fr[r], dfr);
+        base[r] = (int64_t)id[0] * s0 + (int64_t)id[1] * s1 + id[2];
+    }
+    unsigned done = 0;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        if (done & (1u << r)) continue;
+        unsigned grp = 0;
+#pragma unroll
+        for (int q = r; q < NR; q++)
+            if (!(done & (1u << q)) && base[q] == base[r]) grp |= 1u << q;
+        done |= grp;
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int bb = 0; bb < 2; bb++)
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    R acc[10];
+#pragma unroll
+                    for (int f = 0; f < 10; f++) acc[f] = R(0);
+#pragma unroll
+                    for (int q = r; q < NR; q++)
+                        if (grp & (1u << q)) {
+                            const R w = (a ? fr[q][0] : R(1) - fr[q][0]) * (bb ? fr[q][1] : R(1) - fr[q][1]) *
+                                        (c ? fr[q][2] : R(1) - fr[q][2]);
+#pragma unroll
+                            for (int f = 0; f < 10; f++) acc[f] += cb[q][f] * w;
+                        }
+                    grad.add(base[r] + a * s0 + bb * s1 + c, acc, R(1));
+                }
+    }
 }
 
 // dL/dc(q) of the initial amplitudes: a = 2^{3/2}(F.n +- i G.n/(k c(q) |p|))/2, so da/dc = -a_G/c with
@@ -783,7 +868,7 @@ template <> struct AccSetup<float> {
     }
 };
 
-// One reverse step of one class (beams off .. off+n-1).  RS: 4 state slots + RB_FIELDS fields.
+// One reverse step of one class (beams off .. off+n-1).  RS: 4 state slots, RB_FIELDS + 4 DEFER_FIELDS fields.
 template <typename R, int WAVE, int MED>
 fga_status reverse_step(const ModelDev &dev, const R *Sn, const R *Sn1, R *YB, R *RS, int64_t cap, int64_t slot,
                         const int32_t *fl, int64_t off, int64_t nc, R sg, R dt, R w, R k, R rw2, int nrx,
@@ -791,6 +876,8 @@ fga_status reverse_step(const ModelDev &dev, const R *Sn, const R *Sn1, R *YB, R
                         cudaStream_t s) {
     R *T2 = RS, *T3 = RS + slot, *SB4 = RS + 2 * slot, *SB3 = RS + 3 * slot, *RB = RS + 4 * slot;
     R *SB2 = T3;  // t3 is dead once sb3 is formed
+    R *CB = RB + (int64_t)RB_FIELDS * cap;  // deferred node cotangents: record r = stage r + 1
+    const int64_t rst = (int64_t)DEFER_FIELDS * cap;
     const unsigned blocks = (unsigned)((nc + ADJ_THREADS - 1) / ADJ_THREADS);
     ProfScope ps(P_ADJ_REV, s);
     if (ss.nsj > 0) {
@@ -799,13 +886,16 @@ fga_status reverse_step(const ModelDev &dev, const R *Sn, const R *Sn1, R *YB, R
             FGA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks, ADJ_THREADS, smem, s>>>(dev, Sn, Sn1, YB, RB, cap, fl, off, nc, sg, dt, w, k, rw2, nrx, rx, ubs, ss, gr);
     }
-    adj_stage4_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, Sn, YB, T2, T3, SB4, cap, fl, off, nc, sg, dt, gr);
+    adj_stage4_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, Sn, YB, T2, T3, SB4, cap, fl, off, nc, sg, dt,
+                                                                  CB + 3 * rst);
     adj_stage_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, T3, YB, SB4, SB3, cap, fl, off, nc, sg, dt / R(3), dt,
-                                                         gr);
+                                                                 CB + 2 * rst);
     adj_stage_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, T2, YB, SB3, SB2, cap, fl, off, nc, sg, dt / R(3),
-                                                         R(0.5) * dt, gr);
+                                                                 R(0.5) * dt, CB + rst);
     adj_stage1_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, Sn, YB, SB4, SB3, SB2, ss.nsj > 0 ? RB : nullptr,
-                                                          cap, fl, off, nc, sg, dt, gr);
+                                                                  cap, fl, off, nc, sg, dt, CB);
+    if (MED == FGA_MEDIUM_GRID)
+        adj_scatter_kernel<R, WAVE><<<blocks, ADJ_THREADS, 0, s>>>(dev, CB, cap, off, nc, gr);
     FGA_CUDA(cudaGetLastError());
     return FGA_OK;
 }
@@ -838,9 +928,10 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
         if (nrx > 0) FGA_CUDA(cudaMemcpyAsync(rxd.p, rr.data(), sizeof(R) * rr.size(), cudaMemcpyHostToDevice, s));
         FGA_CUDA(cudaStreamSynchronize(s));
     }
-    // reverse-step scratch: t2, t3 (t3's slot then holds sb2), sb4, sb3, and RB_FIELDS record fields
+    // reverse-step scratch: t2, t3 (t3's slot then holds sb2), sb4, sb3, RB_FIELDS record fields and the
+    // four stages' deferred node cotangents
     ScopedDevBuf rs;
-    FGA_TRY(rs.ensure(sizeof(R) * ((size_t)slot * 4 + (size_t)RB_FIELDS * (size_t)cap)));
+    FGA_TRY(rs.ensure(sizeof(R) * ((size_t)slot * 4 + (size_t)(RB_FIELDS + 4 * DEFER_FIELDS) * (size_t)cap)));
     R *CK = ck.as<R>(), *SEG = seg.as<R>(), *YB = yb.as<R>(), *RS = rs.as<R>();
     const int64_t nn = MED == FGA_MEDIUM_GRID ? (int64_t)m->dev.n[0] * m->dev.n[1] * m->dev.n[2] : 0;
     ScopedDevBuf sgp, sgs;
