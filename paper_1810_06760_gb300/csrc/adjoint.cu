@@ -744,60 +744,52 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_stage1_kernel(ModelDev M, con
     store_state(YB, cap, b, yb);
 }
 
-// Node cotangents of one reverse step: the four stage records (DEFER_FIELDS reals each, record r at
-// CB + r * DEFER_FIELDS * cap) are grouped by trilinear cell; each distinct cell is scattered once with
-// the weighted sum of its records (stage inputs lie within dt c of each other, a fraction of a cell,
-// so most steps of a beam touch one or two cells instead of four).
+// Node cotangents of the last few reverse steps: nrec stage records (DEFER_FIELDS reals each, record r
+// at CB + r * DEFER_FIELDS * cap), ordered along the beam's path (consecutive stage inputs lie within
+// dt c / 2 of each other, a fraction of a cell).  The records are summed, with their trilinear weights,
+// into the 8 x 10 cotangents of one open cell; the cell is scattered only when the path leaves it, so
+// a beam touches each cell of its path about once per call instead of once per stage.
 template <typename R, int WAVE>
-__global__ void __launch_bounds__(ADJ_THREADS) adj_scatter_kernel(ModelDev M, const R *__restrict__ CB, int64_t cap,
-                                                                  int64_t off, int64_t n, GradAcc<R> grad) {
+__global__ void __launch_bounds__(ADJ_THREADS) adj_scatter_kernel(ModelDev M, const R *__restrict__ CB, int nrec,
+                                                                  int64_t cap, int64_t off, int64_t n,
+                                                                  GradAcc<R> grad) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !grad.p) return;
     const int64_t b = off + i;
-    constexpr int NR = 4;
     const int64_t s1 = M.n[2], s0 = (int64_t)M.n[1] * M.n[2];
-    int64_t base[NR];
-    R fr[NR][3], cb[NR][10];
+    R acc[8][10];
+    int64_t open = -1;
+    auto flush = [&]() {
 #pragma unroll
-    for (int r = 0; r < NR; r++) {
+        for (int c = 0; c < 8; c++) grad.add(open + (c >> 2) * s0 + ((c >> 1) & 1) * s1 + (c & 1), acc[c], R(1));
+    };
+    for (int r = 0; r < nrec; r++) {
         const R *rp = CB + (int64_t)r * DEFER_FIELDS * cap + b;
         const R x[3] = {__ldcs(rp), __ldcs(rp + cap), __ldcs(rp + 2 * cap)};
+        R cb[10];
 #pragma unroll
-        for (int f = 0; f < 10; f++) cb[r][f] = __ldcs(rp + (int64_t)(3 + f) * cap);
+        for (int f = 0; f < 10; f++) cb[f] = __ldcs(rp + (int64_t)(3 + f) * cap);
         int id[3];
-        R dfr[3];
-        trilinear_cell<R>(M, x, id, fr[r], dfr);
-        base[r] = (int64_t)id[0] * s0 + (int64_t)id[1] * s1 + id[2];
+        R fr[3], dfr[3];
+        trilinear_cell<R>(M, x, id, fr, dfr);
+        const int64_t base = (int64_t)id[0] * s0 + (int64_t)id[1] * s1 + id[2];
+        if (base != open) {
+            if (open >= 0) flush();
+            open = base;
+#pragma unroll
+            for (int c = 0; c < 8; c++)
+#pragma unroll
+                for (int f = 0; f < 10; f++) acc[c][f] = R(0);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const R w = ((c >> 2) ? fr[0] : R(1) - fr[0]) * (((c >> 1) & 1) ? fr[1] : R(1) - fr[1]) *
+                        ((c & 1) ? fr[2] : R(1) - fr[2]);
+#pragma unroll
+            for (int f = 0; f < 10; f++) acc[c][f] += cb[f] * w;
+        }
     }
-    unsigned done = 0;
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
-        if (done & (1u << r)) continue;
-        unsigned grp = 0;
-#pragma unroll
-        for (int q = r; q < NR; q++)
-            if (!(done & (1u << q)) && base[q] == base[r]) grp |= 1u << q;
-        done |= grp;
-#pragma unroll
-        for (int a = 0; a < 2; a++)
-#pragma unroll
-            for (int bb = 0; bb < 2; bb++)
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    R acc[10];
-#pragma unroll
-                    for (int f = 0; f < 10; f++) acc[f] = R(0);
-#pragma unroll
-                    for (int q = r; q < NR; q++)
-                        if (grp & (1u << q)) {
-                            const R w = (a ? fr[q][0] : R(1) - fr[q][0]) * (bb ? fr[q][1] : R(1) - fr[q][1]) *
-                                        (c ? fr[q][2] : R(1) - fr[q][2]);
-#pragma unroll
-                            for (int f = 0; f < 10; f++) acc[f] += cb[q][f] * w;
-                        }
-                    grad.add(base[r] + a * s0 + bb * s1 + c, acc, R(1));
-                }
-    }
+    if (open >= 0) flush();
 }
 
 // dL/dc(q) of the initial amplitudes: a = 2^{3/2}(F.n +- i G.n/(k c(q) |p|))/2, so da/dc = -a_G/c with
@@ -868,16 +860,22 @@ template <> struct AccSetup<float> {
     }
 };
 
-// One reverse step of one class (beams off .. off+n-1).  RS: 4 state slots, RB_FIELDS + 4 DEFER_FIELDS fields.
+// Reverse steps whose node cotangents are scattered together (the records of SCATTER_STEPS steps).
+constexpr int SCATTER_STEPS = 4;
+
+// One reverse step of one class (beams off .. off+n-1).  RS: 4 state slots, RB_FIELDS fields, then
+// 4 SCATTER_STEPS deferred-cotangent records.  The step is the jst-th (0-based) since the last scatter;
+// scatter: scatter the records of steps 0..jst after it.
 template <typename R, int WAVE, int MED>
 fga_status reverse_step(const ModelDev &dev, const R *Sn, const R *Sn1, R *YB, R *RS, int64_t cap, int64_t slot,
                         const int32_t *fl, int64_t off, int64_t nc, R sg, R dt, R w, R k, R rw2, int nrx,
-                        const R *rx, const R *ubs, const StepSamples &ss, size_t smem, GradAcc<R> gr,
-                        cudaStream_t s) {
+                        const R *rx, const R *ubs, const StepSamples &ss, size_t smem, GradAcc<R> gr, int jst,
+                        bool scatter, cudaStream_t s) {
     R *T2 = RS, *T3 = RS + slot, *SB4 = RS + 2 * slot, *SB3 = RS + 3 * slot, *RB = RS + 4 * slot;
     R *SB2 = T3;  // t3 is dead once sb3 is formed
-    R *CB = RB + (int64_t)RB_FIELDS * cap;  // deferred node cotangents: record r = stage r + 1
     const int64_t rst = (int64_t)DEFER_FIELDS * cap;
+    // records in path order (latest first): step j holds stage 4, 3, 2, 1 at records 4j .. 4j+3
+    R *CB0 = RB + (int64_t)RB_FIELDS * cap, *CB = CB0 + (int64_t)(4 * jst) * rst;
     const unsigned blocks = (unsigned)((nc + ADJ_THREADS - 1) / ADJ_THREADS);
     ProfScope ps(P_ADJ_REV, s);
     if (ss.nsj > 0) {
@@ -887,15 +885,15 @@ fga_status reverse_step(const ModelDev &dev, const R *Sn, const R *Sn1, R *YB, R
         kern<<<blocks, ADJ_THREADS, smem, s>>>(dev, Sn, Sn1, YB, RB, cap, fl, off, nc, sg, dt, w, k, rw2, nrx, rx, ubs, ss, gr);
     }
     adj_stage4_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, Sn, YB, T2, T3, SB4, cap, fl, off, nc, sg, dt,
-                                                                  CB + 3 * rst);
+                                                                  CB);
     adj_stage_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, T3, YB, SB4, SB3, cap, fl, off, nc, sg, dt / R(3), dt,
-                                                                 CB + 2 * rst);
+                                                                 CB + rst);
     adj_stage_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, T2, YB, SB3, SB2, cap, fl, off, nc, sg, dt / R(3),
-                                                                 R(0.5) * dt, CB + rst);
+                                                                 R(0.5) * dt, CB + 2 * rst);
     adj_stage1_kernel<R, WAVE, MED><<<blocks, ADJ_THREADS, 0, s>>>(dev, Sn, YB, SB4, SB3, SB2, ss.nsj > 0 ? RB : nullptr,
-                                                                  cap, fl, off, nc, sg, dt, CB);
-    if (MED == FGA_MEDIUM_GRID)
-        adj_scatter_kernel<R, WAVE><<<blocks, ADJ_THREADS, 0, s>>>(dev, CB, cap, off, nc, gr);
+                                                                  cap, fl, off, nc, sg, dt, CB + 3 * rst);
+    if (MED == FGA_MEDIUM_GRID && scatter)
+        adj_scatter_kernel<R, WAVE><<<blocks, ADJ_THREADS, 0, s>>>(dev, CB0, 4 * (jst + 1), cap, off, nc, gr);
     FGA_CUDA(cudaGetLastError());
     return FGA_OK;
 }
@@ -929,9 +927,10 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
         FGA_CUDA(cudaStreamSynchronize(s));
     }
     // reverse-step scratch: t2, t3 (t3's slot then holds sb2), sb4, sb3, RB_FIELDS record fields and the
-    // four stages' deferred node cotangents
+    // deferred node cotangents of SCATTER_STEPS steps
     ScopedDevBuf rs;
-    FGA_TRY(rs.ensure(sizeof(R) * ((size_t)slot * 4 + (size_t)(RB_FIELDS + 4 * DEFER_FIELDS) * (size_t)cap)));
+    FGA_TRY(rs.ensure(sizeof(R) *
+                      ((size_t)slot * 4 + (size_t)(RB_FIELDS + 4 * SCATTER_STEPS * DEFER_FIELDS) * (size_t)cap)));
     R *CK = ck.as<R>(), *SEG = seg.as<R>(), *YB = yb.as<R>(), *RS = rs.as<R>();
     const int64_t nn = MED == FGA_MEDIUM_GRID ? (int64_t)m->dev.n[0] * m->dev.n[1] * m->dev.n[2] : 0;
     ScopedDevBuf sgp, sgs;
@@ -960,6 +959,7 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
     FGA_CUDA(cudaGetLastError());
     const size_t smem_max = 200 * 1024;
     int j = (int)sstep.size() - 1;
+    int jst = 0;  // reverse steps since the last scatter of node cotangents
     for (int sgi = nseg - 1; sgi >= 0; sgi--) {
         const int n0 = sgi * C, len = std::min(C, N - n0);
         // 2a. the segment's states: slot 0 = checkpoint, slots 1..len recomputed
@@ -1001,19 +1001,21 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
             FGA_CHECK(smem <= smem_max, "fga_solve_vjp: receivers x samples per step exceed the shared-memory stage");
             const R *ubs = ss.nsj > 0 ? ub + (size_t)jfirst * nrx * 6 : ub;
             const R *Sn = SEG + (size_t)(n - n0) * slot, *Sn1 = SEG + (size_t)(n - n0 + 1) * slot;
+            const bool scatter = jst == SCATTER_STEPS - 1 || n == 0;
             for (int cls = 0; cls < 4; cls++) {
                 const int64_t nc = b->n_cls[cls];
                 if (!nc) continue;
                 if (cls < 2)
                     FGA_TRY((reverse_step<R, 0, MED>(m->dev, Sn, Sn1, YB, RS, cap, slot, fl, b->off_cls[cls], nc,
                                                      (cls & 1) ? R(-1) : R(1), dt, (R)b->w, (R)b->k, (R)(rw * rw),
-                                                     (int)nrx, rxd.as<R>(), ubs, ss, smem, accp, s)));
+                                                     (int)nrx, rxd.as<R>(), ubs, ss, smem, accp, jst, scatter, s)));
                 else
                     FGA_TRY((reverse_step<R, 1, MED>(m->dev, Sn, Sn1, YB, RS, cap, slot, fl, b->off_cls[cls], nc,
                                                      (cls & 1) ? R(-1) : R(1), dt, (R)b->w, (R)b->k, (R)(rw * rw),
-                                                     (int)nrx, rxd.as<R>(), ubs, ss, smem, accs, s)));
+                                                     (int)nrx, rxd.as<R>(), ubs, ss, smem, accs, jst, scatter, s)));
             }
             FGA_CUDA(cudaGetLastError());
+            jst = scatter ? 0 : jst + 1;
         }
     }
     // 3. initial-velocity term
