@@ -861,7 +861,7 @@ template <> struct AccSetup<float> {
 };
 
 // Reverse steps whose node cotangents are scattered together (the records of SCATTER_STEPS steps).
-constexpr int SCATTER_STEPS = 4;
+constexpr int SCATTER_STEPS = 8;
 
 // One reverse step of one class (beams off .. off+n-1).  RS: 4 state slots, RB_FIELDS fields, then
 // 4 SCATTER_STEPS deferred-cotangent records.  The step is the jst-th (0-based) since the last scatter;
