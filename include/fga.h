@@ -263,13 +263,14 @@ fga_status fga_server_destroy(fga_server *sv);
  * L is the discrete forward map fga_solve computes: initialisation (its c(q) term), classical RK4,
  * Hermite-interpolated records and the windowed Gaussian sums (the window's edge is not
  * differentiated).  The forward pass stores the beam state every checkpoint_every steps (<= 0: 20);
- * each segment is recomputed in reverse, so device memory holds (ceil(nsteps/C) + C + 2) beam states
- * (46 values per beam).  Grid and constant media (constant media have no node fields: grad_p and
+ * each segment is recomputed in reverse, so device memory holds (ceil(nsteps/C) + C + 7) beam states
+ * (46 values per beam) plus 432 values per beam of reverse-step scratch (stage records of 8 steps).  Grid and constant media (constant media have no node fields: grad_p and
  * grad_s may be NULL); receivers as points (sd->rx, sd->n_rx >= 1); snapshots are ignored; at most
  * 4 sample times inside one step and n_rx * (3 + 6 * samples in a step) values of the init
- * precision within 200 KiB.  Node cotangents are accumulated with atomics (FP64 path: FP64 into the
- * outputs; FP32 path: FP32 into a scratch grid that is added to the outputs at the end), so the last
- * bits depend on the order of the updates.  Synchronous on s.  Errors: INVALID_ARG, UNSUPPORTED
+ * precision within 200 KiB.  Node cotangents of a beam are summed along its path over up to 8 steps
+ * per trilinear cell, then accumulated with atomics (FP64 path: FP64 into the outputs; FP32 path:
+ * FP32 into a scratch grid that is added to the outputs at the end), so the last bits depend on the
+ * order of the updates.  Synchronous on s.  Errors: INVALID_ARG, UNSUPPORTED
  * (other media), OOM, CUDA. */
 fga_status fga_solve_vjp(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, const void *ubar,
                          double *grad_p, double *grad_s, int checkpoint_every, fga_stream_t s);
