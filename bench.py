@@ -69,6 +69,18 @@ def workload(size: str):
     return W.smooth()
 
 
+METRIC = "FGA beam-steps/s and Gaussian-sum pts/s at fixed error; p50/p99 solve latency"
+
+
+def workload_desc(w) -> str:
+    """The forward-solve workload, named by its sizes (the same words in both arms' config)."""
+    n = w.medium.grid_p.shape[0]
+    snap = "x".join(str(len(a)) for a in w.snap_axes)
+    return (f"smooth-heterogeneous: {n}^3 grid medium, k={w.k:g}, {w.mesh.nq}^3 q x {w.mesh.np_}^3 p mesh x "
+            f"{len(w.classes)} classes ({w.n_beams} beams), {w.nsteps} RK4 steps, {len(w.receivers)} rx x "
+            f"{len(w.times)} samples + {snap} snapshot")
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -202,12 +214,11 @@ def run_reference(args):
     tot_bs = sum(v[0] for v in vals)
     tot_s = sum(v[1] for v in vals)
     value = tot_bs / tot_s
-    line = {"impl": "reference", "metric": "FGA beam-steps/s (smooth heterogeneous medium, 128^3 grid, k=64)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "beam-steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "smooth-heterogeneous 128^3, 24^3 q x 8^3 p x 4 classes, 400 steps, "
-                                   "400 rx x 1000 samples", "sample": desc},
+            "config": {"workload": workload_desc(w), "sample": desc},
             "cpu_baseline": {"value": value, "unit": "beam-steps/s", "cores": thr, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "beam-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -311,12 +322,11 @@ def run_ours(args):
                 "per_launch_ms": per_launch_ms, "launches": launches}
     gauss_s = gauss_ms_total / 1e3
     line = {
-        "metric": "FGA beam-steps/s and Gaussian-sum pts/s at fixed error; p50/p99 solve latency",
+        "metric": METRIC,
         "value": value, "unit": "beam-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
-        "config": {"workload": "smooth-heterogeneous: 128^3 grid medium, k=64, 24^3 q x 8^3 p mesh x 4 classes "
-                               f"({nb} beams), 400 RK4 steps, 400 rx x 1000 samples + 64^3 snapshot",
+        "config": {"workload": workload_desc(w),
                    "l2": "inputs larger than L2 (beam state 5.2 GB)", "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": statistics.median(per_step_ms),
                        "p99": sorted(per_step_ms)[min(len(per_step_ms) - 1, math.ceil(0.99 * len(per_step_ms)) - 1)]},
@@ -433,7 +443,7 @@ def run_serving(args):
     q = lambda p: float(np.percentile(lat, p))
     beam_steps = sum(w.n_beams * w.nsteps for w, *_ in staged)
     line = {
-        "metric": "FGA beam-steps/s and Gaussian-sum pts/s at fixed error; p50/p99 solve latency",
+        "metric": METRIC,
         "value": beam_steps / wall, "unit": "beam-steps/s", "n_gpus": world, "steps": len(reqs), "warmup": 4,
         "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
