@@ -590,7 +590,8 @@ template <typename R> struct QPBar {
     __device__ __forceinline__ R operator()(int f) const { return f < 6 ? v[f] : R(0); }
 };
 
-template <typename R, int WAVE, int MED>
+// D1: some sample lies strictly inside the step, so the records depend on y_{n+1}'s slope as well
+template <typename R, int WAVE, int MED, bool D1>
 __global__ void __launch_bounds__(ADJ_THREADS) adj_records_kernel(ModelDev M, const R *__restrict__ Sn,
                                                          const R *__restrict__ Sn1, R *__restrict__ YB,
                                                          R *__restrict__ RB, int64_t cap,
@@ -612,7 +613,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_records_kernel(ModelDev M, co
     load_state(Sn, cap, b, y);
     beam_rhs<R, WAVE, MED>(M, sg, e1, y, k1);
     load_state(Sn1, cap, b, y1);
-    if (ss.need_d1)
+    if constexpr (D1)
         beam_rhs<R, WAVE, MED>(M, sg, e1, y1, d1);
     else
 #pragma unroll
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_records_kernel(ModelDev M, co
         gauss_vjp<R>(rec, xs, us + (size_t)6 * nrx * s, nrx, k, rw2, rb);
         record_vjp<R, WAVE>(e1, y, k1, y1, d1, dt, th, w, rb, y0b, f0b, y1b, f1b);
     }
-    if (ss.need_d1) {
+    if constexpr (D1) {
         rhs_vjp<R, WAVE, MED>(M, sg, e1, y1, QPBar<R>{f1b}, y1b, grad);
 #pragma unroll
         for (int f = 0; f < NF; f++) YB[(int64_t)f * cap + b] += y1b[f];
@@ -879,7 +880,7 @@ fga_status reverse_step(const ModelDev &dev, const R *Sn, const R *Sn1, R *YB, R
     const unsigned blocks = (unsigned)((nc + ADJ_THREADS - 1) / ADJ_THREADS);
     ProfScope ps(P_ADJ_REV, s);
     if (ss.nsj > 0) {
-        auto kern = adj_records_kernel<R, WAVE, MED>;
+        auto kern = ss.need_d1 ? adj_records_kernel<R, WAVE, MED, true> : adj_records_kernel<R, WAVE, MED, false>;
         if (smem > 48 * 1024)
             FGA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks, ADJ_THREADS, smem, s>>>(dev, Sn, Sn1, YB, RB, cap, fl, off, nc, sg, dt, w, k, rw2, nrx, rx, ubs, ss, gr);
