@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="the crosswell gradient instead: 16 sources x 3.5 M beams, 200 steps, 256 receivers, L2 "
                          "misfit against data of the bumped model; time per gradient (forward + adjoint)")
+    ap.add_argument("--misfit", default="l2", choices=["l2", "traveltime"],
+                    help="with --adjoint: L2 waveform misfit, or cross-correlation traveltime misfit "
+                         "(delays within +-20 samples) with its synthetic-only adjoint source")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -502,8 +505,12 @@ def run_adjoint(args):
         misfit = 0.0
         for w, desc, f, rx, d in staged:
             u, _ = fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, rw=w.rw)
-            r = u - d
-            misfit += 0.5 * float(r.abs().pow(2).sum())
+            if args.misfit == "traveltime":
+                _, r, mis = fga.traveltime_adjoint(u, d, float(w.times[1] - w.times[0]), 20)
+                misfit += float(mis.item())
+            else:
+                r = u - d
+                misfit += 0.5 * float(r.abs().pow(2).sum())
             fga.solve_vjp(model, desc, w.dt, w.nsteps, w.times, rx, r, grad_p=gp, grad_s=gs, rw=w.rw,
                           checkpoint_every=20)
         return misfit
@@ -522,7 +529,8 @@ def run_adjoint(args):
     fga.profile_enable(0)
     beam_steps = sum(w.n_beams * w.nsteps for w in ws)
     line = {
-        "metric": "crosswell L2-misfit gradient (forward + discrete adjoint)",
+        "metric": ("crosswell traveltime-misfit gradient (forward + discrete adjoint)" if args.misfit == "traveltime"
+                   else "crosswell L2-misfit gradient (forward + discrete adjoint)"),
         "value": wall / args.steps, "unit": "s/gradient", "higher_is_better": False, "n_gpus": world,
         "steps": args.steps, "warmup": max(1, args.warmup), "dtype": "f32" if prec == fga.PREC_FP32 else "f64",
         "data": "synthetic", "config": {"workload": f"crosswell ({args.size}): 64^3 smooth model, {len(ws)} sources x "

@@ -275,6 +275,29 @@ fga_status fga_server_destroy(fga_server *sv);
 fga_status fga_solve_vjp(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, const void *ubar,
                          double *grad_p, double *grad_s, int checkpoint_every, fga_stream_t s);
 
+/* Cross-correlation traveltime misfit and its adjoint source.  The paper's inversion section
+ * (wave-equation-based traveltime tomography and FWI) measures traveltimes as in Tromp, Tape and
+ * Liu (2005) and prints no formula; this is that measurement on the sampled records.
+ * syn, obs: DEVICE complex [n_times][n_rx][3] (the seismogram layout of fga_solve), complex64 for
+ * FGA_PREC_FP32 and complex128 for FGA_PREC_FP64, samples dt apart.  Per receiver r, with
+ * C_r(m) = sum_j sum_c Re(conj(syn[j][r][c]) obs[j+m][r][c]) for m = -max_lag..max_lag (zero
+ * beyond the record) and m* the smallest lag of its largest value:
+ *   tau[r] = (m* + (a - c) / (2 (a - 2b + c))) dt   with a, b, c = C_r(m*-1), C_r(m*), C_r(m*+1),
+ * the step taken only when -max_lag < m* < max_lag and a - 2b + c < 0 (tau > 0: the observed
+ * record arrives later).  misfit = 1/2 sum_r tau[r]^2 (DEVICE double [1], may be NULL).
+ * ubar (DEVICE, the type and layout of syn, may be NULL) receives the misfit's cotangent
+ * dL/dRe syn + i dL/dIm syn in the synthetic-only form: ubar[j][r][c] = tau[r] s'[j] dt / N_r with
+ * s'[j] = (syn[j+1] - syn[j-1]) / (2 dt), N_r = (1/dt) sum_{j=-1}^{n_times-1} sum_c
+ * |syn[j+1] - syn[j]|^2 and syn[-1] = syn[n_times] = 0 (0 where N_r = 0).  It is the exact
+ * derivative of tau when obs is a whole-sample shift of syn; fed to fga_solve_vjp it gives the
+ * traveltime misfit's model gradient.  tau: DEVICE double [n_rx].  The correlation and tau are
+ * computed in FP64 for both precisions.  Non-finite records give unspecified delays.  Needs
+ * 96 n_times + 16 max_lag + 8 bytes within 200 KiB of shared memory.  Asynchronous on s.
+ * Errors: INVALID_ARG (precision, n_times < 1, n_rx < 0, dt, max_lag outside [0, n_times),
+ * missing pointers, record too long), CUDA. */
+fga_status fga_traveltime_adjoint(const void *syn, const void *obs, int precision, int64_t n_times, int64_t n_rx,
+                                  double dt, int max_lag, double *tau, void *ubar, double *misfit, fga_stream_t s);
+
 /* Cell binning (no counterpart in the paper: the fast summation it cites is not printed).
  * For FP32 centres Q (DEVICE float [n][3]) computes key = (c0 nc1 + c1) nc2 + c2 with
  * c_d = floor((Q_d - o_d) * inv_h) in FP32 round-to-nearest, clamped to [0, nc_d-1], then a
@@ -293,7 +316,7 @@ fga_status fga_bin(const float *Q, int64_t n, const float origin[3], float inv_h
  * 3 records, 4 Gaussian sums at sample times inside fga_solve, 5 Gaussian-sum reductions,
  * 6 Gaussian sums at the current beam state (snapshots, fga_reconstruct, fga_reconstruct_lattice),
  * 7 layered-medium steps with interface events, 8 adjoint forward recomputation (checkpoints and
- * segments), 9 adjoint reverse steps, 10 adjoint initial-amplitude term, 11 unused.  pairs_in_window counts the
+ * segments), 9 adjoint reverse steps, 10 adjoint initial-amplitude term, 11 traveltime misfit.  pairs_in_window counts the
  * (beam, point) pairs inside the truncation window that the Gaussian sum evaluated; pairs_tested the
  * pairs it examined; beam_steps the beam RK4 steps advanced.  fga_profile_read waits for the timed
  * launches to finish; reset != 0 zeroes the counters afterwards.  Process-wide state, meant to be

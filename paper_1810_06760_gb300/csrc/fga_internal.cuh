@@ -93,6 +93,7 @@ enum ProfCat {
     P_ADJ_FWD = 8,   // adjoint: forward recomputation (checkpoints, segments)
     P_ADJ_REV = 9,   // adjoint: reverse steps
     P_ADJ_INIT = 10, // adjoint: initial-amplitude term
+    P_MISFIT = 11,   // traveltime misfit and adjoint source
     P_NCAT = 12
 };
 struct ProfScope {  // wraps one kernel launch on stream s

@@ -24,9 +24,9 @@ EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_propa
             "fga_reconstruct_lattice", "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export",
             "fga_beams_export_all", "fga_beams_destroy", "fga_bin", "fga_profile_enable", "fga_profile_read",
             "fga_solve_vjp", "fga_server_create", "fga_server_submit", "fga_server_wait", "fga_server_stats",
-            "fga_server_destroy", "fga_last_error", "fga_version"]
+            "fga_server_destroy", "fga_traveltime_adjoint", "fga_last_error", "fga_version"]
 PROFILE_CATEGORIES = ["decompose", "propagate", "binning", "records", "gauss_sum", "gauss_reduce", "gauss_sum_state",
-                      "interfaces", "adjoint_forward", "adjoint_reverse", "adjoint_init", "unused"]
+                      "interfaces", "adjoint_forward", "adjoint_reverse", "adjoint_init", "misfit"]
 
 
 class FGAError(RuntimeError):
@@ -121,6 +121,7 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_beams_export_all.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
     L.fga_beams_destroy.argtypes = [vp]
     L.fga_bin.argtypes = [vp, i64, vp, C.c_float, vp, vp, vp, vp, vp]
+    L.fga_traveltime_adjoint.argtypes = [vp, vp, i32, i64, i64, C.c_double, i32, vp, vp, vp, vp]
     L.fga_profile_enable.argtypes = [i32]
     L.fga_profile_read.argtypes = [C.POINTER(Profile), i32]
     L.fga_last_error.argtypes = [C.c_char_p, C.c_size_t]
@@ -402,6 +403,24 @@ def solve_vjp(model: Model, desc: InitDesc, dt: float, nsteps: int, times, rx, u
     return grad_p, grad_s
 
 
+def traveltime_adjoint(syn, obs, dt: float, max_lag: int, stream=None):
+    """Cross-correlation delays of obs relative to syn (CUDA complex [n_t, n_rx, 3], both complex64 or
+    both complex128), the misfit 1/2 sum tau^2 and its seismogram cotangent (the adjoint source for
+    solve_vjp).  Returns (tau CUDA float64 [n_rx], ubar like syn, misfit CUDA float64 [1])."""
+    import torch
+    s, o = syn.contiguous(), obs.contiguous()
+    assert s.dtype == o.dtype and s.shape == o.shape and s.dim() == 3 and s.shape[2] == 3
+    assert s.dtype in (torch.complex64, torch.complex128)
+    prec = PREC_FP32 if s.dtype == torch.complex64 else PREC_FP64
+    n_t, n_rx = int(s.shape[0]), int(s.shape[1])
+    tau = torch.empty(n_rx, dtype=torch.float64, device=s.device)
+    ubar = torch.empty_like(s)
+    misfit = torch.empty(1, dtype=torch.float64, device=s.device)
+    _check(lib().fga_traveltime_adjoint(_dptr(s), _dptr(o), prec, n_t, n_rx, float(dt), int(max_lag), _dptr(tau),
+                                        _dptr(ubar), _dptr(misfit), _stream(stream)))
+    return tau, ubar, misfit
+
+
 class Server:
     """Serving loop (fga_server_*): forward solves of independent requests on one resident model.
     submit() returns a request id; wait(id) blocks until it is done and returns its timing record
@@ -479,8 +498,8 @@ def profile_read(reset: bool = True) -> dict:
     p = Profile()
     _check(lib().fga_profile_read(C.byref(p), int(bool(reset))))
     return {"launches": p.launches,
-            "count": {n: p.count[i] for i, n in enumerate(PROFILE_CATEGORIES[:11])},
-            "ms": {n: p.ms[i] for i, n in enumerate(PROFILE_CATEGORIES[:11])},
+            "count": {n: p.count[i] for i, n in enumerate(PROFILE_CATEGORIES)},
+            "ms": {n: p.ms[i] for i, n in enumerate(PROFILE_CATEGORIES)},
             "beam_steps": p.beam_steps, "pairs_in_window": p.pairs_in_window, "pairs_tested": p.pairs_tested}
 
 
