@@ -6,6 +6,8 @@ module only wires them into torch.autograd:
 * ``Seismograms.apply(fields_p, fields_s, spec)`` maps the node fields of the P and S grids
   ([n0, n1, n2, 10] float32 CUDA tensors: c, grad c, Hess c per node) to the seismograms
   [n_times, n_rx, 3] of one source; its backward calls the library's adjoint.
+* ``traveltime_misfit(u, d, dt, max_lag)`` is the cross-correlation traveltime misfit of the
+  seismograms, whose backward is the library's adjoint source (fga_traveltime_adjoint).
 * ``fields_from_nodes(c, h)`` builds the 10 fields of a node grid of speeds with second-order
   finite differences (plain differentiable torch ops), so a gradient with respect to the speeds
   themselves follows by the chain rule, e.g. for c_s = c_p / sqrt(3) tied to c_p.
@@ -93,6 +95,39 @@ def fields_from_nodes(c, h):
 def misfit(u, d):
     """L2 waveform misfit 1/2 sum |u - d|^2."""
     return 0.5 * (u - d).abs().pow(2).sum()
+
+
+def _traveltime():
+    import torch
+
+    class TraveltimeMisfit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u, d, dt, max_lag):
+            _, ubar, mis = fga.traveltime_adjoint(u.detach(), d.detach().to(u.dtype), dt, max_lag)
+            ctx.save_for_backward(ubar)
+            return mis[0]
+
+        @staticmethod
+        def backward(ctx, g):
+            (ubar,) = ctx.saved_tensors
+            # ubar is dL/dRe u + i dL/dIm u, the gradient torch keeps for a real loss of complex u
+            return ubar * g.to(ubar.real.dtype), None, None, None
+
+    return TraveltimeMisfit
+
+
+_TT = None
+
+
+def traveltime_misfit(u, d, dt: float, max_lag: int):
+    """Cross-correlation traveltime misfit 1/2 sum_r tau_r^2 of seismograms u against data d (CUDA complex
+    [n_times, n_rx, 3], samples dt apart, delays within max_lag samples), as a float64 scalar.  Its
+    backward is the synthetic-only adjoint source of fga_traveltime_adjoint, so
+    traveltime_misfit(seismograms(...), d, ...).backward() gives the traveltime-tomography gradient."""
+    global _TT
+    if _TT is None:
+        _TT = _traveltime()
+    return _TT.apply(u, d, float(dt), int(max_lag))
 
 
 def cs_from_cp(cp, ratio: float = 1.0 / math.sqrt(3.0)):

@@ -127,3 +127,20 @@ def test_parity_on_crosswell_seismograms(fga, prec):
     assert np.abs(tau - otau).max() <= 1e-12 * max(np.abs(otau).max(), dt)
     assert _rel(ub, oub) <= (1e-12 if prec == 1 else 2e-7)
     assert abs(float(mis.cpu()[0]) - omis) <= 1e-12 * max(omis, 1e-30)
+
+
+def test_autograd_traveltime_misfit(fga):
+    """adjoint.traveltime_misfit: value = the oracle's misfit; u.grad = the oracle's adjoint source (torch keeps
+    dL/dRe u + i dL/dIm u for a real loss); a scaled loss scales the gradient."""
+    import torch
+    from paper_1810_06760_gb300 import adjoint as A
+    dt = 0.004
+    s, d = _records(11, 200, 6, dt, 12)
+    for cdt, tol in ((torch.complex128, 1e-12), (torch.complex64, 2e-7)):
+        u = torch.as_tensor(s, device="cuda").to(cdt).requires_grad_(True)
+        dd = torch.as_tensor(d, device="cuda").to(cdt)
+        L = 3.0 * A.traveltime_misfit(u, dd, dt, 16)
+        L.backward()
+        _, oub, omis = T.traveltime_adjoint(u.detach().cpu().numpy(), dd.cpu().numpy(), dt, 16)
+        assert abs(float(L.detach()) - 3.0 * omis) <= 1e-12 * 3.0 * omis
+        assert _rel(u.grad.cpu().numpy(), 3.0 * oub) <= tol
