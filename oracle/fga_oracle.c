@@ -19,9 +19,10 @@
  *   - Gaussian summation, untruncated and truncated            (Eq. FGA)
  *   - cell binning of beam centres                             (no counterpart in the paper: the
  *                                                               fast summation it cites is not printed)
- *   - flat-interface Snell / Zoeppritz / F-W jump              (Sec. 3.1, Eqs. p:int, Yilmaz, Inter_DzQDzP)
+ *   - flat-interface events: Snell's law, the printed Zoeppritz (Sec. 3.1, Eqs. p:int, Yilmaz, Inter_DzQDzP)
+ *     system in angle variables, the F-W jump of dzQ and dzP
  *
- * Readings of points the paper leaves open (each listed in the design doc):
+ * Readings of points the paper leaves open:
  *   alpha uses |p| (not |p|^3) and c(q); S beams carry psi folded into (a_sv, a_sh);
  *   no phase S (it is identically zero for H = +-c|P|); the SV/SH frame is
  *   N_sh = e_ref x P / |e_ref x P|, N_sv = N_sh x P/|P| with e_ref = e3, or e1 for
@@ -650,218 +651,217 @@ void orc_bin_sort(int nb, const int32_t *key, int ncells, int32_t *perm, int32_t
 /* ------------------------------------------------------------------------- */
 /* flat interfaces (Sec. 3.1)                                                 */
 /* ------------------------------------------------------------------------- */
-/* A beam crossing the plane x3 = zif between layer A (incident side) and layer B scatters into up to
- * four beams: reflected P and S (back into A), transmitted P and S (into B).  All share the
- * horizontal part of P (tangential continuity); each has c_w |P_w| = c_in |P_in| (the frequency is
- * conserved, so H = c|P| is continuous); reflected beams flip the sign of P_3, transmitted ones keep
- * it (Eq. p:int).  The amplitudes solve the plane-wave continuity conditions of a welded interface:
- * displacement u = a N and traction sigma.e3 continuous, with sigma_i3 = lambda delta_i3 (P.N)
- * + mu (P_i N_3 + P_3 N_i) per unit (i k a) -- the system Eq. Yilmaz writes in angles for a P
- * incidence, here for any incidence and both S polarisations at once (6 x 6, complex so that a
- * post-critical wave keeps its decaying P_3 and the others stay correct).  dzQ, dzP jump by
- * Eq. Inter_DzQDzP: dzQ' = dzQ F, dzP' = dzP W, W = F^{-T} (grad c = 0 on both sides of a flat
- * interface between homogeneous layers). */
+/* A beam crossing the plane x3 = zif from layer 1 (the incident side) into layer 2 scatters into up
+ * to four beams: reflected P and S (back into layer 1) and transmitted P and S (into layer 2).
+ *
+ * Snell's law, Eq. p:int: every child keeps the horizontal part of P and the frequency c|P| of the
+ * incident beam, and its vertical component is p_z' = +-sqrt((p_z n)^2 + (n^2 - 1)(p_x^2 + p_y^2))
+ * with n = c_in / c_child (n_1, n_2, n_3 of the paper for a P incidence); reflected children flip the
+ * sign of p_z, transmitted ones keep it.
+ *
+ * Amplitudes: the Zoeppritz system as printed, Eq. Yilmaz.  It is written in the plane of incidence
+ * of a P wave, with the P angles theta and the S angles phi measured from the interface normal, for
+ * potential amplitudes (a wave of speed c and potential amplitude X has displacement amplitude
+ * proportional to X / c; every matrix entry carries that scaling).  Readings:
+ *   - the last entry of the printed right-hand side, cos(2 theta_r), is garbled: the shear-traction
+ *     row of the same matrix needs sin(2 theta_r), and only sin gives no converted S wave at normal
+ *     incidence;
+ *   - SV incidence (the paper: "handled similarly"): the same matrix, whose columns are the four
+ *     outgoing waves, with the incident S wave's column as right-hand side,
+ *     (-(a1/b1) sin phi, (a1/b1) cos phi, -sin 2phi, (a1/b1)^2 cos 2phi), phi its angle;
+ *   - SH incidence (no P-S interaction, as the paper notes): the textbook coefficients of a welded
+ *     interface for displacement, R = (r1 b1 cos phi1 - r2 b2 cos phi2) / D, T = 2 r1 b1 cos phi1 / D,
+ *     D = r1 b1 cos phi1 + r2 b2 cos phi2;
+ *   - a beam in 3-D: the plane of incidence is spanned by the horizontal direction h of the beam's
+ *     direction of travel V = sigma P (sigma = -1 on the "-" branch, whose beams move along -P) and by
+ *     the normal nrm = sign(V_3) e3 pointing into layer 2.  A wave travelling along d = d_h h + d_n nrm
+ *     is polarised along d (P), along d_n h - d_h nrm (SV, the sign convention of the printed
+ *     matrix) or along s = nrm x h (SH);
+ *   - beyond a critical angle the cosine of that wave's angle is i sigma sqrt(sin^2 - 1), so that it
+ *     decays away from the interface; it takes part in the system but is not created as a beam.
+ *
+ * dzQ and dzP jump by Eq. Inter_DzQDzP: dzQ' = dzQ F, dzP' = dzP W with W = F^{-T}; its grad c term
+ * vanishes between homogeneous layers. */
 
-/* 6x6 complex solve by Gaussian elimination with partial pivoting; returns 0 if singular */
-static int csolve6(cplx A[6][6], cplx b[6], cplx x[6])
+/* 4x4 complex solve by Gaussian elimination with partial pivoting; returns 0 if singular */
+static int solve4(cplx A[4][4], cplx b[4], cplx x[4])
 {
-    for (int c = 0; c < 6; c++) {
+    for (int c = 0; c < 4; c++) {
         int piv = c;
-        for (int r = c + 1; r < 6; r++)
+        for (int r = c + 1; r < 4; r++)
             if (cabs(A[r][c]) > cabs(A[piv][c])) piv = r;
         if (cabs(A[piv][c]) < 1e-300) return 0;
-        if (piv != c) {
-            for (int j = 0; j < 6; j++) {
-                cplx t = A[c][j];
-                A[c][j] = A[piv][j];
-                A[piv][j] = t;
-            }
-            cplx t = b[c];
-            b[c] = b[piv];
-            b[piv] = t;
+        for (int j = 0; j < 4; j++) {
+            cplx t = A[c][j];
+            A[c][j] = A[piv][j];
+            A[piv][j] = t;
         }
-        for (int r = c + 1; r < 6; r++) {
+        cplx t = b[c];
+        b[c] = b[piv];
+        b[piv] = t;
+        for (int r = c + 1; r < 4; r++) {
             cplx f = A[r][c] / A[c][c];
-            for (int j = c; j < 6; j++) A[r][j] -= f * A[c][j];
+            for (int j = c; j < 4; j++) A[r][j] -= f * A[c][j];
             b[r] -= f * b[c];
         }
     }
-    for (int r = 5; r >= 0; r--) {
+    for (int r = 3; r >= 0; r--) {
         cplx s = b[r];
-        for (int j = r + 1; j < 6; j++) s -= A[r][j] * x[j];
+        for (int j = r + 1; j < 4; j++) s -= A[r][j] * x[j];
         x[r] = s / A[r][r];
     }
     return 1;
 }
 
-/* Polarisation vectors of a wave with (possibly complex) propagation vector P of real length pn:
- * P: P/pn;  SH: nsh (shared by every wave of the event);  SV: nsh x P/pn. */
-static void wave_pol(const cplx P[3], double pn, const double nsh[3], int which, cplx N[3])
-{
-    if (which == 0) {
-        for (int d = 0; d < 3; d++) N[d] = P[d] / pn;
-    } else if (which == 2) {
-        for (int d = 0; d < 3; d++) N[d] = nsh[d];
-    } else {
-        N[0] = (nsh[1] * P[2] - nsh[2] * P[1]) / pn;
-        N[1] = (nsh[2] * P[0] - nsh[0] * P[2]) / pn;
-        N[2] = (nsh[0] * P[1] - nsh[1] * P[0]) / pn;
-    }
-}
-
-/* traction sigma . e3 of a plane wave a N exp(i k P.x), per unit i k a */
-static void traction(double lam, double mu, const cplx P[3], const cplx N[3], cplx T[3])
-{
-    cplx pn = P[0] * N[0] + P[1] * N[1] + P[2] * N[2];
-    for (int i = 0; i < 3; i++) T[i] = mu * (P[i] * N[2] + P[2] * N[i]);
-    T[2] += lam * pn;
-}
-
 /* Children of beam y (meta mt, in layer la) that reached the interface to layer lb; at most 4,
  * written in the order reflected P, reflected S, transmitted P, transmitted S (propagating ones
- * whose amplitude is at least rel_min of the incident one).  Returns the count. */
+ * whose displacement amplitude is at least rel_min of the incident one).  Returns the count. */
 int orc_interface_event(const orc_model *m, int mt, const double *y_, int lb, double rel_min, double *out_, int *meta_out)
 {
     const orc_state *y = (const orc_state *)y_;
     orc_state *out = (orc_state *)out_;
-    const int la = META_LAYER(mt), cls = META_CLS(mt), wave = cls >= 2;
-    const double sgn = (cls & 1) ? -1.0 : 1.0;
-    const double cin = wave ? m->lcs[la] : m->lcp[la];
-    const double pin = norm3(y->P), om = cin * pin; /* c |P| is conserved */
-    const double ph2 = y->P[0] * y->P[0] + y->P[1] * y->P[1];
-    double nsh[3];
-    if (ph2 > 0.0) {
-        double phn = sqrt(ph2);
-        nsh[0] = -y->P[1] / phn;
-        nsh[1] = y->P[0] / phn;
-        nsh[2] = 0.0;
-    } else {
-        nsh[0] = 0.0;
-        nsh[1] = 1.0;
-        nsh[2] = 0.0;
-    }
+    const int la = META_LAYER(mt), cls = META_CLS(mt), swave = cls >= 2;
+    const double sigma = (cls & 1) ? -1.0 : 1.0;
+    /* layer 1 is the incident side (the paper's "^" side for its downgoing P wave), layer 2 the other */
+    const double a1 = m->lcp[la], b1 = m->lcs[la], r1 = m->lrho[la];
+    const double a2 = m->lcp[lb], b2 = m->lcs[lb], r2 = m->lrho[lb];
+    const double cin = swave ? b1 : a1;
+    const double px = y->P[0], py = y->P[1], pz = y->P[2];
+    const double pin = norm3(y->P), om = cin * pin, ph = sqrt(px * px + py * py);
+
     /* incident displacement vector */
-    cplx Uin[3];
-    {
-        double Ph[3] = {y->P[0] / pin, y->P[1] / pin, y->P[2] / pin};
-        if (!wave) {
-            for (int d = 0; d < 3; d++) Uin[d] = y->a[0] * Ph[d];
-        } else if (mt & META_VECTOR) {
-            for (int d = 0; d < 3; d++) Uin[d] = y->a[d];
-        } else {
-            double Nsv[3], Nsh[3];
-            s_frame(y->P, (mt & META_REF_E1) != 0, Nsv, Nsh, NULL);
-            for (int d = 0; d < 3; d++) Uin[d] = y->a[0] * Nsv[d] + y->a[1] * Nsh[d];
-        }
+    cplx U[3];
+    if (!swave) {
+        for (int d = 0; d < 3; d++) U[d] = y->a[0] * (y->P[d] / pin);
+    } else if (mt & META_VECTOR) {
+        for (int d = 0; d < 3; d++) U[d] = y->a[d];
+    } else {
+        double Nsv[3], Nsh[3];
+        s_frame(y->P, (mt & META_REF_E1) != 0, Nsv, Nsh, NULL);
+        for (int d = 0; d < 3; d++) U[d] = y->a[0] * Nsv[d] + y->a[1] * Nsh[d];
     }
-    const double lamA = m->lrho[la] * (m->lcp[la] * m->lcp[la] - 2.0 * m->lcs[la] * m->lcs[la]);
-    const double muA = m->lrho[la] * m->lcs[la] * m->lcs[la];
-    const double lamB = m->lrho[lb] * (m->lcp[lb] * m->lcp[lb] - 2.0 * m->lcs[lb] * m->lcs[lb]);
-    const double muB = m->lrho[lb] * m->lcs[lb] * m->lcs[lb];
-    cplx Tin[3];
-    {
-        cplx Pc[3] = {y->P[0], y->P[1], y->P[2]};
-        traction(wave ? lamA : lamA, muA, Pc, Uin, Tin);
+
+    /* plane of incidence of the direction of travel */
+    double h[3] = {1.0, 0.0, 0.0}, nrm[3] = {0.0, 0.0, sigma * pz >= 0.0 ? 1.0 : -1.0}, s[3];
+    if (ph > 0.0) {
+        h[0] = sigma * px / ph;
+        h[1] = sigma * py / ph;
     }
-    /* the four outgoing waves: 0 rP, 1 rS, 2 tP, 3 tS */
-    const double sz = y->P[2] >= 0.0 ? 1.0 : -1.0;
-    cplx Pw[4][3];
-    double pnw[4], cw[4];
+    cross3(nrm, h, s);
+
+    /* the outgoing waves w = 0 rP, 1 rS, 2 tP, 3 tS: Snell's law and the angles from the normal */
+    const double cw[4] = {a1, b1, a2, b2};
+    double pzw[4], sn[4];
+    cplx cs[4];
     int prop[4];
     for (int w = 0; w < 4; w++) {
-        int trans = w >= 2, s_wave = w & 1;
-        int L = trans ? lb : la;
-        cw[w] = s_wave ? m->lcs[L] : m->lcp[L];
-        pnw[w] = om / cw[w];
-        double pz2 = pnw[w] * pnw[w] - ph2;
-        double side = trans ? sz : -sz;
-        Pw[w][0] = y->P[0];
-        Pw[w][1] = y->P[1];
-        if (pz2 >= 0.0) {
-            Pw[w][2] = side * sqrt(pz2);
-            prop[w] = 1;
-        } else {
-            Pw[w][2] = I * sgn * side * sqrt(-pz2); /* decays away from the interface */
-            prop[w] = 0;
-        }
+        const double n = cin / cw[w];
+        const double q = (pz * n) * (pz * n) + (n * n - 1.0) * ph * ph;
+        const double side = w >= 2 ? (pz >= 0.0 ? 1.0 : -1.0) : (pz >= 0.0 ? -1.0 : 1.0);
+        prop[w] = q >= 0.0;
+        pzw[w] = prop[w] ? side * sqrt(q) : 0.0;
+        sn[w] = ph * cw[w] / om;
+        const double c2 = 1.0 - sn[w] * sn[w];
+        cs[w] = c2 >= 0.0 ? (cplx)sqrt(c2) : I * sigma * sqrt(-c2);
     }
-    /* unknowns: a_rP, a_rSV, a_rSH, a_tP, a_tSV, a_tSH */
-    cplx A[6][6], b[6], x[6];
-    const int wv[6] = {0, 1, 1, 2, 3, 3}, pol[6] = {0, 1, 2, 0, 1, 2};
-    for (int u = 0; u < 6; u++) {
-        const int w = wv[u], trans = w >= 2;
-        cplx N[3], T[3];
-        wave_pol(Pw[w], pnw[w], nsh, pol[u], N);
-        traction(trans ? lamB : lamA, trans ? muB : muA, Pw[w], N, T);
-        double sg = trans ? -1.0 : 1.0;
+    /* theta_r, phi_r, theta_t, phi_t of the printed matrix */
+    const double sth_r = sn[0], sph_r = sn[1], sth_t = sn[2], sph_t = sn[3];
+    const cplx cth_r = cs[0], cph_r = cs[1], cth_t = cs[2], cph_t = cs[3];
+    const cplx s2th_r = 2.0 * sth_r * cth_r, s2ph_r = 2.0 * sph_r * cph_r;
+    const cplx s2th_t = 2.0 * sth_t * cth_t, s2ph_t = 2.0 * sph_t * cph_t;
+    const double c2ph_r = 1.0 - 2.0 * sph_r * sph_r, c2ph_t = 1.0 - 2.0 * sph_t * sph_t;
+    cplx M[4][4] = {
+        {cth_r, a1 / b1 * sph_r, a1 / a2 * cth_t, -a1 / b2 * sph_t},
+        {-sth_r, a1 / b1 * cph_r, a1 / a2 * sth_t, a1 / b2 * cph_t},
+        {-c2ph_r, -s2ph_r, r2 / r1 * c2ph_t, -r2 / r1 * s2ph_t},
+        {s2th_r, -(a1 / b1) * (a1 / b1) * c2ph_r, r2 * a1 * a1 * b2 * b2 / (r1 * a2 * a2 * b1 * b1) * s2th_t,
+         r2 * a1 * a1 / (r1 * b1 * b1) * c2ph_t}};
+    /* incident amplitude along its own polarisation in the plane of incidence */
+    const double din_h = ph / pin, din_n = fabs(pz) / pin;       /* V/|V| = din_h h + din_n nrm */
+    cplx rhs[4], X[4];
+    cplx Csh = 0.0;
+    if (!swave) {
+        cplx A = 0.0;
+        for (int d = 0; d < 3; d++) A += U[d] * (din_h * h[d] + din_n * nrm[d]);
+        rhs[0] = cth_r * A;
+        rhs[1] = sth_r * A;
+        rhs[2] = c2ph_r * A;
+        rhs[3] = s2th_r * A;
+    } else {
+        cplx B = 0.0;
         for (int d = 0; d < 3; d++) {
-            A[d][u] = sg * N[d];
-            A[3 + d][u] = sg * T[d];
+            B += U[d] * (din_n * h[d] - din_h * nrm[d]);
+            Csh += U[d] * s[d];
         }
+        rhs[0] = -a1 / b1 * sph_r * B;
+        rhs[1] = a1 / b1 * cph_r * B;
+        rhs[2] = -s2ph_r * B;
+        rhs[3] = (a1 / b1) * (a1 / b1) * c2ph_r * B;
     }
-    for (int d = 0; d < 3; d++) {
-        b[d] = -Uin[d];
-        b[3 + d] = -Tin[d];
-    }
-    if (!csolve6(A, b, x)) return 0;
-    double ain = sqrt(creal(Uin[0] * conj(Uin[0]) + Uin[1] * conj(Uin[1]) + Uin[2] * conj(Uin[2])));
+    if (!solve4(M, rhs, X)) return 0;
+    /* SH: reflected and transmitted displacement factors (zero for a P incidence) */
+    const cplx Dsh = r1 * b1 * cph_r + r2 * b2 * cph_t;
+    const cplx Rsh = (r1 * b1 * cph_r - r2 * b2 * cph_t) / Dsh, Tsh = 2.0 * r1 * b1 * cph_r / Dsh;
+
+    double ain = 0.0;
+    for (int d = 0; d < 3; d++) ain += creal(U[d] * conj(U[d]));
+    ain = sqrt(ain);
     int nout = 0;
     for (int w = 0; w < 4; w++) {
         if (!prop[w]) continue;
-        int s_wave = w & 1, trans = w >= 2;
-        cplx a0 = s_wave ? x[w == 1 ? 1 : 4] : x[w == 0 ? 0 : 3];
-        cplx a1 = s_wave ? x[w == 1 ? 2 : 5] : 0.0;
-        double amag = sqrt(creal(a0 * conj(a0) + a1 * conj(a1)));
+        const int s_wave = w & 1, trans = w >= 2;
+        /* direction of travel of the child in the plane of incidence, and its displacement vector */
+        const double dh = sn[w], dn = trans ? creal(cs[w]) : -creal(cs[w]);
+        const double amp = cin / cw[w];                /* potential -> displacement amplitude */
+        cplx Uc[3];
+        for (int d = 0; d < 3; d++) {
+            if (!s_wave) {
+                Uc[d] = amp * X[w] * (dh * h[d] + dn * nrm[d]);
+            } else {
+                Uc[d] = amp * X[w] * (dn * h[d] - dh * nrm[d]);
+                if (swave) Uc[d] += (trans ? Tsh : Rsh) * Csh * s[d];
+            }
+        }
+        double amag = 0.0;
+        for (int d = 0; d < 3; d++) amag += creal(Uc[d] * conj(Uc[d]));
+        amag = sqrt(amag);
         if (!(amag >= rel_min * ain) || amag == 0.0) continue;
         orc_state *c = out + nout;
         *c = *y;
-        double Pr[3] = {creal(Pw[w][0]), creal(Pw[w][1]), creal(Pw[w][2])};
+        const double Pr[3] = {px, py, pzw[w]};
         for (int d = 0; d < 3; d++) c->P[d] = Pr[d];
-        /* dzQ' = dzQ F, dzP' = dzP F^{-T}; F = I except its last row
-         * ((kappa-1) p_x/p_z, (kappa-1) p_y/p_z, kappa p_z'/p_z), kappa = (c_out/c_in)^2 */
-        double kap = (cw[w] / cin) * (cw[w] / cin);
-        double Fm[3][3] = {{1, 0, 0}, {0, 1, 0},
-                           {(kap - 1.0) * y->P[0] / y->P[2], (kap - 1.0) * y->P[1] / y->P[2], kap * Pr[2] / y->P[2]}};
-        /* F^{-T}: inverse of the transpose of a matrix that differs from I in its last row */
-        double Wm[3][3];
-        {
-            double f20 = Fm[2][0], f21 = Fm[2][1], f22 = Fm[2][2];
-            /* F^{-1} = [[1,0,0],[0,1,0],[-f20/f22, -f21/f22, 1/f22]]; W = (F^{-1})^T */
-            double Fi[3][3] = {{1, 0, 0}, {0, 1, 0}, {-f20 / f22, -f21 / f22, 1.0 / f22}};
-            for (int r = 0; r < 3; r++)
-                for (int q = 0; q < 3; q++) Wm[r][q] = Fi[q][r];
-        }
+        /* F = I except its last row ((kappa-1) p_x/p_z, (kappa-1) p_y/p_z, kappa p_z'/p_z),
+         * kappa = (c_child/c_in)^2; W = F^{-T} */
+        const double kap = (cw[w] / cin) * (cw[w] / cin);
+        const double Fm[3][3] = {{1, 0, 0}, {0, 1, 0}, {(kap - 1.0) * px / pz, (kap - 1.0) * py / pz, kap * Pr[2] / pz}};
+        const double Fi[3][3] = {{1, 0, 0}, {0, 1, 0}, {-Fm[2][0] / Fm[2][2], -Fm[2][1] / Fm[2][2], 1.0 / Fm[2][2]}};
         for (int mm = 0; mm < 3; mm++)
             for (int j = 0; j < 3; j++) {
                 cplx sq = 0, sp = 0;
                 for (int l = 0; l < 3; l++) {
                     sq += y->DQ[3 * mm + l] * Fm[l][j];
-                    sp += y->DP[3 * mm + l] * Wm[l][j];
+                    sp += y->DP[3 * mm + l] * Fi[j][l];   /* (F^{-1})^T */
                 }
                 c->DQ[3 * mm + j] = sq;
                 c->DP[3 * mm + j] = sp;
             }
-        int cc = (s_wave ? 2 : 0) | (cls & 1);
+        const int cc = (s_wave ? 2 : 0) | (cls & 1);
         int mt_c = cc | ((trans ? lb : la) << 4) | ((META_GEN(mt) + 1) << 8) | (mt & (3 << 13));
         c->a[0] = c->a[1] = c->a[2] = 0;
+        const double pn = norm3(Pr);
         if (!s_wave) {
-            c->a[0] = a0;
+            for (int d = 0; d < 3; d++) c->a[0] += Uc[d] * (Pr[d] / pn);
+        } else if (mt & META_VECTOR) {
+            mt_c |= META_VECTOR;
+            for (int d = 0; d < 3; d++) c->a[d] = Uc[d];
         } else {
-            /* SV along nsh x P/|P|, SH along nsh (the e3 frame); re-expressed in the child's own frame */
-            cplx Nsv[3], Ag[3];
-            cplx Pc[3] = {Pr[0], Pr[1], Pr[2]};
-            wave_pol(Pc, pnw[w], nsh, 1, Nsv);
-            for (int d = 0; d < 3; d++) Ag[d] = a0 * Nsv[d] + a1 * nsh[d];
-            if (mt & META_VECTOR) {
-                mt_c |= META_VECTOR;
-                for (int d = 0; d < 3; d++) c->a[d] = Ag[d];
-            } else {
-                int r = orc_s_ref_e1(Pr);
-                if (r) mt_c |= META_REF_E1;
-                double fsv[3], fsh[3];
-                s_frame(Pr, r, fsv, fsh, NULL);
-                c->a[0] = Ag[0] * fsv[0] + Ag[1] * fsv[1] + Ag[2] * fsv[2];
-                c->a[1] = Ag[0] * fsh[0] + Ag[1] * fsh[1] + Ag[2] * fsh[2];
+            const int r = orc_s_ref_e1(Pr);
+            if (r) mt_c |= META_REF_E1;
+            double fsv[3], fsh[3];
+            s_frame(Pr, r, fsv, fsh, NULL);
+            for (int d = 0; d < 3; d++) {
+                c->a[0] += Uc[d] * fsv[d];
+                c->a[1] += Uc[d] * fsh[d];
             }
         }
         meta_out[nout] = mt_c;

@@ -178,3 +178,83 @@ def test_lineage_keys_unique_after_splitting(oracle):
     keys = list(zip(oracle.meta_root(meta).tolist(), mid.tolist(), path.tolist()))
     assert len(keys) > st.shape[0] // 2 and len(set(keys)) == len(keys)
     assert np.any(path > 0)
+
+
+def _displacement(O, st, mt):
+    """Displacement vector a N of a beam: P along P/|P|, S from its own SV/SH frame (Sec. 2.2 frame:
+    N_sh = e x P/|e x P|, N_sv = N_sh x P/|P|, e = e1 for beams flagged so, else e3)."""
+    P = st[3:6]
+    ph = P / np.linalg.norm(P)
+    a = st[42:48].view(complex)
+    if (mt & 3) < 2:
+        return a[0] * ph
+    e = np.array([1.0, 0, 0]) if mt & O.META_REF_E1 else np.array([0, 0, 1.0])
+    nsh = np.cross(e, P)
+    nsh /= np.linalg.norm(nsh)
+    return a[0] * np.cross(nsh, ph) + a[1] * nsh
+
+
+def _traction(lam, mu, P, U):
+    """sigma . e3 of the plane wave U exp(i k P.x), per unit i k: lam (P.U) e3 + mu (P U_3 + P_3 U)."""
+    t = mu * (P * U[2] + P[2] * U)
+    t[2] += lam * np.dot(P, U)
+    return t
+
+
+@pytest.mark.parametrize("cls,p,down", [
+    (0, [0.3, 0.2, 0.9], True), (0, [-0.25, 0.3, -0.8], False),     # P from the slow and the fast side
+    (1, [0.2, -0.3, -0.9], True),                                     # "-" branch: travels along -P
+    (2, [0.3, 0.2, 0.9], True), (3, [0.1, -0.3, 0.9], False),        # S with SV and SH parts
+    (2, [0.02, 0.01, 0.95], True),                                    # near-vertical S (frame about e1)
+])
+def test_children_satisfy_welded_continuity(oracle, cls, p, down):
+    """Below every critical angle all four children propagate, and the printed Zoeppritz system
+    (with the readings of its garbled entry, of SV incidence and of SH incidence) must give children
+    whose displacement and traction sigma.e3 are continuous across the interface: the conditions of a
+    welded interface that Eq. Yilmaz expresses in angle variables, checked here on the 3-D
+    displacement vectors the children carry."""
+    O = oracle
+    cp, cs, rho = [2.0, 2.6], [1.1, 1.5], [1.3, 1.9]
+    model = _layered(O, cp, cs, rho, [0.5])
+    lay = 0 if down else 1
+    st, mt = _beam(O, model, cls, [0.3, 0.4, 0.45 if down else 0.55], p)
+    assert O.meta_layer(mt) == lay
+    kids, km = O.interface_event(model, mt, st, 1 - lay, rel_min=0.0)
+    expect = 2 if (cls >= 2 and abs(st[42:46].view(complex)[0]) == 0) else 4
+    assert len(kids) == expect
+    lam = [r * (a * a - 2 * b * b) for r, a, b in zip(rho, cp, cs)]
+    mu = [r * b * b for r, b in zip(rho, cs)]
+    U_in = _displacement(O, st, mt)
+    du = U_in.copy()
+    dtr = _traction(lam[lay], mu[lay], st[3:6], U_in)
+    T_in = dtr.copy()
+    for k, m in zip(kids, km):
+        L = int(O.meta_layer(m))
+        sgn = 1.0 if L == lay else -1.0
+        U = _displacement(O, k, int(m))
+        du += sgn * U
+        dtr += sgn * _traction(lam[L], mu[L], k[3:6], U)
+    assert np.linalg.norm(du) <= 1e-12 * np.linalg.norm(U_in), du
+    assert np.linalg.norm(dtr) <= 1e-12 * np.linalg.norm(T_in), dtr
+
+
+def test_sh_incidence_textbook_coefficients(oracle):
+    """A pure SH beam (displacement horizontal, normal to the plane of incidence) yields only S
+    children, with R = (Z1 cos phi1 - Z2 cos phi2)/(Z1 cos phi1 + Z2 cos phi2) and
+    T = 2 Z1 cos phi1/(Z1 cos phi1 + Z2 cos phi2), Z = rho c_s (displacement amplitudes)."""
+    O = oracle
+    cp, cs, rho = [2.0, 2.6], [1.1, 1.5], [1.3, 1.9]
+    model = _layered(O, cp, cs, rho, [0.5])
+    p = np.array([0.35, 0.0, 0.8])
+    st, mt = _beam(O, model, 2, [0.3, 0.4, 0.45], p, amps=(0.0, 0.8 - 0.3j))
+    U_in = _displacement(O, st, mt)
+    assert abs(U_in[0]) < 1e-15 and abs(U_in[2]) < 1e-15       # along e2: SH for this plane
+    kids, km = O.interface_event(model, mt, st, 1, rel_min=1e-9)
+    assert len(kids) == 2 and all((m & 2) for m in km)
+    om = cs[0] * np.linalg.norm(p)
+    c1 = math.sqrt(1 - (p[0] * cs[0] / om) ** 2)
+    c2 = math.sqrt(1 - (p[0] * cs[1] / om) ** 2)
+    Z1, Z2 = rho[0] * cs[0] * c1, rho[1] * cs[1] * c2
+    got = {int(O.meta_layer(m)): _displacement(O, k, int(m)) for k, m in zip(kids, km)}
+    np.testing.assert_allclose(got[0], U_in * (Z1 - Z2) / (Z1 + Z2), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(got[1], U_in * 2 * Z1 / (Z1 + Z2), rtol=1e-12, atol=1e-15)
