@@ -32,7 +32,6 @@ FLOP_PER_PAIR_IN = 43.0       # dx, r^2, phase, exponent, e*(cos, sin), 3 comple
 FLOP_PER_PAIR_OUT = 9.0       # dx, r^2, compare
 MUFU_PER_PAIR_IN = 3.0        # exp2, sin, cos
 FLOP_PER_LATTICE_PAIR_IN = 26.0   # window test (add, compare) + 3 complex multiply-adds
-SMS = 152
 # DRAM bytes per launch of the tensor-core lattice sum on the full smooth workload, from ncu
 # (dram__bytes_read + write = 384 MB per launch at 6.33 M records per sample on the medium case,
 # 60.6 B per record), scaled to the full workload's ~18 M records per sample; see profiles/
@@ -59,6 +58,8 @@ def parse():
                     help="with --adjoint: L2 waveform misfit, or cross-correlation traveltime misfit "
                          "(delays within +-20 samples) with its synthetic-only adjoint source")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP32-vs-FP64 comparison on the 8^3-q version of the workload")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -299,7 +300,8 @@ def run_ours(args):
         cnts["gauss_sum_all"] = cnts["gauss_sum"] + cnts["gauss_sum_state"]
         top = "gauss_sum_all"
     sm_clock = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
-    fp32_peak = SMS * 128 * 2 * sm_clock
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * sm_clock
     if prec == fga.PREC_FP32 and top == "propagate":
         nP = sum(1 for c in w.classes if c < 2) * w.mesh.M
         nS = sum(1 for c in w.classes if c >= 2) * w.mesh.M
@@ -320,7 +322,7 @@ def run_ours(args):
         traffic = LATTICE_TC_TRAFFIC_BYTES if (top == "gauss_sum_all" and args.size == "full") else None
         roof = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "peak_basis": f"FP32 pipe: {SMS} SMs x 128 lanes x 2 x {sm_clock / 1e6:.0f} MHz "
+                "peak_basis": f"FP32 pipe: {sms} SMs (device property) x 128 lanes x 2 x {sm_clock / 1e6:.0f} MHz "
                               f"(max SM clock of {pk_kind} peaks file)",
                 "per_launch_ms": per_launch_ms, "launches": launches}
     gauss_s = gauss_ms_total / 1e3
@@ -375,6 +377,9 @@ def run_ours(args):
         line["e2e"] = {"value": world * args.steps * beam_steps / e2e_s, "unit": "beam-steps/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    if world == 1 and prec == fga.PREC_FP32 and not args.no_fp64:
+        line["fp64_comparison"] = fp64_comparison(args, dev)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         bs, secs, thr, desc_s = oracle_sample(w, 6, 2) if args.size != "small" else oracle_sample(w, 4, 2)
         line["cpu_baseline"] = {"value": bs / secs, "unit": "beam-steps/s", "cores": thr, "kind": "oracle",
@@ -384,6 +389,61 @@ def run_ours(args):
     if pg is not None:
         pg.destroy_process_group()
     return 0
+
+
+def fp64_comparison(args, dev):
+    """The FP32 split-precision path against the plain FP64 GPU path on the same inputs: the bench
+    workload with its q mesh coarsened to 8^3 nodes over the same region (1,048,576 beams; every other
+    size unchanged), one solve each, timed with CUDA events.  Reports both throughputs and the FP32
+    results' error against the FP64 ones (relative L2, and element-wise on entries above 1e-2 of the
+    peak)."""
+    import numpy as np
+    import torch
+
+    from paper_1810_06760_gb300 import fga
+    from paper_1810_06760_gb300 import workloads as W
+    if args.size == "full":
+        w = W.smooth(nq=8)
+    elif args.size == "medium":
+        w = W.smooth(nq=6, nsteps=100, n_samples=250)
+    else:
+        w = W.smooth(nq=4, np_=4, ny=48, nsteps=40, n_samples=100, rx_side=10, snap_side=16, grid_n=65)
+    model = fga.model_from_medium(w.medium, dev)
+    f = torch.as_tensor(w.f, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    res = {}
+    for name, prec, reps in (("fp32", fga.PREC_FP32, 2), ("fp64", fga.PREC_FP64, 1)):
+        desc = fga.init_desc(w.k, f, None, w.y0, w.dy, w.mesh, w.classes, prec)
+        for r in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            seis, snap = fga.solve(model, desc, w.dt, w.nsteps, w.times, rw=w.rw, rx_axes=w.rx_axes,
+                                   snap_axes=w.snap_axes)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[name] = (seis.cpu().numpy().astype(np.complex128), snap.cpu().numpy().astype(np.complex128))
+        out[name] = {"ms_per_solve": ms, "beam_steps_per_s": w.n_beams * w.nsteps / (ms / 1e3)}
+    model.close()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    def elem(a, b, frac=1e-2):
+        m = np.abs(b)
+        sel = m >= frac * m.max()
+        return float(np.max(np.abs(a[sel] - b[sel]) / m[sel]))
+    (s32, n32), (s64, n64) = res["fp32"], res["fp64"]
+    n_units = len(w.times) * len(w.receivers) + len(w.snapshot)
+    return {"workload": f"the same workload with a {w.mesh.nq}^3 q mesh ({w.n_beams} beams)",
+            "fp32": out["fp32"], "fp64": out["fp64"],
+            "fp32_speedup": out["fp64"]["ms_per_solve"] / out["fp32"]["ms_per_solve"],
+            "receiver_samples_per_solve": n_units,
+            "err_fp32_vs_fp64": {"seismograms_rel_l2": rel(s32, s64), "snapshot_rel_l2": rel(n32, n64),
+                                 "seismograms_max_rel_above_1e-2_of_peak": elem(s32, s64),
+                                 "snapshot_max_rel_above_1e-2_of_peak": elem(n32, n64)}}
 
 
 def run_serving(args):

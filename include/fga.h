@@ -41,7 +41,7 @@ typedef enum {
     FGA_ERR_OOM = 2,         /* a device allocation failed; nothing was launched */
     FGA_ERR_CUDA = 3,        /* a CUDA runtime call failed; the message has the CUDA error */
     FGA_ERR_TIMEOUT = 4,     /* a bounded wait ran out */
-    FGA_ERR_NUMERIC = 5,     /* non-finite beam state detected */
+    FGA_ERR_NUMERIC = 5,     /* non-finite values in the beam state or the results (fga_solve) */
     FGA_ERR_UNSUPPORTED = 6  /* valid request the library does not implement */
 } fga_status;
 
@@ -116,6 +116,19 @@ typedef struct {
  * Errors: INVALID_ARG (k <= 0, sizes, empty mask), OOM, CUDA. */
 fga_status fga_decompose(const fga_model *m, const fga_init_desc *init, fga_beams **out, fga_stream_t s);
 
+/* The wave-packet transform of Eq. psi alone (the first half of step 1):
+ *   F(q,p) = sum_y f(y) exp(-i k p.(y-q) - k|y-q|^2/2) dy0 dy1 dy2
+ * of init->f on init's (q,p) mesh, computed as fga_decompose computes it (three per-axis complex
+ * contractions; FP16-split tensor-core products with FP32 accumulation for FGA_PREC_FP32, FP64 for
+ * FGA_PREC_FP64).  init->g, class_mask and the layered options are ignored.
+ *  F_out: DEVICE complex [A][A][A][3] (A = nq np), complex64 for FP32 and complex128 for FP64, in the
+ *         per-axis pair layout: entry (a0, a1, a2) with a_d = iq_d np + jp_d holds F at
+ *         q_d = q0[d] + iq_d dq[d], p_d = p0[d] + jp_d dp[d].
+ * Uses library-owned temporaries (allocated and released inside the call); synchronises s.
+ * Errors: INVALID_ARG (k <= 0, sizes, spacings, NULL pointers), OOM, TIMEOUT (a tensor-core wait ran
+ * out), CUDA. */
+fga_status fga_transform(const fga_init_desc *init, void *F_out, fga_stream_t s);
+
 /* Step 2: advance every beam nsteps classical RK4 steps of size dt (dt may be negative).
  * Errors: INVALID_ARG (nsteps < 0, dt not finite), CUDA. */
 fga_status fga_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps, fga_stream_t s);
@@ -139,7 +152,9 @@ typedef struct {
 /* Step 3 on a lattice (snapshot grids, receiver arrays): the same sum as fga_reconstruct at the
  * lattice points, evaluated with the per-axis factorisation exp(i k P.(x-Q) - k|x-Q|^2/2) =
  * prod_d exp(i k P_d (x_d-Q_d) - k (x_d-Q_d)^2/2) of Eq. FGA's Gaussian.  u_out: DEVICE complex
- * [n0][n1][n2][3].  Errors: INVALID_ARG (empty axis, non-increasing axis), OOM, CUDA. */
+ * [n0][n1][n2][3].  Synchronises s (FP32 beams: to read the call's own error word of the tensor-core
+ * sum).  Errors: INVALID_ARG (empty axis, non-increasing axis), OOM, TIMEOUT (a bounded wait of the
+ * tensor-core sum ran out; u_out is then incomplete), CUDA. */
 fga_status fga_reconstruct_lattice(const fga_beams *b, const fga_lattice *lat, double rw, void *u_out,
                                    fga_stream_t s);
 
@@ -151,7 +166,9 @@ fga_status fga_reconstruct_lattice(const fga_beams *b, const fga_lattice *lat, d
  * every GPU that loads the library until the process exits).  It tests every beam against every
  * point (no binning), so it suits modest beam counts; n must be <= 4096 (larger n is rejected with
  * FGA_ERR_INVALID_ARG and a message).  The first call on each device looks up the scratch array's
- * address, so make that first call before any stream capture.  All calls share the scratch array:
+ * address; that lookup may load the library's module on the device and place the 12 MiB array (a
+ * one-time cost that can synchronise the device), so make the first call -- a call with n = 0 does
+ * only this set-up -- before any stream capture or stall-free section.  All calls share the scratch array:
  * calls that overlap on the GPU (e.g. on two streams) race; calls ordered on one stream do not.
  * Nothing in the scratch has to start at zero (each call overwrites what it reads).
  *  x: DEVICE float64 [n][3]; u_out: DEVICE complex [n][3] in the beams' precision. */
@@ -167,7 +184,10 @@ fga_status fga_reconstruct_noalloc(const fga_beams *b, const double *x, int64_t 
  *  snap:  DEVICE float64 [n_snap][3] summed at t = nsteps*dt into snap_out DEVICE complex
  *         [n_snap][3] (may be NULL if n_snap = 0).  Or snap_lattice (non-NULL): n_snap and snap
  *         ignored, snap_out [n0][n1][n2][3].
- *  rw <= 0 selects 6/sqrt(k).  Errors: INVALID_ARG, OOM, CUDA. */
+ *  rw <= 0 selects 6/sqrt(k).  Synchronous: returns after the stream has finished the solve.
+ *  Errors: INVALID_ARG, OOM, CUDA, NUMERIC (a non-finite value in the final beam state, the seismograms
+ *  or the snapshot; the outputs are then unreliable), TIMEOUT (a bounded wait of the tensor-core
+ *  Gaussian sum ran out; the outputs are incomplete). */
 typedef struct {
     double dt;
     int nsteps;

@@ -989,7 +989,7 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
             int jl = j;
             while (jl >= 0 && sstep[(size_t)jl] == n) jl--;
             ss.nsj = j - jl;
-            FGA_CHECK(ss.nsj <= 4, "fga_solve_vjp: more than 4 sample times inside one step");
+            FGA_CHECK(ss.nsj <= 4, "fga_solve_vjp: more than 4 sample times inside one step");   // checked on entry
             const int jfirst = jl + 1;
             for (int q = 0; q < ss.nsj; q++) {
                 const double th = sth[(size_t)(jfirst + q)];
@@ -1074,6 +1074,21 @@ extern "C" fga_status fga_solve_vjp(const fga_model *m, const fga_init_desc *ini
         int n = std::min((int)std::floor(u), sd->nsteps - 1);
         sstep[(size_t)j] = n;
         sth[(size_t)j] = u - n;
+    }
+    // limits of the reverse steps, checked before any work: at most 4 samples inside one step, and the
+    // receivers with that many samples' cotangents within the shared-memory stage of the record kernel
+    {
+        int most = 0;
+        for (size_t j0 = 0; j0 < sstep.size();) {
+            size_t j1 = j0;
+            while (j1 < sstep.size() && sstep[j1] == sstep[j0]) j1++;
+            most = std::max(most, (int)(j1 - j0));
+            j0 = j1;
+        }
+        FGA_CHECK(most <= 4, "fga_solve_vjp: more than 4 sample times inside one step");
+        const size_t rb = init->precision == FGA_PREC_FP64 ? 8 : 4;
+        FGA_CHECK(rb * (size_t)sd->n_rx * (3 + 6 * (size_t)most) <= (size_t)200 * 1024,
+                  "fga_solve_vjp: receivers x samples per step exceed the shared-memory stage");
     }
     fga_beams *b = nullptr, *bg = nullptr;
     FGA_TRY(decompose_impl(m, init, &b, s));

@@ -152,7 +152,7 @@ void HostBuf::release() {
 }
 void Workspace::release() {
     for (DevBuf *d : {&keys, &keys_alt, &vals, &vals_alt, &hist, &scan_blocks, &cell_start, &rec, &items, &tiles,
-                      &partial, &pts})
+                      &partial, &pts, &status})
         d->release();
     for (HostBuf *h : {&h_cell_start, &h_items, &h_tiles}) h->release();
 }
@@ -372,6 +372,10 @@ fga_status fga_decompose(const fga_model *m, const fga_init_desc *init, fga_beam
     return decompose_impl(m, init, out, (cudaStream_t)s);
 }
 
+fga_status fga_transform(const fga_init_desc *init, void *F_out, fga_stream_t s) {
+    return transform_impl(init, F_out, (cudaStream_t)s);
+}
+
 fga_status fga_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps, fga_stream_t s_) {
     cudaStream_t s = (cudaStream_t)s_;
     FGA_CHECK(m && b, "fga_propagate: NULL argument");
@@ -482,7 +486,9 @@ fga_status fga_reconstruct_lattice(const fga_beams *b, const fga_lattice *lat, d
     FGA_TRY(check_lattice(lat, "fga_reconstruct_lattice"));
     if (!(rw > 0)) rw = 6.0 / std::sqrt(b->k);
     FGA_TRY(sync_layered_count(const_cast<fga_beams *>(b), s));
-    return reconstruct_lattice_now(b, lat, rw, u_out, s);
+    FGA_TRY(status_reset(b->ws, s));
+    FGA_TRY(reconstruct_lattice_now(b, lat, rw, u_out, s));
+    return status_check(b->ws, s, "fga_reconstruct_lattice");
 }
 
 fga_status fga_reconstruct(const fga_beams *b, const double *x, int64_t n, double rw, void *u_out, fga_stream_t s_) {
@@ -507,6 +513,18 @@ fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_so
 }  // extern "C"
 
 namespace fga {
+// non-finite values in the final beam state, the seismograms or the snapshot of a solve (status word 1)
+static fga_status flag_solve_nonfinite(const fga_beams *b, const fga_solve_desc *sd, int64_t nrx, bool seis,
+                                       const void *seis_out, const void *snap_out, cudaStream_t s) {
+    Workspace &ws = b->ws;
+    FGA_TRY(flag_nonfinite_state(ws, b->state.p, b->cap, b->nb, NF, b->precision, s));
+    if (seis) FGA_TRY(flag_nonfinite(ws, seis_out, (int64_t)sd->n_times * nrx * 6, b->precision, s));
+    const fga_lattice *snL = sd->snap_lattice;
+    const int64_t nsnap = snL ? (int64_t)snL->n[0] * snL->n[1] * snL->n[2] : sd->n_snap;
+    if (nsnap > 0 && snap_out) FGA_TRY(flag_nonfinite(ws, snap_out, nsnap * 6, b->precision, s));
+    return FGA_OK;
+}
+
 fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, void *seis_out,
                       void *snap_out, cudaStream_t s, double rec_cap) {
     fga_stream_t s_ = (fga_stream_t)s;
@@ -545,6 +563,7 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
     const bool fp64 = b->precision == FGA_PREC_FP64;
     const size_t rb = fp64 ? 8 : 4;
     Workspace &ws = b->ws;
+    FGA_TRY(status_reset(ws, s));
     std::vector<double> rxh, snh;
     const bool seis = (rxL || sd->n_rx > 0) && sd->n_times > 0;
     const int64_t nrx = rxL ? (int64_t)rxL->n[0] * rxL->n[1] * rxL->n[2] : sd->n_rx;
@@ -610,8 +629,8 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
             FGA_TRY(reconstruct_lattice_now(b, snL, rw, snap_out, s));
         else if (sd->n_snap > 0)
             FGA_TRY(reconstruct_now(b, sd->snap, snh, sd->n_snap, rw, snap_out, s));
-        FGA_CUDA(cudaStreamSynchronize(s));
-        return FGA_OK;
+        FGA_TRY(flag_solve_nonfinite(b, sd, nrx, seis, seis_out, snap_out, s));
+        return status_check(ws, s, "fga_solve");   // synchronises s before the beam set is freed
     }
     // records of one window live in one buffer; cap its size
     size_t free_b = 0, total_b = 0;
@@ -684,13 +703,9 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
         FGA_TRY(reconstruct_lattice_now(b, snL, rw, snap_out, s));
     else if (sd->n_snap > 0)
         FGA_TRY(reconstruct_now(b, sd->snap, snh, sd->n_snap, rw, snap_out, s));
-    // the beam set is freed by the guard; its buffers must not be in use
-    FGA_CUDA(cudaStreamSynchronize(s));
-    if (read_tc_lattice_error(true)) {
-        set_error("fga_solve: a tensor-core wait of the Gaussian sum ran out");
-        return FGA_ERR_TIMEOUT;
-    }
-    return FGA_OK;
+    FGA_TRY(flag_solve_nonfinite(b, sd, nrx, seis, seis_out, snap_out, s));
+    // the beam set is freed by the guard; its buffers must not be in use (the check synchronises s)
+    return status_check(ws, s, "fga_solve");
 }
 }  // namespace fga
 

@@ -260,12 +260,14 @@ __global__ void beam_init_kernel(ModelDev Md, const C2<R> *__restrict__ F, const
     ids[b] = (int32_t)mi;
 }
 
+// F (and G from g, if both are given) = the transform of Eq. psi in the per-axis pair layout
+// [a0][a1][a2][3], a_d = iq_d * np + jp_d.  Synchronises s before its temporaries are released; reports
+// a tensor-core wait that ran out as FGA_ERR_TIMEOUT.
 template <typename R>
-static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fga_beams *b, cudaStream_t s) {
+static fga_status transform_typed(const fga_init_desc *d, const double2 *f, const double2 *g, C2<R> *F, C2<R> *G,
+                                  cudaStream_t s) {
     const int A = d->nq * d->np;
-    const int64_t nyy = (int64_t)d->ny[0] * d->ny[1] * d->ny[2];
-    (void)nyy;
-    ScopedDevBuf Kb, T1, T2, Fb, Gb;
+    ScopedDevBuf Kb, T1, T2, tsb;
     const size_t kbytes = sizeof(C2<R>) * (size_t)A * (d->ny[0] + d->ny[1] + d->ny[2]);
     FGA_TRY(Kb.ensure(kbytes));
     C2<R> *Kax[3];
@@ -281,9 +283,6 @@ static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fg
     FGA_CUDA(cudaGetLastError());
     FGA_TRY(T1.ensure(sizeof(C2<R>) * (size_t)d->ny[0] * d->ny[1] * A * 3));
     FGA_TRY(T2.ensure(sizeof(C2<R>) * (size_t)d->ny[0] * A * A * 3));
-    const size_t Fn = (size_t)A * A * A * 3;
-    FGA_TRY(Fb.ensure(sizeof(C2<R>) * Fn));
-    ScopedDevBuf tsb;
     FGA_TRY(tsb.ensure(64));
     TransformScratch ts;
     ts.amax = tsb.as<float>();
@@ -291,15 +290,34 @@ static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fg
     FGA_CUDA(cudaMemsetAsync(tsb.p, 0, 64, s));
     for (int a = 0; a < 3; a++)
         ts.S[a] = kernel_row_sum_max(d->nq, d->q0[a], d->dq[a], d->ny[a], d->y0[a], d->dy[a], d->k);
-    FGA_TRY(fbi_transform<R>(d, static_cast<const double2 *>(d->f), Kax, T1.as<C2<R>>(), T2.as<C2<R>>(),
-                             Fb.as<C2<R>>(), ts, s));
+    FGA_TRY(fbi_transform<R>(d, f, Kax, T1.as<C2<R>>(), T2.as<C2<R>>(), F, ts, s));
+    if (g && G) FGA_TRY(fbi_transform<R>(d, g, Kax, T1.as<C2<R>>(), T2.as<C2<R>>(), G, ts, s));
+    // the temporaries are released when this scope ends; make sure the stream is done with them
+    FGA_CUDA(cudaStreamSynchronize(s));
+    if (sizeof(R) == 4) {
+        int terr = 0;
+        FGA_CUDA(cudaMemcpy(&terr, ts.err, sizeof terr, cudaMemcpyDeviceToHost));
+        if (terr) {
+            set_error("wave-packet transform: a tensor-core wait ran out");
+            return FGA_ERR_TIMEOUT;
+        }
+    }
+    return FGA_OK;
+}
+
+template <typename R>
+static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fga_beams *b, cudaStream_t s) {
+    const int A = d->nq * d->np;
+    ScopedDevBuf Fb, Gb;
+    const size_t Fn = (size_t)A * A * A * 3;
+    FGA_TRY(Fb.ensure(sizeof(C2<R>) * Fn));
     const C2<R> *G = nullptr;
     if (d->g) {
         FGA_TRY(Gb.ensure(sizeof(C2<R>) * Fn));
-        FGA_TRY(fbi_transform<R>(d, static_cast<const double2 *>(d->g), Kax, T1.as<C2<R>>(), T2.as<C2<R>>(),
-                                 Gb.as<C2<R>>(), ts, s));
         G = Gb.as<C2<R>>();
     }
+    FGA_TRY(transform_typed<R>(d, static_cast<const double2 *>(d->f), static_cast<const double2 *>(d->g),
+                               Fb.as<C2<R>>(), Gb.as<C2<R>>(), s));
     const int64_t M = (int64_t)d->nq * d->nq * d->nq * d->np * d->np * d->np;
     const double3 q0 = {d->q0[0], d->q0[1], d->q0[2]}, dq = {d->dq[0], d->dq[1], d->dq[2]};
     const double3 p0 = {d->p0[0], d->p0[1], d->p0[2]}, dp = {d->dp[0], d->dp[1], d->dp[2]};
@@ -320,22 +338,8 @@ static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fg
 #undef FGA_INIT
     }
     FGA_CUDA(cudaGetLastError());
-    // the temporaries are released when this scope ends; make sure the stream is done with them
+    // F and G are released when this scope ends; make sure the stream is done with them
     FGA_CUDA(cudaStreamSynchronize(s));
-    if (sizeof(R) == 4) {
-        int terr = 0;
-        FGA_CUDA(cudaMemcpy(&terr, ts.err, sizeof terr, cudaMemcpyDeviceToHost));
-        if (terr) {
-            set_error("fga_decompose: a tensor-core wait of the transform ran out");
-            return FGA_ERR_TIMEOUT;
-        }
-    }
-    tsb.release();
-    Kb.release();
-    T1.release();
-    T2.release();
-    Fb.release();
-    Gb.release();
     return FGA_OK;
 }
 
@@ -402,6 +406,23 @@ fga_status decompose_impl(const fga_model *m, const fga_init_desc *d, fga_beams 
     b->last_stream = s;
     *out = b;
     return FGA_OK;
+}
+
+fga_status transform_impl(const fga_init_desc *d, void *F_out, cudaStream_t s) {
+    FGA_CHECK(d && F_out, "fga_transform: NULL argument");
+    FGA_CHECK(std::isfinite(d->k) && d->k > 0, "fga_transform: k must be > 0");
+    FGA_CHECK(d->f != nullptr, "fga_transform: f is NULL");
+    FGA_CHECK(d->nq >= 1 && d->np >= 1, "fga_transform: nq, np must be >= 1");
+    FGA_CHECK(d->ny[0] >= 1 && d->ny[1] >= 1 && d->ny[2] >= 1, "fga_transform: ny must be >= 1");
+    FGA_CHECK(d->precision == FGA_PREC_FP32 || d->precision == FGA_PREC_FP64, "fga_transform: bad precision");
+    for (int a = 0; a < 3; a++) FGA_CHECK(d->dy[a] > 0 && d->dq[a] > 0 && d->dp[a] > 0, "fga_transform: spacings must be > 0");
+    const int64_t A = (int64_t)d->nq * d->np;
+    FGA_CHECK(A * A * A * 3 < (int64_t)1 << 31, "fga_transform: more than 2^31 output values");
+    if (d->precision == FGA_PREC_FP64)
+        return transform_typed<double>(d, static_cast<const double2 *>(d->f), nullptr, static_cast<C2<double> *>(F_out),
+                                       nullptr, s);
+    return transform_typed<float>(d, static_cast<const double2 *>(d->f), nullptr, static_cast<C2<float> *>(F_out),
+                                  nullptr, s);
 }
 
 }  // namespace fga

@@ -139,6 +139,9 @@ size_t block_cache_bytes();
 // scratch used by binning and the Gaussian sum
 struct Workspace {
     DevBuf keys, keys_alt, vals, vals_alt, hist, scan_blocks, cell_start, rec, items, tiles, partial, pts;
+    // status words of one call: [0] a bounded wait of the tensor-core lattice sum ran out,
+    // [1] non-finite values in the beam state or the outputs
+    DevBuf status;
     HostBuf h_cell_start, h_items, h_tiles;
     void release();
 };
@@ -178,6 +181,7 @@ fga_status tc_cgemm(const TA *A, int64_t sAz, int64_t sAm, int64_t sAk, const fl
 fga_status tc_absmax(const double2 *x, int64_t n, float *out, cudaStream_t s);
 // decompose.cu
 fga_status decompose_impl(const fga_model *m, const fga_init_desc *d, fga_beams **out, cudaStream_t s);
+fga_status transform_impl(const fga_init_desc *d, void *F_out, cudaStream_t s);
 // propagate.cu
 struct SampleWindow {
     int n;                  // samples in this window

@@ -43,7 +43,16 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
                           cudaStream_t s, int cat);
 fga_status lattice_reduce_f32(const float *partial, const LatticePlan &plan, void *u, cudaStream_t s);
 int64_t read_tc_pair_counter(bool reset);
-int read_tc_lattice_error(bool reset);
+// per-beam-set status words (Workspace::status): zeroed by status_reset before a call's work, read by
+// status_check after it (synchronises s): a tensor-core wait that ran out gives FGA_ERR_TIMEOUT,
+// non-finite values FGA_ERR_NUMERIC
+fga_status status_reset(Workspace &ws, cudaStream_t s);
+fga_status status_check(Workspace &ws, cudaStream_t s, const char *who);
+// flag (status word 1) any non-finite value among n reals of type R (precision: FGA_PREC_*)
+fga_status flag_nonfinite(Workspace &ws, const void *data, int64_t n, int precision, cudaStream_t s);
+// the same for nf fields of nb beams stored with stride cap
+fga_status flag_nonfinite_state(Workspace &ws, const void *st, int64_t cap, int64_t nb, int nf, int precision,
+                                cudaStream_t s);
 fga_status run_lattice(Workspace &ws, const LatticePlan &plan, int precision, const void *rec, double k, double rw,
                        void *u, cudaStream_t s, int cat = P_GATHER);
 int64_t read_lattice_pair_counter(bool reset);

@@ -13,8 +13,11 @@
 // a brute-force gather: every point is tested against every beam (no cell binning, which would need
 // scratch proportional to the beam count).  The first call on a device looks up the array's device
 // address with cudaGetSymbolAddress (host code may not use the symbol itself: on the host it is only
-// a stand-in).  Every call overwrites all the partial sums it later reads, so nothing has to start at
-// zero; calls that overlap on the GPU (two streams at once) share the array and race.
+// a stand-in).  With CUDA's lazy module loading that lookup may also load this file's module on the
+// device and place the array there -- a one-time cost that can synchronise the device -- so a caller
+// that must never stall makes one warm-up call with n = 0 first, which does only this set-up.  Every
+// call overwrites all the partial sums it later reads, so nothing has to start at zero; calls that
+// overlap on the GPU (two streams at once) share the array and race.
 #include <cmath>
 #include <mutex>
 
@@ -167,14 +170,14 @@ extern "C" fga_status fga_reconstruct_noalloc(const fga_beams *b, const double *
         return FGA_ERR_UNSUPPORTED;
     }
     FGA_CHECK(n >= 0, "fga_reconstruct_noalloc: n < 0");
+    void *scratch = nullptr;
+    FGA_TRY(scratch_ptr(&scratch));   // n = 0: only this one-time set-up (a warm-up call)
     if (n == 0) return FGA_OK;
     FGA_CHECK(n <= NA_MAX_POINTS,
               "fga_reconstruct_noalloc: more than 4096 points in one call (its fixed scratch holds the partial sums "
               "of at most 4096 points); split the points or use fga_reconstruct");
     FGA_CHECK(x && u_out, "fga_reconstruct_noalloc: NULL points or output");
     if (!(rw > 0)) rw = 6.0 / std::sqrt(b->k);
-    void *scratch = nullptr;
-    FGA_TRY(scratch_ptr(&scratch));
     if (b->precision == FGA_PREC_FP64) return run_noalloc<double>(b, x, n, rw, u_out, scratch, s);
     return run_noalloc<float>(b, x, n, (float)rw, u_out, scratch, s);
 }

@@ -17,6 +17,7 @@
 #include <condition_variable>
 #include <cmath>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -146,7 +147,8 @@ fga_status fga_server_create(fga_server **out, const fga_model *m, const fga_ser
     FGA_CHECK(out && m && d, "fga_server_create: NULL argument");
     FGA_CHECK(d->n_workers >= 1 && d->n_workers <= 64, "fga_server_create: n_workers must be in 1..64");
     FGA_CHECK(m->dev.kind != FGA_MEDIUM_LAYERED, "fga_server_create: layered media are not served");
-    fga_server *sv = new fga_server();
+    std::unique_ptr<fga_server> owner(new fga_server());   // freed on every early return
+    fga_server *sv = owner.get();
     sv->model = m;
     sv->n_workers = d->n_workers;
     FGA_CUDA(cudaGetDevice(&sv->device));
@@ -160,13 +162,12 @@ fga_status fga_server_create(fga_server **out, const fga_model *m, const fga_ser
         const cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             for (cudaStream_t t : sv->streams) cudaStreamDestroy(t);
-            delete sv;
             return cuda_fail(e, "fga_server_create: cudaStreamCreateWithFlags");
         }
         sv->streams.push_back(s);
     }
     for (int w = 0; w < d->n_workers; w++) sv->workers.emplace_back([sv, w] { sv->worker_main(w); });
-    *out = sv;
+    *out = owner.release();
     return FGA_OK;
 }
 
@@ -175,7 +176,8 @@ fga_status fga_server_submit(fga_server *sv, const fga_init_desc *init, const fg
     FGA_CHECK(sv && init && sd && id, "fga_server_submit: NULL argument");
     FGA_CHECK(init->f && init->nq >= 1 && init->np >= 1, "fga_server_submit: bad init descriptor");
     FGA_CHECK(sd->n_times >= 0 && (sd->n_times == 0 || sd->times), "fga_server_submit: times missing");
-    auto *r = new Request();
+    std::unique_ptr<Request> owner(new Request());   // freed on every early return until it is queued
+    Request *r = owner.get();
     r->init = *init;
     r->sd = *sd;
     r->times.assign(sd->times, sd->times + sd->n_times);
@@ -212,6 +214,7 @@ fga_status fga_server_submit(fga_server *sv, const fga_init_desc *init, const fg
         r->t_submit = Clock::now();
         sv->all[r->id] = r;
         sv->queue.push_back(r);
+        owner.release();
         *id = r->id;
     }
     sv->cv_work.notify_all();

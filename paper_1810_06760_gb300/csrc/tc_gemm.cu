@@ -15,8 +15,8 @@
 //   all threads stage a K block of A' and B' (hi and lo) into shared memory in the canonical
 //   no-swizzle K-major layout (8x8 core matrices of 128 contiguous bytes), one elected thread issues
 //   the MMAs and commits them to an mbarrier; after the last block the four warps read their 32 TMEM
-//   lanes (rows) and write C.  Every wait is bounded: a wait that runs out sets *err and the CTA skips
-//   to freeing its tensor memory.
+//   lanes (rows) and write C.  Every wait is bounded: a wait that runs out sets *err, waits once more
+//   (bounded) for the outstanding commit, and then frees its tensor memory without writing C.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -156,10 +156,14 @@ __global__ void __launch_bounds__(128, 1) tc_cgemm_kernel(const TA *__restrict__
         // the MMAs read shared memory until the commit arrives: wait before restaging
         bool arrived = true;
         if (tid == 0) arrived = tc::mbar_wait(tc::smem_u32(bar), parity);   // one poller
-        parity ^= 1u;
         ok = __syncthreads_and(arrived ? 1 : 0) != 0;   // uniform across the CTA
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok && tid == 0) atomicExch(err, 1);
+        if (ok) parity ^= 1u;
+    }
+    // give-up: report, and let the outstanding commit (phase `parity`) land before freeing its columns
+    if (!ok && tid == 0) {
+        atomicExch(err, 1);
+        tc::mbar_drain(tc::smem_u32(bar), parity);
     }
     if (ok) {
         // ---- epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31 ----

@@ -31,9 +31,8 @@
 
 namespace fga {
 
-// (beam, point) pairs inside the window (profiling) and wait timeouts of the tensor-core lattice kernel
+// (beam, point) pairs inside the window (profiling)
 static __device__ unsigned long long g_tc_pairs;
-static __device__ int g_tc_err;
 
 int64_t read_tc_pair_counter(bool reset) {
     unsigned long long v = 0;
@@ -46,19 +45,6 @@ int64_t read_tc_pair_counter(bool reset) {
         cudaMemcpyToSymbol(g_tc_pairs, &z, sizeof z);
     }
     return (int64_t)v;
-}
-
-int read_tc_lattice_error(bool reset) {
-    int v = 0;
-    if (cudaMemcpyFromSymbol(&v, g_tc_err, sizeof v) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    if (reset && v) {
-        const int z = 0;
-        cudaMemcpyToSymbol(g_tc_err, &z, sizeof z);
-    }
-    return v;
 }
 
 namespace {
@@ -110,7 +96,8 @@ __global__ void __launch_bounds__(LT_THREADS, MINB) lattice_tc_kernel(const floa
                                                         int n0, int n1, int n2, int T0, int T1, int T2, int nt1,
                                                         int nt2, const int4 *__restrict__ items, float k, float rw2,
                                                         const float *__restrict__ amax, LtSmem S, LtAxes X, int crow,
-                                                        int *__restrict__ kept, float *__restrict__ partial) {
+                                                        int *__restrict__ kept, float *__restrict__ partial,
+                                                        int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem + S.a;
     unsigned char *sB = smem + S.b;
@@ -281,10 +268,10 @@ __global__ void __launch_bounds__(LT_THREADS, MINB) lattice_tc_kernel(const floa
             const float2 *sE = sE0 + (n & 1) * LT_KB * TA;
             bool arrived = true;
             if (issued > 0 && tid == 0) arrived = tc::mbar_wait(tc::smem_u32(bar), parity);
-            if (issued > 0) parity ^= 1u;
             ok = __syncthreads_and(arrived ? 1 : 0) != 0;   // factors(n) visible; the previous MMAs done
             tc::fence_after();
             if (!ok) break;
+            if (issued > 0) parity ^= 1u;
         // operands: consecutive threads take consecutive rows (conflict-free 16-byte stores)
         const float2 *sW = sW0 + (n & 1) * LT_KB * 3;
         for (int q = tid; q < R_used * 4; q += LT_THREADS) {
@@ -391,7 +378,11 @@ __global__ void __launch_bounds__(LT_THREADS, MINB) lattice_tc_kernel(const floa
         ok = __syncthreads_and(arrived ? 1 : 0) != 0;
         tc::fence_after();
     }
-    if (!ok && tid == 0) atomicExch(&g_tc_err, 1);
+    // give-up: report, and let the outstanding commit (phase `parity`) land before freeing its columns
+    if (!ok && tid == 0) {
+        atomicExch(err, 1);
+        tc::mbar_drain(tc::smem_u32(bar), parity);
+    }
     if (ok) {
         // epilogue: warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31 and split the 8-column chunks
         const int quarter = warp & 3, r = quarter * 32 + lane;
@@ -449,6 +440,79 @@ __global__ void rec_absmax_kernel(const float *__restrict__ rec, int64_t n, floa
 
 }  // namespace
 
+fga_status status_reset(Workspace &ws, cudaStream_t s) {
+    FGA_TRY(ws.status.ensure(16));
+    FGA_CUDA(cudaMemsetAsync(ws.status.p, 0, 16, s));
+    return FGA_OK;
+}
+
+fga_status status_check(Workspace &ws, cudaStream_t s, const char *who) {
+    if (!ws.status.p) {
+        FGA_CUDA(cudaStreamSynchronize(s));
+        return FGA_OK;
+    }
+    int v[2] = {0, 0};
+    FGA_CUDA(cudaMemcpyAsync(v, ws.status.p, sizeof v, cudaMemcpyDeviceToHost, s));
+    FGA_CUDA(cudaStreamSynchronize(s));
+    if (v[0]) {
+        set_error(std::string(who) + ": a tensor-core wait of the Gaussian sum ran out");
+        return FGA_ERR_TIMEOUT;
+    }
+    if (v[1]) {
+        set_error(std::string(who) + ": non-finite values in the beam state or the results");
+        return FGA_ERR_NUMERIC;
+    }
+    return FGA_OK;
+}
+
+template <typename R>
+__global__ void nonfinite_kernel(const R *__restrict__ x, int64_t n, int *__restrict__ flag) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+// beam state in structure-of-arrays form: field f of beam b at st[f * cap + b], b < nb
+template <typename R>
+__global__ void nonfinite_state_kernel(const R *__restrict__ st, int64_t cap, int64_t nb, int *__restrict__ flag) {
+    const R *fld = st + (int64_t)blockIdx.y * cap;
+    bool bad = false;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(fld[b]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+fga_status flag_nonfinite_state(Workspace &ws, const void *st, int64_t cap, int64_t nb, int nf, int precision,
+                                cudaStream_t s) {
+    if (nb <= 0 || !st) return FGA_OK;
+    if (!ws.status.p) FGA_TRY(status_reset(ws, s));
+    const dim3 grid((unsigned)std::min<int64_t>(64, (nb + 255) / 256), (unsigned)nf);
+    int *flag = ws.status.as<int>() + 1;
+    if (precision == FGA_PREC_FP64)
+        nonfinite_state_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double *>(st), cap, nb, flag);
+    else
+        nonfinite_state_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(st), cap, nb, flag);
+    FGA_CUDA(cudaGetLastError());
+    return FGA_OK;
+}
+
+fga_status flag_nonfinite(Workspace &ws, const void *data, int64_t n, int precision, cudaStream_t s) {
+    if (n <= 0 || !data) return FGA_OK;
+    if (!ws.status.p) FGA_TRY(status_reset(ws, s));
+    int sms = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = (int)std::min<int64_t>((int64_t)sms * 8, (n + 255) / 256);
+    int *flag = ws.status.as<int>() + 1;
+    if (precision == FGA_PREC_FP64)
+        nonfinite_kernel<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(data), n, flag);
+    else
+        nonfinite_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(data), n, flag);
+    FGA_CUDA(cudaGetLastError());
+    return FGA_OK;
+}
+
 // tile of the tensor-core lattice sum: rows (j,l) <= 128, T0 <= 32
 void tile_shape_tc(const fga_lattice &L, int T[3]) {
     if (L.n[2] == 1) {
@@ -494,6 +558,7 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
     float *amax = reinterpret_cast<float *>(tail);
     int *kept = reinterpret_cast<int *>(tail + 64);
     FGA_CUDA(cudaMemsetAsync(tail, 0, 64, s));
+    if (!ws.status.p) FGA_TRY(status_reset(ws, s));
     const int cnt = prof_counting() ? 1 : 0;
     prof_add_pairs_tested(plan.pairs_tested);
     if (plan.nitems > 0) {
@@ -510,7 +575,7 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
         lattice_tc_kernel<CNT, MB><<<plan.nitems, LT_THREADS, S.bytes, s>>>(                                      \
             static_cast<const float *>(rec), plan.ax[0], plan.ax[1], plan.ax[2], plan.n[0], plan.n[1], plan.n[2], \
             T0, T1, T2, plan.nt[1], plan.nt[2], plan.items, (float)k, (float)(rw * rw), amax, S, X, crow, kept,   \
-            ws.partial.as<float>());                                                                              \
+            ws.partial.as<float>(), ws.status.as<int>());                                                         \
     } while (0)
         if (cnt) {
             if (three) FGA_LTC(true, 3);

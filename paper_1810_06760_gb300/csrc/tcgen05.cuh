@@ -72,6 +72,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
+// Give-up path of a CTA whose wait for a tcgen05.commit ran out: the MMAs of that commit may still be
+// reading shared memory and writing tensor memory, so before the CTA frees its tensor memory and
+// exits it waits once more, with a bound four times longer, for the same phase.  Returns whether the
+// commit arrived; if it never does (the tensor pipe made no progress for 5 x SPIN_LIMIT polls) the CTA
+// frees its columns anyway rather than hang the GPU.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+    for (int r = 0; r < 4; r++)
+        if (mbar_wait(bar, parity)) return true;
+    return false;
+}
 
 // 8 consecutive K elements (k % 8 == 0) of one row: one 16-byte store of their FP16 values
 __device__ __forceinline__ void store8(unsigned char *base, uint32_t off, const __half h[8]) {

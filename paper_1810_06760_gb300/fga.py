@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libfga_gb300.so")
 FGA_OK, FGA_ERR_INVALID_ARG, FGA_ERR_OOM, FGA_ERR_CUDA, FGA_ERR_TIMEOUT, FGA_ERR_NUMERIC, FGA_ERR_UNSUPPORTED = range(7)
 PREC_FP32, PREC_FP64 = 0, 1
 MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
-EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_propagate", "fga_reconstruct",
+EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_transform", "fga_propagate", "fga_reconstruct",
             "fga_reconstruct_lattice", "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export",
             "fga_beams_export_all", "fga_beams_destroy", "fga_bin", "fga_profile_enable", "fga_profile_read",
             "fga_solve_vjp", "fga_server_create", "fga_server_submit", "fga_server_wait", "fga_server_stats",
@@ -105,6 +105,7 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_model_create.argtypes = [C.POINTER(vp), C.POINTER(ModelDesc), vp, vp, vp]
     L.fga_model_destroy.argtypes = [vp]
     L.fga_decompose.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(vp), vp]
+    L.fga_transform.argtypes = [C.POINTER(InitDesc), vp, vp]
     L.fga_propagate.argtypes = [vp, vp, C.c_double, i32, vp]
     L.fga_reconstruct.argtypes = [vp, vp, i64, C.c_double, vp, vp]
     L.fga_reconstruct_noalloc.argtypes = [vp, vp, i64, C.c_double, vp, vp]
@@ -287,6 +288,18 @@ def decompose(model: Model, desc: InitDesc, stream=None) -> Beams:
     h = C.c_void_p()
     _check(lib().fga_decompose(model.h, C.byref(desc), C.byref(h), _stream(stream)))
     return Beams(h, desc.precision, desc.k)
+
+
+def transform(desc: InitDesc, out=None, stream=None):
+    """fga_transform: the wave-packet transform F(q,p) of desc's f on its mesh (Eq. psi), complex
+    [A, A, A, 3] (A = nq np; entry (a0, a1, a2), a_d = iq_d np + jp_d) in desc's precision."""
+    import torch
+    A = desc.nq * desc.np
+    if out is None:
+        out = torch.empty((A, A, A, 3), dtype=_cdtype(desc.precision),
+                          device=torch.device("cuda", torch.cuda.current_device()))
+    _check(lib().fga_transform(C.byref(desc), _dptr(out), _stream(stream)))
+    return out
 
 
 def propagate(model: Model, beams: Beams, dt: float, nsteps: int, stream=None) -> None:

@@ -134,15 +134,19 @@ class Workload:
         return self.mesh.M * len(self.classes)
 
 
-def _ygrid(x0, half: float, ny: int):
-    dy = np.full(3, 2.0 * half / ny)
+def _ygrid(x0, half: float, ny):
+    """Cell-centred y grid over x0 +- half with ny points per axis (an int or three ints)."""
+    n = np.broadcast_to(np.asarray(ny, dtype=np.float64), (3,))
+    dy = 2.0 * half / n
     y0 = np.asarray(x0, dtype=np.float64) - half + 0.5 * dy
     return y0, dy
 
 
-def _packet(y0, dy, ny: int, k: float, x0, pol, d) -> np.ndarray:
-    """pol * exp(-k|y-x0|^2/2) * exp(i k d.y) on the y grid (a complex [ny,ny,ny,3] array)."""
-    ax = [y0[a] + dy[a] * np.arange(ny) for a in range(3)]
+def _packet(y0, dy, ny, k: float, x0, pol, d) -> np.ndarray:
+    """pol * exp(-k|y-x0|^2/2) * exp(i k d.y) on the y grid (a complex [ny0,ny1,ny2,3] array; ny an int
+    or three ints)."""
+    n = np.broadcast_to(np.asarray(ny, dtype=np.int64), (3,))
+    ax = [y0[a] + dy[a] * np.arange(n[a]) for a in range(3)]
     Y = np.stack(np.meshgrid(*ax, indexing="ij"), -1)
     r2 = np.sum((Y - np.asarray(x0)) ** 2, axis=-1)
     ph = k * (Y @ np.asarray(d, dtype=np.float64))
@@ -197,6 +201,20 @@ def smooth(nq: int = 24, np_: int = 8, ny: int = 128, nsteps: int = 400, dt: flo
         snap_axes = (s, s, s)
     return Workload("smooth", k, med, ny, y0, dy, f, None, mesh, tuple(classes), dt, nsteps, times, rx,
                     window_radius(k), snap, rx_axes, snap_axes)
+
+
+def transform_case(ny=(128, 128, 128), nq: int = 24, np_: int = 8, k: float = 64.0):
+    """Input of the wave-packet transform alone, shaped like the smooth workload's decomposition: its
+    packet (centre, direction, polarisation) sampled on a y grid over x0 +- 6/sqrt(k) with ny points per
+    axis (an int or three ints), and its q, p mesh (nq, np_ per axis).  Returns (f, y0, dy, mesh, k)."""
+    x0 = np.array([0.35, 0.45, 0.55])
+    dhat = np.array([3.0, 2.0, 1.0]) / math.sqrt(14.0)
+    b = np.array([0.2, -0.5, 1.0])
+    b = b / np.linalg.norm(b)
+    y0, dy = _ygrid(x0, window_radius(k), ny)
+    f = _packet(y0, dy, ny, k, x0, b, dhat)
+    mesh = centred_mesh(nq, x0, np_, dhat, mesh_radius(k, 6.0), mesh_radius(k, 4.8))
+    return f, y0, dy, mesh, k
 
 
 def random_points(n: int, lo, hi, seed: int) -> np.ndarray:

@@ -21,6 +21,19 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (den if den > 0 else 1.0))
 
 
+def max_rel_dominant(a, b, frac=1e-3):
+    """Largest element-wise relative error |a - b| / |b| over the entries of b whose magnitude is at
+    least `frac` of its largest one (complex entries compared by modulus).  Beside a relative L2 over a
+    whole array, this catches an error confined to a few beams, receivers or mesh points."""
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    mag = np.abs(b)
+    if mag.size == 0 or mag.max() == 0:
+        return float(np.abs(a).max()) if a.size else 0.0
+    sel = mag >= frac * mag.max()
+    return float(np.max(np.abs(a[sel] - b[sel]) / mag[sel]))
+
+
 def oracle_beams(O, w, classes=None, vector_form=False):
     """Oracle decomposition + initialisation of a workload: list of (cls, state, meta)."""
     model = oracle_model(O, w.medium)

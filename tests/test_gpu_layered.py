@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_1810_06760_gb300 import workloads as W
-from tests.helpers import gpu_setup, oracle_beams, oracle_model, oracle_mesh, rel_l2
+from tests.helpers import gpu_setup, max_rel_dominant, oracle_beams, oracle_model, oracle_mesh, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -89,4 +89,7 @@ def test_layered_solve_seismograms(fga, oracle, prec):
         while j < len(w.times) and abs(w.times[j] - n * w.dt) < 1e-9:
             ref[j] = oracle.gauss_sum(oracle.records(st, meta, wgt), w.k, w.rw, w.receivers)
             j += 1
-    assert rel_l2(seis.cpu().numpy(), ref) <= (TOL[prec] if prec == 1 else 5e-4)
+    # the oracle's interface events follow the printed Zoeppritz system, the library's the 6 x 6
+    # continuity solve; on this case every lineage matches and FP32 stays near 4e-6
+    assert rel_l2(seis.cpu().numpy(), ref) <= TOL[prec]
+    assert max_rel_dominant(seis.cpu().numpy(), ref, 1e-2) <= (2e-3 if prec == 0 else 1e-9)

@@ -1,19 +1,30 @@
 """GPU library (through the C ABI) against the FP64 oracle on the same seeded inputs.
 
 Tolerances (relative L2 over each compared array): 1e-10 for the FP64 path, 1e-4 for the FP32
-path; binning is compared bit for bit.  Sizes span several sort tiles (2048 keys), several point
-tiles (32 points) and ragged tails."""
+path; binning is compared bit for bit.  Beside the L2 bar, the wavefields are compared element by
+element on the entries above 1e-2 of their largest one (2e-3 FP32, 1e-9 FP64): an FP32 Gaussian sum
+carries an absolute error of a few 1e-6 of the peak (measured rel-L2 ~1e-5), i.e. a few 1e-4 relative
+on such an entry, so a localised error in a few beams or receivers cannot hide under the L2 norm.
+Sizes span several sort tiles (2048 keys), several point tiles (32 points) and ragged tails."""
 import math
 
 import numpy as np
 import pytest
 
 from paper_1810_06760_gb300 import workloads as W
-from tests.helpers import gpu_setup, oracle_beams, oracle_model, oracle_mesh, rel_l2
+from tests.helpers import gpu_setup, max_rel_dominant, oracle_beams, oracle_model, oracle_mesh, rel_l2
 
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-4, 1: 1e-10}   # FGA_PREC_FP32, FGA_PREC_FP64
+ELEM_TOL = {0: 2e-3, 1: 1e-9}
+ELEM_FRAC = 1e-2
+
+
+def _check_field(got, ref, prec):
+    assert rel_l2(got, ref) <= TOL[prec], rel_l2(got, ref)
+    em = max_rel_dominant(got, ref, ELEM_FRAC)
+    assert em <= ELEM_TOL[prec], em
 
 
 @pytest.fixture(scope="module")
@@ -88,16 +99,22 @@ def test_reconstruct_at_points(fga, oracle, prec):
         oracle.propagate(omodel, st, meta, w.dt, w.nsteps)
         ref += oracle.gauss_sum(oracle.records(st, meta, wgt), w.k, w.rw, x)
     u = fga.reconstruct(beams, torch.as_tensor(x, device="cuda"), rw=w.rw).cpu().numpy()
-    assert rel_l2(u, ref) <= TOL[prec]
+    _check_field(u, ref, prec)
     # the untruncated oracle sum differs from the truncated one by at most e^-18 of the amplitudes
     ref_full = sum(oracle.gauss_sum(oracle.records(st, meta, wgt), w.k, 0.0, x) for _, st, meta in obeams)
     assert rel_l2(ref, ref_full) < 1e-6
 
 
 @pytest.mark.parametrize("prec", [1, 0])
-def test_solve_seismograms_and_snapshot(fga, oracle, prec):
+@pytest.mark.parametrize("case", ["k64", "k128", "k128_wide"])
+def test_solve_seismograms_and_snapshot(fga, oracle, prec, case):
+    """Whole solve against the oracle.  k = 128 (the largest wavenumber of the serving mix) makes the
+    phase k P.(x - Q) reach ~68 rad inside the window, which the FP32 path reduces modulo 2 pi before
+    its sine and cosine; the y grid then needs 8 ceil(sqrt(k)) = 96 points per axis."""
     import torch
-    w = _small_smooth(grid=True)
+    w = {"k64": lambda: _small_smooth(grid=True),
+         "k128": lambda: _small_smooth(grid=True, k=128.0, ny=96),
+         "k128_wide": lambda: _small_smooth(grid=True, k=128.0, ny=96, nq=6, np_=4, nsteps=60, n_samples=20)}[case]()
     model, desc, keep = gpu_setup(w, prec)
     rx = torch.as_tensor(w.receivers, device="cuda")
     sn = torch.as_tensor(w.snapshot, device="cuda")
@@ -108,8 +125,8 @@ def test_solve_seismograms_and_snapshot(fga, oracle, prec):
     F = oracle.fbi(w.f, w.y0, w.dy, w.k, mesh)
     ref_seis, ref_snap = oracle.solve(omodel, w.k, mesh, F, None, w.classes, w.dt, w.nsteps, w.times,
                                       w.receivers, w.rw, snap=w.snapshot)
-    assert rel_l2(seis.cpu().numpy(), ref_seis) <= TOL[prec]
-    assert rel_l2(snap.cpu().numpy(), ref_snap) <= TOL[prec]
+    _check_field(seis.cpu().numpy(), ref_seis, prec)
+    _check_field(snap.cpu().numpy(), ref_snap, prec)
 
 
 @pytest.mark.parametrize("prec", [1, 0])
@@ -133,7 +150,7 @@ def test_reconstruct_on_lattice(fga, oracle, prec, shape):
     for cls, st, meta in obeams:
         oracle.propagate(omodel, st, meta, w.dt, w.nsteps)
         ref += oracle.gauss_sum(oracle.records(st, meta, mesh.weight(w.k)), w.k, w.rw, X)
-    assert rel_l2(u.reshape(-1, 3), ref) <= TOL[prec]
+    _check_field(u.reshape(-1, 3), ref, prec)
 
 
 @pytest.mark.parametrize("prec", [1, 0])
@@ -186,3 +203,24 @@ def test_errors_are_reported_not_raised_from_device(fga):
     assert out.shape == (0, 3)
     with pytest.raises(fga.FGAError):   # sample time outside (0, T]
         fga.solve(model, desc, w.dt, w.nsteps, np.array([w.T * 2]), torch.as_tensor(w.receivers, device="cuda"))
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_nonfinite_input_is_reported(fga, prec):
+    """Initial data holding a NaN make non-finite beams: the solve returns FGA_ERR_NUMERIC (its device
+    status word) instead of silently returning NaN seismograms; the library stays usable."""
+    import torch
+    w = _small_smooth(grid=True, nsteps=8, n_samples=4)
+    f = w.f.copy()
+    f[3, 4, 5, 1] = np.nan
+    model = fga.model_from_medium(w.medium, "cuda")
+    df = torch.as_tensor(f, device="cuda")
+    desc = fga.init_desc(w.k, df, None, w.y0, w.dy, w.mesh, w.classes, prec)
+    rx = torch.as_tensor(w.receivers, device="cuda")
+    with pytest.raises(fga.FGAError) as e:
+        fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, rw=w.rw)
+    assert e.value.status == fga.FGA_ERR_NUMERIC
+    ok = torch.as_tensor(w.f, device="cuda")
+    desc2 = fga.init_desc(w.k, ok, None, w.y0, w.dy, w.mesh, w.classes, prec)
+    seis, _ = fga.solve(model, desc2, w.dt, w.nsteps, w.times, rx, rw=w.rw)
+    assert torch.isfinite(torch.view_as_real(seis)).all()
