@@ -840,7 +840,8 @@ fga_status fga_profile_read(fga_profile_t *out, int reset) {
     out->beam_steps = g_prof.beam_steps;
     out->pairs_tested = g_prof.pairs_tested;
     out->pairs_in_window =
-        read_pair_counter(reset != 0) + read_lattice_pair_counter(reset != 0) + read_tc_pair_counter(reset != 0);
+        read_pair_counter(reset != 0) + read_lattice_pair_counter(reset != 0) + read_tc_pair_counter(reset != 0) +
+        read_plane_pair_counter(reset != 0);
     if (reset) {
         g_prof.launches = g_prof.beam_steps = g_prof.pairs_tested = 0;
         for (int c = 0; c < P_NCAT; c++) {

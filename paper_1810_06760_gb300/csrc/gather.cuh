@@ -34,11 +34,20 @@ struct LatticePlan {
     // their 1-D factors by recurrence
     bool uniform[3] = {false, false, false};
     double dx[3] = {0, 0, 0};
+    double x_first[3] = {0, 0, 0};   // first coordinate of each axis
 };
 // tc: tile shape and work split of the tensor-core kernel (the FP32 path); else the CUDA-core kernel's
 fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, const fga_lattice &L,
                               cudaStream_t s, LatticePlan &plan, bool tc);
 void tile_shape_tc(const fga_lattice &L, int T[3]);
+// single-plane lattices with uniform axes 0 and 1: the warp-specialised plane kernel (tc_plane.cu)
+void tile_shape_plane(const fga_lattice &L, int T[3]);
+bool plane_tc_eligible(const LatticePlan &plan);
+fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec, double k, double rw, void *u,
+                        cudaStream_t s, int cat);
+int64_t read_plane_pair_counter(bool reset);
+// |A| bound of n records into *out (zeroed by the caller)
+fga_status rec_absmax(const float *rec, int64_t n, float *out, cudaStream_t s, int cat);
 fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *rec, double k, double rw, void *u,
                           cudaStream_t s, int cat);
 fga_status lattice_reduce_f32(const float *partial, const LatticePlan &plan, void *u, cudaStream_t s);

@@ -328,8 +328,23 @@ static void tile_shape(const fga_lattice &L, int T[3]) {
 
 fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, const fga_lattice &L,
                               cudaStream_t s, LatticePlan &plan, bool tc) {
+    // axes with uniform spacing (the tensor-core kernels form their 1-D factors by recurrence there)
+    for (int d = 0; d < 3; d++) {
+        const double *a = L.axis[d];
+        const int n = L.n[d];
+        bool uni = n >= 2;
+        const double step = n >= 2 ? (a[n - 1] - a[0]) / (n - 1) : 0.0;
+        const double scale = std::max(std::fabs(a[0]), std::fabs(a[n - 1])) + std::fabs(step) * n;
+        for (int i = 0; uni && i < n; i++) uni = std::fabs(a[i] - (a[0] + i * step)) <= 1e-12 * scale;
+        plan.uniform[d] = uni && step != 0.0;
+        plan.dx[d] = step;
+        plan.x_first[d] = a[0];
+    }
+    const bool plane = tc && L.n[2] == 1 && (plan.uniform[0] || L.n[0] == 1) && (plan.uniform[1] || L.n[1] == 1);
     int T[3];
-    if (tc)
+    if (plane)
+        tile_shape_plane(L, T);
+    else if (tc)
         tile_shape_tc(L, T);
     else
         tile_shape(L, T);
@@ -385,8 +400,10 @@ fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *ce
                 }
         }
     }
-    // beams per work item: the tensor-core kernel amortises its set-up over longer ranges
-    int64_t B = tc ? std::max<int64_t>(512, (total + 1215) / 1216) : std::max<int64_t>(256, (total + 2047) / 2048);
+    // beams per work item: the tensor-core kernels amortise their set-up over longer ranges (the plane
+    // kernel runs one persistent CTA per SM over about three items each)
+    int64_t B = plane ? std::max<int64_t>(2048, (total + 455) / 456)
+                      : (tc ? std::max<int64_t>(512, (total + 1215) / 1216) : std::max<int64_t>(256, (total + 2047) / 2048));
     B = (B + 63) / 64 * 64;
     std::vector<int32_t> item_start((size_t)ntiles + 1, 0);
     std::vector<int4> items;
@@ -402,16 +419,6 @@ fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *ce
     item_start[(size_t)ntiles] = (int32_t)items.size();
     plan.ntiles = ntiles;
     plan.nitems = (int)items.size();
-    for (int d = 0; d < 3; d++) {
-        const double *a = L.axis[d];
-        const int n = L.n[d];
-        bool uni = n >= 2;
-        const double step = n >= 2 ? (a[n - 1] - a[0]) / (n - 1) : 0.0;
-        const double scale = std::max(std::fabs(a[0]), std::fabs(a[n - 1])) + std::fabs(step) * n;
-        for (int i = 0; uni && i < n; i++) uni = std::fabs(a[i] - (a[0] + i * step)) <= 1e-12 * scale;
-        plan.uniform[d] = uni && step != 0.0;
-        plan.dx[d] = step;
-    }
     plan.pairs_tested = total * (int64_t)T[0] * T[1] * T[2];
     // device copies: axes, item starts, items
     const size_t axb = sizeof(double) * (size_t)(L.n[0] + L.n[1] + L.n[2]);
@@ -507,6 +514,7 @@ fga_status lattice_reduce_f32(const float *partial, const LatticePlan &plan, voi
 fga_status run_lattice(Workspace &ws, const LatticePlan &plan, int precision, const void *rec, double k, double rw,
                        void *u, cudaStream_t s, int cat) {
     if (precision == FGA_PREC_FP64) return run_lattice_t<double>(ws, plan, rec, k, rw, u, s, cat);
+    if (plane_tc_eligible(plan)) return run_plane_tc(ws, plan, rec, k, rw, u, s, cat);
     return run_lattice_tc(ws, plan, rec, k, rw, u, s, cat);
 }
 

@@ -23,6 +23,7 @@
 // of the next block are formed while the tensor cores work on the current one.  The partial sums go
 // to the plan's per-item buffer in the layout of the CUDA-core lattice kernel and are reduced by it.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 
 #include "fga_beam.cuh"
@@ -441,8 +442,8 @@ __global__ void rec_absmax_kernel(const float *__restrict__ rec, int64_t n, floa
 }  // namespace
 
 fga_status status_reset(Workspace &ws, cudaStream_t s) {
-    FGA_TRY(ws.status.ensure(16));
-    FGA_CUDA(cudaMemsetAsync(ws.status.p, 0, 16, s));
+    FGA_TRY(ws.status.ensure(64));
+    FGA_CUDA(cudaMemsetAsync(ws.status.p, 0, 64, s));
     return FGA_OK;
 }
 
@@ -451,11 +452,19 @@ fga_status status_check(Workspace &ws, cudaStream_t s, const char *who) {
         FGA_CUDA(cudaStreamSynchronize(s));
         return FGA_OK;
     }
-    int v[2] = {0, 0};
+    int v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     FGA_CUDA(cudaMemcpyAsync(v, ws.status.p, sizeof v, cudaMemcpyDeviceToHost, s));
     FGA_CUDA(cudaStreamSynchronize(s));
     if (v[0]) {
-        set_error(std::string(who) + ": a tensor-core wait of the Gaussian sum ran out");
+        std::string m = std::string(who) + ": a tensor-core wait of the Gaussian sum ran out";
+        if (v[2]) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf,
+                          " (wait %d: block %d, stage %d, parity %d, %d blocks claimed, CTA %d, %d blocks taken by the MMA thread)", v[2],
+                          v[3], v[4], v[5], v[6], v[7], v[8]);
+            m += buf;
+        }
+        set_error(m);
         return FGA_ERR_TIMEOUT;
     }
     if (v[1]) {
@@ -509,6 +518,14 @@ fga_status flag_nonfinite(Workspace &ws, const void *data, int64_t n, int precis
         nonfinite_kernel<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(data), n, flag);
     else
         nonfinite_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(data), n, flag);
+    FGA_CUDA(cudaGetLastError());
+    return FGA_OK;
+}
+
+fga_status rec_absmax(const float *rec, int64_t n, float *out, cudaStream_t s, int cat) {
+    ProfScope ps(cat, s);
+    const int blocks = (int)std::min<int64_t>(152 * 4, (n * 6 + 255) / 256 + 1);
+    rec_absmax_kernel<<<blocks, 256, 0, s>>>(rec, n, out);
     FGA_CUDA(cudaGetLastError());
     return FGA_OK;
 }

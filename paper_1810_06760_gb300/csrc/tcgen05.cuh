@@ -30,6 +30,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     return d;                // base offset 0, relative LBO, swizzle none
 }
 
+// the same with explicit byte offsets between K-adjacent (lbo) and row-adjacent (sbo) core matrices
+// (multiples of 16 bytes; padded layouts spread one warp's stores over all banks)
+__device__ __forceinline__ uint64_t smem_desc_lbo_sbo(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
 // instruction descriptor: D f32, A and B f16, both K-major, N and M
 __device__ __forceinline__ uint32_t instr_desc(int n, int m) {
     uint32_t d = 0;

@@ -154,6 +154,29 @@ def test_reconstruct_on_lattice(fga, oracle, prec, shape):
 
 
 @pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("shape", [(20, 20), (23, 45), (1, 7), (32, 20), (33, 41), (16, 16)])
+def test_reconstruct_on_plane(fga, oracle, prec, shape):
+    """Receiver planes (uniform axes 0 and 1, one x3): in FP32 the warp-specialised plane kernel (tiles
+    of at most 32 x 20 points: one tile, several tiles with ragged edges in both axes, a single column);
+    against the oracle's brute-force sum at the same points."""
+    import torch
+    w = _small_smooth(grid=True, nsteps=16)
+    model, desc, keep = gpu_setup(w, prec)
+    beams = fga.decompose(model, desc)
+    fga.propagate(model, beams, w.dt, w.nsteps)
+    axes = (np.linspace(0.05, 0.95, shape[0]) if shape[0] > 1 else np.array([0.41]),
+            np.linspace(0.02, 0.98, shape[1]), np.array([0.3]))
+    u = fga.reconstruct_lattice(beams, axes, rw=w.rw).cpu().numpy()
+    X = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    omodel, mesh, obeams = oracle_beams(oracle, w)
+    ref = np.zeros((X.shape[0], 3), complex)
+    for cls, st, meta in obeams:
+        oracle.propagate(omodel, st, meta, w.dt, w.nsteps)
+        ref += oracle.gauss_sum(oracle.records(st, meta, mesh.weight(w.k)), w.k, w.rw, X)
+    _check_field(u.reshape(-1, 3), ref, prec)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
 def test_solve_on_lattices_equals_solve_on_points(fga, prec):
     """Receivers and snapshot given as lattices give the same seismograms and snapshot as the same
     points given one by one."""
