@@ -11,21 +11,25 @@
 // Both operands are FP16 hi/lo splits of the FP32 values (hi*hi + hi*lo + lo*hi, FP32 accumulation),
 // as in the other tensor-core kernels of the library.
 //
-// One persistent CTA per SM: eight producer warps and one MMA warp.
-//  - Each producer warp filters its share of an item's candidate records (the beams within the window
-//    radius of the tile's box) into a queue and turns every 32 kept beams into one operand block: lane
-//    (h, p) takes beams 2p and 2p+1, forms E0 by a stride-2 recurrence on its parity (the other parity
-//    comes from lane p + 16h' by a shuffle), E1 by recurrence on its half of the rows, W, and writes
-//    32-bit pairs of FP16 values straight into the K-major operand layout.  The layout is padded
-//    (leading byte offset 144, row-group stride chosen per tile) so that these stores are free of bank
-//    conflicts.
-//  - Blocks are numbered in the order they are claimed and go through a ring of shared-memory stages;
-//    per stage a "full" mbarrier (producer -> MMA) and an "empty" one (tcgen05.commit -> producers).
-//  - The MMA warp's elected thread issues 12 tcgen05.mma (two K steps x re/im x three split products)
-//    per block into an M = 128 x N = 2 n_c accumulator; rows 64..127 of the A descriptor read the
-//    neighbouring buffer and their accumulator lanes are never read.
-//  - At the end of an item an END block (no data) closes the sequence; after the last commit the
-//    accumulator rows go to the plan's per-item partial sums, reduced as for the other lattice kernels.
+// One persistent CTA per SM: six producer warps and one MMA warp.
+//  - Each producer warp owns one shared-memory stage.  It filters its share of an item's candidate
+//    records (the beams within the window radius of the tile's box; four chunks of 32 in flight) into a
+//    queue and turns every 32 kept beams into one operand block: lane (h, p) takes beams 2p and 2p+1,
+//    forms W, E1 by recurrence on its half of the rows and E0 by a stride-2 recurrence on its parity
+//    (the other parity comes from lane p + 16(1-h) by a shuffle), all in registers, then waits for its
+//    stage and writes 32-bit pairs of FP16 values straight into the K-major operand layout.  The layout
+//    is padded (leading byte offset 144, row-group stride chosen per tile) so that these stores are
+//    free of bank conflicts.
+//  - Per stage a "full" mbarrier (producer -> MMA) and an "empty" one (tcgen05.commit -> producer).
+//    With one producer per stage every parity wait is exactly one phase behind the barrier.
+//  - The MMA warp's elected thread takes the producers' blocks in a fixed cyclic order (so the
+//    accumulation order, and the result, do not depend on timing) and issues four tcgen05.mma per block
+//    (two K steps x re/im): each multiplies [A_hi; A_lo] (M = 128) by [B_hi; B_lo] (N = 4 n_c), so one
+//    instruction forms the three split products hi*hi, hi*lo and lo*hi (and an unused lo*lo quarter);
+//    a tcgen05.mma costs about the same for N = 48 as for N = 96, so fewer, wider instructions win.
+//  - A producer closes its part of an item with an END block (no data); once every producer has, the
+//    last commit is awaited and the accumulator rows go to the plan's per-item partial sums, reduced as
+//    for the other lattice kernels.
 // Every wait is bounded: a wait that runs out sets the CTA's abort flag and the call's error word; an
 // aborting CTA keeps its barrier schedule, issues no further MMA, waits (bounded) for its outstanding
 // commit and frees its tensor memory.
@@ -56,15 +60,14 @@ int64_t read_plane_pair_counter(bool reset) {
 
 namespace {
 
-constexpr int PL_PROD = 8;                     // producer warps
+constexpr int PL_PROD = 6;                     // producer warps, one shared-memory stage each
 constexpr int PL_THREADS = (PL_PROD + 1) * 32; // + the MMA warp
 constexpr int PL_KB = 32;                      // beams per block
-constexpr int PL_STAGES = 6;                   // most stages (fewer when a stage is large)
 constexpr int PL_LBO = 144;                    // bytes between K-adjacent core matrices
 constexpr int PL_SBO_A = 592;                  // bytes between row-adjacent core matrices of A
 constexpr int PL_A_COPY = 8 * PL_SBO_A;        // one A copy: 64 rows (8 row groups)
-constexpr int PL_QUEUE = 64;                   // kept-beam queue per producer warp
-constexpr int PL_T0_MAX = 32, PL_T1_MAX = 20;
+constexpr int PL_QUEUE = 64;                   // kept records queued per producer warp (31 + 32 used)
+constexpr int PL_T0_MAX = 24, PL_T1_MAX = 20;   // six 32 KB stages fit with n_c <= 24
 
 struct PlaneArgs {
     const float *rec;        // records [n_rec][12]: Q, P, weighted polarised amplitude (3 complex)
@@ -74,7 +77,7 @@ struct PlaneArgs {
     int T0, T1, nt1;         // tile shape and tiles along axis 1
     int nc;                  // complex accumulator columns (T0 rounded up to 8)
     int sbo_b;               // row-group stride of the B copies
-    int b_copy, stage_bytes, nst;
+    int b_copy, stage_bytes;
     float x0, h0, x1, h1, x2;  // uniform axes 0 and 1, the plane's x3
     float k, rw2;
     const float *amax;       // bound of |A| over the records
@@ -122,18 +125,6 @@ __device__ __forceinline__ void bar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// A stage's empty barrier is waited on by parity, which only tells its newest phase from the one
-// before.  Blocks are claimed by several producers, so the producer of block n first waits until the
-// MMA thread has taken block n - nst (the stage's previous use): then the stage's use before that has
-// completed, and the parity wait below refers to the right phase.
-__device__ __forceinline__ bool wait_taken(const int *taken, int need, const int *gerr) {
-    for (int it = 0; it < (1 << 22); it++) {
-        if (*reinterpret_cast<const volatile int *>(taken) >= need) return true;
-        if ((it & 1023) == 1023 && *reinterpret_cast<const volatile int *>(gerr) != 0) return false;
-    }
-    return false;
-}
-
 // first wait of a launch that gave up: the error word plus where (1 producer stage wait, 2 END stage
 // wait, 3 MMA wait for a block, 4 wait for the item's last commit), the block, its stage and parity,
 // the blocks claimed and the CTA (words 2..7 of the call's status words)
@@ -153,28 +144,36 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-template <bool COUNT>
+// row-group stride of the B copies for n_c complex columns: the Re rows (i) and the Im rows (n_c + i),
+// stored by the two lane halves in one instruction, land 16 banks apart
+__host__ __device__ constexpr int plane_sbo_b(int nc) {
+    int sbo = 576;
+    while (((nc / 8) * sbo) % 128 != 64) sbo += 16;
+    return sbo;
+}
+
+// JT, T0T: the tile's j values per row half and points along axis 0 as compile-time constants (the
+// loops over rows and points unroll, operand offsets become immediates); 0 = taken from the launch
+template <bool COUNT, int JT, int T0T>
 __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char *stages = smem;
-    unsigned char *tail = smem + P.nst * P.stage_bytes + PL_A_COPY;   // A rows 64..127 may read past the ring
+    unsigned char *tail = smem + PL_PROD * P.stage_bytes + PL_A_COPY;
     uint64_t *full = reinterpret_cast<uint64_t *>(tail);
-    uint64_t *empty = full + PL_STAGES;
-    uint64_t *done = empty + PL_STAGES;
+    uint64_t *empty = full + PL_PROD;
+    uint64_t *done = empty + PL_PROD;
     int *hdr = reinterpret_cast<int *>(done + 1);          // per stage: beams in the block, -1 = END
-    int *misc = hdr + PL_STAGES;                           // 0 blocks claimed, 1 abort, 2 item had MMAs, 3 blocks taken by the MMA thread
+    int *misc = hdr + PL_PROD;                             // 1 abort, 2 item had MMAs, 3 blocks taken
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 4);
-    int *queues = reinterpret_cast<int *>(misc + 8);       // [PL_PROD][PL_QUEUE]
+    float4 *queues = reinterpret_cast<float4 *>(tail + 256);  // [PL_PROD][PL_QUEUE][3]: kept records
 
     if (warp == PL_PROD) tc::alloc(tc::smem_u32(tmem_slot), P.tcols);
     if (tid == 0) {
-        for (int s = 0; s < P.nst; s++) {
+        for (int s = 0; s < PL_PROD; s++) {
             tc::mbar_init(tc::smem_u32(full + s));
             tc::mbar_init(tc::smem_u32(empty + s));
         }
         tc::mbar_init(tc::smem_u32(done));
-        misc[0] = 0;
         misc[1] = 0;
         misc[3] = 0;
     }
@@ -194,130 +193,141 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
     const uint32_t tmem = *tmem_slot;
     volatile int *abort_flag = misc + 1;
 
-    const int J = (P.T1 + 1) >> 1;           // j values per row half
-    const int NR = 2 * P.nc;
+    const int J = JT ? JT : (P.T1 + 1) >> 1;         // j values per row half
+    const int T0 = T0T ? T0T : P.T0;
+    const int NC = T0T ? (T0T + 7) / 8 * 8 : P.nc;
+    const int SBOB = T0T ? plane_sbo_b((T0T + 7) / 8 * 8) : P.sbo_b;
+    const int NR = 2 * NC;
     const float hk = -0.5f * P.k;
     uint32_t done_par = 0;
-    int mma_n = 0;                           // next block the MMA thread consumes (never reset)
+    int uses = 0;                            // producer: fills of its stage so far (never reset)
+    uint32_t fullpar = 0;                    // MMA thread: bit w = parity of stage w's next full phase
 
     for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
         const int4 it = P.items[item];
         const int t = it.x, tt0 = t / P.nt1, tt1 = t % P.nt1;
-        const int i0 = tt0 * P.T0, j0 = tt1 * P.T1;
-        const int e0 = min(P.T0, P.n0 - i0), e1 = min(P.T1, P.n1 - j0);
+        const int i0 = tt0 * T0, j0 = tt1 * P.T1;
+        const int e0 = min(T0, P.n0 - i0), e1 = min(P.T1, P.n1 - j0);
         // the tile's box (window test of the candidates)
         const float blo0 = P.x0 + P.h0 * i0, bhi0 = P.x0 + P.h0 * (i0 + e0 - 1);
         const float blo1 = P.x1 + P.h1 * j0, bhi1 = P.x1 + P.h1 * (j0 + e1 - 1);
         if (warp < PL_PROD) {
             // ------------------------------------------------ producers ----------------------------
-            int *q = queues + warp * PL_QUEUE;
+            const int w = warp;
+            float4 *q = queues + w * PL_QUEUE * 3;
             int qh = 0, qt = 0;
             const int h = lane >> 4, p = lane & 15;
             unsigned long long pairs = 0;
-            auto produce = [&](int nvalid) {
-                // claim the next block number and its stage
-                int n = 0;
-                if (lane == 0) n = atomicAdd(misc + 0, 1);
-                n = __shfl_sync(0xffffffffu, n, 0);
-                const int s = n % P.nst, use = n / P.nst;
+            unsigned char *st = smem + w * P.stage_bytes;
+            unsigned char *Are = st, *Are_lo = st + PL_A_COPY, *Aim = st + 2 * PL_A_COPY, *Aim_lo = st + 3 * PL_A_COPY;
+            unsigned char *Bre = st + 4 * PL_A_COPY, *Bre_lo = Bre + P.b_copy, *Bim = Bre + 2 * P.b_copy,
+                          *Bim_lo = Bre + 3 * P.b_copy;
+            // wait until the MMAs of this stage's previous block are done (exactly one phase back)
+            auto acquire = [&](int site, int n) -> bool {
                 bool ok = *abort_flag == 0;
-                if (use > 0 && ok) {
-                    bool w = true;
-                    if (lane == 0)
-                        w = wait_taken(misc + 3, n - P.nst + 1, P.err) &&
-                            bar_wait(tc::smem_u32(empty + s), (uint32_t)((use - 1) & 1), P.err);
-                    w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
-                    if (!w) {
+                if (uses > 0 && ok) {
+                    bool wt = true;
+                    if (lane == 0) wt = bar_wait(tc::smem_u32(empty + w), (uint32_t)((uses - 1) & 1), P.err);
+                    wt = __shfl_sync(0xffffffffu, wt ? 1 : 0, 0) != 0;
+                    if (!wt) {
                         if (lane == 0) {
                             *abort_flag = 1;
-                            report_timeout(P.err, 1, n, s, (use - 1) & 1, misc[0], misc[3]);
+                            report_timeout(P.err, site, n, w, (uses - 1) & 1, uses, misc[3]);
                         }
                         ok = false;
                     }
                 }
-                unsigned char *st = stages + s * P.stage_bytes;
-                unsigned char *Are = st, *Are_lo = st + PL_A_COPY, *Aim = st + 2 * PL_A_COPY,
-                              *Aim_lo = st + 3 * PL_A_COPY;
-                unsigned char *Bre = st + 4 * PL_A_COPY, *Bre_lo = Bre + P.b_copy, *Bim = Bre + 2 * P.b_copy,
-                              *Bim_lo = Bre + 3 * P.b_copy;
-                if (ok) {
-                    // the two beams of this lane
-                    float2 W[2][3];
-                    float2 f1[2], q1[2], f0[2], q0[2];
-                    float g1 = 1.f, g0 = 1.f;
+                return ok;
+            };
+            auto release = [&](int value) {
+                __syncwarp();
+                if (lane == 0) {
+                    hdr[w] = value;
+                    bar_arrive(tc::smem_u32(full + w));
+                }
+                uses++;
+            };
+            auto produce = [&](int nvalid) {
+                // factors of the lane's two beams, in registers, before the stage is needed
+                float2 W[2][3];
+                float2 f1[2], q1[2], f0[2], q0[2];
 #pragma unroll
-                    for (int u = 0; u < 2; u++) {
-                        const int slot = 2 * p + u;
-                        float r[REC];
-                        if (slot < nvalid) {
-                            const float4 *src = reinterpret_cast<const float4 *>(P.rec + (int64_t)q[(qh + slot) & (PL_QUEUE - 1)] * REC);
-                            const float4 a = src[0], b = src[1], c = src[2];
-                            r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
-                            r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
-                            r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
-                        } else {
+                for (int u = 0; u < 2; u++) {
+                    const int slot = 2 * p + u;
+                    float r[REC];
+                    if (slot < nvalid) {
+                        const float4 *src = q + ((qh + slot) & (PL_QUEUE - 1)) * 3;
+                        const float4 a = src[0], b = src[1], c = src[2];
+                        r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+                        r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+                        r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
+                    } else {
 #pragma unroll
-                            for (int f = 0; f < REC; f++) r[f] = 0.f;
-                        }
-                        // W_c = A_c E2 (scaled for the A operand); zero for padding beams
-                        const float dz = P.x2 - r[2];
-                        float er, ei;
-                        gauss_phase_exp<float>(P.k * r[5] * dz, hk * dz * dz, &er, &ei);
-                        const float scl = slot < nvalid ? sa : 0.f;
+                        for (int f = 0; f < REC; f++) r[f] = 0.f;
+                    }
+                    // W_c = A_c E2 (scaled for the A operand); zero for padding beams
+                    const float dz = P.x2 - r[2];
+                    float er, ei;
+                    gauss_phase_exp<float>(P.k * r[5] * dz, hk * dz * dz, &er, &ei);
+                    const float scl = slot < nvalid ? sa : 0.f;
 #pragma unroll
-                        for (int c = 0; c < 3; c++)
-                            W[u][c] = make_float2(scl * (r[6 + 2 * c] * er - r[7 + 2 * c] * ei),
-                                                  scl * (r[6 + 2 * c] * ei + r[7 + 2 * c] * er));
-                        // E1 at x_j, j = j0 + h J (start of this half), and its ratio for a step h1
-                        {
-                            const float d = P.x1 + P.h1 * (float)(j0 + h * J) - r[1];
-                            float a0r, a0i, rr, ri;
-                            gauss_phase_exp<float>(P.k * r[4] * d, hk * d * d, &a0r, &a0i);
-                            gauss_phase_exp<float>(P.k * r[4] * P.h1, -P.k * P.h1 * (d + 0.5f * P.h1), &rr, &ri);
-                            f1[u] = make_float2(a0r, a0i);
-                            q1[u] = make_float2(rr, ri);
-                        }
-                        // E0 at x_i, i = i0 + h (this lane's parity), and its ratio for a step 2 h0
-                        {
-                            const float d = P.x0 + P.h0 * (float)(i0 + h) - r[0];
-                            const float s2 = 2.f * P.h0;
-                            float a0r, a0i, rr, ri;
-                            gauss_phase_exp<float>(P.k * r[3] * d, hk * d * d, &a0r, &a0i);
-                            gauss_phase_exp<float>(P.k * r[3] * s2, -P.k * s2 * (d + 0.5f * s2), &rr, &ri);
-                            const float valid = slot < nvalid ? sb : 0.f;
-                            f0[u] = make_float2(valid * a0r, valid * a0i);
-                            q0[u] = make_float2(rr, ri);
-                        }
-                        if (COUNT && slot < nvalid) {
-                            // pairs of this beam inside the window, rows of this half
-                            const float dz2 = (P.x2 - r[2]) * (P.x2 - r[2]);
-                            for (int jj = h * J; jj < min(e1, (h + 1) * J); jj++) {
-                                const float dy = P.x1 + P.h1 * (float)(j0 + jj) - r[1];
-                                const float s2 = P.rw2 - dz2 - dy * dy;
-                                if (s2 < 0.f) continue;
-                                const float sq = sqrtf(s2);
-                                if (P.h0 > 0.f) {
-                                    const int lo = max(0, (int)ceilf((r[0] - sq - blo0) / P.h0));
-                                    const int hi = min(e0 - 1, (int)floorf((r[0] + sq - blo0) / P.h0));
-                                    if (hi >= lo) pairs += (unsigned long long)(hi - lo + 1);
-                                } else if (fabsf(r[0] - blo0) <= sq) {
-                                    pairs += 1ull;
-                                }
+                    for (int c = 0; c < 3; c++)
+                        W[u][c] = make_float2(scl * (r[6 + 2 * c] * er - r[7 + 2 * c] * ei),
+                                              scl * (r[6 + 2 * c] * ei + r[7 + 2 * c] * er));
+                    // E1 at x_j, j = j0 + h J (start of this half), and its ratio for a step h1
+                    {
+                        const float d = P.x1 + P.h1 * (float)(j0 + h * J) - r[1];
+                        float a0r, a0i, rr, ri;
+                        gauss_phase_exp<float>(P.k * r[4] * d, hk * d * d, &a0r, &a0i);
+                        gauss_phase_exp<float>(P.k * r[4] * P.h1, -P.k * P.h1 * (d + 0.5f * P.h1), &rr, &ri);
+                        f1[u] = make_float2(a0r, a0i);
+                        q1[u] = make_float2(rr, ri);
+                    }
+                    // E0 at x_i, i = i0 + h (this lane's parity), and its ratio for a step 2 h0
+                    {
+                        const float d = P.x0 + P.h0 * (float)(i0 + h) - r[0];
+                        const float s2 = 2.f * P.h0;
+                        float a0r, a0i, rr, ri;
+                        gauss_phase_exp<float>(P.k * r[3] * d, hk * d * d, &a0r, &a0i);
+                        gauss_phase_exp<float>(P.k * r[3] * s2, -P.k * s2 * (d + 0.5f * s2), &rr, &ri);
+                        const float valid = slot < nvalid ? sb : 0.f;
+                        f0[u] = make_float2(valid * a0r, valid * a0i);
+                        q0[u] = make_float2(rr, ri);
+                    }
+                    if (COUNT && slot < nvalid) {
+                        // pairs of this beam inside the window, rows of this half
+                        const float dz2 = (P.x2 - r[2]) * (P.x2 - r[2]);
+                        for (int jj = h * J; jj < min(e1, (h + 1) * J); jj++) {
+                            const float dy = P.x1 + P.h1 * (float)(j0 + jj) - r[1];
+                            const float s2 = P.rw2 - dz2 - dy * dy;
+                            if (s2 < 0.f) continue;
+                            const float sq = sqrtf(s2);
+                            if (P.h0 > 0.f) {
+                                const int lo = max(0, (int)ceilf((r[0] - sq - blo0) / P.h0));
+                                const int hi = min(e0 - 1, (int)floorf((r[0] + sq - blo0) / P.h0));
+                                if (hi >= lo) pairs += (unsigned long long)(hi - lo + 1);
+                            } else if (fabsf(r[0] - blo0) <= sq) {
+                                pairs += 1ull;
                             }
                         }
                     }
-                    g1 = __expf(-P.k * P.h1 * P.h1);
-                    g0 = __expf(-4.f * P.k * P.h0 * P.h0);
+                }
+                const float g1 = __expf(-P.k * P.h1 * P.h1);
+                const float g0 = __expf(-4.f * P.k * P.h0 * P.h0);
+                const bool ok = acquire(1, uses);
+                if (ok) {
                     // ---- A: rows r = 32 h + 3 t + c, j = h J + t ----
-                    for (int tj = 0; tj < J; tj++) {
+                    const uint32_t lanek = koff(0, 2 * p, 0) + (uint32_t)(h * 4 * PL_SBO_A);
+#pragma unroll
+                    for (int tj = 0; tj < (JT ? JT : J); tj++) {
 #pragma unroll
                         for (int c = 0; c < 3; c++) {
-                            const int row = 32 * h + 3 * tj + c;
+                            const int row = 3 * tj + c;   // within the half (the half's 32 rows = 4 row groups)
                             const float2 v0 = cmul(W[0][c], f1[0]), v1 = cmul(W[1][c], f1[1]);
                             uint32_t rh, rl, ih, il;
                             split2(v0.x, v1.x, rh, rl);
                             split2(v0.y, v1.y, ih, il);
-                            const uint32_t o = koff(row, 2 * p, PL_SBO_A);
+                            const uint32_t o = lanek + (uint32_t)((row >> 3) * PL_SBO_A + (row & 7) * 16);
                             sts32(Are, o, rh);
                             sts32(Are_lo, o, rl);
                             sts32(Aim, o, ih);
@@ -332,7 +342,11 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
                     }
                     // ---- B: B're = [Re E0; Im E0], B'im = [-Im E0; Re E0]; half 0 stores the Re words,
                     // half 1 the Im words; each half forms E0 on its parity and gets the other one ----
-                    for (int i2 = 0; i2 < P.T0; i2 += 2) {
+                    const uint32_t lanekb = koff(0, 2 * p, 0);
+                    const uint32_t rowoff_a = h == 0 ? 0u : (uint32_t)((NC >> 3) * SBOB);   // Re rows | Im rows
+                    const uint32_t rowoff_b = h == 0 ? (uint32_t)((NC >> 3) * SBOB) : 0u;
+#pragma unroll
+                    for (int i2 = 0; i2 < (T0T ? T0T : T0); i2 += 2) {
                         float2 mine[2] = {f0[0], f0[1]}, other[2];
 #pragma unroll
                         for (int u = 0; u < 2; u++) {
@@ -342,13 +356,13 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
 #pragma unroll
                         for (int par = 0; par < 2; par++) {
                             const int i = i2 + par;
-                            if (i >= P.T0) break;
+                            if (i >= (T0T ? T0T : T0)) break;
                             const float2 v0 = (par == h) ? mine[0] : other[0];
                             const float2 v1 = (par == h) ? mine[1] : other[1];
                             uint32_t wh, wl;
                             split2(h == 0 ? v0.x : v0.y, h == 0 ? v1.x : v1.y, wh, wl);
-                            const uint32_t ra = koff(h == 0 ? i : P.nc + i, 2 * p, P.sbo_b);
-                            const uint32_t rb = koff(h == 0 ? P.nc + i : i, 2 * p, P.sbo_b);
+                            const uint32_t ri = lanekb + (uint32_t)((i >> 3) * SBOB + (i & 7) * 16);
+                            const uint32_t ra = ri + rowoff_a, rb = ri + rowoff_b;
                             const uint32_t neg = h == 0 ? 0u : 0x80008000u;
                             sts32(Bre, ra, wh);
                             sts32(Bre_lo, ra, wl);
@@ -365,25 +379,43 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
                     // make the stores visible to the tensor cores, then hand the stage over
                     tc::fence_async_smem();
                 }
-                __syncwarp();
-                if (lane == 0) {
-                    hdr[s] = ok ? nvalid : 0;
-                    bar_arrive(tc::smem_u32(full + s));
-                }
+                release(ok ? nvalid : 0);
             };
-            // candidates of this warp: chunks of 32 records, round robin over the producers
-            for (int64_t c0 = (int64_t)it.y + 32 * warp; c0 < it.z; c0 += 32 * PL_PROD) {
-                const int64_t c = c0 + lane;
+            // candidates of this producer: chunks of 32 records dealt round robin over the producers; the
+            // next chunk's records are loaded (coalesced, one record per lane) while this one is filtered and
+            // its kept records are queued in shared memory and turned into blocks
+            const int64_t stride = 32 * PL_PROD;
+            int64_t c0 = (int64_t)it.y + 32 * w;
+            float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na, nc = na;
+            if (c0 + lane < it.z) {
+                const float4 *src = reinterpret_cast<const float4 *>(P.rec + (c0 + lane) * REC);
+                na = src[0];
+                nb = src[1];
+                nc = src[2];
+            }
+            for (; c0 < it.z; c0 += stride) {
+                const float4 ra = na, rb = nb, rc = nc;
+                const int64_t c = c0 + lane, cn = c + stride;
+                if (cn < it.z) {
+                    const float4 *src = reinterpret_cast<const float4 *>(P.rec + cn * REC);
+                    na = src[0];
+                    nb = src[1];
+                    nc = src[2];
+                }
                 bool kp = false;
                 if (c < it.z) {
-                    const float *qr = P.rec + c * REC;
-                    const float g0d = fmaxf(fmaxf(blo0 - qr[0], qr[0] - bhi0), 0.f);
-                    const float g1d = fmaxf(fmaxf(blo1 - qr[1], qr[1] - bhi1), 0.f);
-                    const float g2d = P.x2 - qr[2];
+                    const float g0d = fmaxf(fmaxf(blo0 - ra.x, ra.x - bhi0), 0.f);
+                    const float g1d = fmaxf(fmaxf(blo1 - ra.y, ra.y - bhi1), 0.f);
+                    const float g2d = P.x2 - ra.z;
                     kp = g0d * g0d + g1d * g1d + g2d * g2d <= P.rw2;
                 }
                 const unsigned bl = __ballot_sync(0xffffffffu, kp);
-                if (kp) q[(qt + __popc(bl & ((1u << lane) - 1u))) & (PL_QUEUE - 1)] = (int)c;
+                if (kp) {
+                    float4 *dst = q + ((qt + __popc(bl & ((1u << lane) - 1u))) & (PL_QUEUE - 1)) * 3;
+                    dst[0] = ra;
+                    dst[1] = rb;
+                    dst[2] = rc;
+                }
                 qt += __popc(bl);
                 __syncwarp();
                 if (qt - qh >= PL_KB) {
@@ -397,102 +429,109 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
                 for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
                 if (lane == 0 && pairs) atomicAdd(&g_plane_pairs, pairs);
             }
-            // all producers done with the item: one END block closes its sequence
-            asm volatile("bar.sync 1, %0;" ::"r"(PL_PROD * 32) : "memory");
-            if (warp == 0) {
-                int n = 0;
-                if (lane == 0) n = atomicAdd(misc + 0, 1);
-                n = __shfl_sync(0xffffffffu, n, 0);
-                const int s = n % P.nst, use = n / P.nst;
-                if (lane == 0) {
-                    bool w = true;
-                    if (use > 0 && *abort_flag == 0)
-                        w = wait_taken(misc + 3, n - P.nst + 1, P.err) &&
-                            bar_wait(tc::smem_u32(empty + s), (uint32_t)((use - 1) & 1), P.err);
-                    if (!w) {
-                        *abort_flag = 1;
-                        report_timeout(P.err, 2, n, s, (use - 1) & 1, misc[0], misc[3]);
-                    }
-                    hdr[s] = -1;
-                    bar_arrive(tc::smem_u32(full + s));
-                }
-                __syncwarp();
-            }
+            // this producer's part of the item is complete
+            acquire(2, uses);
+            release(-1);
         } else if (lane == 0) {
             // ------------------------------------------------ MMA issuer ---------------------------
-            const uint32_t idesc = tc::instr_desc(NR, 128);
+            const uint32_t idesc = tc::instr_desc(2 * NR, 128);
             bool started = false;
-            for (;;) {
-                const int s = mma_n % P.nst, use = mma_n / P.nst;
-                mma_n++;
-                bool w = bar_wait(tc::smem_u32(full + s), (uint32_t)(use & 1), P.err);
-                if (!w) {
-                    // no END will come in time: stop consuming (the producers time out as well)
+            unsigned active = (1u << PL_PROD) - 1u;
+            for (int w = 0; active != 0u; w = (w + 1 == PL_PROD) ? 0 : w + 1) {
+                if (!((active >> w) & 1u)) continue;
+                const uint32_t par = (fullpar >> w) & 1u;
+                if (!bar_wait(tc::smem_u32(full + w), par, P.err)) {
                     *abort_flag = 1;
-                    report_timeout(P.err, 3, mma_n - 1, s, use & 1, misc[0], misc[3]);
+                    report_timeout(P.err, 3, misc[3], w, (int)par, 0, misc[3]);
                     break;
                 }
-                *reinterpret_cast<volatile int *>(misc + 3) = mma_n;   // blocks taken so far
-                const int nb = hdr[s];
+                fullpar ^= 1u << w;
+                misc[3]++;
+                const int nb = hdr[w];
                 if (nb < 0) {
-                    bar_arrive(tc::smem_u32(empty + s));   // the END block holds no data
-                    break;
+                    active &= ~(1u << w);
+                    bar_arrive(tc::smem_u32(empty + w));   // the END block holds no data
+                    continue;
                 }
                 tc::fence_after();
                 if (nb > 0 && *abort_flag == 0) {
-                    const unsigned char *st = stages + s * P.stage_bytes;
+                    const unsigned char *st = smem + w * P.stage_bytes;
                     const uint32_t a_base = tc::smem_u32(st), b_base = tc::smem_u32(st + 4 * PL_A_COPY);
-                    for (int half = 0; half < 2; half++) {
-                        const uint32_t a_hi = a_base + (2 * half) * PL_A_COPY, a_lo = a_hi + PL_A_COPY;
-                        const uint32_t b_hi = b_base + (2 * half) * P.b_copy, b_lo = b_hi + P.b_copy;
-                        for (int ks = 0; ks < PL_KB / 16; ks++) {
-                            const uint32_t kof = ks * 2 * PL_LBO;
-                            const uint64_t dah = tc::smem_desc_lbo_sbo(a_hi + kof, PL_LBO, PL_SBO_A);
-                            const uint64_t dal = tc::smem_desc_lbo_sbo(a_lo + kof, PL_LBO, PL_SBO_A);
-                            const uint64_t dbh = tc::smem_desc_lbo_sbo(b_hi + kof, PL_LBO, P.sbo_b);
-                            const uint64_t dbl = tc::smem_desc_lbo_sbo(b_lo + kof, PL_LBO, P.sbo_b);
-                            tc::mma_f16(tmem, dah, dbh, idesc, started ? 1u : 0u);
+                    // one MMA per K step and re/im half: A = [A_hi; A_lo] (128 rows: the hi copy is followed by
+                    // the lo copy with the same row stride), B = [B_hi; B_lo] (4 n_c rows, likewise), so the
+                    // accumulator holds hi*hi (rows 0..63, columns 0..2n_c), hi*lo (rows 0..63, columns
+                    // 2n_c..4n_c) and lo*hi (rows 64..127, columns 0..2n_c); the lo*lo quarter is not used
+                    for (int ks = 0; ks < PL_KB / 16; ks++) {
+                        const uint32_t kof = ks * 2 * PL_LBO;
+                        for (int half = 0; half < 2; half++) {
+                            const uint32_t a_hi = a_base + (2 * half) * PL_A_COPY;
+                            const uint32_t b_hi = b_base + (2 * half) * P.b_copy;
+                            const uint64_t da = tc::smem_desc_lbo_sbo(a_hi + kof, PL_LBO, PL_SBO_A);
+                            const uint64_t db = tc::smem_desc_lbo_sbo(b_hi + kof, PL_LBO, SBOB);
+                            tc::mma_f16(tmem, da, db, idesc, started ? 1u : 0u);
                             started = true;
-                            tc::mma_f16(tmem, dah, dbl, idesc, 1u);
-                            tc::mma_f16(tmem, dal, dbh, idesc, 1u);
                         }
                     }
-                    tc::commit(tc::smem_u32(empty + s));
+                    tc::commit(tc::smem_u32(empty + w));
                 } else {
-                    bar_arrive(tc::smem_u32(empty + s));
+                    bar_arrive(tc::smem_u32(empty + w));
                 }
             }
             // every MMA of the item complete before the accumulator is read
             tc::commit(tc::smem_u32(done));
             if (!bar_wait(tc::smem_u32(done), done_par, P.err)) {
                 *abort_flag = 1;
-                report_timeout(P.err, 4, mma_n, 0, done_par, misc[0], misc[3]);
+                report_timeout(P.err, 4, misc[3], 0, (int)done_par, 0, misc[3]);
                 tc::mbar_drain(tc::smem_u32(done), done_par);
             }
             done_par ^= 1u;
             misc[2] = started ? 1 : 0;
         }
-        if (warp == PL_PROD) {
-            // lanes 1..31 of the MMA warp follow lane 0's block counter
-            mma_n = __shfl_sync(0xffffffffu, mma_n, 0);
-            done_par = __shfl_sync(0xffffffffu, done_par, 0);
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        // ---- epilogue (TMEM lane = accumulator row): warps 2 and 3 park the lo*hi rows (lanes 64..127) in
+        // the idle stage memory, then warps 0 and 1 add hi*hi + hi*lo + lo*hi of rows 0..63 and write the
+        // item's partial sums ----
+        const bool have = misc[2] != 0 && *abort_flag == 0;
+        float *park = reinterpret_cast<float *>(smem);   // [64][2 n_c]
+        if (warp == 2 || warp == 3) {
+            const int r = 32 * (warp - 2) + lane;
+            for (int c0 = 0; c0 < NR; c0 += 8) {
+                float v[8];
+                if (have) {
+                    tc::ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 8; u++) v[u] = 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u++) park[r * NR + c0 + u] = v[u];
+            }
         }
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
-        // ---- epilogue: TMEM lanes 0..63 (warps 0 and 1) -> the item's partial sums ----
         if (warp < 2) {
             const int row = 32 * warp + lane;
-            const int tj = (row & 31) / 3, c = (row & 31) - 3 * tj, j = warp * J + tj;
-            const bool have = misc[2] != 0 && *abort_flag == 0;
-            const bool rowok = (row & 31) < 3 * J && j < e1;
+            const int tj = lane / 3, c = lane - 3 * tj, j = warp * J + tj;
+            const bool rowok = lane < 3 * J && j < e1;
             const float inv = 1.0f / (sa * sb);
-            float *dst = P.partial + (int64_t)item * P.T0 * P.T1 * 6;
-            for (int c0 = 0; c0 < P.nc; c0 += 8) {
+            float *dst = P.partial + (int64_t)item * T0 * P.T1 * 6;
+            for (int c0 = 0; c0 < NC; c0 += 8) {
                 float re[8], im[8];
                 if (have) {
-                    tc::ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, re);
-                    tc::ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(P.nc + c0), im);
+                    float a[8], b[8];
+                    const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16);
+                    tc::ld8(base + (uint32_t)c0, re);
+                    tc::ld8(base + (uint32_t)(NC + c0), im);
+                    tc::ld8(base + (uint32_t)(NR + c0), a);
+                    tc::ld8(base + (uint32_t)(NR + NC + c0), b);
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        re[u] += a[u] + park[row * NR + c0 + u];
+                        im[u] += b[u] + park[row * NR + NC + c0 + u];
+                    }
                 } else {
 #pragma unroll
                     for (int u = 0; u < 8; u++) re[u] = im[u] = 0.f;
@@ -501,7 +540,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
 #pragma unroll
                     for (int u = 0; u < 8; u++) {
                         const int i = c0 + u;
-                        if (i < P.T0) {
+                        if (i < T0) {
                             const int pnt = i * P.T1 + j;
                             dst[pnt * 6 + 2 * c] = re[u] * inv;
                             dst[pnt * 6 + 2 * c + 1] = im[u] * inv;
@@ -541,14 +580,11 @@ fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec,
     const int nc = (T0 + 7) / 8 * 8;
     // row-group stride of the B copies: the Re rows (i) and Im rows (nc + i) stored by the two lane
     // halves in one instruction land 16 banks apart
-    int sbo_b = 576;
-    while (((nc / 8) * sbo_b) % 128 != 64) sbo_b += 16;
+    const int sbo_b = plane_sbo_b(nc);
     const int b_copy = (2 * nc / 8) * sbo_b;
     const int stage_bytes = (4 * PL_A_COPY + 4 * b_copy + 1023) / 1024 * 1024;
-    const int extra = PL_A_COPY + 2 * PL_STAGES * 8 + 8 + PL_STAGES * 4 + 8 * 4 + PL_PROD * PL_QUEUE * 4 + 64;
-    const int nst = std::min(PL_STAGES, (227 * 1024 - extra) / stage_bytes);
-    const int bytes = nst * stage_bytes + extra;
-    if (nst < 2) {
+    const int bytes = PL_PROD * stage_bytes + PL_A_COPY + 256 + PL_PROD * PL_QUEUE * 48;
+    if (bytes > 227 * 1024) {
         set_error("plane tile does not fit the tensor-core plane kernel");
         return FGA_ERR_UNSUPPORTED;
     }
@@ -573,7 +609,6 @@ fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec,
         A.sbo_b = sbo_b;
         A.b_copy = b_copy;
         A.stage_bytes = stage_bytes;
-        A.nst = nst;
         A.x0 = (float)plan.x_first[0];
         A.h0 = (float)plan.dx[0];
         A.x1 = (float)plan.x_first[1];
@@ -584,19 +619,33 @@ fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec,
         A.amax = amax;
         A.partial = ws.partial.as<float>();
         A.err = ws.status.as<int>();
-        A.tcols = 2 * nc <= 32 ? 32u : (2 * nc <= 64 ? 64u : 128u);
+        // the accumulator: 4 n_c columns (hi*hi and hi*lo side by side)
+        A.tcols = 4 * nc <= 32 ? 32u : (4 * nc <= 64 ? 64u : 128u);
         int dev = 0, sms = 152;
         FGA_CUDA(cudaGetDevice(&dev));
         FGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         const int grid = std::min(plan.nitems, sms);
         ProfScope ps(cat, s);
-        if (prof_counting()) {
-            FGA_CUDA(cudaFuncSetAttribute(plane_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-            plane_tc_kernel<true><<<grid, PL_THREADS, bytes, s>>>(A);
+        const int J = (T1 + 1) / 2;
+        const bool cnt = prof_counting();
+#define FGA_PLANE(CNT, JT, T0T)                                                                                   \
+    do {                                                                                                          \
+        FGA_CUDA(cudaFuncSetAttribute(plane_tc_kernel<CNT, JT, T0T>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      bytes));                                                                    \
+        plane_tc_kernel<CNT, JT, T0T><<<grid, PL_THREADS, bytes, s>>>(A);                                         \
+    } while (0)
+        // the receiver planes of the benchmark (20 x 20) and of the serving mix (16 x 16) unrolled
+        if (J == 10 && T0 == 20) {
+            if (cnt) FGA_PLANE(true, 10, 20);
+            else FGA_PLANE(false, 10, 20);
+        } else if (J == 8 && T0 == 16) {
+            if (cnt) FGA_PLANE(true, 8, 16);
+            else FGA_PLANE(false, 8, 16);
         } else {
-            FGA_CUDA(cudaFuncSetAttribute(plane_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-            plane_tc_kernel<false><<<grid, PL_THREADS, bytes, s>>>(A);
+            if (cnt) FGA_PLANE(true, 0, 0);
+            else FGA_PLANE(false, 0, 0);
         }
+#undef FGA_PLANE
         FGA_CUDA(cudaGetLastError());
     }
     FGA_TRY(lattice_reduce_f32(ws.partial.as<float>(), plan, u, s));
