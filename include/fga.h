@@ -184,7 +184,9 @@ fga_status fga_reconstruct_noalloc(const fga_beams *b, const double *x, int64_t 
  *  snap:  DEVICE float64 [n_snap][3] summed at t = nsteps*dt into snap_out DEVICE complex
  *         [n_snap][3] (may be NULL if n_snap = 0).  Or snap_lattice (non-NULL): n_snap and snap
  *         ignored, snap_out [n0][n1][n2][3].
- *  rw <= 0 selects 6/sqrt(k).  Synchronous: returns after the stream has finished the solve.
+ *  rw <= 0 selects 6/sqrt(k).  Device memory: the beam set, its sorted copy and a buffer of
+ *  reconstruction records of up to 48 GB (at most 40% of the free memory) per window of steps.
+ *  Synchronous: returns after the stream has finished the solve.
  *  Errors: INVALID_ARG, OOM, CUDA, NUMERIC (a non-finite value in the final beam state, the seismograms
  *  or the snapshot; the outputs are then unreliable), TIMEOUT (a bounded wait of the tensor-core
  *  Gaussian sum ran out; the outputs are incomplete). */

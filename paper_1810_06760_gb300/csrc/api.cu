@@ -507,7 +507,9 @@ fga_status fga_reconstruct(const fga_beams *b, const double *x, int64_t n, doubl
 
 fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, void *seis_out,
                      void *snap_out, fga_stream_t s_) {
-    return solve_impl(m, init, sd, seis_out, snap_out, (cudaStream_t)s_, 12.0e9);
+    // records of up to 48 GB per window of steps (at most 40% of the free device memory): fewer windows,
+    // so fewer sorts and fewer passes over the beam state
+    return solve_impl(m, init, sd, seis_out, snap_out, (cudaStream_t)s_, 48.0e9);
 }
 
 }  // extern "C"
