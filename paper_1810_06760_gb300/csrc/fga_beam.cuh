@@ -339,6 +339,12 @@ __device__ __forceinline__ void beam_rhs(const ModelDev &M, R sg, bool ref_e1, c
     }
 }
 
+// The same record from the end states and only the Q, P parts of the slopes (d0, d1: 6 values each
+// at offsets F_Q..F_P+2, as in the state).
+template <typename R, int WAVE>
+__device__ __forceinline__ void beam_record6(bool ref_e1, const R *y0, const R *d0, const R *y1, const R *d1, R dt,
+                                             R th, R w, R rec[REC]);
+
 // Reconstruction record at fraction th of a step of size dt: Q, P by cubic Hermite from
 // (y0, y0', y1, y1'), amplitudes linear in th; A = w a P^ (P) or w (a_sv N_sv + a_sh N_sh) (S).
 template <typename R, int WAVE>
@@ -373,6 +379,12 @@ __device__ __forceinline__ void beam_record(bool ref_e1, const R *y0, const R *d
             rec[7 + 2 * d] = a0i * Nsv[d] + a1i * Nsh[d];
         }
     }
+}
+
+template <typename R, int WAVE>
+__device__ __forceinline__ void beam_record6(bool ref_e1, const R *y0, const R *d0, const R *y1, const R *d1, R dt,
+                                             R th, R w, R rec[REC]) {
+    beam_record<R, WAVE>(ref_e1, y0, d0, y1, d1, dt, th, w, rec);   // reads only d[F_Q..F_P+2]
 }
 
 }  // namespace fga

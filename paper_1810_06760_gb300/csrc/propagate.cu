@@ -21,6 +21,13 @@ template <typename R> __device__ __forceinline__ void axpy_state(R *out, const R
     }
 }
 
+// One RHS evaluation per iteration of a single loop, so that the large right-hand side is compiled once
+// (four inlined copies overflowed the instruction cache).  Classical RK4 with k1 = f(y_n):
+//   e = 0: k2 = f(y + h/2 k1)   acc += h/3 k2,  tmp = y + h/2 k2
+//   e = 1: k3 = f(tmp)          acc += h/3 k3,  tmp = y + h k3
+//   e = 2: k4 = f(tmp)          acc += h/6 k4 (= y_{n+1}),  tmp = acc
+//   e = 3: k1' = f(y_{n+1})     records of the step; y = acc, acc = y + h/6 k1', tmp = y + h/2 k1'
+// Iteration -1 is an e = 3 without records: it forms k1 of the first step from y_0.
 template <typename R, int WAVE, int MED>
 __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st, const int32_t *__restrict__ flags,
                                                   int64_t cap, int64_t beg, int64_t n, R sg, R dt, int nsteps,
@@ -29,42 +36,46 @@ __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st
                                                   int64_t rec_lim, int64_t rec_stride) {
     const int64_t b = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= beg + n) return;
-    R y[NF];
+    R y[NF], acc[NF], tmp[NF], kk[NF];
 #pragma unroll
-    for (int f = 0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
+    for (int f = 0; f < NF; f++) {
+        y[f] = st[(int64_t)f * cap + b];
+        acc[f] = y[f];
+        tmp[f] = y[f];
+    }
     const bool ref_e1 = (flags[b] & FL_REF_E1) != 0;
-    R k1[NF];
-    beam_rhs<R, WAVE, MED>(M, sg, ref_e1, y, k1);
+    R s0[6];   // Q', P' at y_n (left slopes of the Hermite records)
     int js = 0;
     const R h2 = R(0.5) * dt, h3 = dt / R(3), h6 = dt / R(6);
-    for (int step = 0; step < nsteps; step++) {
-        R acc[NF], tmp[NF], kk[NF];
-        axpy_state<R>(acc, y, h6, k1);
-        axpy_state<R>(tmp, y, h2, k1);
+    for (int it = -1; it < 4 * nsteps; it++) {
+        const int e = it & 3;
         beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-        axpy_state<R>(acc, acc, h3, kk);
-        axpy_state<R>(tmp, y, h2, kk);
-        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-        axpy_state<R>(acc, acc, h3, kk);
-        axpy_state<R>(tmp, y, dt, kk);
-        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
-        axpy_state<R>(acc, acc, h6, kk);
-        // k1 of the next step = f(y_{n+1}); also the right-end slope of the Hermite interpolant
-        beam_rhs<R, WAVE, MED>(M, sg, ref_e1, acc, kk);
-        while (js < n_samp && samp_step[js] == step) {
-            if (b - beg < rec_lim) {
-                R r[REC];
-                beam_record<R, WAVE>(ref_e1, y, k1, acc, kk, dt, samp_theta[js], w, r);
-                R *dst = rec + ((int64_t)js * rec_stride + (b - beg)) * REC;
+        if (e == 3) {
+            const int step = it >> 2;
+            while (it >= 0 && js < n_samp && samp_step[js] == step) {
+                if (b - beg < rec_lim) {
+                    R r[REC];
+                    beam_record6<R, WAVE>(ref_e1, y, s0, acc, kk, dt, samp_theta[js], w, r);
+                    R *dst = rec + ((int64_t)js * rec_stride + (b - beg)) * REC;
 #pragma unroll
-                for (int q = 0; q < REC; q++) dst[q] = r[q];
+                    for (int q = 0; q < REC; q++) dst[q] = r[q];
+                }
+                js++;
             }
-            js++;
-        }
 #pragma unroll
-        for (int f = 0; f < NF; f++) {
-            y[f] = acc[f];
-            k1[f] = kk[f];
+            for (int f = 0; f < 6; f++) s0[f] = kk[f];
+#pragma unroll
+            for (int f = 0; f < NF; f++) y[f] = acc[f];
+        }
+        // acc += ca kk;  tmp = base + ct kk, base = y (e = 0, 1) or acc before its update (e = 2, 3; y for e = 3)
+        const R ca = e < 2 ? h3 : h6;
+        const R ct = e == 0 ? h2 : (e == 1 ? dt : (e == 2 ? h6 : h2));
+        if (e < 2) {
+            axpy_state<R>(tmp, y, ct, kk);
+            axpy_state<R>(acc, acc, ca, kk);
+        } else {
+            axpy_state<R>(tmp, acc, ct, kk);
+            axpy_state<R>(acc, acc, ca, kk);
         }
     }
 #pragma unroll
