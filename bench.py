@@ -54,6 +54,12 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="the crosswell gradient instead: 16 sources x 3.5 M beams, 200 steps, 256 receivers, L2 "
                          "misfit against data of the bumped model; time per gradient (forward + adjoint)")
+    ap.add_argument("--policy", default="shortest", choices=["fifo", "shortest"],
+                    help="with --serving: admission order (submission order, or least estimated work first with a "
+                         "2 s age bound)")
+    ap.add_argument("--requests", type=int, default=64, help="with --serving: requests in the stream")
+    ap.add_argument("--nmax", type=float, default=2e7,
+                    help="with --serving: largest drawn mesh size N (log-uniform in [1e5, nmax])")
     ap.add_argument("--misfit", default="l2", choices=["l2", "traveltime"],
                     help="with --adjoint: L2 waveform misfit, or cross-correlation traveltime misfit "
                          "(delays within +-20 samples) with its synthetic-only adjoint source")
@@ -458,7 +464,8 @@ def run_serving(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = fga.PREC_FP32 if args.precision == "fp32" else fga.PREC_FP64
-    reqs = W.serving_requests(n=64, seed=1)
+    reqs = W.serving_requests(n=args.requests, seed=1, n_range=(1e5, args.nmax))
+    policy = fga.SERVE_SHORTEST if args.policy == "shortest" else fga.SERVE_FIFO
     model = fga.model_from_medium(reqs[0].workload.medium, dev)
     # inputs resident before the timed region: per request its initial data, receivers, descriptor
     staged = []
@@ -471,7 +478,7 @@ def run_serving(args):
     n_workers = 4
 
     def run(arrivals, workers):
-        server = fga.Server(model, n_workers=workers)
+        server = fga.Server(model, n_workers=workers, policy=policy)
         t0 = time.perf_counter()
         ids = []
         for (w, desc, f, rx), ta in zip(staged, arrivals):
@@ -504,17 +511,22 @@ def run_serving(args):
     clocks = clk.stop()
     lat = sorted(i["t_end"] - i["t_submit"] for i in infos)
     q = lambda p: float(np.percentile(lat, p))
+    # slowdown: latency in the stream over the same request's service time alone
+    slow = sorted((i["t_end"] - i["t_submit"]) / max(sv, 1e-9) for i, sv in zip(infos, service))
     beam_steps = sum(w.n_beams * w.nsteps for w, *_ in staged)
     line = {
         "metric": METRIC,
         "value": beam_steps / wall, "unit": "beam-steps/s", "n_gpus": world, "steps": len(reqs), "warmup": 4,
         "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
-        "config": {"workload": "serving stream: 64 requests, Poisson arrivals (seed 1) at 0.7 x solo capacity, "
-                               "k in {32,64,128}, N log-uniform 1e5..2e7 -> q n_q^3 x p 8^3 x 4 classes, "
-                               "smooth 128^3 model resident, T=0.5 (200 steps), 256 rx (16x16 lattice) x 200 samples",
-                   "workers": n_workers, "parallelism": f"replicas x{world}"},
+        "config": {"workload": f"serving stream: {len(reqs)} requests, Poisson arrivals (seed 1) at 0.7 x solo "
+                               f"capacity, k in {{32,64,128}}, N log-uniform 1e5..{args.nmax:g} -> q n_q^3 x p 8^3 x 4 "
+                               "classes, smooth 128^3 model resident, T=0.5 (200 steps), 256 rx (16x16 lattice) x 200 "
+                               "samples",
+                   "workers": n_workers, "policy": args.policy, "parallelism": f"replicas x{world}"},
         "latency_s": {"p50": q(50), "p99": q(99), "max": lat[-1], "mean": float(np.mean(lat))},
+        "slowdown": {"p50": float(np.percentile(slow, 50)), "p99": float(np.percentile(slow, 99)),
+                     "max": slow[-1]},
         "solo": {"capacity_req_per_s": capacity, "service_s_p50": float(np.median(service)),
                  "beam_steps_per_s": beam_steps / solo_wall},
         "offered_rate_req_per_s": rate,

@@ -42,7 +42,8 @@ typedef enum {
     FGA_ERR_CUDA = 3,        /* a CUDA runtime call failed; the message has the CUDA error */
     FGA_ERR_TIMEOUT = 4,     /* a bounded wait ran out */
     FGA_ERR_NUMERIC = 5,     /* non-finite values in the beam state or the results (fga_solve) */
-    FGA_ERR_UNSUPPORTED = 6  /* valid request the library does not implement */
+    FGA_ERR_UNSUPPORTED = 6, /* valid request the library does not implement */
+    FGA_ERR_CANCELLED = 7    /* a served request was cancelled (fga_server_cancel) */
 } fga_status;
 
 enum { FGA_PREC_FP32 = 0, FGA_PREC_FP64 = 1 };
@@ -158,6 +159,16 @@ typedef struct {
 fga_status fga_reconstruct_lattice(const fga_beams *b, const fga_lattice *lat, double rw, void *u_out,
                                    fga_stream_t s);
 
+/* Step 3 at points given in spherical coordinates (Sec. 3, layered-Earth example: only the x of
+ * Eq. FGA changes, every other step is coordinate free): point q = (r, theta, phi), r the distance to
+ * the origin (the Earth's centre), theta the longitude and phi the latitude in radians, is summed at
+ *   x = (r cos(theta) cos(phi), r sin(theta) cos(phi), r sin(phi)).
+ * The conversion runs on the device in FP64; otherwise as fga_reconstruct.
+ *  rtp: DEVICE float64 [n][3];  u_out: DEVICE complex [n][3] (Cartesian components of u).
+ *  Errors: INVALID_ARG, OOM, CUDA. */
+fga_status fga_reconstruct_spherical(const fga_beams *b, const double *rtp, int64_t n, double rw, void *u_out,
+                                     fga_stream_t s);
+
 /* The same sum as fga_reconstruct, for callers that may not allocate device memory: code running
  * where cudaMalloc/cudaFree are unavailable or unsafe (a host callback, a real-time loop that must
  * not stall on the allocator's implicit synchronisation, a plug-in handed buffers by an outside
@@ -202,7 +213,13 @@ typedef struct {
     double rw;
     const fga_lattice *rx_lattice;
     const fga_lattice *snap_lattice;
+    /* FGA_COORDS_CARTESIAN (0, the default of a zeroed descriptor) or FGA_COORDS_SPHERICAL: the point
+     * arrays rx and snap then hold (r, theta, phi), converted in the library as fga_reconstruct_spherical
+     * does (lattices are Cartesian only). */
+    int coords;
 } fga_solve_desc;
+
+enum { FGA_COORDS_CARTESIAN = 0, FGA_COORDS_SPHERICAL = 1 };
 
 fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd,
                      void *seis_out, void *snap_out, fga_stream_t s);
@@ -246,7 +263,14 @@ typedef struct {
     int n_workers;
     double hbm_budget_bytes;
     double record_cap_bytes;
+    /* admission order: FGA_SERVE_FIFO (0, submission order) or FGA_SERVE_SHORTEST (the queued request
+     * with the least estimated work, beams x steps, first; a request queued for longer than
+     * age_limit_s (<= 0: 2 s) goes first, oldest first, so that no request starves) */
+    int policy;
+    double age_limit_s;
 } fga_server_desc;
+
+enum { FGA_SERVE_FIFO = 0, FGA_SERVE_SHORTEST = 1 };
 
 typedef struct {
     int status;       /* the request's fga_status */
@@ -274,6 +298,10 @@ fga_status fga_server_submit(fga_server *sv, const fga_init_desc *init, const fg
                              void *snap_out, int64_t *id);
 fga_status fga_server_wait(fga_server *sv, int64_t id, double timeout_s, fga_request_info *info);
 fga_status fga_server_stats(fga_server *sv, fga_server_stats_t *out);
+/* Cancel a request: a queued one is dropped at once, a running one stops at its next window of steps
+ * (its outputs are then incomplete).  Its fga_server_wait returns FGA_ERR_CANCELLED; a request that has
+ * already finished keeps its own status.  Errors: INVALID_ARG (unknown or collected id). */
+fga_status fga_server_cancel(fga_server *sv, int64_t id);
 fga_status fga_server_destroy(fga_server *sv);
 
 /* Reverse mode of fga_solve's seismograms (no counterpart in the paper, which uses the method as the
@@ -353,6 +381,15 @@ typedef struct {
 } fga_profile_t;
 fga_status fga_profile_enable(int mode);
 fga_status fga_profile_read(fga_profile_t *out, int reset);
+
+/* Upper bound on the device memory the library allocates for its own buffers (beam sets, sort and
+ * record scratch, cached blocks of the serving loop; not the caller's buffers, not the static scratch of
+ * fga_reconstruct_noalloc): an allocation that would pass it fails with FGA_ERR_OOM before cudaMalloc
+ * is called.  bytes <= 0 removes the bound (the default).  fga_device_memory_in_use reports the bytes
+ * currently allocated for such buffers.  Process-wide; meant for hosts that share a GPU, and for testing
+ * the out-of-memory paths without exhausting the device. */
+fga_status fga_set_device_memory_limit(double bytes);
+double fga_device_memory_in_use(void);
 
 /* Message of the last failing call on this thread (always NUL-terminated; truncated to cap). */
 void fga_last_error(char *buf, size_t cap);

@@ -311,6 +311,15 @@ def layered_step(model: Model, st: np.ndarray, meta: np.ndarray, path: np.ndarra
     return out[:n].copy(), mo[:n].copy(), po[:n].copy()
 
 
+def spherical_to_cartesian(rtp: np.ndarray) -> np.ndarray:
+    """Points (r, theta, phi) -> x = (r cos theta cos phi, r sin theta cos phi, r sin phi): the change of
+    the reconstruction point x of Eq. FGA that Sec. 3 uses for its spherical (layered-Earth) geometry,
+    r the distance to the centre, theta the longitude, phi the latitude (radians)."""
+    rtp = np.asarray(rtp, dtype=np.float64).reshape(-1, 3)
+    r, th, ph = rtp[:, 0], rtp[:, 1], rtp[:, 2]
+    return np.stack([r * np.cos(th) * np.cos(ph), r * np.sin(th) * np.cos(ph), r * np.sin(ph)], -1)
+
+
 def bin_keys_f32(Q: np.ndarray, origin, inv_h: float, nc) -> np.ndarray:
     Q = np.ascontiguousarray(Q, dtype=np.float32).reshape(-1, 3)
     o = np.ascontiguousarray(origin, dtype=np.float32).reshape(3)

@@ -1047,11 +1047,16 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
 
 using namespace fga;
 
-extern "C" fga_status fga_solve_vjp(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd,
+extern "C" fga_status fga_solve_vjp(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd_in,
                                     const void *ubar, double *grad_p, double *grad_s, int checkpoint_every,
                                     fga_stream_t s_) {
     cudaStream_t s = (cudaStream_t)s_;
-    FGA_CHECK(m && init && sd, "fga_solve_vjp: NULL argument");
+    FGA_CHECK(m && init && sd_in, "fga_solve_vjp: NULL argument");
+    // receivers given as (r, theta, phi): a Cartesian copy
+    fga_solve_desc sdc;
+    ScopedDevBuf rx_cart, snap_cart;
+    FGA_TRY(cartesian_desc(sd_in, sdc, rx_cart, snap_cart, s));
+    const fga_solve_desc *sd = &sdc;
     const int kind = m->dev.kind;
     if (kind != FGA_MEDIUM_GRID && kind != FGA_MEDIUM_CONST) {
         set_error("fga_solve_vjp: only grid (and constant) media are supported");

@@ -1,5 +1,6 @@
 // C ABI of the library (include/fga.h): handles, argument checks, and the solve orchestration.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -49,6 +50,21 @@ void *cache_take(std::multimap<size_t, void *> &c, size_t &total, size_t need, s
 }
 }  // namespace
 
+// device bytes held by the library's own buffers, and the caller's bound on them (0: none)
+std::atomic<int64_t> g_dev_bytes{0}, g_dev_limit{0};
+
+static cudaError_t dev_alloc(void **p, size_t need) {
+    const int64_t lim = g_dev_limit.load();
+    if (lim > 0 && g_dev_bytes.load() + (int64_t)need > lim) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, need);
+    if (e == cudaSuccess) g_dev_bytes += (int64_t)need;
+    return e;
+}
+static void dev_free(void *p, size_t bytes) {
+    cudaFree(p);
+    g_dev_bytes -= (int64_t)bytes;
+}
+
 void block_cache_enable(cudaStream_t s) {
     tl_cache.on = true;
     tl_cache.stream = s;
@@ -58,7 +74,7 @@ void block_cache_trim(size_t keep) {
     // largest blocks first
     while (tl_cache.dev_bytes > keep && !tl_cache.dev.empty()) {
         auto it = std::prev(tl_cache.dev.end());
-        cudaFree(it->second);
+        dev_free(it->second, it->first);
         tl_cache.dev_bytes -= it->first;
         tl_cache.dev.erase(it);
     }
@@ -84,11 +100,11 @@ fga_status DevBuf::ensure(size_t need) {
             return FGA_OK;
         }
     }
-    cudaError_t e = cudaMalloc(&p, need);
+    cudaError_t e = dev_alloc(&p, need);
     if (e == cudaErrorMemoryAllocation && tl_cache.on && tl_cache.dev_bytes > 0) {
         cudaGetLastError();
         block_cache_trim(0);
-        e = cudaMalloc(&p, need);
+        e = dev_alloc(&p, need);
     }
     if (e != cudaSuccess) {
         p = nullptr;
@@ -108,7 +124,7 @@ void DevBuf::release() {
             tl_cache.dev.emplace(bytes, p);
             tl_cache.dev_bytes += bytes;
         } else {
-            cudaFree(p);
+            dev_free(p, bytes);
         }
     }
     p = nullptr;
@@ -237,6 +253,45 @@ void prof_add_pairs_tested(int64_t n) {
 }  // namespace fga
 
 namespace fga {
+// x = (r cos(theta) cos(phi), r sin(theta) cos(phi), r sin(phi)) for points (r, theta, phi) (Sec. 3)
+__global__ void spherical_to_cartesian_kernel(const double *__restrict__ rtp, int64_t n, double *__restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double r = rtp[3 * i], th = rtp[3 * i + 1], ph = rtp[3 * i + 2];
+    double st, ct, sp, cp;
+    sincos(th, &st, &ct);
+    sincos(ph, &sp, &cp);
+    x[3 * i] = r * ct * cp;
+    x[3 * i + 1] = r * st * cp;
+    x[3 * i + 2] = r * sp;
+}
+
+fga_status spherical_points(const double *rtp, int64_t n, DevBuf &out, cudaStream_t s) {
+    FGA_TRY(out.ensure(sizeof(double) * 3 * (size_t)std::max<int64_t>(n, 1)));
+    if (n > 0) {
+        spherical_to_cartesian_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rtp, n, out.as<double>());
+        FGA_CUDA(cudaGetLastError());
+    }
+    return FGA_OK;
+}
+
+fga_status cartesian_desc(const fga_solve_desc *sd, fga_solve_desc &out, DevBuf &rx, DevBuf &snap, cudaStream_t s) {
+    out = *sd;
+    if (sd->coords == FGA_COORDS_CARTESIAN) return FGA_OK;
+    FGA_CHECK(sd->coords == FGA_COORDS_SPHERICAL, "solve descriptor: coords must be FGA_COORDS_CARTESIAN or _SPHERICAL");
+    FGA_CHECK(!sd->rx_lattice && !sd->snap_lattice, "solve descriptor: lattices take Cartesian coordinates only");
+    if (sd->n_rx > 0 && sd->rx) {
+        FGA_TRY(spherical_points(sd->rx, sd->n_rx, rx, s));
+        out.rx = rx.as<double>();
+    }
+    if (sd->n_snap > 0 && sd->snap) {
+        FGA_TRY(spherical_points(sd->snap, sd->n_snap, snap, s));
+        out.snap = snap.as<double>();
+    }
+    out.coords = FGA_COORDS_CARTESIAN;
+    return FGA_OK;
+}
+
 fga_status sync_layered_count(fga_beams *b, cudaStream_t s) {
     if (!b->layered) return FGA_OK;
     unsigned long long c[2] = {0, 0};
@@ -257,6 +312,13 @@ void fga_last_error(char *buf, size_t cap) {
 }
 
 int fga_version(void) { return 10000; }
+
+fga_status fga_set_device_memory_limit(double bytes) {
+    g_dev_limit.store(bytes > 0 ? (int64_t)bytes : 0);
+    return FGA_OK;
+}
+
+double fga_device_memory_in_use(void) { return (double)g_dev_bytes.load(); }
 
 fga_status fga_model_create(fga_model **out, const fga_model_desc *d, const float *grid_p, const float *grid_s,
                             fga_stream_t s_) {
@@ -505,16 +567,42 @@ fga_status fga_reconstruct(const fga_beams *b, const double *x, int64_t n, doubl
     return reconstruct_now(b, x, xh, n, rw, u_out, s);
 }
 
+fga_status fga_reconstruct_spherical(const fga_beams *b, const double *rtp, int64_t n, double rw, void *u_out,
+                                     fga_stream_t s_) {
+    cudaStream_t s = (cudaStream_t)s_;
+    FGA_CHECK(b, "fga_reconstruct_spherical: NULL beams");
+    FGA_CHECK(n >= 0, "fga_reconstruct_spherical: n < 0");
+    if (n == 0) return FGA_OK;
+    FGA_CHECK(rtp && u_out, "fga_reconstruct_spherical: NULL points or output");
+    FGA_CHECK(n < ((int64_t)1 << 31), "fga_reconstruct_spherical: too many points");
+    if (!(rw > 0)) rw = 6.0 / std::sqrt(b->k);
+    ScopedDevBuf x;
+    FGA_TRY(spherical_points(rtp, n, x, s));
+    std::vector<double> xh;
+    FGA_TRY(host_points(x.as<double>(), n, xh, s));   // synchronises s
+    FGA_TRY(sync_layered_count(const_cast<fga_beams *>(b), s));
+    FGA_TRY(reconstruct_now(b, x.as<double>(), xh, n, rw, u_out, s));
+    FGA_CUDA(cudaStreamSynchronize(s));   // the converted points are released with this scope
+    return FGA_OK;
+}
+
 fga_status fga_solve(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, void *seis_out,
                      void *snap_out, fga_stream_t s_) {
     // records of up to 48 GB per window of steps (at most 40% of the free device memory): fewer windows,
     // so fewer sorts and fewer passes over the beam state
-    return solve_impl(m, init, sd, seis_out, snap_out, (cudaStream_t)s_, 48.0e9);
+    return solve_impl(m, init, sd, seis_out, snap_out, (cudaStream_t)s_, 48.0e9, nullptr);
 }
 
 }  // extern "C"
 
 namespace fga {
+// a cancelled solve: its stream drained before the beam set is freed
+static fga_status cancelled(cudaStream_t s) {
+    cudaStreamSynchronize(s);
+    set_error("the request was cancelled");
+    return FGA_ERR_CANCELLED;
+}
+
 // non-finite values in the final beam state, the seismograms or the snapshot of a solve (status word 1)
 static fga_status flag_solve_nonfinite(const fga_beams *b, const fga_solve_desc *sd, int64_t nrx, bool seis,
                                        const void *seis_out, const void *snap_out, cudaStream_t s) {
@@ -527,10 +615,15 @@ static fga_status flag_solve_nonfinite(const fga_beams *b, const fga_solve_desc 
     return FGA_OK;
 }
 
-fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, void *seis_out,
-                      void *snap_out, cudaStream_t s, double rec_cap) {
+fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd_in, void *seis_out,
+                      void *snap_out, cudaStream_t s, double rec_cap, const std::atomic<int> *cancel) {
     fga_stream_t s_ = (fga_stream_t)s;
-    FGA_CHECK(m && init && sd, "fga_solve: NULL argument");
+    FGA_CHECK(m && init && sd_in, "fga_solve: NULL argument");
+    // receivers and snapshot points given as (r, theta, phi): Cartesian copies for the rest of the solve
+    fga_solve_desc sdc;
+    ScopedDevBuf rx_cart, snap_cart;
+    FGA_TRY(cartesian_desc(sd_in, sdc, rx_cart, snap_cart, s));
+    const fga_solve_desc *sd = &sdc;
     FGA_CHECK(sd->nsteps >= 1 && std::isfinite(sd->dt) && sd->dt != 0.0, "fga_solve: nsteps >= 1 and dt != 0");
     FGA_CHECK(sd->n_times >= 0 && sd->n_rx >= 0 && sd->n_snap >= 0, "fga_solve: negative counts");
     FGA_CHECK(sd->n_times == 0 || sd->times, "fga_solve: times is NULL");
@@ -614,6 +707,7 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
         }
         int js = 0;
         for (int n = 1; n <= sd->nsteps; n++) {
+            if (cancel && cancel->load()) return cancelled(s);
             FGA_TRY(launch_layered_steps(m, b, sd->dt, 1, s));
             if (!seis || js >= sd->n_times || at[(size_t)js] != n) continue;
             FGA_TRY(sync_layered_count(b, s));
@@ -640,6 +734,7 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
     const double rec_budget = std::min(rec_cap, 0.4 * (double)free_b);
     int js = 0;
     for (int n0 = 0; n0 < sd->nsteps;) {
+        if (cancel && cancel->load()) return cancelled(s);
         int nw = std::min(W, sd->nsteps - n0);
         int j1 = js;
         while (seis && j1 < sd->n_times && sstep[(size_t)j1] < n0 + nw) j1++;

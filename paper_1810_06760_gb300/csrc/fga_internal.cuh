@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -198,9 +199,13 @@ fga_status launch_propagate(const fga_model *m, fga_beams *b, double dt, int nst
 // position beg[c] (perm: sorted position -> beam), written at rec_off[c] + (position - beg[c])
 fga_status launch_records_from_state(const fga_beams *b, const int32_t *perm, const int64_t beg[4],
                                      const int64_t n_in[4], const int64_t rec_off[4], void *rec, cudaStream_t s);
+// api.cu: points (r, theta, phi) -> Cartesian device copies (Sec. 3); a solve descriptor with its spherical
+// point arrays replaced by Cartesian copies held in rx / snap
+fga_status spherical_points(const double *rtp, int64_t n, DevBuf &out, cudaStream_t s);
+fga_status cartesian_desc(const fga_solve_desc *sd, fga_solve_desc &out, DevBuf &rx, DevBuf &snap, cudaStream_t s);
 // api.cu: the whole forward solve (fga_solve) with a cap on the record buffer of one window
 fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, void *seis_out,
-                      void *snap_out, cudaStream_t s, double rec_cap);
+                      void *snap_out, cudaStream_t s, double rec_cap, const std::atomic<int> *cancel);
 // layered.cu
 fga_status launch_layered_steps(const fga_model *m, fga_beams *b, double dt, int nsteps, cudaStream_t s);
 // layered media: refresh b->nb from the device slot counter (synchronises s)

@@ -3,8 +3,11 @@
 //
 // * Admission by HBM footprint: each request's peak device memory is estimated from its sizes
 //   (beam state and its sorted copy, sort keys, decomposition temporaries, a capped record buffer);
-//   requests start in arrival order while the sum over running requests stays within the budget
-//   (a request is always admitted when nothing runs, so an oversized one fails on its own).
+//   requests start while the sum over running requests stays within the budget (a request is always
+//   admitted when nothing runs, so an oversized one fails on its own).  Order: submission order, or
+//   the least estimated work (beams x steps) first with an age bound that serves any request waiting
+//   longer than the limit first (oldest first).
+// * Cancellation: a queued request is dropped; a running one stops at its next window of steps.
 // * Continuous batching on streams: each worker thread owns a non-blocking stream and runs one
 //   admitted request at a time through the solve pipeline; requests on different workers share
 //   the GPU, so the kernels of small requests fill the SMs together.  Workers keep the device and
@@ -13,6 +16,7 @@
 // * Latency: submit, start and end times (host steady clock; end after the request's stream has
 //   drained) per request.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cmath>
@@ -40,6 +44,8 @@ struct Request {
     void *seis_out = nullptr, *snap_out = nullptr;
     double bytes = 0.0;
     int64_t beams = 0;
+    double work = 0.0;                         // estimated work: beams x steps
+    std::atomic<int> cancel{0};
     // results
     bool done = false;
     fga_status status = FGA_OK;
@@ -75,9 +81,11 @@ struct fga_server {
     const fga_model *model = nullptr;
     int n_workers = 0;
     double budget = 0.0, rec_cap = 0.0;
+    int policy = FGA_SERVE_FIFO;
+    double age_limit = 2.0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<fga::Request *> queue;
+    std::deque<fga::Request *> queue;   // submission order
     std::unordered_map<int64_t, fga::Request *> all;
     int64_t next_id = 1;
     double inflight_bytes = 0.0, peak_bytes = 0.0;
@@ -89,6 +97,18 @@ struct fga_server {
     std::vector<cudaStream_t> streams;
     int device = 0;
 
+    // the queued request to start next (caller holds mu; queue not empty): FIFO, or the least
+    // estimated work unless the oldest request has waited longer than the age limit
+    std::deque<fga::Request *>::iterator pick() {
+        if (policy != FGA_SERVE_SHORTEST) return queue.begin();
+        const auto now = fga::Clock::now();
+        if (std::chrono::duration<double>(now - queue.front()->t_submit).count() > age_limit) return queue.begin();
+        auto best = queue.begin();
+        for (auto it = queue.begin(); it != queue.end(); ++it)
+            if ((*it)->work < (*best)->work) best = it;
+        return best;
+    }
+
     void worker_main(int w) {
         cudaSetDevice(device);
         cudaStream_t s = streams[(size_t)w];
@@ -97,14 +117,20 @@ struct fga_server {
             fga::Request *r = nullptr;
             {
                 std::unique_lock<std::mutex> lk(mu);
-                cv_work.wait(lk, [&] {
-                    if (queue.empty()) return stop;
-                    const fga::Request *h = queue.front();
-                    return running == 0 || inflight_bytes + h->bytes <= budget;
-                });
+                // wake up at least every 50 ms so that the age limit is honoured while requests wait
+                for (;;) {
+                    if (queue.empty()) {
+                        if (stop) break;
+                    } else {
+                        const fga::Request *h = *pick();
+                        if (running == 0 || inflight_bytes + h->bytes <= budget) break;
+                    }
+                    cv_work.wait_for(lk, std::chrono::milliseconds(50));
+                }
                 if (queue.empty()) break;  // stop requested and nothing left
-                r = queue.front();
-                queue.pop_front();
+                auto it = pick();
+                r = *it;
+                queue.erase(it);
                 inflight_bytes += r->bytes;
                 running++;
                 peak_bytes = std::max(peak_bytes, inflight_bytes);
@@ -112,7 +138,8 @@ struct fga_server {
                 r->worker = w;
                 r->t_start = fga::Clock::now();
             }
-            const fga_status st = fga::solve_impl(model, &r->init, &r->sd, r->seis_out, r->snap_out, s, rec_cap);
+            const fga_status st =
+                fga::solve_impl(model, &r->init, &r->sd, r->seis_out, r->snap_out, s, rec_cap, &r->cancel);
             cudaStreamSynchronize(s);
             std::string err;
             if (st != FGA_OK) {
@@ -156,6 +183,9 @@ fga_status fga_server_create(fga_server **out, const fga_model *m, const fga_ser
     FGA_CUDA(cudaMemGetInfo(&free_b, &total_b));
     sv->budget = d->hbm_budget_bytes > 0 ? d->hbm_budget_bytes : 0.85 * (double)free_b;
     sv->rec_cap = d->record_cap_bytes > 0 ? d->record_cap_bytes : 2.0e9;
+    FGA_CHECK(d->policy == FGA_SERVE_FIFO || d->policy == FGA_SERVE_SHORTEST, "fga_server_create: unknown policy");
+    sv->policy = d->policy;
+    sv->age_limit = d->age_limit_s > 0 ? d->age_limit_s : 2.0;
     sv->t0 = Clock::now();
     for (int w = 0; w < d->n_workers; w++) {
         cudaStream_t s = nullptr;
@@ -207,6 +237,7 @@ fga_status fga_server_submit(fga_server *sv, const fga_init_desc *init, const fg
     r->bytes = estimate_solve_bytes(init, sv->rec_cap);
     r->beams = (int64_t)std::pow((double)init->nq, 3) * (int64_t)std::pow((double)init->np, 3) *
                popcount4(init->class_mask);
+    r->work = (double)r->beams * std::max(sd->nsteps, 1);
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         FGA_CHECK(!sv->stop, "fga_server_submit: server is shutting down");
@@ -250,6 +281,32 @@ fga_status fga_server_wait(fga_server *sv, int64_t id, double timeout_s, fga_req
     sv->all.erase(it);
     delete r;
     return st;
+}
+
+fga_status fga_server_cancel(fga_server *sv, int64_t id) {
+    FGA_CHECK(sv, "fga_server_cancel: NULL server");
+    bool dropped = false;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->all.find(id);
+        FGA_CHECK(it != sv->all.end(), "fga_server_cancel: unknown or already collected request id");
+        Request *r = it->second;
+        if (r->done) return FGA_OK;
+        auto q = std::find(sv->queue.begin(), sv->queue.end(), r);
+        if (q != sv->queue.end()) {   // not started: finished at once
+            sv->queue.erase(q);
+            r->t_start = r->t_end = Clock::now();
+            r->status = FGA_ERR_CANCELLED;
+            r->error = "the request was cancelled before it started";
+            r->done = true;
+            sv->completed++;
+            dropped = true;
+        } else {
+            r->cancel.store(1);      // running: stops at its next window of steps
+        }
+    }
+    if (dropped) sv->cv_done.notify_all();
+    return FGA_OK;
 }
 
 fga_status fga_server_stats(fga_server *sv, fga_server_stats_t *out) {

@@ -17,14 +17,18 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfga_gb300.so")
 
-FGA_OK, FGA_ERR_INVALID_ARG, FGA_ERR_OOM, FGA_ERR_CUDA, FGA_ERR_TIMEOUT, FGA_ERR_NUMERIC, FGA_ERR_UNSUPPORTED = range(7)
+(FGA_OK, FGA_ERR_INVALID_ARG, FGA_ERR_OOM, FGA_ERR_CUDA, FGA_ERR_TIMEOUT, FGA_ERR_NUMERIC, FGA_ERR_UNSUPPORTED,
+ FGA_ERR_CANCELLED) = range(8)
+SERVE_FIFO, SERVE_SHORTEST = 0, 1
 PREC_FP32, PREC_FP64 = 0, 1
 MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
 EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_transform", "fga_propagate", "fga_reconstruct",
+            "fga_reconstruct_spherical",
             "fga_reconstruct_lattice", "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export",
             "fga_beams_export_all", "fga_beams_destroy", "fga_bin", "fga_profile_enable", "fga_profile_read",
             "fga_solve_vjp", "fga_server_create", "fga_server_submit", "fga_server_wait", "fga_server_stats",
-            "fga_server_destroy", "fga_traveltime_adjoint", "fga_last_error", "fga_version"]
+            "fga_server_destroy", "fga_server_cancel", "fga_traveltime_adjoint", "fga_set_device_memory_limit",
+            "fga_device_memory_in_use", "fga_last_error", "fga_version"]
 PROFILE_CATEGORIES = ["decompose", "propagate", "binning", "records", "gauss_sum", "gauss_reduce", "gauss_sum_state",
                       "interfaces", "adjoint_forward", "adjoint_reverse", "adjoint_init", "misfit"]
 
@@ -56,7 +60,8 @@ class Profile(C.Structure):
 
 
 class ServerDesc(C.Structure):
-    _fields_ = [("n_workers", C.c_int), ("hbm_budget_bytes", C.c_double), ("record_cap_bytes", C.c_double)]
+    _fields_ = [("n_workers", C.c_int), ("hbm_budget_bytes", C.c_double), ("record_cap_bytes", C.c_double),
+                ("policy", C.c_int), ("age_limit_s", C.c_double)]
 
 
 class RequestInfo(C.Structure):
@@ -76,7 +81,7 @@ class Lattice(C.Structure):
 class SolveDesc(C.Structure):
     _fields_ = [("dt", C.c_double), ("nsteps", C.c_int), ("n_times", C.c_int), ("times", C.c_void_p),
                 ("n_rx", C.c_int64), ("rx", C.c_void_p), ("n_snap", C.c_int64), ("snap", C.c_void_p),
-                ("rw", C.c_double), ("rx_lattice", C.c_void_p), ("snap_lattice", C.c_void_p)]
+                ("rw", C.c_double), ("rx_lattice", C.c_void_p), ("snap_lattice", C.c_void_p), ("coords", C.c_int)]
 
 
 def make_lattice(axes):
@@ -109,6 +114,7 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_propagate.argtypes = [vp, vp, C.c_double, i32, vp]
     L.fga_reconstruct.argtypes = [vp, vp, i64, C.c_double, vp, vp]
     L.fga_reconstruct_noalloc.argtypes = [vp, vp, i64, C.c_double, vp, vp]
+    L.fga_reconstruct_spherical.argtypes = [vp, vp, i64, C.c_double, vp, vp]
     L.fga_reconstruct_lattice.argtypes = [vp, C.POINTER(Lattice), C.c_double, vp, vp]
     L.fga_solve.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(SolveDesc), vp, vp, vp]
     L.fga_solve_vjp.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(SolveDesc), vp, vp, vp, i32, vp]
@@ -117,6 +123,9 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_server_wait.argtypes = [vp, i64, C.c_double, C.POINTER(RequestInfo)]
     L.fga_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
     L.fga_server_destroy.argtypes = [vp]
+    L.fga_server_cancel.argtypes = [vp, i64]
+    L.fga_set_device_memory_limit.argtypes = [C.c_double]
+    L.fga_device_memory_in_use.argtypes = []
     L.fga_beams_count.argtypes = [vp, vp]
     L.fga_beams_export.argtypes = [vp, vp, vp]
     L.fga_beams_export_all.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
@@ -128,8 +137,9 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_last_error.argtypes = [C.c_char_p, C.c_size_t]
     L.fga_last_error.restype = None
     L.fga_version.restype = C.c_int
+    L.fga_device_memory_in_use.restype = C.c_double
     for name in EXPORTED:
-        if name not in ("fga_last_error", "fga_version"):
+        if name not in ("fga_last_error", "fga_version", "fga_device_memory_in_use"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -322,6 +332,18 @@ def reconstruct(beams: Beams, x, rw: float = 0.0, out=None, stream=None):
     return out
 
 
+def reconstruct_spherical(beams: Beams, rtp, rw: float = 0.0, out=None, stream=None):
+    """u at points given as (r, theta, phi) (float64 CUDA tensor [n, 3]; theta longitude, phi latitude):
+    the sum of Eq. FGA at x = (r cos theta cos phi, r sin theta cos phi, r sin phi).  Returns complex [n, 3]."""
+    import torch
+    n = rtp.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=_cdtype(beams.precision), device=rtp.device)
+    _check(lib().fga_reconstruct_spherical(beams.h, _dptr(rtp) if n else None, n, float(rw), _dptr(out) if n else None,
+                                           _stream(stream)))
+    return out
+
+
 def reconstruct_lattice(beams: Beams, axes, rw: float = 0.0, out=None, stream=None):
     """u at the lattice points (axes[0][i], axes[1][j], axes[2][l]); returns complex [n0, n1, n2, 3]."""
     import torch
@@ -344,13 +366,15 @@ def reconstruct_noalloc(beams: Beams, x, out, rw: float = 0.0, stream=None):
 
 
 def solve(model: Model, desc: InitDesc, dt: float, nsteps: int, times, rx=None, snap=None, rw: float = 0.0,
-          seis_out=None, snap_out=None, stream=None, rx_axes=None, snap_axes=None):
+          seis_out=None, snap_out=None, stream=None, rx_axes=None, snap_axes=None, spherical: bool = False):
     """Whole forward solve.  Receivers: points rx [n_rx, 3] (CUDA float64) or a lattice rx_axes (three
     1-D arrays); snapshot likewise (snap or snap_axes).  Returns (seismograms [n_times, n_rx, 3] or
-    [n_times, n0, n1, n2, 3], snapshot [n_snap, 3] or [n0, n1, n2, 3]); None where not requested."""
+    [n_times, n0, n1, n2, 3], snapshot [n_snap, 3] or [n0, n1, n2, 3]); None where not requested.
+    spherical: the point arrays hold (r, theta, phi) (fga_solve_desc.coords = FGA_COORDS_SPHERICAL)."""
     import torch
     times = np.ascontiguousarray(times, dtype=np.float64)
     sd = SolveDesc()
+    sd.coords = 1 if spherical else 0
     sd.dt, sd.nsteps = float(dt), int(nsteps)
     sd.n_times, sd.times = times.size, times.ctypes.data if times.size else None
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -440,8 +464,9 @@ class Server:
     (seconds since the server started).  Tensors a request uses are kept alive until it is waited."""
 
     def __init__(self, model: Model, n_workers: int = 4, hbm_budget_bytes: float = 0.0,
-                 record_cap_bytes: float = 0.0):
-        d = ServerDesc(int(n_workers), float(hbm_budget_bytes), float(record_cap_bytes))
+                 record_cap_bytes: float = 0.0, policy: int = SERVE_FIFO, age_limit_s: float = 0.0):
+        d = ServerDesc(int(n_workers), float(hbm_budget_bytes), float(record_cap_bytes), int(policy),
+                       float(age_limit_s))
         h = C.c_void_p()
         _check(lib().fga_server_create(C.byref(h), model.h, C.byref(d)))
         self.h, self.model, self._keep = h, model, {}
@@ -485,6 +510,10 @@ class Server:
         return kept[3], {"worker": info.worker, "t_submit": info.t_submit, "t_start": info.t_start,
                          "t_end": info.t_end, "bytes": info.bytes, "beams": info.beams}
 
+    def cancel(self, rid: int) -> None:
+        """fga_server_cancel: drop a queued request, stop a running one at its next window of steps."""
+        _check(lib().fga_server_cancel(self.h, int(rid)))
+
     def stats(self) -> dict:
         st = ServerStats()
         _check(lib().fga_server_stats(self.h, C.byref(st)))
@@ -500,6 +529,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def set_device_memory_limit(nbytes: float) -> None:
+    """fga_set_device_memory_limit: bound on the library's own device allocations (<= 0: none)."""
+    _check(lib().fga_set_device_memory_limit(float(nbytes)))
+
+
+def device_memory_in_use() -> float:
+    return float(lib().fga_device_memory_in_use())
 
 
 def profile_enable(mode: int) -> None:

@@ -491,3 +491,24 @@ def test_binning_keys_and_stable_sort(oracle):
     perm, start = O.bin_sort(key, ncell)
     np.testing.assert_array_equal(perm, np.argsort(key, kind="stable"))
     np.testing.assert_array_equal(start, np.searchsorted(np.sort(key), np.arange(ncell + 1)))
+
+
+# ---------------------------------------------------------------------------------------------
+# spherical reconstruction points (Sec. 3: only the x of Eq. FGA changes)
+# ---------------------------------------------------------------------------------------------
+
+def test_spherical_points(oracle):
+    """(r, theta, phi) with theta the longitude and phi the latitude: the equator at longitude 0 is the
+    x1 axis, longitude pi/2 the x2 axis, latitude pi/2 the x3 axis (north pole); |x| = r, the longitude is
+    atan2(x2, x1) and the latitude asin(x3/r) for any point."""
+    O = oracle
+    x = O.spherical_to_cartesian([[2.0, 0.0, 0.0], [3.0, math.pi / 2, 0.0], [1.5, 0.7, math.pi / 2],
+                                  [1.0, math.pi, -math.pi / 2]])
+    np.testing.assert_allclose(x, [[2, 0, 0], [0, 3, 0], [0, 0, 1.5], [0, 0, -1]], atol=1e-15)
+    rng = np.random.default_rng(5)
+    rtp = np.stack([rng.uniform(0.1, 7.0, 200), rng.uniform(-math.pi, math.pi, 200),
+                    rng.uniform(-1.5, 1.5, 200)], -1)
+    x = O.spherical_to_cartesian(rtp)
+    np.testing.assert_allclose(np.linalg.norm(x, axis=1), rtp[:, 0], rtol=1e-14)
+    np.testing.assert_allclose(np.arctan2(x[:, 1], x[:, 0]), rtp[:, 1], atol=1e-13)
+    np.testing.assert_allclose(np.arcsin(x[:, 2] / rtp[:, 0]), rtp[:, 2], atol=1e-12)
