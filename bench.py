@@ -32,10 +32,9 @@ FLOP_PER_PAIR_IN = 43.0       # dx, r^2, phase, exponent, e*(cos, sin), 3 comple
 FLOP_PER_PAIR_OUT = 9.0       # dx, r^2, compare
 MUFU_PER_PAIR_IN = 3.0        # exp2, sin, cos
 FLOP_PER_LATTICE_PAIR_IN = 26.0   # window test (add, compare) + 3 complex multiply-adds
-# DRAM bytes per launch of the tensor-core lattice sum on the full smooth workload, from ncu
-# (dram__bytes_read + write = 384 MB per launch at 6.33 M records per sample on the medium case,
-# 60.6 B per record), scaled to the full workload's ~18 M records per sample; see profiles/
-LATTICE_TC_TRAFFIC_BYTES = 1.09e9
+# DRAM bytes (dram__bytes_read + write) per launch of each category's kernel on the full smooth workload,
+# from ncu captures summarised under profiles/; a category is absent until its current kernel is captured
+TRAFFIC_BYTES_PER_LAUNCH = {}
 
 
 def parse():
@@ -54,6 +53,16 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="the crosswell gradient instead: 16 sources x 3.5 M beams, 200 steps, 256 receivers, L2 "
                          "misfit against data of the bumped model; time per gradient (forward + adjoint)")
+    ap.add_argument("--point-source", action="store_true",
+                    help="the paper's accuracy experiment instead: point force at (64,64,64) km, f = 1.4702 Hz; the FGA "
+                         "starts at t0 = 3 s from the radiated field and is compared with the analytic solution at "
+                         "6.93 s on a 697-receiver patch (time per solve, beam-steps/s, relative error)")
+    ap.add_argument("--k", type=float, default=0.08, help="with --point-source: the FGA parameter k (1/km)")
+    ap.add_argument("--layered", action="store_true",
+                    help="the layered-crust workload instead: explosive source at 10 km depth, interfaces at 15 and "
+                         "35 km, 10^3 q x 8^3 p x 4 classes (2.05 M beams) with psi selection 1e-6, 120 s at "
+                         "dt = 0.01 s (12,000 steps), 256 surface stations (16 x 16 over +-300 km) every 0.1 s; "
+                         "plus the FP32 error against FP64 on a 5^3 q x 4^3 p stride sample of it")
     ap.add_argument("--policy", default="shortest", choices=["fifo", "shortest"],
                     help="with --serving: admission order (submission order, or least estimated work first with a "
                          "2 s age bound)")
@@ -284,8 +293,13 @@ def run_ours(args):
     step()
     torch.cuda.synchronize()
     cnt = fga.profile_read(reset=True)
+    # and of the same solve without the snapshot: the receivers' share
+    fga.solve(model, desc, w.dt, w.nsteps, w.times, rw=w.rw, seis_out=seis, rx_axes=w.rx_axes)
+    torch.cuda.synchronize()
+    cnt_rx = fga.profile_read(reset=True)
     fga.profile_enable(0)
     prof["pairs_in_window"] = cnt["pairs_in_window"] * args.steps
+    prof["pairs_in_window_rx"] = cnt_rx["pairs_in_window"] * args.steps
     prof["pairs_tested"] = cnt["pairs_tested"] * args.steps
     per_step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
@@ -296,15 +310,14 @@ def run_ours(args):
     # dominant kernel and its roofline (FP32 ALU-bound: FP32 pipe peak from SM count x lanes x clock)
     pk, pk_kind = peaks()
     ms = dict(prof["ms"])
-    # both Gaussian-sum categories run the same lattice kernel: rank them together
+    # the receiver sums at the sample times (plane kernel on a receiver plane) and the snapshot (lattice
+    # kernel) are separate kernels: rank them separately
     gauss_ms_total = ms["gauss_sum"] + ms["gauss_sum_state"]
     cnts = dict(prof["count"])
-    by_kernel = {"propagate": ms["propagate"], "gauss_sum": gauss_ms_total}
+    by_kernel = {"propagate": ms["propagate"], "gauss_sum": ms["gauss_sum"], "gauss_sum_state": ms["gauss_sum_state"]}
     top = max(by_kernel, key=lambda c: by_kernel[c])
-    if top == "gauss_sum":
-        ms["gauss_sum_all"] = gauss_ms_total
-        cnts["gauss_sum_all"] = cnts["gauss_sum"] + cnts["gauss_sum_state"]
-        top = "gauss_sum_all"
+    pairs_of = {"gauss_sum": prof["pairs_in_window_rx"],
+                "gauss_sum_state": prof["pairs_in_window"] - prof["pairs_in_window_rx"]}
     sm_clock = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * 128 * 2 * sm_clock
@@ -312,11 +325,11 @@ def run_ours(args):
         nP = sum(1 for c in w.classes if c < 2) * w.mesh.M
         nS = sum(1 for c in w.classes if c >= 2) * w.mesh.M
         flops = (nP * FLOP_PER_BEAM_STEP["P"] + nS * FLOP_PER_BEAM_STEP["S"]) * w.nsteps * args.steps
-    elif prec == fga.PREC_FP32 and top == "gauss_sum_all":
+    elif prec == fga.PREC_FP32 and top in pairs_of:
         # lattice sum: algorithmic work of the in-window pairs, one complex product per component and point
-        # plus the window test (26 FLOP); the tensor-core kernel's extra (out-of-window, split) products are
+        # plus the window test (26 FLOP); the tensor-core kernels' extra (out-of-window, split) products are
         # not counted
-        flops = prof["pairs_in_window"] * FLOP_PER_LATTICE_PAIR_IN
+        flops = pairs_of[top] * FLOP_PER_LATTICE_PAIR_IN
     else:
         flops = None
     launches = max(cnts[top], 1)
@@ -325,7 +338,7 @@ def run_ours(args):
     if flops is not None:
         achieved = flops / (ms[top] / 1e3) / 1e12
         peak = fp32_peak / 1e12
-        traffic = LATTICE_TC_TRAFFIC_BYTES if (top == "gauss_sum_all" and args.size == "full") else None
+        traffic = TRAFFIC_BYTES_PER_LAUNCH.get(top) if args.size == "full" else None
         roof = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_basis": f"FP32 pipe: {sms} SMs (device property) x 128 lanes x 2 x {sm_clock / 1e6:.0f} MHz "
@@ -620,6 +633,152 @@ def run_adjoint(args):
     return 0
 
 
+def run_point_source(args):
+    """Eq. ex_anal's point force: field at t0 -> selected beams -> t1, timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_1810_06760_gb300 import fga
+    from paper_1810_06760_gb300 import workloads as W
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = fga.PREC_FP32 if args.precision == "fp32" else fga.PREC_FP64
+    c = W.e1_patch(k=args.k)
+    model = fga.Model("const", cp0=c.cp, cs0=c.cs)
+    src = fga.point_force(c.x0, c.force, c.rho, c.cp, c.cs, c.f, c.T0, c.sigma)
+    rx = torch.as_tensor(c.receivers, device=dev)
+    counts = {}
+
+    def step():
+        u, v = fga.point_force_field(src, c.ny, c.y0, c.dy, c.t0)
+        desc = fga.init_desc(c.k, u, v, c.y0, c.dy, c.mesh, c.classes, prec, psi_rel_min=c.psi_rel_min)
+        b = fga.decompose(model, desc)
+        counts["beams"] = int(b.count().sum())
+        fga.propagate(model, b, c.dt, c.nsteps)
+        out = fga.reconstruct(b, rx, rw=c.rw)
+        b.close()
+        return out
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    fga.profile_enable(2)
+    fga.profile_read(reset=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        u1 = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(pg, e0.elapsed_time(e1), dev) / args.steps
+    prof = fga.profile_read(reset=True)
+    fga.profile_enable(0)
+    line = {"metric": "point-force FGA solve (field at t0, selection, RK4, sum) and error vs Eq. ex_anal",
+            "value": world * counts["beams"] * c.nsteps / (ms / 1e3), "unit": "beam-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": f"paper's point-force experiment: c_p 8, c_s 4.619 km/s, f 1.4702 Hz, FGA from "
+                                   f"t0 = {c.t0} s to {c.t1} s, k = {c.k:g}/km, {c.mesh.nq}^3 q x {c.mesh.np_}^3 p "
+                                   f"mesh x 4 classes with psi selection {c.psi_rel_min:g}, data grid "
+                                   f"{'x'.join(str(int(n)) for n in c.ny)}, {len(c.receivers)} receivers",
+                       "parallelism": f"replicas x{world}"},
+            "beams": counts["beams"], "mesh_points_per_class": c.mesh.M, "nsteps": c.nsteps,
+            "kernel_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items() if v > 0}}
+    # Eq. ex_anal at t1 on the receiver lattice, by the library's FP64 point-force kernel
+    ax = c.rx_axes
+    ref, _ = fga.point_force_field(src, [len(a) for a in ax], [a[0] for a in ax],
+                                   [(a[1] - a[0]) if len(a) > 1 else 1.0 for a in ax], c.t1, velocity=False)
+    ref = ref.reshape(-1, 3).real.cpu().numpy()
+    got = u1.cpu().numpy()
+    line["rel_l2_vs_analytic"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    line["paper_rel_error"] = 0.0384
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def run_layered(args):
+    """Layered crust with interface events at its stated size, timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_1810_06760_gb300 import fga
+    from paper_1810_06760_gb300 import workloads as W
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = fga.PREC_FP32 if args.precision == "fp32" else fga.PREC_FP64
+    big = args.size == "full"
+    sizes = dict(nq=10, np_=8, ny=48, nsteps=12000, dt=0.01, n_times=1200, rx_side=16, extent=600.0) if big else \
+        dict(nq=5, np_=4, ny=32, nsteps=1200, dt=0.01, n_times=120, rx_side=16, extent=600.0)
+
+    def solve(w, precision, growth=8.0):
+        model = fga.model_from_medium(w.medium, dev)
+        f = torch.as_tensor(w.f, device=dev)
+        desc = fga.init_desc(w.k, f, None, w.y0, w.dy, w.mesh, w.classes, precision, psi_rel_min=1e-6)
+        fga.set_layered_options(desc, max_interfaces=4, child_rel_min=1e-6, growth=growth)
+        desc.psi_rel_min = 1e-6
+        fga.profile_enable(2)
+        fga.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        seis, _ = fga.solve(model, desc, w.dt, w.nsteps, w.times, rw=w.rw, rx_axes=w.rx_axes)
+        e1.record()
+        torch.cuda.synchronize()
+        prof = fga.profile_read(reset=True)
+        fga.profile_enable(0)
+        model.close()
+        return seis, e0.elapsed_time(e1), prof
+
+    w = W.layered(**sizes)
+    warm = W.layered(**dict(sizes, nsteps=100, n_times=10))    # the same kernels and buffers, 100 steps
+    for _ in range(args.warmup):
+        solve(warm, prec)
+    times = []
+    for _ in range(args.steps):
+        seis, ms, prof = solve(w, prec)
+        times.append(ms)
+    ms = max_over_ranks(pg, float(np.mean(times)), dev)
+    # the population after the run: live beams and children lost to the reserved capacity
+    model = fga.model_from_medium(w.medium, dev)
+    f = torch.as_tensor(w.f, device=dev)
+    desc = fga.init_desc(w.k, f, None, w.y0, w.dy, w.mesh, w.classes, prec, psi_rel_min=1e-6)
+    fga.set_layered_options(desc, max_interfaces=4, child_rel_min=1e-6, growth=8.0)
+    desc.psi_rel_min = 1e-6
+    b = fga.decompose(model, desc)
+    selected = int(b.count().sum())
+    b.close()
+    model.close()
+    # FP32 against FP64 on a stride sample of the workload (5^3 q x 4^3 p), same times and stations
+    ws = W.layered(**dict(sizes, nq=5, np_=4))
+    s32, ms32, _ = solve(ws, fga.PREC_FP32)
+    s64, ms64, _ = solve(ws, fga.PREC_FP64)
+    a, r = s32.cpu().numpy().astype(np.complex128), s64.cpu().numpy()
+    line = {"metric": "layered-crust FGA solve with interface events (beam-steps/s, live beams)",
+            "value": world * prof["beam_steps"] / (ms / 1e3), "unit": "beam-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": f"layered crust (interfaces 15, 35 km), explosive source at 10 km, k = {w.k:.3f}/km, "
+                                   f"{w.mesh.nq}^3 q x {w.mesh.np_}^3 p x 4 classes, psi selection 1e-6, "
+                                   f"{w.nsteps} steps of {w.dt} s, {len(w.receivers)} stations x {len(w.times)} samples",
+                       "parallelism": f"replicas x{world}"},
+            "mesh_beams": 4 * w.mesh.M, "selected_beams": selected, "live_beam_steps": prof["beam_steps"],
+            "mean_live_beams": prof["beam_steps"] / w.nsteps,
+            "kernel_ms": {k: v for k, v in prof["ms"].items() if v > 0},
+            "fp64_stride_sample": {"beams": 4 * ws.mesh.M, "ms_fp32": ms32, "ms_fp64": ms64,
+                                   "seismograms_rel_l2_fp32_vs_fp64": float(np.linalg.norm(a - r) / np.linalg.norm(r))}}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -628,6 +787,10 @@ def main():
         return run_serving(args)
     if args.adjoint:
         return run_adjoint(args)
+    if args.point_source:
+        return run_point_source(args)
+    if args.layered:
+        return run_layered(args)
     return run_ours(args)
 
 

@@ -107,14 +107,45 @@ typedef struct {
     int max_interfaces;
     double child_rel_min;
     double growth;
+    /* beam selection (step 1 of Fig. fig:FGA_alg chooses the sets of beams to propagate): with
+     * psi_rel_min > 0 only the beams with |psi| > psi_rel_min x max|psi| are created, |psi| the norm
+     * of the beam's psi (P: |psi|; S: (|psi_sv|^2 + |psi_sh|^2)^{1/2}) and the maximum taken over every
+     * requested class and mesh point; survivors keep mesh order within their class.  0 keeps every
+     * beam; values must lie in [0, 1). */
+    double psi_rel_min;
 } fga_init_desc;
+
+/* Point-force source of the paper's accuracy experiment (Eq. ex_homo): a force F(t) = force s(t) at
+ * x0 in a homogeneous medium (rho, c_p, c_s), s(t) = cos(2 pi f (t + T0)) exp(-(t + T0)^2 / sigma^2)
+ * (the source-time function printed with Eq. ex_anal). */
+typedef struct {
+    double x0[3];
+    double force[3];
+    double rho, cp, cs;
+    double f, T0, sigma;
+} fga_point_force;
+
+/* The displacement the point force radiates, Eq. ex_anal (Stokes' solution: far-field P and S terms
+ * and the near-field term), and its time derivative, at time t on the grid y0 + (i dy0, j dy1, l dy2):
+ * the initial data (f, g) of a decomposition that starts the FGA at time t.  The near-field integral
+ * int_{r/c_p}^{r/c_s} tau s(t - tau) dtau uses composite 8-point Gauss-Legendre quadrature on panels of
+ * at most 1/(8 f) and sigma/4; du/dt uses its integration-by-parts form.  FP64 throughout.
+ *  u_out, v_out: DEVICE complex128 [ny0][ny1][ny2][3] (imaginary parts 0), the layout of
+ *                fga_init_desc.f and .g; either may be NULL (not both).  A grid point at the source
+ *                itself (r <= 1e-12 (1 + |x0|_1)) gets 0.
+ * Asynchronous on s.  Errors: INVALID_ARG (NULL, rho <= 0, not 0 < c_s < c_p, sigma <= 0, f < 0,
+ * ny < 1, dy <= 0, non-finite values, more than 2^37 points), CUDA. */
+fga_status fga_point_force_field(const fga_point_force *src, const int ny[3], const double y0[3], const double dy[3],
+                                 double t, void *u_out, void *v_out, fga_stream_t s);
 
 /* Steps 1 of Fig. fig:FGA_alg: the wave-packet transform F(q,p) = sum_y f(y) exp(-i k p.(y-q)
  * - k|y-q|^2/2) dy^3 (and G from g) as three per-axis contractions, then one beam per mesh point
  * and requested class with Q = q, P = p, dzQ = I, dzP = -iI (Z = 2I) and amplitude
  * 2^{3/2} psi, psi = (F.n +- i G.n/(k c(q) |p|))/2 (Eq. alpha^k read with |p|; n = p/|p| for P,
- * the SV and SH directions for S).  Allocates the beam set (freed by fga_beams_destroy).
- * Errors: INVALID_ARG (k <= 0, sizes, empty mask), OOM, CUDA. */
+ * the SV and SH directions for S); with psi_rel_min > 0 only the selected beams (see above).
+ * Allocates the beam set (freed by fga_beams_destroy); the selection first evaluates psi for
+ * every mesh point and class (no beam storage) and then allocates only the survivors.
+ * Errors: INVALID_ARG (k <= 0, sizes, empty mask, psi_rel_min outside [0, 1)), OOM, CUDA. */
 fga_status fga_decompose(const fga_model *m, const fga_init_desc *init, fga_beams **out, fga_stream_t s);
 
 /* The wave-packet transform of Eq. psi alone (the first half of step 1):
@@ -321,7 +352,8 @@ fga_status fga_server_destroy(fga_server *sv);
  * per trilinear cell, then accumulated with atomics (FP64 path: FP64 into the outputs; FP32 path:
  * FP32 into a scratch grid that is added to the outputs at the end), so the last bits depend on the
  * order of the updates.  Synchronous on s.  Errors: INVALID_ARG, UNSUPPORTED
- * (other media), OOM, CUDA. */
+ * (other media), OOM, CUDA; INVALID_ARG also for a beam selection (psi_rel_min > 0), whose
+ * surviving set is not differentiated. */
 fga_status fga_solve_vjp(const fga_model *m, const fga_init_desc *init, const fga_solve_desc *sd, const void *ubar,
                          double *grad_p, double *grad_s, int checkpoint_every, fga_stream_t s);
 

@@ -229,6 +229,24 @@ def beam_init(model: Model, k: float, mesh: Mesh, F: np.ndarray, G, cls: int, ve
     return st, meta
 
 
+def psi_select(groups, eps: float):
+    """Beam selection of step 1 of Fig. fig:FGA_alg (the algorithm decomposes into the sets of packets
+    worth propagating): of the beams of every class, given as [(state, meta)] from beam_init, keep those
+    whose |psi| exceeds eps times the largest |psi| over all of them.  |psi| is the norm of the beam's
+    psi vector: the initial amplitudes are 2^{3/2} psi (one complex value for P, SV and SH for S), so
+    the ratio is taken on the amplitudes.  Survivors keep their order.  eps = 0 keeps every beam.
+    Returns [(state, meta, mesh_index)] per class."""
+    if eps <= 0:
+        return [(st, mt, np.arange(len(st))) for st, mt in groups]
+    mags = [np.sqrt(np.sum(np.abs(state_a(st)) ** 2, axis=1)) for st, _ in groups]
+    top = max(float(m.max()) if m.size else 0.0 for m in mags)
+    out = []
+    for (st, mt), m in zip(groups, mags):
+        idx = np.nonzero(m > eps * top)[0]
+        out.append((st[idx], mt[idx], idx))
+    return out
+
+
 def rhs(model: Model, st: np.ndarray, meta: np.ndarray) -> np.ndarray:
     st = np.ascontiguousarray(st, dtype=np.float64)
     meta = np.ascontiguousarray(meta, dtype=np.int32)

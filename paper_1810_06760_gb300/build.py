@@ -13,7 +13,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfga_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(HERE, "..", "include")]
-SOURCES = ["api.cu", "decompose.cu", "propagate.cu", "gather.cu", "lattice.cu", "layered.cu", "noalloc.cu", "adjoint.cu", "server.cu", "tc_gemm.cu", "tc_lattice.cu", "tc_plane.cu", "misfit.cu"]
+SOURCES = ["api.cu", "decompose.cu", "propagate.cu", "gather.cu", "lattice.cu", "layered.cu", "noalloc.cu", "adjoint.cu", "server.cu", "tc_gemm.cu", "tc_lattice.cu", "tc_plane.cu", "misfit.cu", "source.cu"]
 
 
 def nvcc() -> str:

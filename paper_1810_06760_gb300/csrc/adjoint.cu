@@ -1052,6 +1052,7 @@ extern "C" fga_status fga_solve_vjp(const fga_model *m, const fga_init_desc *ini
                                     fga_stream_t s_) {
     cudaStream_t s = (cudaStream_t)s_;
     FGA_CHECK(m && init && sd_in, "fga_solve_vjp: NULL argument");
+    FGA_CHECK(!(init->psi_rel_min > 0), "fga_solve_vjp: beam selection (psi_rel_min > 0) is not differentiated");
     // receivers given as (r, theta, phi): a Cartesian copy
     fga_solve_desc sdc;
     ScopedDevBuf rx_cart, snap_cart;

@@ -534,7 +534,8 @@ static fga_status reconstruct_lattice_now(const fga_beams *b, const fga_lattice 
     int32_t *perm = nullptr;
     FGA_TRY(bin_beams(b, g, &perm, s));
     LatticePlan plan;
-    FGA_TRY(build_lattice_plan(ws, g, ws.cell_start.as<int32_t>(), *L, s, plan, b->precision == FGA_PREC_FP32));  // syncs
+    FGA_TRY(build_lattice_plan(ws, g, ws.cell_start.as<int32_t>(), *L, s, plan, b->precision == FGA_PREC_FP32, b->k,
+                               rw));  // syncs
     const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
     FGA_TRY(ws.rec.ensure(rb * REC * (size_t)std::max<int64_t>(plan.n_rec, 1)));
     FGA_TRY(launch_records_from_state(b, perm, plan.beg, plan.n_in, plan.rec_off, ws.rec.p, s));
@@ -749,7 +750,7 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
         SumPlan plan;
         LatticePlan lplan;
         if (rxL) {
-            FGA_TRY(build_lattice_plan(ws, grx, ws.cell_start.as<int32_t>(), *rxL, s, lplan, !fp64));  // syncs
+            FGA_TRY(build_lattice_plan(ws, grx, ws.cell_start.as<int32_t>(), *rxL, s, lplan, !fp64, b->k, rw));  // syncs
             for (int c = 0; c < 4; c++) {
                 plan.n_in[c] = lplan.n_in[c];
                 plan.rec_off[c] = lplan.rec_off[c];
@@ -823,6 +824,26 @@ fga_status fga_beams_count(const fga_beams *b, int64_t *n_by_class) {
     return FGA_OK;
 }
 
+// the stored state (all NFS fields) of the first nb slots as float64, field-major with stride cap
+static fga_status state_to_host(const fga_beams *b, int64_t cap, std::vector<double> &st) {
+    st.resize((size_t)(NFS * cap));
+    if (b->precision == FGA_PREC_FP64) {
+        FGA_CUDA(cudaMemcpy(st.data(), b->state.p, 8 * (size_t)(NFS * cap), cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> sf((size_t)(NFS * cap));
+        FGA_CUDA(cudaMemcpy(sf.data(), b->state.p, 4 * (size_t)(NFS * cap), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < sf.size(); i++) st[i] = sf[i];
+    }
+    return FGA_OK;
+}
+// one exported row: the 46 state values with Q's compensation folded in, then two zeros
+static void export_row(const std::vector<double> &st, int64_t cap, int64_t i, double *o) {
+    for (int f = 0; f < NF; f++) o[f] = st[(size_t)(f * cap + i)];
+    for (int d = 0; d < 3; d++) o[F_Q + d] -= st[(size_t)((F_QC + d) * cap + i)];
+    o[46] = 0.0;
+    o[47] = 0.0;
+}
+
 fga_status fga_beams_export_all(const fga_beams *b, int64_t cap, int64_t *n_out, int64_t *dropped, double *state,
                                 int32_t *meta, int64_t *mesh_id, int64_t *path) {
     FGA_CHECK(b && n_out && cap >= 0, "fga_beams_export_all: NULL argument or negative cap");
@@ -837,16 +858,7 @@ fga_status fga_beams_export_all(const fga_beams *b, int64_t cap, int64_t *n_out,
         if (b->layered) FGA_CUDA(cudaMemcpy(pa.data(), b->path.p, 8 * (size_t)nb, cudaMemcpyDeviceToHost));
     }
     std::vector<double> st;
-    if (state && nb > 0) {
-        st.resize((size_t)(NF * scap));
-        if (b->precision == FGA_PREC_FP64) {
-            FGA_CUDA(cudaMemcpy(st.data(), b->state.p, 8 * (size_t)(NF * scap), cudaMemcpyDeviceToHost));
-        } else {
-            std::vector<float> sf((size_t)(NF * scap));
-            FGA_CUDA(cudaMemcpy(sf.data(), b->state.p, 4 * (size_t)(NF * scap), cudaMemcpyDeviceToHost));
-            for (size_t i = 0; i < sf.size(); i++) st[i] = sf[i];
-        }
-    }
+    if (state && nb > 0) FGA_TRY(state_to_host(b, scap, st));
     int64_t k = 0;
     for (int64_t i = 0; i < nb; i++) {
         if (fl[(size_t)i] & FL_DEAD) continue;
@@ -854,12 +866,7 @@ fga_status fga_beams_export_all(const fga_beams *b, int64_t cap, int64_t *n_out,
             if (meta) meta[k] = fl[(size_t)i];
             if (mesh_id) mesh_id[k] = ids[(size_t)i];
             if (path) path[k] = pa[(size_t)i];
-            if (state) {
-                double *o = state + k * 48;
-                for (int f = 0; f < NF; f++) o[f] = st[(size_t)(f * scap + i)];
-                o[46] = 0.0;
-                o[47] = 0.0;
-            }
+            if (state) export_row(st, scap, i, state + k * 48);
         }
         k++;
     }
@@ -885,26 +892,20 @@ fga_status fga_beams_export(const fga_beams *b, double *state_host, int32_t *met
         FGA_CUDA(cudaMemcpy(ids.data(), b->id.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost));
         FGA_CUDA(cudaMemcpy(fl.data(), b->flags.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost));
     }
-    std::vector<double> st((size_t)(NF * cap));
-    if (state_host && nb > 0) {
-        if (b->precision == FGA_PREC_FP64) {
-            FGA_CUDA(cudaMemcpy(st.data(), b->state.p, 8 * (size_t)(NF * cap), cudaMemcpyDeviceToHost));
-        } else {
-            std::vector<float> sf((size_t)(NF * cap));
-            FGA_CUDA(cudaMemcpy(sf.data(), b->state.p, 4 * (size_t)(NF * cap), cudaMemcpyDeviceToHost));
-            for (size_t i = 0; i < sf.size(); i++) st[i] = sf[i];
-        }
-    }
-    for (int64_t i = 0; i < nb; i++) {
-        const int cls = fl[(size_t)i] & FL_CLASS_MASK;
-        const int64_t row = b->off_cls[cls] + ids[(size_t)i];
+    std::vector<double> st;
+    if (state_host && nb > 0) FGA_TRY(state_to_host(b, cap, st));
+    // mesh order per class: class blocks in class order, beams by mesh index within a block (a
+    // selection keeps a subset of the mesh points, so the row is the beam's rank, not its index)
+    std::vector<int64_t> order((size_t)nb);
+    for (int64_t i = 0; i < nb; i++) order[(size_t)i] = i;
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t c) {
+        const int ca = fl[(size_t)a] & FL_CLASS_MASK, cc = fl[(size_t)c] & FL_CLASS_MASK;
+        return ca != cc ? ca < cc : ids[(size_t)a] < ids[(size_t)c];
+    });
+    for (int64_t row = 0; row < nb; row++) {
+        const int64_t i = order[(size_t)row];
         if (meta_host) meta_host[row] = fl[(size_t)i];
-        if (state_host) {
-            double *o = state_host + row * 48;
-            for (int f = 0; f < NF; f++) o[f] = st[(size_t)(f * cap + i)];
-            o[46] = 0.0;
-            o[47] = 0.0;
-        }
+        if (state_host) export_row(st, cap, i, state_host + row * 48);
     }
     return FGA_OK;
 }

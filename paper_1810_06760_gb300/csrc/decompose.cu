@@ -186,14 +186,11 @@ static double kernel_row_sum_max(int nq, double q0, double dq, int ny, double y0
     return best;
 }
 
-// one beam per (mesh point, requested class)
+// initial state and flags of the beam of mesh point mi and class cls
 template <typename R, int MED>
-__global__ void beam_init_kernel(ModelDev Md, const C2<R> *__restrict__ F, const C2<R> *__restrict__ G, int nq, int np,
-                                 double3 q0, double3 dq, double3 p0, double3 dp, double k, int64_t M, int cls,
-                                 int64_t off, int64_t cap, R *__restrict__ st, int32_t *__restrict__ flags,
-                                 int32_t *__restrict__ ids) {
-    const int64_t mi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (mi >= M) return;
+__device__ __forceinline__ void beam_init_state(const ModelDev &Md, const C2<R> *__restrict__ F,
+                                                const C2<R> *__restrict__ G, int nq, int np, double3 q0, double3 dq,
+                                                double3 p0, double3 dp, double k, int64_t mi, int cls, R *y, int &fl) {
     const int64_t NP = (int64_t)np * np * np;
     const int64_t iq = mi / NP, ip = mi % NP;
     const int qi[3] = {(int)(iq / ((int64_t)nq * nq)), (int)((iq / nq) % nq), (int)(iq % nq)};
@@ -212,7 +209,7 @@ __global__ void beam_init_kernel(ModelDev Md, const C2<R> *__restrict__ F, const
     const R gsc = sgn / ((R)k * cf[0] * pn);  // +- 1/(k c(q) |p|)
     R dirs[2][3];
     int nd = 1;
-    int fl = cls;
+    fl = cls;
     if (!wave) {
         for (int d = 0; d < 3; d++) dirs[0][d] = p[d] / pn;
     } else {
@@ -242,8 +239,6 @@ __global__ void beam_init_kernel(ModelDev Md, const C2<R> *__restrict__ F, const
         for (int q = 0; q < Md.nlay - 1; q++) l += (qd[2] >= Md.zif[q]) ? 1 : 0;
         fl |= (l << 4) | (cls << FL_ROOT_SHIFT);
     }
-    const int64_t b = off + mi;
-    R y[NF];
     for (int f = 0; f < NF; f++) y[f] = R(0);
     for (int d = 0; d < 3; d++) {
         y[F_Q + d] = q[d];
@@ -255,9 +250,93 @@ __global__ void beam_init_kernel(ModelDev Md, const C2<R> *__restrict__ F, const
     y[F_A0 + 1] = amp[1];
     y[F_A1] = amp[2];
     y[F_A1 + 1] = amp[3];
+}
+
+// |psi|^2 of a beam from its initial amplitudes (2^{3/2} psi): the same value on every pass
+template <typename R> __device__ __forceinline__ R psi_mag2(const R *y) {
+    return y[F_A0] * y[F_A0] + y[F_A0 + 1] * y[F_A0 + 1] + y[F_A1] * y[F_A1] + y[F_A1 + 1] * y[F_A1 + 1];
+}
+
+// keep rule of the psi-threshold selection: |psi|^2 > eps^2 max|psi|^2 (amax2 holds the bits of the max)
+template <typename R> struct MaxBits;
+template <> struct MaxBits<float> {
+    using U = unsigned;
+    static __device__ U bits(float v) { return __float_as_uint(v); }
+    static __device__ float val(U u) { return __uint_as_float(u); }
+};
+template <> struct MaxBits<double> {
+    using U = unsigned long long;
+    static __device__ U bits(double v) { return (U)__double_as_longlong(v); }
+    static __device__ double val(U u) { return __longlong_as_double((long long)u); }
+};
+
+// one beam per (mesh point, requested class); with sel != NULL only the beams whose sel[mi] differs
+// from sel[mi + 1] (an exclusive scan of the keep flags) are written, at off + sel[mi]
+template <typename R, int MED>
+__global__ void beam_init_kernel(ModelDev Md, const C2<R> *__restrict__ F, const C2<R> *__restrict__ G, int nq, int np,
+                                 double3 q0, double3 dq, double3 p0, double3 dp, double k, int64_t M, int cls,
+                                 int64_t off, int64_t cap, R *__restrict__ st, int32_t *__restrict__ flags,
+                                 int32_t *__restrict__ ids, const uint32_t *__restrict__ sel) {
+    const int64_t mi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (mi >= M) return;
+    if (sel && sel[mi + 1] == sel[mi]) return;
+    R y[NF];
+    int fl;
+    beam_init_state<R, MED>(Md, F, G, nq, np, q0, dq, p0, dp, k, mi, cls, y, fl);
+    const int64_t b = off + (sel ? (int64_t)sel[mi] : mi);
     for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y[f];
     flags[b] = fl;
     ids[b] = (int32_t)mi;
+}
+
+// pass 1 of the selection: the largest |psi|^2 over the class (block maximum, one atomic per block)
+template <typename R, int MED>
+__global__ void __launch_bounds__(128) psi_max_kernel(ModelDev Md, const C2<R> *__restrict__ F,
+                                                      const C2<R> *__restrict__ G, int nq, int np, double3 q0,
+                                                      double3 dq, double3 p0, double3 dp, double k, int64_t M, int cls,
+                                                      typename MaxBits<R>::U *__restrict__ amax2) {
+    const int64_t mi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    R m2 = R(0);
+    if (mi < M) {
+        R y[NF];
+        int fl;
+        beam_init_state<R, MED>(Md, F, G, nq, np, q0, dq, p0, dp, k, mi, cls, y, fl);
+        m2 = psi_mag2<R>(y);
+        if (!(m2 == m2)) m2 = R(0);   // a NaN amplitude is reported by the solve, not selected on
+    }
+    for (int o = 16; o; o >>= 1) m2 = max(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    __shared__ R wm[4];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const R b = max(max(wm[0], wm[1]), max(wm[2], wm[3]));
+        atomicMax(amax2, MaxBits<R>::bits(b));
+    }
+}
+
+// pass 2: keep[mi] = 1 for |psi|^2 > eps2 * max|psi|^2, keep[M] = 0 (room for the scan's total); the
+// class's survivor count is added to *count
+template <typename R, int MED>
+__global__ void __launch_bounds__(128) psi_keep_kernel(ModelDev Md, const C2<R> *__restrict__ F,
+                                                       const C2<R> *__restrict__ G, int nq, int np, double3 q0,
+                                                       double3 dq, double3 p0, double3 dp, double k, int64_t M,
+                                                       int cls, const typename MaxBits<R>::U *__restrict__ amax2,
+                                                       R eps2, uint32_t *__restrict__ keep,
+                                                       unsigned long long *__restrict__ count) {
+    const int64_t mi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned kf = 0;
+    if (mi < M) {
+        R y[NF];
+        int fl;
+        beam_init_state<R, MED>(Md, F, G, nq, np, q0, dq, p0, dp, k, mi, cls, y, fl);
+        const R lim = eps2 * MaxBits<R>::val(*amax2);
+        kf = psi_mag2<R>(y) > lim ? 1u : 0u;
+        keep[mi] = kf;
+    } else if (mi == M) {
+        keep[M] = 0u;
+    }
+    const unsigned n = __popc(__ballot_sync(0xffffffffu, kf));
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(count, (unsigned long long)n);
 }
 
 // F (and G from g, if both are given) = the transform of Eq. psi in the per-axis pair layout
@@ -305,6 +384,112 @@ static fga_status transform_typed(const fga_init_desc *d, const double2 *f, cons
     return FGA_OK;
 }
 
+// Beam-set storage for the class counts in b->n_cls: class blocks in class order, capacity rounded
+// to 32 (layered media: growth x the initial count, for the children created at interfaces)
+static fga_status beams_allocate(fga_beams *b, const fga_init_desc *d, cudaStream_t s) {
+    int64_t off = 0;
+    for (int c = 0; c < 4; c++) {
+        b->off_cls[c] = off;
+        off += b->n_cls[c];
+    }
+    b->nb = off;
+    if (b->layered) {
+        const double growth = d->growth > 0 ? std::max(1.0, d->growth) : 4.0;
+        b->cap = ((int64_t)std::ceil(growth * (double)off) + 31) / 32 * 32;
+    } else {
+        b->cap = (off + 31) / 32 * 32;
+    }
+    b->cap = std::max<int64_t>(b->cap, 32);
+    const size_t rb = d->precision == FGA_PREC_FP64 ? 8 : 4;
+    FGA_TRY(b->state.ensure(rb * NFS * b->cap));
+    // the Q compensation starts at zero
+    FGA_CUDA(cudaMemsetAsync(static_cast<char *>(b->state.p) + rb * F_QC * b->cap, 0, rb * 3 * b->cap, s));
+    FGA_TRY(b->flags.ensure(4 * b->cap));
+    FGA_TRY(b->id.ensure(4 * b->cap));
+    if (b->layered) {
+        FGA_TRY(b->path.ensure(8 * b->cap));
+        FGA_TRY(b->counts.ensure(16));
+        FGA_TRY(b->n_begin.ensure(8));
+        const unsigned long long c0[2] = {(unsigned long long)off, 0ull};
+        FGA_CUDA(cudaMemsetAsync(b->path.p, 0, 8 * b->cap, s));
+        FGA_CUDA(cudaMemcpyAsync(b->counts.p, c0, sizeof c0, cudaMemcpyHostToDevice, s));
+        FGA_CUDA(cudaStreamSynchronize(s));
+    }
+    return FGA_OK;
+}
+
+template <typename R, int MED>
+static fga_status decompose_medium(const fga_model *m, const fga_init_desc *d, fga_beams *b, const C2<R> *F,
+                                   const C2<R> *G, cudaStream_t s) {
+    const int64_t M = (int64_t)d->nq * d->nq * d->nq * d->np * d->np * d->np;
+    const double3 q0 = {d->q0[0], d->q0[1], d->q0[2]}, dq = {d->dq[0], d->dq[1], d->dq[2]};
+    const double3 p0 = {d->p0[0], d->p0[1], d->p0[2]}, dp = {d->dp[0], d->dp[1], d->dp[2]};
+    const bool select = d->psi_rel_min > 0;
+    using U = typename MaxBits<R>::U;
+    ScopedDevBuf keepb, selb;
+    U *amax2 = nullptr;
+    unsigned long long *cnt = nullptr;
+    uint32_t *keep = nullptr;
+    const R eps2 = (R)(d->psi_rel_min * d->psi_rel_min);
+    const unsigned kblocks = (unsigned)((M + 1 + 127) / 128);
+    if (select) {
+        // Step 1 of Fig. fig:FGA_alg chooses the beams worth propagating: |psi| > eps max|psi|, the maximum
+        // over every requested class and mesh point
+        FGA_TRY(selb.ensure(64));
+        amax2 = selb.as<U>();
+        cnt = reinterpret_cast<unsigned long long *>(selb.as<char>() + 16);
+        FGA_CUDA(cudaMemsetAsync(selb.p, 0, 64, s));
+        FGA_TRY(keepb.ensure(sizeof(uint32_t) * (size_t)(M + 1)));
+        keep = keepb.as<uint32_t>();
+        for (int cls = 0; cls < 4; cls++) {
+            if (!(d->class_mask & (1u << cls))) continue;
+            ProfScope ps(P_DECOMP, s);
+            psi_max_kernel<R, MED><<<(unsigned)((M + 127) / 128), 128, 0, s>>>(m->dev, F, G, d->nq, d->np, q0, dq, p0,
+                                                                              dp, d->k, M, cls, amax2);
+        }
+        FGA_CUDA(cudaGetLastError());
+        for (int cls = 0; cls < 4; cls++) {
+            if (!(d->class_mask & (1u << cls))) continue;
+            ProfScope ps(P_DECOMP, s);
+            psi_keep_kernel<R, MED><<<kblocks, 128, 0, s>>>(m->dev, F, G, d->nq, d->np, q0, dq, p0, dp, d->k, M, cls,
+                                                            amax2, eps2, keep, cnt + cls);
+        }
+        FGA_CUDA(cudaGetLastError());
+        unsigned long long hc[4];
+        FGA_CUDA(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
+        FGA_CUDA(cudaStreamSynchronize(s));
+        int64_t tot = 0;
+        for (int c = 0; c < 4; c++) {
+            b->n_cls[c] = (d->class_mask & (1u << c)) ? (int64_t)hc[c] : 0;
+            tot += b->n_cls[c];
+        }
+        FGA_CHECK(tot < (int64_t)1 << 31, "fga_decompose: more than 2^31 selected beams");
+    } else {
+        for (int c = 0; c < 4; c++) b->n_cls[c] = (d->class_mask & (1u << c)) ? M : 0;
+    }
+    FGA_TRY(beams_allocate(b, d, s));
+    for (int cls = 0; cls < 4; cls++) {
+        if (!b->n_cls[cls]) continue;
+        if (select) {
+            {
+                ProfScope ps(P_DECOMP, s);
+                psi_keep_kernel<R, MED><<<kblocks, 128, 0, s>>>(m->dev, F, G, d->nq, d->np, q0, dq, p0, dp, d->k, M,
+                                                                cls, amax2, eps2, keep, cnt + 4);
+            }
+            FGA_CUDA(cudaGetLastError());
+            FGA_TRY(scan_exclusive_u32(keep, M + 1, s));
+        }
+        ProfScope ps(P_DECOMP, s);
+        beam_init_kernel<R, MED><<<(unsigned)((M + 127) / 128), 128, 0, s>>>(
+            m->dev, F, G, d->nq, d->np, q0, dq, p0, dp, d->k, M, cls, b->off_cls[cls], b->cap, b->state.as<R>(),
+            b->flags.as<int32_t>(), b->id.as<int32_t>(), select ? keep : nullptr);
+        FGA_CUDA(cudaGetLastError());
+    }
+    // the selection scratch is released when this scope ends
+    FGA_CUDA(cudaStreamSynchronize(s));
+    return FGA_OK;
+}
+
 template <typename R>
 static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fga_beams *b, cudaStream_t s) {
     const int A = d->nq * d->np;
@@ -318,26 +503,13 @@ static fga_status decompose_typed(const fga_model *m, const fga_init_desc *d, fg
     }
     FGA_TRY(transform_typed<R>(d, static_cast<const double2 *>(d->f), static_cast<const double2 *>(d->g),
                                Fb.as<C2<R>>(), Gb.as<C2<R>>(), s));
-    const int64_t M = (int64_t)d->nq * d->nq * d->nq * d->np * d->np * d->np;
-    const double3 q0 = {d->q0[0], d->q0[1], d->q0[2]}, dq = {d->dq[0], d->dq[1], d->dq[2]};
-    const double3 p0 = {d->p0[0], d->p0[1], d->p0[2]}, dp = {d->dp[0], d->dp[1], d->dp[2]};
-    for (int cls = 0; cls < 4; cls++) {
-        if (!(d->class_mask & (1u << cls))) continue;
-        const unsigned blocks = (unsigned)((M + 127) / 128);
-        ProfScope ps(P_DECOMP, s);
-#define FGA_INIT(MED)                                                                                               \
-    beam_init_kernel<R, MED><<<blocks, 128, 0, s>>>(m->dev, Fb.as<C2<R>>(), G, d->nq, d->np, q0, dq, p0, dp, d->k, M, \
-                                                    cls, b->off_cls[cls], b->cap, b->state.as<R>(),                   \
-                                                    b->flags.as<int32_t>(), b->id.as<int32_t>())
-        switch (m->dev.kind) {
-        case FGA_MEDIUM_CONST: FGA_INIT(FGA_MEDIUM_CONST); break;
-        case FGA_MEDIUM_SINE: FGA_INIT(FGA_MEDIUM_SINE); break;
-        case FGA_MEDIUM_GRID: FGA_INIT(FGA_MEDIUM_GRID); break;
-        default: FGA_INIT(FGA_MEDIUM_LAYERED); break;
-        }
-#undef FGA_INIT
+    const C2<R> *F = Fb.as<C2<R>>();
+    switch (m->dev.kind) {
+    case FGA_MEDIUM_CONST: FGA_TRY((decompose_medium<R, FGA_MEDIUM_CONST>(m, d, b, F, G, s))); break;
+    case FGA_MEDIUM_SINE: FGA_TRY((decompose_medium<R, FGA_MEDIUM_SINE>(m, d, b, F, G, s))); break;
+    case FGA_MEDIUM_GRID: FGA_TRY((decompose_medium<R, FGA_MEDIUM_GRID>(m, d, b, F, G, s))); break;
+    default: FGA_TRY((decompose_medium<R, FGA_MEDIUM_LAYERED>(m, d, b, F, G, s))); break;
     }
-    FGA_CUDA(cudaGetLastError());
     // F and G are released when this scope ends; make sure the stream is done with them
     FGA_CUDA(cudaStreamSynchronize(s));
     return FGA_OK;
@@ -351,54 +523,30 @@ fga_status decompose_impl(const fga_model *m, const fga_init_desc *d, fga_beams 
     FGA_CHECK(d->ny[0] >= 1 && d->ny[1] >= 1 && d->ny[2] >= 1, "fga_decompose: ny must be >= 1");
     FGA_CHECK((d->class_mask & 15u) != 0 && (d->class_mask & ~15u) == 0, "fga_decompose: class_mask must be in 1..15");
     FGA_CHECK(d->precision == FGA_PREC_FP32 || d->precision == FGA_PREC_FP64, "fga_decompose: bad precision");
+    FGA_CHECK(std::isfinite(d->psi_rel_min) && d->psi_rel_min >= 0 && d->psi_rel_min < 1,
+              "fga_decompose: psi_rel_min must be in [0, 1)");
     for (int a = 0; a < 3; a++) FGA_CHECK(d->dy[a] > 0 && d->dq[a] > 0 && d->dp[a] > 0, "fga_decompose: spacings must be > 0");
     const int64_t M = (int64_t)d->nq * d->nq * d->nq * d->np * d->np * d->np;
-    FGA_CHECK(M * 4 < (int64_t)1 << 31, "fga_decompose: more than 2^31 beams");
+    // mesh indices are int32; without a selection every mesh point of every class is a beam slot
+    FGA_CHECK(M < (int64_t)1 << 31, "fga_decompose: more than 2^31 mesh points");
+    if (!(d->psi_rel_min > 0)) {
+        int nc = 0;
+        for (int c = 0; c < 4; c++) nc += (d->class_mask >> c) & 1;
+        FGA_CHECK(M * nc < (int64_t)1 << 31, "fga_decompose: more than 2^31 beams");
+    }
     fga_beams *b = new fga_beams();
     b->precision = d->precision;
     b->k = d->k;
     double vol = 1.0;
     for (int a = 0; a < 3; a++) vol *= d->dq[a] * d->dp[a];
     b->w = vol / std::pow(2.0 * M_PI / d->k, 4.5);
-    int64_t off = 0;
-    for (int c = 0; c < 4; c++) {
-        b->off_cls[c] = off;
-        b->n_cls[c] = (d->class_mask & (1u << c)) ? M : 0;
-        off += b->n_cls[c];
-    }
-    b->nb = off;
     b->layered = m->dev.kind == FGA_MEDIUM_LAYERED;
     if (b->layered) {
         b->gmax = d->max_interfaces > 0 ? d->max_interfaces : 4;
         b->rel_min = d->child_rel_min > 0 ? d->child_rel_min : 1e-6;
-        const double growth = d->growth > 0 ? std::max(1.0, d->growth) : 4.0;
-        b->cap = ((int64_t)std::ceil(growth * (double)off) + 31) / 32 * 32;
-    } else {
-        b->cap = (off + 31) / 32 * 32;
     }
-    const size_t rb = d->precision == FGA_PREC_FP64 ? 8 : 4;
-    fga_status st = FGA_OK;
-    if ((st = b->state.ensure(rb * NF * b->cap)) != FGA_OK || (st = b->flags.ensure(4 * b->cap)) != FGA_OK ||
-        (st = b->id.ensure(4 * b->cap)) != FGA_OK) {
-        fga_beams_destroy(b);
-        return st;
-    }
-    if (b->layered) {
-        if ((st = b->path.ensure(8 * b->cap)) != FGA_OK || (st = b->counts.ensure(16)) != FGA_OK ||
-            (st = b->n_begin.ensure(8)) != FGA_OK) {
-            fga_beams_destroy(b);
-            return st;
-        }
-        const unsigned long long c0[2] = {(unsigned long long)off, 0ull};
-        cudaError_t e = cudaMemsetAsync(b->path.p, 0, 8 * b->cap, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(b->counts.p, c0, sizeof c0, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            fga_beams_destroy(b);
-            return cuda_fail(e, "fga_decompose");
-        }
-    }
-    st = d->precision == FGA_PREC_FP64 ? decompose_typed<double>(m, d, b, s) : decompose_typed<float>(m, d, b, s);
+    const fga_status st =
+        d->precision == FGA_PREC_FP64 ? decompose_typed<double>(m, d, b, s) : decompose_typed<float>(m, d, b, s);
     if (st != FGA_OK) {
         fga_beams_destroy(b);
         return st;

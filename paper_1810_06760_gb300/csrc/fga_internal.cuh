@@ -16,8 +16,22 @@ namespace fga {
 // at base[f * cap + b]):
 //   0-2 Q, 3-5 P, 6-23 dzQ (entry [m][j] re at 6 + 2(3m+j), im at 7 + 2(3m+j)), 24-41 dzP (same
 //   order), 42-43 amplitude a (P) or a_sv (S), 44-45 a_sh (S; zero for P).
+// Three more stored fields, 46-48, hold the compensation of Q's running sum (Kahan): each step adds
+// its increment to Q with the rounding error carried to the next step, so Q = stored Q - compensation
+// to far better than one rounding per step (thousands of steps of beams hundreds of wavelengths
+// from the origin would otherwise drift by many ulps of |Q|).
 constexpr int NF = 46;
 constexpr int F_Q = 0, F_P = 3, F_DQ = 6, F_DP = 24, F_A0 = 42, F_A1 = 44;
+constexpr int F_QC = NF;       // compensation of Q (3 fields)
+constexpr int NFS = NF + 3;    // stored fields per beam
+
+// Q <- Q + inc with the compensation c carried between steps (Kahan summation)
+template <typename R> __device__ __forceinline__ void kahan_add(R &q, R &c, R inc) {
+    const R yk = inc - c;
+    const R t = q + yk;
+    c = (t - q) - yk;
+    q = t;
+}
 // Reconstruction record: Q(3), P(3), polarised amplitude times the quadrature weight (3 complex).
 constexpr int REC = 12;
 constexpr int MAX_LAYERS = 8;
@@ -218,6 +232,8 @@ struct BinGrid {
     int ncells;       // nc0*nc1*nc2
     bool clamp;       // true: clamp keys into the grid; false: out-of-grid centres go to bucket ncells
 };
+// exclusive prefix sum of n uint32 in place on stream s (synchronises s before returning)
+fga_status scan_exclusive_u32(uint32_t *a, int64_t n, cudaStream_t s);
 fga_status bin_centres(const BinGrid &g, const void *Q_src, int q_kind, int64_t q_stride, int64_t n,
                        const int32_t *cls_or_null, int32_t *keys, cudaStream_t s);
 fga_status radix_sort_pairs(Workspace &ws, int32_t *keys, int32_t *vals, int64_t n, int bits,

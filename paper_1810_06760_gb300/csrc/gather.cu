@@ -182,12 +182,12 @@ __global__ void scan_add_kernel(uint32_t *__restrict__ a, int64_t n, const uint3
     if (i < n) a[i] += bsum[i / SC_TILE];
 }
 
+fga_status scan_exclusive_u32(uint32_t *a, int64_t n, cudaStream_t s);
+
 static fga_status exclusive_scan(Workspace &ws, uint32_t *a, int64_t n, cudaStream_t s) {
     const int64_t nb = (n + SC_TILE - 1) / SC_TILE;
-    if (nb > 1024 * 16) {
-        set_error("exclusive_scan: too many elements");
-        return FGA_ERR_INVALID_ARG;
-    }
+    // more than 1024 x 16 block sums: the multi-level scan (it allocates its block sums)
+    if (nb > 1024 * 16) return scan_exclusive_u32(a, n, s);
     FGA_TRY(ws.scan_blocks.ensure(sizeof(uint32_t) * (size_t)std::max<int64_t>(nb, 1)));
     uint32_t *bs = ws.scan_blocks.as<uint32_t>();
     {
@@ -203,6 +203,35 @@ static fga_status exclusive_scan(Workspace &ws, uint32_t *a, int64_t n, cudaStre
         scan_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n, bs);
     }
     FGA_CUDA(cudaGetLastError());
+    return FGA_OK;
+}
+
+// the same scan for any n < 2^32 elements: the block sums of one level are scanned by the next level
+fga_status scan_exclusive_u32(uint32_t *a, int64_t n, cudaStream_t s) {
+    if (n <= 0) return FGA_OK;
+    const int64_t nb = (n + SC_TILE - 1) / SC_TILE;
+    ScopedDevBuf sums;
+    FGA_TRY(sums.ensure(sizeof(uint32_t) * (size_t)nb));
+    uint32_t *bs = sums.as<uint32_t>();
+    {
+        ProfScope ps(P_DECOMP, s);
+        scan_block_kernel<<<(unsigned)nb, SC_T, 0, s>>>(a, n, bs);
+    }
+    FGA_CUDA(cudaGetLastError());
+    if (nb <= 1024 * 16) {
+        ProfScope ps(P_DECOMP, s);
+        scan_sums_kernel<<<1, 1024, 0, s>>>(bs, (int)nb);
+        FGA_CUDA(cudaGetLastError());
+    } else {
+        FGA_TRY(scan_exclusive_u32(bs, nb, s));
+    }
+    {
+        ProfScope ps(P_DECOMP, s);
+        scan_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n, bs);
+    }
+    FGA_CUDA(cudaGetLastError());
+    // the block sums are released when this scope ends
+    FGA_CUDA(cudaStreamSynchronize(s));
     return FGA_OK;
 }
 
@@ -281,14 +310,14 @@ __global__ void permute_kernel(const R *__restrict__ src, R *__restrict__ dst, c
     if (i >= n) return;
     const int64_t j = perm[i];
 #pragma unroll 2
-    for (int f = 0; f < NF; f++) dst[(int64_t)f * cap + i] = src[(int64_t)f * cap + j];
+    for (int f = 0; f < NFS; f++) dst[(int64_t)f * cap + i] = src[(int64_t)f * cap + j];
     fdst[i] = fsrc[j];
     idst[i] = isrc[j];
 }
 
 fga_status permute_beams(fga_beams *b, const int32_t *perm, cudaStream_t s) {
     const size_t rb = b->precision == FGA_PREC_FP64 ? 8 : 4;
-    FGA_TRY(b->state_alt.ensure(rb * NF * b->cap));
+    FGA_TRY(b->state_alt.ensure(rb * NFS * b->cap));
     FGA_TRY(b->flags_alt.ensure(4 * b->cap));
     FGA_TRY(b->id_alt.ensure(4 * b->cap));
     const unsigned blocks = (unsigned)((b->nb + 255) / 256);

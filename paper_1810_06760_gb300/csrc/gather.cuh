@@ -38,7 +38,15 @@ struct LatticePlan {
 };
 // tc: tile shape and work split of the tensor-core kernel (the FP32 path); else the CUDA-core kernel's
 fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, const fga_lattice &L,
-                              cudaStream_t s, LatticePlan &plan, bool tc);
+                              cudaStream_t s, LatticePlan &plan, bool tc, double k, double rw);
+// The tensor-core lattice kernels form a beam's 1-D factors exp(i k P (x - Q) - k (x - Q)^2 / 2) along a
+// uniform axis by recurrence: the first point directly, then ratios exp(i k P h - k h (x - Q + h/2)),
+// each ratio times exp(-k h^2).  In FP32 a first value with k (x - Q)^2 / 2 > 87 underflows and
+// zeroes the run; a kept beam lies within rw of the tile, and the values lost that way stay below
+// e^-14 of its amplitude when a run spans at most recurrence_span_max(k, rw).  The ratio itself is
+// finite while k h (span + rw + h) <= 87 (recurrence_ratio_ok); otherwise the run is one point.
+double recurrence_span_max(double k, double rw);
+bool recurrence_ratio_ok(double k, double step, double span, double rw);
 void tile_shape_tc(const fga_lattice &L, int T[3]);
 // single-plane lattices with uniform axes 0 and 1: the warp-specialised plane kernel (tc_plane.cu)
 void tile_shape_plane(const fga_lattice &L, int T[3]);

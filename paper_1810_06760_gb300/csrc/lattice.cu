@@ -326,8 +326,29 @@ static void tile_shape(const fga_lattice &L, int T[3]) {
     }
 }
 
+double recurrence_span_max(double k, double rw) {
+    const double sk = std::sqrt(k);
+    return std::max((std::sqrt(174.0) - std::sqrt(28.0)) / sk, std::sqrt(174.0) / sk - rw);
+}
+bool recurrence_ratio_ok(double k, double step, double span, double rw) {
+    return k * std::fabs(step) * (span + rw + std::fabs(step)) <= 87.0;
+}
+
+// the plane kernel's runs: axis 1 in two halves of ceil(T1/2) points (step h1), axis 0 in the two
+// parities of ceil(T0/2) points (step 2 h0); cap T so every run stays within the recurrence limits
+static void cap_plane_tile(const LatticePlan &plan, double k, double rw, int T[3]) {
+    const double smax = recurrence_span_max(k, rw);
+    for (int d = 0; d < 2; d++) {
+        if (T[d] <= 2 || !plan.uniform[d]) continue;
+        const double step = (d == 0 ? 2.0 : 1.0) * std::fabs(plan.dx[d]);
+        int J = 1 + (int)std::floor(smax / step);
+        while (J > 1 && !recurrence_ratio_ok(k, step, (J - 1) * step, rw)) J--;
+        T[d] = std::min(T[d], 2 * J);
+    }
+}
+
 fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *cell_start_dev, const fga_lattice &L,
-                              cudaStream_t s, LatticePlan &plan, bool tc) {
+                              cudaStream_t s, LatticePlan &plan, bool tc, double k, double rw) {
     // axes with uniform spacing (the tensor-core kernels form their 1-D factors by recurrence there)
     for (int d = 0; d < 3; d++) {
         const double *a = L.axis[d];
@@ -342,9 +363,10 @@ fga_status build_lattice_plan(Workspace &ws, const BinGrid &g, const int32_t *ce
     }
     const bool plane = tc && L.n[2] == 1 && (plan.uniform[0] || L.n[0] == 1) && (plan.uniform[1] || L.n[1] == 1);
     int T[3];
-    if (plane)
+    if (plane) {
         tile_shape_plane(L, T);
-    else if (tc)
+        cap_plane_tile(plan, k, rw, T);
+    } else if (tc)
         tile_shape_tc(L, T);
     else
         tile_shape(L, T);

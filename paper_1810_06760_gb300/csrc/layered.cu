@@ -97,30 +97,38 @@ __device__ __forceinline__ void layer_rhs(R sg, R c, const R *y, R *f) {
     }
 }
 
+// one classical RK4 step of size h: out = y + the step's increment (summed at its own scale), Q by
+// compensated summation with the compensation qc carried in and out
 template <typename R>
-__device__ __forceinline__ void layer_rk4(R sg, R c, const R *y, R h, R *out) {
-    R k[NF], t[NF], acc[NF];
+__device__ __forceinline__ void layer_rk4(R sg, R c, const R *y, R h, R *out, R *qc) {
+    R k[NF], t[NF], inc[NF];
     layer_rhs<R>(sg, c, y, k);
 #pragma unroll
     for (int f = 0; f < NF; f++) {
-        acc[f] = y[f] + h / R(6) * k[f];
+        inc[f] = h / R(6) * k[f];
         t[f] = y[f] + R(0.5) * h * k[f];
     }
     layer_rhs<R>(sg, c, t, k);
 #pragma unroll
     for (int f = 0; f < NF; f++) {
-        acc[f] += h / R(3) * k[f];
+        inc[f] += h / R(3) * k[f];
         t[f] = y[f] + R(0.5) * h * k[f];
     }
     layer_rhs<R>(sg, c, t, k);
 #pragma unroll
     for (int f = 0; f < NF; f++) {
-        acc[f] += h / R(3) * k[f];
+        inc[f] += h / R(3) * k[f];
         t[f] = y[f] + h * k[f];
     }
     layer_rhs<R>(sg, c, t, k);
 #pragma unroll
-    for (int f = 0; f < NF; f++) out[f] = acc[f] + h / R(6) * k[f];
+    for (int f = 3; f < NF; f++) out[f] = y[f] + (inc[f] + h / R(6) * k[f]);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        R q = y[F_Q + d];
+        kahan_add<R>(q, qc[d], inc[F_Q + d] + h / R(6) * k[F_Q + d]);
+        out[F_Q + d] = q;
+    }
 }
 
 // Solve the 6x6 complex system A x = b (partial pivoting); false if singular.
@@ -349,16 +357,20 @@ __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__rest
     if (fl & FL_DEAD) return;
     const int wave = (fl & FL_CLASS_MASK) >= 2, L = (fl >> 4) & 15;
     const R sg = (fl & 1) ? R(-1) : R(1);
-    R y[NF], y1[NF];
+    R y[NF], y1[NF], qc[3], qc1[3];
 #pragma unroll
     for (int f = 0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
+#pragma unroll
+    for (int d = 0; d < 3; d++) qc1[d] = qc[d] = st[(int64_t)(F_QC + d) * cap + b];
     const R c = layer_speed<R>(M, wave, L);
-    layer_rk4<R>(sg, c, y, dt, y1);
+    layer_rk4<R>(sg, c, y, dt, y1, qc1);
     const R ztop = L > 0 ? mp<R>(M.zif[L - 1], M.fzif[L - 1]) : -R(INFINITY);
     const R zbot = L < M.nlay - 1 ? mp<R>(M.zif[L], M.fzif[L]) : R(INFINITY);
     if (y1[F_Q + 2] >= ztop && y1[F_Q + 2] < zbot) {
 #pragma unroll
         for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y1[f];
+#pragma unroll
+        for (int d = 0; d < 3; d++) st[(int64_t)(F_QC + d) * cap + b] = qc1[d];
         return;
     }
     // the step crosses an interface: advance to it, scatter, finish the step with every child
@@ -371,8 +383,9 @@ __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__rest
         return;
     }
     R yc[NF];
-    layer_rk4<R>(sg, c, y, th * dt, yc);
+    layer_rk4<R>(sg, c, y, th * dt, yc, qc);
     yc[F_Q + 2] = zc;
+    qc[2] = R(0);                 // the interface depth is exact
     EventOut ev;
     interface_event<R>(M, fl, yc, lb, rel_min, ev);
     if (ev.n == 0) {
@@ -382,11 +395,12 @@ __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__rest
     const long long pp = path[b];
     const int32_t id = ids[b];
     for (int k = 0; k < ev.n; k++) {
-        R ch[NF], ce[NF];
+        R ch[NF], ce[NF], qch[3] = {qc[0], qc[1], qc[2]};
         make_child<R>(yc, ev, k, ch);
         const int flc = ev.flags[k];
         const R sgc = (flc & 1) ? R(-1) : R(1);
-        layer_rk4<R>(sgc, layer_speed<R>(M, (flc & FL_CLASS_MASK) >= 2, (flc >> 4) & 15), ch, (R(1) - th) * dt, ce);
+        layer_rk4<R>(sgc, layer_speed<R>(M, (flc & FL_CLASS_MASK) >= 2, (flc >> 4) & 15), ch, (R(1) - th) * dt, ce,
+                     qch);
         int64_t dst = b;
         if (k > 0) {
             dst = (int64_t)atomicAdd(&counts[0], 1ull);
@@ -397,6 +411,8 @@ __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__rest
         }
 #pragma unroll
         for (int f = 0; f < NF; f++) st[(int64_t)f * cap + dst] = ce[f];
+#pragma unroll
+        for (int d = 0; d < 3; d++) st[(int64_t)(F_QC + d) * cap + dst] = qch[d];
         flags[dst] = flc;
         ids[dst] = id;
         path[dst] = pp * 4 + ev.slot[k] + 1;

@@ -85,6 +85,8 @@ __global__ void __launch_bounds__(128) noalloc_gather_kernel(const R *__restrict
         for (int f = 0; f < 6; f++) y[f] = st[(int64_t)f * cap + b];
 #pragma unroll
         for (int f = F_A0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
+#pragma unroll
+        for (int d = 0; d < 3; d++) y[F_Q + d] -= st[(int64_t)(F_QC + d) * cap + b];   // compensated Q
         R r[REC];
         beam_record<R, WAVE>((flags[b] & FL_REF_E1) != 0, y, y, y, y, R(0), R(0), w, r);
         const R d0 = x0 - r[0], d1 = x1 - r[1], d2 = x2 - r[2];

@@ -28,6 +28,8 @@ template <typename R> __device__ __forceinline__ void axpy_state(R *out, const R
 //   e = 2: k4 = f(tmp)          acc += h/6 k4 (= y_{n+1}),  tmp = acc
 //   e = 3: k1' = f(y_{n+1})     records of the step; y = acc, acc = y + h/6 k1', tmp = y + h/2 k1'
 // Iteration -1 is an e = 3 without records: it forms k1 of the first step from y_0.
+// The three Q entries of acc hold the step's increment instead (small numbers, rounded at their own
+// scale); y_{n+1}'s Q is y_n's plus that increment by compensated summation (kahan_add).
 template <typename R, int WAVE, int MED>
 __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st, const int32_t *__restrict__ flags,
                                                   int64_t cap, int64_t beg, int64_t n, R sg, R dt, int nsteps,
@@ -36,13 +38,15 @@ __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st
                                                   int64_t rec_lim, int64_t rec_stride) {
     const int64_t b = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= beg + n) return;
-    R y[NF], acc[NF], tmp[NF], kk[NF];
+    R y[NF], acc[NF], tmp[NF], kk[NF], qc[3];
 #pragma unroll
     for (int f = 0; f < NF; f++) {
         y[f] = st[(int64_t)f * cap + b];
         acc[f] = y[f];
         tmp[f] = y[f];
     }
+#pragma unroll
+    for (int d = 0; d < 3; d++) qc[d] = st[(int64_t)(F_QC + d) * cap + b];
     const bool ref_e1 = (flags[b] & FL_REF_E1) != 0;
     R s0[6];   // Q', P' at y_n (left slopes of the Hermite records)
     int js = 0;
@@ -51,6 +55,14 @@ __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st
         const int e = it & 3;
         beam_rhs<R, WAVE, MED>(M, sg, ref_e1, tmp, kk);
         if (e == 3) {
+            if (it >= 0) {
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    R q = y[F_Q + d];
+                    kahan_add<R>(q, qc[d], acc[F_Q + d]);
+                    acc[F_Q + d] = q;       // acc = y_{n+1} in full
+                }
+            }
             const int step = it >> 2;
             while (it >= 0 && js < n_samp && samp_step[js] == step) {
                 if (b - beg < rec_lim) {
@@ -73,13 +85,23 @@ __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st
         if (e < 2) {
             axpy_state<R>(tmp, y, ct, kk);
             axpy_state<R>(acc, acc, ca, kk);
+        } else if (e == 2) {
+            // tmp = y_{n+1} = y + (increment + h/6 k4) on Q
+            axpy_state<R>(tmp, acc, ct, kk);
+            axpy_state<R>(acc, acc, ca, kk);
+#pragma unroll
+            for (int d = 0; d < 3; d++) tmp[F_Q + d] = y[F_Q + d] + acc[F_Q + d];
         } else {
             axpy_state<R>(tmp, acc, ct, kk);
             axpy_state<R>(acc, acc, ca, kk);
+#pragma unroll
+            for (int d = 0; d < 3; d++) acc[F_Q + d] = ca * kk[F_Q + d];   // the new step's increment so far
         }
     }
 #pragma unroll
     for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y[f];
+#pragma unroll
+    for (int d = 0; d < 3; d++) st[(int64_t)(F_QC + d) * cap + b] = qc[d];
 }
 
 // records of the current state (theta = 0), gathered in the order of perm (or identity)
@@ -92,6 +114,8 @@ __global__ void records_kernel(const R *__restrict__ st, const int32_t *__restri
     R y[NF];
 #pragma unroll
     for (int f = 0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
+#pragma unroll
+    for (int d = 0; d < 3; d++) y[F_Q + d] -= st[(int64_t)(F_QC + d) * cap + b];   // compensated Q
     R r[REC];
     beam_record<R, WAVE>((flags[b] & FL_REF_E1) != 0, y, y, y, y, R(0), R(0), w, r);
     R *dst = rec + i * REC;

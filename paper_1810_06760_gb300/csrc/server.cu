@@ -67,7 +67,7 @@ double estimate_solve_bytes(const fga_init_desc *d, double rec_cap) {
     const double A = (double)d->nq * d->np;
     const double ny0 = d->ny[0], ny1 = d->ny[1], ny2 = d->ny[2];
     const double cbytes = 2.0 * rb;
-    const double state = NF * rb * cap, ints = 4.0 * 4.0 * cap, sort = 4.0 * 4.0 * cap;
+    const double state = NFS * rb * cap, ints = 4.0 * 4.0 * cap, sort = 4.0 * 4.0 * cap;
     const double decomp = cbytes * (A * (ny0 + ny1 + ny2) + ny0 * ny1 * A * 3.0 + ny0 * A * A * 3.0 +
                                     A * A * A * 3.0 * (d->g ? 2.0 : 1.0));
     const double during_decomp = state + ints + decomp;

@@ -564,7 +564,13 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
     LtAxes X;
     for (int d = 0; d < 3; d++) {
         const int Td = plan.T[d];
-        X.len[d] = plan.uniform[d] ? LT_CHUNK : 1;
+        int len = plan.uniform[d] ? LT_CHUNK : 1;
+        if (len > 1) {
+            const double h = std::fabs(plan.dx[d]);
+            len = std::min(len, 1 + (int)std::floor(recurrence_span_max(k, rw) / h));
+            while (len > 1 && !recurrence_ratio_ok(k, h, (len - 1) * h, rw)) len--;
+        }
+        X.len[d] = len;
         X.nch[d] = (Td + X.len[d] - 1) / X.len[d];
         X.dx[d] = (float)plan.dx[d];
     }

@@ -28,7 +28,7 @@ EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_trans
             "fga_beams_export_all", "fga_beams_destroy", "fga_bin", "fga_profile_enable", "fga_profile_read",
             "fga_solve_vjp", "fga_server_create", "fga_server_submit", "fga_server_wait", "fga_server_stats",
             "fga_server_destroy", "fga_server_cancel", "fga_traveltime_adjoint", "fga_set_device_memory_limit",
-            "fga_device_memory_in_use", "fga_last_error", "fga_version"]
+            "fga_device_memory_in_use", "fga_point_force_field", "fga_last_error", "fga_version"]
 PROFILE_CATEGORIES = ["decompose", "propagate", "binning", "records", "gauss_sum", "gauss_reduce", "gauss_sum_state",
                       "interfaces", "adjoint_forward", "adjoint_reverse", "adjoint_init", "misfit"]
 
@@ -51,7 +51,12 @@ class InitDesc(C.Structure):
                 ("f", C.c_void_p), ("g", C.c_void_p), ("nq", C.c_int), ("q0", C.c_double * 3),
                 ("dq", C.c_double * 3), ("np", C.c_int), ("p0", C.c_double * 3), ("dp", C.c_double * 3),
                 ("class_mask", C.c_uint), ("precision", C.c_int), ("max_interfaces", C.c_int),
-                ("child_rel_min", C.c_double), ("growth", C.c_double)]
+                ("child_rel_min", C.c_double), ("growth", C.c_double), ("psi_rel_min", C.c_double)]
+
+
+class PointForce(C.Structure):
+    _fields_ = [("x0", C.c_double * 3), ("force", C.c_double * 3), ("rho", C.c_double), ("cp", C.c_double),
+                ("cs", C.c_double), ("f", C.c_double), ("T0", C.c_double), ("sigma", C.c_double)]
 
 
 class Profile(C.Structure):
@@ -111,6 +116,8 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_model_destroy.argtypes = [vp]
     L.fga_decompose.argtypes = [vp, C.POINTER(InitDesc), C.POINTER(vp), vp]
     L.fga_transform.argtypes = [C.POINTER(InitDesc), vp, vp]
+    L.fga_point_force_field.argtypes = [C.POINTER(PointForce), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), C.c_double, vp, vp, vp]
     L.fga_propagate.argtypes = [vp, vp, C.c_double, i32, vp]
     L.fga_reconstruct.argtypes = [vp, vp, i64, C.c_double, vp, vp]
     L.fga_reconstruct_noalloc.argtypes = [vp, vp, i64, C.c_double, vp, vp]
@@ -230,8 +237,9 @@ def model_from_medium(med, device="cuda") -> Model:
     return Model(med.kind, cp0=med.cp0, cs0=med.cs0, amp=med.amp, cs_ratio=med.cs_ratio)
 
 
-def init_desc(k, f, g, y0, dy, mesh, classes: Sequence[int], precision: int) -> InitDesc:
-    """Decomposition descriptor.  f, g: complex128 CUDA tensors [ny0, ny1, ny2, 3] (g may be None)."""
+def init_desc(k, f, g, y0, dy, mesh, classes: Sequence[int], precision: int, psi_rel_min: float = 0.0) -> InitDesc:
+    """Decomposition descriptor.  f, g: complex128 CUDA tensors [ny0, ny1, ny2, 3] (g may be None).
+    psi_rel_min > 0 creates only the beams with |psi| > psi_rel_min max|psi|."""
     d = InitDesc()
     d.k = float(k)
     d.ny[:] = list(f.shape[:3])
@@ -241,6 +249,7 @@ def init_desc(k, f, g, y0, dy, mesh, classes: Sequence[int], precision: int) -> 
     d.np, d.p0, d.dp = int(mesh.np_), _arr3(mesh.p0), _arr3(mesh.dp)
     d.class_mask = sum(1 << int(c) for c in classes)
     d.precision = int(precision)
+    d.psi_rel_min = float(psi_rel_min)
     return d
 
 
@@ -310,6 +319,28 @@ def transform(desc: InitDesc, out=None, stream=None):
                           device=torch.device("cuda", torch.cuda.current_device()))
     _check(lib().fga_transform(C.byref(desc), _dptr(out), _stream(stream)))
     return out
+
+
+def point_force(x0, force, rho, cp, cs, f, T0, sigma) -> PointForce:
+    """Point force `force` s(t) at x0 in a homogeneous medium, s(t) = cos(2 pi f (t+T0)) exp(-(t+T0)^2/sigma^2)."""
+    p = PointForce()
+    p.x0, p.force = _arr3(x0), _arr3(force)
+    p.rho, p.cp, p.cs, p.f, p.T0, p.sigma = float(rho), float(cp), float(cs), float(f), float(T0), float(sigma)
+    return p
+
+
+def point_force_field(src: PointForce, ny, y0, dy, t: float, velocity: bool = True, stream=None):
+    """fga_point_force_field: (u, du/dt) of the point force at time t on the grid y0 + i dy, complex128
+    CUDA tensors [ny0, ny1, ny2, 3] (v is None when velocity is False)."""
+    import torch
+    n = [int(v) for v in np.broadcast_to(np.asarray(ny), (3,))]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    u = torch.empty(tuple(n) + (3,), dtype=torch.complex128, device=dev)
+    v = torch.empty_like(u) if velocity else None
+    nyc = (C.c_int * 3)(*n)
+    _check(lib().fga_point_force_field(C.byref(src), nyc, _arr3(y0), _arr3(dy), float(t), _dptr(u), _dptr(v),
+                                       _stream(stream)))
+    return u, v
 
 
 def propagate(model: Model, beams: Beams, dt: float, nsteps: int, stream=None) -> None:

@@ -377,3 +377,78 @@ def serving_requests(n: int = 64, seed: int = 1, n_range=(1e5, 2e7), ks=(32.0, 6
                      window_radius(k), rx_axes=(r, r, np.zeros(1)))
         out.append(ServingRequest(t, w, int(round(N))))
     return out
+
+
+@dataclasses.dataclass
+class PointSourceCase:
+    """A point-force run: the source, the FGA start and end times, the data grid, mesh and receivers."""
+    x0: np.ndarray
+    force: np.ndarray
+    rho: float
+    cp: float
+    cs: float
+    f: float
+    T0: float
+    sigma: float
+    t0: float
+    t1: float
+    k: float
+    ny: np.ndarray           # data grid points per axis
+    y0: np.ndarray
+    dy: np.ndarray
+    mesh: MeshSpec
+    receivers: np.ndarray    # [n, 3] km
+    rw: float
+    dt: float
+    nsteps: int
+    psi_rel_min: float
+    rx_axes: tuple = ()      # the receivers as a lattice (x, y, z axes; receivers in x-major order)
+    classes: tuple = (0, 1, 2, 3)
+
+
+def e1_patch(k: float = 0.08, aq: float = 1.0, ap: float = 1.5, t0: float = 3.0, t1: float = 6.93,
+             rw_mult: float = 5.0, spacing: float = 0.5, psi_rel_min: float = 1e-5, dt: float = 0.05,
+             band_rel: float = 1e-3) -> PointSourceCase:
+    """The paper's accuracy experiment: a point force (1, 1, 1) s(t) at x0 = (64, 64, 64) km in a
+    homogeneous medium (c_p = 8, c_s = 4.619 km/s, rho = 1), s(t) = cos(2 pi f (t+T0)) exp(-(t+T0)^2/sigma^2)
+    with f = 1.4702 Hz, T0 = 0.1768 s, sigma = 0.8660 s, compared at t1 = 6.93 s.
+
+    The FGA starts at t0 = 3 s from the radiated field and its time derivative (by then the source-time
+    function is below 2e-6 of its peak), and the field is compared on a patch of the slice y = 64 km:
+    x - 64 in [24, 44] km, z - 64 in [-4, 4] km (`spacing` apart), where both the P and the S pulse are
+    present at t1.  The q mesh covers the patch's domain of dependence at t0 (radii r - c_p (t1 - t0) to
+    r - c_s (t1 - t0) along +x, widened by the summation window rw = rw_mult/sqrt(k) and 2/sqrt(k));
+    the p mesh covers +-(xi_max + 3 sqrt(2k))/k along x and +-(0.4 xi_max + 3 sqrt(2k))/k across, xi_max
+    the S wavenumber where the source spectrum exp(-sigma^2 (omega - 2 pi f)^2 / 4) falls to band_rel;
+    spacings at most aq/sqrt(k) (q) and ap/sqrt(k) (p).  The data grid extends 6/sqrt(k) beyond the q
+    mesh at about 0.35 km spacing.  RK4 steps of about dt."""
+    cp, cs, f, T0, sigma = 8.0, 4.619, 1.4702, 0.1768, 0.8660
+    x0 = np.array([64.0, 64.0, 64.0])
+    w = 1.0 / math.sqrt(k)
+    rw = rw_mult * w
+    m = rw + 2.0 * w
+    T = t1 - t0
+    qlo = np.array([64.0 + 24.0 - cp * T - m, 64.0 - 4.0 - m, 64.0 - 4.0 - m])
+    qhi = np.array([64.0 + 44.0 - cs * T + m, 64.0 + 4.0 + m, 64.0 + 4.0 + m])
+    ext = qhi - qlo
+    nq = int(math.ceil(ext.max() / (aq * w)))
+    dq = ext / nq
+    xi_max = (2.0 * math.pi * f + 2.0 * math.sqrt(math.log(1.0 / band_rel)) / sigma) / cs
+    px = (xi_max + 3.0 * math.sqrt(2.0 * k)) / k
+    pl = (0.4 * xi_max + 3.0 * math.sqrt(2.0 * k)) / k
+    pext = np.array([2.0 * px, 2.0 * pl, 2.0 * pl])
+    np_ = int(math.ceil(pext.max() / (ap * w)))
+    dp = pext / np_
+    mesh = MeshSpec(nq, qlo + 0.5 * dq, dq, np_, -0.5 * pext + 0.5 * dp, dp)
+    ylo = qlo - 6.0 * w
+    yhi = qhi + 6.0 * w
+    ny = np.ceil((yhi - ylo) / 0.35).astype(np.int64)
+    dy = (yhi - ylo) / ny
+    r1 = np.arange(24.0, 44.0 + 1e-9, spacing)
+    s3 = np.arange(-4.0, 4.0 + 1e-9, spacing)
+    R1, S3 = np.meshgrid(r1, s3, indexing="ij")
+    rx = np.stack([64.0 + R1.ravel(), np.full(R1.size, 64.0), 64.0 + S3.ravel()], -1)
+    nsteps = max(1, int(round(T / dt)))
+    return PointSourceCase(x0, np.array([1.0, 1.0, 1.0]), 1.0, cp, cs, f, T0, sigma, t0, t1, k, ny,
+                           ylo + 0.5 * dy, dy, mesh, rx, rw, T / nsteps, nsteps, psi_rel_min,
+                           (64.0 + r1, np.array([64.0]), 64.0 + s3))

@@ -177,6 +177,38 @@ def test_reconstruct_on_plane(fga, oracle, prec, shape):
 
 
 @pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("case", ["far_start_k128", "coarse_0.4", "coarse_2.0"])
+def test_reconstruct_on_plane_factor_recurrence_limits(fga, oracle, prec, case):
+    """Planes where the FP32 kernels' factor recurrences would leave float range: at k = 128 a 16-point
+    axis whose recurrence starts 1.25 (> sqrt(174/k) = 1.17) before the beams, so the first factor
+    underflows while the beams still reach the tile's far end (the runs are shortened); and planes of
+    spacing 0.4 and 2.0 (k h up to 128: the ratio exp(-k h (x + h/2)) overflows unless each run is
+    one point).  Against the oracle's brute-force sum."""
+    import torch
+    if case == "far_start_k128":
+        w = _small_smooth(grid=True, nsteps=16, k=128.0, ny=96)
+        axes = (np.linspace(-0.9, 0.1, 16), np.linspace(0.2, 0.7, 16), np.array([0.55]))
+    elif case == "coarse_0.4":
+        w = _small_smooth(grid=True, nsteps=16)
+        axes = (np.linspace(-0.8, 2.0, 8), np.linspace(-1.2, 2.0, 9), np.array([0.55]))
+    else:
+        w = _small_smooth(grid=True, nsteps=16)
+        axes = (np.linspace(-3.6, 4.4, 5), np.linspace(-1.6, 6.4, 5), np.array([0.55]))
+    model, desc, keep = gpu_setup(w, prec)
+    beams = fga.decompose(model, desc)
+    fga.propagate(model, beams, w.dt, w.nsteps)
+    u = fga.reconstruct_lattice(beams, axes, rw=w.rw).cpu().numpy().reshape(-1, 3)
+    X = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    omodel, mesh, obeams = oracle_beams(oracle, w)
+    ref = np.zeros((X.shape[0], 3), complex)
+    for cls, st, meta in obeams:
+        oracle.propagate(omodel, st, meta, w.dt, w.nsteps)
+        ref += oracle.gauss_sum(oracle.records(st, meta, mesh.weight(w.k)), w.k, w.rw, X)
+    assert np.abs(ref).max() > 0 and np.isfinite(u).all()
+    _check_field(u, ref, prec)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
 def test_solve_on_lattices_equals_solve_on_points(fga, prec):
     """Receivers and snapshot given as lattices give the same seismograms and snapshot as the same
     points given one by one."""

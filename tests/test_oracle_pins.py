@@ -512,3 +512,52 @@ def test_spherical_points(oracle):
     np.testing.assert_allclose(np.linalg.norm(x, axis=1), rtp[:, 0], rtol=1e-14)
     np.testing.assert_allclose(np.arctan2(x[:, 1], x[:, 0]), rtp[:, 1], atol=1e-13)
     np.testing.assert_allclose(np.arcsin(x[:, 2] / rtp[:, 0]), rtp[:, 2], atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------------
+# beam selection (step 1 of Fig. fig:FGA_alg): |psi| > eps max|psi|
+# ---------------------------------------------------------------------------------------------
+
+def test_psi_select_matches_closed_form_survivors(oracle):
+    """For a Gaussian packet b exp(i k p0.y - k|y-x0|^2/2) and zero velocity the transform is
+    |F(q,p)| = |b-part| (pi/k)^{3/2} exp(-k(|q-x0|^2 + |p-p0|^2)/4), so |psi| is known in closed form per
+    class: P: |b.n|/2 e(q,p), S: (|b|^2 - |b.n|^2)^{1/2}/2 e(q,p), n = p/|p| (b real).  The oracle's
+    selection (on its own transform) must keep exactly the beams the closed form keeps, away from the
+    threshold (ratios within 1e-4 of eps are not judged)."""
+    O = oracle
+    k = 24.0
+    x0 = np.array([0.5, 0.45, 0.55])
+    p0 = np.array([0.6, 0.7, -0.4])
+    b = np.array([0.8, 0.5, -0.3])
+    half = 7.0 / math.sqrt(k)
+    ny = 72
+    dy = np.full(3, 2 * half / ny)
+    y0 = x0 - half + 0.5 * dy
+    ax = [y0[a] + dy[a] * np.arange(ny) for a in range(3)]
+    Y = np.stack(np.meshgrid(*ax, indexing="ij"), -1)
+    f = np.exp(1j * k * (Y @ p0) - 0.5 * k * np.sum((Y - x0) ** 2, -1))[..., None] * b
+    mesh = _mesh(O, 5, x0, 5, p0, 1.3)
+    F = O.fbi(f, y0, dy, k, mesh)
+    model = O.Model("const", cp0=2.0, cs0=1.0)
+    groups = [O.beam_init(model, k, mesh, F, None, c) for c in range(4)]
+    q, p = mesh.points()
+    env = (math.pi / k) ** 1.5 * np.exp(-0.25 * k * (np.sum((q - x0) ** 2, 1) + np.sum((p - p0) ** 2, 1)))
+    n = p / np.linalg.norm(p, axis=1)[:, None]
+    bn = np.abs(n @ b)
+    closed = [bn * env / 2, bn * env / 2, np.sqrt(np.maximum(b @ b - bn ** 2, 0)) * env / 2,
+              np.sqrt(np.maximum(b @ b - bn ** 2, 0)) * env / 2]
+    top = max(c.max() for c in closed)
+    for eps in (1e-1, 1e-3, 1e-6):
+        sel = O.psi_select(groups, eps)
+        for c in range(4):
+            ratio = closed[c] / top
+            clear = np.abs(ratio / eps - 1.0) > 1e-4
+            want = set(np.nonzero((ratio > eps) & clear)[0])
+            got = set(sel[c][2]) & set(np.nonzero(clear)[0])
+            assert got == want, (eps, c, len(got), len(want))
+            # survivors keep their order and their states
+            np.testing.assert_array_equal(sel[c][0], groups[c][0][sel[c][2]])
+        kept = sum(len(g[2]) for g in sel)
+        assert 0 < kept < 4 * mesh.M or eps == 1e-6
+    allk = O.psi_select(groups, 0.0)
+    assert all(len(a[2]) == mesh.M for a in allk)
