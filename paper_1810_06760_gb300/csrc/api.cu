@@ -168,7 +168,7 @@ void HostBuf::release() {
 }
 void Workspace::release() {
     for (DevBuf *d : {&keys, &keys_alt, &vals, &vals_alt, &hist, &scan_blocks, &cell_start, &rec, &items, &tiles,
-                      &partial, &pts, &status})
+                      &partial, &pts, &status, &rec_amax})
         d->release();
     for (HostBuf *h : {&h_cell_start, &h_items, &h_tiles}) h->release();
 }
@@ -780,7 +780,15 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
         }
         FGA_CUDA(cudaMemcpyAsync(samp.p, hsamp.p, sbytes, cudaMemcpyHostToDevice, s));
         FGA_TRY(ws.rec.ensure((size_t)per_sample * ns));
-        SampleWindow sw{ns, reinterpret_cast<const int *>(samp.as<char>() + soff), samp.p, ws.rec.p, {}, {}, plan.n_rec};
+        // FP32 lattice sums take their operand scale from the amplitude bound the RK4 kernel forms per sample
+        unsigned *amax = nullptr;
+        if (rxL && !fp64) {
+            FGA_TRY(ws.rec_amax.ensure(sizeof(unsigned) * (size_t)ns));
+            amax = ws.rec_amax.as<unsigned>();
+            FGA_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)ns, s));
+        }
+        SampleWindow sw{ns, reinterpret_cast<const int *>(samp.as<char>() + soff), samp.p, ws.rec.p, {}, {}, plan.n_rec,
+                        amax};
         for (int c = 0; c < 4; c++) {
             sw.n_in[c] = plan.n_in[c];
             sw.rec_off[c] = plan.rec_off[c];
@@ -790,7 +798,8 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
             void *out = static_cast<char *>(seis_out) + rb * 6 * (size_t)nrx * (size_t)(js + j);
             const void *rec = static_cast<const char *>(ws.rec.p) + (size_t)per_sample * j;
             if (rxL)
-                FGA_TRY(run_lattice(ws, lplan, b->precision, rec, b->k, rw, out, s));
+                FGA_TRY(run_lattice(ws, lplan, b->precision, rec, b->k, rw, out, s, P_GATHER,
+                                    amax ? reinterpret_cast<const float *>(amax + j) : nullptr));
             else
                 FGA_TRY(run_sum(ws, plan, b->precision, rec, sd->rx, b->k, rw, out, s));
         }

@@ -154,6 +154,7 @@ size_t block_cache_bytes();
 // scratch used by binning and the Gaussian sum
 struct Workspace {
     DevBuf keys, keys_alt, vals, vals_alt, hist, scan_blocks, cell_start, rec, items, tiles, partial, pts;
+    DevBuf rec_amax;   // per sample of a window: bound of the records' amplitude entries (FP32 path)
     // status words of one call: [0] a bounded wait of the tensor-core lattice sum ran out,
     // [1] non-finite values in the beam state or the outputs
     DevBuf status;
@@ -206,6 +207,7 @@ struct SampleWindow {
     int64_t n_in[4];        // class c: the first n_in[c] beams of its block get records ...
     int64_t rec_off[4];     // ... at record index rec_off[c] + (position - off_cls[c])
     int64_t n_rec;          // records per sample
+    unsigned *amax;         // DEVICE, FP32 path or NULL: per sample, bits of max |A entry| over its records
 };
 fga_status launch_propagate(const fga_model *m, fga_beams *b, double dt, int nsteps, const SampleWindow *sw,
                             cudaStream_t s);

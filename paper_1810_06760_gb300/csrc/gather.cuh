@@ -51,13 +51,14 @@ void tile_shape_tc(const fga_lattice &L, int T[3]);
 // single-plane lattices with uniform axes 0 and 1: the warp-specialised plane kernel (tc_plane.cu)
 void tile_shape_plane(const fga_lattice &L, int T[3]);
 bool plane_tc_eligible(const LatticePlan &plan);
+// amax: DEVICE bound of the records' |A| entries (bits of a non-negative float), or NULL to compute it
 fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec, double k, double rw, void *u,
-                        cudaStream_t s, int cat);
+                        cudaStream_t s, int cat, const float *amax = nullptr);
 int64_t read_plane_pair_counter(bool reset);
 // |A| bound of n records into *out (zeroed by the caller)
 fga_status rec_absmax(const float *rec, int64_t n, float *out, cudaStream_t s, int cat);
 fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *rec, double k, double rw, void *u,
-                          cudaStream_t s, int cat);
+                          cudaStream_t s, int cat, const float *amax = nullptr);
 fga_status lattice_reduce_f32(const float *partial, const LatticePlan &plan, void *u, cudaStream_t s);
 int64_t read_tc_pair_counter(bool reset);
 // per-beam-set status words (Workspace::status): zeroed by status_reset before a call's work, read by
@@ -71,7 +72,7 @@ fga_status flag_nonfinite(Workspace &ws, const void *data, int64_t n, int precis
 fga_status flag_nonfinite_state(Workspace &ws, const void *st, int64_t cap, int64_t nb, int nf, int precision,
                                 cudaStream_t s);
 fga_status run_lattice(Workspace &ws, const LatticePlan &plan, int precision, const void *rec, double k, double rw,
-                       void *u, cudaStream_t s, int cat = P_GATHER);
+                       void *u, cudaStream_t s, int cat = P_GATHER, const float *amax = nullptr);
 int64_t read_lattice_pair_counter(bool reset);
 
 fga_status sort_keys_to_perm(Workspace &ws, int32_t *keys, int64_t n, int nbuckets, int32_t **perm_out,

@@ -534,10 +534,10 @@ fga_status lattice_reduce_f32(const float *partial, const LatticePlan &plan, voi
 
 // FP32: the tensor-core kernel (plans built with tc = true); FP64: the CUDA-core kernel
 fga_status run_lattice(Workspace &ws, const LatticePlan &plan, int precision, const void *rec, double k, double rw,
-                       void *u, cudaStream_t s, int cat) {
+                       void *u, cudaStream_t s, int cat, const float *amax) {
     if (precision == FGA_PREC_FP64) return run_lattice_t<double>(ws, plan, rec, k, rw, u, s, cat);
-    if (plane_tc_eligible(plan)) return run_plane_tc(ws, plan, rec, k, rw, u, s, cat);
-    return run_lattice_tc(ws, plan, rec, k, rw, u, s, cat);
+    if (plane_tc_eligible(plan)) return run_plane_tc(ws, plan, rec, k, rw, u, s, cat, amax);
+    return run_lattice_tc(ws, plan, rec, k, rw, u, s, cat, amax);
 }
 
 }  // namespace fga

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st
                                                   int64_t cap, int64_t beg, int64_t n, R sg, R dt, int nsteps,
                                                   int n_samp, const int *__restrict__ samp_step,
                                                   const R *__restrict__ samp_theta, R w, R *__restrict__ rec,
-                                                  int64_t rec_lim, int64_t rec_stride) {
+                                                  int64_t rec_lim, int64_t rec_stride, unsigned *__restrict__ amax) {
     const int64_t b = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= beg + n) return;
     R y[NF], acc[NF], tmp[NF], kk[NF], qc[3];
@@ -65,12 +65,22 @@ __global__ void __launch_bounds__(128) rk4_kernel(ModelDev M, R *__restrict__ st
             }
             const int step = it >> 2;
             while (it >= 0 && js < n_samp && samp_step[js] == step) {
+                float mloc = 0.f;   // largest |A entry| of this thread's record
                 if (b - beg < rec_lim) {
                     R r[REC];
                     beam_record6<R, WAVE>(ref_e1, y, s0, acc, kk, dt, samp_theta[js], w, r);
                     R *dst = rec + ((int64_t)js * rec_stride + (b - beg)) * REC;
 #pragma unroll
                     for (int q = 0; q < REC; q++) dst[q] = r[q];
+#pragma unroll
+                    for (int q = 6; q < REC; q++) mloc = fmaxf(mloc, fabsf((float)r[q]));
+                }
+                if (amax) {
+                    // the sample's bound: maximum over the converged lanes, one atomic by the lowest of them
+                    // (non-negative floats order like their bit patterns; a NaN is left to the solve's check)
+                    const unsigned mask = __activemask();
+                    const unsigned v = __reduce_max_sync(mask, mloc == mloc ? __float_as_uint(mloc) : 0u);
+                    if ((int)(threadIdx.x & 31) == __ffs(mask) - 1 && v) atomicMax(amax + js, v);
                 }
                 js++;
             }
@@ -137,7 +147,7 @@ static void launch_one(const fga_model *m, fga_beams *b, int cls, R dt, int nste
     rk4_kernel<R, WAVE, MED><<<(unsigned)blocks, T, 0, s>>>(
         m->dev, b->state.as<R>(), b->flags.as<int32_t>(), b->cap, b->off_cls[cls], n, sg, dt, nsteps,
         sw ? sw->n : 0, sw ? sw->step : nullptr, sw ? static_cast<const R *>(sw->theta) : nullptr, (R)b->w, rec,
-        sw ? sw->n_in[cls] : 0, sw ? sw->n_rec : 0);
+        sw ? sw->n_in[cls] : 0, sw ? sw->n_rec : 0, (sw && sizeof(R) == 4) ? sw->amax : nullptr);
 }
 
 template <typename R, int MED>

@@ -544,7 +544,7 @@ void tile_shape_tc(const fga_lattice &L, int T[3]) {
 }
 
 fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *rec, double k, double rw, void *u,
-                          cudaStream_t s, int cat) {
+                          cudaStream_t s, int cat, const float *amax_in) {
     const int T0 = plan.T[0], T1 = plan.T[1], T2 = plan.T[2];
     const int TP = T0 * T1 * T2;
     if (T0 > LT_T0_MAX || T1 * T2 > LT_M || T0 + T1 + T2 > LT_TA_MAX) {
@@ -585,7 +585,9 @@ fga_status run_lattice_tc(Workspace &ws, const LatticePlan &plan, const void *re
     const int cnt = prof_counting() ? 1 : 0;
     prof_add_pairs_tested(plan.pairs_tested);
     if (plan.nitems > 0) {
-        {
+        if (amax_in) {
+            amax = const_cast<float *>(amax_in);
+        } else {
             ProfScope ps(cat, s);
             const int blocks = (int)std::min<int64_t>(152 * 4, (plan.n_rec * 6 + 255) / 256 + 1);
             rec_absmax_kernel<<<blocks, 256, 0, s>>>(static_cast<const float *>(rec), plan.n_rec, amax);

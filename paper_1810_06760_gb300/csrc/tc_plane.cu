@@ -6,12 +6,14 @@
 //   U[(j,c)][i] = sum_b  W_bc E1_b(x_j) E0_b(x_i),      W_bc = A_bc E2_b(x_2)
 //
 // is a complex matrix product over the beams b (the contraction index): rows (j, c) -> TMEM lanes
-// r = 32 h + 3 t + c with j = h J + t (J = ceil(T1/2), h in {0, 1}), columns i -> Re/Im of the
-// accumulator (C' = A_re B'_re^T + A_im B'_im^T with B'_re = [Re E0; Im E0], B'_im = [-Im E0; Re E0]).
+// r = 32 h + 3 t + c with j = h J + t (J = ceil(T1/2), h in {0, 1}), columns i.  One B operand
+// B' = [Re E0; Im E0] serves both halves of the complex product: A_re B'^T and A_im B'^T go to two
+// accumulators, and Re U = A_re Re E0 - A_im Im E0, Im U = A_re Im E0 + A_im Re E0 are formed in the
+// epilogue.
 // Both operands are FP16 hi/lo splits of the FP32 values (hi*hi + hi*lo + lo*hi, FP32 accumulation),
 // as in the other tensor-core kernels of the library.
 //
-// One persistent CTA per SM: six producer warps and one MMA warp.
+// One persistent CTA per SM: seven producer warps and one MMA warp.
 //  - Each producer warp owns one shared-memory stage.  It filters its share of an item's candidate
 //    records (the beams within the window radius of the tile's box; four chunks of 32 in flight) into a
 //    queue and turns every 32 kept beams into one operand block: lane (h, p) takes beams 2p and 2p+1,
@@ -24,9 +26,10 @@
 //    With one producer per stage every parity wait is exactly one phase behind the barrier.
 //  - The MMA warp's elected thread takes the producers' blocks in a fixed cyclic order (so the
 //    accumulation order, and the result, do not depend on timing) and issues four tcgen05.mma per block
-//    (two K steps x re/im): each multiplies [A_hi; A_lo] (M = 128) by [B_hi; B_lo] (N = 4 n_c), so one
-//    instruction forms the three split products hi*hi, hi*lo and lo*hi (and an unused lo*lo quarter);
-//    a tcgen05.mma costs about the same for N = 48 as for N = 96, so fewer, wider instructions win.
+//    (two K steps x re/im): each multiplies [A_hi; A_lo] (M = 128) by [B_hi; B_lo] (N = 4 n_c) into the
+//    re or the im accumulator, so one instruction forms the three split products hi*hi, hi*lo and lo*hi
+//    (and an unused lo*lo quarter); a tcgen05.mma costs about the same for N = 48 as for N = 96, so
+//    fewer, wider instructions win.
 //  - A producer closes its part of an item with an END block (no data); once every producer has, the
 //    last commit is awaited and the accumulator rows go to the plan's per-item partial sums, reduced as
 //    for the other lattice kernels.
@@ -60,14 +63,14 @@ int64_t read_plane_pair_counter(bool reset) {
 
 namespace {
 
-constexpr int PL_PROD = 6;                     // producer warps, one shared-memory stage each
+constexpr int PL_PROD = 7;                     // producer warps, one shared-memory stage each
 constexpr int PL_THREADS = (PL_PROD + 1) * 32; // + the MMA warp
 constexpr int PL_KB = 32;                      // beams per block
 constexpr int PL_LBO = 144;                    // bytes between K-adjacent core matrices
 constexpr int PL_SBO_A = 592;                  // bytes between row-adjacent core matrices of A
 constexpr int PL_A_COPY = 8 * PL_SBO_A;        // one A copy: 64 rows (8 row groups)
 constexpr int PL_QUEUE = 64;                   // kept records queued per producer warp (31 + 32 used)
-constexpr int PL_T0_MAX = 24, PL_T1_MAX = 20;   // six 32 KB stages fit with n_c <= 24
+constexpr int PL_T0_MAX = 24, PL_T1_MAX = 20;   // seven 26 KB stages fit with n_c <= 24
 
 struct PlaneArgs {
     const float *rec;        // records [n_rec][12]: Q, P, weighted polarised amplitude (3 complex)
@@ -220,8 +223,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
             unsigned long long pairs = 0;
             unsigned char *st = smem + w * P.stage_bytes;
             unsigned char *Are = st, *Are_lo = st + PL_A_COPY, *Aim = st + 2 * PL_A_COPY, *Aim_lo = st + 3 * PL_A_COPY;
-            unsigned char *Bre = st + 4 * PL_A_COPY, *Bre_lo = Bre + P.b_copy, *Bim = Bre + 2 * P.b_copy,
-                          *Bim_lo = Bre + 3 * P.b_copy;
+            unsigned char *Bre = st + 4 * PL_A_COPY, *Bre_lo = Bre + P.b_copy;
             // wait until the MMAs of this stage's previous block are done (exactly one phase back)
             auto acquire = [&](int site, int n) -> bool {
                 bool ok = *abort_flag == 0;
@@ -340,11 +342,10 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
                             q1[u].y *= g1;
                         }
                     }
-                    // ---- B: B're = [Re E0; Im E0], B'im = [-Im E0; Re E0]; half 0 stores the Re words,
-                    // half 1 the Im words; each half forms E0 on its parity and gets the other one ----
+                    // ---- B: B' = [Re E0; Im E0]; half 0 stores the Re words, half 1 the Im words; each half
+                    // forms E0 on its parity and gets the other one ----
                     const uint32_t lanekb = koff(0, 2 * p, 0);
                     const uint32_t rowoff_a = h == 0 ? 0u : (uint32_t)((NC >> 3) * SBOB);   // Re rows | Im rows
-                    const uint32_t rowoff_b = h == 0 ? (uint32_t)((NC >> 3) * SBOB) : 0u;
 #pragma unroll
                     for (int i2 = 0; i2 < (T0T ? T0T : T0); i2 += 2) {
                         float2 mine[2] = {f0[0], f0[1]}, other[2];
@@ -361,13 +362,9 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
                             const float2 v1 = (par == h) ? mine[1] : other[1];
                             uint32_t wh, wl;
                             split2(h == 0 ? v0.x : v0.y, h == 0 ? v1.x : v1.y, wh, wl);
-                            const uint32_t ri = lanekb + (uint32_t)((i >> 3) * SBOB + (i & 7) * 16);
-                            const uint32_t ra = ri + rowoff_a, rb = ri + rowoff_b;
-                            const uint32_t neg = h == 0 ? 0u : 0x80008000u;
+                            const uint32_t ra = lanekb + (uint32_t)((i >> 3) * SBOB + (i & 7) * 16) + rowoff_a;
                             sts32(Bre, ra, wh);
                             sts32(Bre_lo, ra, wl);
-                            sts32(Bim, rb, wh ^ neg);
-                            sts32(Bim_lo, rb, wl ^ neg);
                         }
 #pragma unroll
                         for (int u = 0; u < 2; u++) {
@@ -458,19 +455,20 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
                     const unsigned char *st = smem + w * P.stage_bytes;
                     const uint32_t a_base = tc::smem_u32(st), b_base = tc::smem_u32(st + 4 * PL_A_COPY);
                     // one MMA per K step and re/im half: A = [A_hi; A_lo] (128 rows: the hi copy is followed by
-                    // the lo copy with the same row stride), B = [B_hi; B_lo] (4 n_c rows, likewise), so the
+                    // the lo copy with the same row stride), B = [B_hi; B_lo] (4 n_c rows, likewise), so each
                     // accumulator holds hi*hi (rows 0..63, columns 0..2n_c), hi*lo (rows 0..63, columns
                     // 2n_c..4n_c) and lo*hi (rows 64..127, columns 0..2n_c); the lo*lo quarter is not used
                     for (int ks = 0; ks < PL_KB / 16; ks++) {
                         const uint32_t kof = ks * 2 * PL_LBO;
+                        const uint32_t acc = started ? 1u : 0u;
+                        const uint64_t db = tc::smem_desc_lbo_sbo(b_base + kof, PL_LBO, SBOB);
                         for (int half = 0; half < 2; half++) {
+                            // half 0: A_re -> accumulator columns [0, 4 n_c); half 1: A_im -> [4 n_c, 8 n_c)
                             const uint32_t a_hi = a_base + (2 * half) * PL_A_COPY;
-                            const uint32_t b_hi = b_base + (2 * half) * P.b_copy;
                             const uint64_t da = tc::smem_desc_lbo_sbo(a_hi + kof, PL_LBO, PL_SBO_A);
-                            const uint64_t db = tc::smem_desc_lbo_sbo(b_hi + kof, PL_LBO, SBOB);
-                            tc::mma_f16(tmem, da, db, idesc, started ? 1u : 0u);
-                            started = true;
+                            tc::mma_f16(tmem + (uint32_t)(half * 2 * NR), da, db, idesc, acc);
                         }
+                        started = true;
                     }
                     tc::commit(tc::smem_u32(empty + w));
                 } else {
@@ -490,24 +488,25 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
-        // ---- epilogue (TMEM lane = accumulator row): warps 2 and 3 park the lo*hi rows (lanes 64..127) in
-        // the idle stage memory, then warps 0 and 1 add hi*hi + hi*lo + lo*hi of rows 0..63 and write the
-        // item's partial sums ----
+        // ---- epilogue (TMEM lane = accumulator row): warps 2 and 3 park the lo*hi rows (lanes 64..127) of
+        // both accumulators in the idle stage memory, then warps 0 and 1 add hi*hi + hi*lo + lo*hi of rows
+        // 0..63, combine the re and im accumulators and write the item's partial sums ----
         const bool have = misc[2] != 0 && *abort_flag == 0;
-        float *park = reinterpret_cast<float *>(smem);   // [64][2 n_c]
+        float *park = reinterpret_cast<float *>(smem);   // [64][2][2 n_c]
         if (warp == 2 || warp == 3) {
             const int r = 32 * (warp - 2) + lane;
-            for (int c0 = 0; c0 < NR; c0 += 8) {
-                float v[8];
-                if (have) {
-                    tc::ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-                } else {
+            for (int a = 0; a < 2; a++)
+                for (int c0 = 0; c0 < NR; c0 += 8) {
+                    float v[8];
+                    if (have) {
+                        tc::ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * 2 * NR + c0), v);
+                    } else {
 #pragma unroll
-                    for (int u = 0; u < 8; u++) v[u] = 0.f;
+                        for (int u = 0; u < 8; u++) v[u] = 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; u++) park[(r * 2 + a) * NR + c0 + u] = v[u];
                 }
-#pragma unroll
-                for (int u = 0; u < 8; u++) park[r * NR + c0 + u] = v[u];
-            }
         }
         tc::fence_before();
         __syncthreads();
@@ -521,16 +520,26 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
             for (int c0 = 0; c0 < NC; c0 += 8) {
                 float re[8], im[8];
                 if (have) {
-                    float a[8], b[8];
+                    // x_a(c) = hi*hi + hi*lo + lo*hi of accumulator a (0: A_re, 1: A_im) against Re E0 (c = 0)
+                    // or Im E0 (c = 1)
+                    float x[2][2][8];
                     const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16);
-                    tc::ld8(base + (uint32_t)c0, re);
-                    tc::ld8(base + (uint32_t)(NC + c0), im);
-                    tc::ld8(base + (uint32_t)(NR + c0), a);
-                    tc::ld8(base + (uint32_t)(NR + NC + c0), b);
+#pragma unroll
+                    for (int a = 0; a < 2; a++)
+#pragma unroll
+                        for (int c = 0; c < 2; c++) {
+                            float hl[8];
+                            const uint32_t col = (uint32_t)(a * 2 * NR + c * NC + c0);
+                            tc::ld8(base + col, x[a][c]);
+                            tc::ld8(base + col + (uint32_t)NR, hl);
+#pragma unroll
+                            for (int u = 0; u < 8; u++)
+                                x[a][c][u] += hl[u] + park[(row * 2 + a) * NR + c * NC + c0 + u];
+                        }
 #pragma unroll
                     for (int u = 0; u < 8; u++) {
-                        re[u] += a[u] + park[row * NR + c0 + u];
-                        im[u] += b[u] + park[row * NR + NC + c0 + u];
+                        re[u] = x[0][0][u] - x[1][1][u];
+                        im[u] = x[0][1][u] + x[1][0][u];
                     }
                 } else {
 #pragma unroll
@@ -574,7 +583,7 @@ void tile_shape_plane(const fga_lattice &L, int T[3]) {
 }
 
 fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec, double k, double rw, void *u,
-                        cudaStream_t s, int cat) {
+                        cudaStream_t s, int cat, const float *amax_in) {
     const int T0 = plan.T[0], T1 = plan.T[1];
     const int TP = T0 * T1;
     const int nc = (T0 + 7) / 8 * 8;
@@ -582,7 +591,7 @@ fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec,
     // halves in one instruction land 16 banks apart
     const int sbo_b = plane_sbo_b(nc);
     const int b_copy = (2 * nc / 8) * sbo_b;
-    const int stage_bytes = (4 * PL_A_COPY + 4 * b_copy + 1023) / 1024 * 1024;
+    const int stage_bytes = (4 * PL_A_COPY + 2 * b_copy + 1023) / 1024 * 1024;
     const int bytes = PL_PROD * stage_bytes + PL_A_COPY + 256 + PL_PROD * PL_QUEUE * 48;
     if (bytes > 227 * 1024) {
         set_error("plane tile does not fit the tensor-core plane kernel");
@@ -595,7 +604,7 @@ fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec,
     if (!ws.status.p) FGA_TRY(status_reset(ws, s));
     prof_add_pairs_tested(plan.pairs_tested);
     if (plan.nitems > 0) {
-        FGA_TRY(rec_absmax(static_cast<const float *>(rec), plan.n_rec, amax, s, cat));
+        if (!amax_in) FGA_TRY(rec_absmax(static_cast<const float *>(rec), plan.n_rec, amax, s, cat));
         PlaneArgs A;
         A.rec = static_cast<const float *>(rec);
         A.items = plan.items;
@@ -616,11 +625,11 @@ fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec,
         A.x2 = (float)plan.x_first[2];
         A.k = (float)k;
         A.rw2 = (float)(rw * rw);
-        A.amax = amax;
+        A.amax = amax_in ? amax_in : amax;
         A.partial = ws.partial.as<float>();
         A.err = ws.status.as<int>();
-        // the accumulator: 4 n_c columns (hi*hi and hi*lo side by side)
-        A.tcols = 4 * nc <= 32 ? 32u : (4 * nc <= 64 ? 64u : 128u);
+        // the accumulators: 2 x 4 n_c columns (re and im, each hi*hi and hi*lo side by side)
+        A.tcols = 8 * nc <= 32 ? 32u : (8 * nc <= 64 ? 64u : (8 * nc <= 128 ? 128u : 256u));
         int dev = 0, sms = 152;
         FGA_CUDA(cudaGetDevice(&dev));
         FGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
