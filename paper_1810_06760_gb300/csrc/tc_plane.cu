@@ -102,6 +102,15 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = *reinterpret_cast<const uint32_t *>(&ll);
 }
 
+// the same split of a packed pair, the residual by one packed subtraction
+__device__ __forceinline__ void split2p(float2 v, uint32_t &hi, uint32_t &lo) {
+    const __half2 hh = __float22half2_rn(v);
+    const float2 hf = __half22float2(hh);
+    const __half2 ll = __float22half2_rn(__fadd2_rn(v, make_float2(-hf.x, -hf.y)));
+    hi = *reinterpret_cast<const uint32_t *>(&hh);
+    lo = *reinterpret_cast<const uint32_t *>(&ll);
+}
+
 __device__ __forceinline__ void sts32(unsigned char *base, uint32_t off, uint32_t v) {
     *reinterpret_cast<uint32_t *>(base + off) = v;
 }
@@ -320,27 +329,40 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
                 if (ok) {
                     // ---- A: rows r = 32 h + 3 t + c, j = h J + t ----
                     const uint32_t lanek = koff(0, 2 * p, 0) + (uint32_t)(h * 4 * PL_SBO_A);
+                    // the lane's two beams side by side in packed FP32x2 registers: (beam 0, beam 1)
+                    float2 Wr[3], Wi[3];
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        Wr[c] = make_float2(W[0][c].x, W[1][c].x);
+                        Wi[c] = make_float2(-W[0][c].y, -W[1][c].y);   // negated: re = Wr F - Wi' ...
+                    }
+                    float2 Fr = make_float2(f1[0].x, f1[1].x), Fi = make_float2(f1[0].y, f1[1].y);
+                    float2 Qr = make_float2(q1[0].x, q1[1].x), Qi = make_float2(q1[0].y, q1[1].y);
+                    const float2 G1 = make_float2(g1, g1);
 #pragma unroll
                     for (int tj = 0; tj < (JT ? JT : J); tj++) {
 #pragma unroll
                         for (int c = 0; c < 3; c++) {
                             const int row = 3 * tj + c;   // within the half (the half's 32 rows = 4 row groups)
-                            const float2 v0 = cmul(W[0][c], f1[0]), v1 = cmul(W[1][c], f1[1]);
+                            // v = W F: re = Wr Fr - Wi Fi, im = Wr Fi + Wi Fr (Wi held negated)
+                            const float2 vr = __ffma2_rn(Wi[c], Fi, __fmul2_rn(Wr[c], Fr));
+                            const float2 vi = __ffma2_rn(make_float2(-Wi[c].x, -Wi[c].y), Fr, __fmul2_rn(Wr[c], Fi));
                             uint32_t rh, rl, ih, il;
-                            split2(v0.x, v1.x, rh, rl);
-                            split2(v0.y, v1.y, ih, il);
+                            split2p(vr, rh, rl);
+                            split2p(vi, ih, il);
                             const uint32_t o = lanek + (uint32_t)((row >> 3) * PL_SBO_A + (row & 7) * 16);
                             sts32(Are, o, rh);
                             sts32(Are_lo, o, rl);
                             sts32(Aim, o, ih);
                             sts32(Aim_lo, o, il);
                         }
-#pragma unroll
-                        for (int u = 0; u < 2; u++) {
-                            f1[u] = cmul(f1[u], q1[u]);
-                            q1[u].x *= g1;
-                            q1[u].y *= g1;
-                        }
+                        // F <- F Q, Q <- Q g1 (both beams at once)
+                        const float2 nr = __ffma2_rn(make_float2(-Fi.x, -Fi.y), Qi, __fmul2_rn(Fr, Qr));
+                        const float2 ni = __ffma2_rn(Fi, Qr, __fmul2_rn(Fr, Qi));
+                        Fr = nr;
+                        Fi = ni;
+                        Qr = __fmul2_rn(Qr, G1);
+                        Qi = __fmul2_rn(Qi, G1);
                     }
                     // ---- B: B' = [Re E0; Im E0]; half 0 stores the Re words, half 1 the Im words; each half
                     // forms E0 on its parity and gets the other one ----
