@@ -264,6 +264,19 @@ fga_status fga_beams_count(const fga_beams *b, int64_t *n_by_class);
 fga_status fga_beams_export(const fga_beams *b, double *state_host, int32_t *meta_host);
 fga_status fga_beams_destroy(fga_beams *b);
 
+/* The parameters a beam set was made with: HOST k, the quadrature weight w = prod_d(dq_d dp_d)/(2 pi/k)^{9/2}
+ * of Eq. FGA, and the precision; any pointer may be NULL. */
+fga_status fga_beams_params(const fga_beams *b, double *k, double *w, int *precision);
+
+/* A beam set from exported beams (to resume a propagation, or to propagate beams made elsewhere): n beams,
+ * HOST state [n][48] float64 in the fga_beams_export layout (the last two values ignored), HOST meta
+ * int32 [n] with only the class (bits 0-1) and S-frame (bit 2) bits, and the k, w and precision of the
+ * set they came from (fga_beams_params).  Beams are grouped by class, keeping their order within a
+ * class; the Q compensation starts at zero.  Smooth media only (a layered population carries lineage
+ * and layer bits).  Synchronous.  Errors: INVALID_ARG (counts, k or w <= 0, other meta bits), OOM, CUDA. */
+fga_status fga_beams_import(int64_t n, const double *state, const int32_t *meta, double k, double w, int precision,
+                            fga_beams **out, fga_stream_t s);
+
 /* All live beams in storage order (the form for layered media, where beams split at interfaces).
  * Writes up to cap beams: HOST state [n][48] (as fga_beams_export), meta int32 [n] (bits 0-1 class,
  * 2 S frame e1, 4-7 layer, 8-11 interfaces crossed, 13-14 class of the initial beam of the lineage),

@@ -944,6 +944,7 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
     const int32_t *fl = b->flags.as<int32_t>();
     const R dt = (R)sd->dt;
     // 1. checkpoints at steps C, 2C, ... (the last one at N when C does not divide N is not needed)
+    NvtxRange nr_fwd("fga_solve_vjp: checkpoints");
     for (int cls = 0; cls < 4; cls++) {
         const int64_t nc = b->n_cls[cls];
         if (!nc) continue;
@@ -962,6 +963,7 @@ fga_status run_vjp(const fga_model *m, const fga_init_desc *init, const fga_solv
     int j = (int)sstep.size() - 1;
     int jst = 0;  // reverse steps since the last scatter of node cotangents
     for (int sgi = nseg - 1; sgi >= 0; sgi--) {
+        NvtxRange nr_seg("fga_solve_vjp: segment (recompute, reverse)");
         const int n0 = sgi * C, len = std::min(C, N - n0);
         // 2a. the segment's states: slot 0 = checkpoint, slots 1..len recomputed
         FGA_CUDA(cudaMemcpyAsync(SEG, CK + (size_t)sgi * slot, sizeof(R) * (size_t)slot, cudaMemcpyDeviceToDevice, s));

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <vector>
 
 #include "fga_beam.cuh"
@@ -650,7 +651,10 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
         sth[(size_t)j] = u - n;
     }
     fga_beams *b = nullptr;
-    FGA_TRY(fga_decompose(m, init, &b, s_));
+    {
+        NvtxRange nr("fga_solve: decompose");
+        FGA_TRY(fga_decompose(m, init, &b, s_));
+    }
     struct Guard {
         fga_beams *b;
         ~Guard() { fga_beams_destroy(b); }
@@ -744,9 +748,13 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
             n0 += nw;
             continue;
         }
+        NvtxRange nr_win("fga_solve: window");
         int32_t *perm = nullptr;
-        FGA_TRY(bin_beams(b, grx, &perm, s));
-        FGA_TRY(permute_beams(b, perm, s));
+        {
+            NvtxRange nr("fga_solve: binning");
+            FGA_TRY(bin_beams(b, grx, &perm, s));
+            FGA_TRY(permute_beams(b, perm, s));
+        }
         SumPlan plan;
         LatticePlan lplan;
         if (rxL) {
@@ -793,7 +801,11 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
             sw.n_in[c] = plan.n_in[c];
             sw.rec_off[c] = plan.rec_off[c];
         }
-        FGA_TRY(launch_propagate(m, b, sd->dt, nw, &sw, s));
+        {
+            NvtxRange nr("fga_solve: propagate");
+            FGA_TRY(launch_propagate(m, b, sd->dt, nw, &sw, s));
+        }
+        NvtxRange nr_sums("fga_solve: sums");
         for (int j = 0; j < ns; j++) {
             void *out = static_cast<char *>(seis_out) + rb * 6 * (size_t)nrx * (size_t)(js + j);
             const void *rec = static_cast<const char *>(ws.rec.p) + (size_t)per_sample * j;
@@ -806,10 +818,13 @@ fga_status solve_impl(const fga_model *m, const fga_init_desc *init, const fga_s
         js = j1;
         n0 += nw;
     }
-    if (snL)
-        FGA_TRY(reconstruct_lattice_now(b, snL, rw, snap_out, s));
-    else if (sd->n_snap > 0)
-        FGA_TRY(reconstruct_now(b, sd->snap, snh, sd->n_snap, rw, snap_out, s));
+    {
+        NvtxRange nr("fga_solve: snapshot");
+        if (snL)
+            FGA_TRY(reconstruct_lattice_now(b, snL, rw, snap_out, s));
+        else if (sd->n_snap > 0)
+            FGA_TRY(reconstruct_now(b, sd->snap, snh, sd->n_snap, rw, snap_out, s));
+    }
     FGA_TRY(flag_solve_nonfinite(b, sd, nrx, seis, seis_out, snap_out, s));
     // the beam set is freed by the guard; its buffers must not be in use (the check synchronises s)
     return status_check(ws, s, "fga_solve");
@@ -916,6 +931,69 @@ fga_status fga_beams_export(const fga_beams *b, double *state_host, int32_t *met
         if (meta_host) meta_host[row] = fl[(size_t)i];
         if (state_host) export_row(st, cap, i, state_host + row * 48);
     }
+    return FGA_OK;
+}
+
+fga_status fga_beams_params(const fga_beams *b, double *k, double *w, int *precision) {
+    FGA_CHECK(b, "fga_beams_params: NULL beams");
+    if (k) *k = b->k;
+    if (w) *w = b->w;
+    if (precision) *precision = b->precision;
+    return FGA_OK;
+}
+
+fga_status fga_beams_import(int64_t n, const double *state, const int32_t *meta, double k, double w, int precision,
+                            fga_beams **out, fga_stream_t s_) {
+    cudaStream_t s = (cudaStream_t)s_;
+    FGA_CHECK(out && (n == 0 || (state && meta)), "fga_beams_import: NULL argument");
+    FGA_CHECK(n >= 0 && n < ((int64_t)1 << 31), "fga_beams_import: n must lie in [0, 2^31)");
+    FGA_CHECK(std::isfinite(k) && k > 0 && std::isfinite(w) && w > 0, "fga_beams_import: k and w must be > 0");
+    FGA_CHECK(precision == FGA_PREC_FP32 || precision == FGA_PREC_FP64, "fga_beams_import: bad precision");
+    for (int64_t i = 0; i < n; i++)
+        FGA_CHECK((meta[i] & ~(FL_CLASS_MASK | FL_REF_E1)) == 0, "fga_beams_import: meta holds more than class and frame bits");
+    fga_beams *b = new fga_beams();
+    std::unique_ptr<fga_beams, fga_status (*)(fga_beams *)> hold(b, fga_beams_destroy);
+    b->precision = precision;
+    b->k = k;
+    b->w = w;
+    // class blocks in class order, beams in their given order within a block
+    std::vector<int64_t> order((size_t)n);
+    int64_t cnt[4] = {0, 0, 0, 0};
+    for (int64_t i = 0; i < n; i++) cnt[meta[i] & FL_CLASS_MASK]++;
+    int64_t off = 0;
+    for (int c = 0; c < 4; c++) {
+        b->off_cls[c] = off;
+        b->n_cls[c] = cnt[c];
+        off += cnt[c];
+    }
+    b->nb = n;
+    b->cap = std::max<int64_t>(32, (n + 31) / 32 * 32);
+    int64_t pos[4] = {b->off_cls[0], b->off_cls[1], b->off_cls[2], b->off_cls[3]};
+    for (int64_t i = 0; i < n; i++) order[(size_t)pos[meta[i] & FL_CLASS_MASK]++] = i;
+    const size_t rb = precision == FGA_PREC_FP64 ? 8 : 4;
+    FGA_TRY(b->state.ensure(rb * NFS * b->cap));
+    FGA_TRY(b->flags.ensure(4 * b->cap));
+    FGA_TRY(b->id.ensure(4 * b->cap));
+    // structure of arrays on the host, then one copy each (compensation of Q starts at zero)
+    std::vector<int32_t> fl((size_t)b->cap, 0), ids((size_t)b->cap, 0);
+    std::vector<double> sd((size_t)(NFS * b->cap), 0.0);
+    for (int64_t r = 0; r < n; r++) {
+        const int64_t i = order[(size_t)r];
+        for (int f = 0; f < NF; f++) sd[(size_t)(f * b->cap + r)] = state[i * 48 + f];
+        fl[(size_t)r] = meta[i];
+        ids[(size_t)r] = (int32_t)(r - b->off_cls[meta[i] & FL_CLASS_MASK]);
+    }
+    if (precision == FGA_PREC_FP64) {
+        FGA_CUDA(cudaMemcpy(b->state.p, sd.data(), 8 * sd.size(), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> sf(sd.size());
+        for (size_t i = 0; i < sd.size(); i++) sf[i] = (float)sd[i];
+        FGA_CUDA(cudaMemcpy(b->state.p, sf.data(), 4 * sf.size(), cudaMemcpyHostToDevice));
+    }
+    FGA_CUDA(cudaMemcpy(b->flags.p, fl.data(), 4 * fl.size(), cudaMemcpyHostToDevice));
+    FGA_CUDA(cudaMemcpy(b->id.p, ids.data(), 4 * ids.size(), cudaMemcpyHostToDevice));
+    b->last_stream = s;
+    *out = hold.release();
     return FGA_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstdint>
@@ -116,6 +117,14 @@ struct ProfScope {  // wraps one kernel launch on stream s
     ~ProfScope();
     int idx;
     cudaStream_t s;
+};
+// NVTX range around a phase of a call (decomposition, a window's propagation or sums, a snapshot, the
+// adjoint's passes): visible in Nsight timelines, a single branch when no tool is attached
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 bool prof_counting();
 void prof_add_beam_steps(int64_t n);

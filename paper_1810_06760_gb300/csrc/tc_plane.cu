@@ -70,7 +70,8 @@ constexpr int PL_LBO = 144;                    // bytes between K-adjacent core 
 constexpr int PL_SBO_A = 592;                  // bytes between row-adjacent core matrices of A
 constexpr int PL_A_COPY = 8 * PL_SBO_A;        // one A copy: 64 rows (8 row groups)
 constexpr int PL_QUEUE = 64;                   // kept records queued per producer warp (31 + 32 used)
-constexpr int PL_T0_MAX = 24, PL_T1_MAX = 20;   // seven 26 KB stages fit with n_c <= 24
+constexpr int PL_T0_MAX = 24, PL_T1_MAX = 20;   // seven 28 KB stages fit with n_c <= 24
+constexpr int PL_PARK = 257;                   // floats per accumulator lane in the epilogue's copy
 
 struct PlaneArgs {
     const float *rec;        // records [n_rec][12]: Q, P, weighted polarised amplitude (3 complex)
@@ -209,7 +210,6 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
     const int T0 = T0T ? T0T : P.T0;
     const int NC = T0T ? (T0T + 7) / 8 * 8 : P.nc;
     const int SBOB = T0T ? plane_sbo_b((T0T + 7) / 8 * 8) : P.sbo_b;
-    const int NR = 2 * NC;
     const float hk = -0.5f * P.k;
     uint32_t done_par = 0;
     int uses = 0;                            // producer: fills of its stage so far (never reset)
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
             release(-1);
         } else if (lane == 0) {
             // ------------------------------------------------ MMA issuer ---------------------------
-            const uint32_t idesc = tc::instr_desc(2 * NR, 128);
+            const uint32_t idesc = tc::instr_desc(256, 128);
             bool started = false;
             unsigned active = (1u << PL_PROD) - 1u;
             for (int w = 0; active != 0u; w = (w + 1 == PL_PROD) ? 0 : w + 1) {
@@ -476,20 +476,17 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
                 if (nb > 0 && *abort_flag == 0) {
                     const unsigned char *st = smem + w * P.stage_bytes;
                     const uint32_t a_base = tc::smem_u32(st), b_base = tc::smem_u32(st + 4 * PL_A_COPY);
-                    // one MMA per K step and re/im half: A = [A_hi; A_lo] (128 rows: the hi copy is followed by
-                    // the lo copy with the same row stride), B = [B_hi; B_lo] (4 n_c rows, likewise), so each
-                    // accumulator holds hi*hi (rows 0..63, columns 0..2n_c), hi*lo (rows 0..63, columns
-                    // 2n_c..4n_c) and lo*hi (rows 64..127, columns 0..2n_c); the lo*lo quarter is not used
+                    // one M = 128 x N = 256 MMA per K step: accumulator lane m = row of [B'_hi; B'_lo] (lanes
+                    // 0..63: Re E0 at i, Im E0 at n_c + i, hi; lanes 64..127 the same, lo), column n = row of
+                    // the A copies (0..63 A_re hi, 64..127 A_re lo, 128..191 A_im hi, 192..255 A_im lo); the
+                    // products lo*lo and the padding rows are not used
                     for (int ks = 0; ks < PL_KB / 16; ks++) {
                         const uint32_t kof = ks * 2 * PL_LBO;
-                        const uint32_t acc = started ? 1u : 0u;
-                        const uint64_t db = tc::smem_desc_lbo_sbo(b_base + kof, PL_LBO, SBOB);
-                        for (int half = 0; half < 2; half++) {
-                            // half 0: A_re -> accumulator columns [0, 4 n_c); half 1: A_im -> [4 n_c, 8 n_c)
-                            const uint32_t a_hi = a_base + (2 * half) * PL_A_COPY;
-                            const uint64_t da = tc::smem_desc_lbo_sbo(a_hi + kof, PL_LBO, PL_SBO_A);
-                            tc::mma_f16(tmem + (uint32_t)(half * 2 * NR), da, db, idesc, acc);
-                        }
+                        // M side: the B copies [B'_hi; B'_lo] (64 rows each); N side: the four A copies
+                        // [A_re_hi; A_re_lo; A_im_hi; A_im_lo] (64 rows each, one row-group stride)
+                        const uint64_t dm = tc::smem_desc_lbo_sbo(b_base + kof, PL_LBO, SBOB);
+                        const uint64_t dn = tc::smem_desc_lbo_sbo(a_base + kof, PL_LBO, PL_SBO_A);
+                        tc::mma_f16(tmem, dm, dn, idesc, started ? 1u : 0u);
                         started = true;
                     }
                     tc::commit(tc::smem_u32(empty + w));
@@ -510,74 +507,51 @@ __global__ void __launch_bounds__(PL_THREADS, 1) plane_tc_kernel(PlaneArgs P) {
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
-        // ---- epilogue (TMEM lane = accumulator row): warps 2 and 3 park the lo*hi rows (lanes 64..127) of
-        // both accumulators in the idle stage memory, then warps 0 and 1 add hi*hi + hi*lo + lo*hi of rows
-        // 0..63, combine the re and im accumulators and write the item's partial sums ----
+        // ---- epilogue: warps 0..3 copy their 32 accumulator lanes (all 256 columns) into the idle stage
+        // memory, then every thread forms outputs U[(j,c)][i]:
+        //   X_a(c', r) = hi*hi + hi*lo + lo*hi of A_a row r against E0 part c' (a, c' in {re, im})
+        //   Re U = X_re(Re) - X_im(Im),  Im U = X_re(Im) + X_im(Re) ----
         const bool have = misc[2] != 0 && *abort_flag == 0;
-        float *park = reinterpret_cast<float *>(smem);   // [64][2][2 n_c]
-        if (warp == 2 || warp == 3) {
-            const int r = 32 * (warp - 2) + lane;
-            for (int a = 0; a < 2; a++)
-                for (int c0 = 0; c0 < NR; c0 += 8) {
-                    float v[8];
-                    if (have) {
-                        tc::ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * 2 * NR + c0), v);
-                    } else {
+        float *park = reinterpret_cast<float *>(smem);   // [128 lanes][PL_PARK] (padded rows: no bank conflicts)
+        if (warp < 4) {
+            const int ln = 32 * warp + lane;
+            for (int c0 = 0; c0 < 256; c0 += 8) {
+                float v[8];
+                if (have) {
+                    tc::ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+                } else {
 #pragma unroll
-                        for (int u = 0; u < 8; u++) v[u] = 0.f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; u++) park[(r * 2 + a) * NR + c0 + u] = v[u];
+                    for (int u = 0; u < 8; u++) v[u] = 0.f;
                 }
+#pragma unroll
+                for (int u = 0; u < 8; u++) park[ln * PL_PARK + c0 + u] = v[u];
+            }
         }
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
-        if (warp < 2) {
-            const int row = 32 * warp + lane;
-            const int tj = lane / 3, c = lane - 3 * tj, j = warp * J + tj;
-            const bool rowok = lane < 3 * J && j < e1;
+        {
             const float inv = 1.0f / (sa * sb);
             float *dst = P.partial + (int64_t)item * T0 * P.T1 * 6;
-            for (int c0 = 0; c0 < NC; c0 += 8) {
-                float re[8], im[8];
-                if (have) {
-                    // x_a(c) = hi*hi + hi*lo + lo*hi of accumulator a (0: A_re, 1: A_im) against Re E0 (c = 0)
-                    // or Im E0 (c = 1)
-                    float x[2][2][8];
-                    const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16);
+            const int nout = T0 * 2 * J * 3;   // (i, half, t, c)
+            for (int o = tid; o < nout; o += PL_THREADS) {
+                const int c = o % 3, t = (o / 3) % J, hh = (o / (3 * J)) % 2, i = o / (6 * J);
+                const int j = hh * J + t;
+                if (j >= e1) continue;
+                const int r = 32 * hh + 3 * t + c;   // A row
+                // x[a][p]: A_a (a: 0 re, 1 im) against Re E0 (p = 0) or Im E0 (p = 1)
+                float x[2][2];
 #pragma unroll
-                    for (int a = 0; a < 2; a++)
+                for (int a2 = 0; a2 < 2; a2++)
 #pragma unroll
-                        for (int c = 0; c < 2; c++) {
-                            float hl[8];
-                            const uint32_t col = (uint32_t)(a * 2 * NR + c * NC + c0);
-                            tc::ld8(base + col, x[a][c]);
-                            tc::ld8(base + col + (uint32_t)NR, hl);
-#pragma unroll
-                            for (int u = 0; u < 8; u++)
-                                x[a][c][u] += hl[u] + park[(row * 2 + a) * NR + c * NC + c0 + u];
-                        }
-#pragma unroll
-                    for (int u = 0; u < 8; u++) {
-                        re[u] = x[0][0][u] - x[1][1][u];
-                        im[u] = x[0][1][u] + x[1][0][u];
+                    for (int p2 = 0; p2 < 2; p2++) {
+                        const int lhi = p2 * NC + i, llo = 64 + lhi;
+                        const int chi = 128 * a2 + r, clo = chi + 64;
+                        x[a2][p2] = park[lhi * PL_PARK + chi] + park[lhi * PL_PARK + clo] + park[llo * PL_PARK + chi];
                     }
-                } else {
-#pragma unroll
-                    for (int u = 0; u < 8; u++) re[u] = im[u] = 0.f;
-                }
-                if (rowok) {
-#pragma unroll
-                    for (int u = 0; u < 8; u++) {
-                        const int i = c0 + u;
-                        if (i < T0) {
-                            const int pnt = i * P.T1 + j;
-                            dst[pnt * 6 + 2 * c] = re[u] * inv;
-                            dst[pnt * 6 + 2 * c + 1] = im[u] * inv;
-                        }
-                    }
-                }
+                const int pnt = i * P.T1 + j;
+                dst[pnt * 6 + 2 * c] = (x[0][0] - x[1][1]) * inv;
+                dst[pnt * 6 + 2 * c + 1] = (x[0][1] + x[1][0]) * inv;
             }
         }
         tc::fence_before();
@@ -612,7 +586,7 @@ fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec,
     // row-group stride of the B copies: the Re rows (i) and Im rows (nc + i) stored by the two lane
     // halves in one instruction land 16 banks apart
     const int sbo_b = plane_sbo_b(nc);
-    const int b_copy = (2 * nc / 8) * sbo_b;
+    const int b_copy = 8 * sbo_b;   // 64 rows: Re E0 (n_c), Im E0 (n_c), padding
     const int stage_bytes = (4 * PL_A_COPY + 2 * b_copy + 1023) / 1024 * 1024;
     const int bytes = PL_PROD * stage_bytes + PL_A_COPY + 256 + PL_PROD * PL_QUEUE * 48;
     if (bytes > 227 * 1024) {
@@ -650,8 +624,8 @@ fga_status run_plane_tc(Workspace &ws, const LatticePlan &plan, const void *rec,
         A.amax = amax_in ? amax_in : amax;
         A.partial = ws.partial.as<float>();
         A.err = ws.status.as<int>();
-        // the accumulators: 2 x 4 n_c columns (re and im, each hi*hi and hi*lo side by side)
-        A.tcols = 8 * nc <= 32 ? 32u : (8 * nc <= 64 ? 64u : (8 * nc <= 128 ? 128u : 256u));
+        // the accumulator: 128 lanes x 256 columns
+        A.tcols = 256u;
         int dev = 0, sms = 152;
         FGA_CUDA(cudaGetDevice(&dev));
         FGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

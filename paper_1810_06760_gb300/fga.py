@@ -25,7 +25,7 @@ MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
 EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_transform", "fga_propagate", "fga_reconstruct",
             "fga_reconstruct_spherical",
             "fga_reconstruct_lattice", "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export",
-            "fga_beams_export_all", "fga_beams_destroy", "fga_bin", "fga_profile_enable", "fga_profile_read",
+            "fga_beams_export_all", "fga_beams_destroy", "fga_beams_params", "fga_beams_import", "fga_bin", "fga_profile_enable", "fga_profile_read",
             "fga_solve_vjp", "fga_server_create", "fga_server_submit", "fga_server_wait", "fga_server_stats",
             "fga_server_destroy", "fga_server_cancel", "fga_traveltime_adjoint", "fga_set_device_memory_limit",
             "fga_device_memory_in_use", "fga_point_force_field", "fga_last_error", "fga_version"]
@@ -137,6 +137,8 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.fga_beams_export.argtypes = [vp, vp, vp]
     L.fga_beams_export_all.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
     L.fga_beams_destroy.argtypes = [vp]
+    L.fga_beams_params.argtypes = [vp, vp, vp, vp]
+    L.fga_beams_import.argtypes = [i64, vp, vp, C.c_double, C.c_double, i32, vp, vp]
     L.fga_bin.argtypes = [vp, i64, vp, C.c_float, vp, vp, vp, vp, vp]
     L.fga_traveltime_adjoint.argtypes = [vp, vp, i32, i64, i64, C.c_double, i32, vp, vp, vp, vp]
     L.fga_profile_enable.argtypes = [i32]
@@ -301,6 +303,25 @@ class Beams:
             self.close()
         except Exception:
             pass
+
+
+def beams_params(beams: Beams):
+    """(k, w, precision) of a beam set: its FGA parameter, quadrature weight and precision."""
+    k, w, prec = C.c_double(), C.c_double(), C.c_int()
+    _check(lib().fga_beams_params(beams.h, C.byref(k), C.byref(w), C.byref(prec)))
+    return k.value, w.value, prec.value
+
+
+def beams_import(state, meta, k: float, w: float, precision: int, stream=None) -> Beams:
+    """fga_beams_import: a beam set from exported states (HOST float64 [n, 48]) and meta (int32 [n], class and
+    S-frame bits), with the k, w and precision of the set they came from."""
+    state = np.ascontiguousarray(state, dtype=np.float64)
+    meta = np.ascontiguousarray(meta, dtype=np.int32)
+    assert state.ndim == 2 and state.shape[1] == 48 and meta.shape == (state.shape[0],)
+    h = C.c_void_p()
+    _check(lib().fga_beams_import(state.shape[0], state.ctypes.data, meta.ctypes.data, float(k), float(w),
+                                  int(precision), C.byref(h), _stream(stream)))
+    return Beams(h, int(precision), float(k))
 
 
 def decompose(model: Model, desc: InitDesc, stream=None) -> Beams:

@@ -279,3 +279,35 @@ def test_nonfinite_input_is_reported(fga, prec):
     desc2 = fga.init_desc(w.k, ok, None, w.y0, w.dy, w.mesh, w.classes, prec)
     seis, _ = fga.solve(model, desc2, w.dt, w.nsteps, w.times, rx, rw=w.rw)
     assert torch.isfinite(torch.view_as_real(seis)).all()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_export_import_resumes_propagation(fga, prec):
+    """fga_beams_export, then fga_beams_import with the set's k, w and precision (fga_beams_params), then
+    more steps: the same states and sums as one uninterrupted propagation (to the rounding of the Q
+    compensation folded into the exported centres)."""
+    import torch
+    w = _small_smooth(grid=True, nsteps=24)
+    model, desc, keep = gpu_setup(w, prec)
+    ref = fga.decompose(model, desc)
+    fga.propagate(model, ref, w.dt, 24)
+    b1 = fga.decompose(model, desc)
+    fga.propagate(model, b1, w.dt, 10)
+    st, meta = b1.export()
+    k, wt, p = fga.beams_params(b1)
+    assert p == prec and k == w.k and wt > 0
+    b1.close()
+    b2 = fga.beams_import(st, meta, k, wt, p)
+    fga.propagate(model, b2, w.dt, 14)
+    s_ref, m_ref = ref.export()
+    s_new, m_new = b2.export()
+    np.testing.assert_array_equal(m_new, m_ref)
+    tol = 1e-12 if prec == 1 else 2e-6
+    for sl in (slice(0, 6), slice(6, 42), slice(42, 46)):
+        assert rel_l2(s_new[:, sl], s_ref[:, sl]) <= tol, sl
+    x = torch.as_tensor(W.random_points(65, 0.0, 1.0, 9), device="cuda")
+    u_ref = fga.reconstruct(ref, x, rw=w.rw).cpu().numpy()
+    u_new = fga.reconstruct(b2, x, rw=w.rw).cpu().numpy()
+    assert rel_l2(u_new, u_ref) <= (1e-11 if prec == 1 else 1e-5)
+    with pytest.raises(fga.FGAError):
+        fga.beams_import(st, meta | 0x100, k, wt, p)
