@@ -574,12 +574,15 @@ def run_adjoint(args):
     model = fga.model_from_medium(ws[0].medium, dev)
     tmodel = fga.model_from_medium(true, dev)
     staged = []
+    cdt = torch.complex64 if prec == fga.PREC_FP32 else torch.complex128
     for w in ws:
         f = torch.as_tensor(w.f, device=dev)
         rx = torch.as_tensor(w.receivers, device=dev)
         desc = fga.init_desc(w.k, f, None, w.y0, w.dy, w.mesh, w.classes, prec)
-        d, _ = fga.solve(tmodel, desc, w.dt, w.nsteps, w.times, rx, rw=w.rw)   # observed data (input)
-        staged.append((w, desc, f, rx, d))
+        # observed data (input, not timed): the FP64 path on the true model
+        d64 = fga.init_desc(w.k, f, None, w.y0, w.dy, w.mesh, w.classes, fga.PREC_FP64)
+        d, _ = fga.solve(tmodel, d64, w.dt, w.nsteps, w.times, rx, rw=w.rw)
+        staged.append((w, desc, f, rx, d.to(cdt)))
     torch.cuda.synchronize()
     shape = tuple(ws[0].medium.grid_p.shape[:3]) + (10,)
     gp = torch.zeros(shape, dtype=torch.float64, device=dev)

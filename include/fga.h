@@ -54,13 +54,16 @@ enum {
                               evaluated exactly with its gradient and Hessian */
     FGA_MEDIUM_GRID = 2,   /* c_p, c_s and their first and second derivatives given on a node
                               grid, trilinearly interpolated (all 10 fields) */
-    FGA_MEDIUM_LAYERED = 3 /* piecewise-constant layers in depth x3 with flat interfaces (Sec. 3.1) */
+    FGA_MEDIUM_LAYERED = 3 /* piecewise-constant layers between parallel planar interfaces (Sec. 3.1) */
 };
 
 /* Velocity model (Eqs. ewe_ps, ps_speed).  Grid media: node (i,j,l) sits at
  * origin + (i*spacing[0], j*spacing[1], l*spacing[2]); positions outside the grid read the nearest
  * boundary value of every field.  Layered media: nlayers <= 8 layers, z_interfaces[nlayers-1]
- * increasing depths (HOST arrays). */
+ * increasing depths (HOST arrays) measured along layer_normal: the interfaces are the planes
+ * layer_normal . x = z_interfaces[i].  layer_normal = (0, 0, 0) means (0, 0, 1) (flat layers in x3);
+ * any other vector is normalised (tilted layers: the library propagates such a medium in the frame
+ * whose third axis is the normal and converts beams, points and results at its boundary). */
 typedef struct {
     int kind;
     double cp0, cs0;
@@ -69,6 +72,7 @@ typedef struct {
     double origin[3], spacing[3];
     int nlayers;
     const double *z_interfaces, *layer_cp, *layer_cs, *layer_rho;
+    double layer_normal[3];
 } fga_model_desc;
 
 typedef struct fga_model fga_model;

@@ -412,6 +412,34 @@ fga_status fga_model_create(fga_model **out, const fga_model_desc *d, const floa
             m->cmax[1] = std::max(m->cmax[1], d->layer_cs[l]);
             if (l + 1 < d->nlayers) m->dev.zif[l] = d->z_interfaces[l];
         }
+        // the layer frame: third axis the normal, first axis the normalised cross product of a coordinate
+        // axis (the one least parallel to the normal) with the normal, second axis completing the frame
+        const double *nv = d->layer_normal;
+        const double nn = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+        if (!std::isfinite(nn)) {
+            delete m;
+            set_error("fga_model_create: layer_normal is not finite");
+            return FGA_ERR_INVALID_ARG;
+        }
+        const double n3[3] = {nn > 0 ? nv[0] / nn : 0.0, nn > 0 ? nv[1] / nn : 0.0, nn > 0 ? nv[2] / nn : 1.0};
+        m->dev.tilted = (n3[0] != 0.0 || n3[1] != 0.0 || n3[2] != 1.0) ? 1 : 0;
+        const int ax = std::fabs(n3[0]) <= std::fabs(n3[1]) && std::fabs(n3[0]) <= std::fabs(n3[2]) ? 0
+                       : (std::fabs(n3[1]) <= std::fabs(n3[2]) ? 1 : 2);
+        double a[3] = {0, 0, 0}, e1[3], e2[3];
+        a[ax] = 1.0;
+        e1[0] = a[1] * n3[2] - a[2] * n3[1];
+        e1[1] = a[2] * n3[0] - a[0] * n3[2];
+        e1[2] = a[0] * n3[1] - a[1] * n3[0];
+        const double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+        for (int c = 0; c < 3; c++) e1[c] /= l1;
+        e2[0] = n3[1] * e1[2] - n3[2] * e1[1];
+        e2[1] = n3[2] * e1[0] - n3[0] * e1[2];
+        e2[2] = n3[0] * e1[1] - n3[1] * e1[0];
+        for (int c = 0; c < 3; c++) {
+            m->dev.R[c] = m->dev.tilted ? e1[c] : (c == 0 ? 1.0 : 0.0);
+            m->dev.R[3 + c] = m->dev.tilted ? e2[c] : (c == 1 ? 1.0 : 0.0);
+            m->dev.R[6 + c] = n3[c];
+        }
     }
     m->dev.fill_f32();
     cudaError_t e = cudaGetLastError();
@@ -480,9 +508,41 @@ static fga_status host_points(const double *x_dev, int64_t n, std::vector<double
 }
 
 // Gaussian sum of the current state at points (records gathered in cell order, state untouched)
+}  // extern "C"
+
+namespace fga {
+struct Mat3 {
+    double a[9];
+};
+
+// tilted layered media: the sums run in the layer frame; the field vectors come back as R^T u'
+template <typename R>
+__global__ void layer_frame_to_global_kernel(R *__restrict__ u, int64_t n, Mat3 Rm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    R v[6];
+    for (int f = 0; f < 6; f++) v[f] = u[6 * i + f];
+    for (int c = 0; c < 3; c++) {
+        R re = 0, im = 0;
+        for (int j = 0; j < 3; j++) {
+            re += (R)Rm.a[3 * j + c] * v[2 * j];
+            im += (R)Rm.a[3 * j + c] * v[2 * j + 1];
+        }
+        u[6 * i + 2 * c] = re;
+        u[6 * i + 2 * c + 1] = im;
+    }
+}
+}  // namespace fga
+
+extern "C" {
+
+static fga_status reconstruct_now_frame(const fga_beams *b, const double *x_dev, const std::vector<double> &xh,
+                                        int64_t n, double rw, void *u_out, cudaStream_t s);
+
 static fga_status reconstruct_now(const fga_beams *b, const double *x_dev, const std::vector<double> &xh, int64_t n,
                                   double rw, void *u_out, cudaStream_t s) {
     if (n == 0) return FGA_OK;
+    if (b->tilted) return reconstruct_now_frame(b, x_dev, xh, n, rw, u_out, s);
     Workspace &ws = b->ws;
     const BinGrid g = make_grid(xh.data(), n, rw);
     int32_t *perm = nullptr;
@@ -526,9 +586,52 @@ static std::vector<double> lattice_corners(const fga_lattice *L) {
     return c;
 }
 
+// points into the layer frame (x' = R x), the sum there, the field vectors back to global coordinates
+static fga_status reconstruct_now_frame(const fga_beams *b, const double *, const std::vector<double> &xh, int64_t n,
+                                        double rw, void *u_out, cudaStream_t s) {
+    std::vector<double> xr((size_t)(3 * n));
+    for (int64_t i = 0; i < n; i++)
+        for (int c = 0; c < 3; c++)
+            xr[(size_t)(3 * i + c)] = b->R[3 * c] * xh[(size_t)(3 * i)] + b->R[3 * c + 1] * xh[(size_t)(3 * i + 1)] +
+                                      b->R[3 * c + 2] * xh[(size_t)(3 * i + 2)];
+    ScopedDevBuf xd;
+    FGA_TRY(xd.ensure(sizeof(double) * xr.size()));
+    FGA_CUDA(cudaMemcpyAsync(xd.p, xr.data(), sizeof(double) * xr.size(), cudaMemcpyHostToDevice, s));
+    fga_beams *bf = const_cast<fga_beams *>(b);
+    bf->tilted = false;   // the sum itself is the flat one, in the layer frame
+    const fga_status st = reconstruct_now(b, xd.as<double>(), xr, n, rw, u_out, s);
+    bf->tilted = true;
+    FGA_TRY(st);
+    Mat3 Rm;
+    for (int i = 0; i < 9; i++) Rm.a[i] = b->R[i];
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (b->precision == FGA_PREC_FP64)
+        layer_frame_to_global_kernel<double><<<blocks, 256, 0, s>>>(static_cast<double *>(u_out), n, Rm);
+    else
+        layer_frame_to_global_kernel<float><<<blocks, 256, 0, s>>>(static_cast<float *>(u_out), n, Rm);
+    FGA_CUDA(cudaGetLastError());
+    // the rotated points are released when this scope ends
+    FGA_CUDA(cudaStreamSynchronize(s));
+    return FGA_OK;
+}
+
 // lattice sum of the current state (records gathered in cell order, state untouched)
 static fga_status reconstruct_lattice_now(const fga_beams *b, const fga_lattice *L, double rw, void *u_out,
                                           cudaStream_t s) {
+    if (b->tilted) {
+        // a lattice is not aligned with the layer frame: its points, x-major, as a point set
+        const int64_t n = (int64_t)L->n[0] * L->n[1] * L->n[2];
+        std::vector<double> xh((size_t)(3 * n));
+        int64_t q = 0;
+        for (int i = 0; i < L->n[0]; i++)
+            for (int j = 0; j < L->n[1]; j++)
+                for (int l = 0; l < L->n[2]; l++, q++) {
+                    xh[(size_t)(3 * q)] = L->axis[0][i];
+                    xh[(size_t)(3 * q + 1)] = L->axis[1][j];
+                    xh[(size_t)(3 * q + 2)] = L->axis[2][l];
+                }
+        return reconstruct_now_frame(b, nullptr, xh, n, rw, u_out, s);
+    }
     Workspace &ws = b->ws;
     const std::vector<double> corners = lattice_corners(L);
     const BinGrid g = make_grid(corners.data(), 8, rw);
@@ -868,6 +971,57 @@ static void export_row(const std::vector<double> &st, int64_t cap, int64_t i, do
     o[47] = 0.0;
 }
 
+// S polarisation frame of P (host): N_sh = e x P / |e x P| (e = e3, or e1 when ref_e1), N_sv = N_sh x P/|P|
+static void s_frame_host(const double *P, bool ref_e1, double *Nsv, double *Nsh) {
+    const double v[3] = {ref_e1 ? 0.0 : -P[1], ref_e1 ? -P[2] : P[0], ref_e1 ? P[1] : 0.0};
+    const double vn = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const double pn = std::sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+    for (int c = 0; c < 3; c++) Nsh[c] = v[c] / vn;
+    Nsv[0] = (Nsh[1] * P[2] - Nsh[2] * P[1]) / pn;
+    Nsv[1] = (Nsh[2] * P[0] - Nsh[0] * P[2]) / pn;
+    Nsv[2] = (Nsh[0] * P[1] - Nsh[1] * P[0]) / pn;
+}
+
+// an exported row of a tilted layered set, from the layer frame back to global coordinates: Q, P and the
+// rows of dzQ, dzP by R^T; an S beam's polarisation vector re-expressed in the S frame of the global P
+// (its frame bit in *mt chosen by the same rule as at decomposition)
+static void row_to_global(const double *Rm, double *o, int32_t *mt) {
+    auto rotT = [&](double *v) {
+        double w[3];
+        for (int c = 0; c < 3; c++) w[c] = Rm[c] * v[0] + Rm[3 + c] * v[1] + Rm[6 + c] * v[2];
+        for (int c = 0; c < 3; c++) v[c] = w[c];
+    };
+    double Pl[3] = {o[F_P], o[F_P + 1], o[F_P + 2]};
+    rotT(o + F_Q);
+    rotT(o + F_P);
+    for (int base : {F_DQ, F_DP})
+        for (int m = 0; m < 3; m++)
+            for (int part = 0; part < 2; part++) {
+                double v[3];
+                for (int j = 0; j < 3; j++) v[j] = o[base + 2 * (3 * m + j) + part];
+                rotT(v);
+                for (int j = 0; j < 3; j++) o[base + 2 * (3 * m + j) + part] = v[j];
+            }
+    if ((*mt & FL_CLASS_MASK) >= 2) {
+        double Nsv[3], Nsh[3], Ar[3], Ai[3];
+        s_frame_host(Pl, (*mt & FL_REF_E1) != 0, Nsv, Nsh);
+        for (int c = 0; c < 3; c++) {
+            Ar[c] = o[F_A0] * Nsv[c] + o[F_A1] * Nsh[c];
+            Ai[c] = o[F_A0 + 1] * Nsv[c] + o[F_A1 + 1] * Nsh[c];
+        }
+        rotT(Ar);
+        rotT(Ai);
+        const double *P = o + F_P;
+        const bool r1 = (P[0] * P[0] + P[1] * P[1]) < 0.01 * (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+        *mt = r1 ? (*mt | FL_REF_E1) : (*mt & ~FL_REF_E1);
+        s_frame_host(P, r1, Nsv, Nsh);
+        o[F_A0] = Ar[0] * Nsv[0] + Ar[1] * Nsv[1] + Ar[2] * Nsv[2];
+        o[F_A0 + 1] = Ai[0] * Nsv[0] + Ai[1] * Nsv[1] + Ai[2] * Nsv[2];
+        o[F_A1] = Ar[0] * Nsh[0] + Ar[1] * Nsh[1] + Ar[2] * Nsh[2];
+        o[F_A1 + 1] = Ai[0] * Nsh[0] + Ai[1] * Nsh[1] + Ai[2] * Nsh[2];
+    }
+}
+
 fga_status fga_beams_export_all(const fga_beams *b, int64_t cap, int64_t *n_out, int64_t *dropped, double *state,
                                 int32_t *meta, int64_t *mesh_id, int64_t *path) {
     FGA_CHECK(b && n_out && cap >= 0, "fga_beams_export_all: NULL argument or negative cap");
@@ -890,7 +1044,14 @@ fga_status fga_beams_export_all(const fga_beams *b, int64_t cap, int64_t *n_out,
             if (meta) meta[k] = fl[(size_t)i];
             if (mesh_id) mesh_id[k] = ids[(size_t)i];
             if (path) path[k] = pa[(size_t)i];
-            if (state) export_row(st, scap, i, state + k * 48);
+            if (state) {
+                export_row(st, scap, i, state + k * 48);
+                if (b->tilted) {
+                    int32_t mt = fl[(size_t)i];
+                    row_to_global(b->R, state + k * 48, &mt);
+                    if (meta) meta[k] = mt;
+                }
+            }
         }
         k++;
     }

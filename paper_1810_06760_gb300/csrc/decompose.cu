@@ -203,7 +203,13 @@ __device__ __forceinline__ void beam_init_state(const ModelDev &Md, const C2<R> 
     R q[3] = {(R)qd[0], (R)qd[1], (R)qd[2]};
     R p[3] = {(R)pd[0], (R)pd[1], (R)pd[2]};
     R cf[10];
-    model_eval<R, MED>(Md, wave, q, cf);
+    // layered media are evaluated at the depth along the layer normal (x3 unless the layers are tilted)
+    const double zl = (MED == FGA_MEDIUM_LAYERED && Md.tilted)
+                          ? Md.R[6] * qd[0] + Md.R[7] * qd[1] + Md.R[8] * qd[2] : qd[2];
+    {
+        const R qe[3] = {q[0], q[1], MED == FGA_MEDIUM_LAYERED ? (R)zl : q[2]};
+        model_eval<R, MED>(Md, wave, qe, cf);
+    }
     const R pn = Real<R>::sqrt_(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
     const R sgn = (cls & 1) ? R(-1) : R(1);
     const R gsc = sgn / ((R)k * cf[0] * pn);  // +- 1/(k c(q) |p|)
@@ -236,7 +242,7 @@ __device__ __forceinline__ void beam_init_state(const ModelDev &Md, const C2<R> 
     }
     if (MED == FGA_MEDIUM_LAYERED) {
         int l = 0;
-        for (int q = 0; q < Md.nlay - 1; q++) l += (qd[2] >= Md.zif[q]) ? 1 : 0;
+        for (int q = 0; q < Md.nlay - 1; q++) l += (zl >= Md.zif[q]) ? 1 : 0;
         fl |= (l << 4) | (cls << FL_ROOT_SHIFT);
     }
     for (int f = 0; f < NF; f++) y[f] = R(0);
@@ -287,6 +293,63 @@ __global__ void beam_init_kernel(ModelDev Md, const C2<R> *__restrict__ F, const
     for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y[f];
     flags[b] = fl;
     ids[b] = (int32_t)mi;
+}
+
+// tilted layered media: the beams of [0, nb) into the layer frame x' = R x (rows of R the frame's axes):
+// Q, P rotate, each row m of dzQ and dzP (the vector dQ/dz_m) rotates, S amplitudes are re-expressed in
+// the S frame of the rotated P (the polarisation vector a_sv N_sv + a_sh N_sh rotates with the beam)
+template <typename R>
+__global__ void rotate_to_layer_frame_kernel(ModelDev Md, R *__restrict__ st, int32_t *__restrict__ flags,
+                                             int64_t nb, int64_t cap) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    R y[NF];
+    for (int f = 0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
+    const R *Rm = nullptr;
+    R Rr[9];
+    for (int i = 0; i < 9; i++) Rr[i] = (R)Md.R[i];
+    Rm = Rr;
+    auto rot = [&](const R *v, R *o) {
+        for (int i = 0; i < 3; i++) o[i] = Rm[3 * i] * v[0] + Rm[3 * i + 1] * v[1] + Rm[3 * i + 2] * v[2];
+    };
+    int fl = flags[b];
+    const bool wave = (fl & FL_CLASS_MASK) >= 2;
+    R Pold[3] = {y[F_P], y[F_P + 1], y[F_P + 2]};
+    R v[3], o[3];
+    for (int base : {F_Q, F_P}) {
+        for (int i = 0; i < 3; i++) v[i] = y[base + i];
+        rot(v, o);
+        for (int i = 0; i < 3; i++) y[base + i] = o[i];
+    }
+    for (int base : {F_DQ, F_DP})
+        for (int m = 0; m < 3; m++)
+            for (int part = 0; part < 2; part++) {
+                for (int j = 0; j < 3; j++) v[j] = y[base + 2 * (3 * m + j) + part];
+                rot(v, o);
+                for (int j = 0; j < 3; j++) y[base + 2 * (3 * m + j) + part] = o[j];
+            }
+    if (wave) {
+        R Nsv[3], Nsh[3], Ar[3], Ai[3];
+        s_frame<R>(Pold, (fl & FL_REF_E1) != 0, Nsv, Nsh);
+        for (int i = 0; i < 3; i++) {
+            Ar[i] = y[F_A0] * Nsv[i] + y[F_A1] * Nsh[i];
+            Ai[i] = y[F_A0 + 1] * Nsv[i] + y[F_A1 + 1] * Nsh[i];
+        }
+        R Arr[3], Air[3];
+        rot(Ar, Arr);
+        rot(Ai, Air);
+        const R *P = y + F_P;
+        const R pn2 = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
+        const bool r1 = (P[0] * P[0] + P[1] * P[1]) < R(0.01) * pn2;
+        fl = r1 ? (fl | FL_REF_E1) : (fl & ~FL_REF_E1);
+        s_frame<R>(P, r1, Nsv, Nsh);
+        y[F_A0] = Arr[0] * Nsv[0] + Arr[1] * Nsv[1] + Arr[2] * Nsv[2];
+        y[F_A0 + 1] = Air[0] * Nsv[0] + Air[1] * Nsv[1] + Air[2] * Nsv[2];
+        y[F_A1] = Arr[0] * Nsh[0] + Arr[1] * Nsh[1] + Arr[2] * Nsh[2];
+        y[F_A1 + 1] = Air[0] * Nsh[0] + Air[1] * Nsh[1] + Air[2] * Nsh[2];
+        flags[b] = fl;
+    }
+    for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y[f];
 }
 
 // pass 1 of the selection: the largest |psi|^2 over the class (block maximum, one atomic per block)
@@ -483,6 +546,16 @@ static fga_status decompose_medium(const fga_model *m, const fga_init_desc *d, f
         beam_init_kernel<R, MED><<<(unsigned)((M + 127) / 128), 128, 0, s>>>(
             m->dev, F, G, d->nq, d->np, q0, dq, p0, dp, d->k, M, cls, b->off_cls[cls], b->cap, b->state.as<R>(),
             b->flags.as<int32_t>(), b->id.as<int32_t>(), select ? keep : nullptr);
+        FGA_CUDA(cudaGetLastError());
+    }
+    if (MED == FGA_MEDIUM_LAYERED && m->dev.tilted) {
+        b->tilted = true;
+        for (int i = 0; i < 9; i++) b->R[i] = m->dev.R[i];
+        if (b->nb > 0) {
+            ProfScope ps(P_DECOMP, s);
+            rotate_to_layer_frame_kernel<R><<<(unsigned)((b->nb + 127) / 128), 128, 0, s>>>(
+                m->dev, b->state.as<R>(), b->flags.as<int32_t>(), b->nb, b->cap);
+        }
         FGA_CUDA(cudaGetLastError());
     }
     // the selection scratch is released when this scope ends

@@ -52,6 +52,10 @@ struct ModelDev {
     const float4 *gp, *gs;  // grid: 3 float4 (10 fields + 2 pad) per node
     int nlay;
     double zif[MAX_LAYERS], lcp[MAX_LAYERS], lcs[MAX_LAYERS], lrho[MAX_LAYERS];
+    // tilted layers: rows of R are the layer frame's axes in global coordinates (row 2 = the normal);
+    // beams live in the layer frame, x' = R x
+    int tilted;
+    double R[9];
     // FP32 copies of the scalar parameters: the FP32 kernels read these and never convert from
     // double (FP64 instructions are very slow on this GPU)
     float fcp0, fcs0, famp, fcs_ratio, fo[3], finv_h[3], fzif[MAX_LAYERS], flcp[MAX_LAYERS], flcs[MAX_LAYERS];
@@ -182,6 +186,9 @@ struct fga_model {
 struct fga_beams {
     int precision;
     double k, w;
+    // tilted layered media: the state is in the layer frame x' = R x (R as in ModelDev)
+    bool tilted = false;
+    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     int64_t nb, cap;
     int64_t n_cls[4], off_cls[4];
     fga::DevBuf state, state_alt, flags, flags_alt, id, id_alt;

@@ -167,6 +167,7 @@ extern "C" fga_status fga_reconstruct_noalloc(const fga_beams *b, const double *
                                               fga_stream_t s_) {
     cudaStream_t s = (cudaStream_t)s_;
     FGA_CHECK(b, "fga_reconstruct_noalloc: NULL beams");
+    FGA_CHECK(!b->tilted, "fga_reconstruct_noalloc: beams of tilted layers are not supported");
     if (b->layered) {
         set_error("fga_reconstruct_noalloc: beams of a layered medium are not supported");
         return FGA_ERR_UNSUPPORTED;

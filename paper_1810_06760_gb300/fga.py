@@ -43,7 +43,8 @@ class ModelDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("cp0", C.c_double), ("cs0", C.c_double), ("amp", C.c_double),
                 ("cs_ratio", C.c_double), ("n", C.c_int * 3), ("origin", C.c_double * 3),
                 ("spacing", C.c_double * 3), ("nlayers", C.c_int), ("z_interfaces", C.c_void_p),
-                ("layer_cp", C.c_void_p), ("layer_cs", C.c_void_p), ("layer_rho", C.c_void_p)]
+                ("layer_cp", C.c_void_p), ("layer_cs", C.c_void_p), ("layer_rho", C.c_void_p),
+                ("layer_normal", C.c_double * 3)]
 
 
 class InitDesc(C.Structure):
@@ -190,7 +191,7 @@ class Model:
 
     def __init__(self, kind: str, *, cp0=2.0, cs0=1.0, amp=0.0, cs_ratio=1.0 / math.sqrt(3.0),
                  grid_p=None, grid_s=None, origin=(0, 0, 0), spacing=(1, 1, 1),
-                 z_interfaces=(), layer_cp=(), layer_cs=(), layer_rho=(), stream=None):
+                 z_interfaces=(), layer_cp=(), layer_cs=(), layer_rho=(), layer_normal=(0.0, 0.0, 0.0), stream=None):
         d = ModelDesc()
         d.kind = MEDIUM[kind]
         d.cp0, d.cs0, d.amp, d.cs_ratio = cp0, cs0, amp, cs_ratio
@@ -206,6 +207,7 @@ class Model:
             self._keep += arrs
             d.nlayers = arrs[1].size
             d.z_interfaces, d.layer_cp, d.layer_cs, d.layer_rho = [a.ctypes.data for a in arrs]
+            d.layer_normal[:] = [float(v) for v in layer_normal]
         h = C.c_void_p()
         _check(lib().fga_model_create(C.byref(h), C.byref(d), _dptr(gp), _dptr(gs), _stream(stream)))
         self.grid_shape = tuple(gp.shape[:3]) if gp is not None else None
@@ -229,7 +231,7 @@ def model_from_medium(med, device="cuda") -> Model:
     import torch
     if med.kind == "layered":
         return Model("layered", z_interfaces=med.z_interfaces, layer_cp=med.layer_cp, layer_cs=med.layer_cs,
-                     layer_rho=med.layer_rho)
+                     layer_rho=med.layer_rho, layer_normal=getattr(med, "layer_normal", (0.0, 0.0, 0.0)))
     if med.kind == "grid":
         gp = torch.as_tensor(med.grid_p, device=device)
         gs = torch.as_tensor(med.grid_s, device=device)

@@ -79,6 +79,7 @@ class Medium:
     layer_cp: Sequence[float] = ()
     layer_cs: Sequence[float] = ()
     layer_rho: Sequence[float] = ()
+    layer_normal: Sequence[float] = (0.0, 0.0, 0.0)   # layered: interfaces are normal . x = z_i ((0,0,0): x3)
 
 
 def sine_fields_on_nodes(n: int, c0: float, amp: float, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
