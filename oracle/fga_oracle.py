@@ -329,6 +329,62 @@ def layered_step(model: Model, st: np.ndarray, meta: np.ndarray, path: np.ndarra
     return out[:n].copy(), mo[:n].copy(), po[:n].copy()
 
 
+def layer_frame(normal) -> np.ndarray:
+    """Tilted layers (interfaces normal . x = z_i): an orthonormal frame whose third axis is the unit
+    normal, as the rows of a rotation R (x' = R x).  The in-plane axes come from Gram-Schmidt on the
+    coordinate axis least parallel to the normal; a layered medium is invariant under rotations about
+    its normal, so any in-plane choice gives the same physics."""
+    n = np.asarray(normal, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    e = np.zeros(3)
+    e[int(np.argmin(np.abs(n)))] = 1.0
+    e1 = e - (e @ n) * n
+    e1 /= np.linalg.norm(e1)
+    return np.stack([e1, np.cross(n, e1), n])
+
+
+def to_vector_form(st: np.ndarray, meta: np.ndarray):
+    """S beams given by (a_sv, a_sh) in their frame (N_sh = e x P/|e x P|, N_sv = N_sh x P/|P|, e = e1
+    for beams flagged META_REF_E1, else e3) rewritten with the displacement vector a_sv N_sv + a_sh N_sh
+    in the amplitude slot (META_VECTOR).  P beams and vector-form beams are unchanged."""
+    out = np.array(st, dtype=np.float64, copy=True)
+    mo = np.array(meta, dtype=np.int32, copy=True)
+    for b in np.nonzero(((mo & 3) >= 2) & ((mo & META_VECTOR) == 0))[0]:
+        P = out[b, 3:6]
+        e = np.array([1.0, 0.0, 0.0]) if mo[b] & META_REF_E1 else np.array([0.0, 0.0, 1.0])
+        nsh = np.cross(e, P)
+        nsh /= np.linalg.norm(nsh)
+        nsv = np.cross(nsh, P / np.linalg.norm(P))
+        a = out[b, 42:48].copy().view(complex)
+        out[b, 42:48] = (a[0] * nsv + a[1] * nsh).view(np.float64)
+        mo[b] |= META_VECTOR
+    return out, mo
+
+
+def rotate_beams(st: np.ndarray, meta: np.ndarray, Rm: np.ndarray, z_interfaces=None):
+    """Beams into the frame x' = Rm x: Q, P, each row m of dzQ and dzP (the vector dQ/dz_m, dP/dz_m) and,
+    for S beams, the amplitude vector rotate (vector form, meta bit META_VECTOR: the amplitude slot holds
+    the displacement vector; a P beam's scalar amplitude along P/|P| is unchanged).
+    With z_interfaces the layer bits (4-7) are set from the rotated depth Q'_3 (a beam on an interface
+    belongs to the deeper side, as in the flat medium).  S beams in frame form are first rewritten in
+    vector form (to_vector_form).  Returns new (st, meta)."""
+    st, meta = to_vector_form(st, meta)
+    swave = (meta & 3) >= 2
+    out = np.array(st, dtype=np.float64, copy=True)
+    out[:, 0:3] = st[:, 0:3] @ Rm.T
+    out[:, 3:6] = st[:, 3:6] @ Rm.T
+    for sl in (slice(6, 24), slice(24, 42)):
+        M = st[:, sl].copy().view(complex).reshape(-1, 3, 3)        # [beam][m][j]
+        out[:, sl] = (M @ Rm.T).reshape(-1, 9).view(np.float64)
+    a = st[:, 42:48].copy().view(complex)
+    out[swave, 42:48] = (a[swave] @ Rm.T).view(np.float64)
+    mo = np.array(meta, dtype=np.int32, copy=True)
+    if z_interfaces is not None:
+        lay = np.searchsorted(np.asarray(z_interfaces, dtype=np.float64), out[:, 2], side="right")
+        mo = (mo & ~np.int32(0xF0)) | (lay.astype(np.int32) << 4)
+    return out, mo
+
+
 def spherical_to_cartesian(rtp: np.ndarray) -> np.ndarray:
     """Points (r, theta, phi) -> x = (r cos theta cos phi, r sin theta cos phi, r sin phi): the change of
     the reconstruction point x of Eq. FGA that Sec. 3 uses for its spherical (layered-Earth) geometry,

@@ -258,3 +258,95 @@ def test_sh_incidence_textbook_coefficients(oracle):
     got = {int(O.meta_layer(m)): _displacement(O, k, int(m)) for k, m in zip(kids, km)}
     np.testing.assert_allclose(got[0], U_in * (Z1 - Z2) / (Z1 + Z2), rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(got[1], U_in * 2 * Z1 / (Z1 + Z2), rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------------------------
+# tilted layers: the flat event in the frame whose third axis is the interface normal
+# ---------------------------------------------------------------------------------------------
+
+_NORMAL = np.array([0.3, -0.4, 0.85])
+
+
+def _vector_beam(O, model, cls, q, p, k=16.0):
+    """One beam in vector form (amplitude slot = displacement vector): P along P/|P|, S a vector
+    normal to P with both in-plane components."""
+    mesh = O.Mesh(1, q, [0.1] * 3, 1, p, [0.1] * 3)
+    st, meta = O.beam_init(model, k, mesh, np.array([[1.0, 0.0, 0.0]], complex), None, cls, vector_form=True)
+    P = np.asarray(p, dtype=np.float64)
+    ph = P / np.linalg.norm(P)
+    if cls < 2:
+        a = np.array([1.0 + 0.5j, 0.0, 0.0])   # P: the scalar amplitude along P/|P|
+    else:
+        t1 = np.cross(ph, [0.2, 0.9, -0.3])
+        t1 /= np.linalg.norm(t1)
+        a = (1.0 + 0.5j) * t1 + (-0.3 + 0.2j) * np.cross(ph, t1)
+    st[0, 42:48] = a.view(np.float64)
+    return st, meta
+
+
+def _traction_n(lam, mu, P, U, n):
+    """sigma . n of the plane wave U exp(i k P.x), per unit i k."""
+    return lam * np.dot(P, U) * n + mu * (P * np.dot(U, n) + np.dot(P, n) * U)
+
+
+@pytest.mark.parametrize("cls,p,down", [(0, [0.3, 0.2, 0.9], True), (2, [0.3, 0.2, 0.9], True),
+                                        (3, [0.1, -0.3, 0.9], False), (1, [0.2, -0.3, -0.9], True)])
+def test_tilted_interface_children_satisfy_welded_continuity(oracle, cls, p, down):
+    """A beam given in global coordinates meets the plane n.x = 0.5 (n tilted): rotated into the layer
+    frame (rotate_beams with layer_frame(n)), split by the flat event, and its children rotated back,
+    the displacement and the traction sigma.n are continuous across the tilted plane in global
+    coordinates.  A transposed rotation or a vector left unrotated breaks this."""
+    O = oracle
+    cp, cs, rho = [2.0, 2.6], [1.1, 1.5], [1.3, 1.9]
+    model = _layered(O, cp, cs, rho, [0.5])
+    Rm = O.layer_frame(_NORMAL)
+    n = Rm[2]
+    lay = 0 if down else 1
+    st_l, mt_l = _vector_beam(O, model, cls, [0.3, 0.4, 0.45 if down else 0.55], p)
+    st_g, mt_g = O.rotate_beams(st_l, mt_l, Rm.T)                 # the beam as given in global coordinates
+    st_r, mt_r = O.rotate_beams(st_g, mt_g, Rm, z_interfaces=[0.5])
+    assert int(O.meta_layer(mt_r[0])) == lay
+    np.testing.assert_allclose(st_r, st_l, rtol=0, atol=1e-14)
+    kids, km = O.interface_event(model, int(mt_r[0]), st_r[0], 1 - lay, rel_min=0.0)
+    assert len(kids) >= 2
+    kids_g, km_g = O.rotate_beams(np.asarray(kids), np.asarray(km), Rm.T)
+    lam = [r * (a * a - 2 * b * b) for r, a, b in zip(rho, cp, cs)]
+    mu = [r * b * b for r, b in zip(rho, cs)]
+    def disp(row, m):
+        a = row[42:48].copy().view(complex)
+        if (m & 3) < 2:
+            return a[0] * row[3:6] / np.linalg.norm(row[3:6])
+        return a
+
+    U_in = disp(st_g[0], int(mt_g[0]))
+    du = U_in.copy()
+    dtr = _traction_n(lam[lay], mu[lay], st_g[0, 3:6], U_in, n)
+    T_in = dtr.copy()
+    for kg, m in zip(kids_g, km_g):
+        L = int(O.meta_layer(m))
+        sgn = 1.0 if L == lay else -1.0
+        U = disp(kg, int(m))
+        du += sgn * U
+        dtr += sgn * _traction_n(lam[L], mu[L], kg[3:6], U, n)
+    assert np.linalg.norm(du) <= 1e-12 * np.linalg.norm(U_in), du
+    assert np.linalg.norm(dtr) <= 1e-12 * np.linalg.norm(T_in), dtr
+
+
+def test_rotated_propagation_equals_global_propagation(oracle):
+    """Inside one homogeneous layer, propagating beams in the layer frame and rotating them back equals
+    propagating them in global coordinates (Q, P, dzQ, dzP and the amplitude vectors), which fixes the
+    rotation of the Jacobian rows as well as of the vectors."""
+    O = oracle
+    Rm = O.layer_frame(_NORMAL)
+    glob = O.Model("const", cp0=2.0, cs0=1.1)
+    lay1 = O.Model("layered", z_interfaces=[], layer_cp=[2.0], layer_cs=[1.1], layer_rho=[1.3])
+    for cls, p in ((0, [0.3, 0.2, 0.9]), (3, [0.1, -0.3, 0.9]), (2, [-0.5, 0.4, 0.2])):
+        st_g, mt_g = _vector_beam(O, glob, cls, [0.3, 0.4, 0.45], p)
+        ref = st_g.copy()
+        O.propagate(glob, ref, mt_g, 0.01, 40)
+        st_r, mt_r = O.rotate_beams(st_g, mt_g, Rm, z_interfaces=[])
+        path = np.zeros(1, dtype=np.int64)
+        for _ in range(40):
+            st_r, mt_r, path = O.layered_step(lay1, st_r, mt_r, path, 0.01)
+        back, _ = O.rotate_beams(st_r, mt_r, Rm.T)
+        np.testing.assert_allclose(back, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
