@@ -34,8 +34,9 @@ MUFU_PER_PAIR_IN = 3.0        # exp2, sin, cos
 FLOP_PER_LATTICE_PAIR_IN = 26.0   # window test (add, compare) + 3 complex multiply-adds
 # DRAM bytes (dram__bytes_read + write) per launch of each category's kernel on the full smooth workload,
 # from ncu captures summarised under profiles/; a category is absent until its current kernel is captured.
-# gauss_sum: plane_tc_kernel<0, 10, 20>, 1.02 GB read + 4-6 MB written per launch (two launches of the timed solve)
-TRAFFIC_BYTES_PER_LAUNCH = {"gauss_sum": 1.025e9}
+# gauss_sum: plane_tc_kernel<0, 10, 20>, 1.02 GB read + 4-6 MB written per launch (two launches of the timed solve);
+# propagate: rk4_kernel, 1.5-1.8 GB read + 13.1-13.6 GB written per launch (the window's records; eight launches)
+TRAFFIC_BYTES_PER_LAUNCH = {"gauss_sum": 1.025e9, "propagate": 1.49e10}
 
 
 def parse():
