@@ -55,6 +55,8 @@ typedef struct {
     const float *gp, *gs;   /* grid medium: 10 fields per node, node-major, axis 0 slowest */
     int nlay;               /* layered medium: nlay layers, nlay-1 interfaces zif (depth = x3, increasing) */
     const double *zif, *lcp, *lcs, *lrho;
+    int shells;             /* layered medium with spherical interfaces |x - ctr| = zif[i] (radii, decreasing) */
+    double ctr[3];
 } orc_model;
 
 /* The 10 model fields at a point: c, dc/dx1..3, d2c/dx1dx1, dx1dx2, dx1dx3, dx2dx2, dx2dx3, dx3dx3. */
@@ -101,10 +103,18 @@ static void grid_fields(const orc_model *m, const float *g, const double x[3], d
             }
 }
 
-static int layer_of(const orc_model *m, double z)
+/* Layer of a point: flat layers by depth x3 (a point on an interface belongs to the deeper layer);
+ * spherical layers by the number of spheres that enclose the point (a point on a sphere is inside it). */
+static int layer_of(const orc_model *m, const double x[3])
 {
     int l = 0;
-    while (l < m->nlay - 1 && z >= m->zif[l]) l++;
+    if (m->shells) {
+        const double r = sqrt((x[0] - m->ctr[0]) * (x[0] - m->ctr[0]) + (x[1] - m->ctr[1]) * (x[1] - m->ctr[1]) +
+                              (x[2] - m->ctr[2]) * (x[2] - m->ctr[2]));
+        while (l < m->nlay - 1 && r <= m->zif[l]) l++;
+        return l;
+    }
+    while (l < m->nlay - 1 && x[2] >= m->zif[l]) l++;
     return l;
 }
 
@@ -125,7 +135,7 @@ void orc_model_eval(const orc_model *m, int wave, const double x[3], double out[
         grid_fields(m, wave ? m->gs : m->gp, x, out);
         break;
     case ORC_LAYERED: {
-        int l = layer_of(m, x[2]);
+        int l = layer_of(m, x);
         for (int f = 0; f < 10; f++) out[f] = 0.0;
         out[0] = wave ? m->lcs[l] : m->lcp[l];
         break;
@@ -338,7 +348,7 @@ void orc_beam_init(const orc_model *m, double k, int nq, const double q0[3], con
         double pn = norm3(y->P);
         const cplx *Fm = F + mi * 3;
         /* layered media: layer (bits 4-7) and the class of the root beam of the lineage (bits 13-14) */
-        int lay_bits = m->kind == ORC_LAYERED ? ((layer_of(m, y->Q[2]) << 4) | (cls << 13)) : 0;
+        int lay_bits = m->kind == ORC_LAYERED ? ((layer_of(m, y->Q) << 4) | (cls << 13)) : 0;
         const cplx *Gm = G ? G + mi * 3 : NULL;
         double dirs[2][3];
         int ndir;
@@ -884,6 +894,7 @@ int orc_layered_step(const orc_model *m, int nb, const double *st_, const int *m
     const orc_state *st = (const orc_state *)st_;
     orc_state *out = (orc_state *)out_;
     int n = 0;
+    if (m->shells) return -1;   /* flat layers only; spherical ones step in fga_oracle.shell_step */
     for (int b = 0; b < nb; b++) {
         const int mt = meta[b], L = META_LAYER(mt);
         orc_state y = st[b], f0, y1;
@@ -925,6 +936,18 @@ int orc_layered_step(const orc_model *m, int nb, const double *st_, const int *m
         }
     }
     return n;
+}
+
+/* One classical RK4 step of size dt for each of n beams (layered media: each in its own layer). */
+void orc_rk4_many(const orc_model *m, int n, const double *st_, const int *meta, double dt, double *out_)
+{
+    const orc_state *st = (const orc_state *)st_;
+    orc_state *out = (orc_state *)out_;
+    for (int b = 0; b < n; b++) {
+        orc_state f0;
+        orc_rhs(m, meta[b], &st[b], &f0);
+        rk4_step(m, meta[b], &st[b], &f0, dt, &out[b]);
+    }
 }
 
 /* ------------------------------------------------------------------------- */

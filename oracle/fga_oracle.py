@@ -94,6 +94,7 @@ class _Model(C.Structure):
         ("gp", C.c_void_p), ("gs", C.c_void_p),
         ("nlay", C.c_int),
         ("zif", C.c_void_p), ("lcp", C.c_void_p), ("lcs", C.c_void_p), ("lrho", C.c_void_p),
+        ("shells", C.c_int), ("ctr", C.c_double * 3),
     ]
 
 
@@ -119,6 +120,7 @@ def _declare(L):
     L.orc_interface_event.restype = C.c_int
     L.orc_layered_step.argtypes = [_P, C.c_int, _P, _P, _P, C.c_double, C.c_int, C.c_double, C.c_int, _P, _P, _P, _P]
     L.orc_layered_step.restype = C.c_int
+    L.orc_rk4_many.argtypes = [_P, C.c_int, _P, _P, C.c_double, _P]
     L.orc_rhs_vjp.argtypes = [_P, C.c_int, _P, _P, _P, _P, _P]
     L.orc_solve_vjp.argtypes = [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.c_int, _P, _P, C.c_double,
                                 C.c_double, C.c_double, C.c_int, _P, _P, _P, _P, _P]
@@ -135,11 +137,14 @@ def _d3(v):
 
 
 class Model:
-    """Velocity model for the oracle.  kinds: 'const', 'sine', 'grid', 'layered'."""
+    """Velocity model for the oracle.  kinds: 'const', 'sine', 'grid', 'layered'.  Layered media have
+    flat interfaces at the depths z_interfaces (x3, increasing) or, with layer_shape='spheres', spherical
+    ones |x - layer_center| = z_interfaces[i] (radii, decreasing; layer 0 outside the largest)."""
 
     def __init__(self, kind: str, *, cp0=2.0, cs0=1.0, amp=0.0, cs_ratio=1.0 / math.sqrt(3.0),
                  grid_p=None, grid_s=None, origin=(0, 0, 0), spacing=(1, 1, 1),
-                 z_interfaces=(), layer_cp=(), layer_cs=(), layer_rho=()):
+                 z_interfaces=(), layer_cp=(), layer_cs=(), layer_rho=(), layer_shape="planes",
+                 layer_center=(0.0, 0.0, 0.0)):
         s = _Model()
         self._keep = []
         s.kind = {"const": 0, "sine": 1, "grid": 2, "layered": 3}[kind]
@@ -162,6 +167,11 @@ class Model:
             self._keep += [zi, lc, ls, lr]
             s.nlay = lc.size
             s.zif, s.lcp, s.lcs, s.lrho = zi.ctypes.data, lc.ctypes.data, ls.ctypes.data, lr.ctypes.data
+            assert layer_shape in ("planes", "spheres")
+            s.shells = int(layer_shape == "spheres")
+            s.ctr[:] = [float(v) for v in layer_center]
+            self.radii = zi.copy() if s.shells else None
+            self.center = np.array(s.ctr[:], dtype=np.float64)
         self.s = s
         self.kind = kind
 
@@ -383,6 +393,118 @@ def rotate_beams(st: np.ndarray, meta: np.ndarray, Rm: np.ndarray, z_interfaces=
         lay = np.searchsorted(np.asarray(z_interfaces, dtype=np.float64), out[:, 2], side="right")
         mo = (mo & ~np.int32(0xF0)) | (lay.astype(np.int32) << 4)
     return out, mo
+
+
+def rk4_many(model: Model, st: np.ndarray, meta: np.ndarray, dt: float) -> np.ndarray:
+    """One classical RK4 step of size dt for each beam (in a layered medium, each in its own layer)."""
+    st = np.ascontiguousarray(st, dtype=np.float64).reshape(-1, STATE_DOUBLES)
+    meta = np.ascontiguousarray(meta, dtype=np.int32).reshape(-1)
+    out = np.zeros_like(st)
+    if st.shape[0]:
+        lib().orc_rk4_many(model.ptr, st.shape[0], _ptr(st), _ptr(meta), float(dt), _ptr(out))
+    return out
+
+
+def shell_layer(model: Model, x: np.ndarray) -> np.ndarray:
+    """Layer of points in spherical layers: the number of spheres |x - centre| = radius that enclose the
+    point (layer 0 outside the largest; a point on a sphere counts as inside it)."""
+    r = np.linalg.norm(np.asarray(x, dtype=np.float64).reshape(-1, 3) - model.center, axis=1)
+    return np.sum(r[:, None] <= model.radii[None, :], axis=1)
+
+
+def shell_crossing(model: Model, q0: np.ndarray, q1: np.ndarray, layer: np.ndarray):
+    """Spherical layers: where the straight path of one step q0 -> q1 (in a homogeneous layer a beam moves
+    on a line) first meets a sphere that bounds its layer.  The points q0 + th (q1 - q0) at distance rho
+    from the centre solve a th^2 + b th + c = 0.  Entering the inner sphere is the smaller root, taken when
+    it lies below 1 with the path heading inward; leaving the enclosing sphere (a ball is convex, so only
+    an end point outside it can mean that) is the larger root.  Returns arrays th (NaN: no crossing), the
+    layer entered and the radius crossed, per beam."""
+    q0 = np.asarray(q0, dtype=np.float64).reshape(-1, 3)
+    q1 = np.asarray(q1, dtype=np.float64).reshape(-1, 3)
+    L = np.asarray(layer).reshape(-1)
+    n = q0.shape[0]
+    s0, d = q0 - model.center, q1 - q0
+    a = np.sum(d * d, axis=1)
+    b = 2.0 * np.sum(s0 * d, axis=1)
+    th = np.full(n, np.nan)
+    lb = L.copy()
+    rho = np.zeros(n)
+    R = model.radii
+    nl = R.size + 1
+    for i in range(n):
+        cand = []
+        if L[i] < nl - 1:                                       # the inner sphere
+            r = R[L[i]]
+            c = s0[i] @ s0[i] - r * r
+            disc = b[i] * b[i] - 4.0 * a[i] * c
+            if b[i] < 0.0 and disc >= 0.0:
+                t = (-b[i] - math.sqrt(disc)) / (2.0 * a[i])
+                if t < 1.0:
+                    cand.append((t, L[i] + 1, r))
+        if L[i] > 0:                                            # the enclosing sphere
+            r = R[L[i] - 1]
+            e = q1[i] - model.center
+            if e @ e > r * r:
+                c = s0[i] @ s0[i] - r * r
+                disc = max(b[i] * b[i] - 4.0 * a[i] * c, 0.0)
+                cand.append(((-b[i] + math.sqrt(disc)) / (2.0 * a[i]), L[i] - 1, r))
+        if cand:
+            th[i], lb[i], rho[i] = min(cand, key=lambda v: v[0])
+    return th, lb, rho
+
+
+def shell_event(model: Model, mt: int, state: np.ndarray, lb: int, rel_min: float = 1e-6):
+    """Children of a beam sitting on a sphere of a spherically layered medium.  Sec. 3.1 handles an
+    interface of general shape in the local tangent-normal coordinates of the point hit, with the tangent
+    plane as the flat interface: the beam is rotated into a frame whose third axis is the sphere's outward
+    normal there (layer_frame), split by the flat event (interface_event), and its children are rotated
+    back.  S beams go through in vector form.  Returns (states, metas) in global coordinates."""
+    st = np.asarray(state, dtype=np.float64).reshape(1, STATE_DOUBLES)
+    nrm = st[0, 0:3] - model.center
+    Rm = layer_frame(nrm)
+    st_l, mt_l = rotate_beams(st, np.array([mt], dtype=np.int32), Rm)
+    kids, km = interface_event(model, int(mt_l[0]), st_l[0], lb, rel_min)
+    if kids.shape[0] == 0:
+        return kids, km
+    return rotate_beams(kids, km, Rm.T)
+
+
+def shell_step(model: Model, st: np.ndarray, meta: np.ndarray, path: np.ndarray, dt: float, gmax: int = 4,
+               rel_min: float = 1e-6, return_parent: bool = False):
+    """One RK4 step of a medium of spherical layers with interface events, the spherical counterpart of
+    layered_step: a beam whose step meets a sphere (shell_crossing) is advanced to the crossing, put on the
+    sphere, replaced by the children of shell_event, and each child is advanced through the rest of the
+    step.  Beams that have crossed gmax interfaces are dropped at their next one.  Returns (st, meta, path)
+    and, with return_parent, the input index of each output beam."""
+    st = np.ascontiguousarray(st, dtype=np.float64)
+    meta = np.ascontiguousarray(meta, dtype=np.int32)
+    path = np.ascontiguousarray(path, dtype=np.int64)
+    y1 = rk4_many(model, st, meta, dt)
+    th, lb, rho = shell_crossing(model, st[:, 0:3], y1[:, 0:3], meta_layer(meta))
+    out, mo, po, par = [], [], [], []
+    for b in range(st.shape[0]):
+        if np.isnan(th[b]):
+            out.append(y1[b])
+            mo.append(meta[b])
+            po.append(path[b])
+            par.append(b)
+            continue
+        if meta_gen(meta[b]) >= gmax:
+            continue
+        yc = rk4_many(model, st[b:b + 1], meta[b:b + 1], th[b] * dt)[0]
+        s = yc[0:3] - model.center
+        yc[0:3] = model.center + rho[b] * s / np.linalg.norm(s)
+        kids, km = shell_event(model, int(meta[b]), yc, int(lb[b]), rel_min)
+        ye = rk4_many(model, kids, km, (1.0 - th[b]) * dt)
+        L = int(meta_layer(meta[b]))
+        for k in range(ye.shape[0]):
+            slot = (1 if km[k] & 2 else 0) + (0 if int(meta_layer(km[k])) == L else 2)   # rP, rS, tP, tS
+            out.append(ye[k])
+            mo.append(km[k])
+            po.append(path[b] * 4 + slot + 1)
+            par.append(b)
+    res = (np.array(out).reshape(-1, STATE_DOUBLES), np.array(mo, dtype=np.int32), np.array(po, dtype=np.int64))
+    return res + (np.array(par, dtype=np.int32),) if return_parent else res
 
 
 def spherical_to_cartesian(rtp: np.ndarray) -> np.ndarray:

@@ -80,6 +80,8 @@ class Medium:
     layer_cs: Sequence[float] = ()
     layer_rho: Sequence[float] = ()
     layer_normal: Sequence[float] = (0.0, 0.0, 0.0)   # layered: interfaces are normal . x = z_i ((0,0,0): x3)
+    layer_shape: str = "planes"                       # layered: 'planes' or 'spheres' (|x - layer_center| = z_i)
+    layer_center: Sequence[float] = (0.0, 0.0, 0.0)
 
 
 def sine_fields_on_nodes(n: int, c0: float, amp: float, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
@@ -260,6 +262,25 @@ def layered(nq: int = 4, np_: int = 6, ny: int = 32, nsteps: int = 60, dt: float
     rx = np.stack([R1.ravel(), R2.ravel(), np.zeros(R1.size)], -1)
     return Workload("layered", k, med, ny, y0, dy, f, None, mesh, tuple(classes), dt, nsteps, times, rx,
                     window_radius(k), None, (r, r, np.zeros(1)), None)
+
+
+def shells(nq: int = 4, np_: int = 6, ny: int = 32, nsteps: int = 60, dt: float = 0.05, n_times: int = 12,
+           rx_side: int = 8, extent: float = 30.0, rc: float = 60.0, classes=(0, 1, 2, 3)) -> Workload:
+    """The 3-layer crust of ``layered`` bent into concentric spheres about (0, 0, rc): the interfaces are the
+    spheres of radii rc - 15 and rc - 35 km (15 and 35 km below the point (0, 0, 0) of the outer sphere
+    r = rc), layer 0 outside the larger one.  With rc = 60 km the interfaces curve strongly over the beams'
+    paths.  The same explosive source at (0, 0, 10) (2 Hz, v0 = 0) and meshes as ``layered``; receivers on
+    an rx_side^2 patch of the sphere r = rc around (0, 0, 0) spanning +-extent/2 km in x1 and x2."""
+    w = layered(nq=nq, np_=np_, ny=ny, nsteps=nsteps, dt=dt, n_times=n_times, rx_side=rx_side, classes=classes)
+    med = Medium("layered", z_interfaces=(rc - 15.0, rc - 35.0), layer_cp=w.medium.layer_cp,
+                 layer_cs=w.medium.layer_cs, layer_rho=w.medium.layer_rho, layer_shape="spheres",
+                 layer_center=(0.0, 0.0, rc))
+    r = np.linspace(-extent / 2, extent / 2, rx_side)
+    R1, R2 = np.meshgrid(r, r, indexing="ij")
+    x3 = rc - np.sqrt(rc * rc - R1 ** 2 - R2 ** 2)
+    rx = np.stack([R1.ravel(), R2.ravel(), x3.ravel()], -1)
+    return Workload("shells", w.k, med, w.ny, w.y0, w.dy, w.f, None, w.mesh, w.classes, w.dt, w.nsteps, w.times, rx,
+                    w.rw, None, None, None)
 
 
 def _bump_fields(fields: np.ndarray, n: int, centre, sigma: float, eps: float, lo: float = 0.0,

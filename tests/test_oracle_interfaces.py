@@ -350,3 +350,181 @@ def test_rotated_propagation_equals_global_propagation(oracle):
             st_r, mt_r, path = O.layered_step(lay1, st_r, mt_r, path, 0.01)
         back, _ = O.rotate_beams(st_r, mt_r, Rm.T)
         np.testing.assert_allclose(back, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+# ---------------------------------------------------------------------------------------------
+# spherical layers: the flat event in the tangent-normal frame of the point where a beam meets a sphere
+# ---------------------------------------------------------------------------------------------
+
+def _spheres(O, centre, radii, cp=(2.0, 2.6, 3.1), cs=(1.1, 1.5, 1.8), rho=(1.3, 1.9, 2.4)):
+    n = len(radii) + 1
+    return O.Model("layered", z_interfaces=radii, layer_cp=cp[:n], layer_cs=cs[:n], layer_rho=rho[:n],
+                   layer_shape="spheres", layer_center=centre)
+
+
+def test_initial_layers_by_enclosing_spheres(oracle):
+    """Beams start in the layer given by the spheres that enclose their centre; a centre on a sphere
+    belongs to its inner side (as a centre on a plane belongs to the deeper layer)."""
+    O = oracle
+    c = np.array([0.2, -0.1, 3.0])
+    model = _spheres(O, c, [2.0, 1.0])
+    u = np.array([0.6, 0.0, -0.8])
+    for r, want in ((2.5, 0), (2.0, 1), (1.5, 1), (1.0, 2), (0.3, 2)):
+        st, mt = _beam(O, model, 0, c + r * u, [0.3, 0.2, 0.9])
+        assert int(O.meta_layer(mt)) == want, (r, mt)
+        assert int(O.shell_layer(model, (c + r * u)[None])[0]) == want
+
+
+def test_crossing_of_a_path_that_dips_into_the_inner_sphere(oracle):
+    """Both ends of a step may lie outside the inner sphere while the straight path between them cuts
+    through it: the crossing is the entry point (on the sphere, inside the step).  A path passing just
+    outside has none, and an end point beyond the enclosing sphere gives the exit point."""
+    O = oracle
+    c = np.zeros(3)
+    model = _spheres(O, c, [3.0, 1.0])
+    q0, q1 = np.array([[-0.5, 0.9, 0.0]]), np.array([[0.5, 0.9, 0.0]])       # chord at distance 0.9 < 1
+    th, lb, rho = O.shell_crossing(model, q0, q1, np.array([1]))
+    assert 0.0 < th[0] < 0.5 and lb[0] == 2 and rho[0] == 1.0
+    x = q0[0] + th[0] * (q1[0] - q0[0])
+    assert abs(np.linalg.norm(x) - 1.0) < 1e-14
+    th, _, _ = O.shell_crossing(model, q0 + [0, 0.2, 0], q1 + [0, 0.2, 0], np.array([1]))
+    assert np.isnan(th[0])
+    q0, q1 = np.array([[0.0, 2.5, 0.5]]), np.array([[0.0, 3.5, 0.5]])
+    th, lb, rho = O.shell_crossing(model, q0, q1, np.array([1]))
+    assert lb[0] == 0 and rho[0] == 3.0
+    x = q0[0] + th[0] * (q1[0] - q0[0])
+    assert 0.0 < th[0] < 1.0 and abs(np.linalg.norm(x) - 3.0) < 1e-14
+
+
+def test_radial_incidence_on_a_sphere(oracle):
+    """A P beam travelling along the radius of a sphere with an arbitrary centre meets it at normal
+    incidence: no converted S waves, the reflected P goes straight back, and the amplitudes are the
+    normal-incidence impedance ratios (Z2 - Z1)/(Z1 + Z2), 2 Z1/(Z1 + Z2).  A normal taken along e3
+    instead of the radius gives oblique incidence and S children."""
+    O = oracle
+    c = np.array([1.0, -2.0, 0.5])
+    cp, rho = (2.0, 3.1), (1.2, 2.5)
+    model = _spheres(O, c, [1.5], cp=cp, cs=(1.0, 1.6), rho=rho)
+    u = np.array([2.0, 1.0, -2.0]) / 3.0
+    x = c + 1.5 * u
+    st, mt = _beam(O, model, 0, c + 1.7 * u, -u, amps=(0.7 - 0.2j, 0))
+    st[0:3] = x
+    kids, km = O.shell_event(model, mt, st, 1, rel_min=1e-9)
+    got = {("r" if O.meta_layer(m) == 0 else "t") + ("S" if m & 2 else "P"): k for k, m in zip(kids, km)}
+    assert set(got) == {"rP", "tP"}
+    Z1, Z2 = rho[0] * cp[0], rho[1] * cp[1]
+    a = st[42:44].view(complex)[0]
+    np.testing.assert_allclose(got["rP"][42:44].view(complex)[0], a * (Z2 - Z1) / (Z1 + Z2), rtol=1e-12)
+    np.testing.assert_allclose(got["tP"][42:44].view(complex)[0], a * 2 * Z1 / (Z1 + Z2), rtol=1e-12)
+    pin = np.linalg.norm(st[3:6])
+    np.testing.assert_allclose(got["rP"][3:6] / pin, u, atol=1e-14)
+    np.testing.assert_allclose(got["tP"][3:6] / np.linalg.norm(got["tP"][3:6]), -u, atol=1e-14)
+
+
+@pytest.mark.parametrize("cls,inward,ang", [(0, True, 0.5), (0, False, 0.4), (2, True, 0.3), (3, False, 0.3),
+                                             (1, True, 0.45), (2, False, 0.25)])
+def test_sphere_event_children_satisfy_welded_continuity(oracle, cls, inward, ang):
+    """A beam meets a sphere (arbitrary centre) at an angle ang from its normal, below every critical angle
+    so that all children propagate: the children, in global coordinates, keep displacement and traction
+    sigma.n continuous across the tangent plane of the crossing point (n the sphere's normal there), keep
+    the tangential part of P and c |P| (Snell), and the reflected ones travel back to the incident side."""
+    O = oracle
+    c = np.array([0.4, -0.3, 2.0])
+    cp, cs, rho = (2.0, 2.6), (1.1, 1.5), (1.3, 1.9)
+    model = _spheres(O, c, [1.5], cp=cp, cs=cs, rho=rho)
+    u = np.array([-0.36, 0.48, -0.8])                   # unit vector: the crossing point is c + 1.5 u
+    x = c + 1.5 * u
+    t = np.cross(u, [0.6, 0.0, 0.8])
+    t /= np.linalg.norm(t)
+    sgn = -1.0 if cls & 1 else 1.0                      # the beam travels along sgn P
+    p = sgn * 0.9 * ((-1.0 if inward else 1.0) * math.cos(ang) * u + math.sin(ang) * t)
+    lay = 0 if inward else 1
+    st, mt = _vector_beam(O, model, cls, x - 0.05 * sgn * np.asarray(p), p)
+    assert int(O.meta_layer(mt[0])) == lay
+    st = st[0].copy()
+    st[0:3] = x
+    kids, km = O.shell_event(model, int(mt[0]), st, 1 - lay, rel_min=0.0)
+    assert len(kids) == 4
+    lam = [r * (a * a - 2 * b * b) for r, a, b in zip(rho, cp, cs)]
+    mu = [r * b * b for r, b in zip(rho, cs)]
+
+    def disp(row, m):
+        a = row[42:48].copy().view(complex)
+        return a[0] * row[3:6] / np.linalg.norm(row[3:6]) if (m & 3) < 2 else a
+
+    U_in = disp(st, int(mt[0]))
+    du, dtr = U_in.copy(), _traction_n(lam[lay], mu[lay], st[3:6], U_in, u)
+    T_in = dtr.copy()
+    cin = (cs if cls >= 2 else cp)[lay] * np.linalg.norm(st[3:6])
+    tang = st[3:6] - np.dot(st[3:6], u) * u
+    for k, m in zip(kids, km):
+        L = int(O.meta_layer(m))
+        s = 1.0 if L == lay else -1.0
+        U = disp(k, int(m))
+        du += s * U
+        dtr += s * _traction_n(lam[L], mu[L], k[3:6], U, u)
+        np.testing.assert_allclose(k[3:6] - np.dot(k[3:6], u) * u, tang, atol=1e-14)
+        np.testing.assert_allclose((cs if m & 2 else cp)[L] * np.linalg.norm(k[3:6]), cin, rtol=1e-13)
+        travel = (-1.0 if m & 1 else 1.0) * np.dot(k[3:6], u)       # outward speed of the child
+        assert (travel > 0) == (L == 0)
+        np.testing.assert_allclose(k[0:3], x, atol=1e-14)
+    assert np.linalg.norm(du) <= 1e-12 * np.linalg.norm(U_in), du
+    assert np.linalg.norm(dtr) <= 1e-12 * np.linalg.norm(T_in), dtr
+
+
+def _sphere_vs_plane_errors(O, big):
+    """Relative L2 differences (Q, P, dzQ, dzP, amplitudes) between the spherical solve with radius ~big
+    about a centre far along the normal n and the tilted-plane solve of the planes n.x = z_i, over
+    lineages, after 30 steps of the layered workload; asserts that both have the same lineages."""
+    from paper_1810_06760_gb300 import workloads as W
+    from tests.helpers import oracle_beams
+    nrm = np.array([0.3, -0.4, 0.85])
+    nrm = nrm / np.linalg.norm(nrm)
+    w = W.layered(nq=2, np_=4, ny=20, nsteps=30, dt=0.1)
+    z = np.asarray(w.medium.z_interfaces)
+    sph = _spheres(O, (z[0] + big) * nrm, [big, big - (z[1] - z[0])], cp=w.medium.layer_cp,
+                   cs=w.medium.layer_cs, rho=w.medium.layer_rho)
+    flat, _, obeams = oracle_beams(O, w)
+    st0 = np.concatenate([b[1] for b in obeams])
+    mt0 = np.concatenate([b[2] for b in obeams])
+    mid0 = np.concatenate([np.arange(b[1].shape[0]) for b in obeams])
+    Rm = O.layer_frame(nrm)
+    # spherical solve in global coordinates (S beams in vector form, layers from the spheres)
+    st, mt = O.to_vector_form(st0, mt0)
+    mt = (mt & ~np.int32(0xF0)) | (O.shell_layer(sph, st[:, 0:3]).astype(np.int32) << 4)
+    path, mid = np.zeros(st.shape[0], dtype=np.int64), mid0.copy()
+    for _ in range(w.nsteps):
+        st, mt, path, par = O.shell_step(sph, st, mt, path, w.dt, return_parent=True)
+        mid = mid[par]
+    # tilted planes: the same beams in the layer frame, flat steps, rotated back
+    tf, tm = O.rotate_beams(st0, mt0, Rm, z_interfaces=z)
+    tpath, tmid = np.zeros(tf.shape[0], dtype=np.int64), mid0.copy()
+    for _ in range(w.nsteps):
+        tf, tm, tpath, par = O.layered_step(flat, tf, tm, tpath, w.dt, return_parent=True)
+        tmid = tmid[par]
+    tf, tm = O.rotate_beams(tf, tm, Rm.T)
+    key = lambda m, i, p: [((int(a) >> 13) & 3, int(b), int(c)) for a, b, c in zip(m, i, p)]
+    ks, kt = key(mt, mid, path), key(tm, tmid, tpath)
+    assert len(set(ks)) == len(ks) and set(ks) == set(kt)
+    assert len(ks) > 1.5 * st0.shape[0]                 # interfaces were crossed
+    it = {k: i for i, k in enumerate(kt)}
+    order = [it[k] for k in ks]
+    A, B = st, tf[order]
+    np.testing.assert_array_equal(mt & 0x6FF3, tm[order] & 0x6FF3)
+    return [np.linalg.norm(A[:, sl] - B[:, sl]) / np.linalg.norm(B[:, sl])
+            for sl in (slice(0, 3), slice(3, 6), slice(6, 24), slice(24, 42), slice(42, 48))]
+
+
+def test_spheres_of_large_radius_reduce_to_tilted_planes(oracle):
+    """Concentric spheres of radius rho about a centre far along the normal n look, over the beams' paths,
+    like the planes n.x = z_i: their gap is |x_perp|^2 / 2 rho and their normals differ by |x_perp| / rho.
+    Every lineage of the spherical solve exists in the tilted-plane solve (the pinned rotate_beams + flat
+    steps), and their difference falls as 1/rho: tenfold from rho = 1e7 to 1e8 km.  At 1e8 the centres,
+    propagation vectors and amplitudes agree to 1e-5; the Jacobians to 2e-3, because a beam meeting an
+    interface at grazing incidence (P.n/|P| ~ 0.01 here) takes the jump F with the factor 1/p_n of Eq.
+    Inter_DzQDzP, which magnifies the 1/rho tilt of the normal a hundredfold."""
+    e7 = _sphere_vs_plane_errors(oracle, 1.0e7)
+    e8 = _sphere_vs_plane_errors(oracle, 1.0e8)
+    for name, a, b, bar in zip(("Q", "P", "dzQ", "dzP", "a"), e7, e8, (1e-5, 1e-5, 2e-3, 2e-3, 1e-5)):
+        assert b < bar, (name, b)
+        assert 5.0 < a / b < 20.0, (name, a, b)
