@@ -54,8 +54,12 @@ enum {
                               evaluated exactly with its gradient and Hessian */
     FGA_MEDIUM_GRID = 2,   /* c_p, c_s and their first and second derivatives given on a node
                               grid, trilinearly interpolated (all 10 fields) */
-    FGA_MEDIUM_LAYERED = 3 /* piecewise-constant layers between parallel planar interfaces (Sec. 3.1) */
+    FGA_MEDIUM_LAYERED = 3 /* piecewise-constant layers between interfaces (Sec. 3.1): parallel planes
+                              or concentric spheres (layer_shape) */
 };
+
+/* Shape of the interfaces of a layered medium. */
+enum { FGA_LAYERS_PLANES = 0, FGA_LAYERS_SPHERES = 1 };
 
 /* Velocity model (Eqs. ewe_ps, ps_speed).  Grid media: node (i,j,l) sits at
  * origin + (i*spacing[0], j*spacing[1], l*spacing[2]); positions outside the grid read the nearest
@@ -63,7 +67,16 @@ enum {
  * increasing depths (HOST arrays) measured along layer_normal: the interfaces are the planes
  * layer_normal . x = z_interfaces[i].  layer_normal = (0, 0, 0) means (0, 0, 1) (flat layers in x3);
  * any other vector is normalised (tilted layers: the library propagates such a medium in the frame
- * whose third axis is the normal and converts beams, points and results at its boundary). */
+ * whose third axis is the normal and converts beams, points and results at its boundary).
+ * layer_shape = FGA_LAYERS_SPHERES: the interfaces are the spheres |x - layer_center| = z_interfaces[i],
+ * radii strictly decreasing and positive (layer 0 lies outside the largest sphere, layer i between
+ * spheres i-1 and i; a point on a sphere belongs to the inner side), and layer_normal must be zero.
+ * Sec. 3.1 treats an interface of general shape in the local tangent-normal coordinates of the point
+ * where a beam meets it, the tangent plane standing in for the flat interface: at each crossing the
+ * library rotates the beam into the frame whose third axis is the sphere's normal there, applies the
+ * flat-interface conditions (Snell's law, continuity of displacement and traction, the dzQ/dzP jump of
+ * Eq. Inter_DzQDzP; the curvature of the sphere does not enter), and rotates the children back.  Beams,
+ * points and results stay in global coordinates. */
 typedef struct {
     int kind;
     double cp0, cs0;
@@ -73,6 +86,8 @@ typedef struct {
     int nlayers;
     const double *z_interfaces, *layer_cp, *layer_cs, *layer_rho;
     double layer_normal[3];
+    int layer_shape;
+    double layer_center[3];
 } fga_model_desc;
 
 typedef struct fga_model fga_model;
@@ -82,7 +97,8 @@ typedef struct fga_beams fga_beams;
  * n[0]*n[1]*n[2]*10 values, node-major (axis 0 slowest), fields per node
  * c, dc/dx1, dc/dx2, dc/dx3, c_11, c_12, c_13, c_22, c_23, c_33; they are copied into the
  * library's own layout (the caller may free them after the call's stream work completes).
- * Other kinds take NULL.  Errors: INVALID_ARG (kind, sizes, spacing <= 0, nlayers > 8), OOM. */
+ * Other kinds take NULL.  Errors: INVALID_ARG (kind, sizes, spacing <= 0, nlayers > 8, interface depths
+ * not increasing or radii not decreasing, a bad layer_shape), OOM. */
 fga_status fga_model_create(fga_model **out, const fga_model_desc *desc, const float *grid_p,
                             const float *grid_s, fga_stream_t s);
 fga_status fga_model_destroy(fga_model *m);

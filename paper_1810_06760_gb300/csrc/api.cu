@@ -402,6 +402,32 @@ fga_status fga_model_create(fga_model **out, const fga_model_desc *d, const floa
             set_error("fga_model_create: layered medium needs 1..8 layers and their arrays");
             return FGA_ERR_INVALID_ARG;
         }
+        const bool spheres = d->layer_shape == FGA_LAYERS_SPHERES;
+        const double *nv = d->layer_normal;
+        const double nn = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+        const char *bad = nullptr;
+        if (d->layer_shape != FGA_LAYERS_PLANES && !spheres)
+            bad = "fga_model_create: layer_shape must be FGA_LAYERS_PLANES or FGA_LAYERS_SPHERES";
+        else if (!std::isfinite(nn))
+            bad = "fga_model_create: layer_normal is not finite";
+        else if (spheres && nn != 0.0)
+            bad = "fga_model_create: spherical layers take no layer_normal";
+        else if (spheres && !(std::isfinite(d->layer_center[0]) && std::isfinite(d->layer_center[1]) &&
+                              std::isfinite(d->layer_center[2])))
+            bad = "fga_model_create: layer_center is not finite";
+        for (int l = 0; !bad && l + 1 < d->nlayers; l++) {
+            const double z = d->z_interfaces[l];
+            if (!std::isfinite(z) || (spheres && !(z > 0.0)))
+                bad = "fga_model_create: interface depths must be finite (radii positive)";
+            else if (l > 0 && (spheres ? !(z < d->z_interfaces[l - 1]) : !(z > d->z_interfaces[l - 1])))
+                bad = spheres ? "fga_model_create: sphere radii must decrease strictly"
+                              : "fga_model_create: interface depths must increase strictly";
+        }
+        if (bad) {
+            delete m;
+            set_error(bad);
+            return FGA_ERR_INVALID_ARG;
+        }
         m->dev.nlay = d->nlayers;
         m->cmax[0] = m->cmax[1] = 0;
         for (int l = 0; l < d->nlayers; l++) {
@@ -410,35 +436,18 @@ fga_status fga_model_create(fga_model **out, const fga_model_desc *d, const floa
             m->dev.lrho[l] = d->layer_rho[l];
             m->cmax[0] = std::max(m->cmax[0], d->layer_cp[l]);
             m->cmax[1] = std::max(m->cmax[1], d->layer_cs[l]);
-            if (l + 1 < d->nlayers) m->dev.zif[l] = d->z_interfaces[l];
+            // spheres: minus the radius, so that the depth -|x - centre| increases across the interfaces
+            if (l + 1 < d->nlayers) m->dev.zif[l] = spheres ? -d->z_interfaces[l] : d->z_interfaces[l];
         }
-        // the layer frame: third axis the normal, first axis the normalised cross product of a coordinate
-        // axis (the one least parallel to the normal) with the normal, second axis completing the frame
-        const double *nv = d->layer_normal;
-        const double nn = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
-        if (!std::isfinite(nn)) {
-            delete m;
-            set_error("fga_model_create: layer_normal is not finite");
-            return FGA_ERR_INVALID_ARG;
-        }
+        m->dev.shells = spheres ? 1 : 0;
+        for (int c = 0; c < 3; c++) m->dev.ctr[c] = spheres ? d->layer_center[c] : 0.0;
+        // the layer frame of planar layers: third axis the normal (frame_from_normal)
         const double n3[3] = {nn > 0 ? nv[0] / nn : 0.0, nn > 0 ? nv[1] / nn : 0.0, nn > 0 ? nv[2] / nn : 1.0};
         m->dev.tilted = (n3[0] != 0.0 || n3[1] != 0.0 || n3[2] != 1.0) ? 1 : 0;
-        const int ax = std::fabs(n3[0]) <= std::fabs(n3[1]) && std::fabs(n3[0]) <= std::fabs(n3[2]) ? 0
-                       : (std::fabs(n3[1]) <= std::fabs(n3[2]) ? 1 : 2);
-        double a[3] = {0, 0, 0}, e1[3], e2[3];
-        a[ax] = 1.0;
-        e1[0] = a[1] * n3[2] - a[2] * n3[1];
-        e1[1] = a[2] * n3[0] - a[0] * n3[2];
-        e1[2] = a[0] * n3[1] - a[1] * n3[0];
-        const double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
-        for (int c = 0; c < 3; c++) e1[c] /= l1;
-        e2[0] = n3[1] * e1[2] - n3[2] * e1[1];
-        e2[1] = n3[2] * e1[0] - n3[0] * e1[2];
-        e2[2] = n3[0] * e1[1] - n3[1] * e1[0];
-        for (int c = 0; c < 3; c++) {
-            m->dev.R[c] = m->dev.tilted ? e1[c] : (c == 0 ? 1.0 : 0.0);
-            m->dev.R[3 + c] = m->dev.tilted ? e2[c] : (c == 1 ? 1.0 : 0.0);
-            m->dev.R[6 + c] = n3[c];
+        if (m->dev.tilted) {
+            frame_from_normal(n3, m->dev.R);
+        } else {
+            for (int c = 0; c < 9; c++) m->dev.R[c] = (c % 4 == 0) ? 1.0 : 0.0;
         }
     }
     m->dev.fill_f32();

@@ -203,9 +203,15 @@ __device__ __forceinline__ void beam_init_state(const ModelDev &Md, const C2<R> 
     R q[3] = {(R)qd[0], (R)qd[1], (R)qd[2]};
     R p[3] = {(R)pd[0], (R)pd[1], (R)pd[2]};
     R cf[10];
-    // layered media are evaluated at the depth along the layer normal (x3 unless the layers are tilted)
-    const double zl = (MED == FGA_MEDIUM_LAYERED && Md.tilted)
-                          ? Md.R[6] * qd[0] + Md.R[7] * qd[1] + Md.R[8] * qd[2] : qd[2];
+    // layered media are evaluated at the depth along the layer normal (x3 unless the layers are tilted),
+    // or at minus the distance to the centre of spherical layers
+    double zl = qd[2];
+    if (MED == FGA_MEDIUM_LAYERED && Md.shells) {
+        const double r0 = qd[0] - Md.ctr[0], r1 = qd[1] - Md.ctr[1], r2 = qd[2] - Md.ctr[2];
+        zl = -sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+    } else if (MED == FGA_MEDIUM_LAYERED && Md.tilted) {
+        zl = Md.R[6] * qd[0] + Md.R[7] * qd[1] + Md.R[8] * qd[2];
+    }
     {
         const R qe[3] = {q[0], q[1], MED == FGA_MEDIUM_LAYERED ? (R)zl : q[2]};
         model_eval<R, MED>(Md, wave, qe, cf);
@@ -305,50 +311,9 @@ __global__ void rotate_to_layer_frame_kernel(ModelDev Md, R *__restrict__ st, in
     if (b >= nb) return;
     R y[NF];
     for (int f = 0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
-    const R *Rm = nullptr;
-    R Rr[9];
-    for (int i = 0; i < 9; i++) Rr[i] = (R)Md.R[i];
-    Rm = Rr;
-    auto rot = [&](const R *v, R *o) {
-        for (int i = 0; i < 3; i++) o[i] = Rm[3 * i] * v[0] + Rm[3 * i + 1] * v[1] + Rm[3 * i + 2] * v[2];
-    };
     int fl = flags[b];
-    const bool wave = (fl & FL_CLASS_MASK) >= 2;
-    R Pold[3] = {y[F_P], y[F_P + 1], y[F_P + 2]};
-    R v[3], o[3];
-    for (int base : {F_Q, F_P}) {
-        for (int i = 0; i < 3; i++) v[i] = y[base + i];
-        rot(v, o);
-        for (int i = 0; i < 3; i++) y[base + i] = o[i];
-    }
-    for (int base : {F_DQ, F_DP})
-        for (int m = 0; m < 3; m++)
-            for (int part = 0; part < 2; part++) {
-                for (int j = 0; j < 3; j++) v[j] = y[base + 2 * (3 * m + j) + part];
-                rot(v, o);
-                for (int j = 0; j < 3; j++) y[base + 2 * (3 * m + j) + part] = o[j];
-            }
-    if (wave) {
-        R Nsv[3], Nsh[3], Ar[3], Ai[3];
-        s_frame<R>(Pold, (fl & FL_REF_E1) != 0, Nsv, Nsh);
-        for (int i = 0; i < 3; i++) {
-            Ar[i] = y[F_A0] * Nsv[i] + y[F_A1] * Nsh[i];
-            Ai[i] = y[F_A0 + 1] * Nsv[i] + y[F_A1 + 1] * Nsh[i];
-        }
-        R Arr[3], Air[3];
-        rot(Ar, Arr);
-        rot(Ai, Air);
-        const R *P = y + F_P;
-        const R pn2 = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
-        const bool r1 = (P[0] * P[0] + P[1] * P[1]) < R(0.01) * pn2;
-        fl = r1 ? (fl | FL_REF_E1) : (fl & ~FL_REF_E1);
-        s_frame<R>(P, r1, Nsv, Nsh);
-        y[F_A0] = Arr[0] * Nsv[0] + Arr[1] * Nsv[1] + Arr[2] * Nsv[2];
-        y[F_A0 + 1] = Air[0] * Nsv[0] + Air[1] * Nsv[1] + Air[2] * Nsv[2];
-        y[F_A1] = Arr[0] * Nsh[0] + Arr[1] * Nsh[1] + Arr[2] * Nsh[2];
-        y[F_A1 + 1] = Air[0] * Nsh[0] + Air[1] * Nsh[1] + Air[2] * Nsh[2];
-        flags[b] = fl;
-    }
+    rotate_state<R>(Md.R, false, true, y, fl);
+    flags[b] = fl;
     for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y[f];
 }
 

@@ -176,6 +176,52 @@ __device__ __forceinline__ R s_frame(const R P[3], bool ref_e1, R Nsv[3], R Nsh[
     return vn;
 }
 
+// A beam state into the frame x' = Rm x (with transpose, x' = Rm^T x), in FP64: P, Q when with_q, and
+// each row m of dzQ and dzP (the vectors dQ/dz_m, dP/dz_m) rotate; an S beam's polarisation vector
+// a_sv N_sv + a_sh N_sh rotates with it and is re-expressed in the S frame of the rotated P, whose
+// reference axis (FL_REF_E1 in fl) follows the decomposition's rule (e1 when |P_h|^2 < 0.01 |P|^2).
+template <typename R>
+__device__ void rotate_state(const double *Rm, bool transpose, bool with_q, R *y, int &fl) {
+    auto rot = [&](const double *v, double *o) {
+        for (int i = 0; i < 3; i++)
+            o[i] = transpose ? Rm[i] * v[0] + Rm[3 + i] * v[1] + Rm[6 + i] * v[2]
+                             : Rm[3 * i] * v[0] + Rm[3 * i + 1] * v[1] + Rm[3 * i + 2] * v[2];
+    };
+    const double Pold[3] = {(double)y[F_P], (double)y[F_P + 1], (double)y[F_P + 2]};
+    double v[3], o[3];
+    for (int base : {F_Q, F_P}) {
+        if (base == F_Q && !with_q) continue;
+        for (int i = 0; i < 3; i++) v[i] = (double)y[base + i];
+        rot(v, o);
+        for (int i = 0; i < 3; i++) y[base + i] = (R)o[i];
+    }
+    for (int base : {F_DQ, F_DP})
+        for (int m = 0; m < 3; m++)
+            for (int part = 0; part < 2; part++) {
+                for (int j = 0; j < 3; j++) v[j] = (double)y[base + 2 * (3 * m + j) + part];
+                rot(v, o);
+                for (int j = 0; j < 3; j++) y[base + 2 * (3 * m + j) + part] = (R)o[j];
+            }
+    if ((fl & FL_CLASS_MASK) < 2) return;
+    double Nsv[3], Nsh[3], Ar[3], Ai[3], Arr[3], Air[3];
+    s_frame<double>(Pold, (fl & FL_REF_E1) != 0, Nsv, Nsh);
+    for (int i = 0; i < 3; i++) {
+        Ar[i] = (double)y[F_A0] * Nsv[i] + (double)y[F_A1] * Nsh[i];
+        Ai[i] = (double)y[F_A0 + 1] * Nsv[i] + (double)y[F_A1 + 1] * Nsh[i];
+    }
+    rot(Ar, Arr);
+    rot(Ai, Air);
+    double P[3];
+    rot(Pold, P);
+    const bool r1 = (P[0] * P[0] + P[1] * P[1]) < 0.01 * (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+    fl = r1 ? (fl | FL_REF_E1) : (fl & ~FL_REF_E1);
+    s_frame<double>(P, r1, Nsv, Nsh);
+    y[F_A0] = (R)(Arr[0] * Nsv[0] + Arr[1] * Nsv[1] + Arr[2] * Nsv[2]);
+    y[F_A0 + 1] = (R)(Air[0] * Nsv[0] + Air[1] * Nsv[1] + Air[2] * Nsv[2]);
+    y[F_A1] = (R)(Arr[0] * Nsh[0] + Arr[1] * Nsh[1] + Arr[2] * Nsh[2]);
+    y[F_A1 + 1] = (R)(Air[0] * Nsh[0] + Air[1] * Nsh[1] + Air[2] * Nsh[2]);
+}
+
 // complex helpers on (re, im) pairs kept in scalars
 template <typename R> struct C2 {
     R r, i;

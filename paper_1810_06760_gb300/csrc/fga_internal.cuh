@@ -56,6 +56,10 @@ struct ModelDev {
     // beams live in the layer frame, x' = R x
     int tilted;
     double R[9];
+    // spherical layers: the interfaces are |x - ctr| = -zif[i] (zif holds minus the radii, so that the
+    // depth -|x - ctr| orders the layers as x3 does for flat ones)
+    int shells;
+    double ctr[3];
     // FP32 copies of the scalar parameters: the FP32 kernels read these and never convert from
     // double (FP64 instructions are very slow on this GPU)
     float fcp0, fcs0, famp, fcs_ratio, fo[3], finv_h[3], fzif[MAX_LAYERS], flcp[MAX_LAYERS], flcs[MAX_LAYERS];
@@ -75,6 +79,30 @@ struct ModelDev {
         }
     }
 };
+
+// An orthonormal frame whose third axis is the unit vector n, as the rows of R (x' = R x): the first
+// axis is the normalised cross product of the coordinate axis least parallel to n with n, the second
+// completes the right-handed frame.
+__host__ __device__ inline void frame_from_normal(const double n[3], double R[9]) {
+    const double a0 = fabs(n[0]), a1 = fabs(n[1]), a2 = fabs(n[2]);
+    const int ax = (a0 <= a1 && a0 <= a2) ? 0 : (a1 <= a2 ? 1 : 2);
+    double a[3] = {0.0, 0.0, 0.0}, e1[3];
+    a[ax] = 1.0;
+    e1[0] = a[1] * n[2] - a[2] * n[1];
+    e1[1] = a[2] * n[0] - a[0] * n[2];
+    e1[2] = a[0] * n[1] - a[1] * n[0];
+    const double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int c = 0; c < 3; c++) e1[c] /= l1;
+    R[0] = e1[0];
+    R[1] = e1[1];
+    R[2] = e1[2];
+    R[3] = n[1] * e1[2] - n[2] * e1[1];
+    R[4] = n[2] * e1[0] - n[0] * e1[2];
+    R[5] = n[0] * e1[1] - n[1] * e1[0];
+    R[6] = n[0];
+    R[7] = n[1];
+    R[8] = n[2];
+}
 
 // error handling ---------------------------------------------------------------------------
 void set_error(const std::string &msg);

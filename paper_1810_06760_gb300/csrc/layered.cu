@@ -1,8 +1,9 @@
-// A7: beams in a medium of flat homogeneous layers (Sec. 3.1).  Inside a layer grad c = 0, so a
-// beam moves on a straight line; a step that crosses an interface is split at the crossing, where
-// the beam is replaced by its reflected and transmitted P and S children (Snell's law, plane-wave
-// continuity of displacement and traction, and the dzQ/dzP jump of Eq. Inter_DzQDzP), and every
-// child finishes the step.  Children are appended to the beam arrays with an atomic counter; the
+// A7: beams in a medium of homogeneous layers (Sec. 3.1) between parallel planes or concentric
+// spheres.  Inside a layer grad c = 0, so a beam moves on a straight line; a step that crosses an
+// interface is split at the crossing, where the beam is replaced by its reflected and transmitted P and
+// S children (Snell's law, plane-wave continuity of displacement and traction, and the dzQ/dzP jump of
+// Eq. Inter_DzQDzP; at a sphere all of it in the local tangent-normal frame of the crossing point), and
+// every child finishes the step.  Children are appended to the beam arrays with an atomic counter; the
 // parent's slot goes to its first child.
 #include <cmath>
 
@@ -341,7 +342,145 @@ __device__ void make_child(const R *yc, const EventOut &ev, int k, R *out) {
     out[F_A1 + 1] = (R)ev.a1[k].i;
 }
 
+// Spherical layers (interfaces |x - c| = rho_i, rho_i = -zif[i] decreasing): the first crossing of the
+// straight path q0 -> q1 of one step (a beam moves on a line in a homogeneous layer) with a sphere that
+// bounds layer L, s(th) = q0 - c + th d, d = q1 - q0, |s(th)|^2 = a th^2 + b th + |q0 - c|^2.  The inner
+// sphere is met when the path heads inward (b < 0) and the smaller root, 2 c0 / (-b + sqrt D), lies below
+// 1 (a path may dip into it and leave again within one step); the outer sphere bounds a convex ball, so
+// only an end point beyond it means a crossing, at the positive root.  Returns false without a crossing,
+// else the fraction th of the step, the layer lb entered and the radius crossed.
+__device__ bool shell_crossing(const ModelDev &M, int L, const double q0[3], const double q1[3], double &th, int &lb,
+                               double &rho) {
+    double s0[3], d[3], s1[3];
+    for (int c = 0; c < 3; c++) {
+        s0[c] = q0[c] - M.ctr[c];
+        s1[c] = q1[c] - M.ctr[c];
+        d[c] = q1[c] - q0[c];
+    }
+    const double a = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double b = 2.0 * (s0[0] * d[0] + s0[1] * d[1] + s0[2] * d[2]);
+    const double ss = s0[0] * s0[0] + s0[1] * s0[1] + s0[2] * s0[2];
+    bool hit = false;
+    if (L < M.nlay - 1) {
+        const double r = -M.zif[L];
+        const double c0 = ss - r * r, D = b * b - 4.0 * a * c0;
+        if (b < 0.0 && D >= 0.0) {
+            const double t = 2.0 * c0 / (-b + sqrt(D));
+            if (t < 1.0) {
+                th = t;
+                lb = L + 1;
+                rho = r;
+                hit = true;
+            }
+        }
+    }
+    if (L > 0) {
+        const double r = -M.zif[L - 1];
+        if (s1[0] * s1[0] + s1[1] * s1[1] + s1[2] * s1[2] > r * r) {
+            const double c0 = ss - r * r, D = fmax(b * b - 4.0 * a * c0, 0.0);
+            const double t = b <= 0.0 ? (-b + sqrt(D)) / (2.0 * a) : -2.0 * c0 / (b + sqrt(D));
+            if (!hit || t < th) {
+                th = t;
+                lb = L - 1;
+                rho = r;
+                hit = true;
+            }
+        }
+    }
+    return hit;
+}
+
 }  // namespace
+
+// Write child ce (with its Q compensation) of the beam in slot b: the first child takes the parent's slot,
+// the others are appended (atomic counter); children beyond cap are counted in counts[1].
+template <typename R>
+__device__ void store_child(R *__restrict__ st, int32_t *__restrict__ flags, int32_t *__restrict__ ids,
+                            long long *__restrict__ path, int64_t cap, unsigned long long *__restrict__ counts, int64_t b,
+                            int k, const R *ce, const R *qch, int flc, int32_t id, long long pp, int slot) {
+    int64_t dst = b;
+    if (k > 0) {
+        dst = (int64_t)atomicAdd(&counts[0], 1ull);
+        if (dst >= cap) {
+            atomicAdd(&counts[1], 1ull);
+            return;
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; f++) st[(int64_t)f * cap + dst] = ce[f];
+#pragma unroll
+    for (int d = 0; d < 3; d++) st[(int64_t)(F_QC + d) * cap + dst] = qch[d];
+    flags[dst] = flc;
+    ids[dst] = id;
+    path[dst] = pp * 4 + slot + 1;
+}
+
+// The step of beam b (state y, its full-step result y1) in spherical layers.  Without a crossing y1 is
+// kept.  Otherwise the beam advances to the crossing, which is put on the sphere in FP64 (its FP32
+// rounding goes to the Q compensation), and is rotated into the local frame whose third axis is the
+// sphere's outward normal there; the flat-interface event runs in that frame (Sec. 3.1: the tangent plane
+// stands in for the interface), and every child is rotated back and finishes the step.
+template <typename R>
+__device__ __noinline__ void shell_step(const ModelDev &M, R *__restrict__ st, int32_t *__restrict__ flags,
+                                        int32_t *__restrict__ ids, long long *__restrict__ path, int64_t cap,
+                                        unsigned long long *__restrict__ counts, R dt, int gmax, double rel_min,
+                                        int64_t b, int fl, R sg, R c, const R *y, const R *y1, const R *qc0,
+                                        const R *qc1) {
+    const int L = (fl >> 4) & 15;
+    double q0[3], q1[3], th = 0.0, rho = 0.0;
+    int lb = L;
+    for (int d = 0; d < 3; d++) {
+        q0[d] = (double)y[F_Q + d] - (double)qc0[d];
+        q1[d] = (double)y1[F_Q + d] - (double)qc1[d];
+    }
+    if (!shell_crossing(M, L, q0, q1, th, lb, rho)) {
+#pragma unroll
+        for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y1[f];
+#pragma unroll
+        for (int d = 0; d < 3; d++) st[(int64_t)(F_QC + d) * cap + b] = qc1[d];
+        return;
+    }
+    if (((fl >> 8) & 15) >= gmax) {
+        flags[b] = fl | FL_DEAD;
+        return;
+    }
+    R yc[NF], qc[3] = {qc0[0], qc0[1], qc0[2]};
+    layer_rk4<R>(sg, c, y, (R)th * dt, yc, qc);
+    double s[3], sn = 0.0;
+    for (int d = 0; d < 3; d++) {
+        s[d] = (double)yc[F_Q + d] - (double)qc[d] - M.ctr[d];
+        sn += s[d] * s[d];
+    }
+    sn = sqrt(sn);
+    double nrm[3], Rl[9];
+    for (int d = 0; d < 3; d++) {
+        nrm[d] = s[d] / sn;
+        const double x = M.ctr[d] + rho * nrm[d];
+        yc[F_Q + d] = (R)x;
+        qc[d] = (R)((double)yc[F_Q + d] - x);
+    }
+    frame_from_normal(nrm, Rl);
+    int fll = fl;
+    rotate_state<R>(Rl, false, false, yc, fll);   // Q stays global: the event does not read it
+    EventOut ev;
+    interface_event<R>(M, fll, yc, lb, rel_min, ev);
+    if (ev.n == 0) {
+        flags[b] = fl | FL_DEAD;
+        return;
+    }
+    const long long pp = path[b];
+    const int32_t id = ids[b];
+    for (int k = 0; k < ev.n; k++) {
+        R ch[NF], ce[NF], qch[3] = {qc[0], qc[1], qc[2]};
+        make_child<R>(yc, ev, k, ch);
+        int flc = ev.flags[k];
+        rotate_state<R>(Rl, true, false, ch, flc);
+        const R sgc = (flc & 1) ? R(-1) : R(1);
+        layer_rk4<R>(sgc, layer_speed<R>(M, (flc & FL_CLASS_MASK) >= 2, (flc >> 4) & 15), ch, R(1.0 - th) * dt, ce,
+                     qch);
+        store_child<R>(st, flags, ids, path, cap, counts, b, k, ce, qch, flc, id, pp, ev.slot[k]);
+    }
+}
 
 // One step for every beam alive at the start of the step (n_begin = *counts); children beyond the
 // first are appended at *counts (atomic); overflow beyond cap is counted in counts[1].
@@ -364,6 +503,10 @@ __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__rest
     for (int d = 0; d < 3; d++) qc1[d] = qc[d] = st[(int64_t)(F_QC + d) * cap + b];
     const R c = layer_speed<R>(M, wave, L);
     layer_rk4<R>(sg, c, y, dt, y1, qc1);
+    if (M.shells) {
+        shell_step<R>(M, st, flags, ids, path, cap, counts, dt, gmax, rel_min, b, fl, sg, c, y, y1, qc, qc1);
+        return;
+    }
     const R ztop = L > 0 ? mp<R>(M.zif[L - 1], M.fzif[L - 1]) : -R(INFINITY);
     const R zbot = L < M.nlay - 1 ? mp<R>(M.zif[L], M.fzif[L]) : R(INFINITY);
     if (y1[F_Q + 2] >= ztop && y1[F_Q + 2] < zbot) {
@@ -401,21 +544,7 @@ __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__rest
         const R sgc = (flc & 1) ? R(-1) : R(1);
         layer_rk4<R>(sgc, layer_speed<R>(M, (flc & FL_CLASS_MASK) >= 2, (flc >> 4) & 15), ch, (R(1) - th) * dt, ce,
                      qch);
-        int64_t dst = b;
-        if (k > 0) {
-            dst = (int64_t)atomicAdd(&counts[0], 1ull);
-            if (dst >= cap) {
-                atomicAdd(&counts[1], 1ull);
-                continue;
-            }
-        }
-#pragma unroll
-        for (int f = 0; f < NF; f++) st[(int64_t)f * cap + dst] = ce[f];
-#pragma unroll
-        for (int d = 0; d < 3; d++) st[(int64_t)(F_QC + d) * cap + dst] = qch[d];
-        flags[dst] = flc;
-        ids[dst] = id;
-        path[dst] = pp * 4 + ev.slot[k] + 1;
+        store_child<R>(st, flags, ids, path, cap, counts, b, k, ce, qch, flc, id, pp, ev.slot[k]);
     }
 }
 
