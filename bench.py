@@ -65,6 +65,9 @@ def parse():
                          "35 km, 10^3 q x 8^3 p x 4 classes (2.05 M beams) with psi selection 1e-6, 120 s at "
                          "dt = 0.01 s (12,000 steps), 256 surface stations (16 x 16 over +-300 km) every 0.1 s; "
                          "plus the FP32 error against FP64 on a 5^3 q x 4^3 p stride sample of it")
+    ap.add_argument("--shells", type=float, default=0.0, metavar="RC",
+                    help="with --layered: the same crust bent into concentric spheres about (0, 0, RC) km (radii "
+                         "RC - 15 and RC - 35; e.g. 6371 for the Earth), stations on the sphere r = RC")
     ap.add_argument("--policy", default="shortest", choices=["fifo", "shortest"],
                     help="with --serving: admission order (submission order, or least estimated work first with a "
                          "2 s age bound)")
@@ -734,7 +737,8 @@ def run_layered(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        seis, _ = fga.solve(model, desc, w.dt, w.nsteps, w.times, rw=w.rw, rx_axes=w.rx_axes)
+        rx = None if w.rx_axes is not None else torch.as_tensor(w.receivers, device=dev)
+        seis, _ = fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, rw=w.rw, rx_axes=w.rx_axes)
         e1.record()
         torch.cuda.synchronize()
         prof = fga.profile_read(reset=True)
@@ -742,8 +746,9 @@ def run_layered(args):
         model.close()
         return seis, e0.elapsed_time(e1), prof
 
-    w = W.layered(**sizes)
-    warm = W.layered(**dict(sizes, nsteps=100, n_times=10))    # the same kernels and buffers, 100 steps
+    make = (lambda **kw: W.shells(rc=args.shells, **kw)) if args.shells > 0 else W.layered
+    w = make(**sizes)
+    warm = make(**dict(sizes, nsteps=100, n_times=10))    # the same kernels and buffers, 100 steps
     for _ in range(args.warmup):
         solve(warm, prec)
     times = []
@@ -762,7 +767,7 @@ def run_layered(args):
     b.close()
     model.close()
     # FP32 against FP64 on a stride sample of the workload (5^3 q x 4^3 p), same times and stations
-    ws = W.layered(**dict(sizes, nq=5, np_=4))
+    ws = make(**dict(sizes, nq=5, np_=4))
     s32, ms32, _ = solve(ws, fga.PREC_FP32)
     s64, ms64, _ = solve(ws, fga.PREC_FP64)
     a, r = s32.cpu().numpy().astype(np.complex128), s64.cpu().numpy()
@@ -770,7 +775,10 @@ def run_layered(args):
             "value": world * prof["beam_steps"] / (ms / 1e3), "unit": "beam-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
-            "config": {"workload": f"layered crust (interfaces 15, 35 km), explosive source at 10 km, k = {w.k:.3f}/km, "
+            "config": {"workload": (f"spherical crust (spheres r = {args.shells - 15:g}, {args.shells - 35:g} km about "
+                                    f"(0, 0, {args.shells:g})), " if args.shells > 0 else
+                                    "layered crust (interfaces 15, 35 km), ") +
+                                   f"explosive source at 10 km, k = {w.k:.3f}/km, "
                                    f"{w.mesh.nq}^3 q x {w.mesh.np_}^3 p x 4 classes, psi selection 1e-6, "
                                    f"{w.nsteps} steps of {w.dt} s, {len(w.receivers)} stations x {len(w.times)} samples",
                        "parallelism": f"replicas x{world}"},

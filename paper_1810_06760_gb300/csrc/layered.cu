@@ -390,6 +390,32 @@ __device__ bool shell_crossing(const ModelDev &M, int L, const double q0[3], con
     return hit;
 }
 
+// FP32 screen for spherical layers: true when the straight path q0 -> q1 certainly meets no sphere of
+// layer L, i.e. the end point lies inside the enclosing sphere and the path's closest approach to the
+// centre lies outside the inner one, each with a relative margin of 1e-5 on r^2.
+__device__ __forceinline__ bool shell_clear(const ModelDev &M, int L, const float *q0, const float *q1) {
+    const float c0 = (float)M.ctr[0], c1 = (float)M.ctr[1], c2 = (float)M.ctr[2];
+    const float s0[3] = {q0[0] - c0, q0[1] - c1, q0[2] - c2};
+    const float d[3] = {q1[0] - q0[0], q1[1] - q0[1], q1[2] - q0[2]};
+    const float r0 = s0[0] * s0[0] + s0[1] * s0[1] + s0[2] * s0[2];
+    const float a = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const float b = 2.0f * (s0[0] * d[0] + s0[1] * d[1] + s0[2] * d[2]);
+    if (L > 0) {
+        const float ro = M.fzif[L - 1];                      // minus the enclosing radius
+        const float r1 = r0 + b + a;                         // |q1 - c|^2
+        if (!(r1 < ro * ro * (1.0f - 1e-5f))) return false;
+    }
+    if (L < M.nlay - 1) {
+        const float ri = M.fzif[L];
+        float t = b < 0.0f ? -b / (2.0f * a) : 0.0f;         // closest approach on the path
+        t = t > 1.0f ? 1.0f : t;
+        const float rmin = r0 + t * (b + a * t);
+        if (!(rmin > ri * ri * (1.0f + 1e-5f))) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ bool shell_clear(const ModelDev &, int, const double *, const double *) { return false; }
+
 }  // namespace
 
 // Write child ce (with its Q compensation) of the beam in slot b: the first child takes the parent's slot,
@@ -415,36 +441,21 @@ __device__ void store_child(R *__restrict__ st, int32_t *__restrict__ flags, int
     path[dst] = pp * 4 + slot + 1;
 }
 
-// The step of beam b (state y, its full-step result y1) in spherical layers.  Without a crossing y1 is
-// kept.  Otherwise the beam advances to the crossing, which is put on the sphere in FP64 (its FP32
-// rounding goes to the Q compensation), and is rotated into the local frame whose third axis is the
-// sphere's outward normal there; the flat-interface event runs in that frame (Sec. 3.1: the tangent plane
-// stands in for the interface), and every child is rotated back and finishes the step.
+// The interface event of beam b in spherical layers, at fraction th of the step where it enters layer lb
+// through the sphere of radius rho.  The beam (still unchanged in st) advances to the crossing, which is
+// put on the sphere in FP64 (its FP32 rounding goes to the Q compensation), and is rotated into the local
+// frame whose third axis is the sphere's outward normal there; the flat-interface event runs in that frame
+// (Sec. 3.1: the tangent plane stands in for the interface), and every child is rotated back and finishes
+// the step.  Kept out of line and reading its beam from memory, so that the step kernel's state stays in
+// registers.
 template <typename R>
-__device__ __noinline__ void shell_step(const ModelDev &M, R *__restrict__ st, int32_t *__restrict__ flags,
-                                        int32_t *__restrict__ ids, long long *__restrict__ path, int64_t cap,
-                                        unsigned long long *__restrict__ counts, R dt, int gmax, double rel_min,
-                                        int64_t b, int fl, R sg, R c, const R *y, const R *y1, const R *qc0,
-                                        const R *qc1) {
-    const int L = (fl >> 4) & 15;
-    double q0[3], q1[3], th = 0.0, rho = 0.0;
-    int lb = L;
-    for (int d = 0; d < 3; d++) {
-        q0[d] = (double)y[F_Q + d] - (double)qc0[d];
-        q1[d] = (double)y1[F_Q + d] - (double)qc1[d];
-    }
-    if (!shell_crossing(M, L, q0, q1, th, lb, rho)) {
-#pragma unroll
-        for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y1[f];
-#pragma unroll
-        for (int d = 0; d < 3; d++) st[(int64_t)(F_QC + d) * cap + b] = qc1[d];
-        return;
-    }
-    if (((fl >> 8) & 15) >= gmax) {
-        flags[b] = fl | FL_DEAD;
-        return;
-    }
-    R yc[NF], qc[3] = {qc0[0], qc0[1], qc0[2]};
+__device__ __noinline__ void shell_event_step(const ModelDev &M, R *__restrict__ st, int32_t *__restrict__ flags,
+                                              int32_t *__restrict__ ids, long long *__restrict__ path, int64_t cap,
+                                              unsigned long long *__restrict__ counts, R dt, double rel_min, int64_t b,
+                                              int fl, R sg, R c, double th, int lb, double rho) {
+    R y[NF], yc[NF], qc[3];
+    for (int f = 0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
+    for (int d = 0; d < 3; d++) qc[d] = st[(int64_t)(F_QC + d) * cap + b];
     layer_rk4<R>(sg, c, y, (R)th * dt, yc, qc);
     double s[3], sn = 0.0;
     for (int d = 0; d < 3; d++) {
@@ -484,7 +495,7 @@ __device__ __noinline__ void shell_step(const ModelDev &M, R *__restrict__ st, i
 
 // One step for every beam alive at the start of the step (n_begin = *counts); children beyond the
 // first are appended at *counts (atomic); overflow beyond cap is counted in counts[1].
-template <typename R>
+template <typename R, bool SHELLS>
 __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__restrict__ st, int32_t *__restrict__ flags,
                                                           int32_t *__restrict__ ids, long long *__restrict__ path,
                                                           int64_t cap, const int64_t *__restrict__ n_begin,
@@ -503,8 +514,31 @@ __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__rest
     for (int d = 0; d < 3; d++) qc1[d] = qc[d] = st[(int64_t)(F_QC + d) * cap + b];
     const R c = layer_speed<R>(M, wave, L);
     layer_rk4<R>(sg, c, y, dt, y1, qc1);
-    if (M.shells) {
-        shell_step<R>(M, st, flags, ids, path, cap, counts, dt, gmax, rel_min, b, fl, sg, c, y, y1, qc, qc1);
+    if (SHELLS) {
+        // FP32: a step that stays clear of every sphere of its layer (by a margin of 1e-5 of r^2, far above
+        // the rounding of the screen) is decided by the screen; the rest take the exact FP64 test
+        bool hit = false;
+        double th = 0.0, rho = 0.0;
+        int lb = L;
+        if (!(sizeof(R) == 4 && shell_clear(M, L, y + F_Q, y1 + F_Q))) {
+            double q0[3], q1[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                q0[d] = (double)y[F_Q + d] - (double)qc[d];
+                q1[d] = (double)y1[F_Q + d] - (double)qc1[d];
+            }
+            hit = shell_crossing(M, L, q0, q1, th, lb, rho);
+        }
+        if (!hit) {
+#pragma unroll
+            for (int f = 0; f < NF; f++) st[(int64_t)f * cap + b] = y1[f];
+#pragma unroll
+            for (int d = 0; d < 3; d++) st[(int64_t)(F_QC + d) * cap + b] = qc1[d];
+        } else if (((fl >> 8) & 15) >= gmax) {
+            flags[b] = fl | FL_DEAD;
+        } else {
+            shell_event_step<R>(M, st, flags, ids, path, cap, counts, dt, rel_min, b, fl, sg, c, th, lb, rho);
+        }
         return;
     }
     const R ztop = L > 0 ? mp<R>(M.zif[L - 1], M.fzif[L - 1]) : -R(INFINITY);
@@ -564,15 +598,17 @@ fga_status launch_layered_steps(const fga_model *m, fga_beams *b, double dt, int
         }
         prof_add_beam_steps(b->nb);
         ProfScope ps(P_PROP, s);
+        // spherical layers in their own instantiation, so that the planar kernel carries none of their code
+        auto kd = m->dev.shells ? layered_step_kernel<double, true> : layered_step_kernel<double, false>;
+        auto kf = m->dev.shells ? layered_step_kernel<float, true> : layered_step_kernel<float, false>;
         if (b->precision == FGA_PREC_FP64)
-            layered_step_kernel<double><<<blocks, T, 0, s>>>(
-                m->dev, b->state.as<double>(), b->flags.as<int32_t>(), b->id.as<int32_t>(), b->path.as<long long>(),
-                b->cap, b->n_begin.as<int64_t>(), b->counts.as<unsigned long long>(), dt, b->gmax, b->rel_min);
+            kd<<<blocks, T, 0, s>>>(m->dev, b->state.as<double>(), b->flags.as<int32_t>(), b->id.as<int32_t>(),
+                                    b->path.as<long long>(), b->cap, b->n_begin.as<int64_t>(),
+                                    b->counts.as<unsigned long long>(), dt, b->gmax, b->rel_min);
         else
-            layered_step_kernel<float><<<blocks, T, 0, s>>>(
-                m->dev, b->state.as<float>(), b->flags.as<int32_t>(), b->id.as<int32_t>(), b->path.as<long long>(),
-                b->cap, b->n_begin.as<int64_t>(), b->counts.as<unsigned long long>(), (float)dt, b->gmax,
-                b->rel_min);
+            kf<<<blocks, T, 0, s>>>(m->dev, b->state.as<float>(), b->flags.as<int32_t>(), b->id.as<int32_t>(),
+                                    b->path.as<long long>(), b->cap, b->n_begin.as<int64_t>(),
+                                    b->counts.as<unsigned long long>(), (float)dt, b->gmax, b->rel_min);
     }
     FGA_CUDA(cudaGetLastError());
     return FGA_OK;
