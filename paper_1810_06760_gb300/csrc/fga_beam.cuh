@@ -11,12 +11,18 @@ namespace fga {
 template <typename R> struct Real;
 template <> struct Real<float> {
     static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    // 1/x for x > 0 as rsqrt(x)^2: two instructions, a few ulp (FP32 only; FP64 divides)
+    static __device__ __forceinline__ float rcp_pos_(float x) {
+        const float r = rsqrtf(x);
+        return r * r;
+    }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
 };
 template <> struct Real<double> {
     static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double rcp_pos_(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
     static __device__ __forceinline__ double floor_(double x) { return floor(x); }
@@ -151,9 +157,9 @@ __device__ __forceinline__ void model_eval(const ModelDev &M, int wave, const R 
 }
 
 // S polarisation frame: N_sh = e x P / |e x P| (e = e3, or e1 for near-vertical beams),
-// N_sv = N_sh x P/|P|.  Returns |e x P|.
+// N_sv = N_sh x P/|P|.  Returns |e x P| (and its reciprocal in *inv when given).
 template <typename R>
-__device__ __forceinline__ R s_frame(const R P[3], bool ref_e1, R Nsv[3], R Nsh[3]) {
+__device__ __forceinline__ R s_frame(const R P[3], bool ref_e1, R Nsv[3], R Nsh[3], R *inv = nullptr) {
     R v0, v1, v2;
     if (ref_e1) {
         v0 = R(0);
@@ -164,8 +170,10 @@ __device__ __forceinline__ R s_frame(const R P[3], bool ref_e1, R Nsv[3], R Nsh[
         v1 = P[0];
         v2 = R(0);
     }
-    const R vn = Real<R>::sqrt_(v0 * v0 + v1 * v1 + v2 * v2);
-    const R iv = R(1) / vn;
+    const R v2s = v0 * v0 + v1 * v1 + v2 * v2;
+    const R iv = Real<R>::rsqrt_(v2s);
+    const R vn = v2s * iv;
+    if (inv) *inv = iv;
     Nsh[0] = v0 * iv;
     Nsh[1] = v1 * iv;
     Nsh[2] = v2 * iv;
@@ -254,8 +262,9 @@ __device__ __forceinline__ void beam_rhs(const ModelDev &M, R sg, bool ref_e1, c
     const R g[3] = {cf[1], cf[2], cf[3]};
     const R H[3][3] = {{cf[4], cf[5], cf[6]}, {cf[5], cf[7], cf[8]}, {cf[6], cf[8], cf[9]}};
     const R P[3] = {y[F_P], y[F_P + 1], y[F_P + 2]};
-    const R ip = Real<R>::rsqrt_(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
-    const R pn = R(1) / ip;
+    const R p2 = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
+    const R ip = Real<R>::rsqrt_(p2);
+    const R pn = p2 * ip;   // |P| without a division
     const R Ph[3] = {P[0] * ip, P[1] * ip, P[2] * ip};
     const R sc = sg * c;
 #pragma unroll
@@ -352,7 +361,7 @@ __device__ __forceinline__ void beam_rhs(const ModelDev &M, R sg, bool ref_e1, c
             tr += Cf[m][j].r * Zd[m][j].r - Cf[m][j].i * Zd[m][j].i;
             ti += Cf[m][j].r * Zd[m][j].i + Cf[m][j].i * Zd[m][j].r;
         }
-    const R idn = R(1) / (dr * dr + di * di);
+    const R idn = Real<R>::rcp_pos_(dr * dr + di * di);
     // gamma = sg grad c . P^ + (tr / det) / 2
     const R gr = sg * (g[0] * Ph[0] + g[1] * Ph[1] + g[2] * Ph[2]) + R(0.5) * (tr * dr + ti * di) * idn;
     const R gi = R(0.5) * (ti * dr - tr * di) * idn;
@@ -363,8 +372,8 @@ __device__ __forceinline__ void beam_rhs(const ModelDev &M, R sg, bool ref_e1, c
         f[F_A1] = R(0);
         f[F_A1 + 1] = R(0);
     } else {
-        R Nsv[3], Nsh[3];
-        const R vn = s_frame<R>(P, ref_e1, Nsv, Nsh);
+        R Nsv[3], Nsh[3], ivn;
+        s_frame<R>(P, ref_e1, Nsv, Nsh, &ivn);
         const R *Pd = f + F_P;
         R ePd0, ePd1, ePd2;
         if (ref_e1) {
@@ -376,7 +385,7 @@ __device__ __forceinline__ void beam_rhs(const ModelDev &M, R sg, bool ref_e1, c
             ePd1 = Pd[0];
             ePd2 = R(0);
         }
-        const R om = (ePd0 * Nsv[0] + ePd1 * Nsv[1] + ePd2 * Nsv[2]) / vn;
+        const R om = (ePd0 * Nsv[0] + ePd1 * Nsv[1] + ePd2 * Nsv[2]) * ivn;
         const R a1r = y[F_A1], a1i = y[F_A1 + 1];
         f[F_A0] = gr * a0r - gi * a0i - om * a1r;
         f[F_A0 + 1] = gr * a0i + gi * a0r - om * a1i;

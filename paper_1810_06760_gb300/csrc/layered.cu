@@ -88,7 +88,7 @@ __device__ __forceinline__ void layer_rhs(R sg, R c, const R *y, R *f) {
             tr += Cf[m][j].r * Zd[m][j].r - Cf[m][j].i * Zd[m][j].i;
             ti += Cf[m][j].r * Zd[m][j].i + Cf[m][j].i * Zd[m][j].r;
         }
-    const R idn = R(1) / (dr * dr + di * di);
+    const R idn = Real<R>::rcp_pos_(dr * dr + di * di);
     const R gr = R(0.5) * (tr * dr + ti * di) * idn, gi = R(0.5) * (ti * dr - tr * di) * idn;
 #pragma unroll
     for (int q = 0; q < 2; q++) {
