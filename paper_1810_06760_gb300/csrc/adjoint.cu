@@ -150,8 +150,9 @@ __device__ __forceinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, co
     const R g[3] = {cf[1], cf[2], cf[3]};
     const R H[3][3] = {{cf[4], cf[5], cf[6]}, {cf[5], cf[7], cf[8]}, {cf[6], cf[8], cf[9]}};
     const R P[3] = {y[F_P], y[F_P + 1], y[F_P + 2]};
-    const R ip = Real<R>::rsqrt_(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
-    const R pn = R(1) / ip;
+    const R p2 = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
+    const R ip = Real<R>::rsqrt_(p2);
+    const R pn = p2 * ip;   // |P| as in beam_rhs
     const R Ph[3] = {P[0] * ip, P[1] * ip, P[2] * ip};
     const R cip = c * ip;
     // forward intermediates: u = dzQ g, v = dzP P^, t3 = dzQ H, Z, Z'
@@ -195,7 +196,7 @@ __device__ __forceinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, co
         C2<R> det = {R(0), R(0)};
 #pragma unroll
         for (int j = 0; j < 3; j++) det = cadd(det, cmul(Z[0][j], Cf[0][j]));
-        const R idn = R(1) / (det.r * det.r + det.i * det.i);
+        const R idn = Real<R>::rcp_pos_(det.r * det.r + det.i * det.i);
         const C2<R> idet = {det.r * idn, -det.i * idn};
 #pragma unroll
         for (int a = 0; a < 3; a++)
@@ -234,8 +235,8 @@ __device__ __forceinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, co
         const R fP[3] = {-sg * pn * g[0], -sg * pn * g[1], -sg * pn * g[2]};
         const R s1 = fP[0] * exP[0] + fP[1] * exP[1] + fP[2] * exP[2];
         const R s2 = ref_e1 ? P[0] : P[2];
-        const R D = pn * pn * pn - s2 * s2 * pn;
-        const R iD = R(1) / D;
+        const R D = pn * pn * pn - s2 * s2 * pn;   // |P| |e x P|^2 > 0 (the S frame keeps e off P)
+        const R iD = Real<R>::rcp_pos_(D);
         const R om = -s1 * s2 * iD;
         // a0' = gam a0 - om a1, a1' = gam a1 + om a0
         add2(yb + F_A0, cadd(cconj_mul(gam, fa0), cscale(om, fa1)));
@@ -363,8 +364,8 @@ __device__ __forceinline__ void rhs_vjp(const ModelDev &M, R sg, bool ref_e1, co
 // adjoint of the S frame: Pb += cotangent of P from those of N_sv and N_sh
 template <typename R>
 __device__ __forceinline__ void s_frame_vjp(const R P[3], bool ref_e1, const R Nsvb[3], const R Nshb[3], R Pb[3]) {
-    R Nsv[3], Nsh[3];
-    const R vn = s_frame<R>(P, ref_e1, Nsv, Nsh);
+    R Nsv[3], Nsh[3], iv;
+    s_frame<R>(P, ref_e1, Nsv, Nsh, &iv);
     const R ip = Real<R>::rsqrt_(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
     const R Ph[3] = {P[0] * ip, P[1] * ip, P[2] * ip};
     // N_sv = N_sh x P^: N_sh_b += P^ x N_sv_b, P^_b = N_sv_b x N_sh
@@ -373,7 +374,6 @@ __device__ __forceinline__ void s_frame_vjp(const R P[3], bool ref_e1, const R N
     const R phb[3] = {Nsvb[1] * Nsh[2] - Nsvb[2] * Nsh[1], Nsvb[2] * Nsh[0] - Nsvb[0] * Nsh[2],
                       Nsvb[0] * Nsh[1] - Nsvb[1] * Nsh[0]};
     const R s1 = Nsh[0] * nb[0] + Nsh[1] * nb[1] + Nsh[2] * nb[2];
-    const R iv = R(1) / vn;
     const R vb[3] = {(nb[0] - Nsh[0] * s1) * iv, (nb[1] - Nsh[1] * s1) * iv, (nb[2] - Nsh[2] * s1) * iv};
     // v = e x P: P_b += v_b x e
     if (ref_e1) {
