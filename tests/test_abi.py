@@ -49,3 +49,32 @@ def test_version_and_error_text_without_gpu(built_lib):
     assert L.fga_propagate(None, None, 0.1, 1, None) == 1
     L.fga_last_error(buf, 64)
     assert b"fga_propagate" in buf.value
+
+
+_STRUCTS = {"ModelDesc": "fga_model_desc", "InitDesc": "fga_init_desc", "PointForce": "fga_point_force",
+            "Profile": "fga_profile_t", "ServerDesc": "fga_server_desc", "RequestInfo": "fga_request_info",
+            "ServerStats": "fga_server_stats_t", "Lattice": "fga_lattice", "SolveDesc": "fga_solve_desc"}
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every descriptor the Python binding mirrors with ctypes has the header's size and field offsets (a
+    program compiled against include/fga.h prints them), so a field added to the header and not to the
+    binding, or in another order, fails here rather than as garbage on the GPU."""
+    import subprocess
+    from paper_1810_06760_gb300 import fga
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fga.h"', "int main(void) {"]
+    want = []
+    for py, c in _STRUCTS.items():
+        cls = getattr(fga, py)
+        lines.append(f'    printf("%zu\\n", sizeof({c}));')
+        want.append(ctypes.sizeof(cls))
+        for name, _ in cls._fields_:
+            lines.append(f'    printf("%zu\\n", offsetof({c}, {name}));')
+            want.append(getattr(cls, name).offset)
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert got == want
