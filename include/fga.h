@@ -98,7 +98,8 @@ typedef struct fga_beams fga_beams;
  * c, dc/dx1, dc/dx2, dc/dx3, c_11, c_12, c_13, c_22, c_23, c_33; they are copied into the
  * library's own layout (the caller may free them after the call's stream work completes).
  * Other kinds take NULL.  Errors: INVALID_ARG (kind, sizes, spacing <= 0, nlayers > 8, interface depths
- * not increasing or radii not decreasing, a bad layer_shape), OOM. */
+ * not increasing or radii not decreasing, a bad layer_shape, a layer without c_p > c_s > 0 and rho > 0),
+ * OOM. */
 fga_status fga_model_create(fga_model **out, const fga_model_desc *desc, const float *grid_p,
                             const float *grid_s, fga_stream_t s);
 fga_status fga_model_destroy(fga_model *m);

@@ -415,6 +415,10 @@ fga_status fga_model_create(fga_model **out, const fga_model_desc *d, const floa
         else if (spheres && !(std::isfinite(d->layer_center[0]) && std::isfinite(d->layer_center[1]) &&
                               std::isfinite(d->layer_center[2])))
             bad = "fga_model_create: layer_center is not finite";
+        for (int l = 0; !bad && l < d->nlayers; l++)
+            if (!(std::isfinite(d->layer_cp[l]) && d->layer_cs[l] > 0.0 && d->layer_cp[l] > d->layer_cs[l] &&
+                  d->layer_rho[l] > 0.0 && std::isfinite(d->layer_rho[l])))
+                bad = "fga_model_create: every layer needs finite c_p > c_s > 0 and rho > 0";
         for (int l = 0; !bad && l + 1 < d->nlayers; l++) {
             const double z = d->z_interfaces[l];
             if (!std::isfinite(z) || (spheres && !(z > 0.0)))

@@ -298,16 +298,20 @@ def test_spherical_layers_seismograms(fga, oracle, prec):
 
 def test_layered_model_rejections(fga):
     """Interface depths of planar layers must increase, radii of spherical ones decrease and stay
-    positive; spherical layers take no normal and a finite centre."""
+    positive; spherical layers take no normal and a finite centre; every layer needs c_p > c_s > 0 and
+    rho > 0."""
     base = dict(layer_cp=(5.8, 6.5, 8.0), layer_cs=(3.4, 3.8, 4.4), layer_rho=(2.7, 2.9, 3.3))
     for kw in (dict(z_interfaces=(35.0, 15.0)),
                dict(z_interfaces=(15.0, 15.0)),
                dict(z_interfaces=(25.0, 45.0), layer_shape="spheres"),
                dict(z_interfaces=(10.0, -5.0), layer_shape="spheres"),
                dict(z_interfaces=(45.0, 25.0), layer_shape="spheres", layer_normal=(0.0, 0.0, 1.0)),
-               dict(z_interfaces=(45.0, 25.0), layer_shape="spheres", layer_center=(0.0, float("nan"), 0.0))):
+               dict(z_interfaces=(45.0, 25.0), layer_shape="spheres", layer_center=(0.0, float("nan"), 0.0)),
+               dict(z_interfaces=(15.0, 35.0), layer_cs=(3.4, 0.0, 4.4)),
+               dict(z_interfaces=(15.0, 35.0), layer_cp=(5.8, 3.0, 8.0)),
+               dict(z_interfaces=(15.0, 35.0), layer_rho=(2.7, -1.0, 3.3))):
         with pytest.raises(fga.FGAError) as e:
-            fga.Model("layered", **base, **kw)
+            fga.Model("layered", **{**base, **kw})
         assert e.value.status == fga.FGA_ERR_INVALID_ARG
     m = fga.Model("layered", z_interfaces=(45.0, 25.0), layer_shape="spheres", layer_center=(0.0, 0.0, 60.0), **base)
     m.close()
