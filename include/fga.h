@@ -59,7 +59,7 @@ enum {
 };
 
 /* Shape of the interfaces of a layered medium. */
-enum { FGA_LAYERS_PLANES = 0, FGA_LAYERS_SPHERES = 1 };
+enum { FGA_LAYERS_PLANES = 0, FGA_LAYERS_SPHERES = 1, FGA_LAYERS_UNDULATING = 2 };
 
 /* Velocity model (Eqs. ewe_ps, ps_speed).  Grid media: node (i,j,l) sits at
  * origin + (i*spacing[0], j*spacing[1], l*spacing[2]); positions outside the grid read the nearest
@@ -76,7 +76,13 @@ enum { FGA_LAYERS_PLANES = 0, FGA_LAYERS_SPHERES = 1 };
  * library rotates the beam into the frame whose third axis is the sphere's normal there, applies the
  * flat-interface conditions (Snell's law, continuity of displacement and traction, the dzQ/dzP jump of
  * Eq. Inter_DzQDzP; the curvature of the sphere does not enter), and rotates the children back.  Beams,
- * points and results stay in global coordinates. */
+ * points and results stay in global coordinates.
+ * layer_shape = FGA_LAYERS_UNDULATING: interface i is the surface
+ *   x3 = z_interfaces[i] + layer_amp[i] cos(2 pi x1 / layer_wavelength[0]) cos(2 pi x2 / layer_wavelength[1])
+ * (z_interfaces increasing, wavelengths > 0, and neighbouring surfaces apart: |a_i| + |a_i+1| <
+ * z_i+1 - z_i, so that the layers are not parallel but never touch).  A point lies in the layer given by the
+ * number of surfaces at or above it; a crossing is handled as for spheres, in the frame of the surface's
+ * normal at the crossing point.  layer_normal must be zero. */
 typedef struct {
     int kind;
     double cp0, cs0;
@@ -88,6 +94,8 @@ typedef struct {
     double layer_normal[3];
     int layer_shape;
     double layer_center[3];
+    double layer_amp[8];
+    double layer_wavelength[2];
 } fga_model_desc;
 
 typedef struct fga_model fga_model;
@@ -98,8 +106,8 @@ typedef struct fga_beams fga_beams;
  * c, dc/dx1, dc/dx2, dc/dx3, c_11, c_12, c_13, c_22, c_23, c_33; they are copied into the
  * library's own layout (the caller may free them after the call's stream work completes).
  * Other kinds take NULL.  Errors: INVALID_ARG (kind, sizes, spacing <= 0, nlayers > 8, interface depths
- * not increasing or radii not decreasing, a bad layer_shape, a layer without c_p > c_s > 0 and rho > 0),
- * OOM. */
+ * not increasing or radii not decreasing, a bad layer_shape, a layer without c_p > c_s > 0 and rho > 0,
+ * undulating surfaces that may touch), OOM. */
 fga_status fga_model_create(fga_model **out, const fga_model_desc *desc, const float *grid_p,
                             const float *grid_s, fga_stream_t s);
 fga_status fga_model_destroy(fga_model *m);

@@ -57,6 +57,9 @@ typedef struct {
     const double *zif, *lcp, *lcs, *lrho;
     int shells;             /* layered medium with spherical interfaces |x - ctr| = zif[i] (radii, decreasing) */
     double ctr[3];
+    int undul;              /* layered medium with undulating interfaces x3 = zif[i] + uamp[i] cos(uk0 x1) cos(uk1 x2) */
+    double uk[2];
+    const double *uamp;
 } orc_model;
 
 /* The 10 model fields at a point: c, dc/dx1..3, d2c/dx1dx1, dx1dx2, dx1dx3, dx2dx2, dx2dx3, dx3dx3. */
@@ -104,7 +107,8 @@ static void grid_fields(const orc_model *m, const float *g, const double x[3], d
 }
 
 /* Layer of a point: flat layers by depth x3 (a point on an interface belongs to the deeper layer);
- * spherical layers by the number of spheres that enclose the point (a point on a sphere is inside it). */
+ * spherical layers by the number of spheres that enclose the point (a point on a sphere is inside it);
+ * undulating layers by the number of surfaces at or above the point. */
 static int layer_of(const orc_model *m, const double x[3])
 {
     int l = 0;
@@ -112,6 +116,11 @@ static int layer_of(const orc_model *m, const double x[3])
         const double r = sqrt((x[0] - m->ctr[0]) * (x[0] - m->ctr[0]) + (x[1] - m->ctr[1]) * (x[1] - m->ctr[1]) +
                               (x[2] - m->ctr[2]) * (x[2] - m->ctr[2]));
         while (l < m->nlay - 1 && r <= m->zif[l]) l++;
+        return l;
+    }
+    if (m->undul) {
+        const double cc = cos(m->uk[0] * x[0]) * cos(m->uk[1] * x[1]);
+        while (l < m->nlay - 1 && x[2] >= m->zif[l] + m->uamp[l] * cc) l++;
         return l;
     }
     while (l < m->nlay - 1 && x[2] >= m->zif[l]) l++;
@@ -894,7 +903,7 @@ int orc_layered_step(const orc_model *m, int nb, const double *st_, const int *m
     const orc_state *st = (const orc_state *)st_;
     orc_state *out = (orc_state *)out_;
     int n = 0;
-    if (m->shells) return -1;   /* flat layers only; spherical ones step in fga_oracle.shell_step */
+    if (m->shells || m->undul) return -1;   /* flat layers only; curved ones step in fga_oracle.py */
     for (int b = 0; b < nb; b++) {
         const int mt = meta[b], L = META_LAYER(mt);
         orc_state y = st[b], f0, y1;

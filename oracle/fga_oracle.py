@@ -95,6 +95,7 @@ class _Model(C.Structure):
         ("nlay", C.c_int),
         ("zif", C.c_void_p), ("lcp", C.c_void_p), ("lcs", C.c_void_p), ("lrho", C.c_void_p),
         ("shells", C.c_int), ("ctr", C.c_double * 3),
+        ("undul", C.c_int), ("uk", C.c_double * 2), ("uamp", C.c_void_p),
     ]
 
 
@@ -144,7 +145,7 @@ class Model:
     def __init__(self, kind: str, *, cp0=2.0, cs0=1.0, amp=0.0, cs_ratio=1.0 / math.sqrt(3.0),
                  grid_p=None, grid_s=None, origin=(0, 0, 0), spacing=(1, 1, 1),
                  z_interfaces=(), layer_cp=(), layer_cs=(), layer_rho=(), layer_shape="planes",
-                 layer_center=(0.0, 0.0, 0.0)):
+                 layer_center=(0.0, 0.0, 0.0), layer_amp=(), layer_wavelength=(1.0, 1.0)):
         s = _Model()
         self._keep = []
         s.kind = {"const": 0, "sine": 1, "grid": 2, "layered": 3}[kind]
@@ -167,11 +168,19 @@ class Model:
             self._keep += [zi, lc, ls, lr]
             s.nlay = lc.size
             s.zif, s.lcp, s.lcs, s.lrho = zi.ctypes.data, lc.ctypes.data, ls.ctypes.data, lr.ctypes.data
-            assert layer_shape in ("planes", "spheres")
+            assert layer_shape in ("planes", "spheres", "undulating")
             s.shells = int(layer_shape == "spheres")
             s.ctr[:] = [float(v) for v in layer_center]
             self.radii = zi.copy() if s.shells else None
             self.center = np.array(s.ctr[:], dtype=np.float64)
+            s.undul = int(layer_shape == "undulating")
+            ua = np.zeros(max(zi.size, 1))
+            ua[:len(layer_amp)] = [float(v) for v in layer_amp]
+            self._keep.append(ua)
+            s.uamp = ua.ctypes.data
+            s.uk[:] = [2.0 * math.pi / float(v) for v in layer_wavelength]
+            self.z_interfaces, self.amp = zi.copy(), ua[:zi.size].copy()
+            self.k_und = np.array(s.uk[:], dtype=np.float64)
         self.s = s
         self.kind = kind
 
@@ -497,6 +506,116 @@ def shell_step(model: Model, st: np.ndarray, meta: np.ndarray, path: np.ndarray,
         kids, km = shell_event(model, int(meta[b]), yc, int(lb[b]), rel_min)
         ye = rk4_many(model, kids, km, (1.0 - th[b]) * dt)
         L = int(meta_layer(meta[b]))
+        for k in range(ye.shape[0]):
+            slot = (1 if km[k] & 2 else 0) + (0 if int(meta_layer(km[k])) == L else 2)   # rP, rS, tP, tS
+            out.append(ye[k])
+            mo.append(km[k])
+            po.append(path[b] * 4 + slot + 1)
+            par.append(b)
+    res = (np.array(out).reshape(-1, STATE_DOUBLES), np.array(mo, dtype=np.int32), np.array(po, dtype=np.int64))
+    return res + (np.array(par, dtype=np.int32),) if return_parent else res
+
+
+def surface_height(model: Model, i: int, x: np.ndarray) -> np.ndarray:
+    """Undulating layers: the height x3 of interface i above the points' (x1, x2),
+    z_i + a_i cos(k1 x1) cos(k2 x2) with k_d = 2 pi / wavelength_d."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    k1, k2 = model.k_und
+    return model.z_interfaces[i] + model.amp[i] * np.cos(k1 * x[:, 0]) * np.cos(k2 * x[:, 1])
+
+
+def surface_normal(model: Model, i: int, x) -> np.ndarray:
+    """Unit normal of undulating interface i at the point x (towards larger x3): (-dh/dx1, -dh/dx2, 1)
+    normalised, from the derivatives of the height."""
+    x = np.asarray(x, dtype=np.float64).reshape(3)
+    k1, k2 = model.k_und
+    a = model.amp[i]
+    h1 = -a * k1 * math.sin(k1 * x[0]) * math.cos(k2 * x[1])
+    h2 = -a * k2 * math.cos(k1 * x[0]) * math.sin(k2 * x[1])
+    n = np.array([-h1, -h2, 1.0])
+    return n / np.linalg.norm(n)
+
+
+def surface_layer(model: Model, x: np.ndarray) -> np.ndarray:
+    """Layer of points in undulating layers: the number of interfaces at or above them."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    nl = model.z_interfaces.size
+    return sum((x[:, 2] >= surface_height(model, i, x)).astype(int) for i in range(nl)) if nl else \
+        np.zeros(x.shape[0], dtype=int)
+
+
+def surface_crossing(model: Model, q0: np.ndarray, q1: np.ndarray, layer: np.ndarray):
+    """Undulating layers: where the straight path of one step q0 -> q1 meets an interface bounding its layer.
+    An end point on or below the lower interface (or above the upper one) means a crossing; g(th) = x3(th) -
+    h(x1(th), x2(th)) along the path then changes sign on [0, 1], and the root is found by Brent's method.
+    Should the start already lie beyond the interface (no sign change), the root of g's linear
+    interpolation between the ends is taken, as the flat layers do.  Returns arrays th (NaN: no crossing)
+    and the layer entered, per beam."""
+    from scipy.optimize import brentq
+    q0 = np.asarray(q0, dtype=np.float64).reshape(-1, 3)
+    q1 = np.asarray(q1, dtype=np.float64).reshape(-1, 3)
+    L = np.asarray(layer).reshape(-1)
+    n = q0.shape[0]
+    nl = model.z_interfaces.size + 1
+    th = np.full(n, np.nan)
+    lb = L.copy()
+    for b in range(n):
+        d = q1[b] - q0[b]
+        cand = []
+        for i, down in ((L[b], True), (L[b] - 1, False)):
+            if i < 0 or i > nl - 2:
+                continue
+            g = lambda t, i=i: (q0[b, 2] + t * d[2]) - surface_height(model, i, (q0[b] + t * d)[None])[0]
+            g0, g1 = g(0.0), g(1.0)
+            if (down and g1 >= 0.0) or (not down and g1 < 0.0):
+                if (g0 < 0.0) == down:          # a sign change on [0, 1]
+                    t = brentq(g, 0.0, 1.0, xtol=1e-15, rtol=1e-15, maxiter=200)
+                else:
+                    t = g0 / (g0 - g1)
+                cand.append((t, L[b] + 1 if down else L[b] - 1))
+        if cand:
+            th[b], lb[b] = min(cand, key=lambda v: v[0])
+    return th, lb
+
+
+def surface_event(model: Model, mt: int, state: np.ndarray, i: int, lb: int, rel_min: float = 1e-6):
+    """Children of a beam sitting on undulating interface i: as shell_event, in the frame of the surface's
+    normal at the beam's centre (Sec. 3.1's local tangent-normal coordinates)."""
+    st = np.asarray(state, dtype=np.float64).reshape(1, STATE_DOUBLES)
+    Rm = layer_frame(surface_normal(model, i, st[0, 0:3]))
+    st_l, mt_l = rotate_beams(st, np.array([mt], dtype=np.int32), Rm)
+    kids, km = interface_event(model, int(mt_l[0]), st_l[0], lb, rel_min)
+    if kids.shape[0] == 0:
+        return kids, km
+    return rotate_beams(kids, km, Rm.T)
+
+
+def surface_step(model: Model, st: np.ndarray, meta: np.ndarray, path: np.ndarray, dt: float, gmax: int = 4,
+                 rel_min: float = 1e-6, return_parent: bool = False):
+    """One RK4 step of a medium of undulating layers with interface events, as shell_step: the crossing of
+    surface_crossing, the crossing point put on the surface (x3 = h(x1, x2)), the children of
+    surface_event, each advanced through the rest of the step."""
+    st = np.ascontiguousarray(st, dtype=np.float64)
+    meta = np.ascontiguousarray(meta, dtype=np.int32)
+    path = np.ascontiguousarray(path, dtype=np.int64)
+    y1 = rk4_many(model, st, meta, dt)
+    th, lb = surface_crossing(model, st[:, 0:3], y1[:, 0:3], meta_layer(meta))
+    out, mo, po, par = [], [], [], []
+    for b in range(st.shape[0]):
+        if np.isnan(th[b]):
+            out.append(y1[b])
+            mo.append(meta[b])
+            po.append(path[b])
+            par.append(b)
+            continue
+        if meta_gen(meta[b]) >= gmax:
+            continue
+        L = int(meta_layer(meta[b]))
+        i = min(L, int(lb[b]))
+        yc = rk4_many(model, st[b:b + 1], meta[b:b + 1], th[b] * dt)[0]
+        yc[2] = surface_height(model, i, yc[None, 0:3])[0]
+        kids, km = surface_event(model, int(meta[b]), yc, i, int(lb[b]), rel_min)
+        ye = rk4_many(model, kids, km, (1.0 - th[b]) * dt)
         for k in range(ye.shape[0]):
             slot = (1 if km[k] & 2 else 0) + (0 if int(meta_layer(km[k])) == L else 2)   # rP, rS, tP, tS
             out.append(ye[k])

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libfga_gb300.so")
 SERVE_FIFO, SERVE_SHORTEST = 0, 1
 PREC_FP32, PREC_FP64 = 0, 1
 MEDIUM = {"const": 0, "sine": 1, "grid": 2, "layered": 3}
-LAYER_SHAPE = {"planes": 0, "spheres": 1}
+LAYER_SHAPE = {"planes": 0, "spheres": 1, "undulating": 2}
 EXPORTED = ["fga_model_create", "fga_model_destroy", "fga_decompose", "fga_transform", "fga_propagate", "fga_reconstruct",
             "fga_reconstruct_spherical",
             "fga_reconstruct_lattice", "fga_reconstruct_noalloc", "fga_solve", "fga_beams_count", "fga_beams_export",
@@ -45,7 +45,8 @@ class ModelDesc(C.Structure):
                 ("cs_ratio", C.c_double), ("n", C.c_int * 3), ("origin", C.c_double * 3),
                 ("spacing", C.c_double * 3), ("nlayers", C.c_int), ("z_interfaces", C.c_void_p),
                 ("layer_cp", C.c_void_p), ("layer_cs", C.c_void_p), ("layer_rho", C.c_void_p),
-                ("layer_normal", C.c_double * 3), ("layer_shape", C.c_int), ("layer_center", C.c_double * 3)]
+                ("layer_normal", C.c_double * 3), ("layer_shape", C.c_int), ("layer_center", C.c_double * 3),
+                ("layer_amp", C.c_double * 8), ("layer_wavelength", C.c_double * 2)]
 
 
 class InitDesc(C.Structure):
@@ -193,7 +194,8 @@ class Model:
     def __init__(self, kind: str, *, cp0=2.0, cs0=1.0, amp=0.0, cs_ratio=1.0 / math.sqrt(3.0),
                  grid_p=None, grid_s=None, origin=(0, 0, 0), spacing=(1, 1, 1),
                  z_interfaces=(), layer_cp=(), layer_cs=(), layer_rho=(), layer_normal=(0.0, 0.0, 0.0),
-                 layer_shape="planes", layer_center=(0.0, 0.0, 0.0), stream=None):
+                 layer_shape="planes", layer_center=(0.0, 0.0, 0.0), layer_amp=(), layer_wavelength=(1.0, 1.0),
+                 stream=None):
         d = ModelDesc()
         d.kind = MEDIUM[kind]
         d.cp0, d.cs0, d.amp, d.cs_ratio = cp0, cs0, amp, cs_ratio
@@ -212,6 +214,9 @@ class Model:
             d.layer_normal[:] = [float(v) for v in layer_normal]
             d.layer_shape = LAYER_SHAPE[layer_shape]
             d.layer_center[:] = [float(v) for v in layer_center]
+            amp = [float(v) for v in layer_amp]
+            d.layer_amp[:] = amp + [0.0] * (8 - len(amp))
+            d.layer_wavelength[:] = [float(v) for v in layer_wavelength]
         h = C.c_void_p()
         _check(lib().fga_model_create(C.byref(h), C.byref(d), _dptr(gp), _dptr(gs), _stream(stream)))
         self.grid_shape = tuple(gp.shape[:3]) if gp is not None else None
@@ -236,7 +241,8 @@ def model_from_medium(med, device="cuda") -> Model:
     if med.kind == "layered":
         return Model("layered", z_interfaces=med.z_interfaces, layer_cp=med.layer_cp, layer_cs=med.layer_cs,
                      layer_rho=med.layer_rho, layer_normal=med.layer_normal, layer_shape=med.layer_shape,
-                     layer_center=med.layer_center)
+                     layer_center=med.layer_center, layer_amp=med.layer_amp,
+                     layer_wavelength=med.layer_wavelength)
     if med.kind == "grid":
         gp = torch.as_tensor(med.grid_p, device=device)
         gs = torch.as_tensor(med.grid_s, device=device)

@@ -80,8 +80,10 @@ class Medium:
     layer_cs: Sequence[float] = ()
     layer_rho: Sequence[float] = ()
     layer_normal: Sequence[float] = (0.0, 0.0, 0.0)   # layered: interfaces are normal . x = z_i ((0,0,0): x3)
-    layer_shape: str = "planes"                       # layered: 'planes' or 'spheres' (|x - layer_center| = z_i)
-    layer_center: Sequence[float] = (0.0, 0.0, 0.0)
+    layer_shape: str = "planes"                       # layered: 'planes', 'spheres' (|x - layer_center| = z_i) or
+    layer_center: Sequence[float] = (0.0, 0.0, 0.0)   # 'undulating' (x3 = z_i + a_i cos(2 pi x1/l1) cos(2 pi x2/l2))
+    layer_amp: Sequence[float] = ()
+    layer_wavelength: Sequence[float] = (1.0, 1.0)
 
 
 def sine_fields_on_nodes(n: int, c0: float, amp: float, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:

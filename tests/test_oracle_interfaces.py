@@ -528,3 +528,197 @@ def test_spheres_of_large_radius_reduce_to_tilted_planes(oracle):
     for name, a, b, bar in zip(("Q", "P", "dzQ", "dzP", "a"), e7, e8, (1e-5, 1e-5, 2e-3, 2e-3, 1e-5)):
         assert b < bar, (name, b)
         assert 5.0 < a / b < 20.0, (name, a, b)
+
+
+# ---------------------------------------------------------------------------------------------
+# undulating layers: interfaces x3 = z_i + a_i cos(k1 x1) cos(k2 x2), not parallel to each other
+# ---------------------------------------------------------------------------------------------
+
+def _undulating(O, amp, z=(15.0, 35.0), wl=(20.0, 30.0), cp=(5.8, 6.5, 8.04), cs=(3.46, 3.85, 4.47),
+                rho=(2.72, 2.92, 3.32)):
+    n = len(z) + 1
+    return O.Model("layered", z_interfaces=z, layer_cp=cp[:n], layer_cs=cs[:n], layer_rho=rho[:n],
+                   layer_shape="undulating", layer_amp=amp, layer_wavelength=wl)
+
+
+def _disp_rows(st, mt):
+    out = np.zeros((st.shape[0], 3), complex)
+    for b in range(st.shape[0]):
+        P = st[b, 3:6]
+        a = st[b, 42:48].copy().view(complex)
+        if (mt[b] & 3) < 2:
+            out[b] = a[0] * P / np.linalg.norm(P)
+        elif mt[b] & 8:
+            out[b] = a
+        else:
+            e = np.array([1.0, 0, 0]) if mt[b] & 4 else np.array([0, 0, 1.0])
+            nsh = np.cross(e, P)
+            nsh /= np.linalg.norm(nsh)
+            out[b] = a[0] * np.cross(nsh, P / np.linalg.norm(P)) + a[1] * nsh
+    return out
+
+
+def test_initial_layers_below_undulating_surfaces(oracle):
+    """Beams start in the layer given by the number of interfaces at or above their centre (a centre on an
+    interface belongs to the deeper layer), the interfaces' heights varying along x1 and x2."""
+    O = oracle
+    model = _undulating(O, [3.0, -2.0])
+    for x, want in (((0.0, 0.0, 17.9), 0), ((0.0, 0.0, 18.0), 1), ((10.0, 0.0, 12.1), 1), ((0.0, 0.0, 33.5), 2),
+                    ((5.0, 7.5, 35.0), 2), ((10.0, 0.0, 36.9), 1)):
+        st, mt = _beam(O, model, 0, x, [0.3, 0.2, 0.9])
+        assert int(O.meta_layer(mt)) == want, (x, mt)
+        assert int(O.surface_layer(model, np.array([x]))[0]) == want
+
+
+def _surface_solve(O, model, w, nsteps):
+    from tests.helpers import oracle_beams
+    _, _, obeams = oracle_beams(O, w)
+    st = np.concatenate([b[1] for b in obeams])
+    mt = np.concatenate([b[2] for b in obeams])
+    mid = np.concatenate([np.arange(b[1].shape[0]) for b in obeams])
+    mt = (mt & ~np.int32(0xF0)) | (O.surface_layer(model, st[:, 0:3]).astype(np.int32) << 4)
+    path = np.zeros(st.shape[0], dtype=np.int64)
+    for _ in range(nsteps):
+        st, mt, path, par = O.surface_step(model, st, mt, path, w.dt, return_parent=True)
+        mid = mid[par]
+    return st, mt, mid, path
+
+
+def _lineage_diff(O, A, B):
+    """Relative L2 differences of Q, P, dzQ, dzP and displacement vectors over common lineages."""
+    key = lambda m, i, p: [((int(a) >> 13) & 3, int(b), int(c)) for a, b, c in zip(m, i, p)]
+    ka, kb = key(A[1], A[2], A[3]), key(B[1], B[2], B[3])
+    assert len(set(ka)) == len(ka) and set(ka) == set(kb)
+    ib = {k: i for i, k in enumerate(kb)}
+    o = [ib[k] for k in ka]
+    sa, sb = A[0], B[0][o]
+    np.testing.assert_array_equal(A[1] & 0x6FF3, B[1][o] & 0x6FF3)
+    errs = [np.linalg.norm(sa[:, sl] - sb[:, sl]) / np.linalg.norm(sb[:, sl])
+            for sl in (slice(0, 3), slice(3, 6), slice(6, 24), slice(24, 42))]
+    da, db = _disp_rows(sa, A[1]), _disp_rows(sb, B[1][o])
+    return errs + [np.linalg.norm(da - db) / np.linalg.norm(db)], len(ka)
+
+
+def test_flat_undulating_layers_equal_flat_layers(oracle):
+    """Zero amplitudes make the undulating solve the flat one: the same lineages after 30 steps and the
+    same states to rounding (the crossing by Brent's method on the path instead of the linear formula, the
+    event in the identity frame with S amplitudes in vector form)."""
+    from paper_1810_06760_gb300 import workloads as W
+    from tests.helpers import oracle_beams
+    O = oracle
+    w = W.layered(nq=2, np_=4, ny=20, nsteps=30, dt=0.1)
+    und = _undulating(O, [0.0, 0.0])
+    A = _surface_solve(O, und, w, w.nsteps)
+    flat, _, obeams = oracle_beams(O, w)
+    st = np.concatenate([b[1] for b in obeams])
+    mt = np.concatenate([b[2] for b in obeams])
+    mid = np.concatenate([np.arange(b[1].shape[0]) for b in obeams])
+    path = np.zeros(st.shape[0], dtype=np.int64)
+    for _ in range(w.nsteps):
+        st, mt, path, par = O.layered_step(flat, st, mt, path, w.dt, return_parent=True)
+        mid = mid[par]
+    errs, n = _lineage_diff(O, A, (st, mt, mid, path))
+    assert n > 1.5 * w.n_beams
+    assert max(errs) < 1e-12, errs
+
+
+def test_undulating_layers_converge_to_flat_with_the_amplitude(oracle):
+    """The difference to the flat solve falls linearly with the amplitudes: tenfold from 1e-3 to 1e-4 km
+    (the interface heights move by a, their normals tilt by a k), for centres, propagation vectors,
+    Jacobians and displacement vectors; lineages are the same."""
+    from paper_1810_06760_gb300 import workloads as W
+    O = oracle
+    w = W.layered(nq=2, np_=4, ny=20, nsteps=30, dt=0.1)
+    ref = _surface_solve(O, _undulating(O, [0.0, 0.0]), w, w.nsteps)
+    e3, _ = _lineage_diff(O, _surface_solve(O, _undulating(O, [1e-3, -1e-3]), w, w.nsteps), ref)
+    e4, _ = _lineage_diff(O, _surface_solve(O, _undulating(O, [1e-4, -1e-4]), w, w.nsteps), ref)
+    for a, b in zip(e3, e4):
+        assert 6.0 < a / b < 16.0, (e3, e4)
+    assert max(e4) < 1e-3
+
+
+def test_crossing_of_an_undulating_surface(oracle):
+    """The crossing lies on the surface and inside the step; an end point short of the surface means no
+    crossing; a path leaving upwards crosses the interface above."""
+    O = oracle
+    model = _undulating(O, [3.0, -2.0])
+    q0 = np.array([[4.0, 1.0, 15.0]])
+    q1 = q0 + np.array([[0.4, 0.1, 1.2]])
+    h = O.surface_height(model, 0, q1)[0]
+    assert int(O.surface_layer(model, q0)[0]) == 0 and q1[0, 2] >= h
+    th, lb = O.surface_crossing(model, q0, q1, np.array([0]))
+    x = q0[0] + th[0] * (q1[0] - q0[0])
+    assert 0.0 < th[0] < 1.0 and lb[0] == 1
+    assert abs(x[2] - O.surface_height(model, 0, x[None])[0]) < 1e-12
+    th, _ = O.surface_crossing(model, q0, q0 + np.array([[0.4, 0.1, 0.2]]), np.array([0]))
+    assert np.isnan(th[0])
+    q0 = np.array([[2.0, -1.0, 19.0]])
+    q1 = q0 + np.array([[0.3, 0.2, -3.0]])
+    assert int(O.surface_layer(model, q0)[0]) == 1 and q1[0, 2] < O.surface_height(model, 0, q1)[0]
+    th, lb = O.surface_crossing(model, q0, q1, np.array([1]))
+    x = q0[0] + th[0] * (q1[0] - q0[0])
+    assert lb[0] == 0 and abs(x[2] - O.surface_height(model, 0, x[None])[0]) < 1e-12
+
+
+@pytest.mark.parametrize("cls,down,ang", [(0, True, 0.4), (2, True, 0.3), (3, False, 0.25), (1, False, 0.35)])
+def test_undulating_interface_children_satisfy_welded_continuity(oracle, cls, down, ang):
+    """A beam meets an undulating interface where it slopes (normal tilted by ~30 degrees): its children
+    keep displacement and traction sigma.n continuous across the tangent plane there, keep the tangential
+    part of P and c |P|, and sit on the right sides; a normal taken as e3 instead breaks continuity.  The
+    normal of the checks comes from central differences of the height (agreeing with the oracle's own to
+    1e-8, hence the 1e-9 bars), so a wrong derivative in the oracle fails here."""
+    O = oracle
+    cp, cs, rho = (2.0, 2.6), (1.1, 1.5), (1.3, 1.9)
+    model = _undulating(O, [3.0], z=(15.0,), wl=(20.0, 30.0), cp=cp, cs=cs, rho=rho)
+    x = np.array([5.0, 3.0, 0.0])
+    x[2] = O.surface_height(model, 0, x[None])[0]
+    # the normal from central differences of the height, not from the oracle's own derivative
+    eps = 1e-5
+    hx = lambda dx, dy: O.surface_height(model, 0, (x + [dx, dy, 0.0])[None])[0]
+    n = np.array([-(hx(eps, 0) - hx(-eps, 0)) / (2 * eps), -(hx(0, eps) - hx(0, -eps)) / (2 * eps), 1.0])
+    n /= np.linalg.norm(n)
+    assert n[2] < 0.9                                    # a sloping part of the surface
+    assert np.linalg.norm(O.surface_normal(model, 0, x) - n) < 1e-8
+    t = np.cross(n, [0.0, 1.0, 0.0])
+    t /= np.linalg.norm(t)
+    sgn = -1.0 if cls & 1 else 1.0
+    p = sgn * 0.9 * ((1.0 if down else -1.0) * math.cos(ang) * n + math.sin(ang) * t)
+    lay = 0 if down else 1
+    st, mt = _vector_beam(O, model, cls, x - 0.05 * sgn * p, p)
+    assert int(O.meta_layer(mt[0])) == lay
+    st = st[0].copy()
+    st[0:3] = x
+    kids, km = O.surface_event(model, int(mt[0]), st, 0, 1 - lay, rel_min=0.0)
+    assert len(kids) == 4
+    lam = [r * (a * a - 2 * b * b) for r, a, b in zip(rho, cp, cs)]
+    mu = [r * b * b for r, b in zip(rho, cs)]
+
+    def disp(row, m):
+        a = row[42:48].copy().view(complex)
+        return a[0] * row[3:6] / np.linalg.norm(row[3:6]) if (m & 3) < 2 else a
+
+    U_in = disp(st, int(mt[0]))
+    du, dtr = U_in.copy(), _traction_n(lam[lay], mu[lay], st[3:6], U_in, n)
+    T_in = dtr.copy()
+    cin = (cs if cls >= 2 else cp)[lay] * np.linalg.norm(st[3:6])
+    tang = st[3:6] - np.dot(st[3:6], n) * n
+    for k, m in zip(kids, km):
+        L = int(O.meta_layer(m))
+        s = 1.0 if L == lay else -1.0
+        U = disp(k, int(m))
+        du += s * U
+        dtr += s * _traction_n(lam[L], mu[L], k[3:6], U, n)
+        np.testing.assert_allclose(k[3:6] - np.dot(k[3:6], n) * n, tang, atol=1e-9)
+        np.testing.assert_allclose((cs if m & 2 else cp)[L] * np.linalg.norm(k[3:6]), cin, rtol=1e-13)
+        travel = (-1.0 if m & 1 else 1.0) * np.dot(k[3:6], n)       # speed towards larger depth
+        assert (travel > 0) == (L == 1)
+    assert np.linalg.norm(du) <= 1e-9 * np.linalg.norm(U_in), du
+    assert np.linalg.norm(dtr) <= 1e-9 * np.linalg.norm(T_in), dtr
+    # the same event with the normal taken as e3 (a flat reading of the sloping surface) is not welded
+    st_l, mt_l = O.to_vector_form(st[None], np.array([mt[0]], dtype=np.int32))
+    bad, bm = O.interface_event(model, int(mt_l[0]), st_l[0], 1 - lay, rel_min=0.0)
+    dtb = _traction_n(lam[lay], mu[lay], st[3:6], U_in, n)
+    for k, m in zip(bad, bm):
+        L = int(O.meta_layer(m))
+        dtb += (1.0 if L == lay else -1.0) * _traction_n(lam[L], mu[L], k[3:6], disp(k, int(m)), n)
+    assert np.linalg.norm(dtb) > 1e-3 * np.linalg.norm(T_in)
