@@ -559,7 +559,12 @@ def surface_crossing(model: Model, q0: np.ndarray, q1: np.ndarray, layer: np.nda
     nl = model.z_interfaces.size + 1
     th = np.full(n, np.nan)
     lb = L.copy()
-    for b in range(n):
+    # beams whose end point lies beyond an interface of their layer (the others have no crossing)
+    beyond = np.zeros(n, dtype=bool)
+    for i in range(nl - 1):
+        g1 = q1[:, 2] - surface_height(model, i, q1)
+        beyond |= ((L == i) & (g1 >= 0.0)) | ((L == i + 1) & (g1 < 0.0))
+    for b in np.nonzero(beyond)[0]:
         d = q1[b] - q0[b]
         cand = []
         for i, down in ((L[b], True), (L[b] - 1, False)):

@@ -402,16 +402,19 @@ fga_status fga_model_create(fga_model **out, const fga_model_desc *d, const floa
             set_error("fga_model_create: layered medium needs 1..8 layers and their arrays");
             return FGA_ERR_INVALID_ARG;
         }
-        const bool spheres = d->layer_shape == FGA_LAYERS_SPHERES;
+        const bool spheres = d->layer_shape == FGA_LAYERS_SPHERES, undul = d->layer_shape == FGA_LAYERS_UNDULATING;
         const double *nv = d->layer_normal;
         const double nn = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
         const char *bad = nullptr;
-        if (d->layer_shape != FGA_LAYERS_PLANES && !spheres)
-            bad = "fga_model_create: layer_shape must be FGA_LAYERS_PLANES or FGA_LAYERS_SPHERES";
+        if (d->layer_shape != FGA_LAYERS_PLANES && !spheres && !undul)
+            bad = "fga_model_create: layer_shape must be FGA_LAYERS_PLANES, _SPHERES or _UNDULATING";
         else if (!std::isfinite(nn))
             bad = "fga_model_create: layer_normal is not finite";
-        else if (spheres && nn != 0.0)
-            bad = "fga_model_create: spherical layers take no layer_normal";
+        else if ((spheres || undul) && nn != 0.0)
+            bad = "fga_model_create: curved layers take no layer_normal";
+        else if (undul && !(d->layer_wavelength[0] > 0.0 && d->layer_wavelength[1] > 0.0 &&
+                            std::isfinite(d->layer_wavelength[0]) && std::isfinite(d->layer_wavelength[1])))
+            bad = "fga_model_create: undulating layers need finite wavelengths > 0";
         else if (spheres && !(std::isfinite(d->layer_center[0]) && std::isfinite(d->layer_center[1]) &&
                               std::isfinite(d->layer_center[2])))
             bad = "fga_model_create: layer_center is not finite";
@@ -426,6 +429,11 @@ fga_status fga_model_create(fga_model **out, const fga_model_desc *d, const floa
             else if (l > 0 && (spheres ? !(z < d->z_interfaces[l - 1]) : !(z > d->z_interfaces[l - 1])))
                 bad = spheres ? "fga_model_create: sphere radii must decrease strictly"
                               : "fga_model_create: interface depths must increase strictly";
+            else if (undul && !std::isfinite(d->layer_amp[l]))
+                bad = "fga_model_create: layer_amp is not finite";
+            else if (undul && l > 0 &&
+                     !(std::fabs(d->layer_amp[l - 1]) + std::fabs(d->layer_amp[l]) < z - d->z_interfaces[l - 1]))
+                bad = "fga_model_create: neighbouring undulating interfaces may touch";
         }
         if (bad) {
             delete m;
@@ -445,6 +453,9 @@ fga_status fga_model_create(fga_model **out, const fga_model_desc *d, const floa
         }
         m->dev.shells = spheres ? 1 : 0;
         for (int c = 0; c < 3; c++) m->dev.ctr[c] = spheres ? d->layer_center[c] : 0.0;
+        m->dev.undul = undul ? 1 : 0;
+        for (int l = 0; l + 1 < d->nlayers; l++) m->dev.uamp[l] = undul ? d->layer_amp[l] : 0.0;
+        for (int c = 0; c < 2; c++) m->dev.uk[c] = undul ? 2.0 * M_PI / d->layer_wavelength[c] : 0.0;
         // the layer frame of planar layers: third axis the normal (frame_from_normal)
         const double n3[3] = {nn > 0 ? nv[0] / nn : 0.0, nn > 0 ? nv[1] / nn : 0.0, nn > 0 ? nv[2] / nn : 1.0};
         m->dev.tilted = (n3[0] != 0.0 || n3[1] != 0.0 || n3[2] != 1.0) ? 1 : 0;

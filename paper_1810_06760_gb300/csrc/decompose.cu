@@ -203,18 +203,28 @@ __device__ __forceinline__ void beam_init_state(const ModelDev &Md, const C2<R> 
     R q[3] = {(R)qd[0], (R)qd[1], (R)qd[2]};
     R p[3] = {(R)pd[0], (R)pd[1], (R)pd[2]};
     R cf[10];
-    // layered media are evaluated at the depth along the layer normal (x3 unless the layers are tilted),
-    // or at minus the distance to the centre of spherical layers
-    double zl = qd[2];
-    if (MED == FGA_MEDIUM_LAYERED && Md.shells) {
-        const double r0 = qd[0] - Md.ctr[0], r1 = qd[1] - Md.ctr[1], r2 = qd[2] - Md.ctr[2];
-        zl = -sqrt(r0 * r0 + r1 * r1 + r2 * r2);
-    } else if (MED == FGA_MEDIUM_LAYERED && Md.tilted) {
-        zl = Md.R[6] * qd[0] + Md.R[7] * qd[1] + Md.R[8] * qd[2];
-    }
-    {
-        const R qe[3] = {q[0], q[1], MED == FGA_MEDIUM_LAYERED ? (R)zl : q[2]};
-        model_eval<R, MED>(Md, wave, qe, cf);
+    // layered media: the layer of q from its depth along the layer normal (x3 unless the layers are tilted),
+    // minus its distance to the centre of spherical layers, or the undulating interfaces at or above it;
+    // c(q) is that layer's speed
+    int lay = 0;
+    if (MED == FGA_MEDIUM_LAYERED) {
+        if (Md.undul) {
+            const double cc = cos(Md.uk[0] * qd[0]) * cos(Md.uk[1] * qd[1]);
+            for (int l = 0; l < Md.nlay - 1; l++) lay += (qd[2] >= Md.zif[l] + Md.uamp[l] * cc) ? 1 : 0;
+        } else {
+            double zl = qd[2];
+            if (Md.shells) {
+                const double r0 = qd[0] - Md.ctr[0], r1 = qd[1] - Md.ctr[1], r2 = qd[2] - Md.ctr[2];
+                zl = -sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+            } else if (Md.tilted) {
+                zl = Md.R[6] * qd[0] + Md.R[7] * qd[1] + Md.R[8] * qd[2];
+            }
+            for (int l = 0; l < Md.nlay - 1; l++) lay += (zl >= Md.zif[l]) ? 1 : 0;
+        }
+        cf[0] = wave ? mp<R>(Md.lcs[lay], Md.flcs[lay]) : mp<R>(Md.lcp[lay], Md.flcp[lay]);
+        for (int f = 1; f < 10; f++) cf[f] = R(0);
+    } else {
+        model_eval<R, MED>(Md, wave, q, cf);
     }
     const R pn = Real<R>::sqrt_(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
     const R sgn = (cls & 1) ? R(-1) : R(1);
@@ -246,11 +256,7 @@ __device__ __forceinline__ void beam_init_state(const ModelDev &Md, const C2<R> 
         amp[2 * j] = a0 * R(0.5) * (fr - gsc * gi);
         amp[2 * j + 1] = a0 * R(0.5) * (fi + gsc * gr);
     }
-    if (MED == FGA_MEDIUM_LAYERED) {
-        int l = 0;
-        for (int q = 0; q < Md.nlay - 1; q++) l += (zl >= Md.zif[q]) ? 1 : 0;
-        fl |= (l << 4) | (cls << FL_ROOT_SHIFT);
-    }
+    if (MED == FGA_MEDIUM_LAYERED) fl |= (lay << 4) | (cls << FL_ROOT_SHIFT);
     for (int f = 0; f < NF; f++) y[f] = R(0);
     for (int d = 0; d < 3; d++) {
         y[F_Q + d] = q[d];

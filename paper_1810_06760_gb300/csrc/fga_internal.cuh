@@ -60,9 +60,13 @@ struct ModelDev {
     // depth -|x - ctr| orders the layers as x3 does for flat ones)
     int shells;
     double ctr[3];
+    // undulating layers: interface i is x3 = zif[i] + uamp[i] cos(uk[0] x1) cos(uk[1] x2)
+    int undul;
+    double uamp[MAX_LAYERS], uk[2];
     // FP32 copies of the scalar parameters: the FP32 kernels read these and never convert from
     // double (FP64 instructions are very slow on this GPU)
     float fcp0, fcs0, famp, fcs_ratio, fo[3], finv_h[3], fzif[MAX_LAYERS], flcp[MAX_LAYERS], flcs[MAX_LAYERS];
+    float fuamp[MAX_LAYERS], fuk[2];
     void fill_f32() {
         fcp0 = (float)cp0;
         fcs0 = (float)cs0;
@@ -72,7 +76,10 @@ struct ModelDev {
             fo[d] = (float)o[d];
             finv_h[d] = (float)inv_h[d];
         }
+        fuk[0] = (float)uk[0];
+        fuk[1] = (float)uk[1];
         for (int l = 0; l < MAX_LAYERS; l++) {
+            fuamp[l] = (float)uamp[l];
             fzif[l] = (float)zif[l];
             flcp[l] = (float)lcp[l];
             flcs[l] = (float)lcs[l];

@@ -1,5 +1,5 @@
-// A7: beams in a medium of homogeneous layers (Sec. 3.1) between parallel planes or concentric
-// spheres.  Inside a layer grad c = 0, so a beam moves on a straight line; a step that crosses an
+// A7: beams in a medium of homogeneous layers (Sec. 3.1) between parallel planes, concentric spheres or
+// undulating surfaces.  Inside a layer grad c = 0, so a beam moves on a straight line; a step that crosses an
 // interface is split at the crossing, where the beam is replaced by its reflected and transmitted P and
 // S children (Snell's law, plane-wave continuity of displacement and traction, and the dzQ/dzP jump of
 // Eq. Inter_DzQDzP; at a sphere all of it in the local tangent-normal frame of the crossing point), and
@@ -416,6 +416,92 @@ __device__ __forceinline__ bool shell_clear(const ModelDev &M, int L, const floa
 }
 __device__ __forceinline__ bool shell_clear(const ModelDev &, int, const double *, const double *) { return false; }
 
+// Undulating layers: height of interface i above (x1, x2), and its slopes dh/dx1, dh/dx2.
+__device__ __forceinline__ double surf_h(const ModelDev &M, int i, double x1, double x2) {
+    return M.zif[i] + M.uamp[i] * cos(M.uk[0] * x1) * cos(M.uk[1] * x2);
+}
+__device__ __forceinline__ void surf_grad(const ModelDev &M, int i, double x1, double x2, double &h1, double &h2) {
+    double s1, c1, s2, c2;
+    sincos(M.uk[0] * x1, &s1, &c1);
+    sincos(M.uk[1] * x2, &s2, &c2);
+    h1 = -M.uamp[i] * M.uk[0] * s1 * c2;
+    h2 = -M.uamp[i] * M.uk[1] * c1 * s2;
+}
+
+// FP32 screen for undulating layers: true when the end point q1 lies clearly between the interfaces that
+// bound layer L (by a margin far above the FP32 rounding of the heights, which grows with the phase
+// k |x| of the cosines).
+__device__ __forceinline__ bool surf_clear(const ModelDev &M, int L, const float *q1) {
+    const float cc = cosf(M.fuk[0] * q1[0]) * cosf(M.fuk[1] * q1[1]);
+    const float ph = M.fuk[0] * fabsf(q1[0]) + M.fuk[1] * fabsf(q1[1]);
+    if (L < M.nlay - 1) {
+        const float h = M.fzif[L] + M.fuamp[L] * cc;
+        const float m = 1e-4f * (1.0f + fabsf(M.fzif[L]) + fabsf(M.fuamp[L])) + 2e-6f * fabsf(M.fuamp[L]) * ph;
+        if (!(q1[2] < h - m)) return false;
+    }
+    if (L > 0) {
+        const float h = M.fzif[L - 1] + M.fuamp[L - 1] * cc;
+        const float m = 1e-4f * (1.0f + fabsf(M.fzif[L - 1]) + fabsf(M.fuamp[L - 1])) + 2e-6f * fabsf(M.fuamp[L - 1]) * ph;
+        if (!(q1[2] >= h + m)) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ bool surf_clear(const ModelDev &, int, const double *) { return false; }
+
+// Undulating layers: the first crossing of the straight path q0 -> q1 of one step with an interface that
+// bounds layer L.  An end point on or below the lower interface (above the upper one) means a crossing;
+// g(th) = x3(th) - h(x1(th), x2(th)) then changes sign on [0, 1] and its root is found by Newton's method
+// kept inside a shrinking bracket (bisection where a Newton step leaves it; at most 100 iterations).  A
+// start already beyond the interface (no sign change) takes the root of g's linear interpolation.
+// Returns false without a crossing, else th, the layer lb entered and the interface index.
+__device__ bool surf_crossing(const ModelDev &M, int L, const double q0[3], const double q1[3], double &th, int &lb,
+                              int &iface) {
+    const double d[3] = {q1[0] - q0[0], q1[1] - q0[1], q1[2] - q0[2]};
+    bool hit = false;
+    for (int side = 0; side < 2; side++) {
+        const bool down = side == 0;
+        const int i = down ? L : L - 1;
+        if (i < 0 || i > M.nlay - 2) continue;
+        const double g0 = q0[2] - surf_h(M, i, q0[0], q0[1]), g1 = q1[2] - surf_h(M, i, q1[0], q1[1]);
+        if (down ? !(g1 >= 0.0) : !(g1 < 0.0)) continue;
+        double t;
+        if ((g0 < 0.0) == down) {
+            double lo = 0.0, hi = 1.0, glo = g0;   // g(lo) and g(hi) of opposite signs
+            t = g0 / (g0 - g1);
+            for (int it = 0; it < 100 && hi - lo > 1e-15; it++) {
+                const double x1 = q0[0] + t * d[0], x2 = q0[1] + t * d[1];
+                const double g = q0[2] + t * d[2] - surf_h(M, i, x1, x2);
+                if (g == 0.0) break;
+                if ((g < 0.0) == (glo < 0.0)) {
+                    lo = t;
+                    glo = g;
+                } else {
+                    hi = t;
+                }
+                double h1, h2;
+                surf_grad(M, i, x1, x2, h1, h2);
+                const double dg = d[2] - h1 * d[0] - h2 * d[1];
+                double tn = dg != 0.0 ? t - g / dg : 0.5 * (lo + hi);
+                if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+                if (fabs(tn - t) < 1e-16) {
+                    t = tn;
+                    break;
+                }
+                t = tn;
+            }
+        } else {
+            t = g0 / (g0 - g1);
+        }
+        if (!hit || t < th) {
+            th = t;
+            lb = down ? L + 1 : L - 1;
+            iface = i;
+            hit = true;
+        }
+    }
+    return hit;
+}
+
 }  // namespace
 
 // Write child ce (with its Q compensation) of the beam in slot b: the first child takes the parent's slot,
@@ -441,34 +527,48 @@ __device__ void store_child(R *__restrict__ st, int32_t *__restrict__ flags, int
     path[dst] = pp * 4 + slot + 1;
 }
 
-// The interface event of beam b in spherical layers, at fraction th of the step where it enters layer lb
-// through the sphere of radius rho.  The beam (still unchanged in st) advances to the crossing, which is
-// put on the sphere in FP64 (its FP32 rounding goes to the Q compensation), and is rotated into the local
-// frame whose third axis is the sphere's outward normal there; the flat-interface event runs in that frame
-// (Sec. 3.1: the tangent plane stands in for the interface), and every child is rotated back and finishes
-// the step.  Kept out of line and reading its beam from memory, so that the step kernel's state stays in
-// registers.
-template <typename R>
-__device__ __noinline__ void shell_event_step(const ModelDev &M, R *__restrict__ st, int32_t *__restrict__ flags,
-                                              int32_t *__restrict__ ids, long long *__restrict__ path, int64_t cap,
-                                              unsigned long long *__restrict__ counts, R dt, double rel_min, int64_t b,
-                                              int fl, R sg, R c, double th, int lb, double rho) {
+// The interface event of beam b in curved layers (SHAPE 1: spheres, SHAPE 2: undulating interfaces), at
+// fraction th of the step where it enters layer lb through the sphere of radius rho or through interface
+// iface.  The beam (still unchanged in st) advances to the crossing, which is put on the interface in FP64
+// (radially onto the sphere, vertically onto the undulating surface; its FP32 rounding goes to the Q
+// compensation), and is rotated into the local frame whose third axis is the interface's normal there; the
+// flat-interface event runs in that frame (Sec. 3.1: the tangent plane stands in for the interface), and
+// every child is rotated back and finishes the step.  Kept out of line and reading its beam from memory, so
+// that the step kernel's state stays in registers.
+template <typename R, int SHAPE>
+__device__ __noinline__ void curved_event_step(const ModelDev &M, R *__restrict__ st, int32_t *__restrict__ flags,
+                                               int32_t *__restrict__ ids, long long *__restrict__ path, int64_t cap,
+                                               unsigned long long *__restrict__ counts, R dt, double rel_min, int64_t b,
+                                               int fl, R sg, R c, double th, int lb, double rho, int iface) {
     R y[NF], yc[NF], qc[3];
     for (int f = 0; f < NF; f++) y[f] = st[(int64_t)f * cap + b];
     for (int d = 0; d < 3; d++) qc[d] = st[(int64_t)(F_QC + d) * cap + b];
     layer_rk4<R>(sg, c, y, (R)th * dt, yc, qc);
-    double s[3], sn = 0.0;
-    for (int d = 0; d < 3; d++) {
-        s[d] = (double)yc[F_Q + d] - (double)qc[d] - M.ctr[d];
-        sn += s[d] * s[d];
+    double x[3], nrm[3], Rl[9];
+    for (int d = 0; d < 3; d++) x[d] = (double)yc[F_Q + d] - (double)qc[d];
+    if (SHAPE == 1) {
+        double s[3], sn = 0.0;
+        for (int d = 0; d < 3; d++) {
+            s[d] = x[d] - M.ctr[d];
+            sn += s[d] * s[d];
+        }
+        sn = sqrt(sn);
+        for (int d = 0; d < 3; d++) {
+            nrm[d] = s[d] / sn;
+            x[d] = M.ctr[d] + rho * nrm[d];
+        }
+    } else {
+        x[2] = surf_h(M, iface, x[0], x[1]);
+        double h1, h2;
+        surf_grad(M, iface, x[0], x[1], h1, h2);
+        const double nn = sqrt(1.0 + h1 * h1 + h2 * h2);
+        nrm[0] = -h1 / nn;
+        nrm[1] = -h2 / nn;
+        nrm[2] = 1.0 / nn;
     }
-    sn = sqrt(sn);
-    double nrm[3], Rl[9];
     for (int d = 0; d < 3; d++) {
-        nrm[d] = s[d] / sn;
-        const double x = M.ctr[d] + rho * nrm[d];
-        yc[F_Q + d] = (R)x;
-        qc[d] = (R)((double)yc[F_Q + d] - x);
+        yc[F_Q + d] = (R)x[d];
+        qc[d] = (R)((double)yc[F_Q + d] - x[d]);
     }
     frame_from_normal(nrm, Rl);
     int fll = fl;
@@ -495,7 +595,7 @@ __device__ __noinline__ void shell_event_step(const ModelDev &M, R *__restrict__
 
 // One step for every beam alive at the start of the step (n_begin = *counts); children beyond the
 // first are appended at *counts (atomic); overflow beyond cap is counted in counts[1].
-template <typename R, bool SHELLS>
+template <typename R, int SHAPE>
 __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__restrict__ st, int32_t *__restrict__ flags,
                                                           int32_t *__restrict__ ids, long long *__restrict__ path,
                                                           int64_t cap, const int64_t *__restrict__ n_begin,
@@ -514,20 +614,22 @@ __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__rest
     for (int d = 0; d < 3; d++) qc1[d] = qc[d] = st[(int64_t)(F_QC + d) * cap + b];
     const R c = layer_speed<R>(M, wave, L);
     layer_rk4<R>(sg, c, y, dt, y1, qc1);
-    if (SHELLS) {
-        // FP32: a step that stays clear of every sphere of its layer (by a margin of 1e-5 of r^2, far above
-        // the rounding of the screen) is decided by the screen; the rest take the exact FP64 test
+    if (SHAPE != 0) {
+        // FP32: a step that stays clear of the interfaces of its layer (by a margin far above the rounding of
+        // the screen) is decided by the screen; the rest take the exact FP64 test
         bool hit = false;
         double th = 0.0, rho = 0.0;
-        int lb = L;
-        if (!(sizeof(R) == 4 && shell_clear(M, L, y + F_Q, y1 + F_Q))) {
+        int lb = L, iface = 0;
+        const bool clear = sizeof(R) == 4 && (SHAPE == 1 ? shell_clear(M, L, y + F_Q, y1 + F_Q)
+                                                          : surf_clear(M, L, y1 + F_Q));
+        if (!clear) {
             double q0[3], q1[3];
 #pragma unroll
             for (int d = 0; d < 3; d++) {
                 q0[d] = (double)y[F_Q + d] - (double)qc[d];
                 q1[d] = (double)y1[F_Q + d] - (double)qc1[d];
             }
-            hit = shell_crossing(M, L, q0, q1, th, lb, rho);
+            hit = SHAPE == 1 ? shell_crossing(M, L, q0, q1, th, lb, rho) : surf_crossing(M, L, q0, q1, th, lb, iface);
         }
         if (!hit) {
 #pragma unroll
@@ -537,7 +639,8 @@ __global__ void __launch_bounds__(128) layered_step_kernel(ModelDev M, R *__rest
         } else if (((fl >> 8) & 15) >= gmax) {
             flags[b] = fl | FL_DEAD;
         } else {
-            shell_event_step<R>(M, st, flags, ids, path, cap, counts, dt, rel_min, b, fl, sg, c, th, lb, rho);
+            curved_event_step<R, SHAPE>(M, st, flags, ids, path, cap, counts, dt, rel_min, b, fl, sg, c, th, lb, rho,
+                                        iface);
         }
         return;
     }
@@ -598,9 +701,11 @@ fga_status launch_layered_steps(const fga_model *m, fga_beams *b, double dt, int
         }
         prof_add_beam_steps(b->nb);
         ProfScope ps(P_PROP, s);
-        // spherical layers in their own instantiation, so that the planar kernel carries none of their code
-        auto kd = m->dev.shells ? layered_step_kernel<double, true> : layered_step_kernel<double, false>;
-        auto kf = m->dev.shells ? layered_step_kernel<float, true> : layered_step_kernel<float, false>;
+        // curved layers in their own instantiations, so that the planar kernel carries none of their code
+        auto kd = m->dev.shells ? layered_step_kernel<double, 1>
+                                : (m->dev.undul ? layered_step_kernel<double, 2> : layered_step_kernel<double, 0>);
+        auto kf = m->dev.shells ? layered_step_kernel<float, 1>
+                                : (m->dev.undul ? layered_step_kernel<float, 2> : layered_step_kernel<float, 0>);
         if (b->precision == FGA_PREC_FP64)
             kd<<<blocks, T, 0, s>>>(m->dev, b->state.as<double>(), b->flags.as<int32_t>(), b->id.as<int32_t>(),
                                     b->path.as<long long>(), b->cap, b->n_begin.as<int64_t>(),

@@ -285,6 +285,21 @@ def shells(nq: int = 4, np_: int = 6, ny: int = 32, nsteps: int = 60, dt: float 
                     w.rw, None, None, None)
 
 
+def undulating(nq: int = 4, np_: int = 6, ny: int = 32, nsteps: int = 60, dt: float = 0.05, n_times: int = 12,
+               rx_side: int = 8, extent: float = 40.0, amp=(3.0, -2.0), wavelength=(20.0, 30.0),
+               classes=(0, 1, 2, 3)) -> Workload:
+    """The 3-layer crust of ``layered`` with undulating interfaces x3 = z_i + a_i cos(2 pi x1/l1) cos(2 pi x2/l2),
+    z = (15, 35) km, a = amp (opposite signs by default, so the layer between them thickens and thins:
+    the interfaces are not parallel), wavelengths (20, 30) km.  Same source, meshes and surface receivers."""
+    w = layered(nq=nq, np_=np_, ny=ny, nsteps=nsteps, dt=dt, n_times=n_times, rx_side=rx_side, extent=extent,
+                classes=classes)
+    med = Medium("layered", z_interfaces=w.medium.z_interfaces, layer_cp=w.medium.layer_cp,
+                 layer_cs=w.medium.layer_cs, layer_rho=w.medium.layer_rho, layer_shape="undulating",
+                 layer_amp=tuple(amp), layer_wavelength=tuple(wavelength))
+    return Workload("undulating", w.k, med, w.ny, w.y0, w.dy, w.f, None, w.mesh, w.classes, w.dt, w.nsteps, w.times,
+                    w.receivers, w.rw, None, w.rx_axes, None)
+
+
 def _bump_fields(fields: np.ndarray, n: int, centre, sigma: float, eps: float, lo: float = 0.0,
                  hi: float = 1.0) -> np.ndarray:
     """Fields (c, grad c, Hess c) of c * (1 + eps exp(-|x - centre|^2 / (2 sigma^2))) by the product rule,

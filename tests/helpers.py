@@ -5,7 +5,8 @@ import numpy as np
 def oracle_model(O, med):
     if med.kind == "layered":
         return O.Model("layered", z_interfaces=med.z_interfaces, layer_cp=med.layer_cp, layer_cs=med.layer_cs,
-                       layer_rho=med.layer_rho, layer_shape=med.layer_shape, layer_center=med.layer_center)
+                       layer_rho=med.layer_rho, layer_shape=med.layer_shape, layer_center=med.layer_center,
+                       layer_amp=med.layer_amp, layer_wavelength=med.layer_wavelength)
     return O.Model(med.kind, cp0=med.cp0, cs0=med.cs0, amp=med.amp, cs_ratio=med.cs_ratio,
                    grid_p=med.grid_p, grid_s=med.grid_s, origin=med.origin, spacing=med.spacing)
 

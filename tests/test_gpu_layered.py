@@ -315,3 +315,88 @@ def test_layered_model_rejections(fga):
         assert e.value.status == fga.FGA_ERR_INVALID_ARG
     m = fga.Model("layered", z_interfaces=(45.0, 25.0), layer_shape="spheres", layer_center=(0.0, 0.0, 60.0), **base)
     m.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# undulating layers: interfaces x3 = z_i + a_i cos(k1 x1) cos(k2 x2), not parallel to each other
+# ---------------------------------------------------------------------------------------------
+
+def _oracle_undulating(O, w, nsteps, times=None, x=None):
+    """The oracle's undulating-layer solve (surface_step: crossings by Brent's method, events in the frame
+    of the surface normal), with the sums at step-end samples."""
+    omodel, mesh, obeams = oracle_beams(O, w)
+    st = np.concatenate([b[1] for b in obeams])
+    meta = np.concatenate([b[2] for b in obeams])
+    mid = np.concatenate([np.arange(b[1].shape[0]) for b in obeams])
+    path = np.zeros(st.shape[0], dtype=np.int64)
+    wgt = mesh.weight(w.k)
+    ref = None if times is None else np.zeros((len(times), x.shape[0], 3), complex)
+    j = 0
+    for n in range(1, nsteps + 1):
+        st, meta, path, parent = O.surface_step(omodel, st, meta, path, w.dt, return_parent=True)
+        mid = mid[parent]
+        while times is not None and j < len(times) and abs(times[j] - n * w.dt) < 1e-9:
+            ref[j] = O.gauss_sum(O.records(st, meta, wgt), w.k, w.rw, x)
+            j += 1
+    return st, meta, mid, path, ref
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_undulating_layers_population_matches_oracle(fga, oracle, prec):
+    """Beams of a medium whose two interfaces undulate with opposite amplitudes (3 and -2 km over
+    wavelengths of 20 and 30 km) after 30 steps, against the oracle's solve (Brent's method for the
+    crossings, its own frames and vector-form S amplitudes): lineages, centres, propagation vectors,
+    Jacobians and displacement vectors, at the bars of the tilted and spherical layers."""
+    w = W.undulating(nq=3, np_=4, ny=24, nsteps=30, dt=0.1)
+    model, desc, keep = gpu_setup(w, prec)
+    beams = fga.decompose(model, desc)
+    fga.propagate(model, beams, w.dt, w.nsteps)
+    gst, gmeta, gmid, gpath, dropped = beams.export_all()
+    ost, ometa, omid, opath, _ = _oracle_undulating(oracle, w, w.nsteps)
+    assert dropped == 0
+    gk, ok = _key(gmeta, gmid, gpath), _key(ometa, omid, opath)
+    assert len(set(ok)) == len(ok) and len(set(gk)) == len(gk)
+    common = sorted(set(gk) & set(ok))
+    need = 1.0 if prec == 1 else 0.999
+    assert len(common) >= need * len(ok) and len(common) >= need * len(gk), (len(common), len(ok), len(gk))
+    assert len(ok) > 1.5 * w.n_beams
+    gi = {k: i for i, k in enumerate(gk)}
+    oi = {k: i for i, k in enumerate(ok)}
+    G = np.stack([gst[gi[k]] for k in common])
+    Ob = np.stack([ost[oi[k]] for k in common])
+    gm = np.array([gmeta[gi[k]] for k in common])
+    om = np.array([ometa[oi[k]] for k in common])
+    np.testing.assert_array_equal(gm & 0x6FF3, om & 0x6FF3)
+    for name in ("Q", "P", "dzQ", "dzP"):
+        bar = 5e-4 if (prec == 0 and name in ("dzQ", "dzP")) else TOL[prec]
+        assert rel_l2(G[:, GROUPS[name]], Ob[:, GROUPS[name]]) <= bar, name
+    assert rel_l2(_disp(G, gm), _disp(Ob, om)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_undulating_layers_seismograms(fga, oracle, prec):
+    """fga_solve with undulating interfaces at surface receivers over 40 steps against the oracle."""
+    import torch
+    w = W.undulating(nq=3, np_=4, ny=24, nsteps=40, dt=0.1, n_times=8, rx_side=6)
+    model, desc, keep = gpu_setup(w, prec)
+    rx = torch.as_tensor(w.receivers, device="cuda")
+    seis, _ = fga.solve(model, desc, w.dt, w.nsteps, w.times, rx, rw=w.rw)
+    torch.cuda.synchronize()
+    *_, ref = _oracle_undulating(oracle, w, w.nsteps, w.times, w.receivers)
+    got = seis.cpu().numpy()
+    assert np.abs(ref).max() > 0
+    assert rel_l2(got, ref) <= TOL[prec], rel_l2(got, ref)
+    assert max_rel_dominant(got, ref, 1e-2) <= (2e-3 if prec == 0 else 1e-9)
+
+
+def test_undulating_model_rejections(fga):
+    """Undulating interfaces that may touch, a wavelength <= 0 and a normal given with them are refused."""
+    base = dict(layer_cp=(5.8, 6.5, 8.0), layer_cs=(3.4, 3.8, 4.4), layer_rho=(2.7, 2.9, 3.3),
+                z_interfaces=(15.0, 35.0), layer_shape="undulating")
+    for kw in (dict(layer_amp=(12.0, -9.0)), dict(layer_amp=(3.0, 2.0), layer_wavelength=(20.0, 0.0)),
+               dict(layer_amp=(3.0, 2.0), layer_normal=(0.0, 0.0, 1.0)),
+               dict(layer_amp=(float("inf"), 2.0))):
+        with pytest.raises(fga.FGAError) as e:
+            fga.Model("layered", **{**base, **kw})
+        assert e.value.status == fga.FGA_ERR_INVALID_ARG
+    fga.Model("layered", **{**base, "layer_amp": (3.0, -2.0), "layer_wavelength": (20.0, 30.0)}).close()
