@@ -65,6 +65,9 @@ def parse():
                          "35 km, 10^3 q x 8^3 p x 4 classes (2.05 M beams) with psi selection 1e-6, 120 s at "
                          "dt = 0.01 s (12,000 steps), 256 surface stations (16 x 16 over +-300 km) every 0.1 s; "
                          "plus the FP32 error against FP64 on a 5^3 q x 4^3 p stride sample of it")
+    ap.add_argument("--undulating", action="store_true",
+                    help="with --layered: the interfaces undulate, x3 = 15 + 3 cos(2 pi x1/20) cos(2 pi x2/30) and "
+                         "35 - 2 cos(...) cos(...) km (not parallel)")
     ap.add_argument("--shells", type=float, default=0.0, metavar="RC",
                     help="with --layered: the same crust bent into concentric spheres about (0, 0, RC) km (radii "
                          "RC - 15 and RC - 35; e.g. 6371 for the Earth), stations on the sphere r = RC")
@@ -746,7 +749,8 @@ def run_layered(args):
         model.close()
         return seis, e0.elapsed_time(e1), prof
 
-    make = (lambda **kw: W.shells(rc=args.shells, **kw)) if args.shells > 0 else W.layered
+    make = (lambda **kw: W.shells(rc=args.shells, **kw)) if args.shells > 0 else \
+        (W.undulating if args.undulating else W.layered)
     w = make(**sizes)
     warm = make(**dict(sizes, nsteps=100, n_times=10))    # the same kernels and buffers, 100 steps
     for _ in range(args.warmup):
@@ -777,6 +781,8 @@ def run_layered(args):
             "dtype": "f32" if prec == fga.PREC_FP32 else "f64", "data": "synthetic",
             "config": {"workload": (f"spherical crust (spheres r = {args.shells - 15:g}, {args.shells - 35:g} km about "
                                     f"(0, 0, {args.shells:g})), " if args.shells > 0 else
+                                    "undulating crust (interfaces 15 + 3 cc, 35 - 2 cc km, cc = cos(2 pi x1/20) "
+                                    "cos(2 pi x2/30)), " if args.undulating else
                                     "layered crust (interfaces 15, 35 km), ") +
                                    f"explosive source at 10 km, k = {w.k:.3f}/km, "
                                    f"{w.mesh.nq}^3 q x {w.mesh.np_}^3 p x 4 classes, psi selection 1e-6, "
