@@ -549,7 +549,8 @@ def surface_crossing(model: Model, q0: np.ndarray, q1: np.ndarray, layer: np.nda
     An end point on or below the lower interface (or above the upper one) means a crossing; g(th) = x3(th) -
     h(x1(th), x2(th)) along the path then changes sign on [0, 1], and the root is found by Brent's method.
     Should the start already lie beyond the interface (no sign change), the root of g's linear
-    interpolation between the ends is taken, as the flat layers do.  Returns arrays th (NaN: no crossing)
+    interpolation between the ends is taken, as the flat layers do (the start itself when g is the same at
+    both ends).  Returns arrays th (NaN: no crossing)
     and the layer entered, per beam."""
     from scipy.optimize import brentq
     q0 = np.asarray(q0, dtype=np.float64).reshape(-1, 3)
@@ -576,7 +577,7 @@ def surface_crossing(model: Model, q0: np.ndarray, q1: np.ndarray, layer: np.nda
                 if (g0 < 0.0) == down:          # a sign change on [0, 1]
                     t = brentq(g, 0.0, 1.0, xtol=1e-15, rtol=1e-15, maxiter=200)
                 else:
-                    t = g0 / (g0 - g1)
+                    t = g0 / (g0 - g1) if g0 != g1 else 0.0
                 cand.append((t, L[b] + 1 if down else L[b] - 1))
         if cand:
             th[b], lb[b] = min(cand, key=lambda v: v[0])

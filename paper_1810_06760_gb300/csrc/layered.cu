@@ -452,7 +452,8 @@ __device__ __forceinline__ bool surf_clear(const ModelDev &, int, const double *
 // bounds layer L.  An end point on or below the lower interface (above the upper one) means a crossing;
 // g(th) = x3(th) - h(x1(th), x2(th)) then changes sign on [0, 1] and its root is found by Newton's method
 // kept inside a shrinking bracket (bisection where a Newton step leaves it; at most 100 iterations).  A
-// start already beyond the interface (no sign change) takes the root of g's linear interpolation.
+// start already beyond the interface (no sign change) takes the root of g's linear interpolation (the start
+// itself when g does not change along the path).
 // Returns false without a crossing, else th, the layer lb entered and the interface index.
 __device__ bool surf_crossing(const ModelDev &M, int L, const double q0[3], const double q1[3], double &th, int &lb,
                               int &iface) {
@@ -490,7 +491,7 @@ __device__ bool surf_crossing(const ModelDev &M, int L, const double q0[3], cons
                 t = tn;
             }
         } else {
-            t = g0 / (g0 - g1);
+            t = g0 != g1 ? g0 / (g0 - g1) : 0.0;   // no motion across the surface: the start itself
         }
         if (!hit || t < th) {
             th = t;
