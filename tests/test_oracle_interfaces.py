@@ -722,3 +722,53 @@ def test_undulating_interface_children_satisfy_welded_continuity(oracle, cls, do
         L = int(O.meta_layer(m))
         dtb += (1.0 if L == lay else -1.0) * _traction_n(lam[L], mu[L], k[3:6], disp(k, int(m)), n)
     assert np.linalg.norm(dtb) > 1e-3 * np.linalg.norm(T_in)
+
+
+def _flux_n(model_cp, model_cs, rho, st, mt, lay, n):
+    """rho c |A|^2 |P.n|/|P|: the energy flux of a beam's plane wave through a plane of normal n (per
+    omega^2 / 2)."""
+    P = st[3:6]
+    a = st[42:48].copy().view(complex)
+    wave = (mt & 3) >= 2
+    A2 = float(np.sum(np.abs(a) ** 2)) if (wave and (mt & 8)) else abs(a[0]) ** 2 + (abs(a[1]) ** 2 if wave else 0.0)
+    c = (model_cs if wave else model_cp)[lay]
+    return rho[lay] * c * A2 * abs(np.dot(P, n)) / np.linalg.norm(P)
+
+
+@pytest.mark.parametrize("shape", ["spheres", "undulating"])
+@pytest.mark.parametrize("cls,ang", [(0, 0.3), (0, 0.9), (2, 0.2), (3, 0.6), (1, 0.5)])
+def test_curved_interface_energy_flux_balance(oracle, shape, cls, ang):
+    """At a sphere or a sloping undulating surface, the energy flux of the incident wave through the tangent
+    plane equals the sum over the propagating children, below and beyond the critical angles (a
+    post-critical child is not created and carries no normal flux)."""
+    O = oracle
+    cp, cs, rho = (2.0, 2.6), (1.1, 1.5), (1.3, 1.9)
+    if shape == "spheres":
+        c = np.array([0.4, -0.3, 2.0])
+        model = _spheres(O, c, [1.5], cp=cp, cs=cs, rho=rho)
+        u = np.array([-0.36, 0.48, -0.8])
+        x = c + 1.5 * u
+        n = u                                             # outward; layer 0 outside
+        inward = -n                                       # towards layer 1
+    else:
+        model = _undulating(O, [3.0], z=(15.0,), cp=cp, cs=cs, rho=rho)
+        x = np.array([5.0, 3.0, 0.0])
+        x[2] = O.surface_height(model, 0, x[None])[0]
+        n = O.surface_normal(model, 0, x)                 # towards larger x3, layer 1
+        inward = n
+    t = np.cross(n, [0.0, 1.0, 0.0])
+    t /= np.linalg.norm(t)
+    sgn = -1.0 if cls & 1 else 1.0
+    p = sgn * 0.9 * (math.cos(ang) * inward + math.sin(ang) * t)     # travels from layer 0 into layer 1
+    st, mt = _vector_beam(O, model, cls, x - 0.05 * sgn * p, p)
+    assert int(O.meta_layer(mt[0])) == 0
+    st = st[0].copy()
+    st[0:3] = x
+    if shape == "spheres":
+        kids, km = O.shell_event(model, int(mt[0]), st, 1, rel_min=0.0)
+    else:
+        kids, km = O.surface_event(model, int(mt[0]), st, 0, 1, rel_min=0.0)
+    assert len(kids) >= 2
+    e_in = _flux_n(cp, cs, rho, st, int(mt[0]), 0, n)
+    e_out = sum(_flux_n(cp, cs, rho, k, int(m), int(O.meta_layer(m)), n) for k, m in zip(kids, km))
+    np.testing.assert_allclose(e_out, e_in, rtol=1e-10)
