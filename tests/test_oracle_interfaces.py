@@ -772,3 +772,44 @@ def test_curved_interface_energy_flux_balance(oracle, shape, cls, ang):
     e_in = _flux_n(cp, cs, rho, st, int(mt[0]), 0, n)
     e_out = sum(_flux_n(cp, cs, rho, k, int(m), int(O.meta_layer(m)), n) for k, m in zip(kids, km))
     np.testing.assert_allclose(e_out, e_in, rtol=1e-10)
+
+
+@pytest.mark.parametrize("shape", ["spheres", "undulating"])
+def test_curved_interface_children_stay_symplectic(oracle, shape):
+    """The children of an event at a sphere or a sloping undulating surface, rotated back to global
+    coordinates, keep the Jacobian (dzQ, dzP) symplectic and Z^-1 dzQ symmetric, as at a flat interface:
+    rotating the rows of dzQ and dzP by one orthogonal map preserves both, and a rotation applied to one of
+    them only would not."""
+    O = oracle
+    cp, cs, rho = (2.0, 2.6), (1.1, 1.5), (1.3, 1.9)
+    if shape == "spheres":
+        c = np.array([0.4, -0.3, 2.0])
+        model = _spheres(O, c, [1.5], cp=cp, cs=cs, rho=rho)
+        n = np.array([-0.36, 0.48, -0.8])
+        x = c + 1.5 * n
+        inward = -n
+    else:
+        model = _undulating(O, [3.0], z=(15.0,), cp=cp, cs=cs, rho=rho)
+        x = np.array([5.0, 3.0, 0.0])
+        x[2] = O.surface_height(model, 0, x[None])[0]
+        inward = O.surface_normal(model, 0, x)
+    t = np.cross(inward, [0.0, 1.0, 0.0])
+    t /= np.linalg.norm(t)
+    p = 0.9 * (math.cos(0.35) * inward + math.sin(0.35) * t)
+    st, mt = _vector_beam(O, model, 2, x - 0.3 * p, p)
+    O.propagate(model, st, mt, 0.05, 6)                 # dzQ, dzP away from their initial values
+    st = st[0].copy()
+    st[0:3] = x
+    if shape == "spheres":
+        kids, km = O.shell_event(model, int(mt[0]), st, 1, rel_min=0.0)
+    else:
+        kids, km = O.surface_event(model, int(mt[0]), st, 0, 1, rel_min=0.0)
+    assert len(kids) == 4
+    Om = np.block([[np.zeros((3, 3)), np.eye(3)], [-np.eye(3), np.zeros((3, 3))]])
+    for k in kids:
+        DQ = k[6:24].view(complex).reshape(3, 3)
+        DP = k[24:42].view(complex).reshape(3, 3)
+        J = np.block([[DQ.real.T, -DQ.imag.T], [DP.real.T, -DP.imag.T]])
+        np.testing.assert_allclose(J.T @ Om @ J, Om, atol=1e-11)
+        S = np.linalg.solve(DQ + 1j * DP, DQ)
+        np.testing.assert_allclose(S, S.T, atol=1e-11)
